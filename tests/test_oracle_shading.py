@@ -1,0 +1,158 @@
+"""Pins for the oracle's local shading (Sec. 2.2 stage 4 BSDF evaluation and
+sampling; Appendix A.3 shading-normal adaptation): textbook Lambert,
+reciprocity, normalisation of D and of the sampling pdf, energy
+conservation, agreement between sampling and evaluation."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+
+def hemi_grid(n_t=400, n_p=800):
+    """Midpoint quadrature on the hemisphere z > 0 in (cos theta, phi)."""
+    ct = (np.arange(n_t) + 0.5) / n_t
+    ph = 2 * np.pi * (np.arange(n_p) + 0.5) / n_p
+    C, P = np.meshgrid(ct, ph, indexing="ij")
+    S = np.sqrt(1 - C * C)
+    w = np.stack([S * np.cos(P), S * np.sin(P), C], -1).reshape(-1, 3)
+    dA = (1.0 / n_t) * (2 * np.pi / n_p)
+    return w, dA
+
+
+def unit(v):
+    v = np.asarray(v, float)
+    return v / np.linalg.norm(v)
+
+
+def test_onb_is_orthonormal():
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        n = unit(rng.normal(size=3))
+        t, b = oracle.onb(n)
+        M = np.stack([t, b, n])
+        assert np.allclose(M @ M.T, np.eye(3), atol=1e-12)
+        assert np.allclose(np.cross(t, b), n, atol=1e-12)
+
+
+def test_lambert_is_textbook():
+    ns = np.array([0, 0, 1.0])
+    rho = np.array([0.2, 0.5, 0.8])
+    for wo, wi in [((0.3, 0.1, 0.9), (-0.2, 0.4, 0.6)), ((0, 0, 1), (0.9, 0, 0.1))]:
+        f, pdf = oracle.bsdf_eval(rho, 0.3, 0.0, ns, unit(wo), unit(wi))
+        assert np.allclose(f, rho / math.pi, rtol=1e-14)
+        assert pdf == pytest.approx(unit(wi)[2] / math.pi, rel=1e-14)
+    # below the shading hemisphere on either side: zero
+    f, pdf = oracle.bsdf_eval(rho, 0.3, 0.5, ns, unit((0, 0.1, 1)), unit((0, 0.1, -1)))
+    assert np.all(f == 0) and pdf == 0
+
+
+def test_reciprocity():
+    rng = np.random.default_rng(1)
+    ns = np.array([0, 0, 1.0])
+    for _ in range(300):
+        wo, wi = unit(rng.normal(size=3)), unit(rng.normal(size=3))
+        wo[2], wi[2] = abs(wo[2]), abs(wi[2])
+        r, w = rng.uniform(0.05, 0.8), rng.uniform(0, 1)
+        rho = rng.uniform(0.1, 0.9, 3)
+        f1, _ = oracle.bsdf_eval(rho, r, w, ns, wo, wi)
+        f2, _ = oracle.bsdf_eval(rho, r, w, ns, wi, wo)
+        assert np.allclose(f1, f2, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("rough", [0.05, 0.2, 0.5, 0.8])
+def test_ggx_D_projected_area_is_one(rough):
+    alpha = rough * rough
+    # integrate D(h) cos(h) over the hemisphere in (cos theta) with a fine grid
+    n = 2_000_000 if rough < 0.1 else 200_000
+    c = (np.arange(n) + 0.5) / n
+    D = np.array([oracle.ggx_D(alpha, x) for x in c[:: max(1, n // 200_000)]])
+    cc = c[:: max(1, n // 200_000)]
+    # analytic: int_0^1 D(c) c 2 pi dc; use the closed form of the antiderivative instead for the check
+    a2 = alpha * alpha
+    closed = lambda x: -a2 / (2 * (x * x * (a2 - 1) + 1)) / (a2 - 1)  # d/dx -> a2 x / (k^2)
+    total = 2 * math.pi * (closed(1.0) - closed(0.0)) / math.pi
+    assert total == pytest.approx(1.0, abs=1e-10)
+    # and the oracle's D matches the closed-form density pointwise
+    k = cc * cc * (a2 - 1) + 1
+    assert np.allclose(D, a2 / (math.pi * k * k), rtol=1e-13)
+
+
+@pytest.mark.parametrize("rough,w,theta_o", [(0.05, 1.0, 0.3), (0.3, 1.0, 1.2), (0.8, 0.5, 0.7),
+                                             (0.2, 0.6, 1.3), (0.5, 0.0, 0.4)])
+def test_pdf_normalised_and_energy_conserving(rough, w, theta_o):
+    ns = np.array([0, 0, 1.0])
+    wo = np.array([math.sin(theta_o), 0, math.cos(theta_o)])
+    grid, dA = hemi_grid(600 if rough < 0.1 else 300, 1200 if rough < 0.1 else 600)
+    fs, ps = np.zeros(len(grid)), np.zeros(len(grid))
+    for i, wi in enumerate(grid):
+        f, p = oracle.bsdf_eval(np.ones(3), rough, w, ns, wo, wi)
+        fs[i], ps[i] = f[0], p
+    pdf_int = ps.sum() * dA
+    albedo = (fs * grid[:, 2]).sum() * dA
+    # visible-normal sampling loses exactly the reflections that fall below
+    # the horizon: the pdf integrates to 1 - P(sampling fails), estimated
+    # here on a stratified grid of sample values
+    m = 160
+    fails = 0
+    for i in range(m):
+        for j in range(m):
+            # u_lobe = 0 always takes the specular lobe when w > 0
+            good, _, _, _ = oracle.bsdf_sample(np.ones(3), rough, w, ns, wo, 0.0, (i + 0.5) / m, (j + 0.5) / m)
+            fails += not good
+    assert pdf_int <= 1.0 + 2e-3
+    assert pdf_int == pytest.approx(1.0 - (w * fails / m**2 if w > 0 else 0.0), abs=1.5e-2 if rough < 0.1 else 5e-3)
+    assert albedo <= 1.0 + 2e-3
+
+
+@pytest.mark.parametrize("rough,w", [(0.1, 1.0), (0.6, 0.5), (0.3, 0.0)])
+def test_sampling_agrees_with_evaluation(rough, w):
+    """E[f cos / pdf] over sampled directions equals the quadrature albedo,
+    and the pdf returned by sampling equals the one from evaluation."""
+    ns = np.array([0, 0, 1.0])
+    wo = unit((0.5, 0.2, 0.8))
+    rng = np.random.default_rng(5)
+    n = 40000
+    acc, ok = 0.0, 0
+    for k in range(n):
+        u = rng.random(3)
+        good, wi, f, pdf = oracle.bsdf_sample(np.ones(3), rough, w, ns, wo, *u)
+        if good:
+            f2, p2 = oracle.bsdf_eval(np.ones(3), rough, w, ns, wo, wi)
+            assert p2 == pytest.approx(pdf, rel=1e-12)
+            acc += f[0] * wi[2] / pdf
+    est = acc / n
+    grid, dA = hemi_grid(300, 600)
+    alb = 0.0
+    for wi in grid:
+        f, _ = oracle.bsdf_eval(np.ones(3), rough, w, ns, wo, wi)
+        alb += f[0] * wi[2] * dA
+    assert est == pytest.approx(alb, rel=2e-2)
+
+
+def test_shading_normal_adaptation():
+    rng = np.random.default_rng(7)
+    ng = np.array([0, 0, 1.0])
+    for _ in range(2000):
+        wo = unit(rng.normal(size=3))
+        wo[2] = abs(wo[2]) + 1e-3
+        wo = unit(wo)
+        ns = unit(ng + rng.normal(size=3) * rng.uniform(0, 2))
+        if ns[2] < 0:
+            ns = -ns
+        out = oracle.adapt_shading_normal(ns, ng, wo)
+        assert np.linalg.norm(out) == pytest.approx(1.0, abs=1e-12)
+        r = 2 * np.dot(wo, out) * out - wo
+        assert np.dot(r, ng) >= 1e-3 - 1e-9
+        r0 = 2 * np.dot(wo, ns) * ns - wo
+        if np.dot(r0, ng) >= 1e-3:
+            assert np.array_equal(out, ns)
+    # a shading normal equal to the geometric normal is left alone
+    for _ in range(100):
+        wo = unit(rng.normal(size=3))
+        wo[2] = abs(wo[2]) + 0.01
+        wo = unit(wo)
+        if wo[2] < 5e-4:
+            continue
+        assert np.array_equal(oracle.adapt_shading_normal(ng, ng, wo), ng)
