@@ -1,0 +1,304 @@
+"""Benchmark of the GB300 QMC path tracer.
+
+Workload (default): the 1,000,000-triangle sphere field (200 noise-displaced
+tessellated spheres on a displaced plane, GGX + Lambert layered materials,
+256 emissive triangles, 2048 x 1024 procedural sky) rendered at 1920 x 1080,
+64 samples per pixel, max depth 16. One step = one full render of that
+configuration (132,710,400 camera paths) through rt_render. Inputs are
+synthetic and seeded (scenes.sphere_field).
+
+Prints ONE JSON line (rank 0). Multi-GPU (torchrun): every rank renders its
+own disjoint iteration range (weak scaling, no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpaths/s"
+UNIT = "Mpaths/s"
+WORKLOAD = "sphere-field 1M tris, 1920x1080, 64 spp, depth 16"
+SPP, DEPTH = 64, 16
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_oracle(sd, cam, seconds_target=15.0):
+    """The FP64 oracle as it stands, on all host cores, on a bounded sample of
+    the workload: the full scene at reduced resolution, 1 spp, depth 16."""
+    import oracle
+    t0 = time.time()
+    osc = oracle.Scene(sd)
+    build_s = time.time() - t0
+    from paper_1705_01263_gb300 import scenes as sc_mod
+    W, H = 480, 270
+    spp = 1
+    c2 = sc_mod.Camera(cam.eye, cam.look_at, cam.up, cam.vfov_deg, W, H)
+    t0 = time.time()
+    _, _, cnt, rays = osc.render(c2, spp, DEPTH)
+    dt = time.time() - t0
+    paths = int(cnt.sum())
+    cores = os.cpu_count() or 1
+    return {"value": paths / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{W}x{H} px x {spp} spp of the same scene and camera (depth {DEPTH}), "
+                      f"{paths} paths in {dt:.1f} s; oracle BVH build {build_s:.1f} s not timed",
+            "mrays_per_s": rays / dt / 1e6}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    from paper_1705_01263_gb300 import scenes
+    sd, cam = scenes.sphere_field()
+    import oracle
+    osc = oracle.Scene(sd)
+    W, H = 240, 135
+    c2 = scenes.Camera(cam.eye, cam.look_at, cam.up, cam.vfov_deg, W, H)
+    for _ in range(args.warmup):
+        osc.render(c2, 1, DEPTH)
+    times, paths = [], 0
+    for k in range(args.steps):
+        t0 = time.time()
+        _, _, cnt, _ = osc.render(c2, 1, DEPTH, iter0=k)
+        times.append(time.time() - t0)
+        paths += int(cnt.sum())
+    total = sum(times)
+    v = paths / total / 1e6
+    cores = os.cpu_count() or 1
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "reference_sample": f"{W}x{H} px, 1 spp per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{W}x{H} px x 1 spp per step of the same scene/camera, depth {DEPTH}"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--spp", type=int, default=SPP)
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1705_01263_gb300 import rt, scenes
+    rt.lib()
+    sd, cam = scenes.sphere_field()
+    scene = rt.Scene(sd)
+    film = rt.Film(cam.width, cam.height)
+    stream = torch.cuda.current_stream()
+    # each rank renders a disjoint iteration range: rank r starts at pass r * 10^6
+    base_iter = rank * 1_000_000
+    opts_plain = rt.make_opts(seed=0)
+    l2_flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    WH = cam.width * cam.height
+
+    def render_step(stats=None, profile=0):
+        o = rt.make_opts(seed=0, stats=stats, profile=profile)
+        rt.rt_render(scene, cam, args.spp, DEPTH, film, o)
+
+    film.seek(base_iter)
+    for _ in range(args.warmup):
+        render_step()
+    torch.cuda.synchronize()
+    # instrumented pass (not timed): traversal work per ray for the roofline
+    wstats = rt.rt_stats()
+    render_step(wstats, profile=2)
+    torch.cuda.synchronize()
+    # timed steps: device time per step with CUDA events on the render stream,
+    # L2 flushed between steps (outside the events)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, stats_list = [], []
+    with ClockSampler(local) as clk:
+        t_wall0 = time.time()
+        for k in range(args.steps):
+            l2_flush.zero_()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s = rt.rt_stats()
+            ev0.record(stream)
+            rt.rt_render(scene, cam, args.spp, DEPTH, film, rt.make_opts(seed=0, stats=s, profile=1))
+            ev1.record(stream)
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+            stats_list.append(s)
+        torch.cuda.synchronize()
+        t_wall = time.time() - t_wall0
+    if dist:
+        dist.barrier()
+    tot_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([tot_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    paths_per_step = WH * args.spp
+    value = paths_per_step * args.steps * world / (tot_ms / 1e3) / 1e6
+    ext = sum(s.extension_rays for s in stats_list)
+    shd = sum(s.shadow_rays for s in stats_list)
+    mrays = (ext + shd) * world / (tot_ms / 1e3) / 1e6
+    launches = sum(s.kernel_launches for s in stats_list)
+    # roofline of the dominant kernel (closest-hit traversal)
+    trace_ms = sum(s.trace_ms for s in stats_list)
+    tl = sum(s.trace_launches for s in stats_list)
+    ext_rays_timed = ext
+    nodes_per_ray = wstats.ext_nodes / max(1, wstats.extension_rays)
+    tris_per_ray = wstats.ext_tris / max(1, wstats.extension_rays)
+    bytes_per_ray = nodes_per_ray * 80 + tris_per_ray * 48 + 32 + 16 + 4
+    # per launch: bytes of all rays of all launches / their total device time
+    achieved_gbs = ext_rays_timed * bytes_per_ray / (trace_ms / 1e3) / 1e9 if trace_ms > 0 else None
+    hbm, bf16, peak_src = peaks()
+    shares = {"trace_ext": sum(s.trace_ms for s in stats_list), "shade": sum(s.shade_ms for s in stats_list),
+              "trace_shadow": sum(s.shadow_ms for s in stats_list),
+              "megakernel": sum(s.megakernel_ms for s in stats_list), "other": sum(s.other_ms for s in stats_list)}
+    # end to end through the public API with host buffers: camera in, image out
+    mean_dev = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+    host_img = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, pin_memory=True)
+    cam_bytes = 48
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for k in range(max(2, args.steps // 2)):
+        l2_flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rt.rt_render(scene, cam, args.spp, DEPTH, film, rt.make_opts(seed=0))
+        film.resolve(mean_dev)
+        host_img.copy_(mean_dev, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_value = paths_per_step * world / (statistics.mean(e2e_ms) / 1e3) / 1e6
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_oracle(sd, cam)
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded generators; the paper's scenes are not available)",
+            "config": {"workload": WORKLOAD, "triangles": sd.num_triangles, "width": cam.width,
+                       "height": cam.height, "spp": args.spp, "max_depth": DEPTH,
+                       "paths_per_step": paths_per_step, "l2": "flushed between steps (256 MiB write)",
+                       "film": "FP64 sums", "parallelism": f"weak: {world} rank(s), disjoint iteration ranges"},
+            "mrays_per_s": mrays,
+            "rays_per_path": (ext + shd) / (paths_per_step * args.steps),
+            "roofline": {"bound": "hbm", "kernel": "k_trace_ext (closest-hit BVH8 traversal)",
+                         "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": (achieved_gbs / hbm) if achieved_gbs else None, "traffic": None,
+                         "peak_source": f"{peak_src} hbm_gbs",
+                         "bytes_per_ray": bytes_per_ray, "nodes_per_ray": nodes_per_ray,
+                         "tris_per_ray": tris_per_ray, "launches": tl,
+                         "avg_launch_ms": trace_ms / max(1, tl)},
+            "kernel_ms_share": {k: v / max(1e-9, sum(shares.values())) for k, v in shares.items()},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": cam_bytes,
+                    "d2h_bytes_per_step": cam.width * cam.height * 3 * 4},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "wall_s": t_wall,
+        }
+        s = json.dumps(line)
+        print(s, flush=True)
+        if args.out:
+            with open(args.out, "w") as f:
+                f.write(s + "\n")
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,266 @@
+/*
+ * rt.h - C ABI of the GB300 consistent quasi-Monte Carlo path tracer.
+ *
+ * The library implements the data-parallel hot path of the light transport
+ * simulation described in "The Iray Light Transport Simulation and Rendering
+ * System" (Keller et al., arXiv:1705.01263): forward path tracing with next
+ * event estimation combined by multiple importance sampling (Sec. 2),
+ * importance sampling of triangle emitters and of the environment (Sec. 2.1),
+ * a generic layered BSDF (Sec. 2.2), a wavefront state machine with
+ * structure-of-arrays sample state, just-in-time queues, regeneration and a
+ * megakernel tail (Sec. 3.1), per-pixel FP64 accumulation and sample counts
+ * (Sec. 3.2.2, Appendix A.4), filter importance sampling (Appendix A.1),
+ * integer-exact scrambled Halton sampling with 64-bit indices (Appendix A.2)
+ * and local shading-normal adaptation (Appendix A.3).
+ *
+ * Conventions for every entry point:
+ *   - All functions return rt_status; RT_OK (0) on success. On failure a
+ *     message is available from rt_last_error() (thread-local, valid until the
+ *     next call on the same thread). No C++ exception crosses this boundary.
+ *   - "device" pointers are CUDA global-memory addresses on the current
+ *     device; "host" pointers are ordinary CPU memory. The caller owns every
+ *     buffer it passes in; the library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Calls that take a stream are asynchronous on it unless stated.
+ *   - Handles (rt_scene, rt_film, rt_guide) own device memory allocated by the
+ *     library and are released by their destroy function.
+ *   - Kernels never trap: overflow of a fixed-size structure is reported as a
+ *     status (RT_STACK_OVERFLOW, RT_QUEUE_OVERFLOW) and device-side waits are
+ *     bounded (RT_TIMEOUT).
+ */
+#ifndef RT_GB300_H
+#define RT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RT_OK = 0,
+    RT_INVALID_ARG = 1,
+    RT_OOM = 2,
+    RT_CUDA_ERROR = 3,
+    RT_TIMEOUT = 4,          /* time budget or abort flag: film is consistent and resumable */
+    RT_QUEUE_OVERFLOW = 5,
+    RT_STACK_OVERFLOW = 6,
+    RT_NOT_SUPPORTED = 7
+} rt_status;
+
+typedef struct rt_scene rt_scene;
+typedef struct rt_film rt_film;
+typedef struct rt_guide rt_guide;
+
+/* Scene description (all HOST pointers, copied by rt_scene_create).
+ * Triangles are the only geometry and the only emitters (Sec. 2.1.1). A
+ * triangle's geometric normal is normalize(cross(v1 - v0, v2 - v0)); emitters
+ * radiate on that side only. Materials are the fixed layered model
+ *   f = ggx_weight * f_GGX(roughness) + (1 - ggx_weight) * albedo / pi
+ * (Sec. 2.2 names a generic layered BSDF without formulas). Emission of a
+ * material is `emission` (RGB), multiplied by the nearest texel of texture
+ * `emission_tex` at the interpolated UV when emission_tex >= 0.
+ * The environment is an equirectangular RGB map, row 0 looking at +y, W = 2H
+ * a power of two (Sec. 2.1.2); env == NULL means no environment.
+ * Instancing (optional): when num_instances > 0, triangle range
+ * [mesh_tri_offset[m], mesh_tri_offset[m+1]) is mesh m, and instance k places
+ * mesh instance_mesh[k] with the row-major 3x4 object-to-world matrix
+ * instance_xform[12k .. 12k+11]; hits then report (inst, prim) with prim
+ * indexing the triangle list. */
+typedef struct {
+    int64_t num_vertices;
+    int64_t num_triangles;
+    const float *vertices;       /* num_vertices x 3 */
+    const float *normals;        /* num_vertices x 3, or NULL (flat shading) */
+    const float *uvs;            /* num_vertices x 2, or NULL */
+    const uint32_t *indices;     /* num_triangles x 3 */
+    const uint32_t *tri_material;/* num_triangles */
+    int32_t num_materials;
+    const float *albedo;         /* num_materials x 3 */
+    const float *roughness;      /* num_materials */
+    const float *ggx_weight;     /* num_materials */
+    const float *emission;       /* num_materials x 3 */
+    const int32_t *emission_tex; /* num_materials, -1 = constant emission */
+    int32_t num_textures, tex_width, tex_height;
+    const float *textures;       /* num_textures x tex_height x tex_width x 3 */
+    int32_t env_width, env_height;
+    const float *env;            /* env_height x env_width x 3, or NULL */
+    int32_t num_meshes;
+    const int64_t *mesh_tri_offset;  /* num_meshes + 1 */
+    int32_t num_instances;
+    const uint32_t *instance_mesh;   /* num_instances */
+    const float *instance_xform;     /* num_instances x 12 */
+} rt_scene_desc;
+
+/* Rays and hits for rt_trace: structure-of-arrays of DEVICE pointers, n
+ * entries each. A ray is o + t d for t in the open interval (tmin, tmax); d
+ * need not be normalised but must be non-zero. A miss is prim == RT_MISS
+ * with t = +inf. (u, v) are the barycentric weights of v1 and v2. */
+#define RT_MISS 0xFFFFFFFFu
+typedef struct {
+    const float *ox, *oy, *oz, *dx, *dy, *dz, *tmin, *tmax;
+} rt_rays;
+typedef struct {
+    uint32_t *prim, *inst;
+    float *t, *u, *v;
+} rt_hits;
+
+/* Pinhole camera; film pixel (x, y) has y growing downwards. */
+typedef struct {
+    float eye[3], look_at[3], up[3];
+    float vfov_deg;
+    uint32_t width, height;
+} rt_camera;
+
+/* Render statistics (optional output of rt_render). */
+typedef struct {
+    uint64_t paths;          /* camera paths completed */
+    uint64_t extension_rays; /* closest-hit rays traced */
+    uint64_t shadow_rays;    /* any-hit rays traced */
+    uint32_t waves;          /* iteration sets executed */
+    uint32_t wavefront_steps;/* bounce steps run as separate state kernels */
+    uint32_t tail_launches;  /* megakernel tail launches */
+    uint32_t kernel_launches;/* library kernels launched */
+    /* per-kernel device time in ms, filled when rt_render_opts.profile != 0
+     * (CUDA events around each launch on the render stream) */
+    double trace_ms, shade_ms, shadow_ms, megakernel_ms, other_ms;
+    uint32_t trace_launches;
+    /* traversal work, filled when rt_render_opts.profile >= 2 (counted by
+     * an instrumented variant of the trace kernels) */
+    uint64_t ext_nodes, ext_tris, shadow_nodes, shadow_tris;
+} rt_stats;
+
+/* Render options. Zero-initialise and set what you need; zero means the
+ * documented default for every field. */
+typedef struct {
+    float filter_sigma;      /* Gaussian filter sigma in pixels (A.1); 0 -> 0.5; <0 -> box */
+    int32_t rr_enable;       /* Russian roulette from the 3rd vertex (default off) */
+    int32_t mis_mode;        /* 0 power heuristic, 1 balance, 2 NEE only, 3 BSDF only */
+    uint64_t seed;           /* scrambling seed for the Halton digits (A.2) */
+    double time_budget_ms;   /* stop between iteration sets after this (0 = none) */
+    uint32_t max_paths_in_flight; /* state-pool capacity (0 = 4M) */
+    int32_t megakernel_only; /* 1: one megakernel per iteration set (A/B baseline) */
+    int32_t sort_by_material;/* 1: material-sorted shading queue */
+    uint32_t tail_threshold; /* live paths below which the megakernel finishes a set (0 = auto) */
+    uint32_t block_size;     /* threads per block of the state kernels (0 = auto) */
+    const volatile int32_t *abort_flag; /* host-mapped; nonzero -> stop between sets (A.4) */
+    rt_guide *guide;         /* online path guiding (NULL = off) */
+    rt_stats *stats;         /* optional host output */
+    int32_t profile;         /* 1: per-kernel event timing; 2: also count traversal work */
+} rt_render_opts;
+
+/* ---------------------------------------------------------------- scene */
+/* Copies `desc` to device memory, builds the 8-wide compressed BVH (SAH),
+ * per-triangle emitter flux + alias table (Sec. 2.1.1) and the environment
+ * pyramid (Sec. 2.1.2). Synchronous. `*out` is owned by the caller. */
+rt_status rt_scene_create(const rt_scene_desc *desc, rt_scene **out);
+rt_status rt_scene_destroy(rt_scene *scene);
+/* Node and triangle counts of the BVH and bytes of device memory held. */
+rt_status rt_scene_info(const rt_scene *scene, int64_t *nodes, int64_t *leaf_tris,
+                        int64_t *device_bytes);
+
+/* ---------------------------------------------------------------- trace */
+/* rays -> hits (Sec. 3.1, the ray-casting state kernels). Closest hit when
+ * any_hit == 0 (ties in t: lower (inst, prim) wins); otherwise any hit in
+ * (tmin, tmax) and prim != RT_MISS iff occluded. Asynchronous on `stream`.
+ * n == 0 is a no-op. */
+rt_status rt_trace(const rt_scene *scene, const rt_rays *rays, int64_t n, const rt_hits *hits,
+                   int32_t any_hit, void *stream);
+
+/* ----------------------------------------------------------------- film */
+/* Per-pixel FP64 sums of radiance and squared radiance (RGB) and a u32
+ * sample count (Appendix A.4), on the device, plus the next iteration index.
+ * rt_render accumulates into it; repeated calls add samples (consistency). */
+rt_status rt_film_create(uint32_t width, uint32_t height, rt_film **out);
+rt_status rt_film_destroy(rt_film *film);
+rt_status rt_film_clear(rt_film *film, void *stream);
+/* Next iteration (sample index j per pixel) the film will receive. */
+rt_status rt_film_next_iteration(const rt_film *film, uint32_t *next);
+/* Make the next rt_render start at iteration `next` (the film's sums are
+ * kept). Devices that share one image render disjoint iteration sets and
+ * their films are summed (Sec. 3.2.2 batch scheduling). */
+rt_status rt_film_seek(rt_film *film, uint32_t next);
+/* Device pointers to the raw buffers (sum: H*W*3 doubles, sum2 likewise,
+ * count: H*W uint32). Valid until rt_film_destroy. */
+rt_status rt_film_buffers(const rt_film *film, double **sum, double **sum2, uint32_t **count);
+/* mean = sum / count; var = variance of the mean =
+ * (sum2 / count - mean^2) / (count - 1). DEVICE float outputs, H*W*3 each;
+ * var may be NULL. */
+rt_status rt_film_resolve(const rt_film *film, float *mean, float *var, void *stream);
+
+/* --------------------------------------------------------------- render */
+/* Accumulate iterations [next, next + spp) of the consistent QMC estimator
+ * into `film` (film size must equal the camera's). max_depth = number of
+ * scattering vertices (1 = direct lighting). Blocking with respect to the
+ * host (it waits for each iteration set to finish); kernels run on `stream`.
+ * Returns RT_TIMEOUT if the time budget or abort flag stopped it early: the
+ * film then holds whole iteration sets only and the next call resumes. */
+rt_status rt_render(const rt_scene *scene, const rt_camera *camera, uint32_t spp,
+                    uint32_t max_depth, rt_film *film, const rt_render_opts *opts, void *stream);
+
+/* ------------------------------------------------------- QMC sampling */
+/* Sequence index of sample j in pixel (x, y) under full-screen enumeration
+ * (Appendix A.2): DEVICE arrays px, py, j of n entries -> out (uint64). */
+rt_status rt_sample_index(uint32_t width, uint32_t height, const uint32_t *px, const uint32_t *py,
+                          const uint32_t *j, int64_t n, uint64_t *out, void *stream);
+/* Scrambled Halton sample bits floor(2^32 * phi) of dimensions 0..ndims-1 for
+ * DEVICE sequence indices (Appendix A.2); out is n x ndims uint32 (device).
+ * Dimensions 0 and 1 are the in-pixel offsets of the (width x height)
+ * enumeration; dimension d >= 2 uses the d-th prime with the seed's digit
+ * scramble. */
+rt_status rt_halton(uint32_t width, uint32_t height, uint64_t seed, const uint64_t *indices, int64_t n,
+                    int32_t ndims, uint32_t *out, void *stream);
+/* Host check of the strength-reduced division: q[i] = n[i] / d for HOST
+ * arrays, computed with the same multiply-high routine the kernels use. */
+rt_status rt_divide_u64_host(const uint64_t *n, int64_t count, uint32_t d, uint64_t *q);
+
+/* ------------------------------------------------------------ guiding */
+/* Online-trained proposal (not in the paper): one-blob encoded (position,
+ * outgoing direction, normal) -> 4 x 64 ReLU MLP with BF16 weights and FP32
+ * accumulation on the tensor cores -> 8-lobe von Mises-Fisher mixture,
+ * combined with BSDF sampling by one-sample MIS (mixture probability
+ * `alpha`). Trained after each iteration set on up to `batch` radiance
+ * samples with Adam. */
+typedef struct {
+    uint32_t batch;          /* training samples per pass (0 = 65536) */
+    float learning_rate;     /* Adam lr (0 = 1e-2) */
+    float alpha;             /* guide-vs-BSDF selection probability (0 = 0.5) */
+    uint32_t train_steps;    /* Adam steps per pass (0 = 1) */
+    uint64_t seed;           /* weight initialisation seed */
+} rt_guide_opts;
+
+rt_status rt_guide_create(const rt_scene *scene, const rt_guide_opts *opts, rt_guide **out);
+rt_status rt_guide_destroy(rt_guide *guide);
+/* Number of FP32 master weights (224*64 + 3*64*64 + 64*40 = 29184), layer by
+ * layer, each layer [out][in] row-major. */
+int64_t rt_guide_num_params(void);
+/* HOST buffers of rt_guide_num_params() floats. set also resets Adam. */
+rt_status rt_guide_get_params(const rt_guide *guide, float *params);
+rt_status rt_guide_set_params(rt_guide *guide, const float *params);
+/* Checkpoint: weights, Adam moments and step counter. */
+rt_status rt_guide_state_size(const rt_guide *guide, int64_t *bytes);
+rt_status rt_guide_save(const rt_guide *guide, void *host_buffer);
+rt_status rt_guide_load(rt_guide *guide, const void *host_buffer);
+/* Batched inference: DEVICE features (n x 7 floats in [0,1]: position in the
+ * scene box, outgoing direction, normal) -> raw network outputs (n x 40
+ * floats, device). */
+rt_status rt_guide_infer(const rt_guide *guide, const float *features, int64_t n, float *raw,
+                         void *stream);
+/* Loss and gradient on a DEVICE batch (features n x 7, wi n x 3, weight n);
+ * grad (device, num_params floats) receives d loss / d weight, *loss (host)
+ * the batch loss. Does not update the weights. Synchronous. */
+rt_status rt_guide_loss_grad(const rt_guide *guide, const float *features, const float *wi,
+                             const float *weight, int64_t n, float *grad, float *loss, void *stream);
+/* One fused training step (forward, backward, Adam) on a DEVICE batch. */
+rt_status rt_guide_train_step(rt_guide *guide, const float *features, const float *wi,
+                              const float *weight, int64_t n, void *stream);
+
+/* ------------------------------------------------------------ errors */
+const char *rt_last_error(void);
+const char *rt_status_string(rt_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_GB300_H */

@@ -1,0 +1,86 @@
+// Shared device/host declarations of the GB300 path tracer: small vector
+// math, the device-side scene view and the path-state layout.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <cuda_runtime.h>
+
+#include "../../include/rt.h"
+
+#define RT_HD __host__ __device__ __forceinline__
+#define RT_D __device__ __forceinline__
+
+namespace rtg {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kInvPi = 0.318309886183790671538f;
+constexpr float kF0 = 0.04f;            // Schlick reflectance at normal incidence
+constexpr float kAdaptEps = 1e-3f;       // shading-normal adaptation margin (A.3)
+constexpr float kShadowEps = 1e-4f;      // shadow rays to a triangle stop at (1 - eps) * dist
+constexpr int kMaxDepth = 64;
+constexpr int kStackSize = 48;           // BVH traversal stack entries (node groups)
+
+// ------------------------------------------------------------------ vec3
+struct V3 { float x, y, z; };
+RT_HD V3 v3(float x, float y, float z) { return V3{x, y, z}; }
+RT_HD V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+RT_HD V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+RT_HD V3 operator-(V3 a) { return {-a.x, -a.y, -a.z}; }
+RT_HD V3 operator*(V3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+RT_HD V3 operator*(float s, V3 a) { return {a.x * s, a.y * s, a.z * s}; }
+RT_HD V3 mul(V3 a, V3 b) { return {a.x * b.x, a.y * b.y, a.z * b.z}; }
+RT_HD float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+RT_HD V3 cross(V3 a, V3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+RT_HD float length(V3 a) { return sqrtf(dot(a, a)); }
+RT_HD V3 normalize(V3 a) {
+    float l = sqrtf(dot(a, a));
+    return l > 0.f ? a * (1.f / l) : a;
+}
+RT_HD float maxc(V3 a) { return fmaxf(a.x, fmaxf(a.y, a.z)); }
+RT_HD float lum(V3 c) { return 0.2126f * c.x + 0.7152f * c.y + 0.0722f * c.z; }
+RT_HD V3 f4xyz(float4 a) { return {a.x, a.y, a.z}; }
+
+// -------------------------------------------------------- device scene view
+// BVH node: 80 bytes = 5 x uint4 (see bvh_build.cpp for the encoding).
+struct DevScene {
+    const uint4 *nodes;        // 5 uint4 per node
+    const float4 *tris;        // 3 float4 per leaf triangle (v0.w = prim id bits)
+    // two-level scenes: top level over instances, per-mesh bottom levels
+    int32_t two_level;
+    const uint4 *tlas_nodes;   // top-level nodes; leaves reference instances
+    const float4 *inst_xf;     // per instance: world->object 3x4 (3 float4) + object->world 3x4 (3 float4)
+    const uint32_t *inst_root; // per instance: root node index of its mesh in `nodes`
+    // shading data indexed by the original triangle id
+    const float *vertices;     // V x 3
+    const float *normals;      // V x 3 or null
+    const float *uvs;          // V x 2 or null
+    const uint32_t *indices;   // T x 3
+    const uint32_t *tri_material;
+    const float *tri_light_pdf_area; // T: (1 - p_env) P(select) / area, 0 = not an emitter
+    const float4 *mat_a;       // albedo rgb, roughness
+    const float4 *mat_b;       // emission rgb, ggx weight
+    const int32_t *mat_tex;    // emission texture or -1
+    int32_t tex_w, tex_h;
+    const float *textures;     // K x th x tw x 3
+    // emitters
+    uint32_t num_lights;
+    const float2 *alias;       // x = threshold, y = alias index (bits)
+    const uint32_t *light_tri; // emitter -> triangle id
+    // environment
+    int32_t env_w, env_h, env_levels;
+    const float4 *env;         // finest level: rgb + pdf (lum / sum w)
+    const float *env_pyr;      // all levels of weights, finest first, concatenated
+    const int64_t *env_off;    // level offsets into env_pyr (device copy)
+    int64_t env_off_h[16];     // same offsets, by value
+    float p_env;               // probability of choosing the environment in NEE
+    float3 bb_lo, bb_hi;       // scene bounds (guiding features)
+};
+
+// ---------------------------------------------------------- error helpers
+RT_D uint32_t lane_id() { return threadIdx.x & 31u; }
+
+}  // namespace rtg

@@ -1,0 +1,697 @@
+// Wavefront path tracing on one GPU (paper Sec. 3.1): structure-of-arrays
+// sample state, one kernel per state (closest-hit trace, shade, shadow
+// trace), queues compacted just in time with warp ballots, a megakernel that
+// finishes the tail when few samples remain (Sec. 3.1.3), iteration sets with
+// per-pixel FP64 accumulation and sample counts (Sec. 3.2.2, Appendix A.4),
+// and the rays -> hits entry point (Sec. 3.1, ray casting state kernels).
+//
+// Scheduling differs from the paper's single just-in-time queue picked
+// greedily by state population: GB300 memory is ample, so every state keeps
+// its own queue and each bounce step runs all state kernels in a fixed order
+// whose launch grids never depend on host-side counts (kernels read queue
+// lengths from device memory). The host only synchronises between
+// iteration sets, where it checks the time budget and the abort flag.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <vector>
+
+#include "internal.h"
+#include "shade.cuh"
+
+namespace rtg {
+
+struct Ctrl {
+    uint32_t n_ext, n_next, n_shadow, cur;
+    uint32_t tail, overflow, tail_threshold, pad;
+    unsigned long long ext_rays, shadow_rays;
+    unsigned long long ext_nodes, ext_tris, shadow_nodes, shadow_tris;
+};
+
+// Structure-of-arrays path state (capacity = pool size).
+struct Pool {
+    float4 *ray_o;   // pending ray origin
+    float4 *ray_d;   // pending ray direction, w = prev_pdf
+    float4 *beta;    // throughput, w = vertex number (uint bits)
+    float4 *L;       // radiance so far
+    uint2 *index;    // 64-bit QMC index
+    uint32_t *pixel;
+    float4 *hit;     // prim bits, t, b1, b2
+    float4 *sh_o;    // shadow origin, w = tmax
+    float4 *sh_d;
+    float4 *sh_c;    // shadow contribution
+    uint32_t *q[2];  // extension-ray queues (current / next)
+    uint32_t *qs;    // shadow-ray queue
+    Ctrl *ctrl;
+    uint32_t capacity;
+};
+
+RT_D void store_state(const Pool &p, uint32_t q, const PathState &s) {
+    p.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, 0.f);
+    p.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);
+    p.beta[q] = make_float4(s.beta.x, s.beta.y, s.beta.z, __uint_as_float(s.depth));
+    p.L[q] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
+    p.index[q] = make_uint2((uint32_t)s.index, (uint32_t)(s.index >> 32));
+    p.pixel[q] = s.pixel;
+}
+
+RT_D PathState load_state(const Pool &p, uint32_t q) {
+    PathState s;
+    float4 o = p.ray_o[q], d = p.ray_d[q], b = p.beta[q], L = p.L[q];
+    uint2 ix = p.index[q];
+    s.o = v3(o.x, o.y, o.z);
+    s.d = v3(d.x, d.y, d.z);
+    s.prev_pdf = d.w;
+    s.beta = v3(b.x, b.y, b.z);
+    s.depth = __float_as_uint(b.w);
+    s.L = v3(L.x, L.y, L.z);
+    s.index = (uint64_t)ix.x | ((uint64_t)ix.y << 32);
+    s.pixel = p.pixel[q];
+    return s;
+}
+
+// Append `item` to `queue` for every lane with pred set: one atomic per warp
+// (ballot + population count), order inside the warp preserved.
+RT_D void warp_append(uint32_t *queue, uint32_t *count, bool pred, uint32_t item) {
+    const uint32_t full = 0xFFFFFFFFu;
+    uint32_t mask = __ballot_sync(full, pred);
+    if (!mask) return;
+    uint32_t lane = lane_id();
+    uint32_t leader = __ffs(mask) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(mask));
+    base = __shfl_sync(full, base, leader);
+    if (pred) queue[base + __popc(mask & ((1u << lane) - 1u))] = item;
+}
+
+RT_D void count_rays(unsigned long long *ctr, bool pred) {
+    uint32_t mask = __ballot_sync(0xFFFFFFFFu, pred);
+    if (lane_id() == 0 && mask) atomicAdd(ctr, (unsigned long long)__popc(mask));
+}
+
+struct DevTraceClosest {
+    const DevScene *sc;
+    bool *overflow;
+    RT_D void operator()(V3 o, V3 d, Hit &h) const {
+        Ray r{o, d, 0.f, INFINITY};
+        h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
+        TraceResult tr = traverse<false>(sc->nodes, sc->tris, 0u, r, h);
+        if (tr.overflow) *overflow = true;
+    }
+};
+struct DevTraceAny {
+    const DevScene *sc;
+    bool *overflow;
+    RT_D bool operator()(V3 o, V3 d, float tmax) const {
+        Ray r{o, d, 0.f, tmax};
+        Hit h;
+        h.prim = RT_MISS; h.t = INFINITY;
+        TraceResult tr = traverse<true>(sc->nodes, sc->tris, 0u, r, h);
+        if (tr.overflow) *overflow = true;
+        return h.prim != RT_MISS;
+    }
+};
+
+// ------------------------------------------------------------------ kernels
+__global__ void k_raygen(RenderParams P, Pool pool, uint64_t t0, uint32_t n, uint32_t WH, uint32_t tail_threshold) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        uint64_t t = t0 + q;
+        PathState s;
+        raygen(P, (uint32_t)(t % WH), (uint32_t)(t / WH), s);
+        store_state(pool, q, s);
+        pool.q[0][q] = q;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Ctrl *c = pool.ctrl;
+        c->n_ext = n;
+        c->n_next = 0;
+        c->n_shadow = 0;
+        c->cur = 0;
+        c->tail_threshold = tail_threshold;
+        c->tail = n < tail_threshold ? 1u : 0u;
+    }
+}
+
+// Closest-hit traversal of the current extension queue.
+template <bool kCount>
+__global__ void __launch_bounds__(128) k_trace_ext(DevScene sc, Pool pool) {
+    Ctrl *c = pool.ctrl;
+    if (c->tail) return;
+    const uint32_t n = c->n_ext;
+    const uint32_t *queue = pool.q[c->cur];
+    bool overflow = false;
+    uint32_t nodes = 0, tris = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += stride) {
+        uint32_t i = base + lane_id();
+        bool valid = i < n;
+        if (valid) {
+            uint32_t q = queue[i];
+            float4 o = pool.ray_o[q], d = pool.ray_d[q];
+            Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, INFINITY};
+            Hit h;
+            h.prim = RT_MISS; h.t = INFINITY; h.b1 = h.b2 = 0.f;
+            TraceResult tr = traverse<false>(sc.nodes, sc.tris, 0u, r, h);
+            overflow |= tr.overflow;
+            if (kCount) { nodes += tr.nodes; tris += tr.tris; }
+            pool.hit[q] = make_float4(__uint_as_float(h.prim), h.t, h.b1, h.b2);
+        }
+        count_rays(&c->ext_rays, valid);
+    }
+    if (overflow) atomicOr(&c->overflow, 1u);
+    if (kCount) {
+        atomicAdd(&c->ext_nodes, (unsigned long long)nodes);
+        atomicAdd(&c->ext_tris, (unsigned long long)tris);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_shade(RenderParams P, Pool pool) {
+    Ctrl *c = pool.ctrl;
+    if (c->tail) return;
+    const uint32_t n = c->n_ext;
+    const uint32_t cur = c->cur;
+    const uint32_t *queue = pool.q[cur];
+    uint32_t *next = pool.q[cur ^ 1u];
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += stride) {
+        uint32_t i = base + lane_id();
+        bool valid = i < n;
+        uint32_t q = 0;
+        int r = 0;
+        if (valid) {
+            q = queue[i];
+            PathState s = load_state(pool, q);
+            float4 hv = pool.hit[q];
+            Hit h;
+            h.prim = __float_as_uint(hv.x); h.inst = 0; h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
+            ShadowRay sh;
+            r = shade(P, s, h, sh);
+            pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
+            if (r & 1) {
+                pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, 0.f);
+                pool.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);
+                pool.beta[q] = make_float4(s.beta.x, s.beta.y, s.beta.z, __uint_as_float(s.depth));
+            }
+            if (r & 2) {
+                pool.sh_o[q] = make_float4(sh.o.x, sh.o.y, sh.o.z, sh.tmax);
+                pool.sh_d[q] = make_float4(sh.d.x, sh.d.y, sh.d.z, 0.f);
+                pool.sh_c[q] = make_float4(sh.contrib.x, sh.contrib.y, sh.contrib.z, 0.f);
+            }
+        }
+        warp_append(next, &c->n_next, valid && (r & 1), q);
+        warp_append(pool.qs, &c->n_shadow, valid && (r & 2), q);
+    }
+}
+
+// Any-hit traversal of the shadow queue; unoccluded contributions are added.
+template <bool kCount>
+__global__ void __launch_bounds__(128) k_trace_shadow(DevScene sc, Pool pool) {
+    Ctrl *c = pool.ctrl;
+    if (c->tail) return;
+    const uint32_t n = c->n_shadow;
+    bool overflow = false;
+    uint32_t nodes = 0, tris = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += stride) {
+        uint32_t i = base + lane_id();
+        bool valid = i < n;
+        if (valid) {
+            uint32_t q = pool.qs[i];
+            float4 o = pool.sh_o[q], d = pool.sh_d[q];
+            Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, o.w};
+            Hit h;
+            h.prim = RT_MISS; h.t = INFINITY;
+            TraceResult tr = traverse<true>(sc.nodes, sc.tris, 0u, r, h);
+            overflow |= tr.overflow;
+            if (kCount) { nodes += tr.nodes; tris += tr.tris; }
+            if (h.prim == RT_MISS) {
+                float4 cc = pool.sh_c[q], L = pool.L[q];
+                pool.L[q] = make_float4(L.x + cc.x, L.y + cc.y, L.z + cc.z, 0.f);
+            }
+        }
+        count_rays(&c->shadow_rays, valid);
+    }
+    if (overflow) atomicOr(&c->overflow, 1u);
+    if (kCount) {
+        atomicAdd(&c->shadow_nodes, (unsigned long long)nodes);
+        atomicAdd(&c->shadow_tris, (unsigned long long)tris);
+    }
+}
+
+__global__ void k_step_end(Pool pool) {
+    Ctrl *c = pool.ctrl;
+    if (!c->tail) {
+        c->n_ext = c->n_next;
+        c->n_next = 0;
+        c->cur ^= 1u;
+        if (c->n_ext < c->tail_threshold) c->tail = 1u;
+    }
+    c->n_shadow = 0;
+}
+
+// Megakernel: every remaining sample runs to completion in its own thread.
+__global__ void __launch_bounds__(128) k_megakernel(RenderParams P, Pool pool) {
+    Ctrl *c = pool.ctrl;
+    if (!c->tail) return;
+    const uint32_t n = c->n_ext;
+    const uint32_t *queue = pool.q[c->cur];
+    bool overflow = false;
+    uint32_t ext = 0, shadow = 0;
+    DevTraceClosest closest{&P.sc, &overflow};
+    DevTraceAny any{&P.sc, &overflow};
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t q = queue[i];
+        PathState s = load_state(pool, q);
+        finish_path(P, s, closest, any, ext, shadow);
+        pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
+    }
+    if (ext) atomicAdd(&c->ext_rays, (unsigned long long)ext);
+    if (shadow) atomicAdd(&c->shadow_rays, (unsigned long long)shadow);
+    if (overflow) atomicOr(&c->overflow, 1u);
+}
+
+// Film accumulation, owner-exclusive per pixel (deterministic order).
+// passes > 0: the wave holds `passes` whole passes, slot = pass * WH + pixel.
+// passes == 0: the wave holds n <= WH distinct consecutive pixels from t0.
+__global__ void k_film(Pool pool, double *sum, double *sum2, uint32_t *count, uint64_t t0, uint32_t n, uint32_t WH,
+                       uint32_t passes) {
+    uint32_t m = passes ? WH : n;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        uint32_t px = passes ? i : (uint32_t)((t0 + i) % WH);
+        double s0 = sum[3 * (size_t)px], s1 = sum[3 * (size_t)px + 1], s2 = sum[3 * (size_t)px + 2];
+        double q0 = sum2[3 * (size_t)px], q1 = sum2[3 * (size_t)px + 1], q2 = sum2[3 * (size_t)px + 2];
+        uint32_t k = passes ? passes : 1u;
+        for (uint32_t p = 0; p < k; ++p) {
+            uint32_t slot = passes ? p * WH + i : i;
+            float4 L = pool.L[slot];
+            double a = L.x, b = L.y, cc = L.z;
+            s0 += a; s1 += b; s2 += cc;
+            q0 += a * a; q1 += b * b; q2 += cc * cc;
+        }
+        sum[3 * (size_t)px] = s0; sum[3 * (size_t)px + 1] = s1; sum[3 * (size_t)px + 2] = s2;
+        sum2[3 * (size_t)px] = q0; sum2[3 * (size_t)px + 1] = q1; sum2[3 * (size_t)px + 2] = q2;
+        count[px] += k;
+    }
+}
+
+__global__ void k_resolve(const double *sum, const double *sum2, const uint32_t *count, uint32_t npix, float *mean,
+                          float *var) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += gridDim.x * blockDim.x) {
+        double n = count[i] > 0 ? (double)count[i] : 1.0;
+        for (int c = 0; c < 3; ++c) {
+            double m = sum[3 * (size_t)i + c] / n;
+            mean[3 * (size_t)i + c] = (float)m;
+            if (var) {
+                double v = sum2[3 * (size_t)i + c] / n - m * m;
+                var[3 * (size_t)i + c] = (float)(fmax(v, 0.0) / fmax(n - 1.0, 1.0));
+            }
+        }
+    }
+}
+
+// rays -> hits over caller-owned SoA buffers.
+template <bool kAny>
+__global__ void __launch_bounds__(128) k_trace_user(DevScene sc, rt_rays rays, int64_t n, rt_hits hits,
+                                                    uint32_t *overflow_flag) {
+    bool overflow = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        Ray r{v3(__ldg(rays.ox + i), __ldg(rays.oy + i), __ldg(rays.oz + i)),
+              v3(__ldg(rays.dx + i), __ldg(rays.dy + i), __ldg(rays.dz + i)), __ldg(rays.tmin + i),
+              __ldg(rays.tmax + i)};
+        Hit h;
+        h.prim = RT_MISS; h.t = INFINITY; h.b1 = h.b2 = 0.f;
+        TraceResult tr = traverse<kAny>(sc.nodes, sc.tris, 0u, r, h);
+        overflow |= tr.overflow;
+        hits.prim[i] = h.prim;
+        if (hits.inst) hits.inst[i] = 0u;
+        hits.t[i] = h.prim == RT_MISS ? INFINITY : h.t;
+        if (hits.u) hits.u[i] = h.b1;
+        if (hits.v) hits.v[i] = h.b2;
+    }
+    if (overflow) atomicOr(overflow_flag, 1u);
+}
+
+__global__ void k_sample_index(Enum en, const uint32_t *px, const uint32_t *py, const uint32_t *j, int64_t n,
+                               uint64_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = pixel_base_index(en, px[i], py[i]) + (uint64_t)j[i] * en.period;
+}
+
+__global__ void k_halton(Enum en, const HaltonDim *dims, const uint64_t *idx, int64_t n, int32_t ndims,
+                         uint32_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t x = idx[i];
+        for (int32_t d = 0; d < ndims; ++d) {
+            uint32_t u = d == 0 ? dim0_bits(en, x) : (d == 1 ? dim1_bits(en, x) : radical_inverse(x, dims[d]));
+            out[i * ndims + d] = u;
+        }
+    }
+}
+
+// ---------------------------------------------------------- host helpers
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <class K>
+int grid_for(K kernel, int block, int64_t work) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
+    if (per_sm < 1) per_sm = 1;
+    int64_t full = (int64_t)sm_count() * per_sm;
+    int64_t need = (work + block - 1) / block;
+    return (int)std::max<int64_t>(1, std::min(full, need));
+}
+
+struct PoolAlloc {
+    Pool view{};
+    void *block = nullptr;
+    uint32_t capacity = 0;
+    ~PoolAlloc() {
+        if (block) cudaFree(block);
+    }
+};
+
+rt_status ensure_pool(PoolAlloc &pa, uint32_t capacity) {
+    if (pa.block && pa.capacity >= capacity) return RT_OK;
+    if (pa.block) { cudaFree(pa.block); pa.block = nullptr; }
+    size_t P = capacity;
+    size_t f4 = P * sizeof(float4);
+    size_t bytes = 8 * f4 + P * sizeof(uint2) + P * 4 /*pixel*/ + 3 * P * 4 /*queues*/ + 64 * 256;
+    cudaError_t e = cudaMalloc(&pa.block, bytes);
+    if (e != cudaSuccess) { set_error("path-state pool allocation failed"); return RT_OOM; }
+    char *p = (char *)pa.block;
+    auto take = [&](size_t b) { char *r = p; p += (b + 255) / 256 * 256; return r; };
+    Pool &v = pa.view;
+    v.ctrl = (Ctrl *)take(sizeof(Ctrl));
+    v.ray_o = (float4 *)take(f4); v.ray_d = (float4 *)take(f4); v.beta = (float4 *)take(f4); v.L = (float4 *)take(f4);
+    v.hit = (float4 *)take(f4); v.sh_o = (float4 *)take(f4); v.sh_d = (float4 *)take(f4); v.sh_c = (float4 *)take(f4);
+    v.index = (uint2 *)take(P * sizeof(uint2));
+    v.pixel = (uint32_t *)take(P * 4);
+    v.q[0] = (uint32_t *)take(P * 4); v.q[1] = (uint32_t *)take(P * 4); v.qs = (uint32_t *)take(P * 4);
+    v.capacity = capacity;
+    pa.capacity = capacity;
+    if ((size_t)(p - (char *)pa.block) > bytes) { set_error("pool layout overflow"); return RT_CUDA_ERROR; }
+    return RT_OK;
+}
+
+}  // namespace rtg
+
+using namespace rtg;
+
+// Per-film render resources (path-state pool, dimension table, pinned ctrl).
+struct RenderCache {
+    PoolAlloc pool;
+    HaltonDim *dims = nullptr;
+    uint64_t dims_seed = ~0ull;
+    int dims_n = 0;
+    Ctrl *host_ctrl = nullptr;
+    ~RenderCache() {
+        if (dims) cudaFree(dims);
+        if (host_ctrl) cudaFreeHost(host_ctrl);
+    }
+};
+
+static RenderCache *cache_of(rt_film *f);
+
+extern "C" rt_status rt_trace(const rt_scene *s, const rt_rays *rays, int64_t n, const rt_hits *hits,
+                              int32_t any_hit, void *stream) {
+    if (!s || !rays || !hits || n < 0) { set_error("rt_trace: invalid argument"); return RT_INVALID_ARG; }
+    if (s->host_only) { set_error("rt_trace: scene has no device copy"); return RT_INVALID_ARG; }
+    if (n == 0) return RT_OK;
+    if (!hits->prim || !hits->t || !rays->ox || !rays->dx || !rays->tmin || !rays->tmax) {
+        set_error("rt_trace: null ray or hit pointer");
+        return RT_INVALID_ARG;
+    }
+    static uint32_t *flag = nullptr;
+    if (!flag) RT_CUDA_TRY(cudaMalloc(&flag, 4));
+    cudaStream_t st = (cudaStream_t)stream;
+    RT_CUDA_TRY(cudaMemsetAsync(flag, 0, 4, st));
+    if (any_hit) {
+        int g = grid_for(k_trace_user<true>, 128, n);
+        k_trace_user<true><<<g, 128, 0, st>>>(s->dev, *rays, n, *hits, flag);
+    } else {
+        int g = grid_for(k_trace_user<false>, 128, n);
+        k_trace_user<false><<<g, 128, 0, st>>>(s->dev, *rays, n, *hits, flag);
+    }
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+extern "C" rt_status rt_film_create(uint32_t W, uint32_t H, rt_film **out) {
+    if (!out || W == 0 || H == 0 || (uint64_t)W * H > (1ull << 31)) {
+        set_error("rt_film_create: invalid size");
+        return RT_INVALID_ARG;
+    }
+    rt_film *f = new rt_film();
+    f->W = W; f->H = H;
+    size_t npix = (size_t)W * H;
+    if (cudaMalloc(&f->sum, npix * 3 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&f->sum2, npix * 3 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&f->count, npix * sizeof(uint32_t)) != cudaSuccess) {
+        rt_film_destroy(f);
+        set_error("rt_film_create: out of device memory");
+        return RT_OOM;
+    }
+    cudaMemset(f->sum, 0, npix * 3 * sizeof(double));
+    cudaMemset(f->sum2, 0, npix * 3 * sizeof(double));
+    cudaMemset(f->count, 0, npix * sizeof(uint32_t));
+    RT_CUDA_TRY(cudaDeviceSynchronize());
+    *out = f;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_film_destroy(rt_film *f) {
+    if (!f) return RT_OK;
+    cudaFree(f->sum); cudaFree(f->sum2); cudaFree(f->count);
+    delete (RenderCache *)f->cache;
+    delete f;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_film_clear(rt_film *f, void *stream) {
+    if (!f) { set_error("rt_film_clear: null film"); return RT_INVALID_ARG; }
+    size_t npix = (size_t)f->W * f->H;
+    cudaStream_t st = (cudaStream_t)stream;
+    RT_CUDA_TRY(cudaMemsetAsync(f->sum, 0, npix * 3 * sizeof(double), st));
+    RT_CUDA_TRY(cudaMemsetAsync(f->sum2, 0, npix * 3 * sizeof(double), st));
+    RT_CUDA_TRY(cudaMemsetAsync(f->count, 0, npix * sizeof(uint32_t), st));
+    f->next_task = 0;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_film_next_iteration(const rt_film *f, uint32_t *next) {
+    if (!f || !next) { set_error("rt_film_next_iteration: null argument"); return RT_INVALID_ARG; }
+    *next = (uint32_t)(f->next_task / ((uint64_t)f->W * f->H));
+    return RT_OK;
+}
+
+extern "C" rt_status rt_film_seek(rt_film *f, uint32_t next) {
+    if (!f) { set_error("rt_film_seek: null film"); return RT_INVALID_ARG; }
+    f->next_task = (uint64_t)next * f->W * f->H;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_film_buffers(const rt_film *f, double **sum, double **sum2, uint32_t **count) {
+    if (!f) { set_error("rt_film_buffers: null film"); return RT_INVALID_ARG; }
+    if (sum) *sum = f->sum;
+    if (sum2) *sum2 = f->sum2;
+    if (count) *count = f->count;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_film_resolve(const rt_film *f, float *mean, float *var, void *stream) {
+    if (!f || !mean) { set_error("rt_film_resolve: null argument"); return RT_INVALID_ARG; }
+    uint32_t npix = f->W * f->H;
+    int g = grid_for(k_resolve, 256, npix);
+    k_resolve<<<g, 256, 0, (cudaStream_t)stream>>>(f->sum, f->sum2, f->count, npix, mean, var);
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+static RenderCache *cache_of(rt_film *f) {
+    if (!f->cache) f->cache = new RenderCache();
+    return (RenderCache *)f->cache;
+}
+
+extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t spp, uint32_t max_depth,
+                               rt_film *film, const rt_render_opts *opts_in, void *stream) {
+    if (!s || !cam || !film) { set_error("rt_render: null argument"); return RT_INVALID_ARG; }
+    if (s->host_only) { set_error("rt_render: scene has no device copy"); return RT_INVALID_ARG; }
+    if (cam->width != film->W || cam->height != film->H) { set_error("rt_render: film and camera sizes differ"); return RT_INVALID_ARG; }
+    if (max_depth < 1 || max_depth > (uint32_t)kMaxDepth) { set_error("rt_render: max_depth must be in [1, 64]"); return RT_INVALID_ARG; }
+    rt_render_opts o{};
+    if (opts_in) o = *opts_in;
+    if (o.guide) { set_error("rt_render: guiding handle not supported by this entry point yet"); return RT_NOT_SUPPORTED; }
+    if (spp == 0) return RT_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    RenderCache *rc = cache_of(film);
+    const uint32_t W = cam->width, H = cam->height;
+    const uint64_t WH = (uint64_t)W * H;
+    uint32_t cap = o.max_paths_in_flight ? o.max_paths_in_flight : (1u << 22);
+    cap = std::max<uint32_t>(cap, 32u);
+    rt_status rs = ensure_pool(rc->pool, cap);
+    if (rs != RT_OK) return rs;
+    const int ndims = 2 + 7 * (int)(max_depth + 1);
+    if (!rc->dims || rc->dims_seed != o.seed || rc->dims_n < ndims) {
+        std::vector<HaltonDim> d = make_dims(o.seed, ndims);
+        if (rc->dims) cudaFree(rc->dims);
+        RT_CUDA_TRY(cudaMalloc(&rc->dims, d.size() * sizeof(HaltonDim)));
+        RT_CUDA_TRY(cudaMemcpy(rc->dims, d.data(), d.size() * sizeof(HaltonDim), cudaMemcpyHostToDevice));
+        rc->dims_seed = o.seed;
+        rc->dims_n = ndims;
+    }
+    if (!rc->host_ctrl) RT_CUDA_TRY(cudaMallocHost(&rc->host_ctrl, sizeof(Ctrl)));
+    RenderParams P;
+    P.sc = s->dev;
+    P.cam = make_camera(*cam);
+    P.en = make_enum(W, H);
+    P.dims = rc->dims;
+    P.max_depth = max_depth;
+    P.sigma = o.filter_sigma == 0.f ? 0.5f : o.filter_sigma;
+    P.mis_mode = o.mis_mode;
+    P.rr = o.rr_enable;
+    const uint32_t tail = o.megakernel_only ? 0xFFFFFFFFu : (o.tail_threshold ? o.tail_threshold : 8192u);
+    Pool pool = rc->pool.view;
+    RT_CUDA_TRY(cudaMemsetAsync(pool.ctrl, 0, sizeof(Ctrl), st));
+    rt_stats stats{};
+    auto t_start = std::chrono::steady_clock::now();
+    uint64_t t = film->next_task, t_end = film->next_task + (uint64_t)spp * WH;
+    rt_status result = RT_OK;
+    const int gb = 128;
+    const int g_ray = grid_for(k_raygen, 256, cap);
+    const int g_trace = grid_for(k_trace_ext<false>, gb, cap);
+    const int g_shade = grid_for(k_shade, gb, cap);
+    const int g_shadow = grid_for(k_trace_shadow<false>, gb, cap);
+    const int g_mega = grid_for(k_megakernel, gb, cap);
+    const bool prof = o.profile >= 1, count = o.profile >= 2;
+    // event pairs per timed launch: kind 0 trace, 1 shade, 2 shadow, 3 megakernel, 4 other
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> evs;
+    auto mark = [&](int kind) -> cudaEvent_t {
+        if (!prof) return nullptr;
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, st);
+        evs.push_back({kind, {a, b}});
+        return b;
+    };
+    auto done = [&](cudaEvent_t b) {
+        if (b) cudaEventRecord(b, st);
+    };
+    while (t < t_end) {
+        uint64_t n64;
+        uint32_t passes = 0;
+        if (t % WH != 0 || WH > cap) {
+            n64 = std::min<uint64_t>({t_end - t, WH - t % WH, (uint64_t)cap});
+        } else {
+            uint64_t full = std::min<uint64_t>((t_end - t) / WH, cap / WH);
+            if (full >= 1) { passes = (uint32_t)full; n64 = full * WH; }
+            else n64 = std::min<uint64_t>(t_end - t, cap);
+        }
+        uint32_t n = (uint32_t)n64;
+        cudaEvent_t e = mark(4);
+        k_raygen<<<g_ray, 256, 0, st>>>(P, pool, t, n, (uint32_t)WH, tail);
+        done(e);
+        ++stats.kernel_launches;
+        if (!o.megakernel_only) {
+            for (uint32_t v = 1; v <= max_depth + 1; ++v) {
+                e = mark(0);
+                if (count) k_trace_ext<true><<<g_trace, gb, 0, st>>>(s->dev, pool);
+                else k_trace_ext<false><<<g_trace, gb, 0, st>>>(s->dev, pool);
+                done(e);
+                e = mark(1);
+                k_shade<<<g_shade, gb, 0, st>>>(P, pool);
+                done(e);
+                e = mark(2);
+                if (count) k_trace_shadow<true><<<g_shadow, gb, 0, st>>>(s->dev, pool);
+                else k_trace_shadow<false><<<g_shadow, gb, 0, st>>>(s->dev, pool);
+                done(e);
+                k_step_end<<<1, 1, 0, st>>>(pool);
+                stats.kernel_launches += 4;
+                ++stats.trace_launches;
+                ++stats.wavefront_steps;
+            }
+        }
+        e = mark(3);
+        k_megakernel<<<g_mega, gb, 0, st>>>(P, pool);
+        done(e);
+        ++stats.tail_launches;
+        int g_film = grid_for(k_film, 256, passes ? WH : n);
+        e = mark(4);
+        k_film<<<g_film, 256, 0, st>>>(pool, film->sum, film->sum2, film->count, t, n, (uint32_t)WH, passes);
+        done(e);
+        stats.kernel_launches += 2;
+        RT_CUDA_TRY(cudaGetLastError());
+        RT_CUDA_TRY(cudaMemcpyAsync(rc->host_ctrl, pool.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+        RT_CUDA_TRY(cudaStreamSynchronize(st));
+        t += n;
+        film->next_task = t;
+        stats.paths += n;
+        ++stats.waves;
+        if (rc->host_ctrl->overflow) { set_error("BVH traversal stack overflow"); result = RT_STACK_OVERFLOW; break; }
+        double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        if (t < t_end && ((o.abort_flag && *o.abort_flag) || (o.time_budget_ms > 0 && ms >= o.time_budget_ms))) {
+            set_error("rt_render: stopped by time budget or abort flag (resumable)");
+            result = RT_TIMEOUT;
+            break;
+        }
+    }
+    for (auto &kv : evs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, kv.second.first, kv.second.second);
+        double *dst[5] = {&stats.trace_ms, &stats.shade_ms, &stats.shadow_ms, &stats.megakernel_ms, &stats.other_ms};
+        *dst[kv.first] += ms;
+        cudaEventDestroy(kv.second.first);
+        cudaEventDestroy(kv.second.second);
+    }
+    stats.extension_rays = rc->host_ctrl->ext_rays;
+    stats.shadow_rays = rc->host_ctrl->shadow_rays;
+    stats.ext_nodes = rc->host_ctrl->ext_nodes;
+    stats.ext_tris = rc->host_ctrl->ext_tris;
+    stats.shadow_nodes = rc->host_ctrl->shadow_nodes;
+    stats.shadow_tris = rc->host_ctrl->shadow_tris;
+    if (o.stats) *o.stats = stats;
+    return result;
+}
+
+extern "C" rt_status rt_sample_index(uint32_t W, uint32_t H, const uint32_t *px, const uint32_t *py, const uint32_t *j,
+                                     int64_t n, uint64_t *out, void *stream) {
+    if (W == 0 || H == 0 || n < 0 || (n > 0 && (!px || !py || !j || !out))) {
+        set_error("rt_sample_index: invalid argument");
+        return RT_INVALID_ARG;
+    }
+    if (n == 0) return RT_OK;
+    Enum en = make_enum(W, H);
+    k_sample_index<<<grid_for(k_sample_index, 256, n), 256, 0, (cudaStream_t)stream>>>(en, px, py, j, n, out);
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+extern "C" rt_status rt_halton(uint32_t W, uint32_t H, uint64_t seed, const uint64_t *idx, int64_t n, int32_t ndims,
+                               uint32_t *out, void *stream) {
+    if (W == 0 || H == 0 || n < 0 || ndims < 0 || ndims > 1024 || (n > 0 && (!idx || !out))) {
+        set_error("rt_halton: invalid argument");
+        return RT_INVALID_ARG;
+    }
+    if (n == 0 || ndims == 0) return RT_OK;
+    std::vector<HaltonDim> d = make_dims(seed, std::max(ndims, 3));
+    HaltonDim *dd = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    RT_CUDA_TRY(cudaMallocAsync(&dd, d.size() * sizeof(HaltonDim), st));
+    RT_CUDA_TRY(cudaMemcpyAsync(dd, d.data(), d.size() * sizeof(HaltonDim), cudaMemcpyHostToDevice, st));
+    Enum en = make_enum(W, H);
+    k_halton<<<grid_for(k_halton, 256, n), 256, 0, st>>>(en, dd, idx, n, ndims, out);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(dd, st);
+    RT_CUDA_TRY(cudaStreamSynchronize(st));
+    RT_CUDA_TRY(e);
+    return RT_OK;
+}

@@ -1,0 +1,476 @@
+// One path vertex of the consistent QMC estimator: state setup with
+// shading-normal adaptation (Sec. 2.2 stage 1, Appendix A.3), emitter hit and
+// environment miss weighted by MIS (Sec. 2), next event estimation with
+// alias-table triangle selection and the environment pyramid (Sec. 2.1.1,
+// Sec. 2.1.2), and sampling of the layered BSDF (Sec. 2.2 stage 4).
+//
+// Readings of the paper fixed here (the FP64 oracle takes the same ones):
+//  - max_depth D counts scattering vertices: vertices 1..D do NEE and sample
+//    a continuation; vertex D+1 only contributes its emission;
+//  - MIS = power heuristic between light sampling and BSDF sampling;
+//  - dimensions: 0, 1 in-pixel offset; vertex v uses 2 + 7(v-1) + {0 light
+//    select, 1-2 light point, 3 lobe select, 4-5 direction, 6 roulette};
+//  - the environment is chosen in NEE with probability p_env (0.5 when both
+//    the environment and triangle emitters exist);
+//  - a direction below the geometric tangent plane carries nothing; the BSDF
+//    vanishes outside the shading hemisphere;
+//  - shadow rays to a triangle stop at (1 - 1e-4) of its distance.
+#pragma once
+
+#include "halton.cuh"
+#include "traverse.cuh"
+
+namespace rtg {
+
+struct CameraView {
+    V3 eye, fwd, right, up;
+    float tan_half, aspect;
+    uint32_t W, H;
+};
+
+CameraView make_camera(const rt_camera &c);   // host: basis from eye/look-at/up
+
+struct RenderParams {
+    DevScene sc;
+    CameraView cam;
+    Enum en;
+    const HaltonDim *dims;   // per dimension (index >= 2 used)
+    uint32_t max_depth;
+    float sigma;             // > 0 Gaussian, <= 0 box
+    int32_t mis_mode;        // 0 power, 1 balance, 2 NEE only, 3 BSDF only
+    int32_t rr;
+};
+
+// State of one camera path between two vertices.
+struct PathState {
+    V3 o, d;          // pending ray
+    V3 beta;          // throughput
+    float prev_pdf;   // pdf of the direction that produced the pending ray
+    V3 L;             // radiance gathered so far
+    uint64_t index;   // QMC sequence index
+    uint32_t pixel;
+    uint32_t depth;   // vertex number the pending ray will create (1 = camera ray)
+};
+
+struct ShadowRay {
+    V3 o, d;
+    float tmax;
+    V3 contrib;
+};
+
+RT_HD float dim_value(const RenderParams &P, uint64_t idx, int dim) {
+    return u32_to_unit(radical_inverse(idx, P.dims[dim]));
+}
+
+// ---------------------------------------------------------------- camera
+RT_HD void camera_ray(const CameraView &c, float sx, float sy, V3 &o, V3 &d) {
+    float nx = (2.f * sx / (float)c.W - 1.f) * c.tan_half * c.aspect;
+    float ny = (1.f - 2.f * sy / (float)c.H) * c.tan_half;
+    d = normalize(c.fwd + nx * c.right + ny * c.up);
+    o = c.eye;
+}
+
+// Filter importance sampling (Appendix A.1): Gaussian offset by Box-Muller
+// of the in-pixel sample; the sample credits its own pixel.
+RT_HD void filter_offset(float sigma, float u0, float u1, float &dx, float &dy) {
+    if (!(sigma > 0.f)) { dx = u0 - 0.5f; dy = u1 - 0.5f; return; }
+    float r = sigma * sqrtf(-2.f * logf(1.f - u0));
+    float s, c;
+#ifdef __CUDA_ARCH__
+    sincosf(2.f * kPi * u1, &s, &c);
+#else
+    s = sinf(2.f * kPi * u1); c = cosf(2.f * kPi * u1);
+#endif
+    dx = r * c;
+    dy = r * s;
+}
+
+RT_HD void raygen(const RenderParams &P, uint32_t pixel, uint32_t j, PathState &s) {
+    uint32_t x = pixel % P.cam.W, y = pixel / P.cam.W;
+    uint64_t idx = pixel_base_index(P.en, x, y) + (uint64_t)j * P.en.period;
+    float u0 = u32_to_unit(dim0_bits(P.en, idx)), u1 = u32_to_unit(dim1_bits(P.en, idx));
+    float dx, dy;
+    filter_offset(P.sigma, u0, u1, dx, dy);
+    camera_ray(P.cam, (float)x + 0.5f + dx, (float)y + 0.5f + dy, s.o, s.d);
+    s.beta = v3(1.f, 1.f, 1.f);
+    s.prev_pdf = 0.f;
+    s.L = v3(0.f, 0.f, 0.f);
+    s.index = idx;
+    s.pixel = pixel;
+    s.depth = 1;
+}
+
+// ------------------------------------------------------------------ BSDF
+RT_HD void onb(V3 n, V3 &t, V3 &b) {
+    float sign = n.z >= 0.f ? 1.f : -1.f;
+    float a = -1.f / (sign + n.z);
+    float bb = n.x * n.y * a;
+    t = v3(1.f + sign * n.x * n.x * a, sign * bb, -sign * n.x);
+    b = v3(bb, sign + n.y * n.y * a, -n.y);
+}
+
+RT_HD V3 adapt_shading_normal(V3 ns, V3 ng, V3 wo) {
+    float c = dot(wo, ns);
+    V3 r = 2.f * c * ns - wo;
+    float a = dot(r, ng);
+    if (a >= kAdaptEps) return ns;
+    const float e = kAdaptEps;
+    float sq = e * sqrtf(fmaxf(0.f, (1.f - a * a) / (1.f - e * e)));
+    float t = sq - a;
+    V3 rp = r + t * ng;
+    float lr = length(rp);
+    if (!(lr > 1e-12f)) return ng;
+    rp = rp * (1.f / lr);
+    V3 h = wo + rp;
+    float lh = length(h);
+    if (!(lh > 1e-12f)) return ng;
+    return h * (1.f / lh);
+}
+
+RT_HD float ggx_D(float a2, float ch) {
+    if (ch <= 0.f) return 0.f;
+    float k = ch * ch * (a2 - 1.f) + 1.f;
+    return a2 / (kPi * k * k);
+}
+RT_HD float ggx_lambda(float a2, float c) {
+    float c2 = c * c;
+    float t2 = fmaxf(0.f, 1.f - c2) / c2;
+    return 0.5f * (-1.f + sqrtf(1.f + a2 * t2));
+}
+RT_HD float schlick(float c) {
+    float m = 1.f - fmaxf(0.f, fminf(1.f, c));
+    float m2 = m * m;
+    return kF0 + (1.f - kF0) * m2 * m2 * m;
+}
+
+struct Material {
+    V3 albedo;
+    float alpha;   // roughness^2, >= 1e-4
+    float w;       // GGX weight
+};
+
+RT_HD void bsdf_eval(const Material &m, V3 ns, V3 wo, V3 wi, V3 &f, float &pdf) {
+    float co = dot(wo, ns), ci = dot(wi, ns);
+    f = v3(0.f, 0.f, 0.f);
+    pdf = 0.f;
+    if (co <= 0.f || ci <= 0.f) return;
+    float a2 = m.alpha * m.alpha;
+    V3 h = normalize(wo + wi);
+    float ch = dot(h, ns), cih = dot(wi, h);
+    float D = ggx_D(a2, ch);
+    float lo = ggx_lambda(a2, co);
+    float G2 = 1.f / (1.f + lo + ggx_lambda(a2, ci));
+    float spec = D * G2 * schlick(cih) / (4.f * co * ci);
+    float kd = (1.f - m.w) * kInvPi;
+    f = v3(m.w * spec + kd * m.albedo.x, m.w * spec + kd * m.albedo.y, m.w * spec + kd * m.albedo.z);
+    float pdf_spec = D / ((1.f + lo) * 4.f * co);
+    pdf = m.w * pdf_spec + (1.f - m.w) * ci * kInvPi;
+}
+
+RT_HD V3 ggx_vndf(float alpha, V3 v, float u1, float u2) {
+    V3 vh = normalize(v3(alpha * v.x, alpha * v.y, v.z));
+    float lensq = vh.x * vh.x + vh.y * vh.y;
+    V3 T1 = lensq > 0.f ? v3(-vh.y, vh.x, 0.f) * (1.f / sqrtf(lensq)) : v3(1.f, 0.f, 0.f);
+    V3 T2 = cross(vh, T1);
+    float r = sqrtf(u1), phi = 2.f * kPi * u2;
+    float sp, cp;
+#ifdef __CUDA_ARCH__
+    sincosf(phi, &sp, &cp);
+#else
+    sp = sinf(phi); cp = cosf(phi);
+#endif
+    float t1 = r * cp, t2 = r * sp;
+    float s = 0.5f * (1.f + vh.z);
+    t2 = (1.f - s) * sqrtf(fmaxf(0.f, 1.f - t1 * t1)) + s * t2;
+    float tz = sqrtf(fmaxf(0.f, 1.f - t1 * t1 - t2 * t2));
+    V3 nh = t1 * T1 + t2 * T2 + tz * vh;
+    return normalize(v3(alpha * nh.x, alpha * nh.y, fmaxf(0.f, nh.z)));
+}
+
+RT_HD bool bsdf_sample(const Material &m, V3 ns, V3 wo, float u_lobe, float u1, float u2, V3 &wi, V3 &f,
+                       float &pdf) {
+    V3 t, b;
+    onb(ns, t, b);
+    float co = dot(wo, ns);
+    if (co <= 0.f) return false;
+    V3 local;
+    if (u_lobe < m.w) {
+        V3 vl = v3(dot(wo, t), dot(wo, b), co);
+        V3 h = ggx_vndf(m.alpha, vl, u1, u2);
+        local = 2.f * dot(vl, h) * h - vl;
+    } else {
+        float r = sqrtf(u1), phi = 2.f * kPi * u2;
+        float sp, cp;
+#ifdef __CUDA_ARCH__
+        sincosf(phi, &sp, &cp);
+#else
+        sp = sinf(phi); cp = cosf(phi);
+#endif
+        local = v3(r * cp, r * sp, sqrtf(fmaxf(0.f, 1.f - u1)));
+    }
+    wi = normalize(local.x * t + local.y * b + local.z * ns);
+    bsdf_eval(m, ns, wo, wi, f, pdf);
+    return pdf > 0.f;
+}
+
+RT_HD Material load_material(const DevScene &sc, uint32_t mid) {
+    float4 a = ldg(sc.mat_a + mid);
+    float4 b = ldg(sc.mat_b + mid);
+    Material m;
+    m.albedo = v3(a.x, a.y, a.z);
+    m.alpha = fmaxf(a.w * a.w, 1e-4f);
+    m.w = b.w;
+    return m;
+}
+
+// --------------------------------------------------------------- lights
+RT_HD float mis_weight(int mode, float pa, float pb) {
+    if (mode == 1) return pa / (pa + pb);
+    float a = pa * pa, b = pb * pb;
+    return a / (a + b);
+}
+
+RT_HD V3 tri_vertex(const DevScene &sc, uint32_t prim, int k) {
+    uint32_t vi = ldg(sc.indices + 3 * (size_t)prim + k);
+    const float *v = sc.vertices + 3 * (size_t)vi;
+    return v3(ldg(v), ldg(v + 1), ldg(v + 2));
+}
+
+RT_HD V3 tri_emission(const DevScene &sc, uint32_t prim, float b1, float b2) {
+    uint32_t mid = ldg(sc.tri_material + prim);
+    float4 e = ldg(sc.mat_b + mid);
+    V3 Le = v3(e.x, e.y, e.z);
+    int32_t tex = ldg(sc.mat_tex + mid);
+    if (tex < 0) return Le;
+    float b0 = 1.f - b1 - b2;
+    uint32_t i0 = ldg(sc.indices + 3 * (size_t)prim), i1 = ldg(sc.indices + 3 * (size_t)prim + 1),
+             i2 = ldg(sc.indices + 3 * (size_t)prim + 2);
+    float u = b0 * ldg(sc.uvs + 2 * (size_t)i0) + b1 * ldg(sc.uvs + 2 * (size_t)i1) + b2 * ldg(sc.uvs + 2 * (size_t)i2);
+    float v = b0 * ldg(sc.uvs + 2 * (size_t)i0 + 1) + b1 * ldg(sc.uvs + 2 * (size_t)i1 + 1) +
+              b2 * ldg(sc.uvs + 2 * (size_t)i2 + 1);
+    int x = (int)floorf(fminf(1.f, fmaxf(0.f, u)) * (float)sc.tex_w);
+    int y = (int)floorf(fminf(1.f, fmaxf(0.f, v)) * (float)sc.tex_h);
+    x = x >= sc.tex_w ? sc.tex_w - 1 : x;
+    y = y >= sc.tex_h ? sc.tex_h - 1 : y;
+    const float *t = sc.textures + 3 * (((size_t)tex * sc.tex_h + y) * sc.tex_w + x);
+    return v3(Le.x * ldg(t), Le.y * ldg(t + 1), Le.z * ldg(t + 2));
+}
+
+// Equirectangular texel of a direction (row 0 looks at +y).
+RT_HD int env_texel(const DevScene &sc, V3 w) {
+    float cy = fmaxf(-1.f, fminf(1.f, w.y));
+    float th = acosf(cy);
+    float ph = atan2f(w.z, w.x);
+    if (ph < 0.f) ph += 2.f * kPi;
+    int x = (int)floorf(ph * (1.f / (2.f * kPi)) * (float)sc.env_w);
+    int y = (int)floorf(th * kInvPi * (float)sc.env_h);
+    x = x < 0 ? 0 : (x >= sc.env_w ? sc.env_w - 1 : x);
+    y = y < 0 ? 0 : (y >= sc.env_h ? sc.env_h - 1 : y);
+    return y * sc.env_w + x;
+}
+
+RT_HD float envw(const DevScene &sc, int level, int x, int y) {
+    int w = sc.env_w >> level;
+    return ldg(sc.env_pyr + sc.env_off_h[level] + (int64_t)y * w + x);
+}
+
+RT_HD int choose2(float a, float b, float &u) {
+    float p = a / (a + b);
+    if (u < p) { u = u / p; return 0; }
+    u = (u - p) / (1.f - p);
+    if (u >= 1.f) u = 0.99999994f;
+    return 1;
+}
+
+// Pyramid descent (Sec. 2.1.2): column by u then row by v at each level,
+// then a uniform direction in (phi, cos theta) inside the texel.
+RT_HD V3 env_sample(const DevScene &sc, float u, float v) {
+    int top = sc.env_levels - 1;
+    int x = choose2(envw(sc, top, 0, 0), envw(sc, top, 1, 0), u), y = 0;
+    for (int l = top - 1; l >= 0; --l) {
+        float left = envw(sc, l, 2 * x, 2 * y) + envw(sc, l, 2 * x, 2 * y + 1);
+        float right = envw(sc, l, 2 * x + 1, 2 * y) + envw(sc, l, 2 * x + 1, 2 * y + 1);
+        x = 2 * x + choose2(left, right, u);
+        y = 2 * y + choose2(envw(sc, l, x, 2 * y), envw(sc, l, x, 2 * y + 1), v);
+    }
+    float phi = 2.f * kPi * ((float)x + u) / (float)sc.env_w;
+    float c0 = cosf(kPi * (float)y / (float)sc.env_h), c1 = cosf(kPi * (float)(y + 1) / (float)sc.env_h);
+    float ct = c0 - v * (c0 - c1);
+    float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
+    float sp, cp;
+#ifdef __CUDA_ARCH__
+    sincosf(phi, &sp, &cp);
+#else
+    sp = sinf(phi); cp = cosf(phi);
+#endif
+    return v3(st * cp, ct, st * sp);
+}
+
+// Ray origin moved off the surface along n by an offset that grows with the
+// magnitude of the position (integer-ULP offset as in Waechter and Binder,
+// "A fast and robust method for avoiding self-intersection", 2019).
+RT_HD V3 offset_origin(V3 p, V3 n) {
+    const float kOrigin = 1.f / 32.f, kFloatScale = 1.f / 65536.f, kIntScale = 256.f;
+    float pc[3] = {p.x, p.y, p.z}, nc[3] = {n.x, n.y, n.z}, out[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int of = (int)(kIntScale * nc[a]);
+        int bits = (int)as_uint(pc[a]);
+        float pi = as_float((uint32_t)(bits + (pc[a] < 0.f ? -of : of)));
+        out[a] = fabsf(pc[a]) < kOrigin ? pc[a] + kFloatScale * nc[a] : pi;
+    }
+    return v3(out[0], out[1], out[2]);
+}
+
+// --------------------------------------------------------------- shading
+// Shade the hit of the pending ray of `s`. Returns bit 0 when the path
+// continues (new pending ray in s.o, s.d) and bit 1 when `sh` holds a shadow
+// ray whose unoccluded contribution must be added to s.L.
+RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh) {
+    const DevScene &sc = P.sc;
+    const int mode = P.mis_mode;
+    const uint32_t v = s.depth;
+    if (h.prim == RT_MISS) {
+        if (sc.env_w > 0) {
+            int tx = env_texel(sc, s.d);
+            float4 e = ldg(sc.env + tx);
+            float w = 1.f;
+            if (v > 1) {
+                if (mode == 3) w = 1.f;
+                else if (mode == 2) w = 0.f;
+                else w = sc.p_env > 0.f ? mis_weight(mode, s.prev_pdf, sc.p_env * e.w) : 1.f;
+            }
+            s.L = s.L + mul(s.beta, v3(e.x, e.y, e.z)) * w;
+        }
+        return 0;
+    }
+    const uint32_t prim = h.prim;
+    V3 v0 = tri_vertex(sc, prim, 0), v1 = tri_vertex(sc, prim, 1), v2 = tri_vertex(sc, prim, 2);
+    float b0 = 1.f - h.b1 - h.b2;
+    V3 x = b0 * v0 + h.b1 * v1 + h.b2 * v2;
+    V3 ng = normalize(cross(v1 - v0, v2 - v0));
+    V3 wo = -s.d;
+    float cog = dot(wo, ng);
+    float lpa = ldg(sc.tri_light_pdf_area + prim);
+    if (cog > 0.f && lpa > 0.f) {
+        V3 Le = tri_emission(sc, prim, h.b1, h.b2);
+        float w = 1.f;
+        if (v > 1) {
+            if (mode == 3) w = 1.f;
+            else if (mode == 2) w = 0.f;
+            else w = mis_weight(mode, s.prev_pdf, lpa * h.t * h.t / cog);
+        }
+        s.L = s.L + mul(s.beta, Le) * w;
+    }
+    if (v == P.max_depth + 1) return 0;
+    if (cog < 0.f) ng = -ng;
+    V3 ns = ng;
+    if (sc.normals) {
+        uint32_t i0 = ldg(sc.indices + 3 * (size_t)prim), i1 = ldg(sc.indices + 3 * (size_t)prim + 1),
+                 i2 = ldg(sc.indices + 3 * (size_t)prim + 2);
+        const float *n0 = sc.normals + 3 * (size_t)i0, *n1 = sc.normals + 3 * (size_t)i1,
+                    *n2 = sc.normals + 3 * (size_t)i2;
+        ns = normalize(b0 * v3(ldg(n0), ldg(n0 + 1), ldg(n0 + 2)) + h.b1 * v3(ldg(n1), ldg(n1 + 1), ldg(n1 + 2)) +
+                       h.b2 * v3(ldg(n2), ldg(n2 + 1), ldg(n2 + 2)));
+        if (dot(ns, ng) < 0.f) ns = -ns;
+    }
+    ns = adapt_shading_normal(ns, ng, wo);
+    Material m = load_material(sc, ldg(sc.tri_material + prim));
+    const int base = 2 + 7 * (int)(v - 1);
+    V3 xo = offset_origin(x, ng);
+    int ret = 0;
+    // next-event estimation
+    if ((sc.num_lights > 0 || sc.p_env > 0.f) && mode != 3) {
+        float us = dim_value(P, s.index, base), ua = dim_value(P, s.index, base + 1),
+              ub = dim_value(P, s.index, base + 2);
+        V3 wi = v3(0.f, 0.f, 1.f), Le = v3(0.f, 0.f, 0.f);
+        float pdf_l = 0.f, tmax = INFINITY;
+        if (us < sc.p_env) {
+            wi = env_sample(sc, ua, ub);
+            float4 e = ldg(sc.env + env_texel(sc, wi));
+            Le = v3(e.x, e.y, e.z);
+            pdf_l = sc.p_env * e.w;
+        } else {
+            float u2 = (us - sc.p_env) / (1.f - sc.p_env);
+            float xn = u2 * (float)sc.num_lights;
+            uint32_t bin = (uint32_t)xn;
+            if (bin >= sc.num_lights) bin = sc.num_lights - 1;
+            float frac = xn - (float)bin;
+            float2 al = ldg(sc.alias + bin);
+            uint32_t li = frac < al.x ? bin : as_uint(al.y);
+            uint32_t lt = ldg(sc.light_tri + li);
+            V3 l0 = tri_vertex(sc, lt, 0), l1 = tri_vertex(sc, lt, 1), l2 = tri_vertex(sc, lt, 2);
+            float sq = sqrtf(ua);
+            float lb1 = sq * (1.f - ub), lb2 = sq * ub;
+            V3 y = (1.f - sq) * l0 + lb1 * l1 + lb2 * l2;
+            V3 dv = y - x;
+            float dist = length(dv);
+            if (dist > 0.f) {
+                wi = dv * (1.f / dist);
+                V3 lng = normalize(cross(l1 - l0, l2 - l0));
+                float cl = -dot(wi, lng);
+                if (cl > 0.f) {
+                    pdf_l = ldg(sc.tri_light_pdf_area + lt) * dist * dist / cl;
+                    Le = tri_emission(sc, lt, lb1, lb2);
+                    tmax = dist * (1.f - kShadowEps);
+                }
+            }
+        }
+        if (pdf_l > 0.f && dot(wi, ng) > 0.f) {
+            V3 f;
+            float pdf_b;
+            bsdf_eval(m, ns, wo, wi, f, pdf_b);
+            if (pdf_b > 0.f) {
+                float w = mode == 2 ? 1.f : mis_weight(mode, pdf_l, pdf_b);
+                float k = dot(wi, ns) * w / pdf_l;
+                sh.o = xo;
+                sh.d = wi;
+                sh.tmax = tmax;
+                sh.contrib = mul(mul(s.beta, f), Le) * k;
+                ret |= 2;
+            }
+        }
+    }
+    // continuation
+    V3 wi, f;
+    float pdf;
+    if (!bsdf_sample(m, ns, wo, dim_value(P, s.index, base + 3), dim_value(P, s.index, base + 4),
+                     dim_value(P, s.index, base + 5), wi, f, pdf))
+        return ret;
+    if (dot(wi, ng) <= 0.f) return ret;
+    float ci = dot(wi, ns);
+    s.beta = mul(s.beta, f) * (ci / pdf);
+    if (P.rr && v >= 3) {
+        float q = fmaxf(0.05f, 1.f - maxc(s.beta));
+        if (dim_value(P, s.index, base + 6) < q) return ret;
+        s.beta = s.beta * (1.f / (1.f - q));
+    }
+    if (s.beta.x == 0.f && s.beta.y == 0.f && s.beta.z == 0.f) return ret;
+    s.prev_pdf = pdf;
+    s.o = xo;
+    s.d = wi;
+    s.depth = v + 1;
+    return ret | 1;
+}
+
+// Whole path in one thread: the megakernel body (Sec. 3.1 hybrid scheme)
+// and the host debug path.
+#pragma nv_exec_check_disable
+template <class TraceClosest, class TraceAny>
+RT_HD void finish_path(const RenderParams &P, PathState &s, TraceClosest closest, TraceAny any,
+                       uint32_t &ext_rays, uint32_t &shadow_rays) {
+    for (;;) {
+        Hit h;
+        closest(s.o, s.d, h);
+        ++ext_rays;
+        ShadowRay sh;
+        int r = shade(P, s, h, sh);
+        if (r & 2) {
+            ++shadow_rays;
+            if (!any(sh.o, sh.d, sh.tmax)) s.L = s.L + sh.contrib;
+        }
+        if (!(r & 1)) break;
+    }
+}
+
+}  // namespace rtg

@@ -1,0 +1,298 @@
+// Ray casting on the 8-wide compressed BVH: watertight ray/triangle
+// intersection (the paper relies on watertight traversal so that no boundary
+// crossing is missed, Sec. 2.3) and stack-based traversal of node groups.
+//
+// Every routine is __host__ __device__: the kernels run them on the GPU, and
+// the library's host debug entry point runs the very same code on the CPU so
+// that the BVH build and traversal can be checked without a device.
+#pragma once
+
+#include "common.cuh"
+
+namespace rtg {
+
+// ----------------------------------------------------------- intrinsics
+RT_HD int clz32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+    return __clz(x);
+#else
+    return x ? __builtin_clz(x) : 32;
+#endif
+}
+RT_HD int popc32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+    return __popc(x);
+#else
+    return __builtin_popcount(x);
+#endif
+}
+RT_HD int ffs32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+    return __ffs(x);
+#else
+    return __builtin_ffs(x);
+#endif
+}
+template <class T>
+RT_HD T ldg(const T *p) {
+#ifdef __CUDA_ARCH__
+    return __ldg(p);
+#else
+    return *p;
+#endif
+}
+// IEEE operations that the compiler may not fuse into FMAs: the watertight
+// test needs the mirrored edge functions of two neighbouring triangles to be
+// exact negatives of each other.
+RT_HD float mul_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+RT_HD float sub_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fsub_rn(a, b);
+#else
+    return a - b;
+#endif
+}
+RT_HD double dmul_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+    return __dmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+RT_HD double dsub_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+    return __dsub_rn(a, b);
+#else
+    return a - b;
+#endif
+}
+RT_HD float fma_rn(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+    return __fmaf_rn(a, b, c);
+#else
+    return fmaf(a, b, c);
+#endif
+}
+
+struct Ray {
+    V3 o, d;
+    float tmin, tmax;
+};
+
+struct Hit {
+    uint32_t prim, inst;
+    float t, b1, b2;
+};
+
+// Per-ray constants of the watertight test (Woop, Benthin, Wald 2013) and of
+// the slab test.
+struct RayPre {
+    V3 o, d;
+    V3 inv;          // 1 / d with zero components replaced by +-1e-20
+    uint32_t oct;    // bit a set when d[a] < 0
+    int kx, ky, kz;
+    float Sx, Sy, Sz;
+};
+
+RT_HD float comp(V3 v, int a) { return a == 0 ? v.x : (a == 1 ? v.y : v.z); }
+
+RT_HD RayPre prepare(const Ray &r) {
+    RayPre p;
+    p.o = r.o;
+    p.d = r.d;
+    float dx = fabsf(r.d.x) < 1e-20f ? copysignf(1e-20f, r.d.x) : r.d.x;
+    float dy = fabsf(r.d.y) < 1e-20f ? copysignf(1e-20f, r.d.y) : r.d.y;
+    float dz = fabsf(r.d.z) < 1e-20f ? copysignf(1e-20f, r.d.z) : r.d.z;
+    p.inv = v3(1.f / dx, 1.f / dy, 1.f / dz);
+    p.oct = (r.d.x < 0.f ? 1u : 0u) | (r.d.y < 0.f ? 2u : 0u) | (r.d.z < 0.f ? 4u : 0u);
+    float ax = fabsf(r.d.x), ay = fabsf(r.d.y), az = fabsf(r.d.z);
+    int kz = 0;
+    if (ay > ax) kz = 1;
+    if (az > fmaxf(ax, ay)) kz = 2;
+    int kx = kz + 1 == 3 ? 0 : kz + 1;
+    int ky = kx + 1 == 3 ? 0 : kx + 1;
+    float dkz = comp(r.d, kz);
+    if (dkz < 0.f) { int t = kx; kx = ky; ky = t; }
+    p.kx = kx; p.ky = ky; p.kz = kz;
+    p.Sx = comp(r.d, kx) / dkz;
+    p.Sy = comp(r.d, ky) / dkz;
+    p.Sz = 1.f / dkz;
+    return p;
+}
+
+// Watertight intersection; accepts t in (tmin, tmax) and t <= tbest.
+RT_HD bool intersect_tri(const RayPre &rp, V3 v0, V3 v1, V3 v2, float tmin, float tmax, float tbest,
+                         float &t, float &b1, float &b2) {
+    V3 A = v0 - rp.o, B = v1 - rp.o, C = v2 - rp.o;
+    float Akx = comp(A, rp.kx), Aky = comp(A, rp.ky), Akz = comp(A, rp.kz);
+    float Bkx = comp(B, rp.kx), Bky = comp(B, rp.ky), Bkz = comp(B, rp.kz);
+    float Ckx = comp(C, rp.kx), Cky = comp(C, rp.ky), Ckz = comp(C, rp.kz);
+    float Ax = fma_rn(-rp.Sx, Akz, Akx), Ay = fma_rn(-rp.Sy, Akz, Aky);
+    float Bx = fma_rn(-rp.Sx, Bkz, Bkx), By = fma_rn(-rp.Sy, Bkz, Bky);
+    float Cx = fma_rn(-rp.Sx, Ckz, Ckx), Cy = fma_rn(-rp.Sy, Ckz, Cky);
+    float U = sub_rn(mul_rn(Cx, By), mul_rn(Cy, Bx));
+    float V = sub_rn(mul_rn(Ax, Cy), mul_rn(Ay, Cx));
+    float W = sub_rn(mul_rn(Bx, Ay), mul_rn(By, Ax));
+    if (U == 0.f || V == 0.f || W == 0.f) {
+        // exact products in double decide the sign on an edge
+        U = (float)dsub_rn(dmul_rn((double)Cx, (double)By), dmul_rn((double)Cy, (double)Bx));
+        V = (float)dsub_rn(dmul_rn((double)Ax, (double)Cy), dmul_rn((double)Ay, (double)Cx));
+        W = (float)dsub_rn(dmul_rn((double)Bx, (double)Ay), dmul_rn((double)By, (double)Ax));
+    }
+    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return false;
+    float det = U + V + W;
+    if (det == 0.f) return false;
+    float Az = rp.Sz * Akz, Bz = rp.Sz * Bkz, Cz = rp.Sz * Ckz;
+    float T = U * Az + V * Bz + W * Cz;
+    float tt = T / det;
+    if (!(tt > tmin && tt < tmax && tt <= tbest)) return false;
+    float inv = 1.f / det;
+    t = tt;
+    b1 = V * inv;
+    b2 = W * inv;
+    return true;
+}
+
+RT_HD uint32_t byte_of(uint32_t lo4, uint32_t hi4, int i) {
+    uint32_t w = i < 4 ? lo4 : hi4;
+    return (w >> (8 * (i & 3))) & 0xFFu;
+}
+
+RT_HD float exp2i(int e) {
+#ifdef __CUDA_ARCH__
+    return __int_as_float((e + 127) << 23);
+#else
+    uint32_t b = (uint32_t)(e + 127) << 23;
+    float f;
+    memcpy(&f, &b, 4);
+    return f;
+#endif
+}
+
+RT_HD float as_float(uint32_t u) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+#endif
+}
+RT_HD uint32_t as_uint(float f) {
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(f);
+#else
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u;
+#endif
+}
+
+// Intersect the 8 child boxes of node (n0..n4); returns the internal-child
+// hit bits at 24 + (slot ^ oct) and, through tri_bits, the triangle bits.
+RT_HD uint32_t intersect_children(const RayPre &rp, uint4 n0, uint4 n1, uint4 n2, uint4 n3, uint4 n4,
+                                  float tmin, float tmax, uint32_t &tri_bits) {
+    V3 p = v3(as_float(n0.x), as_float(n0.y), as_float(n0.z));
+    int ex = (int)(int8_t)(n0.w & 0xFF), ey = (int)(int8_t)((n0.w >> 8) & 0xFF),
+        ez = (int)(int8_t)((n0.w >> 16) & 0xFF);
+    uint32_t imask = n0.w >> 24;
+    float ax = exp2i(ex) * rp.inv.x, ay = exp2i(ey) * rp.inv.y, az = exp2i(ez) * rp.inv.z;
+    float bx = (p.x - rp.o.x) * rp.inv.x, by = (p.y - rp.o.y) * rp.inv.y, bz = (p.z - rp.o.z) * rp.inv.z;
+    const bool sx = rp.inv.x < 0.f, sy = rp.inv.y < 0.f, sz = rp.inv.z < 0.f;
+    uint32_t inner = 0, tris = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float lx = (float)byte_of(n2.x, n2.y, i), hx = (float)byte_of(n2.z, n2.w, i);
+        float ly = (float)byte_of(n3.x, n3.y, i), hy = (float)byte_of(n3.z, n3.w, i);
+        float lz = (float)byte_of(n4.x, n4.y, i), hz = (float)byte_of(n4.z, n4.w, i);
+        float nx = fma_rn(sx ? hx : lx, ax, bx), fx = fma_rn(sx ? lx : hx, ax, bx);
+        float ny = fma_rn(sy ? hy : ly, ay, by), fy = fma_rn(sy ? ly : hy, ay, by);
+        float nz = fma_rn(sz ? hz : lz, az, bz), fz = fma_rn(sz ? lz : hz, az, bz);
+        float t0 = fmaxf(fmaxf(nx, ny), fmaxf(nz, tmin));
+        float t1 = fminf(fminf(fx, fy), fminf(fz, tmax));
+        bool hit = t0 <= t1 * 1.000001f;
+        uint32_t meta = byte_of(n1.z, n1.w, i);
+        if (hit && meta) {
+            if (imask & (1u << i)) inner |= 1u << (24 + (i ^ rp.oct));
+            else tris |= (meta >> 5) << (meta & 31u);
+        }
+    }
+    tri_bits = tris;
+    return inner;
+}
+
+struct TraceResult {
+    bool overflow;
+    uint32_t nodes;   // nodes visited
+    uint32_t tris;    // triangles tested
+};
+
+// Closest hit (any_hit = false) or any hit (true) against one BVH.
+// On return hit.prim == RT_MISS if nothing was found; hit.t, b1, b2 valid
+// otherwise. `hit` may hold a previous best (used for two-level scenes).
+template <bool kAnyHit>
+RT_HD TraceResult traverse(const uint4 *nodes, const float4 *tris, uint32_t root, const Ray &ray, Hit &hit) {
+    TraceResult res{false, 0u, 0u};
+    RayPre rp = prepare(ray);
+    float tbest = hit.prim == RT_MISS ? ray.tmax : hit.t;
+    uint2 stack[kStackSize];
+    int sp = 0;
+    // a virtual group holding the root as its only internal child (slot 0)
+    uint2 ng = make_uint2(root, (1u << (24 + (0u ^ rp.oct))) | 1u);
+    for (;;) {
+        uint32_t tbase = 0, tmask = 0;
+        if (ng.y & 0xFF000000u) {
+            int bit = 31 - clz32(ng.y);
+            uint32_t slot = ((uint32_t)bit - 24u) ^ rp.oct;
+            uint32_t rel = popc32((ng.y & 0xFFu) & ((1u << slot) - 1u));
+            uint32_t child = ng.x + rel;
+            ng.y &= ~(1u << bit);
+            if (ng.y & 0xFF000000u) {
+                if (sp == kStackSize) { res.overflow = true; break; }
+                stack[sp++] = ng;
+            }
+            const uint4 *N = nodes + 5 * (size_t)child;
+            uint4 n0 = ldg(N), n1 = ldg(N + 1), n2 = ldg(N + 2), n3 = ldg(N + 3), n4 = ldg(N + 4);
+            ++res.nodes;
+            uint32_t tb;
+            uint32_t inner = intersect_children(rp, n0, n1, n2, n3, n4, ray.tmin, tbest, tb);
+            ng = make_uint2(n1.x, inner | (n0.w >> 24));
+            tbase = n1.y;
+            tmask = tb;
+        } else {
+            ng.y = 0u;
+        }
+        while (tmask) {
+            int k = ffs32(tmask) - 1;
+            tmask &= tmask - 1u;
+            const float4 *T = tris + 3 * (size_t)(tbase + (uint32_t)k);
+            float4 a = ldg(T), b = ldg(T + 1), c = ldg(T + 2);
+            ++res.tris;
+            float t, u, v;
+            if (intersect_tri(rp, f4xyz(a), f4xyz(b), f4xyz(c), ray.tmin, ray.tmax, tbest, t, u, v)) {
+                uint32_t prim = as_uint(a.w);
+                if (kAnyHit) {
+                    hit.prim = prim; hit.t = t; hit.b1 = u; hit.b2 = v;
+                    return res;
+                }
+                if (t < tbest || hit.prim == RT_MISS || prim < hit.prim) {
+                    hit.prim = prim; hit.t = t; hit.b1 = u; hit.b2 = v;
+                    tbest = t;
+                }
+            }
+        }
+        if (!(ng.y & 0xFF000000u)) {
+            if (sp == 0) break;
+            ng = stack[--sp];
+        }
+    }
+    return res;
+}
+
+}  // namespace rtg

@@ -1,0 +1,437 @@
+"""Thin Python binding of the C ABI in include/rt.h (ctypes).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library. Device buffers are torch CUDA tensors (PyTorch provides device
+memory and streams); host buffers are numpy arrays. The library must have
+been built (``paper_1705_01263_gb300.build.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+RT_MISS = 0xFFFFFFFF
+STATUS = {0: "RT_OK", 1: "RT_INVALID_ARG", 2: "RT_OOM", 3: "RT_CUDA_ERROR", 4: "RT_TIMEOUT",
+          5: "RT_QUEUE_OVERFLOW", 6: "RT_STACK_OVERFLOW", 7: "RT_NOT_SUPPORTED"}
+RT_OK, RT_TIMEOUT = 0, 4
+
+
+class RtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class rt_scene_desc(C.Structure):
+    _fields_ = [
+        ("num_vertices", C.c_int64), ("num_triangles", C.c_int64),
+        ("vertices", C.c_void_p), ("normals", C.c_void_p), ("uvs", C.c_void_p),
+        ("indices", C.c_void_p), ("tri_material", C.c_void_p),
+        ("num_materials", C.c_int32), ("albedo", C.c_void_p), ("roughness", C.c_void_p),
+        ("ggx_weight", C.c_void_p), ("emission", C.c_void_p), ("emission_tex", C.c_void_p),
+        ("num_textures", C.c_int32), ("tex_width", C.c_int32), ("tex_height", C.c_int32),
+        ("textures", C.c_void_p),
+        ("env_width", C.c_int32), ("env_height", C.c_int32), ("env", C.c_void_p),
+        ("num_meshes", C.c_int32), ("mesh_tri_offset", C.c_void_p),
+        ("num_instances", C.c_int32), ("instance_mesh", C.c_void_p), ("instance_xform", C.c_void_p),
+    ]
+
+
+class rt_rays(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("ox", "oy", "oz", "dx", "dy", "dz", "tmin", "tmax")]
+
+
+class rt_hits(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("prim", "inst", "t", "u", "v")]
+
+
+class rt_camera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("look_at", C.c_float * 3), ("up", C.c_float * 3),
+                ("vfov_deg", C.c_float), ("width", C.c_uint32), ("height", C.c_uint32)]
+
+
+class rt_stats(C.Structure):
+    _fields_ = [("paths", C.c_uint64), ("extension_rays", C.c_uint64), ("shadow_rays", C.c_uint64),
+                ("waves", C.c_uint32), ("wavefront_steps", C.c_uint32), ("tail_launches", C.c_uint32),
+                ("kernel_launches", C.c_uint32), ("trace_ms", C.c_double), ("shade_ms", C.c_double),
+                ("shadow_ms", C.c_double), ("megakernel_ms", C.c_double), ("other_ms", C.c_double),
+                ("trace_launches", C.c_uint32), ("ext_nodes", C.c_uint64), ("ext_tris", C.c_uint64),
+                ("shadow_nodes", C.c_uint64), ("shadow_tris", C.c_uint64)]
+
+
+class rt_render_opts(C.Structure):
+    _fields_ = [("filter_sigma", C.c_float), ("rr_enable", C.c_int32), ("mis_mode", C.c_int32),
+                ("seed", C.c_uint64), ("time_budget_ms", C.c_double), ("max_paths_in_flight", C.c_uint32),
+                ("megakernel_only", C.c_int32), ("sort_by_material", C.c_int32),
+                ("tail_threshold", C.c_uint32), ("block_size", C.c_uint32),
+                ("abort_flag", C.c_void_p), ("guide", C.c_void_p), ("stats", C.POINTER(rt_stats)),
+                ("profile", C.c_int32)]
+
+
+class rt_guide_opts(C.Structure):
+    _fields_ = [("batch", C.c_uint32), ("learning_rate", C.c_float), ("alpha", C.c_float),
+                ("train_steps", C.c_uint32), ("seed", C.c_uint64)]
+
+
+_lib = None
+
+EXPORTED = [
+    "rt_scene_create", "rt_scene_destroy", "rt_scene_info", "rt_trace", "rt_film_create", "rt_film_destroy",
+    "rt_film_clear", "rt_film_next_iteration", "rt_film_seek", "rt_film_buffers", "rt_film_resolve", "rt_render",
+    "rt_sample_index", "rt_halton", "rt_divide_u64_host", "rt_guide_create", "rt_guide_destroy",
+    "rt_guide_num_params", "rt_guide_get_params", "rt_guide_set_params", "rt_guide_state_size", "rt_guide_save",
+    "rt_guide_load", "rt_guide_infer", "rt_guide_loss_grad", "rt_guide_train_step", "rt_last_error",
+    "rt_status_string",
+]
+
+
+def lib(build_if_missing: bool = True):
+    """Load the CUDA library (building it first if needed). Raises if the
+    library cannot be built or loaded: there is no CPU fallback."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library missing: {path}")
+        L = C.CDLL(path)
+        _declare(L)
+        _lib = L
+    return _lib
+
+
+def _declare(L):
+    vp, i64, u32, u64, i32 = C.c_void_p, C.c_int64, C.c_uint32, C.c_uint64, C.c_int32
+    sigs = {
+        "rt_scene_create": [C.POINTER(rt_scene_desc), C.POINTER(vp)],
+        "rt_debug_scene_create_host": [C.POINTER(rt_scene_desc), C.POINTER(vp)],
+        "rt_scene_destroy": [vp],
+        "rt_scene_info": [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)],
+        "rt_trace": [vp, C.POINTER(rt_rays), i64, C.POINTER(rt_hits), i32, vp],
+        "rt_film_create": [u32, u32, C.POINTER(vp)],
+        "rt_film_destroy": [vp],
+        "rt_film_clear": [vp, vp],
+        "rt_film_next_iteration": [vp, C.POINTER(u32)],
+        "rt_film_seek": [vp, u32],
+        "rt_film_buffers": [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)],
+        "rt_film_resolve": [vp, vp, vp, vp],
+        "rt_render": [vp, C.POINTER(rt_camera), u32, u32, vp, C.POINTER(rt_render_opts), vp],
+        "rt_sample_index": [u32, u32, vp, vp, vp, i64, vp, vp],
+        "rt_halton": [u32, u32, u64, vp, i64, i32, vp, vp],
+        "rt_divide_u64_host": [vp, i64, u32, vp],
+        "rt_debug_trace_host": [vp, vp, i64, i32, vp, vp, vp, vp, vp],
+        "rt_debug_render_host": [vp, C.POINTER(rt_camera), u32, C.POINTER(rt_render_opts), vp, vp, vp, i64, vp],
+        "rt_debug_halton_host": [u32, u32, u64, vp, i64, i32, vp],
+        "rt_debug_sample_index_host": [u32, u32, u32, u32, u32, C.POINTER(u64)],
+    }
+    for name, args in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.rt_last_error.restype = C.c_char_p
+    L.rt_status_string.restype = C.c_char_p
+    L.rt_status_string.argtypes = [C.c_int]
+    if hasattr(L, "rt_guide_num_params"):
+        L.rt_guide_num_params.restype = C.c_int64
+        L.rt_guide_num_params.argtypes = []
+    for name, args in {
+        "rt_guide_create": [vp, C.POINTER(rt_guide_opts), C.POINTER(vp)],
+        "rt_guide_destroy": [vp],
+        "rt_guide_get_params": [vp, vp],
+        "rt_guide_set_params": [vp, vp],
+        "rt_guide_state_size": [vp, C.POINTER(i64)],
+        "rt_guide_save": [vp, vp],
+        "rt_guide_load": [vp, vp],
+        "rt_guide_infer": [vp, vp, i64, vp, vp],
+        "rt_guide_loss_grad": [vp, vp, vp, vp, i64, vp, C.POINTER(C.c_float), vp],
+        "rt_guide_train_step": [vp, vp, vp, vp, i64, vp],
+    }.items():
+        if hasattr(L, name):
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+
+
+def check(status: int):
+    if status != RT_OK:
+        raise RtError(status, lib().rt_last_error().decode())
+    return status
+
+
+def _ptr(t) -> Optional[int]:
+    """Device address of a torch tensor (or host address of a numpy array)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ------------------------------------------------------------------ scene
+class Scene:
+    """Device scene built from a scenes.SceneData (rt_scene_create)."""
+
+    def __init__(self, sd, host_only: bool = False):
+        self._keep = []
+        d = rt_scene_desc()
+
+        def arr(a, dt, cols=None):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(np.asarray(a, dtype=dt))
+            self._keep.append(a)
+            return a.ctypes.data
+
+        d.num_vertices = int(sd.vertices.shape[0])
+        d.num_triangles = int(sd.indices.shape[0])
+        d.vertices = arr(sd.vertices, np.float32)
+        d.normals = arr(sd.normals, np.float32)
+        d.uvs = arr(sd.uvs, np.float32)
+        d.indices = arr(sd.indices, np.uint32)
+        d.tri_material = arr(sd.tri_material, np.uint32)
+        d.num_materials = int(np.asarray(sd.roughness).size)
+        d.albedo = arr(sd.albedo, np.float32)
+        d.roughness = arr(sd.roughness, np.float32)
+        d.ggx_weight = arr(sd.ggx_weight, np.float32)
+        d.emission = arr(sd.emission, np.float32)
+        d.emission_tex = arr(sd.emission_tex, np.int32)
+        if sd.textures is not None:
+            d.num_textures, d.tex_height, d.tex_width = (int(x) for x in sd.textures.shape[:3])
+            d.textures = arr(sd.textures, np.float32)
+        if sd.env is not None:
+            d.env_height, d.env_width = int(sd.env.shape[0]), int(sd.env.shape[1])
+            d.env = arr(sd.env, np.float32)
+        if getattr(sd, "instance_mesh", None) is not None:
+            d.num_meshes = int(len(sd.mesh_tri_offset) - 1)
+            d.mesh_tri_offset = arr(sd.mesh_tri_offset, np.int64)
+            d.num_instances = int(len(sd.instance_mesh))
+            d.instance_mesh = arr(sd.instance_mesh, np.uint32)
+            d.instance_xform = arr(sd.instance_xform, np.float32)
+        self.desc = d
+        h = C.c_void_p()
+        fn = lib().rt_debug_scene_create_host if host_only else lib().rt_scene_create
+        check(fn(C.byref(d), C.byref(h)))
+        self.handle = h
+        self.host_only = host_only
+        self._keep = None  # the library copied everything
+
+    def info(self):
+        n, t, b = C.c_int64(), C.c_int64(), C.c_int64()
+        check(lib().rt_scene_info(self.handle, C.byref(n), C.byref(t), C.byref(b)))
+        return {"nodes": n.value, "leaf_tris": t.value, "device_bytes": b.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rt_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rt_scene_create(sd) -> Scene:
+    return Scene(sd)
+
+
+def rt_trace(scene: Scene, rays, any_hit: bool = False, hits=None, stream=None):
+    """rays: torch CUDA float32 tensor n x 8 (ox oy oz dx dy dz tmin tmax),
+    column-sliced into the SoA pointers (the tensor is transposed to 8 x n).
+    Returns (prim, inst, t, u, v) torch tensors."""
+    import torch
+    soa = rays.t().contiguous() if rays.shape[-1] == 8 else rays
+    n = soa.shape[1]
+    if hits is None:
+        hits = (torch.empty(n, dtype=torch.int32, device=soa.device),
+                torch.empty(n, dtype=torch.int32, device=soa.device),
+                torch.empty(n, dtype=torch.float32, device=soa.device),
+                torch.empty(n, dtype=torch.float32, device=soa.device),
+                torch.empty(n, dtype=torch.float32, device=soa.device))
+    r = rt_rays(*[soa[k].data_ptr() for k in range(8)])
+    h = rt_hits(*[x.data_ptr() for x in hits])
+    check(lib().rt_trace(scene.handle, C.byref(r), n, C.byref(h), int(any_hit), _stream(stream)))
+    return hits, soa
+
+
+class Film:
+    def __init__(self, width: int, height: int):
+        h = C.c_void_p()
+        check(lib().rt_film_create(width, height, C.byref(h)))
+        self.handle = h
+        self.width, self.height = width, height
+
+    def clear(self, stream=None):
+        check(lib().rt_film_clear(self.handle, _stream(stream)))
+
+    def next_iteration(self) -> int:
+        v = C.c_uint32()
+        check(lib().rt_film_next_iteration(self.handle, C.byref(v)))
+        return v.value
+
+    def seek(self, next_iteration: int):
+        check(lib().rt_film_seek(self.handle, next_iteration))
+
+    def buffers(self):
+        """(sum, sum2, count) as torch tensors viewing the film's device memory."""
+        import torch
+        s, s2, c = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        check(lib().rt_film_buffers(self.handle, C.byref(s), C.byref(s2), C.byref(c)))
+        n = self.width * self.height
+        return (_wrap_device(s.value, (self.height, self.width, 3), torch.float64),
+                _wrap_device(s2.value, (self.height, self.width, 3), torch.float64),
+                _wrap_device(c.value, (self.height, self.width), torch.int32))
+
+    def download(self):
+        import torch
+        torch.cuda.synchronize()
+        s, s2, c = self.buffers()
+        return s.cpu().numpy().copy(), s2.cpu().numpy().copy(), c.cpu().numpy().view(np.uint32).copy()
+
+    def resolve(self, mean=None, var=None, stream=None):
+        import torch
+        if mean is None:
+            mean = torch.empty((self.height, self.width, 3), dtype=torch.float32, device="cuda")
+        check(lib().rt_film_resolve(self.handle, mean.data_ptr(), None if var is None else var.data_ptr(),
+                                    _stream(stream)))
+        return mean, var
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rt_film_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _wrap_device(ptr: int, shape, dtype):
+    """Zero-copy torch view of library-owned device memory."""
+    import torch
+    n = int(np.prod(shape))
+    itemsize = torch.empty((), dtype=dtype).element_size()
+
+    class _Arr:
+        __cuda_array_interface__ = {
+            "shape": (n,), "typestr": {torch.float64: "<f8", torch.int32: "<i4", torch.float32: "<f4"}[dtype],
+            "data": (ptr, False), "version": 3, "strides": None,
+        }
+    t = torch.as_tensor(_Arr(), device="cuda")
+    return t.view(*shape)
+
+
+def rt_film_create(width: int, height: int) -> Film:
+    return Film(width, height)
+
+
+def make_camera(cam) -> rt_camera:
+    c = rt_camera()
+    for k in range(3):
+        c.eye[k], c.look_at[k], c.up[k] = cam.eye[k], cam.look_at[k], cam.up[k]
+    c.vfov_deg, c.width, c.height = cam.vfov_deg, cam.width, cam.height
+    return c
+
+
+def make_opts(sigma: float = 0.5, rr: bool = False, mis_mode: int = 0, seed: int = 0, time_budget_ms: float = 0.0,
+              max_paths: int = 0, megakernel_only: bool = False, sort_by_material: bool = False,
+              tail_threshold: int = 0, abort_flag=None, guide=None, stats: Optional[rt_stats] = None,
+              profile: int = 0):
+    o = rt_render_opts()
+    o.filter_sigma = sigma if sigma > 0 else -1.0
+    o.rr_enable, o.mis_mode, o.seed = int(rr), mis_mode, seed
+    o.time_budget_ms, o.max_paths_in_flight = time_budget_ms, max_paths
+    o.megakernel_only, o.sort_by_material, o.tail_threshold = int(megakernel_only), int(sort_by_material), tail_threshold
+    o.abort_flag = abort_flag
+    o.guide = guide.handle if guide is not None else None
+    if stats is not None:
+        o.stats = C.pointer(stats)
+    o.profile = profile
+    return o
+
+
+def rt_render(scene: Scene, cam, spp: int, max_depth: int, film: Film, opts: Optional[rt_render_opts] = None,
+              stream=None, allow_timeout: bool = False) -> int:
+    c = make_camera(cam)
+    o = opts if opts is not None else make_opts()
+    st = lib().rt_render(scene.handle, C.byref(c), spp, max_depth, film.handle, C.byref(o), _stream(stream))
+    if st == RT_TIMEOUT and allow_timeout:
+        return st
+    return check(st)
+
+
+def rt_sample_index(width, height, px, py, j, out=None, stream=None):
+    import torch
+    n = px.numel()
+    if out is None:
+        out = torch.empty(n, dtype=torch.int64, device=px.device)
+    check(lib().rt_sample_index(width, height, px.data_ptr(), py.data_ptr(), j.data_ptr(), n, out.data_ptr(),
+                                _stream(stream)))
+    return out
+
+
+def rt_halton(width, height, seed, indices, ndims, out=None, stream=None):
+    import torch
+    n = indices.numel()
+    if out is None:
+        out = torch.empty((n, ndims), dtype=torch.int32, device=indices.device)
+    check(lib().rt_halton(width, height, seed, indices.data_ptr(), n, ndims, out.data_ptr(), _stream(stream)))
+    return out
+
+
+def rt_divide_u64_host(n: np.ndarray, d: int) -> np.ndarray:
+    n = np.ascontiguousarray(n, np.uint64)
+    q = np.zeros_like(n)
+    check(lib().rt_divide_u64_host(n.ctypes.data, n.size, d, q.ctypes.data))
+    return q
+
+
+# -------------------------------------------------- host test hooks (CPU)
+def debug_trace_host(scene: Scene, rays: np.ndarray, any_hit: bool = False):
+    r = np.ascontiguousarray(rays, np.float32)
+    n = r.shape[0]
+    prim = np.zeros(n, np.uint32)
+    t, u, v = np.zeros(n, np.float32), np.zeros(n, np.float32), np.zeros(n, np.float32)
+    nodes = np.zeros(n, np.uint32)
+    check(lib().rt_debug_trace_host(scene.handle, r.ctypes.data, n, int(any_hit), prim.ctypes.data, t.ctypes.data,
+                                    u.ctypes.data, v.ctypes.data, nodes.ctypes.data))
+    return prim, t, u, v, nodes
+
+
+def debug_render_host(scene: Scene, cam, max_depth, px, py, j, opts: Optional[rt_render_opts] = None):
+    c = make_camera(cam)
+    o = opts if opts is not None else make_opts()
+    px = np.ascontiguousarray(px, np.uint32)
+    py = np.ascontiguousarray(py, np.uint32)
+    j = np.ascontiguousarray(j, np.uint32)
+    L = np.zeros((px.size, 3), np.float32)
+    check(lib().rt_debug_render_host(scene.handle, C.byref(c), max_depth, C.byref(o), px.ctypes.data,
+                                     py.ctypes.data, j.ctypes.data, px.size, L.ctypes.data))
+    return L
+
+
+def debug_halton_host(width, height, seed, indices, ndims):
+    idx = np.ascontiguousarray(indices, np.uint64)
+    out = np.zeros((idx.size, ndims), np.uint32)
+    check(lib().rt_debug_halton_host(width, height, seed, idx.ctypes.data, idx.size, ndims, out.ctypes.data))
+    return out
+
+
+def debug_sample_index_host(width, height, x, y, j) -> int:
+    v = C.c_uint64()
+    check(lib().rt_debug_sample_index_host(width, height, x, y, j, C.byref(v)))
+    return v.value

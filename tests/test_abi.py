@@ -1,0 +1,149 @@
+"""CPU checks of the C-ABI library: it builds, loads and exports every
+function declared in include/rt.h; host logic (strength-reduced division,
+BVH8 build, traversal and per-sample path code executed on the host) agrees
+with the oracle."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1705_01263_gb300 import build, rt, scenes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "rt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w]+\s*\*?\s*(rt_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_library_exports_every_declared_function():
+    path = build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (rt_\w+)", out))
+    declared = header_functions()
+    assert len(declared) >= 25
+    missing = [f for f in declared if f not in exported]
+    assert not missing, missing
+    rt.lib()  # and it loads
+
+
+def test_no_cpu_fallback_in_device_entry_points():
+    """Without a GPU the device entry points report a CUDA error; they never
+    compute on the host."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    sd, cam = scenes.cornell_box()
+    with pytest.raises(rt.RtError):
+        rt.Scene(sd)
+    with pytest.raises(rt.RtError):
+        rt.Film(8, 8)
+
+
+def test_strength_reduced_division_matches_integer_division():
+    rng = np.random.default_rng(0)
+    n = np.concatenate([rng.integers(0, 2**63, 200_000, dtype=np.int64).astype(np.uint64) * np.uint64(2)
+                        + rng.integers(0, 2, 200_000, dtype=np.int64).astype(np.uint64),
+                        np.arange(0, 70_000, dtype=np.uint64),
+                        np.array([2**64 - 1, 2**64 - 2, 2**63, 2**32, 2**32 - 1], np.uint64)])
+    for d in [2, 3, 5, 7, 11, 619, 2187, 177147, 4294967291, 2**31, 3**20]:
+        assert np.array_equal(rt.rt_divide_u64_host(n, d), n // np.uint64(d)), d
+
+
+def test_strength_reduced_division_exhaustive_16bit_dividends_all_small_bases():
+    n = np.arange(0, 1 << 16, dtype=np.uint64)
+    for d in range(2, 700):
+        assert np.array_equal(rt.rt_divide_u64_host(n, d), n // np.uint64(d))
+
+
+def test_halton_host_code_matches_oracle_bits():
+    rng = np.random.default_rng(1)
+    idx = np.concatenate([np.arange(0, 4096, dtype=np.uint64),
+                          rng.integers(0, 2**63, 2000, dtype=np.int64).astype(np.uint64) * np.uint64(2),
+                          np.array([2**64 - 1, 2**63, 2**32 - 1, 2**32], np.uint64)])
+    for (W, H, seed) in [(64, 64, 0), (1920, 1080, 17050126), (1, 1, 5)]:
+        a = rt.debug_halton_host(W, H, seed, idx, 40)
+        b = oracle.sample_dims_u32(idx, 40, W, H, seed)
+        assert np.array_equal(a, b)
+
+
+def test_sample_index_host_code_matches_oracle():
+    for W, H in [(64, 64), (1920, 1080), (7, 5), (1, 1), (333, 100)]:
+        k = max(0, (W - 1).bit_length())
+        l = 0
+        while 3**l < H:
+            l += 1
+        P = 2**k * 3**l
+        rng = np.random.default_rng(W * H)
+        for _ in range(50):
+            x, y, j = int(rng.integers(0, W)), int(rng.integers(0, H)), int(rng.integers(0, 5000))
+            assert rt.debug_sample_index_host(W, H, x, y, j) == oracle.pixel_base_index(W, H, x, y) + j * P
+
+
+@pytest.fixture(scope="module")
+def small_field():
+    sd, cam = scenes.sphere_field(n_spheres=6, seg=24, rings=12, plane_res=(40, 20), n_emissive_spheres=2,
+                                  env_size=(64, 32), width=96, height=54)
+    return sd, cam, rt.Scene(sd, host_only=True), oracle.Scene(sd)
+
+
+@pytest.mark.parametrize("kind", ["primary", "incoherent", "shadow"])
+def test_bvh8_traversal_host_matches_oracle(small_field, kind):
+    from helpers import t_close
+    sd, cam, s, o = small_field
+    rays = scenes.random_rays(sd, 20000, seed=3, kind=kind, cam=cam)
+    p, t, u, v, nodes = rt.debug_trace_host(s, rays, any_hit=(kind == "shadow"))
+    po, to, _, _ = o.trace(rays, any_hit=(kind == "shadow"))
+    if kind == "shadow":
+        assert np.array_equal(p != rt.RT_MISS, po != rt.RT_MISS)
+        return
+    assert np.mean(p == po) >= 0.99999
+    hit = (po != rt.RT_MISS) & (p == po)
+    assert np.all(t_close(t[hit], to[hit], rays[hit]))
+
+
+def test_bvh8_build_shapes(small_field):
+    sd, cam, s, o = small_field
+    info = s.info()
+    assert info["leaf_tris"] == sd.num_triangles
+    assert 0 < info["nodes"] < sd.num_triangles
+
+
+def test_empty_and_single_triangle_scenes_host():
+    from test_oracle_geometry import tri_scene
+    s = rt.Scene(tri_scene([[0, 0, 0], [1, 0, 0], [0, 1, 0]], [[0, 1, 2]]), host_only=True)
+    rays = np.array([[0.2, 0.2, 1, 0, 0, -1, 0, np.inf], [2, 2, 1, 0, 0, -1, 0, np.inf],
+                     [0.2, 0.2, 1, 0, 0, -1, 0, 0.5]], np.float32)
+    p, t, u, v, _ = rt.debug_trace_host(s, rays)
+    assert p.tolist() == [0, rt.RT_MISS, rt.RT_MISS]
+    assert t[0] == pytest.approx(1.0) and u[0] == pytest.approx(0.2) and v[0] == pytest.approx(0.2)
+    e = rt.Scene(tri_scene(np.zeros((3, 3)), np.zeros((0, 3))), host_only=True)
+    p, t, _, _, _ = rt.debug_trace_host(e, rays)
+    assert np.all(p == rt.RT_MISS) and np.all(np.isinf(t))
+
+
+@pytest.mark.parametrize("which", ["cornell", "field", "furnace"])
+def test_path_code_host_matches_oracle_per_sample(small_field, which):
+    if which == "cornell":
+        sd, cam = scenes.cornell_box()
+        s, o, D = rt.Scene(sd, host_only=True), oracle.Scene(sd), 8
+    elif which == "field":
+        sd, cam, s, o = small_field
+        D = 6
+    else:
+        sd, cam = scenes.furnace_sphere(res=16)
+        s, o, D = rt.Scene(sd, host_only=True), oracle.Scene(sd), 4
+    rng = np.random.default_rng(0)
+    n = 3000
+    px, py, j = rng.integers(0, cam.width, n), rng.integers(0, cam.height, n), rng.integers(0, 64, n)
+    Lg = rt.debug_render_host(s, cam, D, px, py, j)
+    Lo = o.render_samples(cam, px, py, j, D)
+    d = np.abs(Lg - Lo).sum(1)
+    close = d <= 1e-3 * np.maximum(np.abs(Lo).sum(1), 1e-3)
+    assert close.mean() >= 0.99
+    assert np.abs(Lg.mean(0) - Lo.mean(0)).max() <= 1e-2 * np.abs(Lo.mean(0)).max()

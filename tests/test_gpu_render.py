@@ -1,0 +1,206 @@
+"""GPU parity of the whole estimator (Sec. 2, 2.1, 2.2, 3.1, A.1-A.4)
+against the FP64 oracle on the same seeded inputs: white furnace, closed-form
+direct lighting, the Cornell-box configuration (64 x 64, 16 spp, depth 8),
+the sphere field at reduced size and a sampled full-size pass, wavefront vs
+megakernel, determinism, split-and-merge of iteration sets, and
+abort/resume."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import allowed_4sigma, image_parity
+from paper_1705_01263_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def gpu_render(scene, cam, spp, depth, film=None, **kw):
+    from paper_1705_01263_gb300 import rt
+    film = film or rt.Film(cam.width, cam.height)
+    stats = rt.rt_stats()
+    allow = kw.pop("allow_timeout", False)
+    st = rt.rt_render(scene, cam, spp, depth, film, rt.make_opts(stats=stats, **kw), allow_timeout=allow)
+    torch.cuda.synchronize()
+    return film, stats, st
+
+
+def resolved(film):
+    s, s2, c = film.download()
+    return oracle.resolve(s, s2, c) + (c,)
+
+
+def test_white_furnace_bsdf_sampling_exact():
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.furnace_sphere(res=32)
+    film, _, _ = gpu_render(rt.Scene(sd), cam, 16, 4, mis_mode=3)
+    mean, var, cnt = resolved(film)
+    assert np.all(cnt == 16)
+    assert np.allclose(mean, 1.0, atol=1e-5)
+
+
+def test_white_furnace_mis_within_1e3():
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.furnace_sphere(res=64)
+    film, _, _ = gpu_render(rt.Scene(sd), cam, 64, 8)
+    mean, var, cnt = resolved(film)
+    assert abs(mean.mean() - 1.0) < 1e-3
+    assert np.abs(mean - 1.0).max() < 0.05
+
+
+def corner_ff(A, B):
+    import math
+    a1, b1 = math.sqrt(1 + A * A), math.sqrt(1 + B * B)
+    return (A / a1 * math.atan(B / a1) + B / b1 * math.atan(A / b1)) / (2 * math.pi)
+
+
+def test_direct_light_closed_form():
+    from paper_1705_01263_gb300 import rt
+    h, a, b, L, rho = 1.0, 0.5, 0.75, 3.0, 0.6
+    sd, cam = scenes.parallel_emitter(h, a, b, L, rho)
+    film, _, _ = gpu_render(rt.Scene(sd), cam, 4096, 1)
+    mean, _, _ = resolved(film)
+    assert mean[0, 0, 0] == pytest.approx(rho * L * 4 * corner_ff(a / h, b / h), rel=3e-3)
+
+
+def test_cornell_config_parity():
+    """64 x 64, 16 spp, depth 8 (the small configuration)."""
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.cornell_box()
+    film, stats, _ = gpu_render(rt.Scene(sd), cam, 16, 8)
+    mg, vg, cg = resolved(film)
+    S, S2, C, rays = oracle.Scene(sd).render(cam, 16, 8)
+    mo, vo = oracle.resolve(S, S2, C)
+    assert np.array_equal(cg, C)
+    l1, out, n = image_parity(mg, vg, mo, vo)
+    assert l1 <= 0.01, l1
+    assert out <= allowed_4sigma(n), (out, n)
+    assert stats.paths == 64 * 64 * 16
+    assert stats.extension_rays + stats.shadow_rays == pytest.approx(rays, rel=0.01)
+
+
+@pytest.mark.parametrize("mis_mode", [1, 2, 3])
+def test_cornell_mis_modes_parity(mis_mode):
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.cornell_box()
+    film, _, _ = gpu_render(rt.Scene(sd), cam, 16, 6, mis_mode=mis_mode)
+    mg, vg, _ = resolved(film)
+    S, S2, C, _ = oracle.Scene(sd).render(cam, 16, 6, mis_mode=mis_mode)
+    mo, vo = oracle.resolve(S, S2, C)
+    l1, out, n = image_parity(mg, vg, mo, vo)
+    assert l1 <= 0.01 and out <= allowed_4sigma(n)
+
+
+def test_field_reduced_size_parity():
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.sphere_field(n_spheres=40, plane_res=(120, 60), env_size=(512, 256), width=160, height=90)
+    film, _, _ = gpu_render(rt.Scene(sd), cam, 8, 16)
+    mg, vg, _ = resolved(film)
+    S, S2, C, _ = oracle.Scene(sd).render(cam, 8, 16)
+    mo, vo = oracle.resolve(S, S2, C)
+    l1, out, n = image_parity(mg, vg, mo, vo)
+    assert l1 <= 0.01, l1
+    assert out <= allowed_4sigma(n), (out, n)
+
+
+def test_field_full_size_sampled_pixels():
+    """1920 x 1080, 1,000,000 triangles, depth 16, one pass in the launch
+    configuration of the benchmark; sampled pixels recomputed by the oracle
+    sample by sample (same sequence indices)."""
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.sphere_field()
+    film, stats, _ = gpu_render(rt.Scene(sd), cam, 1, 16)
+    mg, _, cg = resolved(film)
+    assert np.all(cg == 1)
+    rng = np.random.default_rng(7)
+    n = 3000
+    px, py = rng.integers(0, cam.width, n), rng.integers(0, cam.height, n)
+    Lo = oracle.Scene(sd).render_samples(cam, px, py, np.zeros(n), 16)
+    Lg = mg[py, px].astype(np.float64)
+    close = np.abs(Lg - Lo).sum(1) <= 1e-3 * np.maximum(np.abs(Lo).sum(1), 1e-3)
+    assert close.mean() >= 0.99, close.mean()
+    assert np.abs(Lg - Lo).sum() / np.abs(Lo).sum() <= 0.01
+
+
+def test_wavefront_equals_megakernel():
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.cornell_box()
+    s = rt.Scene(sd)
+    a, _, _ = gpu_render(s, cam, 8, 8)
+    b, _, _ = gpu_render(s, cam, 8, 8, megakernel_only=True)
+    ma, _, ca = resolved(a)
+    mb, _, cb = resolved(b)
+    assert np.array_equal(ca, cb)
+    assert np.abs(ma - mb).sum() / np.abs(mb).sum() < 1e-5
+
+
+def test_deterministic_and_split_merge():
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.cornell_box()
+    s = rt.Scene(sd)
+    a, _, _ = gpu_render(s, cam, 16, 8)
+    b, _, _ = gpu_render(s, cam, 16, 8)
+    sa, s2a, ca = a.download()
+    sb, s2b, cb = b.download()
+    assert np.array_equal(sa, sb) and np.array_equal(s2a, s2b) and np.array_equal(ca, cb)
+    c = rt.Film(cam.width, cam.height)
+    gpu_render(s, cam, 5, 8, film=c)
+    assert c.next_iteration() == 5
+    gpu_render(s, cam, 11, 8, film=c)
+    sc, s2c, cc = c.download()
+    assert np.array_equal(cc, ca)
+    assert np.allclose(sc, sa, rtol=1e-5, atol=1e-9) and np.allclose(s2c, s2a, rtol=1e-5, atol=1e-9)
+
+
+def test_abort_flag_and_resume():
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.cornell_box()
+    s = rt.Scene(sd)
+    ref, _, _ = gpu_render(s, cam, 12, 8, max_paths=4096 * 3)
+    flag = np.ones(1, np.int32)
+    f = rt.Film(cam.width, cam.height)
+    _, st1, status = gpu_render(s, cam, 12, 8, film=f, max_paths=4096 * 3, abort_flag=flag.ctypes.data,
+                                allow_timeout=True)
+    assert status == rt.RT_TIMEOUT and st1.waves == 1 and f.next_iteration() == 3
+    _, _, c_mid = f.download()
+    assert np.all(c_mid == 3)
+    _, st2, status = gpu_render(s, cam, 9, 8, film=f, max_paths=4096 * 3)
+    assert status == rt.RT_OK and f.next_iteration() == 12
+    sa, s2a, ca = ref.download()
+    sb, s2b, cb = f.download()
+    assert np.array_equal(ca, cb)
+    assert np.allclose(sa, sb, rtol=1e-5, atol=1e-9)
+
+
+def test_small_pool_partial_passes():
+    """A pool smaller than the image renders in pixel chunks; result equals
+    the whole-pass schedule."""
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.cornell_box()
+    s = rt.Scene(sd)
+    a, _, _ = gpu_render(s, cam, 4, 8)
+    b, st, _ = gpu_render(s, cam, 4, 8, max_paths=1000)
+    assert st.waves == 4 * 5
+    ma, _, ca = resolved(a)
+    mb, _, cb = resolved(b)
+    assert np.array_equal(ca, cb)
+    assert np.abs(ma - mb).sum() / np.abs(mb).sum() < 1e-5
+
+
+def test_invalid_arguments():
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.cornell_box()
+    s = rt.Scene(sd)
+    f = rt.Film(32, 32)
+    with pytest.raises(rt.RtError):
+        rt.rt_render(s, cam, 1, 8, f)           # film size differs from the camera
+    f2 = rt.Film(cam.width, cam.height)
+    with pytest.raises(rt.RtError):
+        rt.rt_render(s, cam, 1, 0, f2)          # max_depth 0
+    rt.rt_render(s, cam, 0, 8, f2)              # spp 0 is a no-op
+    assert f2.next_iteration() == 0
+    bad = scenes.cornell_box()[0]
+    bad.indices = bad.indices.copy()
+    bad.indices[0, 0] = 10**6
+    with pytest.raises(rt.RtError):
+        rt.Scene(bad)
