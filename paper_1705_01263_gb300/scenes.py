@@ -221,7 +221,8 @@ class _Builder:
 # ------------------------------------------------------------ Cornell box
 def cornell_box(seed: int = BASE_SEED + 1):
     """Box [0,1]^3 open towards -z: 5 walls (10 triangles), two boxes rotated
-    +-17 degrees about y (24 triangles) and a 0.25 x 0.25 emitter quad
+    +-17 degrees about y resting 1e-3 above the floor (24 triangles) and a
+    0.25 x 0.25 emitter quad
     (2 triangles) 1e-3 below the ceiling facing down, radiance (17, 12, 4).
     Lambertian albedo in U[0.2, 0.8]^3 per object. 64 x 64 pinhole camera."""
     rng = Rng(seed)
@@ -240,8 +241,10 @@ def cornell_box(seed: int = BASE_SEED + 1):
     for quad, facing in walls:
         p, t = _oriented_quad(*quad, facing)
         b.add(p, t, mat())
-    for center, size, ang in (((0.33, 0.15, 0.62), (0.3, 0.3, 0.3), 17.0),
-                              ((0.68, 0.3, 0.42), (0.3, 0.6, 0.3), -17.0)):
+    # the boxes float 1e-3 above the floor so that no two triangles are
+    # coplanar and overlapping (a tie in t would make the hit ambiguous)
+    for center, size, ang in (((0.33, 0.151, 0.62), (0.3, 0.3, 0.3), 17.0),
+                              ((0.68, 0.301, 0.42), (0.3, 0.6, 0.3), -17.0)):
         v, t = _box(center, size, ang)
         b.add(v, t, mat())
     lm = b.material((0.78, 0.78, 0.78), 0.5, 0.0, (17.0, 12.0, 4.0))

@@ -24,18 +24,31 @@ def gpu_trace(scene, rays, any_hit=False):
     return (prim.cpu().numpy().view(np.uint32), t.cpu().numpy(), u.cpu().numpy(), v.cpu().numpy())
 
 
-def check_closest(sd, rays, gpu, ref, min_agree=0.99999):
+def check_closest(sd, rays, gpu, ref, min_agree=0.99999, grazing_ok=False):
+    """Identical primitive on >= min_agree of the rays; every disagreement
+    must be a valid alternative (the GPU's triangle contains the hit point
+    within 1e-5 barycentric slack in float64, at the oracle's distance).
+    With grazing_ok (rays aimed exactly at silhouette vertices and edges) a
+    hit/miss disagreement is allowed when the hit point lies on a triangle
+    boundary within that slack."""
     p, t, u, v = gpu
     po, to, uo, vo = ref
     same = p == po
     agree = same.mean()
     bad = np.where(~same)[0]
-    # every disagreement must be a valid alternative hit at the same distance
     if bad.size:
-        assert np.all((p[bad] != MISS) & (po[bad] != MISS)), "a hit was missed or invented"
-        b0, b1, b2, tt = bary_fp64(rays[bad], sd.vertices, sd.indices, p[bad])
+        both = (p[bad] != MISS) & (po[bad] != MISS)
+        if not grazing_ok:
+            assert np.all(both), "a hit was missed or invented"
+        gb = bad[p[bad] != MISS]
+        b0, b1, b2, tt = bary_fp64(rays[gb], sd.vertices, sd.indices, p[gb])
         assert np.all(np.minimum(np.minimum(b0, b1), b2) > -1e-5)
-        assert np.all(t_close(t[bad], to[bad], rays[bad], 1e-5))
+        if grazing_ok:
+            ob = bad[(po[bad] != MISS) & (p[bad] == MISS)]
+            c0, c1, c2, _ = bary_fp64(rays[ob], sd.vertices, sd.indices, po[ob])
+            assert np.all(np.minimum(np.minimum(c0, c1), c2) < 1e-5), "a clear hit was missed"
+        bb = bad[both]
+        assert np.all(t_close(t[bb], to[bb], rays[bb], 1e-5))
     hit = same & (po != MISS)
     assert np.all(t_close(t[hit], to[hit], rays[hit], 1e-5))
     assert np.all(np.isinf(t[p == MISS]))
@@ -80,7 +93,7 @@ def test_edge_aimed_rays(field_full):
     agrees, and any primitive reported is a valid hit."""
     sd, cam, s, o = field_full
     rays = scenes.random_rays(sd, 200_000, seed=4, kind="edges")
-    check_closest(sd, rays, gpu_trace(s, rays), o.trace(rays), min_agree=0.5)
+    check_closest(sd, rays, gpu_trace(s, rays), o.trace(rays), min_agree=0.5, grazing_ok=True)
 
 
 def test_watertight_closed_mesh_on_gpu():
