@@ -100,16 +100,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline_oracle(sd, cam, seconds_target=15.0):
+def cpu_baseline_oracle(sd, cam):
     """The FP64 oracle as it stands, on all host cores, on a bounded sample of
-    the workload: the full scene at reduced resolution, 1 spp, depth 16."""
+    the workload: the full scene and image at 8 of the 64 spp (about 10-20 s
+    on 16 cores)."""
     import oracle
     t0 = time.time()
     osc = oracle.Scene(sd)
     build_s = time.time() - t0
     from paper_1705_01263_gb300 import scenes as sc_mod
-    W, H = 480, 270
-    spp = 1
+    W, H = 1920, 1080
+    spp = 8
     c2 = sc_mod.Camera(cam.eye, cam.look_at, cam.up, cam.vfov_deg, W, H)
     t0 = time.time()
     _, _, cnt, rays = osc.render(c2, spp, DEPTH)

@@ -18,12 +18,14 @@
 
 #include "internal.h"
 #include "shade.cuh"
+#include "trace_kernel.cuh"
 
 namespace rtg {
 
 struct Ctrl {
     uint32_t n_ext, n_next, n_shadow, cur;
     uint32_t tail, overflow, tail_threshold, pad;
+    uint32_t fetch_ext, fetch_shadow, pad2[2];
     unsigned long long ext_rays, shadow_rays;
     unsigned long long ext_nodes, ext_tris, shadow_nodes, shadow_tris;
 };
@@ -127,41 +129,42 @@ __global__ void k_raygen(RenderParams P, Pool pool, uint64_t t0, uint32_t n, uin
         c->n_next = 0;
         c->n_shadow = 0;
         c->cur = 0;
+        c->fetch_ext = 0;
+        c->fetch_shadow = 0;
         c->tail_threshold = tail_threshold;
         c->tail = n < tail_threshold ? 1u : 0u;
     }
 }
 
 // Closest-hit traversal of the current extension queue.
+struct ExtJob {
+    const float4 *ray_o, *ray_d;
+    float4 *hit;
+    const uint32_t *queue;
+    RT_D Ray load(uint32_t i) const {
+        uint32_t q = queue[i];
+        float4 o = ray_o[q], d = ray_d[q];
+        return Ray{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, INFINITY};
+    }
+    RT_D void store(uint32_t i, const Hit &h) const {
+        hit[queue[i]] = make_float4(__uint_as_float(h.prim), h.t, h.b1, h.b2);
+    }
+};
+
 template <bool kCount>
 __global__ void __launch_bounds__(128) k_trace_ext(DevScene sc, Pool pool) {
     Ctrl *c = pool.ctrl;
     if (c->tail) return;
     const uint32_t n = c->n_ext;
-    const uint32_t *queue = pool.q[c->cur];
+    ExtJob job{pool.ray_o, pool.ray_d, pool.hit, pool.q[c->cur]};
     bool overflow = false;
-    uint32_t nodes = 0, tris = 0;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += stride) {
-        uint32_t i = base + lane_id();
-        bool valid = i < n;
-        if (valid) {
-            uint32_t q = queue[i];
-            float4 o = pool.ray_o[q], d = pool.ray_d[q];
-            Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, INFINITY};
-            Hit h;
-            h.prim = RT_MISS; h.t = INFINITY; h.b1 = h.b2 = 0.f;
-            TraceResult tr = traverse<false>(sc.nodes, sc.tris, 0u, r, h);
-            overflow |= tr.overflow;
-            if (kCount) { nodes += tr.nodes; tris += tr.tris; }
-            pool.hit[q] = make_float4(__uint_as_float(h.prim), h.t, h.b1, h.b2);
-        }
-        count_rays(&c->ext_rays, valid);
-    }
+    WorkCount wc;
+    trace_persistent<false, kCount>(sc.nodes, sc.tris, job, n, &c->fetch_ext, overflow, wc);
     if (overflow) atomicOr(&c->overflow, 1u);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&c->ext_rays, (unsigned long long)n);
     if (kCount) {
-        atomicAdd(&c->ext_nodes, (unsigned long long)nodes);
-        atomicAdd(&c->ext_tris, (unsigned long long)tris);
+        atomicAdd(&c->ext_nodes, (unsigned long long)wc.nodes);
+        atomicAdd(&c->ext_tris, (unsigned long long)wc.tris);
     }
 }
 
@@ -204,37 +207,37 @@ __global__ void __launch_bounds__(128) k_shade(RenderParams P, Pool pool) {
 }
 
 // Any-hit traversal of the shadow queue; unoccluded contributions are added.
+struct ShadowJob {
+    const float4 *sh_o, *sh_d, *sh_c;
+    float4 *L;
+    const uint32_t *qs;
+    RT_D Ray load(uint32_t i) const {
+        uint32_t q = qs[i];
+        float4 o = sh_o[q], d = sh_d[q];
+        return Ray{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, o.w};
+    }
+    RT_D void store(uint32_t i, const Hit &h) const {
+        if (h.prim != RT_MISS) return;
+        uint32_t q = qs[i];
+        float4 cc = sh_c[q], l = L[q];
+        L[q] = make_float4(l.x + cc.x, l.y + cc.y, l.z + cc.z, 0.f);
+    }
+};
+
 template <bool kCount>
 __global__ void __launch_bounds__(128) k_trace_shadow(DevScene sc, Pool pool) {
     Ctrl *c = pool.ctrl;
     if (c->tail) return;
     const uint32_t n = c->n_shadow;
+    ShadowJob job{pool.sh_o, pool.sh_d, pool.sh_c, pool.L, pool.qs};
     bool overflow = false;
-    uint32_t nodes = 0, tris = 0;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += stride) {
-        uint32_t i = base + lane_id();
-        bool valid = i < n;
-        if (valid) {
-            uint32_t q = pool.qs[i];
-            float4 o = pool.sh_o[q], d = pool.sh_d[q];
-            Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, o.w};
-            Hit h;
-            h.prim = RT_MISS; h.t = INFINITY;
-            TraceResult tr = traverse<true>(sc.nodes, sc.tris, 0u, r, h);
-            overflow |= tr.overflow;
-            if (kCount) { nodes += tr.nodes; tris += tr.tris; }
-            if (h.prim == RT_MISS) {
-                float4 cc = pool.sh_c[q], L = pool.L[q];
-                pool.L[q] = make_float4(L.x + cc.x, L.y + cc.y, L.z + cc.z, 0.f);
-            }
-        }
-        count_rays(&c->shadow_rays, valid);
-    }
+    WorkCount wc;
+    trace_persistent<true, kCount>(sc.nodes, sc.tris, job, n, &c->fetch_shadow, overflow, wc);
     if (overflow) atomicOr(&c->overflow, 1u);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&c->shadow_rays, (unsigned long long)n);
     if (kCount) {
-        atomicAdd(&c->shadow_nodes, (unsigned long long)nodes);
-        atomicAdd(&c->shadow_tris, (unsigned long long)tris);
+        atomicAdd(&c->shadow_nodes, (unsigned long long)wc.nodes);
+        atomicAdd(&c->shadow_tris, (unsigned long long)wc.tris);
     }
 }
 
@@ -247,6 +250,8 @@ __global__ void k_step_end(Pool pool) {
         if (c->n_ext < c->tail_threshold) c->tail = 1u;
     }
     c->n_shadow = 0;
+    c->fetch_ext = 0;
+    c->fetch_shadow = 0;
 }
 
 // Megakernel: every remaining sample runs to completion in its own thread.
@@ -310,25 +315,31 @@ __global__ void k_resolve(const double *sum, const double *sum2, const uint32_t 
 }
 
 // rays -> hits over caller-owned SoA buffers.
-template <bool kAny>
-__global__ void __launch_bounds__(128) k_trace_user(DevScene sc, rt_rays rays, int64_t n, rt_hits hits,
-                                                    uint32_t *overflow_flag) {
-    bool overflow = false;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        Ray r{v3(__ldg(rays.ox + i), __ldg(rays.oy + i), __ldg(rays.oz + i)),
-              v3(__ldg(rays.dx + i), __ldg(rays.dy + i), __ldg(rays.dz + i)), __ldg(rays.tmin + i),
-              __ldg(rays.tmax + i)};
-        Hit h;
-        h.prim = RT_MISS; h.t = INFINITY; h.b1 = h.b2 = 0.f;
-        TraceResult tr = traverse<kAny>(sc.nodes, sc.tris, 0u, r, h);
-        overflow |= tr.overflow;
+struct UserJob {
+    rt_rays rays;
+    rt_hits hits;
+    RT_D Ray load(uint32_t i) const {
+        return Ray{v3(__ldg(rays.ox + i), __ldg(rays.oy + i), __ldg(rays.oz + i)),
+                   v3(__ldg(rays.dx + i), __ldg(rays.dy + i), __ldg(rays.dz + i)), __ldg(rays.tmin + i),
+                   __ldg(rays.tmax + i)};
+    }
+    RT_D void store(uint32_t i, const Hit &h) const {
         hits.prim[i] = h.prim;
         if (hits.inst) hits.inst[i] = 0u;
         hits.t[i] = h.prim == RT_MISS ? INFINITY : h.t;
         if (hits.u) hits.u[i] = h.b1;
         if (hits.v) hits.v[i] = h.b2;
     }
-    if (overflow) atomicOr(overflow_flag, 1u);
+};
+
+template <bool kAny>
+__global__ void __launch_bounds__(128) k_trace_user(DevScene sc, rt_rays rays, uint32_t n, rt_hits hits,
+                                                    uint32_t *scratch /* [0] fetch counter, [1] overflow */) {
+    UserJob job{rays, hits};
+    bool overflow = false;
+    WorkCount wc;
+    trace_persistent<kAny, false>(sc.nodes, sc.tris, job, n, &scratch[0], overflow, wc);
+    if (overflow) atomicOr(&scratch[1], 1u);
 }
 
 __global__ void k_sample_index(Enum en, const uint32_t *px, const uint32_t *py, const uint32_t *j, int64_t n,
@@ -359,6 +370,17 @@ int sm_count() {
     }
     return n;
 }
+
+// Persistent traversal kernels: one wave of resident blocks.
+template <class K>
+int grid_persistent(K kernel, int block, size_t smem) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+    if (per_sm < 1) per_sm = 1;
+    return sm_count() * per_sm;
+}
+
+inline size_t stack_smem(int block) { return (size_t)kShStack * block * sizeof(uint2); }
 
 template <class K>
 int grid_for(K kernel, int block, int64_t work) {
@@ -430,16 +452,22 @@ extern "C" rt_status rt_trace(const rt_scene *s, const rt_rays *rays, int64_t n,
         set_error("rt_trace: null ray or hit pointer");
         return RT_INVALID_ARG;
     }
-    static uint32_t *flag = nullptr;
-    if (!flag) RT_CUDA_TRY(cudaMalloc(&flag, 4));
+    if (n > 0xFFFFFFFFll) { set_error("rt_trace: at most 2^32 - 1 rays per call"); return RT_INVALID_ARG; }
+    // per-device scratch: ray fetch counter and overflow flag
+    static uint32_t *scratch[64] = {nullptr};
+    int dev = 0;
+    RT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) { set_error("rt_trace: device index out of range"); return RT_INVALID_ARG; }
+    if (!scratch[dev]) RT_CUDA_TRY(cudaMalloc(&scratch[dev], 2 * sizeof(uint32_t)));
     cudaStream_t st = (cudaStream_t)stream;
-    RT_CUDA_TRY(cudaMemsetAsync(flag, 0, 4, st));
+    RT_CUDA_TRY(cudaMemsetAsync(scratch[dev], 0, 2 * sizeof(uint32_t), st));
+    const int gb = 128;
     if (any_hit) {
-        int g = grid_for(k_trace_user<true>, 128, n);
-        k_trace_user<true><<<g, 128, 0, st>>>(s->dev, *rays, n, *hits, flag);
+        int g = grid_persistent(k_trace_user<true>, gb, stack_smem(gb));
+        k_trace_user<true><<<g, gb, stack_smem(gb), st>>>(s->dev, *rays, (uint32_t)n, *hits, scratch[dev]);
     } else {
-        int g = grid_for(k_trace_user<false>, 128, n);
-        k_trace_user<false><<<g, 128, 0, st>>>(s->dev, *rays, n, *hits, flag);
+        int g = grid_persistent(k_trace_user<false>, gb, stack_smem(gb));
+        k_trace_user<false><<<g, gb, stack_smem(gb), st>>>(s->dev, *rays, (uint32_t)n, *hits, scratch[dev]);
     }
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
@@ -567,9 +595,10 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     rt_status result = RT_OK;
     const int gb = 128;
     const int g_ray = grid_for(k_raygen, 256, cap);
-    const int g_trace = grid_for(k_trace_ext<false>, gb, cap);
+    const size_t smem = stack_smem(gb);
+    const int g_trace = grid_persistent(k_trace_ext<false>, gb, smem);
     const int g_shade = grid_for(k_shade, gb, cap);
-    const int g_shadow = grid_for(k_trace_shadow<false>, gb, cap);
+    const int g_shadow = grid_persistent(k_trace_shadow<false>, gb, smem);
     const int g_mega = grid_for(k_megakernel, gb, cap);
     const bool prof = o.profile >= 1, count = o.profile >= 2;
     // event pairs per timed launch: kind 0 trace, 1 shade, 2 shadow, 3 megakernel, 4 other
@@ -604,15 +633,15 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         if (!o.megakernel_only) {
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
                 e = mark(0);
-                if (count) k_trace_ext<true><<<g_trace, gb, 0, st>>>(s->dev, pool);
-                else k_trace_ext<false><<<g_trace, gb, 0, st>>>(s->dev, pool);
+                if (count) k_trace_ext<true><<<g_trace, gb, smem, st>>>(s->dev, pool);
+                else k_trace_ext<false><<<g_trace, gb, smem, st>>>(s->dev, pool);
                 done(e);
                 e = mark(1);
                 k_shade<<<g_shade, gb, 0, st>>>(P, pool);
                 done(e);
                 e = mark(2);
-                if (count) k_trace_shadow<true><<<g_shadow, gb, 0, st>>>(s->dev, pool);
-                else k_trace_shadow<false><<<g_shadow, gb, 0, st>>>(s->dev, pool);
+                if (count) k_trace_shadow<true><<<g_shadow, gb, smem, st>>>(s->dev, pool);
+                else k_trace_shadow<false><<<g_shadow, gb, smem, st>>>(s->dev, pool);
                 done(e);
                 k_step_end<<<1, 1, 0, st>>>(pool);
                 stats.kernel_launches += 4;

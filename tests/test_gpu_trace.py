@@ -24,6 +24,19 @@ def gpu_trace(scene, rays, any_hit=False):
     return (prim.cpu().numpy().view(np.uint32), t.cpu().numpy(), u.cpu().numpy(), v.cpu().numpy())
 
 
+def bary_slack(sd, rays, prim, t):
+    """Barycentric slack equivalent to a position error of 1e-5 x
+    max(t, |origin|, 1): the FP32 ray itself is only known to that precision,
+    and a triangle of size s turns it into a barycentric error of that over s."""
+    V = sd.vertices.astype(np.float64)
+    tri = sd.indices[prim.astype(np.int64)]
+    e1 = V[tri[:, 1]] - V[tri[:, 0]]
+    e2 = V[tri[:, 2]] - V[tri[:, 0]]
+    size = np.sqrt(np.linalg.norm(np.cross(e1, e2), axis=1))
+    scale = np.maximum(np.maximum(np.abs(t), np.abs(rays[:, 0:3]).max(1)), 1.0)
+    return np.maximum(1e-5, 1e-5 * scale / np.maximum(size, 1e-30))
+
+
 def check_closest(sd, rays, gpu, ref, min_agree=0.99999, grazing_ok=False):
     """Identical primitive on >= min_agree of the rays; every disagreement
     must be a valid alternative (the GPU's triangle contains the hit point
@@ -42,11 +55,12 @@ def check_closest(sd, rays, gpu, ref, min_agree=0.99999, grazing_ok=False):
             assert np.all(both), "a hit was missed or invented"
         gb = bad[p[bad] != MISS]
         b0, b1, b2, tt = bary_fp64(rays[gb], sd.vertices, sd.indices, p[gb])
-        assert np.all(np.minimum(np.minimum(b0, b1), b2) > -1e-5)
+        assert np.all(np.minimum(np.minimum(b0, b1), b2) > -bary_slack(sd, rays[gb], p[gb], t[gb]))
         if grazing_ok:
             ob = bad[(po[bad] != MISS) & (p[bad] == MISS)]
             c0, c1, c2, _ = bary_fp64(rays[ob], sd.vertices, sd.indices, po[ob])
-            assert np.all(np.minimum(np.minimum(c0, c1), c2) < 1e-5), "a clear hit was missed"
+            assert np.all(np.minimum(np.minimum(c0, c1), c2) < bary_slack(sd, rays[ob], po[ob], to[ob])), \
+                "a clear hit was missed"
         bb = bad[both]
         assert np.all(t_close(t[bb], to[bb], rays[bb], 1e-5))
     hit = same & (po != MISS)
