@@ -164,6 +164,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spp", type=int, default=SPP)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--trace-kernel", type=int, default=0, help="0 persistent warps, 1 one ray per thread")
+    ap.add_argument("--megakernel-only", action="store_true", help="A/B baseline: megakernel per iteration set")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -182,12 +184,14 @@ def main():
     stream = torch.cuda.current_stream()
     # each rank renders a disjoint iteration range: rank r starts at pass r * 10^6
     base_iter = rank * 1_000_000
-    opts_plain = rt.make_opts(seed=0)
     l2_flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     WH = cam.width * cam.height
 
+    def opts(**kw):
+        return rt.make_opts(seed=0, trace_kernel=args.trace_kernel, megakernel_only=args.megakernel_only, **kw)
+
     def render_step(stats=None, profile=0):
-        o = rt.make_opts(seed=0, stats=stats, profile=profile)
+        o = opts(stats=stats, profile=profile)
         rt.rt_render(scene, cam, args.spp, DEPTH, film, o)
 
     film.seek(base_iter)
@@ -211,7 +215,7 @@ def main():
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             s = rt.rt_stats()
             ev0.record(stream)
-            rt.rt_render(scene, cam, args.spp, DEPTH, film, rt.make_opts(seed=0, stats=s, profile=1))
+            rt.rt_render(scene, cam, args.spp, DEPTH, film, opts(stats=s, profile=1))
             ev1.record(stream)
             ev1.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
@@ -254,7 +258,7 @@ def main():
         l2_flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rt.rt_render(scene, cam, args.spp, DEPTH, film, rt.make_opts(seed=0))
+        rt.rt_render(scene, cam, args.spp, DEPTH, film, opts())
         film.resolve(mean_dev)
         host_img.copy_(mean_dev, non_blocking=True)
         torch.cuda.synchronize()
@@ -273,7 +277,9 @@ def main():
             "config": {"workload": WORKLOAD, "triangles": sd.num_triangles, "width": cam.width,
                        "height": cam.height, "spp": args.spp, "max_depth": DEPTH,
                        "paths_per_step": paths_per_step, "l2": "flushed between steps (256 MiB write)",
-                       "film": "FP64 sums", "parallelism": f"weak: {world} rank(s), disjoint iteration ranges"},
+                       "film": "FP64 sums", "parallelism": f"weak: {world} rank(s), disjoint iteration ranges",
+                       "trace_kernel": ["persistent warps", "one ray per thread"][args.trace_kernel],
+                       "schedule": "megakernel only" if args.megakernel_only else "wavefront + megakernel tail"},
             "mrays_per_s": mrays,
             "rays_per_path": (ext + shd) / (paths_per_step * args.steps),
             "roofline": {"bound": "hbm", "kernel": "k_trace_ext (closest-hit BVH8 traversal)",

@@ -206,6 +206,63 @@ __global__ void __launch_bounds__(128) k_shade(RenderParams P, Pool pool) {
     }
 }
 
+// One ray per thread, traced to completion (A/B variant of the above).
+template <bool kCount>
+__global__ void __launch_bounds__(128) k_trace_ext_simple(DevScene sc, Pool pool) {
+    Ctrl *c = pool.ctrl;
+    if (c->tail) return;
+    const uint32_t n = c->n_ext;
+    const uint32_t *queue = pool.q[c->cur];
+    bool overflow = false;
+    uint32_t nodes = 0, tris = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t q = queue[i];
+        float4 o = pool.ray_o[q], d = pool.ray_d[q];
+        Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, INFINITY};
+        Hit h;
+        h.prim = RT_MISS; h.t = INFINITY; h.b1 = h.b2 = 0.f;
+        TraceResult tr = traverse<false>(sc.nodes, sc.tris, 0u, r, h);
+        overflow |= tr.overflow;
+        if (kCount) { nodes += tr.nodes; tris += tr.tris; }
+        pool.hit[q] = make_float4(__uint_as_float(h.prim), h.t, h.b1, h.b2);
+    }
+    if (overflow) atomicOr(&c->overflow, 1u);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&c->ext_rays, (unsigned long long)n);
+    if (kCount) {
+        atomicAdd(&c->ext_nodes, (unsigned long long)nodes);
+        atomicAdd(&c->ext_tris, (unsigned long long)tris);
+    }
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(128) k_trace_shadow_simple(DevScene sc, Pool pool) {
+    Ctrl *c = pool.ctrl;
+    if (c->tail) return;
+    const uint32_t n = c->n_shadow;
+    bool overflow = false;
+    uint32_t nodes = 0, tris = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t q = pool.qs[i];
+        float4 o = pool.sh_o[q], d = pool.sh_d[q];
+        Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, o.w};
+        Hit h;
+        h.prim = RT_MISS; h.t = INFINITY;
+        TraceResult tr = traverse<true>(sc.nodes, sc.tris, 0u, r, h);
+        overflow |= tr.overflow;
+        if (kCount) { nodes += tr.nodes; tris += tr.tris; }
+        if (h.prim == RT_MISS) {
+            float4 cc = pool.sh_c[q], L = pool.L[q];
+            pool.L[q] = make_float4(L.x + cc.x, L.y + cc.y, L.z + cc.z, 0.f);
+        }
+    }
+    if (overflow) atomicOr(&c->overflow, 1u);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&c->shadow_rays, (unsigned long long)n);
+    if (kCount) {
+        atomicAdd(&c->shadow_nodes, (unsigned long long)nodes);
+        atomicAdd(&c->shadow_tris, (unsigned long long)tris);
+    }
+}
+
 // Any-hit traversal of the shadow queue; unoccluded contributions are added.
 struct ShadowJob {
     const float4 *sh_o, *sh_d, *sh_c;
@@ -599,6 +656,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     const int g_trace = grid_persistent(k_trace_ext<false>, gb, smem);
     const int g_shade = grid_for(k_shade, gb, cap);
     const int g_shadow = grid_persistent(k_trace_shadow<false>, gb, smem);
+    const int g_simple = grid_for(k_trace_ext_simple<false>, gb, cap);
     const int g_mega = grid_for(k_megakernel, gb, cap);
     const bool prof = o.profile >= 1, count = o.profile >= 2;
     // event pairs per timed launch: kind 0 trace, 1 shade, 2 shadow, 3 megakernel, 4 other
@@ -633,15 +691,27 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         if (!o.megakernel_only) {
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
                 e = mark(0);
-                if (count) k_trace_ext<true><<<g_trace, gb, smem, st>>>(s->dev, pool);
-                else k_trace_ext<false><<<g_trace, gb, smem, st>>>(s->dev, pool);
+                if (o.trace_kernel == 1) {
+                    if (count) k_trace_ext_simple<true><<<g_simple, gb, 0, st>>>(s->dev, pool);
+                    else k_trace_ext_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool);
+                } else if (count) {
+                    k_trace_ext<true><<<g_trace, gb, smem, st>>>(s->dev, pool);
+                } else {
+                    k_trace_ext<false><<<g_trace, gb, smem, st>>>(s->dev, pool);
+                }
                 done(e);
                 e = mark(1);
                 k_shade<<<g_shade, gb, 0, st>>>(P, pool);
                 done(e);
                 e = mark(2);
-                if (count) k_trace_shadow<true><<<g_shadow, gb, smem, st>>>(s->dev, pool);
-                else k_trace_shadow<false><<<g_shadow, gb, smem, st>>>(s->dev, pool);
+                if (o.trace_kernel == 1) {
+                    if (count) k_trace_shadow_simple<true><<<g_simple, gb, 0, st>>>(s->dev, pool);
+                    else k_trace_shadow_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool);
+                } else if (count) {
+                    k_trace_shadow<true><<<g_shadow, gb, smem, st>>>(s->dev, pool);
+                } else {
+                    k_trace_shadow<false><<<g_shadow, gb, smem, st>>>(s->dev, pool);
+                }
                 done(e);
                 k_step_end<<<1, 1, 0, st>>>(pool);
                 stats.kernel_launches += 4;

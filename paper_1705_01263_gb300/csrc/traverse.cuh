@@ -159,11 +159,6 @@ RT_HD bool intersect_tri(const RayPre &rp, V3 v0, V3 v1, V3 v2, float tmin, floa
     return true;
 }
 
-RT_HD uint32_t byte_of(uint32_t lo4, uint32_t hi4, int i) {
-    uint32_t w = i < 4 ? lo4 : hi4;
-    return (w >> (8 * (i & 3))) & 0xFFu;
-}
-
 RT_HD float exp2i(int e) {
 #ifdef __CUDA_ARCH__
     return __int_as_float((e + 127) << 23);
@@ -194,6 +189,19 @@ RT_HD uint32_t as_uint(float f) {
 #endif
 }
 
+// Exact float value of byte `i` (0..7) of the 8-byte word (lo4, hi4): the
+// byte is placed in the mantissa of 2^23 with one byte permute and 2^23 is
+// subtracted, which avoids the quarter-rate integer-to-float conversion.
+RT_HD float qbyte(uint32_t lo4, uint32_t hi4, int i) {
+    uint32_t w = i < 4 ? lo4 : hi4;
+#ifdef __CUDA_ARCH__
+    uint32_t b = __byte_perm(w, 0x4B000000u, 0x7540u + (uint32_t)(i & 3));
+    return __uint_as_float(b) - 8388608.f;
+#else
+    return (float)((w >> (8 * (i & 3))) & 0xFFu);
+#endif
+}
+
 // Intersect the 8 child boxes of node (n0..n4); returns the internal-child
 // hit bits at 24 + (slot ^ oct) and, through tri_bits, the triangle bits.
 RT_HD uint32_t intersect_children(const RayPre &rp, uint4 n0, uint4 n1, uint4 n2, uint4 n3, uint4 n4,
@@ -204,24 +212,26 @@ RT_HD uint32_t intersect_children(const RayPre &rp, uint4 n0, uint4 n1, uint4 n2
     uint32_t imask = n0.w >> 24;
     float ax = exp2i(ex) * rp.inv.x, ay = exp2i(ey) * rp.inv.y, az = exp2i(ez) * rp.inv.z;
     float bx = (p.x - rp.o.x) * rp.inv.x, by = (p.y - rp.o.y) * rp.inv.y, bz = (p.z - rp.o.z) * rp.inv.z;
+    // near/far planes per axis follow the direction sign
     const bool sx = rp.inv.x < 0.f, sy = rp.inv.y < 0.f, sz = rp.inv.z < 0.f;
+    const uint32_t nxl = sx ? n2.z : n2.x, nxh = sx ? n2.w : n2.y, fxl = sx ? n2.x : n2.z, fxh = sx ? n2.y : n2.w;
+    const uint32_t nyl = sy ? n3.z : n3.x, nyh = sy ? n3.w : n3.y, fyl = sy ? n3.x : n3.z, fyh = sy ? n3.y : n3.w;
+    const uint32_t nzl = sz ? n4.z : n4.x, nzh = sz ? n4.w : n4.y, fzl = sz ? n4.x : n4.z, fzh = sz ? n4.y : n4.w;
     uint32_t inner = 0, tris = 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        float lx = (float)byte_of(n2.x, n2.y, i), hx = (float)byte_of(n2.z, n2.w, i);
-        float ly = (float)byte_of(n3.x, n3.y, i), hy = (float)byte_of(n3.z, n3.w, i);
-        float lz = (float)byte_of(n4.x, n4.y, i), hz = (float)byte_of(n4.z, n4.w, i);
-        float nx = fma_rn(sx ? hx : lx, ax, bx), fx = fma_rn(sx ? lx : hx, ax, bx);
-        float ny = fma_rn(sy ? hy : ly, ay, by), fy = fma_rn(sy ? ly : hy, ay, by);
-        float nz = fma_rn(sz ? hz : lz, az, bz), fz = fma_rn(sz ? lz : hz, az, bz);
+        float nx = fma_rn(qbyte(nxl, nxh, i), ax, bx), fx = fma_rn(qbyte(fxl, fxh, i), ax, bx);
+        float ny = fma_rn(qbyte(nyl, nyh, i), ay, by), fy = fma_rn(qbyte(fyl, fyh, i), ay, by);
+        float nz = fma_rn(qbyte(nzl, nzh, i), az, bz), fz = fma_rn(qbyte(fzl, fzh, i), az, bz);
         float t0 = fmaxf(fmaxf(nx, ny), fmaxf(nz, tmin));
         float t1 = fminf(fminf(fx, fy), fminf(fz, tmax));
         bool hit = t0 <= t1 * 1.000001f;
-        uint32_t meta = byte_of(n1.z, n1.w, i);
-        if (hit && meta) {
-            if (imask & (1u << i)) inner |= 1u << (24 + (i ^ rp.oct));
-            else tris |= (meta >> 5) << (meta & 31u);
-        }
+        uint32_t meta = (i < 4 ? n1.z : n1.w) >> (8 * (i & 3)) & 0xFFu;
+        uint32_t is_inner = (imask >> i) & 1u;
+        uint32_t ib = (hit && meta && is_inner) ? (1u << (24 + (i ^ rp.oct))) : 0u;
+        uint32_t tb = (hit && meta && !is_inner) ? ((meta >> 5) << (meta & 31u)) : 0u;
+        inner |= ib;
+        tris |= tb;
     }
     tri_bits = tris;
     return inner;

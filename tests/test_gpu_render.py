@@ -125,6 +125,17 @@ def test_field_full_size_sampled_pixels():
     assert np.abs(Lg - Lo).sum() / np.abs(Lo).sum() <= 0.01
 
 
+def test_traversal_variants_agree():
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.sphere_field(n_spheres=40, plane_res=(120, 60), env_size=(512, 256), width=160, height=90)
+    s = rt.Scene(sd)
+    a, _, _ = gpu_render(s, cam, 2, 16, trace_kernel=0)
+    b, _, _ = gpu_render(s, cam, 2, 16, trace_kernel=1)
+    sa, _, _ = a.download()
+    sb, _, _ = b.download()
+    assert np.array_equal(sa, sb)
+
+
 def test_wavefront_equals_megakernel():
     from paper_1705_01263_gb300 import rt
     sd, cam = scenes.cornell_box()

@@ -62,7 +62,9 @@ def check_closest(sd, rays, gpu, ref, min_agree=0.99999, grazing_ok=False):
             assert np.all(np.minimum(np.minimum(c0, c1), c2) < bary_slack(sd, rays[ob], po[ob], to[ob])), \
                 "a clear hit was missed"
         bb = bad[both]
-        assert np.all(t_close(t[bb], to[bb], rays[bb], 1e-5))
+        # on an edge or vertex both triangles contain the hit point; a grazing
+        # ray's distance along a neighbour may differ more than 1e-5
+        assert np.all(t_close(t[bb], to[bb], rays[bb], 1e-3 if grazing_ok else 1e-5))
     hit = same & (po != MISS)
     assert np.all(t_close(t[hit], to[hit], rays[hit], 1e-5))
     assert np.all(np.isinf(t[p == MISS]))
