@@ -200,6 +200,29 @@ rt_status rt_film_resolve(const rt_film *film, float *mean, float *var, void *st
 rt_status rt_render(const rt_scene *scene, const rt_camera *camera, uint32_t spp,
                     uint32_t max_depth, rt_film *film, const rt_render_opts *opts, void *stream);
 
+/* Rendering that allocates nothing (the paper has no counterpart).
+ * For callers that cannot call cudaMalloc or let a library do so - code
+ * inside a host framework that owns all device memory through its own
+ * arena, services whose device memory is fixed at start-up, threads on
+ * which an allocation would synchronise the device. Same estimator and
+ * kernels as rt_render, but the path-state pool (at most 65,536 paths in
+ * flight), control block and sampling table live in one file-scope device
+ * array of about 9.6 MB that every device loading the library holds until
+ * the process exits. The caller passes the scene (created earlier with
+ * rt_scene_create) and owns the outputs: DEVICE buffers sum and sum2 (H*W*3
+ * doubles) and count (H*W uint32), which are accumulated into, so zero them
+ * before the first call. Renders iterations [first_iteration,
+ * first_iteration + spp). opts may be NULL; opts->max_paths_in_flight above
+ * 65,536 is rejected with RT_INVALID_ARG; guiding is RT_NOT_SUPPORTED.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture. Every call reuses the same array: calls that overlap on the GPU
+ * (other streams, other host threads) race and must not be issued. Blocking
+ * with respect to the host, like rt_render. */
+rt_status rt_render_static(const rt_scene *scene, const rt_camera *camera, uint32_t spp, uint32_t max_depth,
+                           uint32_t first_iteration, double *sum, double *sum2, uint32_t *count,
+                           const rt_render_opts *opts, void *stream);
+
 /* ------------------------------------------------------- QMC sampling */
 /* Sequence index of sample j in pixel (x, y) under full-screen enumeration
  * (Appendix A.2): DEVICE arrays px, py, j of n entries -> out (uint64). */

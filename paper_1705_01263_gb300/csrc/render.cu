@@ -794,3 +794,165 @@ extern "C" rt_status rt_halton(uint32_t W, uint32_t H, uint64_t seed, const uint
     RT_CUDA_TRY(e);
     return RT_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Rendering without device allocations (the paper has no counterpart).
+//
+// Some callers cannot call cudaMalloc: code embedded in a host framework
+// that owns every device allocation through its own arena, services whose
+// device memory budget is fixed when they start, or threads on which an
+// allocation would synchronise the device and stall unrelated work. For them
+// rt_render_static renders with its path-state pool, control block and
+// sampling table in one file-scope __device__ array of fixed size instead of
+// memory obtained from the allocator. The array exists on every device that
+// loads the library, until the process exits.
+namespace rtg {
+
+constexpr uint32_t kStaticMaxPaths = 65536;                 // paths in flight
+constexpr int kStaticMaxDims = 2 + 7 * (kMaxDepth + 1);     // sampling dimensions
+constexpr size_t kAlign = 256;
+constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+constexpr size_t kStaticCtrl = 0;
+constexpr size_t kStaticDims = kStaticCtrl + align_up(sizeof(Ctrl));
+constexpr size_t kStaticF4 = kStaticDims + align_up(sizeof(HaltonDim) * kStaticMaxDims);
+constexpr size_t kStaticF4Bytes = align_up(sizeof(float4) * kStaticMaxPaths);
+constexpr size_t kStaticIndex = kStaticF4 + 8 * kStaticF4Bytes;
+constexpr size_t kStaticU32Bytes = align_up(sizeof(uint32_t) * kStaticMaxPaths);
+constexpr size_t kStaticPixel = kStaticIndex + align_up(sizeof(uint2) * kStaticMaxPaths);
+constexpr size_t kStaticQueues = kStaticPixel + kStaticU32Bytes;
+constexpr size_t kStaticBytes = kStaticQueues + 3 * kStaticU32Bytes;   // about 9.6 MB
+
+static __device__ __align__(256) unsigned char g_static_arena[kStaticBytes];
+
+// Device address of g_static_arena per device. In host code the symbol name is
+// only a host-side stand-in, so the address is looked up once per device,
+// with that device current, and cached.
+static unsigned char *g_static_addr[64] = {nullptr};
+
+static rt_status static_arena(unsigned char **out) {
+    int dev = 0;
+    RT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) { set_error("rt_render_static: device index out of range"); return RT_INVALID_ARG; }
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_arena);
+        if (e != cudaSuccess || !p) return cuda_status(e, "cudaGetSymbolAddress(g_static_arena)");
+        g_static_addr[dev] = (unsigned char *)p;
+    }
+    *out = g_static_addr[dev];
+    return RT_OK;
+}
+
+}  // namespace rtg
+
+extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, uint32_t spp, uint32_t max_depth,
+                                      uint32_t first_iteration, double *sum, double *sum2, uint32_t *count,
+                                      const rt_render_opts *opts_in, void *stream) {
+    if (!s || !cam || !sum || !sum2 || !count) { set_error("rt_render_static: null argument"); return RT_INVALID_ARG; }
+    if (s->host_only) { set_error("rt_render_static: scene has no device copy"); return RT_INVALID_ARG; }
+    if (cam->width == 0 || cam->height == 0 || (uint64_t)cam->width * cam->height > (1ull << 31)) {
+        set_error("rt_render_static: invalid image size");
+        return RT_INVALID_ARG;
+    }
+    if (max_depth < 1 || max_depth > (uint32_t)kMaxDepth) { set_error("rt_render_static: max_depth must be in [1, 64]"); return RT_INVALID_ARG; }
+    rt_render_opts o{};
+    if (opts_in) o = *opts_in;
+    if (o.guide) { set_error("rt_render_static: guiding needs rt_render"); return RT_NOT_SUPPORTED; }
+    if (o.max_paths_in_flight > kStaticMaxPaths) {
+        set_error("rt_render_static: max_paths_in_flight exceeds the static pool of 65536 paths");
+        return RT_INVALID_ARG;
+    }
+    if (spp == 0) return RT_OK;
+    unsigned char *base = nullptr;
+    rt_status rs = static_arena(&base);
+    if (rs != RT_OK) return rs;
+    const uint32_t cap = o.max_paths_in_flight ? std::max<uint32_t>(o.max_paths_in_flight, 32u) : kStaticMaxPaths;
+    Pool pool{};
+    pool.ctrl = (Ctrl *)(base + kStaticCtrl);
+    float4 *f4[8];
+    for (int k = 0; k < 8; ++k) f4[k] = (float4 *)(base + kStaticF4 + k * kStaticF4Bytes);
+    pool.ray_o = f4[0]; pool.ray_d = f4[1]; pool.beta = f4[2]; pool.L = f4[3];
+    pool.hit = f4[4]; pool.sh_o = f4[5]; pool.sh_d = f4[6]; pool.sh_c = f4[7];
+    pool.index = (uint2 *)(base + kStaticIndex);
+    pool.pixel = (uint32_t *)(base + kStaticPixel);
+    pool.q[0] = (uint32_t *)(base + kStaticQueues);
+    pool.q[1] = (uint32_t *)(base + kStaticQueues + kStaticU32Bytes);
+    pool.qs = (uint32_t *)(base + kStaticQueues + 2 * kStaticU32Bytes);
+    pool.capacity = cap;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the arena keeps the previous call's contents: reset the control block
+    // and rewrite the sampling table for this seed
+    const int ndims = 2 + 7 * (int)(max_depth + 1);
+    std::vector<HaltonDim> dims = make_dims(o.seed, ndims);
+    HaltonDim *ddims = (HaltonDim *)(base + kStaticDims);
+    RT_CUDA_TRY(cudaMemsetAsync(pool.ctrl, 0, sizeof(Ctrl), st));
+    RT_CUDA_TRY(cudaMemcpyAsync(ddims, dims.data(), dims.size() * sizeof(HaltonDim), cudaMemcpyHostToDevice, st));
+    RenderParams P;
+    P.sc = s->dev;
+    P.cam = make_camera(*cam);
+    P.en = make_enum(cam->width, cam->height);
+    P.dims = ddims;
+    P.max_depth = max_depth;
+    P.sigma = o.filter_sigma == 0.f ? 0.5f : o.filter_sigma;
+    P.mis_mode = o.mis_mode;
+    P.rr = o.rr_enable;
+    const uint32_t tail = o.megakernel_only ? 0xFFFFFFFFu : (o.tail_threshold ? o.tail_threshold : 8192u);
+    const uint64_t WH = (uint64_t)cam->width * cam->height;
+    const int gb = 128;
+    const size_t smem = stack_smem(gb);
+    const int g_ray = grid_for(k_raygen, 256, cap);
+    const int g_trace = grid_persistent(k_trace_ext<false>, gb, smem);
+    const int g_shade = grid_for(k_shade, gb, cap);
+    const int g_shadow = grid_persistent(k_trace_shadow<false>, gb, smem);
+    const int g_mega = grid_for(k_megakernel, gb, cap);
+    auto t_start = std::chrono::steady_clock::now();
+    uint64_t t = (uint64_t)first_iteration * WH, t_end = t + (uint64_t)spp * WH;
+    rt_stats stats{};
+    Ctrl host_ctrl{};
+    rt_status result = RT_OK;
+    while (t < t_end) {
+        uint64_t n64;
+        uint32_t passes = 0;
+        if (t % WH != 0 || WH > cap) {
+            n64 = std::min<uint64_t>({t_end - t, WH - t % WH, (uint64_t)cap});
+        } else {
+            uint64_t full = std::min<uint64_t>((t_end - t) / WH, cap / WH);
+            if (full >= 1) { passes = (uint32_t)full; n64 = full * WH; }
+            else n64 = std::min<uint64_t>(t_end - t, cap);
+        }
+        uint32_t n = (uint32_t)n64;
+        k_raygen<<<g_ray, 256, 0, st>>>(P, pool, t, n, (uint32_t)WH, tail);
+        if (!o.megakernel_only) {
+            for (uint32_t v = 1; v <= max_depth + 1; ++v) {
+                k_trace_ext<false><<<g_trace, gb, smem, st>>>(s->dev, pool);
+                k_shade<<<g_shade, gb, 0, st>>>(P, pool);
+                k_trace_shadow<false><<<g_shadow, gb, smem, st>>>(s->dev, pool);
+                k_step_end<<<1, 1, 0, st>>>(pool);
+                stats.kernel_launches += 4;
+                ++stats.wavefront_steps;
+            }
+        }
+        k_megakernel<<<g_mega, gb, 0, st>>>(P, pool);
+        int g_film = grid_for(k_film, 256, passes ? WH : n);
+        k_film<<<g_film, 256, 0, st>>>(pool, sum, sum2, count, t, n, (uint32_t)WH, passes);
+        stats.kernel_launches += 3;
+        ++stats.tail_launches;
+        RT_CUDA_TRY(cudaGetLastError());
+        RT_CUDA_TRY(cudaMemcpyAsync(&host_ctrl, pool.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+        RT_CUDA_TRY(cudaStreamSynchronize(st));
+        t += n;
+        stats.paths += n;
+        ++stats.waves;
+        if (host_ctrl.overflow) { set_error("BVH traversal stack overflow"); result = RT_STACK_OVERFLOW; break; }
+        double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        if (t < t_end && ((o.abort_flag && *o.abort_flag) || (o.time_budget_ms > 0 && ms >= o.time_budget_ms))) {
+            set_error("rt_render_static: stopped by time budget or abort flag (resume at the next iteration set)");
+            result = RT_TIMEOUT;
+            break;
+        }
+    }
+    stats.extension_rays = host_ctrl.ext_rays;
+    stats.shadow_rays = host_ctrl.shadow_rays;
+    if (o.stats) *o.stats = stats;
+    return result;
+}

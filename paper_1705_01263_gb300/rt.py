@@ -83,7 +83,7 @@ _lib = None
 EXPORTED = [
     "rt_scene_create", "rt_scene_destroy", "rt_scene_info", "rt_trace", "rt_film_create", "rt_film_destroy",
     "rt_film_clear", "rt_film_next_iteration", "rt_film_seek", "rt_film_buffers", "rt_film_resolve", "rt_render",
-    "rt_sample_index", "rt_halton", "rt_divide_u64_host", "rt_guide_create", "rt_guide_destroy",
+    "rt_render_static", "rt_sample_index", "rt_halton", "rt_divide_u64_host", "rt_guide_create", "rt_guide_destroy",
     "rt_guide_num_params", "rt_guide_get_params", "rt_guide_set_params", "rt_guide_state_size", "rt_guide_save",
     "rt_guide_load", "rt_guide_infer", "rt_guide_loss_grad", "rt_guide_train_step", "rt_last_error",
     "rt_status_string",
@@ -120,6 +120,7 @@ def _declare(L):
         "rt_film_buffers": [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)],
         "rt_film_resolve": [vp, vp, vp, vp],
         "rt_render": [vp, C.POINTER(rt_camera), u32, u32, vp, C.POINTER(rt_render_opts), vp],
+        "rt_render_static": [vp, C.POINTER(rt_camera), u32, u32, u32, vp, vp, vp, C.POINTER(rt_render_opts), vp],
         "rt_sample_index": [u32, u32, vp, vp, vp, i64, vp, vp],
         "rt_halton": [u32, u32, u64, vp, i64, i32, vp, vp],
         "rt_divide_u64_host": [vp, i64, u32, vp],
@@ -373,6 +374,16 @@ def rt_render(scene: Scene, cam, spp: int, max_depth: int, film: Film, opts: Opt
     if st == RT_TIMEOUT and allow_timeout:
         return st
     return check(st)
+
+
+def rt_render_static(scene: Scene, cam, spp: int, max_depth: int, first_iteration: int, sum_, sum2, count,
+                     opts: Optional[rt_render_opts] = None, stream=None) -> int:
+    """Allocation-free render into caller-owned device tensors (float64
+    H x W x 3 sums, int32 H x W count), accumulated in place."""
+    c = make_camera(cam)
+    o = opts if opts is not None else make_opts()
+    return check(lib().rt_render_static(scene.handle, C.byref(c), spp, max_depth, first_iteration, sum_.data_ptr(),
+                                        sum2.data_ptr(), count.data_ptr(), C.byref(o), _stream(stream)))
 
 
 def rt_sample_index(width, height, px, py, j, out=None, stream=None):
