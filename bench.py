@@ -164,7 +164,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spp", type=int, default=SPP)
     ap.add_argument("--out", default=None)
-    ap.add_argument("--trace-kernel", type=int, default=0, help="0 persistent warps, 1 one ray per thread")
+    ap.add_argument("--trace-kernel", type=int, default=0, help="0 one ray per thread with warp fetch, 1 persistent warps refilling lanes")
     ap.add_argument("--megakernel-only", action="store_true", help="A/B baseline: megakernel per iteration set")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -278,7 +278,7 @@ def main():
                        "height": cam.height, "spp": args.spp, "max_depth": DEPTH,
                        "paths_per_step": paths_per_step, "l2": "flushed between steps (256 MiB write)",
                        "film": "FP64 sums", "parallelism": f"weak: {world} rank(s), disjoint iteration ranges",
-                       "trace_kernel": ["persistent warps", "one ray per thread"][args.trace_kernel],
+                       "trace_kernel": ["one ray per thread, warp fetch", "persistent warps, lane refill"][args.trace_kernel],
                        "schedule": "megakernel only" if args.megakernel_only else "wavefront + megakernel tail"},
             "mrays_per_s": mrays,
             "rays_per_path": (ext + shd) / (paths_per_step * args.steps),

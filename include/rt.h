@@ -148,7 +148,7 @@ typedef struct {
     rt_guide *guide;         /* online path guiding (NULL = off) */
     rt_stats *stats;         /* optional host output */
     int32_t profile;         /* 1: per-kernel event timing; 2: also count traversal work */
-    int32_t trace_kernel;    /* 0: persistent warps with dynamic ray fetch; 1: one ray per thread */
+    int32_t trace_kernel;    /* 0: one ray per thread, warps fetch 32 rays at a time; 1: persistent warps refilling idle lanes */
 } rt_render_opts;
 
 /* ---------------------------------------------------------------- scene */

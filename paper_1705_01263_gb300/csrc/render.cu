@@ -25,7 +25,7 @@ namespace rtg {
 struct Ctrl {
     uint32_t n_ext, n_next, n_shadow, cur;
     uint32_t tail, overflow, tail_threshold, pad;
-    uint32_t fetch_ext, fetch_shadow, pad2[2];
+    uint32_t fetch_ext, fetch_shadow, fetch_shade, fetch_ext2;
     unsigned long long ext_rays, shadow_rays;
     unsigned long long ext_nodes, ext_tris, shadow_nodes, shadow_tris;
 };
@@ -86,6 +86,16 @@ RT_D void warp_append(uint32_t *queue, uint32_t *count, bool pred, uint32_t item
     if (pred) queue[base + __popc(mask & ((1u << lane) - 1u))] = item;
 }
 
+// Warp-granular dynamic work distribution: lane 0 reserves the next 32 queue
+// entries with one atomic and broadcasts the base; warps that drew short
+// work come back for more, so a launch ends when the queue is drained
+// rather than when the unluckiest statically assigned thread finishes.
+RT_D uint32_t warp_fetch32(uint32_t *counter) {
+    uint32_t base = 0;
+    if (lane_id() == 0) base = atomicAdd(counter, 32u);
+    return __shfl_sync(0xFFFFFFFFu, base, 0);
+}
+
 RT_D void count_rays(unsigned long long *ctr, bool pred) {
     uint32_t mask = __ballot_sync(0xFFFFFFFFu, pred);
     if (lane_id() == 0 && mask) atomicAdd(ctr, (unsigned long long)__popc(mask));
@@ -131,6 +141,8 @@ __global__ void k_raygen(RenderParams P, Pool pool, uint64_t t0, uint32_t n, uin
         c->cur = 0;
         c->fetch_ext = 0;
         c->fetch_shadow = 0;
+        c->fetch_shade = 0;
+        c->fetch_ext2 = 0;
         c->tail_threshold = tail_threshold;
         c->tail = n < tail_threshold ? 1u : 0u;
     }
@@ -175,8 +187,9 @@ __global__ void __launch_bounds__(128) k_shade(RenderParams P, Pool pool) {
     const uint32_t cur = c->cur;
     const uint32_t *queue = pool.q[cur];
     uint32_t *next = pool.q[cur ^ 1u];
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += stride) {
+    for (;;) {
+        uint32_t base = warp_fetch32(&c->fetch_shade);
+        if (base >= n) break;
         uint32_t i = base + lane_id();
         bool valid = i < n;
         uint32_t q = 0;
@@ -215,7 +228,11 @@ __global__ void __launch_bounds__(128) k_trace_ext_simple(DevScene sc, Pool pool
     const uint32_t *queue = pool.q[c->cur];
     bool overflow = false;
     uint32_t nodes = 0, tris = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (;;) {
+        uint32_t base = warp_fetch32(&c->fetch_ext);
+        if (base >= n) break;
+        uint32_t i = base + lane_id();
+        if (i >= n) continue;
         uint32_t q = queue[i];
         float4 o = pool.ray_o[q], d = pool.ray_d[q];
         Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, INFINITY};
@@ -241,7 +258,11 @@ __global__ void __launch_bounds__(128) k_trace_shadow_simple(DevScene sc, Pool p
     const uint32_t n = c->n_shadow;
     bool overflow = false;
     uint32_t nodes = 0, tris = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (;;) {
+        uint32_t base = warp_fetch32(&c->fetch_shadow);
+        if (base >= n) break;
+        uint32_t i = base + lane_id();
+        if (i >= n) continue;
         uint32_t q = pool.qs[i];
         float4 o = pool.sh_o[q], d = pool.sh_d[q];
         Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, o.w};
@@ -309,6 +330,8 @@ __global__ void k_step_end(Pool pool) {
     c->n_shadow = 0;
     c->fetch_ext = 0;
     c->fetch_shadow = 0;
+    c->fetch_shade = 0;
+    c->fetch_ext2 = 0;
 }
 
 // Megakernel: every remaining sample runs to completion in its own thread.
@@ -654,9 +677,9 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     const int g_ray = grid_for(k_raygen, 256, cap);
     const size_t smem = stack_smem(gb);
     const int g_trace = grid_persistent(k_trace_ext<false>, gb, smem);
-    const int g_shade = grid_for(k_shade, gb, cap);
+    const int g_shade = grid_persistent(k_shade, gb, 0);
     const int g_shadow = grid_persistent(k_trace_shadow<false>, gb, smem);
-    const int g_simple = grid_for(k_trace_ext_simple<false>, gb, cap);
+    const int g_simple = grid_persistent(k_trace_ext_simple<false>, gb, 0);
     const int g_mega = grid_for(k_megakernel, gb, cap);
     const bool prof = o.profile >= 1, count = o.profile >= 2;
     // event pairs per timed launch: kind 0 trace, 1 shade, 2 shadow, 3 megakernel, 4 other
@@ -691,7 +714,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         if (!o.megakernel_only) {
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
                 e = mark(0);
-                if (o.trace_kernel == 1) {
+                if (o.trace_kernel == 0) {
                     if (count) k_trace_ext_simple<true><<<g_simple, gb, 0, st>>>(s->dev, pool);
                     else k_trace_ext_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool);
                 } else if (count) {
@@ -704,7 +727,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
                 k_shade<<<g_shade, gb, 0, st>>>(P, pool);
                 done(e);
                 e = mark(2);
-                if (o.trace_kernel == 1) {
+                if (o.trace_kernel == 0) {
                     if (count) k_trace_shadow_simple<true><<<g_simple, gb, 0, st>>>(s->dev, pool);
                     else k_trace_shadow_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool);
                 } else if (count) {
@@ -902,8 +925,9 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
     const size_t smem = stack_smem(gb);
     const int g_ray = grid_for(k_raygen, 256, cap);
     const int g_trace = grid_persistent(k_trace_ext<false>, gb, smem);
-    const int g_shade = grid_for(k_shade, gb, cap);
+    const int g_shade = grid_persistent(k_shade, gb, 0);
     const int g_shadow = grid_persistent(k_trace_shadow<false>, gb, smem);
+    const int g_simple = grid_persistent(k_trace_ext_simple<false>, gb, 0);
     const int g_mega = grid_for(k_megakernel, gb, cap);
     auto t_start = std::chrono::steady_clock::now();
     uint64_t t = (uint64_t)first_iteration * WH, t_end = t + (uint64_t)spp * WH;
@@ -924,9 +948,11 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
         k_raygen<<<g_ray, 256, 0, st>>>(P, pool, t, n, (uint32_t)WH, tail);
         if (!o.megakernel_only) {
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
-                k_trace_ext<false><<<g_trace, gb, smem, st>>>(s->dev, pool);
+                if (o.trace_kernel == 0) k_trace_ext_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool);
+                else k_trace_ext<false><<<g_trace, gb, smem, st>>>(s->dev, pool);
                 k_shade<<<g_shade, gb, 0, st>>>(P, pool);
-                k_trace_shadow<false><<<g_shadow, gb, smem, st>>>(s->dev, pool);
+                if (o.trace_kernel == 0) k_trace_shadow_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool);
+                else k_trace_shadow<false><<<g_shadow, gb, smem, st>>>(s->dev, pool);
                 k_step_end<<<1, 1, 0, st>>>(pool);
                 stats.kernel_launches += 4;
                 ++stats.wavefront_steps;
