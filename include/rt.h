@@ -280,6 +280,16 @@ rt_status rt_guide_loss_grad(const rt_guide *guide, const float *features, const
 rt_status rt_guide_train_step(rt_guide *guide, const float *features, const float *wi,
                               const float *weight, int64_t n, void *stream);
 
+/* BF16 GEMM on the tcgen05 tensor cores with FP32 accumulation (the
+ * guiding network's dense-layer primitive; not in the paper):
+ * C[M x N] = A[M x K] * B[N x K]^T, or C += ... when accumulate != 0.
+ * A, B: DEVICE bf16 row-major with row strides lda, ldb (elements; K, lda,
+ * ldb multiples of 8, A and B 16-byte aligned); C: DEVICE float row-major
+ * with stride ldc. Synchronous; RT_TIMEOUT if a tensor-core completion wait
+ * ran out (the kernel returns without trapping). */
+rt_status rt_gemm_bf16(const void *A, const void *B, float *C, int32_t M, int32_t N, int32_t K, int32_t lda,
+                       int32_t ldb, int32_t ldc, int32_t accumulate, void *stream);
+
 /* ------------------------------------------------------------ errors */
 const char *rt_last_error(void);
 const char *rt_status_string(rt_status s);

@@ -1,38 +1,426 @@
-// Online path-guiding proposal (placeholder entry points; the network
-// kernels are added in a later change).
+// Online-trained path-guiding proposal (not part of the paper): a one-blob
+// encoded (position, outgoing direction, normal) -> 224 -> 64 -> 64 -> 64 ->
+// 64 -> 40 ReLU MLP whose 40 outputs parameterise an 8-lobe von Mises-Fisher
+// mixture over directions. It is mixed with BSDF sampling by one-sample MIS
+// in the shading kernel, so the estimator stays consistent whatever the
+// network predicts. Weights are kept as FP32 masters with Adam moments on the
+// device and as BF16 copies for the tensor cores; every dense product (the
+// forward layers, the input gradients and the weight gradients) runs on
+// tcgen05 through gemm_bf16, with FP32 accumulation.
+//
+// Layouts (row-major): weights W_l [out][in] (layer 5 padded to 48 output
+// rows); activations H_l [n][64] BF16 plus their transposes [64][n] for the
+// weight gradients; network outputs [n][48] FP32 (first 40 used, lobe k at
+// 5k: mu xyz, kappa (softplus), logit).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <cuda_bf16.h>
+#include <vector>
+
+#include "guide.cuh"
 #include "internal.h"
+
+namespace rtg {
+
+rt_status gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *C, int M, int N, int K, int lda, int ldb,
+                    int ldc, int accumulate, uint32_t *err, cudaStream_t st);
+
+static const int kIn[5] = {kGuideIn, kGuideHid, kGuideHid, kGuideHid, kGuideHid};
+static const int kOut[5] = {kGuideHid, kGuideHid, kGuideHid, kGuideHid, kGuideOut};
+static const int kOutPad[5] = {kGuideHid, kGuideHid, kGuideHid, kGuideHid, kGuideOutPad};
+
+static int64_t param_offset(int l) {
+    int64_t o = 0;
+    for (int i = 0; i < l; ++i) o += (int64_t)kIn[i] * kOut[i];
+    return o;
+}
+
+// ------------------------------------------------------------ kernels
+__global__ void k_oneblob(const float *feat, int64_t n, int64_t n_pad, __nv_bfloat16 *X, __nv_bfloat16 *XT) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_pad * kGuideIn;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = i / kGuideIn;
+        int c = (int)(i % kGuideIn);
+        float v = 0.f;
+        if (r < n) v = oneblob_bin(feat[r * 7 + c / kGuideBins], c % kGuideBins);
+        __nv_bfloat16 b = __float2bfloat16(v);
+        X[r * kGuideIn + c] = b;
+        if (XT) XT[(int64_t)c * n_pad + r] = b;
+    }
+}
+
+// H = bf16(relu(Z)); optional transpose HT [64][n_pad].
+__global__ void k_relu_pack(const float *Z, int64_t n, int64_t n_pad, int cols, __nv_bfloat16 *H, __nv_bfloat16 *HT) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_pad * cols;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = i / cols;
+        int c = (int)(i % cols);
+        float v = r < n ? fmaxf(Z[i], 0.f) : 0.f;
+        __nv_bfloat16 b = __float2bfloat16(v);
+        H[i] = b;
+        if (HT) HT[(int64_t)c * n_pad + r] = b;
+    }
+}
+
+// dY = bf16(dH * (H > 0)) and its transpose.
+__global__ void k_relu_bwd(const float *dH, const __nv_bfloat16 *H, int64_t n_pad, int cols, __nv_bfloat16 *dY,
+                           __nv_bfloat16 *dYT) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_pad * cols;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = i / cols;
+        int c = (int)(i % cols);
+        float v = __bfloat162float(H[i]) > 0.f ? dH[i] : 0.f;
+        __nv_bfloat16 b = __float2bfloat16(v);
+        dY[i] = b;
+        dYT[(int64_t)c * n_pad + r] = b;
+    }
+}
+
+// Loss -weight * log q_mix(wi) / n and its gradient w.r.t. the raw outputs.
+__global__ void k_loss_grad(const float *raw, const float *wi, const float *weight, int64_t n, int64_t n_pad,
+                            float inv_n, __nv_bfloat16 *dY, __nv_bfloat16 *dYT, float *loss_sum) {
+    float local = 0.f;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_pad; r += (int64_t)gridDim.x * blockDim.x) {
+        float g[kGuideOutPad];
+        for (int k = 0; k < kGuideOutPad; ++k) g[k] = 0.f;
+        if (r < n) {
+            float w3[3] = {wi[3 * r], wi[3 * r + 1], wi[3 * r + 2]};
+            float lw = mixture_loss_grad(raw + r * kGuideOutPad, w3, weight[r] * inv_n, g);
+            local += lw;
+        }
+        for (int k = 0; k < kGuideOutPad; ++k) {
+            __nv_bfloat16 b = __float2bfloat16(g[k]);
+            dY[r * kGuideOutPad + k] = b;
+            dYT[(int64_t)k * n_pad + r] = b;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xFFFFFFFFu, local, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, local);
+}
+
+__global__ void k_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float gi = g[i];
+        float mi = b1 * m[i] + (1.f - b1) * gi;
+        float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// BF16 copies of layer l: W [out_pad][in] and W^T [in][out_pad].
+__global__ void k_pack_layer(const float *W32, int in, int out, int out_pad, __nv_bfloat16 *W, __nv_bfloat16 *WT) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < out_pad * in; i += gridDim.x * blockDim.x) {
+        int o = i / in, k = i % in;
+        float v = o < out ? W32[(int64_t)o * in + k] : 0.f;
+        __nv_bfloat16 b = __float2bfloat16(v);
+        W[i] = b;
+        if (WT) WT[(int64_t)k * out_pad + o] = b;
+    }
+}
+
+// Gradient of the padded layer-5 output (48 rows) into the 40-row layout.
+__global__ void k_copy_rows(const float *src, int rows, int cols, float *dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows * cols; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+static int grid1d(int64_t n, int block = 256) {
+    int64_t g = (n + block - 1) / block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+}
+
+}  // namespace rtg
 
 using namespace rtg;
 
 struct rt_guide {
-    int dummy;
+    rt_guide_opts opts{};
+    int64_t nparams = 0;
+    float *W32 = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+    __nv_bfloat16 *Wb[5] = {nullptr}, *WTb[5] = {nullptr};
+    int64_t step = 0;
+    // scratch for a batch of up to cap rows
+    int64_t cap = 0;
+    __nv_bfloat16 *X0 = nullptr, *X0T = nullptr, *H[4] = {nullptr}, *HT[4] = {nullptr}, *dY = nullptr, *dYT = nullptr;
+    float *Z = nullptr, *raw = nullptr, *dW5 = nullptr, *loss = nullptr;
+    uint32_t *err = nullptr;
+    std::vector<void *> allocs;
+    float3 bb_lo, bb_hi;
 };
 
-extern "C" int64_t rt_guide_num_params(void) { return 224 * 64 + 3 * 64 * 64 + 64 * 40; }
+namespace {
 
-#define RT_GUIDE_UNSUPPORTED(name)                                        \
-    do {                                                                  \
-        set_error(name ": guiding is not available in this build");       \
-        return RT_NOT_SUPPORTED;                                          \
-    } while (0)
+template <class T>
+rt_status galloc(rt_guide *g, T **p, size_t count) {
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) { set_error("guide: device allocation failed"); return RT_OOM; }
+    g->allocs.push_back(*p);
+    return RT_OK;
+}
 
-extern "C" rt_status rt_guide_create(const rt_scene *, const rt_guide_opts *, rt_guide **out) {
-    if (out) *out = nullptr;
-    RT_GUIDE_UNSUPPORTED("rt_guide_create");
+rt_status repack(rt_guide *g, cudaStream_t st) {
+    for (int l = 0; l < 5; ++l) {
+        k_pack_layer<<<grid1d((int64_t)kOutPad[l] * kIn[l]), 256, 0, st>>>(g->W32 + param_offset(l), kIn[l], kOut[l],
+                                                                            kOutPad[l], g->Wb[l], g->WTb[l]);
+    }
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
 }
-extern "C" rt_status rt_guide_destroy(rt_guide *) { return RT_OK; }
-extern "C" rt_status rt_guide_get_params(const rt_guide *, float *) { RT_GUIDE_UNSUPPORTED("rt_guide_get_params"); }
-extern "C" rt_status rt_guide_set_params(rt_guide *, const float *) { RT_GUIDE_UNSUPPORTED("rt_guide_set_params"); }
-extern "C" rt_status rt_guide_state_size(const rt_guide *, int64_t *) { RT_GUIDE_UNSUPPORTED("rt_guide_state_size"); }
-extern "C" rt_status rt_guide_save(const rt_guide *, void *) { RT_GUIDE_UNSUPPORTED("rt_guide_save"); }
-extern "C" rt_status rt_guide_load(rt_guide *, const void *) { RT_GUIDE_UNSUPPORTED("rt_guide_load"); }
-extern "C" rt_status rt_guide_infer(const rt_guide *, const float *, int64_t, float *, void *) {
-    RT_GUIDE_UNSUPPORTED("rt_guide_infer");
+
+rt_status ensure_scratch(rt_guide *g, int64_t n) {
+    int64_t need = (n + 127) / 128 * 128;
+    if (need <= g->cap) return RT_OK;
+    // grow: drop the old scratch (weights stay)
+    cudaDeviceSynchronize();
+    for (void *p : {(void *)g->X0, (void *)g->X0T, (void *)g->H[0], (void *)g->H[1], (void *)g->H[2], (void *)g->H[3],
+                    (void *)g->HT[0], (void *)g->HT[1], (void *)g->HT[2], (void *)g->HT[3], (void *)g->dY, (void *)g->dYT,
+                    (void *)g->Z, (void *)g->raw}) {
+        if (!p) continue;
+        cudaFree(p);
+        g->allocs.erase(std::remove(g->allocs.begin(), g->allocs.end(), p), g->allocs.end());
+    }
+    rt_status s;
+    if ((s = galloc(g, &g->X0, need * kGuideIn)) || (s = galloc(g, &g->X0T, need * kGuideIn)) ||
+        (s = galloc(g, &g->dY, need * kGuideHid)) || (s = galloc(g, &g->dYT, need * kGuideHid)) ||
+        (s = galloc(g, &g->Z, need * kGuideHid)) || (s = galloc(g, &g->raw, need * kGuideOutPad)))
+        return s;
+    for (int l = 0; l < 4; ++l)
+        if ((s = galloc(g, &g->H[l], need * kGuideHid)) || (s = galloc(g, &g->HT[l], need * kGuideHid))) return s;
+    g->cap = need;
+    return RT_OK;
 }
-extern "C" rt_status rt_guide_loss_grad(const rt_guide *, const float *, const float *, const float *, int64_t, float *,
-                                        float *, void *) {
-    RT_GUIDE_UNSUPPORTED("rt_guide_loss_grad");
+
+// Forward pass over n rows of features; raw outputs in g->raw [n_pad][48].
+rt_status forward(rt_guide *g, const float *feat, int64_t n, bool keep_transposes, cudaStream_t st) {
+    const int64_t n_pad = (n + 127) / 128 * 128;
+    k_oneblob<<<grid1d(n_pad * kGuideIn), 256, 0, st>>>(feat, n, n_pad, g->X0, keep_transposes ? g->X0T : nullptr);
+    const __nv_bfloat16 *x = g->X0;
+    for (int l = 0; l < 4; ++l) {
+        rt_status s = gemm_bf16(x, g->Wb[l], g->Z, (int)n_pad, kGuideHid, kIn[l], kIn[l], kIn[l], kGuideHid, 0, g->err, st);
+        if (s != RT_OK) return s;
+        k_relu_pack<<<grid1d(n_pad * kGuideHid), 256, 0, st>>>(g->Z, n, n_pad, kGuideHid, g->H[l],
+                                                               keep_transposes ? g->HT[l] : nullptr);
+        x = g->H[l];
+    }
+    rt_status s = gemm_bf16(x, g->Wb[4], g->raw, (int)n_pad, kGuideOutPad, kGuideHid, kGuideHid, kGuideHid,
+                            kGuideOutPad, 0, g->err, st);
+    if (s != RT_OK) return s;
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
 }
-extern "C" rt_status rt_guide_train_step(rt_guide *, const float *, const float *, const float *, int64_t, void *) {
-    RT_GUIDE_UNSUPPORTED("rt_guide_train_step");
+
+// Gradient of the mean loss into g->grad (FP32, layer-major [out][in]).
+rt_status backward(rt_guide *g, const float *wi, const float *weight, int64_t n, cudaStream_t st) {
+    const int64_t n_pad = (n + 127) / 128 * 128;
+    RT_CUDA_TRY(cudaMemsetAsync(g->loss, 0, sizeof(float), st));
+    k_loss_grad<<<grid1d(n_pad), 256, 0, st>>>(g->raw, wi, weight, n, n_pad, 1.f / (float)n, g->dY, g->dYT, g->loss);
+    rt_status s;
+    // layer 5: dW5 [48][64] = dY5^T H4 ; dH4 = dY5 W5
+    if ((s = gemm_bf16(g->dYT, g->HT[3], g->dW5, kGuideOutPad, kGuideHid, (int)n_pad, (int)n_pad, (int)n_pad,
+                       kGuideHid, 0, g->err, st)))
+        return s;
+    k_copy_rows<<<grid1d(kGuideOut * kGuideHid), 256, 0, st>>>(g->dW5, kGuideOut, kGuideHid, g->grad + param_offset(4));
+    if ((s = gemm_bf16(g->dY, g->WTb[4], g->Z, (int)n_pad, kGuideHid, kGuideOutPad, kGuideOutPad, kGuideOutPad,
+                       kGuideHid, 0, g->err, st)))
+        return s;
+    for (int l = 3; l >= 0; --l) {
+        // dY_l = dH_l * relu'(H_l)  (dY/dYT buffers hold [n_pad][64])
+        k_relu_bwd<<<grid1d(n_pad * kGuideHid), 256, 0, st>>>(g->Z, g->H[l], n_pad, kGuideHid, g->dY, g->dYT);
+        // dW_l [64][in] = dY_l^T X_{l-1}
+        const __nv_bfloat16 *xT = l == 0 ? g->X0T : g->HT[l - 1];
+        if ((s = gemm_bf16(g->dYT, xT, g->grad + param_offset(l), kGuideHid, kIn[l], (int)n_pad, (int)n_pad,
+                           (int)n_pad, kIn[l], 0, g->err, st)))
+            return s;
+        if (l > 0 &&
+            (s = gemm_bf16(g->dY, g->WTb[l], g->Z, (int)n_pad, kGuideHid, kGuideHid, kGuideHid, kGuideHid, kGuideHid,
+                           0, g->err, st)))
+            return s;
+    }
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+rt_status check_err(rt_guide *g, cudaStream_t st) {
+    uint32_t h = 0;
+    RT_CUDA_TRY(cudaMemcpyAsync(&h, g->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    RT_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h) {
+        cudaMemsetAsync(g->err, 0, sizeof(uint32_t), st);
+        set_error("guide: tensor-core completion wait timed out");
+        return RT_TIMEOUT;
+    }
+    return RT_OK;
+}
+
+}  // namespace
+
+namespace rtg {
+// Used by the renderer: raw outputs for n feature rows (device), no sync.
+rt_status guide_infer_async(rt_guide *g, const float *feat, int64_t n, const float **raw_out, cudaStream_t st) {
+    rt_status s = ensure_scratch(g, n);
+    if (s != RT_OK) return s;
+    s = forward(g, feat, n, false, st);
+    *raw_out = g->raw;
+    return s;
+}
+rt_status guide_train_async(rt_guide *g, const float *feat, const float *wi, const float *weight, int64_t n,
+                            cudaStream_t st) {
+    if (n <= 0) return RT_OK;
+    rt_status s = ensure_scratch(g, n);
+    if (s != RT_OK) return s;
+    for (uint32_t it = 0; it < std::max(1u, g->opts.train_steps); ++it) {
+        if ((s = forward(g, feat, n, true, st)) || (s = backward(g, wi, weight, n, st))) return s;
+        ++g->step;
+        float b1 = 0.9f, b2 = 0.999f;
+        float c1 = 1.f - (float)std::pow(0.9, (double)g->step), c2 = 1.f - (float)std::pow(0.999, (double)g->step);
+        k_adam<<<grid1d(g->nparams), 256, 0, st>>>(g->W32, g->grad, g->m, g->v, g->nparams, g->opts.learning_rate, b1,
+                                                   b2, 1e-8f, c1, c2);
+        if ((s = repack(g, st))) return s;
+    }
+    return RT_OK;
+}
+float guide_alpha(const rt_guide *g) { return g->opts.alpha; }
+void guide_bounds(const rt_guide *g, float3 &lo, float3 &hi) { lo = g->bb_lo; hi = g->bb_hi; }
+uint32_t guide_batch(const rt_guide *g) { return g->opts.batch; }
+}  // namespace rtg
+
+extern "C" int64_t rt_guide_num_params(void) { return kGuideParams; }
+
+extern "C" rt_status rt_guide_create(const rt_scene *scene, const rt_guide_opts *opts, rt_guide **out) {
+    if (!out) { set_error("rt_guide_create: null output"); return RT_INVALID_ARG; }
+    *out = nullptr;
+    rt_guide *g = new rt_guide();
+    if (opts) g->opts = *opts;
+    if (!g->opts.batch) g->opts.batch = 65536;
+    if (!(g->opts.learning_rate > 0.f)) g->opts.learning_rate = 1e-2f;
+    if (!(g->opts.alpha > 0.f)) g->opts.alpha = 0.5f;
+    if (g->opts.alpha > 1.f) { delete g; set_error("rt_guide_create: alpha must be in (0, 1]"); return RT_INVALID_ARG; }
+    if (!g->opts.train_steps) g->opts.train_steps = 1;
+    g->nparams = kGuideParams;
+    if (scene) { g->bb_lo = scene->dev.bb_lo; g->bb_hi = scene->dev.bb_hi; }
+    else { g->bb_lo = make_float3(0.f, 0.f, 0.f); g->bb_hi = make_float3(1.f, 1.f, 1.f); }
+    auto fail = [&](rt_status s) { rt_guide_destroy(g); return s; };
+    rt_status s;
+    if ((s = galloc(g, &g->W32, g->nparams)) || (s = galloc(g, &g->m, g->nparams)) || (s = galloc(g, &g->v, g->nparams)) ||
+        (s = galloc(g, &g->grad, g->nparams)) || (s = galloc(g, &g->dW5, (size_t)kGuideOutPad * kGuideHid)) ||
+        (s = galloc(g, &g->loss, 1)) || (s = galloc(g, &g->err, 1)))
+        return fail(s);
+    for (int l = 0; l < 5; ++l)
+        if ((s = galloc(g, &g->Wb[l], (size_t)kOutPad[l] * kIn[l])) || (s = galloc(g, &g->WTb[l], (size_t)kOutPad[l] * kIn[l])))
+            return fail(s);
+    // He-style initialisation from SplitMix64 (seeded), uniform in +-sqrt(6 / fan_in)
+    std::vector<float> w(g->nparams);
+    uint64_t st = g->opts.seed ^ 0x6A09E667F3BCC908ull;
+    for (int l = 0; l < 5; ++l) {
+        double a = std::sqrt(6.0 / kIn[l]) * (l == 4 ? 0.1 : 1.0);
+        for (int64_t i = 0; i < (int64_t)kIn[l] * kOut[l]; ++i) {
+            uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+            w[param_offset(l) + i] = (float)((2.0 * u - 1.0) * a);
+        }
+    }
+    if (cudaMemcpy(g->W32, w.data(), w.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(g->m, 0, g->nparams * 4) != cudaSuccess || cudaMemset(g->v, 0, g->nparams * 4) != cudaSuccess ||
+        cudaMemset(g->err, 0, 4) != cudaSuccess) {
+        set_error("rt_guide_create: upload failed");
+        return fail(RT_CUDA_ERROR);
+    }
+    if ((s = repack(g, 0)) != RT_OK) return fail(s);
+    if (cudaDeviceSynchronize() != cudaSuccess) { set_error("rt_guide_create: init failed"); return fail(RT_CUDA_ERROR); }
+    *out = g;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_guide_destroy(rt_guide *g) {
+    if (!g) return RT_OK;
+    for (void *p : g->allocs) cudaFree(p);
+    delete g;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_guide_get_params(const rt_guide *g, float *params) {
+    if (!g || !params) { set_error("rt_guide_get_params: null argument"); return RT_INVALID_ARG; }
+    RT_CUDA_TRY(cudaMemcpy(params, g->W32, g->nparams * 4, cudaMemcpyDeviceToHost));
+    return RT_OK;
+}
+
+extern "C" rt_status rt_guide_set_params(rt_guide *g, const float *params) {
+    if (!g || !params) { set_error("rt_guide_set_params: null argument"); return RT_INVALID_ARG; }
+    RT_CUDA_TRY(cudaMemcpy(g->W32, params, g->nparams * 4, cudaMemcpyHostToDevice));
+    RT_CUDA_TRY(cudaMemset(g->m, 0, g->nparams * 4));
+    RT_CUDA_TRY(cudaMemset(g->v, 0, g->nparams * 4));
+    g->step = 0;
+    rt_status s = repack(g, 0);
+    if (s != RT_OK) return s;
+    RT_CUDA_TRY(cudaDeviceSynchronize());
+    return RT_OK;
+}
+
+extern "C" rt_status rt_guide_state_size(const rt_guide *g, int64_t *bytes) {
+    if (!g || !bytes) { set_error("rt_guide_state_size: null argument"); return RT_INVALID_ARG; }
+    *bytes = 3 * g->nparams * 4 + 8;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_guide_save(const rt_guide *g, void *buf) {
+    if (!g || !buf) { set_error("rt_guide_save: null argument"); return RT_INVALID_ARG; }
+    char *b = (char *)buf;
+    RT_CUDA_TRY(cudaMemcpy(b, g->W32, g->nparams * 4, cudaMemcpyDeviceToHost));
+    RT_CUDA_TRY(cudaMemcpy(b + g->nparams * 4, g->m, g->nparams * 4, cudaMemcpyDeviceToHost));
+    RT_CUDA_TRY(cudaMemcpy(b + 2 * g->nparams * 4, g->v, g->nparams * 4, cudaMemcpyDeviceToHost));
+    std::memcpy(b + 3 * g->nparams * 4, &g->step, 8);
+    return RT_OK;
+}
+
+extern "C" rt_status rt_guide_load(rt_guide *g, const void *buf) {
+    if (!g || !buf) { set_error("rt_guide_load: null argument"); return RT_INVALID_ARG; }
+    const char *b = (const char *)buf;
+    RT_CUDA_TRY(cudaMemcpy(g->W32, b, g->nparams * 4, cudaMemcpyHostToDevice));
+    RT_CUDA_TRY(cudaMemcpy(g->m, b + g->nparams * 4, g->nparams * 4, cudaMemcpyHostToDevice));
+    RT_CUDA_TRY(cudaMemcpy(g->v, b + 2 * g->nparams * 4, g->nparams * 4, cudaMemcpyHostToDevice));
+    std::memcpy(&g->step, b + 3 * g->nparams * 4, 8);
+    rt_status s = repack(g, 0);
+    if (s != RT_OK) return s;
+    RT_CUDA_TRY(cudaDeviceSynchronize());
+    return RT_OK;
+}
+
+extern "C" rt_status rt_guide_infer(const rt_guide *gc, const float *features, int64_t n, float *raw, void *stream) {
+    rt_guide *g = const_cast<rt_guide *>(gc);
+    if (!g || (n > 0 && (!features || !raw)) || n < 0) { set_error("rt_guide_infer: invalid argument"); return RT_INVALID_ARG; }
+    if (n == 0) return RT_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const float *r = nullptr;
+    rt_status s = guide_infer_async(g, features, n, &r, st);
+    if (s != RT_OK) return s;
+    RT_CUDA_TRY(cudaMemcpy2DAsync(raw, kGuideOut * 4, r, kGuideOutPad * 4, kGuideOut * 4, n, cudaMemcpyDeviceToDevice, st));
+    return check_err(g, st);
+}
+
+extern "C" rt_status rt_guide_loss_grad(const rt_guide *gc, const float *features, const float *wi, const float *weight,
+                                        int64_t n, float *grad, float *loss, void *stream) {
+    rt_guide *g = const_cast<rt_guide *>(gc);
+    if (!g || n <= 0 || !features || !wi || !weight || !grad) { set_error("rt_guide_loss_grad: invalid argument"); return RT_INVALID_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    rt_status s = ensure_scratch(g, n);
+    if (s != RT_OK) return s;
+    if ((s = forward(g, features, n, true, st)) || (s = backward(g, wi, weight, n, st))) return s;
+    RT_CUDA_TRY(cudaMemcpyAsync(grad, g->grad, g->nparams * 4, cudaMemcpyDeviceToDevice, st));
+    if (loss) RT_CUDA_TRY(cudaMemcpyAsync(loss, g->loss, 4, cudaMemcpyDeviceToHost, st));
+    return check_err(g, st);
+}
+
+extern "C" rt_status rt_guide_train_step(rt_guide *g, const float *features, const float *wi, const float *weight,
+                                         int64_t n, void *stream) {
+    if (!g || n <= 0 || !features || !wi || !weight) { set_error("rt_guide_train_step: invalid argument"); return RT_INVALID_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    rt_status s = guide_train_async(g, features, wi, weight, n, st);
+    if (s != RT_OK) return s;
+    return check_err(g, st);
 }

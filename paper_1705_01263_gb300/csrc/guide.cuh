@@ -1,0 +1,137 @@
+// Device-side math of the guiding proposal: one-blob input encoding, the
+// 8-lobe von Mises-Fisher mixture decoded from the network outputs, its pdf
+// and sampling, and the gradient of the training loss -w log q(wi) with
+// respect to the raw outputs. Definitions (not from the paper, which has no
+// learned component): vMF q(w) = k / (2 pi (1 - e^{-2k})) exp(k (mu.w - 1)),
+// sampled as in Jakob 2012; one-blob bins per Mueller et al. 2019; mu =
+// normalise(raw xyz), kappa = clamp(softplus(raw), 1e-2, 1e4), weights =
+// softmax(logits).
+#pragma once
+
+#include "common.cuh"
+
+namespace rtg {
+
+constexpr int kGuideBins = 32;
+constexpr int kGuideIn = 7 * kGuideBins;   // 224
+constexpr int kGuideHid = 64;
+constexpr int kGuideOut = 40;
+constexpr int kGuideOutPad = 48;           // MMA N must be a multiple of 16
+constexpr int kGuideLobes = 8;
+constexpr int64_t kGuideParams = (int64_t)kGuideIn * kGuideHid + 3 * kGuideHid * kGuideHid + kGuideHid * kGuideOut;
+constexpr float kKappaMin = 1e-2f, kKappaMax = 1e4f;
+
+RT_HD float oneblob_bin(float s, int c) {
+    const float sig = 1.f / kGuideBins;
+    float d = s - ((float)c + 0.5f) / kGuideBins;
+    return expf(-d * d / (2.f * sig * sig));
+}
+
+// Features in [0,1]: position in the scene box (3), outgoing direction and
+// normal as ((cos theta + 1) / 2, phi / 2 pi) with theta measured from +y.
+RT_HD void dir_features(V3 w, float &a, float &b) {
+    float cy = fmaxf(-1.f, fminf(1.f, w.y));
+    float phi = atan2f(w.z, w.x);
+    if (phi < 0.f) phi += 2.f * kPi;
+    a = 0.5f * (cy + 1.f);
+    b = phi * (0.5f * kInvPi);
+}
+
+RT_HD void guide_features(V3 x, V3 wo, V3 n, float3 lo, float3 hi, float *f) {
+    f[0] = fminf(1.f, fmaxf(0.f, (x.x - lo.x) / fmaxf(hi.x - lo.x, 1e-20f)));
+    f[1] = fminf(1.f, fmaxf(0.f, (x.y - lo.y) / fmaxf(hi.y - lo.y, 1e-20f)));
+    f[2] = fminf(1.f, fmaxf(0.f, (x.z - lo.z) / fmaxf(hi.z - lo.z, 1e-20f)));
+    dir_features(wo, f[3], f[4]);
+    dir_features(n, f[5], f[6]);
+}
+
+RT_HD float softplusf(float x) { return x > 20.f ? x : log1pf(expf(x)); }
+
+struct Mixture {
+    V3 mu[kGuideLobes];
+    float kappa[kGuideLobes];
+    float w[kGuideLobes];
+};
+
+RT_HD void decode_mixture(const float *raw, Mixture &m) {
+    float mx = -INFINITY;
+    for (int k = 0; k < kGuideLobes; ++k) mx = fmaxf(mx, raw[5 * k + 4]);
+    float z = 0.f;
+    for (int k = 0; k < kGuideLobes; ++k) {
+        const float *r = raw + 5 * k;
+        float l = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        m.mu[k] = l > 0.f ? v3(r[0] / l, r[1] / l, r[2] / l) : v3(0.f, 0.f, 1.f);
+        m.kappa[k] = fminf(kKappaMax, fmaxf(kKappaMin, softplusf(r[3])));
+        m.w[k] = expf(r[4] - mx);
+        z += m.w[k];
+    }
+    for (int k = 0; k < kGuideLobes; ++k) m.w[k] /= z;
+}
+
+RT_HD float vmf_pdf(float kappa, V3 mu, V3 w) {
+    return kappa / (2.f * kPi * -expm1f(-2.f * kappa)) * expf(kappa * (dot(mu, w) - 1.f));
+}
+
+RT_HD float mixture_pdf(const Mixture &m, V3 w) {
+    float p = 0.f;
+    for (int k = 0; k < kGuideLobes; ++k) p += m.w[k] * vmf_pdf(m.kappa[k], m.mu[k], w);
+    return p;
+}
+
+// Lobe by u_sel, then cos theta = 1 + ln(u1 + (1 - u1) e^{-2k}) / k about mu.
+RT_HD V3 mixture_sample(const Mixture &m, float u_sel, float u1, float u2) {
+    int k = 0;
+    float acc = 0.f;
+    for (k = 0; k < kGuideLobes - 1; ++k) {
+        if (u_sel < acc + m.w[k]) break;
+        acc += m.w[k];
+    }
+    float kap = m.kappa[k];
+    float ct = 1.f + logf(u1 + (1.f - u1) * expf(-2.f * kap)) / kap;
+    ct = fminf(1.f, fmaxf(-1.f, ct));
+    float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
+    float phi = 2.f * kPi * u2;
+    V3 n = m.mu[k];
+    float sign = n.z >= 0.f ? 1.f : -1.f;
+    float a = -1.f / (sign + n.z);
+    float bb = n.x * n.y * a;
+    V3 t = v3(1.f + sign * n.x * n.x * a, sign * bb, -sign * n.x);
+    V3 b = v3(bb, sign + n.y * n.y * a, -n.y);
+    return normalize(st * cosf(phi) * t + st * sinf(phi) * b + ct * n);
+}
+
+// Loss contribution scale * -log q(wi) and its gradient w.r.t. raw (40
+// entries written; entries 40..47 left untouched).
+RT_HD float mixture_loss_grad(const float *raw, const float *wi3, float scale, float *g) {
+    Mixture m;
+    decode_mixture(raw, m);
+    V3 wi = v3(wi3[0], wi3[1], wi3[2]);
+    float q[kGuideLobes], qm = 0.f;
+    for (int k = 0; k < kGuideLobes; ++k) {
+        q[k] = vmf_pdf(m.kappa[k], m.mu[k], wi);
+        qm += m.w[k] * q[k];
+    }
+    qm = fmaxf(qm, 1e-30f);
+    for (int k = 0; k < kGuideLobes; ++k) {
+        const float *rk = raw + 5 * k;
+        float resp = m.w[k] * q[k] / qm;
+        float c = dot(m.mu[k], wi);
+        float l = sqrtf(rk[0] * rk[0] + rk[1] * rk[1] + rk[2] * rk[2]);
+        float inv_l = l > 0.f ? 1.f / l : 0.f;
+        g[5 * k + 0] = -scale * resp * m.kappa[k] * (wi.x - c * m.mu[k].x) * inv_l;
+        g[5 * k + 1] = -scale * resp * m.kappa[k] * (wi.y - c * m.mu[k].y) * inv_l;
+        g[5 * k + 2] = -scale * resp * m.kappa[k] * (wi.z - c * m.mu[k].z) * inv_l;
+        float sp = softplusf(rk[3]);
+        float dk = 0.f;
+        if (sp > kKappaMin && sp < kKappaMax) {
+            float kk = m.kappa[k];
+            float dlogq = 1.f / kk - 2.f / expm1f(2.f * kk) + (c - 1.f);
+            dk = resp * dlogq / (1.f + expf(-rk[3]));
+        }
+        g[5 * k + 3] = -scale * dk;
+        g[5 * k + 4] = -scale * (resp - m.w[k]);
+    }
+    return -scale * logf(qm);
+}
+
+}  // namespace rtg

@@ -86,7 +86,7 @@ EXPORTED = [
     "rt_render_static", "rt_sample_index", "rt_halton", "rt_divide_u64_host", "rt_guide_create", "rt_guide_destroy",
     "rt_guide_num_params", "rt_guide_get_params", "rt_guide_set_params", "rt_guide_state_size", "rt_guide_save",
     "rt_guide_load", "rt_guide_infer", "rt_guide_loss_grad", "rt_guide_train_step", "rt_last_error",
-    "rt_status_string",
+    "rt_status_string", "rt_gemm_bf16",
 ]
 
 
@@ -124,6 +124,7 @@ def _declare(L):
         "rt_sample_index": [u32, u32, vp, vp, vp, i64, vp, vp],
         "rt_halton": [u32, u32, u64, vp, i64, i32, vp, vp],
         "rt_divide_u64_host": [vp, i64, u32, vp],
+        "rt_gemm_bf16": [vp, vp, vp, i32, i32, i32, i32, i32, i32, i32, vp],
         "rt_debug_trace_host": [vp, vp, i64, i32, vp, vp, vp, vp, vp],
         "rt_debug_render_host": [vp, C.POINTER(rt_camera), u32, C.POINTER(rt_render_opts), vp, vp, vp, i64, vp],
         "rt_debug_halton_host": [u32, u32, u64, vp, i64, i32, vp],
@@ -410,6 +411,83 @@ def rt_divide_u64_host(n: np.ndarray, d: int) -> np.ndarray:
     q = np.zeros_like(n)
     check(lib().rt_divide_u64_host(n.ctypes.data, n.size, d, q.ctypes.data))
     return q
+
+
+def rt_gemm_bf16(A, B, C=None, accumulate=False, stream=None):
+    """C = A @ B.T on the tensor cores (A: M x K bf16, B: N x K bf16, C: M x N f32)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    if C is None:
+        C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    check(lib().rt_gemm_bf16(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, A.stride(0), B.stride(0),
+                             C.stride(0), int(accumulate), _stream(stream)))
+    return C
+
+
+class Guide:
+    """Online path-guiding network (rt_guide_*)."""
+
+    def __init__(self, scene=None, batch=0, lr=0.0, alpha=0.0, train_steps=0, seed=0):
+        o = rt_guide_opts(batch, lr, alpha, train_steps, seed)
+        h = C.c_void_p()
+        check(lib().rt_guide_create(scene.handle if scene is not None else None, C.byref(o), C.byref(h)))
+        self.handle = h
+
+    @staticmethod
+    def num_params() -> int:
+        return lib().rt_guide_num_params()
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.num_params(), np.float32)
+        check(lib().rt_guide_get_params(self.handle, p.ctypes.data))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        check(lib().rt_guide_set_params(self.handle, p.ctypes.data))
+
+    def state(self) -> bytes:
+        n = C.c_int64()
+        check(lib().rt_guide_state_size(self.handle, C.byref(n)))
+        buf = np.zeros(n.value, np.uint8)
+        check(lib().rt_guide_save(self.handle, buf.ctypes.data))
+        return buf.tobytes()
+
+    def load(self, blob: bytes):
+        buf = np.frombuffer(blob, np.uint8).copy()
+        check(lib().rt_guide_load(self.handle, buf.ctypes.data))
+
+    def infer(self, features, stream=None):
+        import torch
+        n = features.shape[0]
+        raw = torch.empty((n, 40), dtype=torch.float32, device=features.device)
+        check(lib().rt_guide_infer(self.handle, features.data_ptr(), n, raw.data_ptr(), _stream(stream)))
+        return raw
+
+    def loss_grad(self, features, wi, weight, stream=None):
+        import torch
+        n = features.shape[0]
+        g = torch.empty(self.num_params(), dtype=torch.float32, device=features.device)
+        loss = C.c_float()
+        check(lib().rt_guide_loss_grad(self.handle, features.data_ptr(), wi.data_ptr(), weight.data_ptr(), n,
+                                       g.data_ptr(), C.byref(loss), _stream(stream)))
+        return loss.value, g
+
+    def train_step(self, features, wi, weight, stream=None):
+        check(lib().rt_guide_train_step(self.handle, features.data_ptr(), wi.data_ptr(), weight.data_ptr(),
+                                        features.shape[0], _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rt_guide_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # -------------------------------------------------- host test hooks (CPU)
