@@ -285,6 +285,7 @@ rt_status guide_train_async(rt_guide *g, const float *feat, const float *wi, con
 float guide_alpha(const rt_guide *g) { return g->opts.alpha; }
 void guide_bounds(const rt_guide *g, float3 &lo, float3 &hi) { lo = g->bb_lo; hi = g->bb_hi; }
 uint32_t guide_batch(const rt_guide *g) { return g->opts.batch; }
+bool guide_trained(const rt_guide *g) { return g->step > 0; }
 }  // namespace rtg
 
 extern "C" int64_t rt_guide_num_params(void) { return kGuideParams; }

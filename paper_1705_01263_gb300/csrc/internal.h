@@ -38,6 +38,15 @@ rt_status cuda_status(cudaError_t e, const char *what);
     } while (0)
 
 std::vector<HaltonDim> make_dims(uint64_t seed, int ndims);
+
+// guiding network (guide.cu)
+rt_status guide_infer_async(rt_guide *g, const float *feat, int64_t n, const float **raw_out, cudaStream_t st);
+rt_status guide_train_async(rt_guide *g, const float *feat, const float *wi, const float *weight, int64_t n,
+                            cudaStream_t st);
+float guide_alpha(const rt_guide *g);
+void guide_bounds(const rt_guide *g, float3 &lo, float3 &hi);
+uint32_t guide_batch(const rt_guide *g);
+bool guide_trained(const rt_guide *g);
 uint32_t nth_prime(int dim);
 
 }  // namespace rtg

@@ -25,7 +25,7 @@ namespace rtg {
 struct Ctrl {
     uint32_t n_ext, n_next, n_shadow, cur;
     uint32_t tail, overflow, tail_threshold, pad;
-    uint32_t fetch_ext, fetch_shadow, fetch_shade, fetch_ext2;
+    uint32_t fetch_ext, fetch_shadow, fetch_shade, n_train;
     unsigned long long ext_rays, shadow_rays;
     unsigned long long ext_nodes, ext_tris, shadow_nodes, shadow_tris;
 };
@@ -46,6 +46,7 @@ struct Pool {
     uint32_t *qs;    // shadow-ray queue
     Ctrl *ctrl;
     uint32_t capacity;
+    uint32_t *nrec;  // guided rendering: training records per path (count | pending flag), else null
 };
 
 RT_D void store_state(const Pool &p, uint32_t q, const PathState &s) {
@@ -132,6 +133,7 @@ __global__ void k_raygen(RenderParams P, Pool pool, uint64_t t0, uint32_t n, uin
         raygen(P, (uint32_t)(t % WH), (uint32_t)(t / WH), s);
         store_state(pool, q, s);
         pool.q[0][q] = q;
+        if (pool.nrec) pool.nrec[q] = 0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         Ctrl *c = pool.ctrl;
@@ -142,7 +144,7 @@ __global__ void k_raygen(RenderParams P, Pool pool, uint64_t t0, uint32_t n, uin
         c->fetch_ext = 0;
         c->fetch_shadow = 0;
         c->fetch_shade = 0;
-        c->fetch_ext2 = 0;
+        c->n_train = 0;
         c->tail_threshold = tail_threshold;
         c->tail = n < tail_threshold ? 1u : 0u;
     }
@@ -331,7 +333,6 @@ __global__ void k_step_end(Pool pool) {
     c->fetch_ext = 0;
     c->fetch_shadow = 0;
     c->fetch_shade = 0;
-    c->fetch_ext2 = 0;
 }
 
 // Megakernel: every remaining sample runs to completion in its own thread.
@@ -439,6 +440,124 @@ __global__ void k_halton(Enum en, const HaltonDim *dims, const uint64_t *idx, in
     }
 }
 
+// ------------------------------------------------------- guided rendering
+constexpr uint32_t kGuideMaxRec = 8;       // vertices per path that feed training
+constexpr uint32_t kRecPending = 0x80000000u;
+
+// Network inputs of every vertex in the extension queue (zeros for misses
+// and for the last vertex, which only adds emission).
+__global__ void k_guide_features(RenderParams P, Pool pool, float *feat, float3 lo, float3 hi) {
+    Ctrl *c = pool.ctrl;
+    const uint32_t n = c->n_ext;
+    const uint32_t *queue = pool.q[c->cur];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t q = queue[i];
+        PathState s = load_state(pool, q);
+        float4 hv = pool.hit[q];
+        Hit h;
+        h.prim = __float_as_uint(hv.x); h.inst = 0; h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
+        float f[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (h.prim != RT_MISS && s.depth <= P.max_depth) {
+            Vertex vx;
+            setup_vertex(P.sc, s, h, vx);
+            guide_features(vx.x, vx.wo, vx.ns, lo, hi, f);
+        }
+#pragma unroll
+        for (int k = 0; k < 7; ++k) feat[7 * (size_t)i + k] = f[k];
+    }
+}
+
+// Shading with the guided mixture; records (features, wi, throughput) of
+// every continuing vertex and, at the next vertex, the radiance gathered so
+// far, so that the radiance returned through wi is L_end - L_snapshot.
+__global__ void __launch_bounds__(128) k_shade_guided(RenderParams P, Pool pool, const float *raw, float alpha,
+                                                      float4 *rec, float3 lo, float3 hi) {
+    Ctrl *c = pool.ctrl;
+    const uint32_t n = c->n_ext;
+    const uint32_t cur = c->cur;
+    const uint32_t *queue = pool.q[cur];
+    uint32_t *next = pool.q[cur ^ 1u];
+    for (;;) {
+        uint32_t base = warp_fetch32(&c->fetch_shade);
+        if (base >= n) break;
+        uint32_t i = base + lane_id();
+        bool valid = i < n;
+        uint32_t q = 0;
+        int r = 0;
+        if (valid) {
+            q = queue[i];
+            PathState s = load_state(pool, q);
+            uint32_t nr = pool.nrec[q];
+            if (nr & kRecPending) {
+                nr &= ~kRecPending;
+                float4 *R = rec + ((size_t)q * kGuideMaxRec + (nr - 1)) * 4;
+                R[3] = make_float4(R[3].x, s.L.x, s.L.y, s.L.z);
+                pool.nrec[q] = nr;
+            }
+            float4 hv = pool.hit[q];
+            Hit h;
+            h.prim = __float_as_uint(hv.x); h.inst = 0; h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
+            ShadowRay sh;
+            GuideRecord gr;
+            const uint32_t v = s.depth;
+            const bool want = v <= kGuideMaxRec;
+            r = shade(P, s, h, sh, raw ? raw + (size_t)kGuideOutPad * i : nullptr, alpha, want ? &gr : nullptr, lo, hi);
+            pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
+            if (r & 1) {
+                pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, 0.f);
+                pool.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);
+                pool.beta[q] = make_float4(s.beta.x, s.beta.y, s.beta.z, __uint_as_float(s.depth));
+                if (want) {
+                    float4 *R = rec + ((size_t)q * kGuideMaxRec + (v - 1)) * 4;
+                    R[0] = make_float4(gr.feat[0], gr.feat[1], gr.feat[2], gr.feat[3]);
+                    R[1] = make_float4(gr.feat[4], gr.feat[5], gr.feat[6], gr.wi.x);
+                    R[2] = make_float4(gr.wi.y, gr.wi.z, gr.beta.x, gr.beta.y);
+                    R[3] = make_float4(gr.beta.z, 0.f, 0.f, 0.f);
+                    pool.nrec[q] = v | kRecPending;
+                }
+            }
+            if (r & 2) {
+                pool.sh_o[q] = make_float4(sh.o.x, sh.o.y, sh.o.z, sh.tmax);
+                pool.sh_d[q] = make_float4(sh.d.x, sh.d.y, sh.d.z, 0.f);
+                pool.sh_c[q] = make_float4(sh.contrib.x, sh.contrib.y, sh.contrib.z, 0.f);
+            }
+        }
+        warp_append(next, &c->n_next, valid && (r & 1), q);
+        warp_append(pool.qs, &c->n_shadow, valid && (r & 2), q);
+    }
+}
+
+// Training samples of finished paths: weight = luminance of the radiance that
+// came back through wi divided by the throughput on arrival, i.e. the
+// sampled f cos Li / p of that vertex.
+__global__ void k_guide_collect(Pool pool, uint32_t n, const float4 *rec, float *tr_feat, float *tr_wi, float *tr_w,
+                                uint32_t batch) {
+    Ctrl *c = pool.ctrl;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        uint32_t nr = pool.nrec[q];
+        uint32_t complete = (nr & kRecPending) ? (nr & ~kRecPending) - 1 : nr;
+        float4 L = pool.L[q];
+        for (uint32_t k = 0; k < complete; ++k) {
+            const float4 *R = rec + ((size_t)q * kGuideMaxRec + k) * 4;
+            float4 r0 = R[0], r1 = R[1], r2 = R[2], r3 = R[3];
+            float bx = r2.z, by = r2.w, bz = r3.x;
+            float ax = bx > 0.f ? fmaxf(L.x - r3.y, 0.f) / bx : 0.f;
+            float ay = by > 0.f ? fmaxf(L.y - r3.z, 0.f) / by : 0.f;
+            float az = bz > 0.f ? fmaxf(L.z - r3.w, 0.f) / bz : 0.f;
+            float w = lum(v3(ax, ay, az));
+            if (!(w > 0.f) || !isfinite(w)) continue;
+            uint32_t idx = atomicAdd(&c->n_train, 1u);
+            if (idx >= batch) continue;
+            float f[7] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z};
+            for (int j = 0; j < 7; ++j) tr_feat[7 * (size_t)idx + j] = f[j];
+            tr_wi[3 * (size_t)idx] = r1.w;
+            tr_wi[3 * (size_t)idx + 1] = r2.x;
+            tr_wi[3 * (size_t)idx + 2] = r2.y;
+            tr_w[idx] = w;
+        }
+    }
+}
+
 // ---------------------------------------------------------- host helpers
 int sm_count() {
     static int n = 0;
@@ -515,11 +634,40 @@ struct RenderCache {
     uint64_t dims_seed = ~0ull;
     int dims_n = 0;
     Ctrl *host_ctrl = nullptr;
+    // guided rendering
+    uint32_t gcap = 0, gbatch = 0;
+    float *gfeat = nullptr, *tr_feat = nullptr, *tr_wi = nullptr, *tr_w = nullptr;
+    float4 *grec = nullptr;
+    uint32_t *gnrec = nullptr;
     ~RenderCache() {
         if (dims) cudaFree(dims);
         if (host_ctrl) cudaFreeHost(host_ctrl);
+        for (void *p : {(void *)gfeat, (void *)tr_feat, (void *)tr_wi, (void *)tr_w, (void *)grec, (void *)gnrec})
+            if (p) cudaFree(p);
     }
 };
+
+static rt_status ensure_guided(RenderCache *rc, uint32_t cap, uint32_t batch) {
+    if (rc->gcap >= cap && rc->gbatch >= batch) return RT_OK;
+    for (void *p : {(void *)rc->gfeat, (void *)rc->tr_feat, (void *)rc->tr_wi, (void *)rc->tr_w, (void *)rc->grec,
+                    (void *)rc->gnrec})
+        if (p) cudaFree(p);
+    rc->gfeat = rc->tr_feat = rc->tr_wi = rc->tr_w = nullptr;
+    rc->grec = nullptr;
+    rc->gnrec = nullptr;
+    if (cudaMalloc(&rc->gfeat, (size_t)cap * 7 * 4) != cudaSuccess ||
+        cudaMalloc(&rc->grec, (size_t)cap * kGuideMaxRec * 4 * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc(&rc->gnrec, (size_t)cap * 4) != cudaSuccess ||
+        cudaMalloc(&rc->tr_feat, (size_t)batch * 7 * 4) != cudaSuccess ||
+        cudaMalloc(&rc->tr_wi, (size_t)batch * 3 * 4) != cudaSuccess ||
+        cudaMalloc(&rc->tr_w, (size_t)batch * 4) != cudaSuccess) {
+        set_error("guided rendering: out of device memory");
+        return RT_OOM;
+    }
+    rc->gcap = cap;
+    rc->gbatch = batch;
+    return RT_OK;
+}
 
 static RenderCache *cache_of(rt_film *f);
 
@@ -673,6 +821,94 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     auto t_start = std::chrono::steady_clock::now();
     uint64_t t = film->next_task, t_end = film->next_task + (uint64_t)spp * WH;
     rt_status result = RT_OK;
+    if (o.guide) {
+        // Guided iteration sets: every bounce step reads the queue length,
+        // runs the network on the queue's vertices, shades with the
+        // one-sample MIS mixture and records training samples; each set ends
+        // with one training step on up to `batch` samples. The megakernel
+        // tail is off (it has no guided branch). Until the first training
+        // step the proposal is BSDF-only.
+        rt_guide *gd = o.guide;
+        const uint32_t batch = guide_batch(gd);
+        if ((rs = ensure_guided(rc, cap, batch)) != RT_OK) return rs;
+        rc->pool.view.nrec = rc->gnrec;
+        Pool gpool = rc->pool.view;
+        float3 glo, ghi;
+        guide_bounds(gd, glo, ghi);
+        const float alpha = guide_alpha(gd);
+        const int gbk = 128;
+        const int g_ray = grid_for(k_raygen, 256, cap);
+        const int g_trace = grid_persistent(k_trace_ext_simple<false>, gbk, 0);
+        const int g_shade = grid_persistent(k_shade_guided, gbk, 0);
+        const int g_feat = grid_for(k_guide_features, 256, cap);
+        rt_stats stats{};
+        auto t_start = std::chrono::steady_clock::now();
+        uint64_t t = film->next_task, t_end = film->next_task + (uint64_t)spp * WH;
+        rt_status result = RT_OK;
+        while (t < t_end) {
+            uint64_t n64;
+            uint32_t passes = 0;
+            if (t % WH != 0 || WH > cap) {
+                n64 = std::min<uint64_t>({t_end - t, WH - t % WH, (uint64_t)cap});
+            } else {
+                uint64_t full = std::min<uint64_t>((t_end - t) / WH, cap / WH);
+                if (full >= 1) { passes = (uint32_t)full; n64 = full * WH; }
+                else n64 = std::min<uint64_t>(t_end - t, cap);
+            }
+            uint32_t n = (uint32_t)n64;
+            const float a = guide_trained(gd) ? alpha : 0.f;
+            k_raygen<<<g_ray, 256, 0, st>>>(P, gpool, t, n, (uint32_t)WH, 0u);
+            stats.kernel_launches += 1;
+            for (uint32_t v = 1; v <= max_depth + 1; ++v) {
+                k_trace_ext_simple<false><<<g_trace, gbk, 0, st>>>(s->dev, gpool);
+                RT_CUDA_TRY(cudaMemcpyAsync(rc->host_ctrl, gpool.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+                RT_CUDA_TRY(cudaStreamSynchronize(st));
+                const uint32_t n_ext = rc->host_ctrl->n_ext;
+                if (n_ext == 0) break;
+                const float *raw = nullptr;
+                if (a > 0.f) {
+                    k_guide_features<<<g_feat, 256, 0, st>>>(P, gpool, rc->gfeat, glo, ghi);
+                    if ((rs = guide_infer_async(gd, rc->gfeat, n_ext, &raw, st)) != RT_OK) return rs;
+                    stats.kernel_launches += 1 + 12;
+                }
+                k_shade_guided<<<g_shade, gbk, 0, st>>>(P, gpool, raw, a, rc->grec, glo, ghi);
+                k_trace_shadow_simple<false><<<g_trace, gbk, 0, st>>>(s->dev, gpool);
+                k_step_end<<<1, 1, 0, st>>>(gpool);
+                stats.kernel_launches += 4;
+                ++stats.wavefront_steps;
+            }
+            int g_film = grid_for(k_film, 256, passes ? WH : n);
+            k_film<<<g_film, 256, 0, st>>>(gpool, film->sum, film->sum2, film->count, t, n, (uint32_t)WH, passes);
+            k_guide_collect<<<grid_for(k_guide_collect, 256, n), 256, 0, st>>>(gpool, n, rc->grec, rc->tr_feat,
+                                                                               rc->tr_wi, rc->tr_w, batch);
+            stats.kernel_launches += 2;
+            RT_CUDA_TRY(cudaGetLastError());
+            RT_CUDA_TRY(cudaMemcpyAsync(rc->host_ctrl, gpool.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+            RT_CUDA_TRY(cudaStreamSynchronize(st));
+            t += n;
+            film->next_task = t;
+            stats.paths += n;
+            ++stats.waves;
+            if (rc->host_ctrl->overflow) { set_error("BVH traversal stack overflow"); result = RT_STACK_OVERFLOW; break; }
+            const uint32_t n_train = std::min(rc->host_ctrl->n_train, batch);
+            if (n_train >= 256) {
+                if ((rs = guide_train_async(gd, rc->tr_feat, rc->tr_wi, rc->tr_w, n_train, st)) != RT_OK) return rs;
+                stats.kernel_launches += 40;
+            }
+            double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+            if (t < t_end && ((o.abort_flag && *o.abort_flag) || (o.time_budget_ms > 0 && ms >= o.time_budget_ms))) {
+                set_error("rt_render: stopped by time budget or abort flag (resumable)");
+                result = RT_TIMEOUT;
+                break;
+            }
+        }
+        RT_CUDA_TRY(cudaStreamSynchronize(st));
+        rc->pool.view.nrec = nullptr;
+        stats.extension_rays = rc->host_ctrl->ext_rays;
+        stats.shadow_rays = rc->host_ctrl->shadow_rays;
+        if (o.stats) *o.stats = stats;
+        return result;
+    }
     const int gb = 128;
     const int g_ray = grid_for(k_raygen, 256, cap);
     const size_t smem = stack_smem(gb);

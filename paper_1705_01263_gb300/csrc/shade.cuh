@@ -17,6 +17,7 @@
 //  - shadow rays to a triangle stop at (1 - 1e-4) of its distance.
 #pragma once
 
+#include "guide.cuh"
 #include "halton.cuh"
 #include "traverse.cuh"
 
@@ -323,10 +324,57 @@ RT_HD V3 offset_origin(V3 p, V3 n) {
 }
 
 // --------------------------------------------------------------- shading
+// Local frame of a hit (Sec. 2.2 stage 1): position from barycentrics,
+// geometric normal turned towards wo, interpolated shading normal on the same
+// side, adapted so the perfect reflection stays above the tangent plane
+// (Appendix A.3).
+struct Vertex {
+    V3 x, ng, ns, wo;
+    float cog;        // cos between wo and the unflipped geometric normal
+};
+
+RT_HD void setup_vertex(const DevScene &sc, const PathState &s, const Hit &h, Vertex &vx) {
+    const uint32_t prim = h.prim;
+    V3 v0 = tri_vertex(sc, prim, 0), v1 = tri_vertex(sc, prim, 1), v2 = tri_vertex(sc, prim, 2);
+    float b0 = 1.f - h.b1 - h.b2;
+    vx.x = b0 * v0 + h.b1 * v1 + h.b2 * v2;
+    V3 ng = normalize(cross(v1 - v0, v2 - v0));
+    vx.wo = -s.d;
+    vx.cog = dot(vx.wo, ng);
+    if (vx.cog < 0.f) ng = -ng;
+    V3 ns = ng;
+    if (sc.normals) {
+        uint32_t i0 = ldg(sc.indices + 3 * (size_t)prim), i1 = ldg(sc.indices + 3 * (size_t)prim + 1),
+                 i2 = ldg(sc.indices + 3 * (size_t)prim + 2);
+        const float *n0 = sc.normals + 3 * (size_t)i0, *n1 = sc.normals + 3 * (size_t)i1,
+                    *n2 = sc.normals + 3 * (size_t)i2;
+        ns = normalize(b0 * v3(ldg(n0), ldg(n0 + 1), ldg(n0 + 2)) + h.b1 * v3(ldg(n1), ldg(n1 + 1), ldg(n1 + 2)) +
+                       h.b2 * v3(ldg(n2), ldg(n2 + 1), ldg(n2 + 2)));
+        if (dot(ns, ng) < 0.f) ns = -ns;
+    }
+    vx.ng = ng;
+    vx.ns = adapt_shading_normal(ns, ng, vx.wo);
+}
+
+// Training record of a guided vertex: network input, sampled direction and
+// the throughput on arrival (the radiance that comes back through wi is
+// known only when the path ends).
+struct GuideRecord {
+    float feat[7];
+    V3 wi;
+    V3 beta;
+};
+
 // Shade the hit of the pending ray of `s`. Returns bit 0 when the path
 // continues (new pending ray in s.o, s.d) and bit 1 when `sh` holds a shadow
-// ray whose unoccluded contribution must be added to s.L.
-RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh) {
+// ray whose unoccluded contribution must be added to s.L. With `graw` (the
+// guiding network's 40 outputs for this vertex) the continuation is drawn
+// from the one-sample MIS mixture alpha * vMF-mixture + (1 - alpha) * BSDF
+// and every pdf used for MIS is that mixture's; with `rec` the vertex's
+// training record is filled when the path continues.
+RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh, const float *graw = nullptr,
+                float alpha = 0.f, GuideRecord *rec = nullptr, float3 glo = float3{0.f, 0.f, 0.f},
+                float3 ghi = float3{1.f, 1.f, 1.f}) {
     const DevScene &sc = P.sc;
     const int mode = P.mis_mode;
     const uint32_t v = s.depth;
@@ -345,37 +393,25 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
         return 0;
     }
     const uint32_t prim = h.prim;
-    V3 v0 = tri_vertex(sc, prim, 0), v1 = tri_vertex(sc, prim, 1), v2 = tri_vertex(sc, prim, 2);
-    float b0 = 1.f - h.b1 - h.b2;
-    V3 x = b0 * v0 + h.b1 * v1 + h.b2 * v2;
-    V3 ng = normalize(cross(v1 - v0, v2 - v0));
-    V3 wo = -s.d;
-    float cog = dot(wo, ng);
+    Vertex vx;
+    setup_vertex(sc, s, h, vx);
     float lpa = ldg(sc.tri_light_pdf_area + prim);
-    if (cog > 0.f && lpa > 0.f) {
+    if (vx.cog > 0.f && lpa > 0.f) {
         V3 Le = tri_emission(sc, prim, h.b1, h.b2);
         float w = 1.f;
         if (v > 1) {
             if (mode == 3) w = 1.f;
             else if (mode == 2) w = 0.f;
-            else w = mis_weight(mode, s.prev_pdf, lpa * h.t * h.t / cog);
+            else w = mis_weight(mode, s.prev_pdf, lpa * h.t * h.t / vx.cog);
         }
         s.L = s.L + mul(s.beta, Le) * w;
     }
     if (v == P.max_depth + 1) return 0;
-    if (cog < 0.f) ng = -ng;
-    V3 ns = ng;
-    if (sc.normals) {
-        uint32_t i0 = ldg(sc.indices + 3 * (size_t)prim), i1 = ldg(sc.indices + 3 * (size_t)prim + 1),
-                 i2 = ldg(sc.indices + 3 * (size_t)prim + 2);
-        const float *n0 = sc.normals + 3 * (size_t)i0, *n1 = sc.normals + 3 * (size_t)i1,
-                    *n2 = sc.normals + 3 * (size_t)i2;
-        ns = normalize(b0 * v3(ldg(n0), ldg(n0 + 1), ldg(n0 + 2)) + h.b1 * v3(ldg(n1), ldg(n1 + 1), ldg(n1 + 2)) +
-                       h.b2 * v3(ldg(n2), ldg(n2 + 1), ldg(n2 + 2)));
-        if (dot(ns, ng) < 0.f) ns = -ns;
-    }
-    ns = adapt_shading_normal(ns, ng, wo);
+    const V3 x = vx.x, ng = vx.ng, ns = vx.ns, wo = vx.wo;
     Material m = load_material(sc, ldg(sc.tri_material + prim));
+    Mixture mix;
+    const bool guided = graw != nullptr && alpha > 0.f;
+    if (guided) decode_mixture(graw, mix);
     const int base = 2 + 7 * (int)(v - 1);
     V3 xo = offset_origin(x, ng);
     int ret = 0;
@@ -420,7 +456,8 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
             V3 f;
             float pdf_b;
             bsdf_eval(m, ns, wo, wi, f, pdf_b);
-            if (pdf_b > 0.f) {
+            if (guided) pdf_b = alpha * mixture_pdf(mix, wi) + (1.f - alpha) * pdf_b;
+            if (pdf_b > 0.f && (!guided || f.x > 0.f || f.y > 0.f || f.z > 0.f)) {
                 float w = mode == 2 ? 1.f : mis_weight(mode, pdf_l, pdf_b);
                 float k = dot(wi, ns) * w / pdf_l;
                 sh.o = xo;
@@ -434,11 +471,25 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
     // continuation
     V3 wi, f;
     float pdf;
-    if (!bsdf_sample(m, ns, wo, dim_value(P, s.index, base + 3), dim_value(P, s.index, base + 4),
-                     dim_value(P, s.index, base + 5), wi, f, pdf))
+    float u3 = dim_value(P, s.index, base + 3), u4 = dim_value(P, s.index, base + 4),
+          u5 = dim_value(P, s.index, base + 5);
+    if (guided) {
+        if (u3 < alpha) {
+            wi = mixture_sample(mix, u3 / alpha, u4, u5);
+        } else {
+            V3 fb;
+            float pb;
+            if (!bsdf_sample(m, ns, wo, (u3 - alpha) / (1.f - alpha), u4, u5, wi, fb, pb)) return ret;
+        }
+        bsdf_eval(m, ns, wo, wi, f, pdf);
+        pdf = alpha * mixture_pdf(mix, wi) + (1.f - alpha) * pdf;
+        if (!(pdf > 0.f) || (f.x <= 0.f && f.y <= 0.f && f.z <= 0.f)) return ret;
+    } else if (!bsdf_sample(m, ns, wo, u3, u4, u5, wi, f, pdf)) {
         return ret;
+    }
     if (dot(wi, ng) <= 0.f) return ret;
     float ci = dot(wi, ns);
+    V3 beta_in = s.beta;
     s.beta = mul(s.beta, f) * (ci / pdf);
     if (P.rr && v >= 3) {
         float q = fmaxf(0.05f, 1.f - maxc(s.beta));
@@ -446,6 +497,11 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
         s.beta = s.beta * (1.f / (1.f - q));
     }
     if (s.beta.x == 0.f && s.beta.y == 0.f && s.beta.z == 0.f) return ret;
+    if (rec) {
+        guide_features(x, wo, ns, glo, ghi, rec->feat);
+        rec->wi = wi;
+        rec->beta = beta_in;
+    }
     s.prev_pdf = pdf;
     s.o = xo;
     s.d = wi;
