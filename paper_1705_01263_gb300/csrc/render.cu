@@ -785,7 +785,6 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     if (max_depth < 1 || max_depth > (uint32_t)kMaxDepth) { set_error("rt_render: max_depth must be in [1, 64]"); return RT_INVALID_ARG; }
     rt_render_opts o{};
     if (opts_in) o = *opts_in;
-    if (o.guide) { set_error("rt_render: guiding handle not supported by this entry point yet"); return RT_NOT_SUPPORTED; }
     if (spp == 0) return RT_OK;
     cudaStream_t st = (cudaStream_t)stream;
     RenderCache *rc = cache_of(film);
