@@ -123,6 +123,59 @@ def cpu_baseline_oracle(sd, cam):
             "mrays_per_s": rays / dt / 1e6}
 
 
+def guided_vs_plain(target_spp=256, chunk=16, max_spp=1024, seed=5):
+    """Time to equal RMSE on the Cornell configuration (64 x 64, depth 8):
+    RMSE against the stored FP64 oracle reference (2^15 spp) after every
+    iteration set of `chunk` spp; the target is the plain tracer's RMSE at
+    `target_spp`; guided time includes its inference and training."""
+    import torch
+    from paper_1705_01263_gb300 import rt, scenes
+    ref_path = os.path.join(ROOT, "tests", "golden", "cornell_64_depth8_ref.npz")
+    if not os.path.exists(ref_path):
+        return None
+    ref = np.load(ref_path)["mean"]
+    sd, cam = scenes.cornell_box()
+    scene = rt.Scene(sd)
+    mean = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+
+    def curve(guided):
+        film = rt.Film(cam.width, cam.height)
+        guide = rt.Guide(scene, seed=seed) if guided else None
+        # warm-up of the code path on a scratch film (not timed)
+        scratch = rt.Film(cam.width, cam.height)
+        rt.rt_render(scene, cam, chunk, 8, scratch, rt.make_opts(guide=rt.Guide(scene, seed=seed + 1) if guided else None))
+        torch.cuda.synchronize()
+        pts = []
+        t0 = time.perf_counter()
+        spp = 0
+        while spp < max_spp:
+            rt.rt_render(scene, cam, chunk, 8, film, rt.make_opts(guide=guide))
+            spp += chunk
+            film.resolve(mean)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            img = mean.cpu().numpy().astype(np.float64)
+            pts.append((spp, el, float(np.sqrt(np.mean((img - ref) ** 2)))))
+            if not guided and spp >= target_spp:
+                break
+        return pts
+
+    plain = curve(False)
+    target = plain[-1][2]
+    t_plain = plain[-1][1]
+    guided = curve(True)
+    t_guided, spp_guided = None, None
+    for spp, el, r in guided:
+        if r <= target:
+            t_guided, spp_guided = el, spp
+            break
+    return {"scene": "cornell 64x64, depth 8", "reference": "FP64 oracle, 32768 spp", "target_rmse": target,
+            "target": f"plain RMSE at {target_spp} spp", "plain_seconds": t_plain, "plain_spp": plain[-1][0],
+            "guided_seconds": t_guided, "guided_spp": spp_guided,
+            "guided_speedup": (t_plain / t_guided) if t_guided else None,
+            "plain_curve": plain, "guided_curve": guided[:40]}
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -162,6 +215,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-guided", action="store_true", help="skip the guided-vs-plain time-to-RMSE run")
     ap.add_argument("--spp", type=int, default=SPP)
     ap.add_argument("--out", default=None)
     ap.add_argument("--trace-kernel", type=int, default=0, help="0 one ray per thread with warp fetch, 1 persistent warps refilling lanes")
@@ -264,6 +318,9 @@ def main():
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_value = paths_per_step * world / (statistics.mean(e2e_ms) / 1e3) / 1e6
+    gvp = None
+    if rank == 0 and not args.no_guided:
+        gvp = guided_vs_plain()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_oracle(sd, cam)
@@ -295,6 +352,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "guided_vs_plain": gvp,
             "wall_s": t_wall,
         }
         s = json.dumps(line)

@@ -829,7 +829,11 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         // step the proposal is BSDF-only.
         rt_guide *gd = o.guide;
         const uint32_t batch = guide_batch(gd);
-        if ((rs = ensure_guided(rc, cap, batch)) != RT_OK) return rs;
+        // one iteration set per training batch: the proposal improves every
+        // `batch` paths (2^16 by default)
+        const uint32_t cap_full = cap;
+        cap = std::min(cap, std::max(batch, 32u));
+        if ((rs = ensure_guided(rc, cap_full, batch)) != RT_OK) return rs;
         rc->pool.view.nrec = rc->gnrec;
         Pool gpool = rc->pool.view;
         float3 glo, ghi;
