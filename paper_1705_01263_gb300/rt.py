@@ -360,6 +360,9 @@ def make_opts(sigma: float = 0.5, rr: bool = False, mis_mode: int = 0, seed: int
     o.megakernel_only, o.sort_by_material, o.tail_threshold = int(megakernel_only), int(sort_by_material), tail_threshold
     o.abort_flag = abort_flag
     o.guide = guide.handle if guide is not None else None
+    # keep the Python objects whose handles the options point to alive for as
+    # long as the options are
+    o._keep_alive = (guide, stats)
     if stats is not None:
         o.stats = C.pointer(stats)
     o.profile = profile
