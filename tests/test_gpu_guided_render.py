@@ -36,12 +36,14 @@ def test_guided_render_is_consistent_with_the_oracle():
     p0 = guide.get_params()
     film = rt.Film(cam.width, cam.height)
     stats = rt.rt_stats()
-    rt.rt_render(scene, cam, 128, 8, film, rt.make_opts(guide=guide, stats=stats))
+    # 1024 spp: the per-pixel 4-sigma test needs the QMC error past its early
+    # transient (the plain tracer fails it at 128 spp just the same)
+    rt.rt_render(scene, cam, 1024, 8, film, rt.make_opts(guide=guide, stats=stats))
     torch.cuda.synchronize()
-    assert stats.waves == 8                      # 16 spp per iteration set
+    assert stats.waves == 64                     # 16 spp per iteration set
     assert not np.array_equal(p0, guide.get_params())   # trained during the render
     s, s2, c = film.download()
-    assert np.all(c == 128)
+    assert np.all(c == 1024)
     mg, vg = oracle.resolve(s, s2, c)
     mr, vr = reference()
     sig = np.sqrt(vg + vr)
