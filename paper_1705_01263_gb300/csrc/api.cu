@@ -158,21 +158,22 @@ extern "C" rt_status rt_divide_u64_host(const uint64_t *n, int64_t count, uint32
 /* Host execution of the kernels' traversal routine on a host-only scene
  * (rt_debug_scene_create_host). rays: n x 8 floats (o, d, tmin, tmax). */
 extern "C" rt_status rt_debug_trace_host(const rt_scene *s, const float *rays, int64_t n, int32_t any_hit,
-                                         uint32_t *prim, float *t, float *u, float *v, uint32_t *nodes_visited) {
+                                         uint32_t *prim, float *t, float *u, float *v, uint32_t *nodes_visited,
+                                         uint32_t *inst) {
     if (!s || !s->host_only || n < 0) { set_error("rt_debug_trace_host: needs a host-only scene"); return RT_INVALID_ARG; }
     for (int64_t i = 0; i < n; ++i) {
         const float *r = rays + 8 * i;
         Ray ray{v3(r[0], r[1], r[2]), v3(r[3], r[4], r[5]), r[6], r[7]};
         Hit h;
         h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
-        TraceResult tr = any_hit ? traverse<true>(s->host.nodes, s->host.tris, 0u, ray, h)
-                                 : traverse<false>(s->host.nodes, s->host.tris, 0u, ray, h);
+        TraceResult tr = any_hit ? trace_scene<true>(s->host, ray, h) : trace_scene<false>(s->host, ray, h);
         if (tr.overflow) { set_error("stack overflow"); return RT_STACK_OVERFLOW; }
         prim[i] = h.prim;
         t[i] = h.prim == RT_MISS ? INFINITY : h.t;
         if (u) u[i] = h.b1;
         if (v) v[i] = h.b2;
         if (nodes_visited) nodes_visited[i] = tr.nodes;
+        if (inst) inst[i] = h.inst;
     }
     return RT_OK;
 }
@@ -199,13 +200,13 @@ extern "C" rt_status rt_debug_render_host(const rt_scene *s, const rt_camera *ca
     auto closest = [sc](V3 oo, V3 dd, Hit &h) {
         Ray r{oo, dd, 0.f, INFINITY};
         h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
-        traverse<false>(sc->nodes, sc->tris, 0u, r, h);
+        trace_scene<false>(*sc, r, h);
     };
     auto any = [sc](V3 oo, V3 dd, float tmax) {
         Ray r{oo, dd, 0.f, tmax};
         Hit h;
-        h.prim = RT_MISS; h.t = INFINITY;
-        traverse<true>(sc->nodes, sc->tris, 0u, r, h);
+        h.prim = RT_MISS; h.inst = 0; h.t = INFINITY;
+        trace_scene<true>(*sc, r, h);
         return h.prim != RT_MISS;
     };
     for (int64_t i = 0; i < n; ++i) {

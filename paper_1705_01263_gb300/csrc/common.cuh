@@ -51,7 +51,9 @@ struct DevScene {
     const float4 *tris;        // 3 float4 per leaf triangle (v0.w = prim id bits)
     // two-level scenes: top level over instances, per-mesh bottom levels
     int32_t two_level;
-    const uint4 *tlas_nodes;   // top-level nodes; leaves reference instances
+    uint32_t num_instances;
+    const uint4 *tlas_nodes;   // top-level nodes; leaf slots index tlas_inst
+    const uint32_t *tlas_inst; // top-level leaf slot -> instance id
     const float4 *inst_xf;     // per instance: world->object 3x4 (3 float4) + object->world 3x4 (3 float4)
     const uint32_t *inst_root; // per instance: root node index of its mesh in `nodes`
     // shading data indexed by the original triangle id
@@ -70,6 +72,8 @@ struct DevScene {
     uint32_t num_lights;
     const float2 *alias;       // x = threshold, y = alias index (bits)
     const uint32_t *light_tri; // emitter -> triangle id
+    const uint32_t *light_inst;// emitter -> instance id (two-level scenes)
+    const float4 *light_v;     // emitter -> three world-space vertices
     // environment
     int32_t env_w, env_h, env_levels;
     const float4 *env;         // finest level: rgb + pdf (lum / sum w)

@@ -39,6 +39,7 @@ struct Pool {
     uint2 *index;    // 64-bit QMC index
     uint32_t *pixel;
     float4 *hit;     // prim bits, t, b1, b2
+    uint32_t *hit_inst; // instance of the hit (two-level scenes only)
     float4 *sh_o;    // shadow origin, w = tmax
     float4 *sh_d;
     float4 *sh_c;    // shadow contribution
@@ -108,7 +109,7 @@ struct DevTraceClosest {
     RT_D void operator()(V3 o, V3 d, Hit &h) const {
         Ray r{o, d, 0.f, INFINITY};
         h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
-        TraceResult tr = traverse<false>(sc->nodes, sc->tris, 0u, r, h);
+        TraceResult tr = trace_scene<false>(*sc, r, h);
         if (tr.overflow) *overflow = true;
     }
 };
@@ -119,7 +120,7 @@ struct DevTraceAny {
         Ray r{o, d, 0.f, tmax};
         Hit h;
         h.prim = RT_MISS; h.t = INFINITY;
-        TraceResult tr = traverse<true>(sc->nodes, sc->tris, 0u, r, h);
+        TraceResult tr = trace_scene<true>(*sc, r, h);
         if (tr.overflow) *overflow = true;
         return h.prim != RT_MISS;
     }
@@ -201,7 +202,8 @@ __global__ void __launch_bounds__(128) k_shade(RenderParams P, Pool pool) {
             PathState s = load_state(pool, q);
             float4 hv = pool.hit[q];
             Hit h;
-            h.prim = __float_as_uint(hv.x); h.inst = 0; h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
+            h.prim = __float_as_uint(hv.x); h.inst = P.sc.two_level ? pool.hit_inst[q] : 0u;
+            h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
             ShadowRay sh;
             r = shade(P, s, h, sh);
             pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
@@ -239,11 +241,12 @@ __global__ void __launch_bounds__(128) k_trace_ext_simple(DevScene sc, Pool pool
         float4 o = pool.ray_o[q], d = pool.ray_d[q];
         Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, INFINITY};
         Hit h;
-        h.prim = RT_MISS; h.t = INFINITY; h.b1 = h.b2 = 0.f;
-        TraceResult tr = traverse<false>(sc.nodes, sc.tris, 0u, r, h);
+        h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
+        TraceResult tr = trace_scene<false>(sc, r, h);
         overflow |= tr.overflow;
         if (kCount) { nodes += tr.nodes; tris += tr.tris; }
         pool.hit[q] = make_float4(__uint_as_float(h.prim), h.t, h.b1, h.b2);
+        if (sc.two_level) pool.hit_inst[q] = h.inst;
     }
     if (overflow) atomicOr(&c->overflow, 1u);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&c->ext_rays, (unsigned long long)n);
@@ -269,8 +272,8 @@ __global__ void __launch_bounds__(128) k_trace_shadow_simple(DevScene sc, Pool p
         float4 o = pool.sh_o[q], d = pool.sh_d[q];
         Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, o.w};
         Hit h;
-        h.prim = RT_MISS; h.t = INFINITY;
-        TraceResult tr = traverse<true>(sc.nodes, sc.tris, 0u, r, h);
+        h.prim = RT_MISS; h.inst = 0; h.t = INFINITY;
+        TraceResult tr = trace_scene<true>(sc, r, h);
         overflow |= tr.overflow;
         if (kCount) { nodes += tr.nodes; tris += tr.tris; }
         if (h.prim == RT_MISS) {
@@ -406,7 +409,7 @@ struct UserJob {
     }
     RT_D void store(uint32_t i, const Hit &h) const {
         hits.prim[i] = h.prim;
-        if (hits.inst) hits.inst[i] = 0u;
+        if (hits.inst) hits.inst[i] = h.inst;
         hits.t[i] = h.prim == RT_MISS ? INFINITY : h.t;
         if (hits.u) hits.u[i] = h.b1;
         if (hits.v) hits.v[i] = h.b2;
@@ -416,10 +419,20 @@ struct UserJob {
 template <bool kAny>
 __global__ void __launch_bounds__(128) k_trace_user(DevScene sc, rt_rays rays, uint32_t n, rt_hits hits,
                                                     uint32_t *scratch /* [0] fetch counter, [1] overflow */) {
-    UserJob job{rays, hits};
     bool overflow = false;
-    WorkCount wc;
-    trace_persistent<kAny, false>(sc.nodes, sc.tris, job, n, &scratch[0], overflow, wc);
+    UserJob job{rays, hits};
+    for (;;) {
+        uint32_t base = warp_fetch32(&scratch[0]);
+        if (base >= n) break;
+        uint32_t i = base + lane_id();
+        if (i >= n) continue;
+        Ray r = job.load(i);
+        Hit h;
+        h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
+        TraceResult tr = trace_scene<kAny>(sc, r, h);
+        overflow |= tr.overflow;
+        job.store(i, h);
+    }
     if (overflow) atomicOr(&scratch[1], 1u);
 }
 
@@ -455,7 +468,8 @@ __global__ void k_guide_features(RenderParams P, Pool pool, float *feat, float3 
         PathState s = load_state(pool, q);
         float4 hv = pool.hit[q];
         Hit h;
-        h.prim = __float_as_uint(hv.x); h.inst = 0; h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
+        h.prim = __float_as_uint(hv.x); h.inst = P.sc.two_level ? pool.hit_inst[q] : 0u;
+        h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
         float f[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (h.prim != RT_MISS && s.depth <= P.max_depth) {
             Vertex vx;
@@ -496,7 +510,8 @@ __global__ void __launch_bounds__(128) k_shade_guided(RenderParams P, Pool pool,
             }
             float4 hv = pool.hit[q];
             Hit h;
-            h.prim = __float_as_uint(hv.x); h.inst = 0; h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
+            h.prim = __float_as_uint(hv.x); h.inst = P.sc.two_level ? pool.hit_inst[q] : 0u;
+            h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
             ShadowRay sh;
             GuideRecord gr;
             const uint32_t v = s.depth;
@@ -605,7 +620,7 @@ rt_status ensure_pool(PoolAlloc &pa, uint32_t capacity) {
     if (pa.block) { cudaFree(pa.block); pa.block = nullptr; }
     size_t P = capacity;
     size_t f4 = P * sizeof(float4);
-    size_t bytes = 8 * f4 + P * sizeof(uint2) + P * 4 /*pixel*/ + 3 * P * 4 /*queues*/ + 64 * 256;
+    size_t bytes = 8 * f4 + P * sizeof(uint2) + P * 4 /*pixel*/ + P * 4 /*hit_inst*/ + 3 * P * 4 /*queues*/ + 64 * 256;
     cudaError_t e = cudaMalloc(&pa.block, bytes);
     if (e != cudaSuccess) { set_error("path-state pool allocation failed"); return RT_OOM; }
     char *p = (char *)pa.block;
@@ -616,6 +631,7 @@ rt_status ensure_pool(PoolAlloc &pa, uint32_t capacity) {
     v.hit = (float4 *)take(f4); v.sh_o = (float4 *)take(f4); v.sh_d = (float4 *)take(f4); v.sh_c = (float4 *)take(f4);
     v.index = (uint2 *)take(P * sizeof(uint2));
     v.pixel = (uint32_t *)take(P * 4);
+    v.hit_inst = (uint32_t *)take(P * 4);
     v.q[0] = (uint32_t *)take(P * 4); v.q[1] = (uint32_t *)take(P * 4); v.qs = (uint32_t *)take(P * 4);
     v.capacity = capacity;
     pa.capacity = capacity;
@@ -691,11 +707,11 @@ extern "C" rt_status rt_trace(const rt_scene *s, const rt_rays *rays, int64_t n,
     RT_CUDA_TRY(cudaMemsetAsync(scratch[dev], 0, 2 * sizeof(uint32_t), st));
     const int gb = 128;
     if (any_hit) {
-        int g = grid_persistent(k_trace_user<true>, gb, stack_smem(gb));
-        k_trace_user<true><<<g, gb, stack_smem(gb), st>>>(s->dev, *rays, (uint32_t)n, *hits, scratch[dev]);
+        int g = grid_persistent(k_trace_user<true>, gb, 0);
+        k_trace_user<true><<<g, gb, 0, st>>>(s->dev, *rays, (uint32_t)n, *hits, scratch[dev]);
     } else {
-        int g = grid_persistent(k_trace_user<false>, gb, stack_smem(gb));
-        k_trace_user<false><<<g, gb, stack_smem(gb), st>>>(s->dev, *rays, (uint32_t)n, *hits, scratch[dev]);
+        int g = grid_persistent(k_trace_user<false>, gb, 0);
+        k_trace_user<false><<<g, gb, 0, st>>>(s->dev, *rays, (uint32_t)n, *hits, scratch[dev]);
     }
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
@@ -786,6 +802,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     rt_render_opts o{};
     if (opts_in) o = *opts_in;
     if (spp == 0) return RT_OK;
+    if (s->dev.two_level) o.trace_kernel = 0;   // the persistent variant is single-level only
     cudaStream_t st = (cudaStream_t)stream;
     RenderCache *rc = cache_of(film);
     const uint32_t W = cam->width, H = cam->height;
@@ -1081,7 +1098,8 @@ constexpr size_t kStaticF4Bytes = align_up(sizeof(float4) * kStaticMaxPaths);
 constexpr size_t kStaticIndex = kStaticF4 + 8 * kStaticF4Bytes;
 constexpr size_t kStaticU32Bytes = align_up(sizeof(uint32_t) * kStaticMaxPaths);
 constexpr size_t kStaticPixel = kStaticIndex + align_up(sizeof(uint2) * kStaticMaxPaths);
-constexpr size_t kStaticQueues = kStaticPixel + kStaticU32Bytes;
+constexpr size_t kStaticHitInst = kStaticPixel + kStaticU32Bytes;
+constexpr size_t kStaticQueues = kStaticHitInst + kStaticU32Bytes;
 constexpr size_t kStaticBytes = kStaticQueues + 3 * kStaticU32Bytes;   // about 9.6 MB
 
 static __device__ __align__(256) unsigned char g_static_arena[kStaticBytes];
@@ -1125,6 +1143,7 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
         return RT_INVALID_ARG;
     }
     if (spp == 0) return RT_OK;
+    if (s->dev.two_level) o.trace_kernel = 0;   // the persistent variant is single-level only
     unsigned char *base = nullptr;
     rt_status rs = static_arena(&base);
     if (rs != RT_OK) return rs;
@@ -1137,6 +1156,7 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
     pool.hit = f4[4]; pool.sh_o = f4[5]; pool.sh_d = f4[6]; pool.sh_c = f4[7];
     pool.index = (uint2 *)(base + kStaticIndex);
     pool.pixel = (uint32_t *)(base + kStaticPixel);
+    pool.hit_inst = (uint32_t *)(base + kStaticHitInst);
     pool.q[0] = (uint32_t *)(base + kStaticQueues);
     pool.q[1] = (uint32_t *)(base + kStaticQueues + kStaticU32Bytes);
     pool.qs = (uint32_t *)(base + kStaticQueues + 2 * kStaticU32Bytes);

@@ -122,8 +122,24 @@ rt_status rtg::scene_create(const rt_scene_desc *d, rt_scene **out, bool host_on
         return RT_INVALID_ARG;
     }
     if (d->num_instances > 0) {
-        set_error("rt_scene_create: instanced scenes are not supported by this build");
-        return RT_NOT_SUPPORTED;
+        if (d->num_meshes <= 0 || !d->mesh_tri_offset || !d->instance_mesh || !d->instance_xform) {
+            set_error("rt_scene_create: instancing needs meshes, instance_mesh and instance_xform");
+            return RT_INVALID_ARG;
+        }
+        for (int32_t m = 0; m < d->num_meshes; ++m)
+            if (d->mesh_tri_offset[m] < 0 || d->mesh_tri_offset[m] > d->mesh_tri_offset[m + 1] ||
+                d->mesh_tri_offset[m + 1] > d->num_triangles) {
+                set_error("rt_scene_create: mesh_tri_offset must be non-decreasing within [0, num_triangles]");
+                return RT_INVALID_ARG;
+            }
+        for (int32_t k = 0; k < d->num_instances; ++k) {
+            if ((int32_t)d->instance_mesh[k] >= d->num_meshes) { set_error("rt_scene_create: instance_mesh out of range"); return RT_INVALID_ARG; }
+            const float *X = d->instance_xform + 12 * (size_t)k;
+            double det = (double)X[0] * ((double)X[5] * X[10] - (double)X[6] * X[9]) -
+                         (double)X[1] * ((double)X[4] * X[10] - (double)X[6] * X[8]) +
+                         (double)X[2] * ((double)X[4] * X[9] - (double)X[5] * X[8]);
+            if (!std::isfinite(det) || std::fabs(det) < 1e-30) { set_error("rt_scene_create: singular instance transform"); return RT_INVALID_ARG; }
+        }
     }
     if (d->num_materials <= 0 || !d->albedo || !d->roughness || !d->ggx_weight || !d->emission) {
         set_error("rt_scene_create: material arrays missing");
@@ -158,17 +174,107 @@ rt_status rtg::scene_create(const rt_scene_desc *d, rt_scene **out, bool host_on
     DevScene &D = s->dev, &Hs = s->host;
     s->num_triangles = T;
 
-    // ---- BVH
-    Bvh8 bvh;
-    build_bvh8(d->vertices, d->indices, nullptr, T, bvh);
-    s->num_nodes = bvh.num_nodes();
-    s->num_leaf_tris = bvh.num_tris();
-    s->bvh_depth = bvh.depth;
+    // ---- BVH: one level, or per-mesh bottom levels + a top level over instances
     rt_status st;
-    if ((st = upload(s, (const uint4 *)bvh.nodes.data(), bvh.nodes.size() / 4, &D.nodes, &Hs.nodes)) != RT_OK) return fail(st);
-    if ((st = upload(s, (const float4 *)bvh.tris.data(), bvh.tris.size() / 4, &D.tris, &Hs.tris)) != RT_OK) return fail(st);
-    D.bb_lo = Hs.bb_lo = make_float3(bvh.lo[0], bvh.lo[1], bvh.lo[2]);
-    D.bb_hi = Hs.bb_hi = make_float3(bvh.hi[0], bvh.hi[1], bvh.hi[2]);
+    std::vector<double> o2w, w2o;   // 12 doubles per instance
+    if (d->num_instances > 0) {
+        const int32_t M = d->num_meshes, I = d->num_instances;
+        std::vector<uint32_t> nodes_all;
+        std::vector<float> tris_all;
+        std::vector<uint32_t> mesh_root(M);
+        std::vector<float> mlo(3 * M), mhi(3 * M);
+        int depth = 0;
+        for (int32_t m = 0; m < M; ++m) {
+            int64_t t0 = d->mesh_tri_offset[m], t1 = d->mesh_tri_offset[m + 1];
+            std::vector<uint32_t> ids((size_t)(t1 - t0));
+            for (int64_t t = t0; t < t1; ++t) ids[(size_t)(t - t0)] = (uint32_t)t;
+            Bvh8 b;
+            build_bvh8(d->vertices, d->indices, ids.data(), t1 - t0, b);
+            const uint32_t noff = (uint32_t)(nodes_all.size() / 20), toff = (uint32_t)(tris_all.size() / 12);
+            for (size_t i = 0; i < b.nodes.size(); i += 20) {
+                uint32_t nd[20];
+                std::memcpy(nd, &b.nodes[i], sizeof nd);
+                nd[4] += noff;
+                nd[5] += toff;
+                nodes_all.insert(nodes_all.end(), nd, nd + 20);
+            }
+            tris_all.insert(tris_all.end(), b.tris.begin(), b.tris.end());
+            mesh_root[m] = noff;
+            for (int a = 0; a < 3; ++a) { mlo[3 * m + a] = b.lo[a]; mhi[3 * m + a] = b.hi[a]; }
+            depth = std::max(depth, b.depth);
+        }
+        o2w.resize(12 * (size_t)I);
+        w2o.resize(12 * (size_t)I);
+        std::vector<float> ilo(3 * (size_t)I), ihi(3 * (size_t)I);
+        std::vector<uint32_t> iroot(I);
+        float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int32_t k = 0; k < I; ++k) {
+            const float *X = d->instance_xform + 12 * (size_t)k;
+            double *A = &o2w[12 * (size_t)k], *B = &w2o[12 * (size_t)k];
+            for (int i = 0; i < 12; ++i) A[i] = X[i];
+            // inverse of the affine map [R | t]: [R^-1 | -R^-1 t]
+            double r00 = A[0], r01 = A[1], r02 = A[2], r10 = A[4], r11 = A[5], r12 = A[6], r20 = A[8], r21 = A[9], r22 = A[10];
+            double det = r00 * (r11 * r22 - r12 * r21) - r01 * (r10 * r22 - r12 * r20) + r02 * (r10 * r21 - r11 * r20);
+            double inv[9] = {(r11 * r22 - r12 * r21) / det, (r02 * r21 - r01 * r22) / det, (r01 * r12 - r02 * r11) / det,
+                             (r12 * r20 - r10 * r22) / det, (r00 * r22 - r02 * r20) / det, (r02 * r10 - r00 * r12) / det,
+                             (r10 * r21 - r11 * r20) / det, (r01 * r20 - r00 * r21) / det, (r00 * r11 - r01 * r10) / det};
+            for (int i = 0; i < 3; ++i) {
+                for (int j = 0; j < 3; ++j) B[4 * i + j] = inv[3 * i + j];
+                B[4 * i + 3] = -(inv[3 * i] * A[3] + inv[3 * i + 1] * A[7] + inv[3 * i + 2] * A[11]);
+            }
+            uint32_t m = d->instance_mesh[k];
+            iroot[k] = mesh_root[m];
+            double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            for (int c = 0; c < 8; ++c) {
+                double p[3] = {(c & 1) ? mhi[3 * m] : mlo[3 * m], (c & 2) ? mhi[3 * m + 1] : mlo[3 * m + 1],
+                               (c & 4) ? mhi[3 * m + 2] : mlo[3 * m + 2]};
+                for (int a = 0; a < 3; ++a) {
+                    double w = A[4 * a] * p[0] + A[4 * a + 1] * p[1] + A[4 * a + 2] * p[2] + A[4 * a + 3];
+                    lo[a] = std::min(lo[a], w);
+                    hi[a] = std::max(hi[a], w);
+                }
+            }
+            for (int a = 0; a < 3; ++a) {
+                double pad = 1e-6 * (std::fabs(lo[a]) + std::fabs(hi[a]) + 1e-3);
+                ilo[3 * (size_t)k + a] = std::nextafter((float)(lo[a] - pad), -INFINITY);
+                ihi[3 * (size_t)k + a] = std::nextafter((float)(hi[a] + pad), INFINITY);
+                blo[a] = std::min(blo[a], ilo[3 * (size_t)k + a]);
+                bhi[a] = std::max(bhi[a], ihi[3 * (size_t)k + a]);
+            }
+        }
+        Bvh8 tl;
+        build_bvh8_boxes(ilo.data(), ihi.data(), I, tl);
+        s->num_nodes = (int64_t)nodes_all.size() / 20 + tl.num_nodes();
+        s->num_leaf_tris = (int64_t)tris_all.size() / 12;
+        s->bvh_depth = depth + tl.depth;
+        if ((st = upload(s, (const uint4 *)nodes_all.data(), nodes_all.size() / 4, &D.nodes, &Hs.nodes)) != RT_OK) return fail(st);
+        if ((st = upload(s, (const float4 *)tris_all.data(), tris_all.size() / 4, &D.tris, &Hs.tris)) != RT_OK) return fail(st);
+        if ((st = upload(s, (const uint4 *)tl.nodes.data(), tl.nodes.size() / 4, &D.tlas_nodes, &Hs.tlas_nodes)) != RT_OK) return fail(st);
+        if ((st = upload(s, tl.tri_ids.data(), tl.tri_ids.size(), &D.tlas_inst, &Hs.tlas_inst)) != RT_OK) return fail(st);
+        std::vector<float4> xf(6 * (size_t)I);
+        for (int32_t k = 0; k < I; ++k)
+            for (int r = 0; r < 3; ++r) {
+                const double *B = &w2o[12 * (size_t)k + 4 * r], *A = &o2w[12 * (size_t)k + 4 * r];
+                xf[6 * (size_t)k + r] = make_float4((float)B[0], (float)B[1], (float)B[2], (float)B[3]);
+                xf[6 * (size_t)k + 3 + r] = make_float4((float)A[0], (float)A[1], (float)A[2], (float)A[3]);
+            }
+        if ((st = upload(s, xf.data(), xf.size(), &D.inst_xf, &Hs.inst_xf)) != RT_OK) return fail(st);
+        if ((st = upload(s, iroot.data(), iroot.size(), &D.inst_root, &Hs.inst_root)) != RT_OK) return fail(st);
+        D.two_level = Hs.two_level = 1;
+        D.num_instances = Hs.num_instances = (uint32_t)I;
+        D.bb_lo = Hs.bb_lo = make_float3(blo[0], blo[1], blo[2]);
+        D.bb_hi = Hs.bb_hi = make_float3(bhi[0], bhi[1], bhi[2]);
+    } else {
+        Bvh8 bvh;
+        build_bvh8(d->vertices, d->indices, nullptr, T, bvh);
+        s->num_nodes = bvh.num_nodes();
+        s->num_leaf_tris = bvh.num_tris();
+        s->bvh_depth = bvh.depth;
+        if ((st = upload(s, (const uint4 *)bvh.nodes.data(), bvh.nodes.size() / 4, &D.nodes, &Hs.nodes)) != RT_OK) return fail(st);
+        if ((st = upload(s, (const float4 *)bvh.tris.data(), bvh.tris.size() / 4, &D.tris, &Hs.tris)) != RT_OK) return fail(st);
+        D.bb_lo = Hs.bb_lo = make_float3(bvh.lo[0], bvh.lo[1], bvh.lo[2]);
+        D.bb_hi = Hs.bb_hi = make_float3(bvh.hi[0], bvh.hi[1], bvh.hi[2]);
+    }
 
     // ---- shading arrays
     if ((st = upload(s, d->vertices, (size_t)V * 3, &D.vertices, &Hs.vertices)) != RT_OK) return fail(st);
@@ -238,25 +344,51 @@ rt_status rtg::scene_create(const rt_scene_desc *d, rt_scene **out, bool host_on
         if ((st = upload(s, off.data(), off.size(), &D.env_off, &Hs.env_off)) != RT_OK) return fail(st);
     }
 
-    // ---- emitters: flux per triangle, alias table, per-triangle area pdf
-    std::vector<double> flux;
-    std::vector<uint32_t> light_tri;
-    std::vector<double> area(T);
+    // ---- emitters: mean luminance per triangle; one emitter per emissive
+    // (instance, triangle) with its world-space vertices, flux = mean
+    // luminance x world area, alias table over the fluxes; the solid-angle
+    // pdf of a hit emitter needs only (1 - p_env) * mean luminance / sum(flux)
+    std::vector<double> lum_avg((size_t)std::max<int64_t>(T, 1), 0.0);
     for (int64_t t = 0; t < T; ++t) {
-        const float *p0 = d->vertices + 3 * (size_t)d->indices[3 * t], *p1 = d->vertices + 3 * (size_t)d->indices[3 * t + 1],
-                    *p2 = d->vertices + 3 * (size_t)d->indices[3 * t + 2];
-        double e1[3] = {(double)p1[0] - p0[0], (double)p1[1] - p0[1], (double)p1[2] - p0[2]};
-        double e2[3] = {(double)p2[0] - p0[0], (double)p2[1] - p0[1], (double)p2[2] - p0[2]};
-        double c[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-        area[t] = 0.5 * std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
         uint32_t m = d->tri_material[t];
         double L = lum3(d->emission + 3 * m);
-        if (!(L > 0.0) || !(area[t] > 0.0)) continue;
+        if (!(L > 0.0)) continue;
         int32_t tex = d->emission_tex ? d->emission_tex[m] : -1;
         if (tex >= 0) L *= textured_mean(d, t, tex);
-        if (!(L > 0.0)) continue;
-        flux.push_back(L * area[t]);
+        lum_avg[t] = L > 0.0 ? L : 0.0;
+    }
+    std::vector<double> flux;
+    std::vector<uint32_t> light_tri, light_inst;
+    std::vector<float4> light_v;
+    auto add_light = [&](uint32_t inst, int64_t t, const double *X /* o2w or null */) {
+        double p[3][3];
+        for (int k = 0; k < 3; ++k) {
+            const float *v = d->vertices + 3 * (size_t)d->indices[3 * t + k];
+            for (int a = 0; a < 3; ++a)
+                p[k][a] = X ? X[4 * a] * v[0] + X[4 * a + 1] * v[1] + X[4 * a + 2] * v[2] + X[4 * a + 3] : (double)v[a];
+        }
+        float pf[3][3];
+        for (int k = 0; k < 3; ++k)
+            for (int a = 0; a < 3; ++a) pf[k][a] = (float)p[k][a];
+        double e1[3] = {(double)pf[1][0] - pf[0][0], (double)pf[1][1] - pf[0][1], (double)pf[1][2] - pf[0][2]};
+        double e2[3] = {(double)pf[2][0] - pf[0][0], (double)pf[2][1] - pf[0][1], (double)pf[2][2] - pf[0][2]};
+        double c[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double area = 0.5 * std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        if (!(area > 0.0)) return;
+        flux.push_back(lum_avg[t] * area);
         light_tri.push_back((uint32_t)t);
+        light_inst.push_back(inst);
+        for (int k = 0; k < 3; ++k) light_v.push_back(make_float4(pf[k][0], pf[k][1], pf[k][2], 0.f));
+    };
+    if (d->num_instances > 0) {
+        for (int32_t k = 0; k < d->num_instances; ++k) {
+            uint32_t m = d->instance_mesh[k];
+            for (int64_t t = d->mesh_tri_offset[m]; t < d->mesh_tri_offset[m + 1]; ++t)
+                if (lum_avg[t] > 0.0) add_light((uint32_t)k, t, &o2w[12 * (size_t)k]);
+        }
+    } else {
+        for (int64_t t = 0; t < T; ++t)
+            if (lum_avg[t] > 0.0) add_light(0u, t, nullptr);
     }
     double flux_sum = 0.0;
     for (double f : flux) flux_sum += f;
@@ -264,8 +396,9 @@ rt_status rtg::scene_create(const rt_scene_desc *d, rt_scene **out, bool host_on
     const float p_env = has_env ? (flux.empty() ? 1.f : 0.5f) : 0.f;
     D.p_env = Hs.p_env = p_env;
     std::vector<float> lpa((size_t)std::max<int64_t>(T, 1), 0.f);
-    for (size_t i = 0; i < flux.size(); ++i)
-        lpa[light_tri[i]] = (float)((1.0 - p_env) * (flux[i] / flux_sum) / area[light_tri[i]]);
+    if (!flux.empty())
+        for (int64_t t = 0; t < T; ++t)
+            if (lum_avg[t] > 0.0) lpa[t] = (float)((1.0 - p_env) * lum_avg[t] / flux_sum);
     if ((st = upload(s, lpa.data(), (size_t)T, &D.tri_light_pdf_area, &Hs.tri_light_pdf_area)) != RT_OK) return fail(st);
     if (!flux.empty()) {
         std::vector<float2> alias;
@@ -273,6 +406,8 @@ rt_status rtg::scene_create(const rt_scene_desc *d, rt_scene **out, bool host_on
         D.num_lights = Hs.num_lights = (uint32_t)flux.size();
         if ((st = upload(s, alias.data(), alias.size(), &D.alias, &Hs.alias)) != RT_OK) return fail(st);
         if ((st = upload(s, light_tri.data(), light_tri.size(), &D.light_tri, &Hs.light_tri)) != RT_OK) return fail(st);
+        if ((st = upload(s, light_inst.data(), light_inst.size(), &D.light_inst, &Hs.light_inst)) != RT_OK) return fail(st);
+        if ((st = upload(s, light_v.data(), light_v.size(), &D.light_v, &Hs.light_v)) != RT_OK) return fail(st);
     }
     *out = s;
     return RT_OK;

@@ -231,10 +231,25 @@ RT_HD float mis_weight(int mode, float pa, float pb) {
     return a / (a + b);
 }
 
-RT_HD V3 tri_vertex(const DevScene &sc, uint32_t prim, int k) {
+// Instance transforms (rows 0..2 world->object, rows 3..5 object->world).
+RT_HD V3 xf_point(const float4 *xf, uint32_t inst, V3 p) {
+    const float4 a = ldg(xf + 6 * (size_t)inst + 3), b = ldg(xf + 6 * (size_t)inst + 4), c = ldg(xf + 6 * (size_t)inst + 5);
+    return v3(a.x * p.x + a.y * p.y + a.z * p.z + a.w, b.x * p.x + b.y * p.y + b.z * p.z + b.w,
+              c.x * p.x + c.y * p.y + c.z * p.z + c.w);
+}
+// Normals map with the inverse transpose of object->world, i.e. the
+// transpose of the world->object linear part.
+RT_HD V3 xf_normal(const float4 *xf, uint32_t inst, V3 n) {
+    const float4 a = ldg(xf + 6 * (size_t)inst), b = ldg(xf + 6 * (size_t)inst + 1), c = ldg(xf + 6 * (size_t)inst + 2);
+    return v3(a.x * n.x + b.x * n.y + c.x * n.z, a.y * n.x + b.y * n.y + c.y * n.z, a.z * n.x + b.z * n.y + c.z * n.z);
+}
+
+// World-space vertex k of triangle prim (of instance inst in two-level scenes).
+RT_HD V3 tri_vertex(const DevScene &sc, uint32_t inst, uint32_t prim, int k) {
     uint32_t vi = ldg(sc.indices + 3 * (size_t)prim + k);
     const float *v = sc.vertices + 3 * (size_t)vi;
-    return v3(ldg(v), ldg(v + 1), ldg(v + 2));
+    V3 p = v3(ldg(v), ldg(v + 1), ldg(v + 2));
+    return sc.two_level ? xf_point(sc.inst_xf, inst, p) : p;
 }
 
 RT_HD V3 tri_emission(const DevScene &sc, uint32_t prim, float b1, float b2) {
@@ -335,7 +350,7 @@ struct Vertex {
 
 RT_HD void setup_vertex(const DevScene &sc, const PathState &s, const Hit &h, Vertex &vx) {
     const uint32_t prim = h.prim;
-    V3 v0 = tri_vertex(sc, prim, 0), v1 = tri_vertex(sc, prim, 1), v2 = tri_vertex(sc, prim, 2);
+    V3 v0 = tri_vertex(sc, h.inst, prim, 0), v1 = tri_vertex(sc, h.inst, prim, 1), v2 = tri_vertex(sc, h.inst, prim, 2);
     float b0 = 1.f - h.b1 - h.b2;
     vx.x = b0 * v0 + h.b1 * v1 + h.b2 * v2;
     V3 ng = normalize(cross(v1 - v0, v2 - v0));
@@ -348,8 +363,10 @@ RT_HD void setup_vertex(const DevScene &sc, const PathState &s, const Hit &h, Ve
                  i2 = ldg(sc.indices + 3 * (size_t)prim + 2);
         const float *n0 = sc.normals + 3 * (size_t)i0, *n1 = sc.normals + 3 * (size_t)i1,
                     *n2 = sc.normals + 3 * (size_t)i2;
-        ns = normalize(b0 * v3(ldg(n0), ldg(n0 + 1), ldg(n0 + 2)) + h.b1 * v3(ldg(n1), ldg(n1 + 1), ldg(n1 + 2)) +
-                       h.b2 * v3(ldg(n2), ldg(n2 + 1), ldg(n2 + 2)));
+        ns = b0 * v3(ldg(n0), ldg(n0 + 1), ldg(n0 + 2)) + h.b1 * v3(ldg(n1), ldg(n1 + 1), ldg(n1 + 2)) +
+             h.b2 * v3(ldg(n2), ldg(n2 + 1), ldg(n2 + 2));
+        if (sc.two_level) ns = xf_normal(sc.inst_xf, h.inst, ns);
+        ns = normalize(ns);
         if (dot(ns, ng) < 0.f) ns = -ns;
     }
     vx.ng = ng;
@@ -435,7 +452,8 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
             float2 al = ldg(sc.alias + bin);
             uint32_t li = frac < al.x ? bin : as_uint(al.y);
             uint32_t lt = ldg(sc.light_tri + li);
-            V3 l0 = tri_vertex(sc, lt, 0), l1 = tri_vertex(sc, lt, 1), l2 = tri_vertex(sc, lt, 2);
+            const float4 *LV = sc.light_v + 3 * (size_t)li;
+            V3 l0 = f4xyz(ldg(LV)), l1 = f4xyz(ldg(LV + 1)), l2 = f4xyz(ldg(LV + 2));
             float sq = sqrtf(ua);
             float lb1 = sq * (1.f - ub), lb2 = sq * ub;
             V3 y = (1.f - sq) * l0 + lb1 * l1 + lb2 * l2;

@@ -247,7 +247,8 @@ struct TraceResult {
 // On return hit.prim == RT_MISS if nothing was found; hit.t, b1, b2 valid
 // otherwise. `hit` may hold a previous best (used for two-level scenes).
 template <bool kAnyHit>
-RT_HD TraceResult traverse(const uint4 *nodes, const float4 *tris, uint32_t root, const Ray &ray, Hit &hit) {
+RT_HD TraceResult traverse(const uint4 *nodes, const float4 *tris, uint32_t root, const Ray &ray, Hit &hit,
+                           uint32_t inst = 0u) {
     TraceResult res{false, 0u, 0u};
     RayPre rp = prepare(ray);
     float tbest = hit.prim == RT_MISS ? ray.tmax : hit.t;
@@ -288,11 +289,12 @@ RT_HD TraceResult traverse(const uint4 *nodes, const float4 *tris, uint32_t root
             if (intersect_tri(rp, f4xyz(a), f4xyz(b), f4xyz(c), ray.tmin, ray.tmax, tbest, t, u, v)) {
                 uint32_t prim = as_uint(a.w);
                 if (kAnyHit) {
-                    hit.prim = prim; hit.t = t; hit.b1 = u; hit.b2 = v;
+                    hit.prim = prim; hit.inst = inst; hit.t = t; hit.b1 = u; hit.b2 = v;
                     return res;
                 }
-                if (t < tbest || hit.prim == RT_MISS || prim < hit.prim) {
-                    hit.prim = prim; hit.t = t; hit.b1 = u; hit.b2 = v;
+                // equal t: the lower (instance, primitive) wins
+                if (t < tbest || hit.prim == RT_MISS || inst < hit.inst || (inst == hit.inst && prim < hit.prim)) {
+                    hit.prim = prim; hit.inst = inst; hit.t = t; hit.b1 = u; hit.b2 = v;
                     tbest = t;
                 }
             }
@@ -303,6 +305,81 @@ RT_HD TraceResult traverse(const uint4 *nodes, const float4 *tris, uint32_t root
         }
     }
     return res;
+}
+
+// Ray in the object space of instance `inst`: rows 0..2 of inst_xf hold the
+// world->object affine map. The direction is not renormalised, so t is the
+// same in both spaces.
+RT_HD Ray to_object(const float4 *xf, uint32_t inst, const Ray &r) {
+    const float4 a = ldg(xf + 6 * (size_t)inst), b = ldg(xf + 6 * (size_t)inst + 1), c = ldg(xf + 6 * (size_t)inst + 2);
+    Ray o;
+    o.o = v3(a.x * r.o.x + a.y * r.o.y + a.z * r.o.z + a.w, b.x * r.o.x + b.y * r.o.y + b.z * r.o.z + b.w,
+             c.x * r.o.x + c.y * r.o.y + c.z * r.o.z + c.w);
+    o.d = v3(a.x * r.d.x + a.y * r.d.y + a.z * r.d.z, b.x * r.d.x + b.y * r.d.y + b.z * r.d.z,
+             c.x * r.d.x + c.y * r.d.y + c.z * r.d.z);
+    o.tmin = r.tmin;
+    o.tmax = r.tmax;
+    return o;
+}
+
+// Two-level traversal: the top-level BVH8 over instance boxes; a leaf slot
+// is an instance, whose mesh BVH8 is traversed with the ray mapped to object
+// space and the best hit so far.
+template <bool kAnyHit>
+RT_HD TraceResult traverse_tlas(const DevScene &sc, const Ray &ray, Hit &hit) {
+    TraceResult res{false, 0u, 0u};
+    RayPre rp = prepare(ray);
+    uint2 stack[kStackSize];
+    int sp = 0;
+    uint2 ng = make_uint2(0u, (1u << (24 + (0u ^ rp.oct))) | 1u);
+    for (;;) {
+        uint32_t ibase = 0, imask = 0;
+        if (ng.y & 0xFF000000u) {
+            int bit = 31 - clz32(ng.y);
+            uint32_t slot = ((uint32_t)bit - 24u) ^ rp.oct;
+            uint32_t rel = popc32((ng.y & 0xFFu) & ((1u << slot) - 1u));
+            uint32_t child = ng.x + rel;
+            ng.y &= ~(1u << bit);
+            if (ng.y & 0xFF000000u) {
+                if (sp == kStackSize) { res.overflow = true; break; }
+                stack[sp++] = ng;
+            }
+            const uint4 *N = sc.tlas_nodes + 5 * (size_t)child;
+            uint4 n0 = ldg(N), n1 = ldg(N + 1), n2 = ldg(N + 2), n3 = ldg(N + 3), n4 = ldg(N + 4);
+            ++res.nodes;
+            uint32_t tb;
+            float tcur = hit.prim == RT_MISS ? ray.tmax : hit.t;
+            uint32_t inner = intersect_children(rp, n0, n1, n2, n3, n4, ray.tmin, tcur, tb);
+            ng = make_uint2(n1.x, inner | (n0.w >> 24));
+            ibase = n1.y;
+            imask = tb;
+        } else {
+            ng.y = 0u;
+        }
+        while (imask) {
+            int k = ffs32(imask) - 1;
+            imask &= imask - 1u;
+            uint32_t inst = ldg(sc.tlas_inst + ibase + (uint32_t)k);
+            Ray ro = to_object(sc.inst_xf, inst, ray);
+            TraceResult r2 = traverse<kAnyHit>(sc.nodes, sc.tris, ldg(sc.inst_root + inst), ro, hit, inst);
+            res.nodes += r2.nodes;
+            res.tris += r2.tris;
+            res.overflow |= r2.overflow;
+            if (kAnyHit && hit.prim != RT_MISS) return res;
+        }
+        if (!(ng.y & 0xFF000000u)) {
+            if (sp == 0) break;
+            ng = stack[--sp];
+        }
+    }
+    return res;
+}
+
+// Closest (or any) hit against the scene, one level or two.
+template <bool kAnyHit>
+RT_HD TraceResult trace_scene(const DevScene &sc, const Ray &ray, Hit &hit) {
+    if (sc.two_level) return traverse_tlas<kAnyHit>(sc, ray, hit);
+    return traverse<kAnyHit>(sc.nodes, sc.tris, 0u, ray, hit);
 }
 
 }  // namespace rtg

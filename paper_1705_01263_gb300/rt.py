@@ -125,7 +125,7 @@ def _declare(L):
         "rt_halton": [u32, u32, u64, vp, i64, i32, vp, vp],
         "rt_divide_u64_host": [vp, i64, u32, vp],
         "rt_gemm_bf16": [vp, vp, vp, i32, i32, i32, i32, i32, i32, i32, vp],
-        "rt_debug_trace_host": [vp, vp, i64, i32, vp, vp, vp, vp, vp],
+        "rt_debug_trace_host": [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp],
         "rt_debug_render_host": [vp, C.POINTER(rt_camera), u32, C.POINTER(rt_render_opts), vp, vp, vp, i64, vp],
         "rt_debug_halton_host": [u32, u32, u64, vp, i64, i32, vp],
         "rt_debug_sample_index_host": [u32, u32, u32, u32, u32, C.POINTER(u64)],
@@ -494,14 +494,17 @@ class Guide:
 
 
 # -------------------------------------------------- host test hooks (CPU)
-def debug_trace_host(scene: Scene, rays: np.ndarray, any_hit: bool = False):
+def debug_trace_host(scene: Scene, rays: np.ndarray, any_hit: bool = False, return_inst: bool = False):
     r = np.ascontiguousarray(rays, np.float32)
     n = r.shape[0]
     prim = np.zeros(n, np.uint32)
     t, u, v = np.zeros(n, np.float32), np.zeros(n, np.float32), np.zeros(n, np.float32)
     nodes = np.zeros(n, np.uint32)
+    inst = np.zeros(n, np.uint32)
     check(lib().rt_debug_trace_host(scene.handle, r.ctypes.data, n, int(any_hit), prim.ctypes.data, t.ctypes.data,
-                                    u.ctypes.data, v.ctypes.data, nodes.ctypes.data))
+                                    u.ctypes.data, v.ctypes.data, nodes.ctypes.data, inst.ctypes.data))
+    if return_inst:
+        return prim, t, u, v, nodes, inst
     return prim, t, u, v, nodes
 
 

@@ -443,7 +443,8 @@ def instanced_field(seed: int = BASE_SEED + 3, n_meshes: int = 100, n_instances:
     """1000 instances of 100 unique seeded meshes whose sizes are log-uniform
     in [1k, 50k] triangles, rescaled so that the instanced total is
     `total_tris`; `n_emissive` instanced emitter triangles carry one of 16
-    64 x 64 lognormal(0, 1) RGB textures. No environment."""
+    64 x 64 lognormal(0, 1) RGB textures (emission scale 20). No
+    environment."""
     rng = Rng(seed)
     b = _Builder()
     sizes = np.exp(rng.uniform(n_meshes, math.log(min_tris), math.log(max_tris)))
@@ -455,7 +456,7 @@ def instanced_field(seed: int = BASE_SEED + 3, n_meshes: int = 100, n_instances:
     emissive_mesh = set(range(0, n_meshes, 4))
     em_mats = []
     for t in range(n_textures):
-        em_mats.append(b.material((0.5, 0.5, 0.5), 0.5, 0.0, (1.0, 1.0, 1.0), tex=t))
+        em_mats.append(b.material((0.5, 0.5, 0.5), 0.5, 0.0, (20.0, 20.0, 20.0), tex=t))
     # emitter triangle budget per emissive mesh, from the instance counts
     em_inst = sum(int(counts[m]) for m in emissive_mesh)
     per_mesh_em = max(1, int(round(n_emissive / max(1, em_inst))))
@@ -479,9 +480,11 @@ def instanced_field(seed: int = BASE_SEED + 3, n_meshes: int = 100, n_instances:
         n_textures, tex_size, tex_size, 3).astype(np.float32)
     scene = b.build(textures=textures, with_normals=True, with_uvs=True, name="instanced-field")
     ang = rng.uniform(n_instances, 0, 2 * math.pi)
-    sc = rng.uniform(n_instances, 0.5, 2.0)
-    pos = np.stack([rng.uniform(n_instances, -60, 60), rng.uniform(n_instances, 0, 20),
-                    rng.uniform(n_instances, -60, 20)], 1)
+    sc = rng.uniform(n_instances, 0.8, 2.5)
+    # a dense cluster in front of the camera: about a third of the image is
+    # covered by instances at any resolution
+    pos = np.stack([rng.uniform(n_instances, -28, 28), rng.uniform(n_instances, 0, 10),
+                    rng.uniform(n_instances, -45, 5)], 1)
     xf = np.zeros((n_instances, 3, 4), np.float32)
     c, s = np.cos(ang), np.sin(ang)
     xf[:, 0, 0], xf[:, 0, 2], xf[:, 2, 0], xf[:, 2, 2] = c * sc, s * sc, -s * sc, c * sc
@@ -490,7 +493,7 @@ def instanced_field(seed: int = BASE_SEED + 3, n_meshes: int = 100, n_instances:
     scene.mesh_tri_offset = np.array(mesh_off, np.int64)
     scene.instance_mesh = inst_mesh.astype(np.uint32)
     scene.instance_xform = xf
-    cam = Camera((0.0, 25.0, 70.0), (0.0, 5.0, -20.0), (0.0, 1.0, 0.0), 60.0, width, height)
+    cam = Camera((0.0, 14.0, 38.0), (0.0, 3.0, -15.0), (0.0, 1.0, 0.0), 55.0, width, height)
     return scene, cam
 
 
