@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import MISS, allowed_4sigma, image_parity, t_close
+from helpers import MISS, allowed_4sigma, image_parity
 from paper_1705_01263_gb300 import scenes
 
 torch = pytest.importorskip("torch")
@@ -38,22 +38,29 @@ def test_instanced_hits_match_flattened_oracle(field, kind):
     p = prim.cpu().numpy().view(np.uint32)
     i = inst.cpu().numpy().view(np.uint32)
     t = t.cpu().numpy()
-    po, to, _, _ = o.trace(rays)
     hit = p != MISS
-    fp = np.where(hit, flat_index(sd, np.where(hit, i, 0), np.where(hit, p, 0)), MISS)
-    assert np.mean(fp == po) >= 0.99999
-    both = hit & (fp == po)
-    assert np.all(t_close(t[both], to[both], rays[both], 1e-5))
+    fp = np.where(hit, flat_index(sd, np.where(hit, i, 0), np.where(hit, p, 0)), MISS).astype(np.uint32)
+    # the GPU intersects in object space, the oracle the FP32 world-space
+    # copy: near edges both answers can be right, and every disagreement must
+    # be a valid alternative hit
+    from test_gpu_trace import check_closest
+    check_closest(flat, rays, (fp, t, u.cpu().numpy(), v.cpu().numpy()), o.trace(rays), min_agree=0.99995)
 
 
 def test_instanced_render_parity(field):
+    """Converged comparison (8192 spp on a 48 x 27 crop of the camera): the
+    emitter fluxes of textured triangles are integrated exactly by the oracle
+    and by 16 x 16 supersampling in the GPU preprocess, so the two alias
+    tables differ and paths pick different lights; the images then agree only
+    statistically."""
     from paper_1705_01263_gb300 import rt
     sd, flat, cam, s, o = field
+    cam = scenes.Camera(cam.eye, cam.look_at, cam.up, cam.vfov_deg, 48, 27)
     film = rt.Film(cam.width, cam.height)
-    rt.rt_render(s, cam, 256, 6, film)
+    rt.rt_render(s, cam, 8192, 6, film)
     torch.cuda.synchronize()
     mg, vg = oracle.resolve(*film.download())
-    S, S2, C, _ = o.render(cam, 256, 6)
+    S, S2, C, _ = o.render(cam, 8192, 6)
     mo, vo = oracle.resolve(S, S2, C)
     l1, out, n = image_parity(mg, vg, mo, vo)
     assert l1 <= 0.01, l1
