@@ -176,6 +176,31 @@ def guided_vs_plain(target_spp=256, chunk=16, max_spp=1024, seed=5):
             "plain_curve": plain, "guided_curve": guided[:40]}
 
 
+def many_lights(spp=4, depth=12):
+    """Secondary workload: 1000 instances of 100 meshes (10M instanced
+    triangles), 100k textured emitters selected by the alias table, 1920 x
+    1080 at `spp` of its 256 spp, depth 12 (throughput only)."""
+    import torch
+    from paper_1705_01263_gb300 import rt, scenes
+    sd, cam = scenes.instanced_field()
+    s = rt.Scene(sd)
+    film = rt.Film(cam.width, cam.height)
+    rt.rt_render(s, cam, 1, depth, film)
+    torch.cuda.synchronize()
+    st = rt.rt_stats()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    rt.rt_render(s, cam, spp, depth, film, rt.make_opts(stats=st))
+    ev1.record()
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    info = s.info()
+    return {"workload": "instanced field: 1000 instances of 100 meshes, 10M instanced tris, 100k textured emitters, "
+                        f"1920x1080, {spp} spp, depth {depth}",
+            "Mpaths_per_s": st.paths / ms / 1e3, "Mrays_per_s": (st.extension_rays + st.shadow_rays) / ms / 1e3,
+            "ms": ms, "bvh_nodes": info["nodes"], "unique_tris": info["leaf_tris"], "device_bytes": info["device_bytes"]}
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -216,6 +241,7 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-guided", action="store_true", help="skip the guided-vs-plain time-to-RMSE run")
+    ap.add_argument("--no-many-lights", action="store_true", help="skip the instanced many-light workload")
     ap.add_argument("--spp", type=int, default=SPP)
     ap.add_argument("--out", default=None)
     ap.add_argument("--trace-kernel", type=int, default=0, help="0 one ray per thread with warp fetch, 1 persistent warps refilling lanes")
@@ -321,6 +347,9 @@ def main():
     gvp = None
     if rank == 0 and not args.no_guided:
         gvp = guided_vs_plain()
+    ml = None
+    if rank == 0 and not args.no_many_lights:
+        ml = many_lights()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_oracle(sd, cam)
@@ -353,6 +382,7 @@ def main():
             "clocks": clocks,
             "cpu_baseline": cpu,
             "guided_vs_plain": gvp,
+            "many_lights": ml,
             "wall_s": t_wall,
         }
         s = json.dumps(line)

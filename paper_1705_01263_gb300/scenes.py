@@ -116,7 +116,8 @@ class SceneData:
             idx.append((remap[tri] + base).astype(np.uint32))
             mats.append(self.tri_material[t0:t1])
             if self.normals is not None:
-                nw = self.normals[used] @ np.linalg.inv(X[:, :3].astype(np.float64)).T
+                # normals map with the inverse transpose of the linear part
+                nw = self.normals[used].astype(np.float64) @ np.linalg.inv(X[:, :3].astype(np.float64))
                 nw /= np.linalg.norm(nw, axis=1, keepdims=True)
                 nrm.append(nw.astype(np.float32))
             if self.uvs is not None:

@@ -40,11 +40,15 @@ def test_instanced_hits_match_flattened_oracle(field, kind):
     t = t.cpu().numpy()
     hit = p != MISS
     fp = np.where(hit, flat_index(sd, np.where(hit, i, 0), np.where(hit, p, 0)), MISS).astype(np.uint32)
-    # the GPU intersects in object space, the oracle the FP32 world-space
-    # copy: near edges both answers can be right, and every disagreement must
-    # be a valid alternative hit
+    # the GPU intersects FP32 object-space triangles with the ray mapped to
+    # object space, the oracle the FP32 world-space copy of each instance: the
+    # two geometries differ by the rounding of the transform (about 1e-7 of
+    # the coordinates), so distances agree to 1e-4 of max(t, |o|, 1), grazing
+    # hits included, and near edges both answers can be right; every
+    # disagreement must be a valid alternative hit
     from test_gpu_trace import check_closest
-    check_closest(flat, rays, (fp, t, u.cpu().numpy(), v.cpu().numpy()), o.trace(rays), min_agree=0.99995)
+    check_closest(flat, rays, (fp, t, u.cpu().numpy(), v.cpu().numpy()), o.trace(rays), min_agree=0.99995,
+                  t_rel=1e-4)
 
 
 def test_instanced_render_parity(field):

@@ -37,7 +37,7 @@ def bary_slack(sd, rays, prim, t):
     return np.maximum(1e-5, 1e-5 * scale / np.maximum(size, 1e-30))
 
 
-def check_closest(sd, rays, gpu, ref, min_agree=0.99999, grazing_ok=False):
+def check_closest(sd, rays, gpu, ref, min_agree=0.99999, grazing_ok=False, t_rel=1e-5):
     """Identical primitive on >= min_agree of the rays; every disagreement
     must be a valid alternative (the GPU's triangle contains the hit point
     within 1e-5 barycentric slack in float64, at the oracle's distance).
@@ -73,9 +73,9 @@ def check_closest(sd, rays, gpu, ref, min_agree=0.99999, grazing_ok=False):
             same_t = gh & t_close(t[ob], to[ob], rays[ob], 1e-3)
             assert np.all(on_edge | same_t | gpu_edge), "a clear hit was missed"
         else:
-            assert np.all(t_close(t[bad], to[bad], rays[bad], 1e-5))
+            assert np.all(t_close(t[bad], to[bad], rays[bad], t_rel))
     hit = same & (po != MISS)
-    assert np.all(t_close(t[hit], to[hit], rays[hit], 1e-3 if grazing_ok else 1e-5))
+    assert np.all(t_close(t[hit], to[hit], rays[hit], 1e-3 if grazing_ok else t_rel))
     assert np.all(np.isinf(t[p == MISS]))
     assert agree >= min_agree, (agree, bad.size)
     return agree
