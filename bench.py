@@ -246,6 +246,7 @@ def main():
     ap.add_argument("--out", default=None)
     ap.add_argument("--trace-kernel", type=int, default=0, help="0 one ray per thread with warp fetch, 1 persistent warps refilling lanes")
     ap.add_argument("--megakernel-only", action="store_true", help="A/B baseline: megakernel per iteration set")
+    ap.add_argument("--sort-by-material", action="store_true", help="A/B: material-sorted shading queue")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -268,7 +269,8 @@ def main():
     WH = cam.width * cam.height
 
     def opts(**kw):
-        return rt.make_opts(seed=0, trace_kernel=args.trace_kernel, megakernel_only=args.megakernel_only, **kw)
+        return rt.make_opts(seed=0, trace_kernel=args.trace_kernel, megakernel_only=args.megakernel_only,
+                            sort_by_material=args.sort_by_material, **kw)
 
     def render_step(stats=None, profile=0):
         o = opts(stats=stats, profile=profile)
@@ -365,7 +367,8 @@ def main():
                        "paths_per_step": paths_per_step, "l2": "flushed between steps (256 MiB write)",
                        "film": "FP64 sums", "parallelism": f"weak: {world} rank(s), disjoint iteration ranges",
                        "trace_kernel": ["one ray per thread, warp fetch", "persistent warps, lane refill"][args.trace_kernel],
-                       "schedule": "megakernel only" if args.megakernel_only else "wavefront + megakernel tail"},
+                       "schedule": "megakernel only" if args.megakernel_only else "wavefront + megakernel tail",
+                       "shading_queue": "material-sorted" if args.sort_by_material else "compaction order"},
             "mrays_per_s": mrays,
             "rays_per_path": (ext + shd) / (paths_per_step * args.steps),
             "roofline": {"bound": "hbm", "kernel": "k_trace_ext (closest-hit BVH8 traversal)",

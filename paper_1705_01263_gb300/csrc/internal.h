@@ -15,6 +15,7 @@ struct rt_scene {
     std::vector<std::vector<uint8_t>> host_keep;
     int64_t num_nodes = 0, num_leaf_tris = 0, device_bytes = 0;
     int64_t num_triangles = 0;
+    uint32_t num_materials = 0;
     int bvh_depth = 0;
     bool host_only = false;
 };

@@ -183,12 +183,12 @@ __global__ void __launch_bounds__(128) k_trace_ext(DevScene sc, Pool pool) {
     }
 }
 
-__global__ void __launch_bounds__(128) k_shade(RenderParams P, Pool pool) {
+__global__ void __launch_bounds__(128) k_shade(RenderParams P, Pool pool, const uint32_t *sorted) {
     Ctrl *c = pool.ctrl;
     if (c->tail) return;
     const uint32_t n = c->n_ext;
     const uint32_t cur = c->cur;
-    const uint32_t *queue = pool.q[cur];
+    const uint32_t *queue = sorted ? sorted : pool.q[cur];
     uint32_t *next = pool.q[cur ^ 1u];
     for (;;) {
         uint32_t base = warp_fetch32(&c->fetch_shade);
@@ -286,6 +286,53 @@ __global__ void __launch_bounds__(128) k_trace_shadow_simple(DevScene sc, Pool p
     if (kCount) {
         atomicAdd(&c->shadow_nodes, (unsigned long long)nodes);
         atomicAdd(&c->shadow_tris, (unsigned long long)tris);
+    }
+}
+
+// Material-sorted shading queue (A/B option): a counting sort of the
+// extension queue by the material of the hit (misses last) so that lanes of
+// a warp shade the same material. Histogram in shared memory per block,
+// exclusive scan in one block, then a scatter with one atomic per entry.
+__global__ void k_mat_hist(DevScene sc, Pool pool, uint32_t nmat, uint32_t *hist) {
+    extern __shared__ uint32_t sh_hist[];
+    Ctrl *c = pool.ctrl;
+    if (c->tail) return;
+    for (uint32_t k = threadIdx.x; k <= nmat; k += blockDim.x) sh_hist[k] = 0;
+    __syncthreads();
+    const uint32_t n = c->n_ext;
+    const uint32_t *queue = pool.q[c->cur];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t prim = __float_as_uint(pool.hit[queue[i]].x);
+        uint32_t key = prim == RT_MISS ? nmat : __ldg(sc.tri_material + prim);
+        atomicAdd(&sh_hist[key], 1u);
+    }
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k <= nmat; k += blockDim.x)
+        if (sh_hist[k]) atomicAdd(&hist[k], sh_hist[k]);
+}
+
+__global__ void k_mat_scan(Pool pool, uint32_t nmat, uint32_t *hist) {
+    if (pool.ctrl->tail) return;
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (uint32_t k = 0; k <= nmat; ++k) {
+            uint32_t v = hist[k];
+            hist[k] = acc;
+            acc += v;
+        }
+    }
+}
+
+__global__ void k_mat_scatter(DevScene sc, Pool pool, uint32_t nmat, uint32_t *offsets, uint32_t *sorted) {
+    Ctrl *c = pool.ctrl;
+    if (c->tail) return;
+    const uint32_t n = c->n_ext;
+    const uint32_t *queue = pool.q[c->cur];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t q = queue[i];
+        uint32_t prim = __float_as_uint(pool.hit[q].x);
+        uint32_t key = prim == RT_MISS ? nmat : __ldg(sc.tri_material + prim);
+        sorted[atomicAdd(&offsets[key], 1u)] = q;
     }
 }
 
@@ -650,6 +697,9 @@ struct RenderCache {
     uint64_t dims_seed = ~0ull;
     int dims_n = 0;
     Ctrl *host_ctrl = nullptr;
+    // material-sorted shading queue
+    uint32_t *mat_hist = nullptr, *mat_sorted = nullptr;
+    uint32_t mat_cap = 0, mat_nmat = 0;
     // guided rendering
     uint32_t gcap = 0, gbatch = 0;
     float *gfeat = nullptr, *tr_feat = nullptr, *tr_wi = nullptr, *tr_w = nullptr;
@@ -658,7 +708,8 @@ struct RenderCache {
     ~RenderCache() {
         if (dims) cudaFree(dims);
         if (host_ctrl) cudaFreeHost(host_ctrl);
-        for (void *p : {(void *)gfeat, (void *)tr_feat, (void *)tr_wi, (void *)tr_w, (void *)grec, (void *)gnrec})
+        for (void *p : {(void *)gfeat, (void *)tr_feat, (void *)tr_wi, (void *)tr_w, (void *)grec, (void *)gnrec,
+                        (void *)mat_hist, (void *)mat_sorted})
             if (p) cudaFree(p);
     }
 };
@@ -938,6 +989,20 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     const int g_simple = grid_persistent(k_trace_ext_simple<false>, gb, 0);
     const int g_mega = grid_for(k_megakernel, gb, cap);
     const bool prof = o.profile >= 1, count = o.profile >= 2;
+    const uint32_t nmat = s->num_materials;
+    const int g_hist = grid_for(k_mat_scatter, 256, cap);
+    if (o.sort_by_material && (rc->mat_cap < cap || rc->mat_nmat < nmat + 1)) {
+        if (rc->mat_hist) cudaFree(rc->mat_hist);
+        if (rc->mat_sorted) cudaFree(rc->mat_sorted);
+        rc->mat_hist = rc->mat_sorted = nullptr;
+        if (cudaMalloc(&rc->mat_hist, sizeof(uint32_t) * (nmat + 1)) != cudaSuccess ||
+            cudaMalloc(&rc->mat_sorted, sizeof(uint32_t) * (size_t)cap) != cudaSuccess) {
+            set_error("rt_render: material sort buffers");
+            return RT_OOM;
+        }
+        rc->mat_cap = cap;
+        rc->mat_nmat = nmat + 1;
+    }
     // event pairs per timed launch: kind 0 trace, 1 shade, 2 shadow, 3 megakernel, 4 other
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> evs;
     auto mark = [&](int kind) -> cudaEvent_t {
@@ -979,8 +1044,19 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
                     k_trace_ext<false><<<g_trace, gb, smem, st>>>(s->dev, pool);
                 }
                 done(e);
+                const uint32_t *sorted = nullptr;
+                if (o.sort_by_material) {
+                    e = mark(4);
+                    RT_CUDA_TRY(cudaMemsetAsync(rc->mat_hist, 0, sizeof(uint32_t) * (nmat + 1), st));
+                    k_mat_hist<<<g_hist, 256, (nmat + 1) * sizeof(uint32_t), st>>>(s->dev, pool, nmat, rc->mat_hist);
+                    k_mat_scan<<<1, 32, 0, st>>>(pool, nmat, rc->mat_hist);
+                    k_mat_scatter<<<g_hist, 256, 0, st>>>(s->dev, pool, nmat, rc->mat_hist, rc->mat_sorted);
+                    done(e);
+                    sorted = rc->mat_sorted;
+                    stats.kernel_launches += 3;
+                }
                 e = mark(1);
-                k_shade<<<g_shade, gb, 0, st>>>(P, pool);
+                k_shade<<<g_shade, gb, 0, st>>>(P, pool, sorted);
                 done(e);
                 e = mark(2);
                 if (o.trace_kernel == 0) {
@@ -1209,7 +1285,7 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
                 if (o.trace_kernel == 0) k_trace_ext_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool);
                 else k_trace_ext<false><<<g_trace, gb, smem, st>>>(s->dev, pool);
-                k_shade<<<g_shade, gb, 0, st>>>(P, pool);
+                k_shade<<<g_shade, gb, 0, st>>>(P, pool, nullptr);
                 if (o.trace_kernel == 0) k_trace_shadow_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool);
                 else k_trace_shadow<false><<<g_shadow, gb, smem, st>>>(s->dev, pool);
                 k_step_end<<<1, 1, 0, st>>>(pool);

@@ -173,6 +173,7 @@ rt_status rtg::scene_create(const rt_scene_desc *d, rt_scene **out, bool host_on
     auto fail = [&](rt_status st) { rt_scene_destroy(s); return st; };
     DevScene &D = s->dev, &Hs = s->host;
     s->num_triangles = T;
+    s->num_materials = (uint32_t)d->num_materials;
 
     // ---- BVH: one level, or per-mesh bottom levels + a top level over instances
     rt_status st;

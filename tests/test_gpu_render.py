@@ -136,6 +136,19 @@ def test_traversal_variants_agree():
     assert np.array_equal(sa, sb)
 
 
+def test_material_sorted_queue_gives_the_same_image():
+    """Sorting the shading queue by material only changes the order in which
+    paths are shaded; every path and so the film are unchanged."""
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.sphere_field(n_spheres=40, plane_res=(120, 60), env_size=(512, 256), width=160, height=90)
+    s = rt.Scene(sd)
+    a, _, _ = gpu_render(s, cam, 4, 16)
+    b, st, _ = gpu_render(s, cam, 4, 16, sort_by_material=True)
+    sa, s2a, ca = a.download()
+    sb, s2b, cb = b.download()
+    assert np.array_equal(ca, cb) and np.array_equal(sa, sb) and np.array_equal(s2a, s2b)
+
+
 def test_wavefront_equals_megakernel():
     from paper_1705_01263_gb300 import rt
     sd, cam = scenes.cornell_box()
