@@ -301,10 +301,17 @@ __global__ void k_mat_hist(DevScene sc, Pool pool, uint32_t nmat, uint32_t *hist
     __syncthreads();
     const uint32_t n = c->n_ext;
     const uint32_t *queue = pool.q[c->cur];
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint32_t prim = __float_as_uint(pool.hit[queue[i]].x);
-        uint32_t key = prim == RT_MISS ? nmat : __ldg(sc.tri_material + prim);
-        atomicAdd(&sh_hist[key], 1u);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += stride) {
+        uint32_t i = base + lane_id();
+        uint32_t key = 0xFFFFFFFFu;
+        if (i < n) {
+            uint32_t prim = __float_as_uint(pool.hit[queue[i]].x);
+            key = prim == RT_MISS ? nmat : __ldg(sc.tri_material + prim);
+        }
+        // one shared atomic per distinct key in the warp
+        uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
+        if (i < n && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sh_hist[key], (uint32_t)__popc(peers));
     }
     __syncthreads();
     for (uint32_t k = threadIdx.x; k <= nmat; k += blockDim.x)
@@ -328,11 +335,22 @@ __global__ void k_mat_scatter(DevScene sc, Pool pool, uint32_t nmat, uint32_t *o
     if (c->tail) return;
     const uint32_t n = c->n_ext;
     const uint32_t *queue = pool.q[c->cur];
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint32_t q = queue[i];
-        uint32_t prim = __float_as_uint(pool.hit[q].x);
-        uint32_t key = prim == RT_MISS ? nmat : __ldg(sc.tri_material + prim);
-        sorted[atomicAdd(&offsets[key], 1u)] = q;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += stride) {
+        uint32_t i = base + lane_id();
+        uint32_t key = 0xFFFFFFFFu, q = 0;
+        if (i < n) {
+            q = queue[i];
+            uint32_t prim = __float_as_uint(pool.hit[q].x);
+            key = prim == RT_MISS ? nmat : __ldg(sc.tri_material + prim);
+        }
+        // lanes with the same key reserve their slots with one global atomic
+        uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
+        uint32_t leader = __ffs(peers) - 1;
+        uint32_t pos = 0;
+        if (i < n && lane_id() == leader) pos = atomicAdd(&offsets[key], (uint32_t)__popc(peers));
+        pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
+        if (i < n) sorted[pos + __popc(peers & ((1u << lane_id()) - 1u))] = q;
     }
 }
 
