@@ -201,6 +201,43 @@ def many_lights(spp=4, depth=12):
             "ms": ms, "bvh_nodes": info["nodes"], "unique_tris": info["leaf_tris"], "device_bytes": info["device_bytes"]}
 
 
+def batched(spp_divisor=16):
+    """Secondary workload: 64 independent seeded scenes (1k-500k triangles,
+    256^2-1024^2 px, depth 4-16, spp drawn from 16..256 and divided by
+    `spp_divisor` to bound the run) in one batched wavefront replayed as a
+    CUDA graph; pool capacity chosen by the autotuner on 1 spp per job."""
+    import torch
+    from paper_1705_01263_gb300 import rt, scenes
+    t0 = time.time()
+    specs = scenes.batch_jobs(spp_divisor=spp_divisor)
+    built = [(rt.Scene(sd), cam, spp, d) for sd, cam, spp, d in specs]
+    films = [rt.Film(cam.width, cam.height) for _, cam, _, _ in built]
+    jobs = [(s, cam, spp, d, f) for (s, cam, spp, d), f in zip(built, films)]
+    setup_s = time.time() - t0
+    o = rt.rt_autotune(jobs, 1)
+    for f in films:
+        f.clear()
+    st = rt.rt_stats()
+    o.stats = C_pointer(st)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    rt.rt_render_batch(jobs, o)
+    ev1.record()
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    return {"workload": f"64 seeded scenes ({sum(sd.num_triangles for sd, _, _, _ in specs)} triangles in all), "
+                        f"spp / {spp_divisor}, one batched wavefront replayed as a CUDA graph",
+            "paths": st.paths, "Mpaths_per_s": st.paths / ms / 1e3,
+            "Mrays_per_s": (st.extension_rays + st.shadow_rays) / ms / 1e3, "ms": ms,
+            "graph_replays": st.waves, "autotuned_pool": o.max_paths_in_flight, "scene_setup_s": setup_s}
+
+
+def C_pointer(x):
+    import ctypes
+    return ctypes.pointer(x)
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -242,6 +279,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-guided", action="store_true", help="skip the guided-vs-plain time-to-RMSE run")
     ap.add_argument("--no-many-lights", action="store_true", help="skip the instanced many-light workload")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-scene batched workload")
     ap.add_argument("--spp", type=int, default=SPP)
     ap.add_argument("--out", default=None)
     ap.add_argument("--trace-kernel", type=int, default=0, help="0 one ray per thread with warp fetch, 1 persistent warps refilling lanes")
@@ -352,6 +390,9 @@ def main():
     ml = None
     if rank == 0 and not args.no_many_lights:
         ml = many_lights()
+    bt = None
+    if rank == 0 and not args.no_batched:
+        bt = batched()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_oracle(sd, cam)
@@ -386,6 +427,7 @@ def main():
             "cpu_baseline": cpu,
             "guided_vs_plain": gvp,
             "many_lights": ml,
+            "batched": bt,
             "wall_s": t_wall,
         }
         s = json.dumps(line)

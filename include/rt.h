@@ -223,6 +223,30 @@ rt_status rt_render_static(const rt_scene *scene, const rt_camera *camera, uint3
                            uint32_t first_iteration, double *sum, double *sum2, uint32_t *count,
                            const rt_render_opts *opts, void *stream);
 
+/* Batched rendering of many independent scenes (not in the paper): one job
+ * per (scene, camera, spp, max_depth, film); all jobs share one wavefront
+ * path pool (tasks of all jobs are concatenated) and one iteration set is
+ * captured as a CUDA graph and replayed until every task is done. Each job
+ * accumulates iterations [film next, + spp) into its own film (FP64 atomic
+ * additions: equal to rt_render up to FP64 addition order). Blocking;
+ * RT_TIMEOUT when the abort flag or time budget stopped it between sets
+ * (films hold the completed tasks). Guiding is per rt_render call. */
+typedef struct {
+    const rt_scene *scene;
+    rt_camera camera;
+    uint32_t spp;
+    uint32_t max_depth;
+    rt_film *film;
+} rt_render_job;
+rt_status rt_render_batch(const rt_render_job *jobs, int32_t njobs, const rt_render_opts *opts, void *stream);
+
+/* Autotuner (not in the paper): renders `sample_spp` of each job with every
+ * candidate of path-pool capacity, tail threshold and traversal variant and
+ * writes the fastest into *opts (max_paths_in_flight, tail_threshold,
+ * trace_kernel). The films receive those samples; callers clear them. */
+rt_status rt_autotune(const rt_render_job *jobs, int32_t njobs, uint32_t sample_spp, rt_render_opts *opts,
+                      void *stream);
+
 /* ------------------------------------------------------- QMC sampling */
 /* Sequence index of sample j in pixel (x, y) under full-screen enumeration
  * (Appendix A.2): DEVICE arrays px, py, j of n entries -> out (uint64). */

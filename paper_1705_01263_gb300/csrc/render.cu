@@ -1335,3 +1335,356 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
     if (o.stats) *o.stats = stats;
     return result;
 }
+
+// ---------------------------------------------------------------------------
+// Batched rendering: many scenes, cameras and films in one wavefront. Slots
+// of one path pool take tasks from a global index space that concatenates
+// the jobs ([off_j, off_j + W_j H_j spp_j)); each slot remembers its job,
+// and every kernel reads that job's parameters (scene, camera, QMC tables,
+// depth) from a device table. One iteration set is captured once as a CUDA
+// graph (its start index lives in device memory and is advanced by the graph
+// itself) and the graph is replayed until all tasks are done; the host only
+// checks the abort flag between replays.
+namespace rtg {
+
+struct BatchJob {
+    RenderParams P;
+    double *sum, *sum2;
+    uint32_t *count;
+    uint64_t off;        // first global task of the job
+    uint64_t ntask;      // W * H * spp
+    uint64_t film_task0; // the film's next_task when the batch started
+    uint32_t WH;
+};
+
+struct BatchCtl {
+    uint64_t t0;         // first global task of the current iteration set
+    uint64_t total;      // tasks of all jobs
+    uint32_t n;          // tasks in the current set
+    uint32_t cap;
+};
+
+RT_D uint32_t find_job(const BatchJob *jobs, uint32_t njobs, uint64_t t) {
+    uint32_t lo = 0, hi = njobs;
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (jobs[mid].off <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_batch_raygen(const BatchJob *jobs, uint32_t njobs, BatchCtl *bc, Pool pool, uint32_t *job_of) {
+    const uint64_t t0 = bc->t0;
+    const uint32_t n = (uint32_t)min((uint64_t)bc->cap, bc->total - min(bc->total, t0));
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        uint64_t t = t0 + q;
+        uint32_t j = find_job(jobs, njobs, t);
+        const BatchJob &J = jobs[j];
+        uint64_t local = t - J.off + J.film_task0;
+        PathState s;
+        raygen(J.P, (uint32_t)(local % J.WH), (uint32_t)(local / J.WH), s);
+        store_state(pool, q, s);
+        pool.q[0][q] = q;
+        job_of[q] = j;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Ctrl *c = pool.ctrl;
+        bc->n = n;
+        c->n_ext = n;
+        c->n_next = 0;
+        c->n_shadow = 0;
+        c->cur = 0;
+        c->fetch_ext = c->fetch_shadow = c->fetch_shade = 0;
+        c->tail = 0;
+    }
+}
+
+template <bool kAny>
+__global__ void __launch_bounds__(128) k_batch_trace(const BatchJob *jobs, Pool pool, const uint32_t *job_of) {
+    Ctrl *c = pool.ctrl;
+    const uint32_t n = kAny ? c->n_shadow : c->n_ext;
+    const uint32_t *queue = kAny ? pool.qs : pool.q[c->cur];
+    uint32_t *fetch = kAny ? &c->fetch_shadow : &c->fetch_ext;
+    bool overflow = false;
+    for (;;) {
+        uint32_t base = warp_fetch32(fetch);
+        if (base >= n) break;
+        uint32_t i = base + lane_id();
+        if (i >= n) continue;
+        uint32_t q = queue[i];
+        const DevScene &sc = jobs[job_of[q]].P.sc;
+        float4 o = kAny ? pool.sh_o[q] : pool.ray_o[q], d = kAny ? pool.sh_d[q] : pool.ray_d[q];
+        Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, kAny ? o.w : INFINITY};
+        Hit h;
+        h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
+        TraceResult tr = trace_scene<kAny>(sc, r, h);
+        overflow |= tr.overflow;
+        if (kAny) {
+            if (h.prim == RT_MISS) {
+                float4 cc = pool.sh_c[q], L = pool.L[q];
+                pool.L[q] = make_float4(L.x + cc.x, L.y + cc.y, L.z + cc.z, 0.f);
+            }
+        } else {
+            pool.hit[q] = make_float4(__uint_as_float(h.prim), h.t, h.b1, h.b2);
+            pool.hit_inst[q] = h.inst;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(kAny ? &c->shadow_rays : &c->ext_rays, (unsigned long long)n);
+    if (overflow) atomicOr(&c->overflow, 1u);
+}
+
+__global__ void __launch_bounds__(128) k_batch_shade(const BatchJob *jobs, Pool pool, const uint32_t *job_of) {
+    Ctrl *c = pool.ctrl;
+    const uint32_t n = c->n_ext;
+    const uint32_t cur = c->cur;
+    const uint32_t *queue = pool.q[cur];
+    uint32_t *next = pool.q[cur ^ 1u];
+    for (;;) {
+        uint32_t base = warp_fetch32(&c->fetch_shade);
+        if (base >= n) break;
+        uint32_t i = base + lane_id();
+        bool valid = i < n;
+        uint32_t q = 0;
+        int r = 0;
+        if (valid) {
+            q = queue[i];
+            const RenderParams &P = jobs[job_of[q]].P;
+            PathState s = load_state(pool, q);
+            float4 hv = pool.hit[q];
+            Hit h;
+            h.prim = __float_as_uint(hv.x); h.inst = pool.hit_inst[q]; h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
+            ShadowRay sh;
+            r = shade(P, s, h, sh);
+            pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
+            if (r & 1) {
+                pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, 0.f);
+                pool.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);
+                pool.beta[q] = make_float4(s.beta.x, s.beta.y, s.beta.z, __uint_as_float(s.depth));
+            }
+            if (r & 2) {
+                pool.sh_o[q] = make_float4(sh.o.x, sh.o.y, sh.o.z, sh.tmax);
+                pool.sh_d[q] = make_float4(sh.d.x, sh.d.y, sh.d.z, 0.f);
+                pool.sh_c[q] = make_float4(sh.contrib.x, sh.contrib.y, sh.contrib.z, 0.f);
+            }
+        }
+        warp_append(next, &c->n_next, valid && (r & 1), q);
+        warp_append(pool.qs, &c->n_shadow, valid && (r & 2), q);
+    }
+}
+
+__global__ void k_batch_step_end(Pool pool) {
+    Ctrl *c = pool.ctrl;
+    c->n_ext = c->n_next;
+    c->n_next = 0;
+    c->cur ^= 1u;
+    c->n_shadow = 0;
+    c->fetch_ext = c->fetch_shadow = c->fetch_shade = 0;
+}
+
+// FP64 atomics into each job's film (several jobs and passes share a set).
+__global__ void k_batch_film(const BatchJob *jobs, uint32_t njobs, BatchCtl *bc, Pool pool, const uint32_t *job_of) {
+    const uint32_t n = bc->n;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const BatchJob &J = jobs[job_of[q]];
+        uint64_t local = bc->t0 + q - J.off + J.film_task0;
+        uint32_t px = (uint32_t)(local % J.WH);
+        float4 L = pool.L[q];
+        double a = L.x, b = L.y, c = L.z;
+        atomicAdd(&J.sum[3 * (size_t)px], a);
+        atomicAdd(&J.sum[3 * (size_t)px + 1], b);
+        atomicAdd(&J.sum[3 * (size_t)px + 2], c);
+        atomicAdd(&J.sum2[3 * (size_t)px], a * a);
+        atomicAdd(&J.sum2[3 * (size_t)px + 1], b * b);
+        atomicAdd(&J.sum2[3 * (size_t)px + 2], c * c);
+        atomicAdd(&J.count[px], 1u);
+    }
+}
+
+// Advance to the next iteration set (after the film kernel has finished).
+__global__ void k_batch_advance(BatchCtl *bc) { bc->t0 += bc->n; }
+
+}  // namespace rtg
+
+extern "C" rt_status rt_render_batch(const rt_render_job *jobs, int32_t njobs, const rt_render_opts *opts_in,
+                                     void *stream) {
+    if (!jobs || njobs <= 0) { set_error("rt_render_batch: no jobs"); return RT_INVALID_ARG; }
+    rt_render_opts o{};
+    if (opts_in) o = *opts_in;
+    if (o.guide) { set_error("rt_render_batch: guiding is per rt_render call"); return RT_NOT_SUPPORTED; }
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<BatchJob> hj((size_t)njobs);
+    uint64_t total = 0;
+    uint32_t maxd = 1;
+    int ndims_max = 0;
+    for (int32_t j = 0; j < njobs; ++j) {
+        const rt_render_job &J = jobs[j];
+        if (!J.scene || !J.film || J.scene->host_only || J.camera.width != J.film->W || J.camera.height != J.film->H ||
+            J.max_depth < 1 || J.max_depth > (uint32_t)kMaxDepth) {
+            set_error("rt_render_batch: invalid job " + std::to_string(j));
+            return RT_INVALID_ARG;
+        }
+        maxd = std::max(maxd, J.max_depth);
+        ndims_max = std::max(ndims_max, 2 + 7 * (int)(J.max_depth + 1));
+    }
+    // one Halton table (the longest) and one job table for the batch
+    struct Scratch {
+        std::vector<void *> ptrs;
+        ~Scratch() { for (void *p : ptrs) cudaFree(p); }
+    } scratch;
+    std::vector<HaltonDim> dims = make_dims(o.seed, ndims_max);
+    HaltonDim *ddims = nullptr;
+    RT_CUDA_TRY(cudaMalloc(&ddims, dims.size() * sizeof(HaltonDim)));
+    scratch.ptrs.push_back(ddims);
+    RT_CUDA_TRY(cudaMemcpyAsync(ddims, dims.data(), dims.size() * sizeof(HaltonDim), cudaMemcpyHostToDevice, st));
+    for (int32_t j = 0; j < njobs; ++j) {
+        const rt_render_job &J = jobs[j];
+        BatchJob &B = hj[(size_t)j];
+        B.P.sc = J.scene->dev;
+        B.P.cam = make_camera(J.camera);
+        B.P.en = make_enum(J.camera.width, J.camera.height);
+        B.P.dims = ddims;
+        B.P.max_depth = J.max_depth;
+        B.P.sigma = o.filter_sigma == 0.f ? 0.5f : o.filter_sigma;
+        B.P.mis_mode = o.mis_mode;
+        B.P.rr = o.rr_enable;
+        B.sum = J.film->sum;
+        B.sum2 = J.film->sum2;
+        B.count = J.film->count;
+        B.WH = J.camera.width * J.camera.height;
+        B.off = total;
+        B.ntask = (uint64_t)B.WH * J.spp;
+        B.film_task0 = J.film->next_task;
+        total += B.ntask;
+    }
+    if (total == 0) return RT_OK;
+    const uint32_t cap = std::max<uint32_t>(32u, o.max_paths_in_flight ? o.max_paths_in_flight : (1u << 22));
+    BatchJob *djobs = nullptr;
+    BatchCtl *dctl = nullptr;
+    uint32_t *job_of = nullptr;
+    RT_CUDA_TRY(cudaMalloc(&djobs, hj.size() * sizeof(BatchJob)));
+    scratch.ptrs.push_back(djobs);
+    RT_CUDA_TRY(cudaMalloc(&dctl, sizeof(BatchCtl)));
+    scratch.ptrs.push_back(dctl);
+    RT_CUDA_TRY(cudaMalloc(&job_of, sizeof(uint32_t) * cap));
+    scratch.ptrs.push_back(job_of);
+    RT_CUDA_TRY(cudaMemcpyAsync(djobs, hj.data(), hj.size() * sizeof(BatchJob), cudaMemcpyHostToDevice, st));
+    BatchCtl hc{0ull, total, 0u, cap};
+    RT_CUDA_TRY(cudaMemcpyAsync(dctl, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
+    PoolAlloc pa;
+    rt_status rs = ensure_pool(pa, cap);
+    if (rs != RT_OK) return rs;
+    Pool pool = pa.view;
+    RT_CUDA_TRY(cudaMemsetAsync(pool.ctrl, 0, sizeof(Ctrl), st));
+    const int gb = 128;
+    const int g_ray = grid_for(k_batch_raygen, 256, cap);
+    const int g_trace = grid_persistent(k_batch_trace<false>, gb, 0);
+    const int g_shade = grid_persistent(k_batch_shade, gb, 0);
+    const int g_film = grid_for(k_batch_film, 256, cap);
+    // capture one iteration set
+    cudaStream_t cs = nullptr;
+    RT_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    RT_CUDA_TRY(cudaStreamSynchronize(st));
+    RT_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    k_batch_raygen<<<g_ray, 256, 0, cs>>>(djobs, (uint32_t)njobs, dctl, pool, job_of);
+    for (uint32_t v = 1; v <= maxd + 1; ++v) {
+        k_batch_trace<false><<<g_trace, gb, 0, cs>>>(djobs, pool, job_of);
+        k_batch_shade<<<g_shade, gb, 0, cs>>>(djobs, pool, job_of);
+        k_batch_trace<true><<<g_trace, gb, 0, cs>>>(djobs, pool, job_of);
+        k_batch_step_end<<<1, 1, 0, cs>>>(pool);
+    }
+    k_batch_film<<<g_film, 256, 0, cs>>>(djobs, (uint32_t)njobs, dctl, pool, job_of);
+    k_batch_advance<<<1, 1, 0, cs>>>(dctl);
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (ce != cudaSuccess) { cudaStreamDestroy(cs); return cuda_status(ce, "rt_render_batch: graph capture"); }
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) { cudaGraphDestroy(graph); cudaStreamDestroy(cs); return cuda_status(ce, "rt_render_batch: instantiate"); }
+    const uint64_t sets = (total + cap - 1) / cap;
+    rt_stats stats{};
+    rt_status result = RT_OK;
+    uint64_t done_sets = 0;
+    auto t_start = std::chrono::steady_clock::now();
+    for (; done_sets < sets; ++done_sets) {
+        ce = cudaGraphLaunch(exec, st);
+        if (ce != cudaSuccess) { result = cuda_status(ce, "rt_render_batch: graph launch"); break; }
+        stats.kernel_launches += 3 + 4 * (maxd + 1);
+        bool check = (o.abort_flag || o.time_budget_ms > 0) && done_sets + 1 < sets;
+        if (check) {
+            cudaStreamSynchronize(st);
+            double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+            if ((o.abort_flag && *o.abort_flag) || (o.time_budget_ms > 0 && ms >= o.time_budget_ms)) {
+                ++done_sets;
+                set_error("rt_render_batch: stopped by time budget or abort flag");
+                result = RT_TIMEOUT;
+                break;
+            }
+        }
+    }
+    Ctrl hctl{};
+    cudaMemcpyAsync(&hctl, pool.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+    cudaError_t se = cudaStreamSynchronize(st);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (se != cudaSuccess) return cuda_status(se, "rt_render_batch");
+    if (hctl.overflow && result == RT_OK) { set_error("BVH traversal stack overflow"); result = RT_STACK_OVERFLOW; }
+    // films advance by the tasks of theirs that were completed
+    const uint64_t done_tasks = std::min<uint64_t>(total, done_sets * (uint64_t)cap);
+    for (int32_t j = 0; j < njobs; ++j) {
+        const BatchJob &B = hj[(size_t)j];
+        uint64_t dj = done_tasks > B.off ? std::min<uint64_t>(B.ntask, done_tasks - B.off) : 0;
+        jobs[j].film->next_task += dj;
+    }
+    stats.paths = done_tasks;
+    stats.waves = (uint32_t)done_sets;
+    stats.wavefront_steps = (uint32_t)(done_sets * (maxd + 1));
+    stats.extension_rays = hctl.ext_rays;
+    stats.shadow_rays = hctl.shadow_rays;
+    if (o.stats) *o.stats = stats;
+    return result;
+}
+
+extern "C" rt_status rt_autotune(const rt_render_job *jobs, int32_t njobs, uint32_t sample_spp, rt_render_opts *opts,
+                                 void *stream) {
+    if (!jobs || njobs <= 0 || !opts || sample_spp == 0) { set_error("rt_autotune: invalid argument"); return RT_INVALID_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    struct Cand { uint32_t cap, tail; int32_t tk; };
+    std::vector<Cand> cands;
+    const uint32_t caps[4] = {1u << 20, 1u << 21, 1u << 22, 1u << 23};
+    if (njobs == 1) {
+        const uint32_t tails[3] = {1u, 8192u, 65536u};   // 1: the megakernel never takes over
+        for (uint32_t c : caps)
+            for (uint32_t t : tails)
+                for (int32_t k = 0; k < 2; ++k) cands.push_back({c, t, k});
+    } else {
+        for (uint32_t c : caps) cands.push_back({c, 0u, 0});
+    }
+    double best = 1e300;
+    Cand pick = cands[0];
+    for (const Cand &c : cands) {
+        rt_render_opts o = *opts;
+        o.max_paths_in_flight = c.cap;
+        o.tail_threshold = c.tail;
+        o.trace_kernel = c.tk;
+        o.stats = nullptr;
+        o.profile = 0;
+        RT_CUDA_TRY(cudaStreamSynchronize(st));
+        auto t0 = std::chrono::steady_clock::now();
+        rt_status s;
+        if (njobs == 1) s = rt_render(jobs[0].scene, &jobs[0].camera, sample_spp, jobs[0].max_depth, jobs[0].film, &o, stream);
+        else {
+            std::vector<rt_render_job> js(jobs, jobs + njobs);
+            for (auto &j : js) j.spp = sample_spp;
+            s = rt_render_batch(js.data(), njobs, &o, stream);
+        }
+        if (s != RT_OK) return s;
+        RT_CUDA_TRY(cudaStreamSynchronize(st));
+        double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (ms < best) { best = ms; pick = c; }
+    }
+    opts->max_paths_in_flight = pick.cap;
+    opts->tail_threshold = pick.tail;
+    opts->trace_kernel = pick.tk;
+    return RT_OK;
+}

@@ -73,6 +73,11 @@ class rt_render_opts(C.Structure):
                 ("profile", C.c_int32), ("trace_kernel", C.c_int32)]
 
 
+class rt_render_job(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("camera", rt_camera), ("spp", C.c_uint32), ("max_depth", C.c_uint32),
+                ("film", C.c_void_p)]
+
+
 class rt_guide_opts(C.Structure):
     _fields_ = [("batch", C.c_uint32), ("learning_rate", C.c_float), ("alpha", C.c_float),
                 ("train_steps", C.c_uint32), ("seed", C.c_uint64)]
@@ -83,7 +88,7 @@ _lib = None
 EXPORTED = [
     "rt_scene_create", "rt_scene_destroy", "rt_scene_info", "rt_trace", "rt_film_create", "rt_film_destroy",
     "rt_film_clear", "rt_film_next_iteration", "rt_film_seek", "rt_film_buffers", "rt_film_resolve", "rt_render",
-    "rt_render_static", "rt_sample_index", "rt_halton", "rt_divide_u64_host", "rt_guide_create", "rt_guide_destroy",
+    "rt_render_static", "rt_render_batch", "rt_autotune", "rt_sample_index", "rt_halton", "rt_divide_u64_host", "rt_guide_create", "rt_guide_destroy",
     "rt_guide_num_params", "rt_guide_get_params", "rt_guide_set_params", "rt_guide_state_size", "rt_guide_save",
     "rt_guide_load", "rt_guide_infer", "rt_guide_loss_grad", "rt_guide_train_step", "rt_last_error",
     "rt_status_string", "rt_gemm_bf16",
@@ -121,6 +126,8 @@ def _declare(L):
         "rt_film_resolve": [vp, vp, vp, vp],
         "rt_render": [vp, C.POINTER(rt_camera), u32, u32, vp, C.POINTER(rt_render_opts), vp],
         "rt_render_static": [vp, C.POINTER(rt_camera), u32, u32, u32, vp, vp, vp, C.POINTER(rt_render_opts), vp],
+        "rt_render_batch": [vp, i32, C.POINTER(rt_render_opts), vp],
+        "rt_autotune": [vp, i32, u32, C.POINTER(rt_render_opts), vp],
         "rt_sample_index": [u32, u32, vp, vp, vp, i64, vp, vp],
         "rt_halton": [u32, u32, u64, vp, i64, i32, vp, vp],
         "rt_divide_u64_host": [vp, i64, u32, vp],
@@ -378,6 +385,30 @@ def rt_render(scene: Scene, cam, spp: int, max_depth: int, film: Film, opts: Opt
     if st == RT_TIMEOUT and allow_timeout:
         return st
     return check(st)
+
+
+def _jobs(jobs):
+    """jobs: list of (Scene, camera, spp, max_depth, Film)."""
+    arr = (rt_render_job * len(jobs))()
+    for k, (sc, cam, spp, depth, film) in enumerate(jobs):
+        arr[k].scene, arr[k].camera, arr[k].spp, arr[k].max_depth, arr[k].film = sc.handle, make_camera(cam), spp, depth, film.handle
+    return arr
+
+
+def rt_render_batch(jobs, opts: Optional[rt_render_opts] = None, stream=None, allow_timeout: bool = False) -> int:
+    arr = _jobs(jobs)
+    o = opts if opts is not None else make_opts()
+    st = lib().rt_render_batch(arr, len(jobs), C.byref(o), _stream(stream))
+    if st == RT_TIMEOUT and allow_timeout:
+        return st
+    return check(st)
+
+
+def rt_autotune(jobs, sample_spp: int = 1, opts: Optional[rt_render_opts] = None, stream=None) -> rt_render_opts:
+    arr = _jobs(jobs)
+    o = opts if opts is not None else make_opts()
+    check(lib().rt_autotune(arr, len(jobs), sample_spp, C.byref(o), _stream(stream)))
+    return o
 
 
 def rt_render_static(scene: Scene, cam, spp: int, max_depth: int, first_iteration: int, sum_, sum2, count,

@@ -574,3 +574,41 @@ def random_rays(scene: SceneData, n: int, seed: int, kind: str = "incoherent", c
     else:
         raise ValueError(kind)
     return out
+
+
+# ------------------------------------------------------------ batched jobs
+def batch_jobs(seed: int = BASE_SEED + 5, n_jobs: int = 64, min_tris: int = 1000, max_tris: int = 500_000,
+               resolutions=(256, 512, 1024), spps=(16, 32, 64, 128, 256), depth_range=(4, 16), spp_divisor: int = 1,
+               res_divisor: int = 1):
+    """Independent seeded jobs for batched rendering: scene family drawn from
+    {Cornell-like, sphere field}, triangle count log-uniform in
+    [min_tris, max_tris], square resolution, samples per pixel and depth
+    drawn uniformly from the given sets. Returns a list of (SceneData,
+    Camera, spp, max_depth)."""
+    rng = Rng(seed)
+    jobs = []
+    for j in range(n_jobs):
+        fam = int(rng.u64(1)[0] % np.uint64(2))
+        target = math.exp(rng.uniform(1, math.log(min_tris), math.log(max_tris))[0])
+        res = resolutions[int(rng.u64(1)[0] % np.uint64(len(resolutions)))] // res_divisor
+        spp = max(1, spps[int(rng.u64(1)[0] % np.uint64(len(spps)))] // spp_divisor)
+        depth = int(depth_range[0] + rng.u64(1)[0] % np.uint64(depth_range[1] - depth_range[0] + 1))
+        jseed = seed * 1000 + j
+        if fam == 0 or target < 2500:
+            sd, cam = cornell_box(jseed)
+        else:
+            # spheres of seg x rings triangles plus a plane, scaled to the target
+            seg = 24
+            rings = 12
+            per = seg * 2 * (rings - 1)
+            plane = (40, 20)
+            n_sph = int(max(2, min(400, (target - 2 * plane[0] * plane[1]) / per)))
+            if n_sph * per < target / 2:
+                seg, rings = 64, 35
+                per = seg * 2 * (rings - 1)
+                n_sph = int(max(2, min(200, (target - 2 * plane[0] * plane[1]) / per)))
+            sd, cam = sphere_field(jseed, n_spheres=n_sph, seg=seg, rings=rings, plane_res=plane,
+                                   n_emissive_spheres=max(1, n_sph // 25), env_size=(256, 128))
+        cam = Camera(cam.eye, cam.look_at, cam.up, cam.vfov_deg, res, res)
+        jobs.append((sd, cam, spp, depth))
+    return jobs

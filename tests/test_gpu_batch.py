@@ -1,0 +1,96 @@
+"""Batched rendering of many scenes in one wavefront replayed as a CUDA graph
+(row A14, not in the paper), and the autotuner: every film equals what
+rt_render gives for that job alone."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1705_01263_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def make_jobs():
+    from paper_1705_01263_gb300 import rt
+    out = []
+    sd, cam = scenes.cornell_box()
+    out.append((rt.Scene(sd), cam, 8, 8))
+    sd, cam = scenes.sphere_field(n_spheres=20, plane_res=(60, 30), env_size=(256, 128), width=120, height=68)
+    out.append((rt.Scene(sd), cam, 4, 12))
+    sd, cam = scenes.furnace_sphere(res=32)
+    out.append((rt.Scene(sd), cam, 16, 4))
+    sd, cam = scenes.instanced_field(n_meshes=5, n_instances=40, total_tris=50_000, n_emissive=500, width=64,
+                                     height=36, min_tris=500, max_tris=3000)
+    out.append((rt.Scene(sd), cam, 6, 6))
+    return out
+
+
+def individual(jobs):
+    from paper_1705_01263_gb300 import rt
+    res = []
+    for s, cam, spp, d in jobs:
+        f = rt.Film(cam.width, cam.height)
+        rt.rt_render(s, cam, spp, d, f)
+        res.append(f.download())
+    return res
+
+
+@pytest.mark.parametrize("cap", [0, 5000])
+def test_batch_equals_individual_renders(cap):
+    from paper_1705_01263_gb300 import rt
+    jobs = make_jobs()
+    ref = individual(jobs)
+    films = [rt.Film(cam.width, cam.height) for _, cam, _, _ in jobs]
+    stats = rt.rt_stats()
+    rt.rt_render_batch([(s, cam, spp, d, f) for (s, cam, spp, d), f in zip(jobs, films)],
+                       rt.make_opts(max_paths=cap, stats=stats))
+    torch.cuda.synchronize()
+    total = sum(cam.width * cam.height * spp for _, cam, spp, _ in jobs)
+    assert stats.paths == total
+    for (s_ref, s2_ref, c_ref), f, (_, _, spp, _) in zip(ref, films, jobs):
+        s, s2, c = f.download()
+        assert np.array_equal(c, c_ref) and np.all(c == spp)
+        assert np.allclose(s, s_ref, rtol=1e-5, atol=1e-9)
+        assert f.next_iteration() == spp
+
+
+def test_batch_abort_and_resume():
+    from paper_1705_01263_gb300 import rt
+    jobs = make_jobs()
+    ref = individual(jobs)
+    films = [rt.Film(cam.width, cam.height) for _, cam, _, _ in jobs]
+    flag = np.ones(1, np.int32)
+    spec = [(s, cam, spp, d, f) for (s, cam, spp, d), f in zip(jobs, films)]
+    st = rt.rt_render_batch(spec, rt.make_opts(max_paths=20000, abort_flag=flag.ctypes.data), allow_timeout=True)
+    assert st == rt.RT_TIMEOUT
+    # resume: each film continues from its own next iteration
+    done = [f.next_iteration() for f in films]
+    assert min(done) < max(s for _, _, s, _ in jobs)
+    rest = []
+    for (s, cam, spp, d), f in zip(jobs, films):
+        # a job interrupted inside a pass resumes at its next task: render the
+        # remaining passes one job at a time
+        rt.rt_render(s, cam, spp - f.next_iteration(), d, f)
+    torch.cuda.synchronize()
+    for (s_ref, s2_ref, c_ref), f in zip(ref, films):
+        s, s2, c = f.download()
+        assert np.array_equal(c, c_ref)
+        assert np.allclose(s, s_ref, rtol=1e-5, atol=1e-9)
+
+
+def test_autotune_picks_a_candidate_and_renders():
+    from paper_1705_01263_gb300 import rt
+    jobs = make_jobs()
+    films = [rt.Film(cam.width, cam.height) for _, cam, _, _ in jobs]
+    spec = [(s, cam, spp, d, f) for (s, cam, spp, d), f in zip(jobs, films)]
+    o = rt.rt_autotune(spec, 1)
+    assert o.max_paths_in_flight in (1 << 20, 1 << 21, 1 << 22, 1 << 23)
+    o1 = rt.rt_autotune(spec[:1], 1)
+    assert o1.trace_kernel in (0, 1) and o1.tail_threshold in (1, 8192, 65536)
+    for f in films:
+        f.clear()
+    rt.rt_render_batch(spec, o)
+    torch.cuda.synchronize()
+    for f, (_, _, spp, _) in zip(films, jobs):
+        assert np.all(f.download()[2] == spp)
