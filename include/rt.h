@@ -192,7 +192,10 @@ rt_status rt_film_resolve(const rt_film *film, float *mean, float *var, void *st
 
 /* --------------------------------------------------------------- render */
 /* Accumulate iterations [next, next + spp) of the consistent QMC estimator
- * into `film` (film size must equal the camera's). max_depth = number of
+ * into `film` (film size must equal the camera's); next =
+ * rt_film_next_iteration(film). A film stopped inside an iteration (abort,
+ * time budget) first completes that iteration, so rendering
+ * total - next more iterations always ends exactly at `total`. max_depth = number of
  * scattering vertices (1 = direct lighting). Blocking with respect to the
  * host (it waits for each iteration set to finish); kernels run on `stream`.
  * Returns RT_TIMEOUT if the time budget or abort flag stopped it early: the

@@ -904,7 +904,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     RT_CUDA_TRY(cudaMemsetAsync(pool.ctrl, 0, sizeof(Ctrl), st));
     rt_stats stats{};
     auto t_start = std::chrono::steady_clock::now();
-    uint64_t t = film->next_task, t_end = film->next_task + (uint64_t)spp * WH;
+    uint64_t t = film->next_task, t_end = (film->next_task / WH + (uint64_t)spp) * WH;
     rt_status result = RT_OK;
     if (o.guide) {
         // Guided iteration sets: every bounce step reads the queue length,
@@ -932,7 +932,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         const int g_feat = grid_for(k_guide_features, 256, cap);
         rt_stats stats{};
         auto t_start = std::chrono::steady_clock::now();
-        uint64_t t = film->next_task, t_end = film->next_task + (uint64_t)spp * WH;
+        uint64_t t = film->next_task, t_end = (film->next_task / WH + (uint64_t)spp) * WH;
         rt_status result = RT_OK;
         while (t < t_end) {
             uint64_t n64;
@@ -1552,7 +1552,9 @@ extern "C" rt_status rt_render_batch(const rt_render_job *jobs, int32_t njobs, c
         B.count = J.film->count;
         B.WH = J.camera.width * J.camera.height;
         B.off = total;
-        B.ntask = (uint64_t)B.WH * J.spp;
+        // up to the end of pass (next iteration + spp): a film stopped inside
+        // a pass first completes it
+        B.ntask = (J.film->next_task / B.WH + (uint64_t)J.spp) * B.WH - J.film->next_task;
         B.film_task0 = J.film->next_task;
         total += B.ntask;
     }
