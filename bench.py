@@ -282,9 +282,11 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-scene batched workload")
     ap.add_argument("--spp", type=int, default=SPP)
     ap.add_argument("--out", default=None)
-    ap.add_argument("--trace-kernel", type=int, default=0, help="0 one ray per thread with warp fetch, 1 persistent warps refilling lanes")
+    ap.add_argument("--trace-kernel", type=int, default=0,
+                    help="0 one ray per thread with warp fetch, 1 persistent warps refilling lanes, 2 as 0 with a shared-memory stack")
     ap.add_argument("--megakernel-only", action="store_true", help="A/B baseline: megakernel per iteration set")
     ap.add_argument("--sort-by-material", action="store_true", help="A/B: material-sorted shading queue")
+    ap.add_argument("--sort-rays", action="store_true", help="A/B: reorder extension rays by octant and origin cell")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -308,7 +310,7 @@ def main():
 
     def opts(**kw):
         return rt.make_opts(seed=0, trace_kernel=args.trace_kernel, megakernel_only=args.megakernel_only,
-                            sort_by_material=args.sort_by_material, **kw)
+                            sort_by_material=args.sort_by_material, sort_rays=args.sort_rays, **kw)
 
     def render_step(stats=None, profile=0):
         o = opts(stats=stats, profile=profile)
@@ -407,7 +409,9 @@ def main():
                        "height": cam.height, "spp": args.spp, "max_depth": DEPTH,
                        "paths_per_step": paths_per_step, "l2": "flushed between steps (256 MiB write)",
                        "film": "FP64 sums", "parallelism": f"weak: {world} rank(s), disjoint iteration ranges",
-                       "trace_kernel": ["one ray per thread, warp fetch", "persistent warps, lane refill"][args.trace_kernel],
+                       "trace_kernel": ["one ray per thread, warp fetch", "persistent warps, lane refill",
+                                        "one ray per thread, shared-memory stack"][args.trace_kernel],
+                       "ray_order": "octant + origin cell" if args.sort_rays else "compaction order",
                        "schedule": "megakernel only" if args.megakernel_only else "wavefront + megakernel tail",
                        "shading_queue": "material-sorted" if args.sort_by_material else "compaction order"},
             "mrays_per_s": mrays,

@@ -148,7 +148,9 @@ typedef struct {
     rt_guide *guide;         /* online path guiding (NULL = off) */
     rt_stats *stats;         /* optional host output */
     int32_t profile;         /* 1: per-kernel event timing; 2: also count traversal work */
-    int32_t trace_kernel;    /* 0: one ray per thread, warps fetch 32 rays at a time; 1: persistent warps refilling idle lanes */
+    int32_t trace_kernel;    /* 0: one ray per thread, warps fetch 32 rays at a time; 1: persistent warps
+                              * refilling idle lanes; 2: as 0 with the stack top in shared memory */
+    int32_t sort_rays;       /* 1: reorder extension rays by direction octant and origin cell (A/B) */
 } rt_render_opts;
 
 /* ---------------------------------------------------------------- scene */

@@ -224,12 +224,14 @@ __global__ void __launch_bounds__(128) k_shade(RenderParams P, Pool pool, const 
 }
 
 // One ray per thread, traced to completion (A/B variant of the above).
-template <bool kCount>
-__global__ void __launch_bounds__(128) k_trace_ext_simple(DevScene sc, Pool pool) {
+template <bool kCount, bool kSmemStack = false>
+__global__ void __launch_bounds__(128) k_trace_ext_simple(DevScene sc, Pool pool, const uint32_t *sorted) {
     Ctrl *c = pool.ctrl;
     if (c->tail) return;
     const uint32_t n = c->n_ext;
-    const uint32_t *queue = pool.q[c->cur];
+    const uint32_t *queue = sorted ? sorted : pool.q[c->cur];
+    extern __shared__ uint2 s_stk[];
+    SharedStack sst{s_stk + threadIdx.x, (int)blockDim.x};
     bool overflow = false;
     uint32_t nodes = 0, tris = 0;
     for (;;) {
@@ -242,7 +244,9 @@ __global__ void __launch_bounds__(128) k_trace_ext_simple(DevScene sc, Pool pool
         Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, INFINITY};
         Hit h;
         h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
-        TraceResult tr = trace_scene<false>(sc, r, h);
+        TraceResult tr = (kSmemStack && !sc.two_level)
+                             ? traverse<false, SharedStack>(sc.nodes, sc.tris, 0u, r, h, 0u, &sst)
+                             : trace_scene<false>(sc, r, h);
         overflow |= tr.overflow;
         if (kCount) { nodes += tr.nodes; tris += tr.tris; }
         pool.hit[q] = make_float4(__uint_as_float(h.prim), h.t, h.b1, h.b2);
@@ -256,11 +260,13 @@ __global__ void __launch_bounds__(128) k_trace_ext_simple(DevScene sc, Pool pool
     }
 }
 
-template <bool kCount>
+template <bool kCount, bool kSmemStack = false>
 __global__ void __launch_bounds__(128) k_trace_shadow_simple(DevScene sc, Pool pool) {
     Ctrl *c = pool.ctrl;
     if (c->tail) return;
     const uint32_t n = c->n_shadow;
+    extern __shared__ uint2 s_stk[];
+    SharedStack sst{s_stk + threadIdx.x, (int)blockDim.x};
     bool overflow = false;
     uint32_t nodes = 0, tris = 0;
     for (;;) {
@@ -273,7 +279,9 @@ __global__ void __launch_bounds__(128) k_trace_shadow_simple(DevScene sc, Pool p
         Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, o.w};
         Hit h;
         h.prim = RT_MISS; h.inst = 0; h.t = INFINITY;
-        TraceResult tr = trace_scene<true>(sc, r, h);
+        TraceResult tr = (kSmemStack && !sc.two_level)
+                             ? traverse<true, SharedStack>(sc.nodes, sc.tris, 0u, r, h, 0u, &sst)
+                             : trace_scene<true>(sc, r, h);
         overflow |= tr.overflow;
         if (kCount) { nodes += tr.nodes; tris += tr.tris; }
         if (h.prim == RT_MISS) {
@@ -289,48 +297,82 @@ __global__ void __launch_bounds__(128) k_trace_shadow_simple(DevScene sc, Pool p
     }
 }
 
-// Material-sorted shading queue (A/B option): a counting sort of the
-// extension queue by the material of the hit (misses last) so that lanes of
-// a warp shade the same material. Histogram in shared memory per block,
-// exclusive scan in one block, then a scatter with one atomic per entry.
-__global__ void k_mat_hist(DevScene sc, Pool pool, uint32_t nmat, uint32_t *hist) {
+// Counting sorts of the extension queue (A/B options), with one shared
+// atomic per distinct key per warp in the histogram and one global atomic
+// per distinct key per warp in the scatter:
+//  - by material of the hit (misses last), so that lanes shade one material;
+//  - by ray direction octant and an 8 x 8 x 8 Morton cell of the origin in
+//    the scene box, so that neighbouring lanes traverse similar subtrees.
+struct MatKey {
+    DevScene sc;
+    uint32_t nmat;
+    RT_D uint32_t operator()(const Pool &pool, uint32_t q) const {
+        uint32_t prim = __float_as_uint(pool.hit[q].x);
+        return prim == RT_MISS ? nmat : __ldg(sc.tri_material + prim);
+    }
+};
+RT_D uint32_t spread3(uint32_t x) {   // 3 bits -> every third bit
+    return (x & 1u) | ((x & 2u) << 2) | ((x & 4u) << 4);
+}
+struct RayKey {
+    float3 lo, inv_ext;
+    RT_D uint32_t operator()(const Pool &pool, uint32_t q) const {
+        float4 o = pool.ray_o[q], d = pool.ray_d[q];
+        uint32_t cx = (uint32_t)fminf(7.f, fmaxf(0.f, (o.x - lo.x) * inv_ext.x * 8.f));
+        uint32_t cy = (uint32_t)fminf(7.f, fmaxf(0.f, (o.y - lo.y) * inv_ext.y * 8.f));
+        uint32_t cz = (uint32_t)fminf(7.f, fmaxf(0.f, (o.z - lo.z) * inv_ext.z * 8.f));
+        uint32_t oct = (d.x < 0.f ? 1u : 0u) | (d.y < 0.f ? 2u : 0u) | (d.z < 0.f ? 4u : 0u);
+        return (oct << 9) | spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2);
+    }
+};
+
+template <class Key>
+__global__ void k_sort_hist(Key key, Pool pool, uint32_t nkeys, uint32_t *hist) {
     extern __shared__ uint32_t sh_hist[];
     Ctrl *c = pool.ctrl;
     if (c->tail) return;
-    for (uint32_t k = threadIdx.x; k <= nmat; k += blockDim.x) sh_hist[k] = 0;
+    for (uint32_t k = threadIdx.x; k < nkeys; k += blockDim.x) sh_hist[k] = 0;
     __syncthreads();
     const uint32_t n = c->n_ext;
     const uint32_t *queue = pool.q[c->cur];
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += stride) {
         uint32_t i = base + lane_id();
-        uint32_t key = 0xFFFFFFFFu;
-        if (i < n) {
-            uint32_t prim = __float_as_uint(pool.hit[queue[i]].x);
-            key = prim == RT_MISS ? nmat : __ldg(sc.tri_material + prim);
-        }
-        // one shared atomic per distinct key in the warp
-        uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
-        if (i < n && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sh_hist[key], (uint32_t)__popc(peers));
+        uint32_t k = i < n ? key(pool, queue[i]) : 0xFFFFFFFFu;
+        uint32_t peers = __match_any_sync(0xFFFFFFFFu, k);
+        if (i < n && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sh_hist[k], (uint32_t)__popc(peers));
     }
     __syncthreads();
-    for (uint32_t k = threadIdx.x; k <= nmat; k += blockDim.x)
+    for (uint32_t k = threadIdx.x; k < nkeys; k += blockDim.x)
         if (sh_hist[k]) atomicAdd(&hist[k], sh_hist[k]);
 }
 
-__global__ void k_mat_scan(Pool pool, uint32_t nmat, uint32_t *hist) {
+// Exclusive scan of up to a few thousand counts in one block of 1024 threads.
+__global__ void k_sort_scan(Pool pool, uint32_t nkeys, uint32_t *hist) {
+    __shared__ uint32_t part[1024];
     if (pool.ctrl->tail) return;
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0;
-        for (uint32_t k = 0; k <= nmat; ++k) {
-            uint32_t v = hist[k];
-            hist[k] = acc;
-            acc += v;
-        }
+    const uint32_t per = (nkeys + blockDim.x - 1) / blockDim.x;
+    const uint32_t b = threadIdx.x * per, e = min(nkeys, b + per);
+    uint32_t sum = 0;
+    for (uint32_t k = b; k < e; ++k) sum += hist[k];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (uint32_t off = 1; off < blockDim.x; off <<= 1) {
+        uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t acc = part[threadIdx.x] - sum;
+    for (uint32_t k = b; k < e; ++k) {
+        uint32_t v = hist[k];
+        hist[k] = acc;
+        acc += v;
     }
 }
 
-__global__ void k_mat_scatter(DevScene sc, Pool pool, uint32_t nmat, uint32_t *offsets, uint32_t *sorted) {
+template <class Key>
+__global__ void k_sort_scatter(Key key, Pool pool, uint32_t *offsets, uint32_t *sorted) {
     Ctrl *c = pool.ctrl;
     if (c->tail) return;
     const uint32_t n = c->n_ext;
@@ -338,17 +380,15 @@ __global__ void k_mat_scatter(DevScene sc, Pool pool, uint32_t nmat, uint32_t *o
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += stride) {
         uint32_t i = base + lane_id();
-        uint32_t key = 0xFFFFFFFFu, q = 0;
+        uint32_t k = 0xFFFFFFFFu, q = 0;
         if (i < n) {
             q = queue[i];
-            uint32_t prim = __float_as_uint(pool.hit[q].x);
-            key = prim == RT_MISS ? nmat : __ldg(sc.tri_material + prim);
+            k = key(pool, q);
         }
-        // lanes with the same key reserve their slots with one global atomic
-        uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
+        uint32_t peers = __match_any_sync(0xFFFFFFFFu, k);
         uint32_t leader = __ffs(peers) - 1;
         uint32_t pos = 0;
-        if (i < n && lane_id() == leader) pos = atomicAdd(&offsets[key], (uint32_t)__popc(peers));
+        if (i < n && lane_id() == leader) pos = atomicAdd(&offsets[k], (uint32_t)__popc(peers));
         pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
         if (i < n) sorted[pos + __popc(peers & ((1u << lane_id()) - 1u))] = q;
     }
@@ -715,9 +755,9 @@ struct RenderCache {
     uint64_t dims_seed = ~0ull;
     int dims_n = 0;
     Ctrl *host_ctrl = nullptr;
-    // material-sorted shading queue
-    uint32_t *mat_hist = nullptr, *mat_sorted = nullptr;
-    uint32_t mat_cap = 0, mat_nmat = 0;
+    // sorted queues (A/B options)
+    uint32_t *sort_hist = nullptr, *sort_buf[2] = {nullptr, nullptr};
+    uint32_t sort_cap = 0, sort_nkeys = 0;
     // guided rendering
     uint32_t gcap = 0, gbatch = 0;
     float *gfeat = nullptr, *tr_feat = nullptr, *tr_wi = nullptr, *tr_w = nullptr;
@@ -727,7 +767,7 @@ struct RenderCache {
         if (dims) cudaFree(dims);
         if (host_ctrl) cudaFreeHost(host_ctrl);
         for (void *p : {(void *)gfeat, (void *)tr_feat, (void *)tr_wi, (void *)tr_w, (void *)grec, (void *)gnrec,
-                        (void *)mat_hist, (void *)mat_sorted})
+                        (void *)sort_hist, (void *)sort_buf[0], (void *)sort_buf[1]})
             if (p) cudaFree(p);
     }
 };
@@ -949,7 +989,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
             k_raygen<<<g_ray, 256, 0, st>>>(P, gpool, t, n, (uint32_t)WH, 0u);
             stats.kernel_launches += 1;
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
-                k_trace_ext_simple<false><<<g_trace, gbk, 0, st>>>(s->dev, gpool);
+                k_trace_ext_simple<false><<<g_trace, gbk, 0, st>>>(s->dev, gpool, nullptr);
                 RT_CUDA_TRY(cudaMemcpyAsync(rc->host_ctrl, gpool.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
                 RT_CUDA_TRY(cudaStreamSynchronize(st));
                 const uint32_t n_ext = rc->host_ctrl->n_ext;
@@ -1008,19 +1048,30 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     const int g_mega = grid_for(k_megakernel, gb, cap);
     const bool prof = o.profile >= 1, count = o.profile >= 2;
     const uint32_t nmat = s->num_materials;
-    const int g_hist = grid_for(k_mat_scatter, 256, cap);
-    if (o.sort_by_material && (rc->mat_cap < cap || rc->mat_nmat < nmat + 1)) {
-        if (rc->mat_hist) cudaFree(rc->mat_hist);
-        if (rc->mat_sorted) cudaFree(rc->mat_sorted);
-        rc->mat_hist = rc->mat_sorted = nullptr;
-        if (cudaMalloc(&rc->mat_hist, sizeof(uint32_t) * (nmat + 1)) != cudaSuccess ||
-            cudaMalloc(&rc->mat_sorted, sizeof(uint32_t) * (size_t)cap) != cudaSuccess) {
-            set_error("rt_render: material sort buffers");
+    const uint32_t nkeys_mat = nmat + 1, nkeys_ray = 8u * 512u;
+    const int g_hist = grid_for(k_sort_scatter<RayKey>, 256, cap);
+    if ((o.sort_by_material || o.sort_rays) && (rc->sort_cap < cap || rc->sort_nkeys < std::max(nkeys_mat, nkeys_ray))) {
+        for (void *p : {(void *)rc->sort_hist, (void *)rc->sort_buf[0], (void *)rc->sort_buf[1]})
+            if (p) cudaFree(p);
+        rc->sort_hist = rc->sort_buf[0] = rc->sort_buf[1] = nullptr;
+        const uint32_t nk = std::max(nkeys_mat, nkeys_ray);
+        if (cudaMalloc(&rc->sort_hist, sizeof(uint32_t) * nk) != cudaSuccess ||
+            cudaMalloc(&rc->sort_buf[0], sizeof(uint32_t) * (size_t)cap) != cudaSuccess ||
+            cudaMalloc(&rc->sort_buf[1], sizeof(uint32_t) * (size_t)cap) != cudaSuccess) {
+            set_error("rt_render: sort buffers");
             return RT_OOM;
         }
-        rc->mat_cap = cap;
-        rc->mat_nmat = nmat + 1;
+        rc->sort_cap = cap;
+        rc->sort_nkeys = nk;
     }
+    RayKey rkey;
+    rkey.lo = s->dev.bb_lo;
+    rkey.inv_ext = make_float3(1.f / fmaxf(s->dev.bb_hi.x - s->dev.bb_lo.x, 1e-20f),
+                               1.f / fmaxf(s->dev.bb_hi.y - s->dev.bb_lo.y, 1e-20f),
+                               1.f / fmaxf(s->dev.bb_hi.z - s->dev.bb_lo.z, 1e-20f));
+    MatKey mkey{s->dev, nmat};
+    const size_t smem_stk = (size_t)kSharedEntries * gb * sizeof(uint2);
+    const int g_simple_sm = grid_persistent(k_trace_ext_simple<false, true>, gb, smem_stk);
     // event pairs per timed launch: kind 0 trace, 1 shade, 2 shadow, 3 megakernel, 4 other
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> evs;
     auto mark = [&](int kind) -> cudaEvent_t {
@@ -1052,25 +1103,39 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         ++stats.kernel_launches;
         if (!o.megakernel_only) {
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
+                const uint32_t *rsorted = nullptr;
+                if (o.sort_rays && v >= 2) {
+                    e = mark(4);
+                    RT_CUDA_TRY(cudaMemsetAsync(rc->sort_hist, 0, sizeof(uint32_t) * nkeys_ray, st));
+                    k_sort_hist<RayKey><<<g_hist, 256, nkeys_ray * sizeof(uint32_t), st>>>(rkey, pool, nkeys_ray, rc->sort_hist);
+                    k_sort_scan<<<1, 1024, 0, st>>>(pool, nkeys_ray, rc->sort_hist);
+                    k_sort_scatter<RayKey><<<g_hist, 256, 0, st>>>(rkey, pool, rc->sort_hist, rc->sort_buf[0]);
+                    done(e);
+                    rsorted = rc->sort_buf[0];
+                    stats.kernel_launches += 3;
+                }
                 e = mark(0);
                 if (o.trace_kernel == 0) {
-                    if (count) k_trace_ext_simple<true><<<g_simple, gb, 0, st>>>(s->dev, pool);
-                    else k_trace_ext_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool);
+                    if (count) k_trace_ext_simple<true><<<g_simple, gb, 0, st>>>(s->dev, pool, rsorted);
+                    else k_trace_ext_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool, rsorted);
+                } else if (o.trace_kernel == 2) {
+                    if (count) k_trace_ext_simple<true, true><<<g_simple_sm, gb, smem_stk, st>>>(s->dev, pool, rsorted);
+                    else k_trace_ext_simple<false, true><<<g_simple_sm, gb, smem_stk, st>>>(s->dev, pool, rsorted);
                 } else if (count) {
                     k_trace_ext<true><<<g_trace, gb, smem, st>>>(s->dev, pool);
                 } else {
                     k_trace_ext<false><<<g_trace, gb, smem, st>>>(s->dev, pool);
                 }
                 done(e);
-                const uint32_t *sorted = nullptr;
+                const uint32_t *sorted = rsorted;
                 if (o.sort_by_material) {
                     e = mark(4);
-                    RT_CUDA_TRY(cudaMemsetAsync(rc->mat_hist, 0, sizeof(uint32_t) * (nmat + 1), st));
-                    k_mat_hist<<<g_hist, 256, (nmat + 1) * sizeof(uint32_t), st>>>(s->dev, pool, nmat, rc->mat_hist);
-                    k_mat_scan<<<1, 32, 0, st>>>(pool, nmat, rc->mat_hist);
-                    k_mat_scatter<<<g_hist, 256, 0, st>>>(s->dev, pool, nmat, rc->mat_hist, rc->mat_sorted);
+                    RT_CUDA_TRY(cudaMemsetAsync(rc->sort_hist, 0, sizeof(uint32_t) * nkeys_mat, st));
+                    k_sort_hist<MatKey><<<g_hist, 256, nkeys_mat * sizeof(uint32_t), st>>>(mkey, pool, nkeys_mat, rc->sort_hist);
+                    k_sort_scan<<<1, 1024, 0, st>>>(pool, nkeys_mat, rc->sort_hist);
+                    k_sort_scatter<MatKey><<<g_hist, 256, 0, st>>>(mkey, pool, rc->sort_hist, rc->sort_buf[1]);
                     done(e);
-                    sorted = rc->mat_sorted;
+                    sorted = rc->sort_buf[1];
                     stats.kernel_launches += 3;
                 }
                 e = mark(1);
@@ -1080,6 +1145,9 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
                 if (o.trace_kernel == 0) {
                     if (count) k_trace_shadow_simple<true><<<g_simple, gb, 0, st>>>(s->dev, pool);
                     else k_trace_shadow_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool);
+                } else if (o.trace_kernel == 2) {
+                    if (count) k_trace_shadow_simple<true, true><<<g_simple_sm, gb, smem_stk, st>>>(s->dev, pool);
+                    else k_trace_shadow_simple<false, true><<<g_simple_sm, gb, smem_stk, st>>>(s->dev, pool);
                 } else if (count) {
                     k_trace_shadow<true><<<g_shadow, gb, smem, st>>>(s->dev, pool);
                 } else {
@@ -1301,10 +1369,10 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
         k_raygen<<<g_ray, 256, 0, st>>>(P, pool, t, n, (uint32_t)WH, tail);
         if (!o.megakernel_only) {
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
-                if (o.trace_kernel == 0) k_trace_ext_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool);
+                if (o.trace_kernel != 1) k_trace_ext_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool, nullptr);
                 else k_trace_ext<false><<<g_trace, gb, smem, st>>>(s->dev, pool);
                 k_shade<<<g_shade, gb, 0, st>>>(P, pool, nullptr);
-                if (o.trace_kernel == 0) k_trace_shadow_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool);
+                if (o.trace_kernel != 1) k_trace_shadow_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool);
                 else k_trace_shadow<false><<<g_shadow, gb, smem, st>>>(s->dev, pool);
                 k_step_end<<<1, 1, 0, st>>>(pool);
                 stats.kernel_launches += 4;

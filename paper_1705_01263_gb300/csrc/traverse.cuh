@@ -246,13 +246,33 @@ struct TraceResult {
 // Closest hit (any_hit = false) or any hit (true) against one BVH.
 // On return hit.prim == RT_MISS if nothing was found; hit.t, b1, b2 valid
 // otherwise. `hit` may hold a previous best (used for two-level scenes).
-template <bool kAnyHit>
+// Traversal stack in a thread-local array (registers / local memory).
+struct LocalStack {
+    uint2 e[kStackSize];
+    RT_HD uint2 &operator[](int i) { return e[i]; }
+};
+#ifdef __CUDACC__
+// Traversal stack whose top kSharedEntries entries live in shared memory,
+// entry-major so that the lanes of a warp touch consecutive words
+// (conflict-free); deeper entries spill to a thread-local array. `base`
+// points at this thread's first shared entry and `stride` is the block size.
+constexpr int kSharedEntries = 16;
+struct SharedStack {
+    uint2 *base;
+    int stride;
+    uint2 deep[kStackSize - kSharedEntries];
+    __device__ uint2 &operator[](int i) { return i < kSharedEntries ? base[i * stride] : deep[i - kSharedEntries]; }
+};
+#endif
+
+template <bool kAnyHit, class Stack = LocalStack>
 RT_HD TraceResult traverse(const uint4 *nodes, const float4 *tris, uint32_t root, const Ray &ray, Hit &hit,
-                           uint32_t inst = 0u) {
+                           uint32_t inst = 0u, Stack *ext_stack = nullptr) {
     TraceResult res{false, 0u, 0u};
     RayPre rp = prepare(ray);
     float tbest = hit.prim == RT_MISS ? ray.tmax : hit.t;
-    uint2 stack[kStackSize];
+    Stack own;
+    Stack &stack = ext_stack ? *ext_stack : own;
     int sp = 0;
     // a virtual group holding the root as its only internal child (slot 0)
     uint2 ng = make_uint2(root, (1u << (24 + (0u ^ rp.oct))) | 1u);

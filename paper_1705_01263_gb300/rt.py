@@ -70,7 +70,7 @@ class rt_render_opts(C.Structure):
                 ("megakernel_only", C.c_int32), ("sort_by_material", C.c_int32),
                 ("tail_threshold", C.c_uint32), ("block_size", C.c_uint32),
                 ("abort_flag", C.c_void_p), ("guide", C.c_void_p), ("stats", C.POINTER(rt_stats)),
-                ("profile", C.c_int32), ("trace_kernel", C.c_int32)]
+                ("profile", C.c_int32), ("trace_kernel", C.c_int32), ("sort_rays", C.c_int32)]
 
 
 class rt_render_job(C.Structure):
@@ -359,7 +359,7 @@ def make_camera(cam) -> rt_camera:
 def make_opts(sigma: float = 0.5, rr: bool = False, mis_mode: int = 0, seed: int = 0, time_budget_ms: float = 0.0,
               max_paths: int = 0, megakernel_only: bool = False, sort_by_material: bool = False,
               tail_threshold: int = 0, abort_flag=None, guide=None, stats: Optional[rt_stats] = None,
-              profile: int = 0, trace_kernel: int = 0):
+              profile: int = 0, trace_kernel: int = 0, sort_rays: bool = False):
     o = rt_render_opts()
     o.filter_sigma = sigma if sigma > 0 else -1.0
     o.rr_enable, o.mis_mode, o.seed = int(rr), mis_mode, seed
@@ -374,6 +374,7 @@ def make_opts(sigma: float = 0.5, rr: bool = False, mis_mode: int = 0, seed: int
         o.stats = C.pointer(stats)
     o.profile = profile
     o.trace_kernel = trace_kernel
+    o.sort_rays = int(sort_rays)
     return o
 
 

@@ -143,10 +143,12 @@ def test_material_sorted_queue_gives_the_same_image():
     sd, cam = scenes.sphere_field(n_spheres=40, plane_res=(120, 60), env_size=(512, 256), width=160, height=90)
     s = rt.Scene(sd)
     a, _, _ = gpu_render(s, cam, 4, 16)
-    b, st, _ = gpu_render(s, cam, 4, 16, sort_by_material=True)
     sa, s2a, ca = a.download()
-    sb, s2b, cb = b.download()
-    assert np.array_equal(ca, cb) and np.array_equal(sa, sb) and np.array_equal(s2a, s2b)
+    for kw in (dict(sort_by_material=True), dict(sort_rays=True), dict(trace_kernel=2),
+               dict(sort_rays=True, sort_by_material=True, trace_kernel=2)):
+        b, st, _ = gpu_render(s, cam, 4, 16, **kw)
+        sb, s2b, cb = b.download()
+        assert np.array_equal(ca, cb) and np.array_equal(sa, sb) and np.array_equal(s2a, s2b), kw
 
 
 def test_wavefront_equals_megakernel():
