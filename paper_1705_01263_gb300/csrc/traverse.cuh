@@ -204,8 +204,8 @@ RT_HD float qbyte(uint32_t lo4, uint32_t hi4, int i) {
 
 // Intersect the 8 child boxes of node (n0..n4); returns the internal-child
 // hit bits at 24 + (slot ^ oct) and, through tri_bits, the triangle bits.
-RT_HD uint32_t intersect_children(const RayPre &rp, uint4 n0, uint4 n1, uint4 n2, uint4 n3, uint4 n4,
-                                  float tmin, float tmax, uint32_t &tri_bits) {
+RT_HD uint32_t intersect_children_scalar(const RayPre &rp, uint4 n0, uint4 n1, uint4 n2, uint4 n3, uint4 n4,
+                                         float tmin, float tmax, uint32_t &tri_bits) {
     V3 p = v3(as_float(n0.x), as_float(n0.y), as_float(n0.z));
     int ex = (int)(int8_t)(n0.w & 0xFF), ey = (int)(int8_t)((n0.w >> 8) & 0xFF),
         ez = (int)(int8_t)((n0.w >> 16) & 0xFF);
@@ -236,6 +236,94 @@ RT_HD uint32_t intersect_children(const RayPre &rp, uint4 n0, uint4 n1, uint4 n2
     tri_bits = tris;
     return inner;
 }
+
+#ifdef __CUDA_ARCH__
+// Blackwell packed FP32 pairs: the near and far plane of one axis go through
+// one fma.rn.f32x2 (and the byte decode through one add.rn.f32x2); each lane
+// of the pair is the IEEE result of the scalar operation, so the outcome is
+// bit-identical to intersect_children_scalar. Three-input min / max fold the
+// slab reductions.
+__device__ __forceinline__ uint64_t pk2(uint32_t lo, uint32_t hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(uint64_t v, float &lo, float &hi) {
+    uint32_t a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(a), "=r"(b) : "l"(v));
+    lo = __uint_as_float(a);
+    hi = __uint_as_float(b);
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ float max3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float min3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t intersect_children(const RayPre &rp, uint4 n0, uint4 n1, uint4 n2, uint4 n3,
+                                                       uint4 n4, float tmin, float tmax, uint32_t &tri_bits) {
+    const float px = __uint_as_float(n0.x), py = __uint_as_float(n0.y), pz = __uint_as_float(n0.z);
+    const int ex = (int)(int8_t)(n0.w & 0xFF), ey = (int)(int8_t)((n0.w >> 8) & 0xFF),
+              ez = (int)(int8_t)((n0.w >> 16) & 0xFF);
+    const uint32_t imask = n0.w >> 24;
+    const float ax = exp2i(ex) * rp.inv.x, ay = exp2i(ey) * rp.inv.y, az = exp2i(ez) * rp.inv.z;
+    const float bx = (px - rp.o.x) * rp.inv.x, by = (py - rp.o.y) * rp.inv.y, bz = (pz - rp.o.z) * rp.inv.z;
+    const uint64_t AX = pk2(__float_as_uint(ax), __float_as_uint(ax)), BX = pk2(__float_as_uint(bx), __float_as_uint(bx));
+    const uint64_t AY = pk2(__float_as_uint(ay), __float_as_uint(ay)), BY = pk2(__float_as_uint(by), __float_as_uint(by));
+    const uint64_t AZ = pk2(__float_as_uint(az), __float_as_uint(az)), BZ = pk2(__float_as_uint(bz), __float_as_uint(bz));
+    const uint64_t MAG = pk2(0xCB000000u, 0xCB000000u);   // (-2^23, -2^23)
+    const bool sx = rp.inv.x < 0.f, sy = rp.inv.y < 0.f, sz = rp.inv.z < 0.f;
+    const uint32_t nxl = sx ? n2.z : n2.x, nxh = sx ? n2.w : n2.y, fxl = sx ? n2.x : n2.z, fxh = sx ? n2.y : n2.w;
+    const uint32_t nyl = sy ? n3.z : n3.x, nyh = sy ? n3.w : n3.y, fyl = sy ? n3.x : n3.z, fyh = sy ? n3.y : n3.w;
+    const uint32_t nzl = sz ? n4.z : n4.x, nzh = sz ? n4.w : n4.y, fzl = sz ? n4.x : n4.z, fzh = sz ? n4.y : n4.w;
+    uint32_t inner = 0, tris = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t sel = 0x7540u + (uint32_t)(i & 3);
+        const uint32_t wnx = i < 4 ? nxl : nxh, wfx = i < 4 ? fxl : fxh;
+        const uint32_t wny = i < 4 ? nyl : nyh, wfy = i < 4 ? fyl : fyh;
+        const uint32_t wnz = i < 4 ? nzl : nzh, wfz = i < 4 ? fzl : fzh;
+        uint64_t qx = add2(pk2(__byte_perm(wnx, 0x4B000000u, sel), __byte_perm(wfx, 0x4B000000u, sel)), MAG);
+        uint64_t qy = add2(pk2(__byte_perm(wny, 0x4B000000u, sel), __byte_perm(wfy, 0x4B000000u, sel)), MAG);
+        uint64_t qz = add2(pk2(__byte_perm(wnz, 0x4B000000u, sel), __byte_perm(wfz, 0x4B000000u, sel)), MAG);
+        float nx, fx, ny, fy, nz, fz;
+        upk2(fma2(qx, AX, BX), nx, fx);
+        upk2(fma2(qy, AY, BY), ny, fy);
+        upk2(fma2(qz, AZ, BZ), nz, fz);
+        float t0 = fmaxf(max3(nx, ny, nz), tmin);
+        float t1 = fminf(min3(fx, fy, fz), tmax);
+        bool hit = t0 <= t1 * 1.000001f;
+        uint32_t meta = ((i < 4 ? n1.z : n1.w) >> (8 * (i & 3))) & 0xFFu;
+        uint32_t is_inner = (imask >> i) & 1u;
+        uint32_t ib = (hit && meta && is_inner) ? (1u << (24 + (i ^ rp.oct))) : 0u;
+        uint32_t tb = (hit && meta && !is_inner) ? ((meta >> 5) << (meta & 31u)) : 0u;
+        inner |= ib;
+        tris |= tb;
+    }
+    tri_bits = tris;
+    return inner;
+}
+#else
+RT_HD uint32_t intersect_children(const RayPre &rp, uint4 n0, uint4 n1, uint4 n2, uint4 n3, uint4 n4, float tmin,
+                                  float tmax, uint32_t &tri_bits) {
+    return intersect_children_scalar(rp, n0, n1, n2, n3, n4, tmin, tmax, tri_bits);
+}
+#endif
 
 struct TraceResult {
     bool overflow;
