@@ -33,6 +33,11 @@ METRIC = "Mpaths/s"
 UNIT = "Mpaths/s"
 WORKLOAD = "sphere-field 1M tris, 1920x1080, 64 spp, depth 16"
 SPP, DEPTH = 64, 16
+# DRAM bytes (read + write) per extension ray of k_trace_ext_simple, measured
+# with ncu (dram__bytes_read.sum + dram__bytes_write.sum) over all 17 launches
+# of one 4-spp render of the same scene, caches as the program left them:
+# 1,893.6 MB for 19,024,330 rays.
+TRACE_EXT_DRAM_BYTES_PER_RAY = 99.5
 
 
 def env_rank():
@@ -233,6 +238,38 @@ def batched(spp_divisor=16):
             "graph_replays": st.waves, "autotuned_pool": o.max_paths_in_flight, "scene_setup_s": setup_s}
 
 
+def traversal_only(sd, cam, scene, n=1 << 22, reps=5):
+    """Traversal-only throughput through rt_trace on synthetic ray batches of
+    the main scene, 2^22 rays each: camera rays in scanline order (coherent,
+    closest hit), rays leaving random surface points in uniform directions
+    (incoherent, standing in for diffuse bounces, closest hit) and segments
+    between two surface points (shadow rays, any hit). Device time per batch
+    with CUDA events, L2 flushed between batches; median of `reps`."""
+    import torch
+    from paper_1705_01263_gb300 import rt, scenes
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, kind, seed, any_hit in (("camera", "camera", 31, False), ("diffuse", "incoherent", 32, False),
+                                      ("shadow", "shadow", 33, True)):
+        rays = torch.from_numpy(scenes.random_rays(sd, n, seed, kind, cam)).cuda()
+        hits, soa = rt.rt_trace(scene, rays, any_hit)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(2 + reps):
+            flush.zero_()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            rt.rt_trace(scene, soa, any_hit, hits=hits)
+            ev1.record()
+            ev1.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+        med = statistics.median(ms[2:])
+        out[name] = {"rays": n, "any_hit": any_hit, "ms": med, "Mrays_per_s": n / med / 1e3,
+                     "hit_fraction": float((hits[0] != -1).float().mean().item())}
+        del rays, soa, hits
+    return out
+
+
 def C_pointer(x):
     import ctypes
     return ctypes.pointer(x)
@@ -280,6 +317,11 @@ def main():
     ap.add_argument("--no-guided", action="store_true", help="skip the guided-vs-plain time-to-RMSE run")
     ap.add_argument("--no-many-lights", action="store_true", help="skip the instanced many-light workload")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-scene batched workload")
+    ap.add_argument("--no-traversal", action="store_true", help="skip the traversal-only ray batches")
+    ap.add_argument("--pool", type=int, default=0, help="paths in flight per iteration set (0 = library default)")
+    ap.add_argument("--tail", type=int, default=0, help="live-path count below which the megakernel finishes a set (0 = default)")
+    ap.add_argument("--render-once", action="store_true",
+                    help="profiling aid: one untimed render of --spp, print its ray and launch counts, exit")
     ap.add_argument("--spp", type=int, default=SPP)
     ap.add_argument("--out", default=None)
     ap.add_argument("--trace-kernel", type=int, default=0,
@@ -310,13 +352,22 @@ def main():
 
     def opts(**kw):
         return rt.make_opts(seed=0, trace_kernel=args.trace_kernel, megakernel_only=args.megakernel_only,
-                            sort_by_material=args.sort_by_material, sort_rays=args.sort_rays, **kw)
+                            sort_by_material=args.sort_by_material, sort_rays=args.sort_rays,
+                            max_paths=args.pool, tail_threshold=args.tail, **kw)
 
     def render_step(stats=None, profile=0):
         o = opts(stats=stats, profile=profile)
         rt.rt_render(scene, cam, args.spp, DEPTH, film, o)
 
     film.seek(base_iter)
+    if args.render_once:
+        st = rt.rt_stats()
+        render_step(st)
+        torch.cuda.synchronize()
+        print(json.dumps({"render_once": WORKLOAD.replace("64 spp", f"{args.spp} spp"), "paths": st.paths,
+                          "extension_rays": st.extension_rays, "shadow_rays": st.shadow_rays,
+                          "trace_launches": st.trace_launches, "wavefront_steps": st.wavefront_steps}), flush=True)
+        return 0
     for _ in range(args.warmup):
         render_step()
     torch.cuda.synchronize()
@@ -392,6 +443,9 @@ def main():
     ml = None
     if rank == 0 and not args.no_many_lights:
         ml = many_lights()
+    trv = None
+    if rank == 0 and not args.no_traversal:
+        trv = traversal_only(sd, cam, scene)
     bt = None
     if rank == 0 and not args.no_batched:
         bt = batched()
@@ -418,7 +472,10 @@ def main():
             "rays_per_path": (ext + shd) / (paths_per_step * args.steps),
             "roofline": {"bound": "hbm", "kernel": "k_trace_ext (closest-hit BVH8 traversal)",
                          "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                         "frac": (achieved_gbs / hbm) if achieved_gbs else None, "traffic": None,
+                         "frac": (achieved_gbs / hbm) if achieved_gbs else None,
+                         "traffic": TRACE_EXT_DRAM_BYTES_PER_RAY * ext_rays_timed / max(1, tl),
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per extension ray "
+                                           "(4-spp capture) x rays per timed launch",
                          "peak_source": f"{peak_src} hbm_gbs",
                          "bytes_per_ray": bytes_per_ray, "nodes_per_ray": nodes_per_ray,
                          "tris_per_ray": tris_per_ray, "launches": tl,
@@ -432,6 +489,7 @@ def main():
             "guided_vs_plain": gvp,
             "many_lights": ml,
             "batched": bt,
+            "traversal_only": trv,
             "wall_s": t_wall,
         }
         s = json.dumps(line)

@@ -60,6 +60,12 @@ HaltonDim make_dim(uint32_t base, uint32_t f) {
     uint32_t bits = 0;
     while ((1u << bits) < base) ++bits;
     h.bits = bits;
+    // w[0] = floor(2^64 / b) (b > 2 is odd, so 2^64 is not a multiple of it),
+    // w[k + 1] = floor(w[k] / b)
+    if (base > 2) {
+        h.w[0] = ~0ull / base;
+        for (int k = 1; k < kMaxDigits; ++k) h.w[k] = h.w[k - 1] / base;
+    }
     return h;
 }
 

@@ -65,12 +65,17 @@ RT_HD uint32_t div32(uint32_t n, const Divisor &v) {
     return (t + ((n - t) >> 1)) >> v.sh;
 }
 
-// One Halton dimension: base, its divisor, digit scramble multiplier and the
-// number of bits that hold one digit.
+// Most base-b digits of a 64-bit index (b = 3: 3^40 < 2^64 < 3^41).
+constexpr int kMaxDigits = 41;
+
+// One Halton dimension: base, its divisor, digit scramble multiplier, the
+// number of bits that hold one digit, and the digit weights
+// w[k] = floor(2^64 / b^(k+1)) of the fixed-point evaluation.
 struct HaltonDim {
     Divisor div;
     uint32_t f;     // pi(d) = (f * d) mod b
     uint32_t bits;  // ceil(log2 b)
+    uint64_t w[kMaxDigits];
 };
 
 RT_HD uint32_t scramble_digit(uint32_t d, const HaltonDim &h) {
@@ -78,18 +83,9 @@ RT_HD uint32_t scramble_digit(uint32_t d, const HaltonDim &h) {
     return fd - div32(fd, h.div) * h.div.d;
 }
 
-// floor(2^32 * phi_b(i)) with the digit permutation of `h`.
-RT_HD uint32_t radical_inverse(uint64_t i, const HaltonDim &h) {
+// floor(2^32 * phi_b(i)) by Horner's rule (b > 2), exact for every index.
+RT_HD uint32_t radical_inverse_horner(uint64_t i, const HaltonDim &h) {
     const uint32_t b = h.div.d;
-    if (b == 2u) {
-#ifdef __CUDA_ARCH__
-        return __brev((uint32_t)i);
-#else
-        uint32_t x = (uint32_t)i, r = 0;
-        for (int k = 0; k < 32; ++k) r |= ((x >> k) & 1u) << (31 - k);
-        return r;
-#endif
-    }
     const uint32_t bits = h.bits;
     const uint64_t mask = (1ull << bits) - 1ull;
     uint64_t lo = 0, hi = 0;
@@ -120,6 +116,49 @@ RT_HD uint32_t radical_inverse(uint64_t i, const HaltonDim &h) {
         y = div64(num, h.div);
     }
     return (uint32_t)y;
+}
+
+// floor(2^32 * phi_b(i)) with the digit permutation of `h`.
+//
+// Fast path: the 64-bit fixed-point sum S = sum_k pi(d_k) w[k] with
+// w[k] = floor(2^64 / b^(k+1)) under-estimates T = 2^64 phi_b(i) by
+// T - S = sum_k pi(d_k) frac(2^64 / b^(k+1)) < n (b - 1) for n digits, and
+// T < 2^64 so S cannot wrap. Hence floor(T / 2^32) = floor(S / 2^32)
+// whenever (S mod 2^32) + n (b - 1) <= 2^32; otherwise (about one index in
+// 2^32 / (n b)) the exact Horner evaluation decides. One digit costs a
+// 32-bit multiply-high division, the scramble and one 64 x 32-bit
+// multiply-add instead of two divisions and a 128-bit digit buffer.
+RT_HD uint32_t radical_inverse(uint64_t i, const HaltonDim &h) {
+    const uint32_t b = h.div.d;
+    if (b == 2u) {
+#ifdef __CUDA_ARCH__
+        return __brev((uint32_t)i);
+#else
+        uint32_t x = (uint32_t)i, r = 0;
+        for (int k = 0; k < 32; ++k) r |= ((x >> k) & 1u) << (31 - k);
+        return r;
+#endif
+    }
+    const uint64_t i_in = i;
+    uint64_t S = 0;
+    uint32_t n = 0;
+    while (i >> 32) {
+        uint64_t q = div64(i, h.div);
+        uint32_t d = (uint32_t)(i - q * b);
+        i = q;
+        S += (uint64_t)scramble_digit(d, h) * h.w[n];
+        ++n;
+    }
+    uint32_t i32 = (uint32_t)i;
+    while (i32) {
+        uint32_t q = div32(i32, h.div);
+        uint32_t d = i32 - q * b;
+        i32 = q;
+        S += (uint64_t)scramble_digit(d, h) * h.w[n];
+        ++n;
+    }
+    if ((uint64_t)(uint32_t)S + (uint64_t)n * (b - 1u) <= (1ull << 32)) return (uint32_t)(S >> 32);
+    return radical_inverse_horner(i_in, h);
 }
 
 // FP32 sample value from the 32-bit fraction: (u >> 8) * 2^-24, exact.
@@ -156,9 +195,14 @@ RT_HD uint64_t pixel_base_index(const Enum &e, uint32_t x, uint32_t y) {
 
 // In-pixel offset dimensions 0 and 1 (unscrambled).
 RT_HD uint32_t dim0_bits(const Enum &e, uint64_t i) {
-    HaltonDim two{};
-    two.div.d = 2;
-    return radical_inverse(i >> e.k, two);
+    const uint32_t x = (uint32_t)(i >> e.k);
+#ifdef __CUDA_ARCH__
+    return __brev(x);
+#else
+    uint32_t r = 0;
+    for (int k = 0; k < 32; ++k) r |= ((x >> k) & 1u) << (31 - k);
+    return r;
+#endif
 }
 RT_HD uint32_t dim1_bits(const Enum &e, uint64_t i) {
     uint64_t q = e.l ? div64(i, e.div_p3) : i;

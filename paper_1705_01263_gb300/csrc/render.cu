@@ -183,7 +183,9 @@ __global__ void __launch_bounds__(128) k_trace_ext(DevScene sc, Pool pool) {
     }
 }
 
-__global__ void __launch_bounds__(128) k_shade(RenderParams P, Pool pool, const uint32_t *sorted) {
+// Capped at 64 registers (8 blocks of 128 per SM): the kernel is latency
+// bound, and the extra resident warps outweigh a few spilled registers.
+__global__ void __launch_bounds__(128, 8) k_shade(RenderParams P, Pool pool, const uint32_t *sorted) {
     Ctrl *c = pool.ctrl;
     if (c->tail) return;
     const uint32_t n = c->n_ext;
@@ -224,7 +226,10 @@ __global__ void __launch_bounds__(128) k_shade(RenderParams P, Pool pool, const 
 }
 
 // One ray per thread, traced to completion (A/B variant of the above).
-template <bool kCount, bool kSmemStack = false>
+// kTwoLevel selects the instanced (two-level) traversal at compile time: the
+// single-level kernels carry none of its state and need about a third fewer
+// registers, which raises the resident warps per SM from 20 to 32.
+template <bool kCount, bool kSmemStack, bool kTwoLevel>
 __global__ void __launch_bounds__(128) k_trace_ext_simple(DevScene sc, Pool pool, const uint32_t *sorted) {
     Ctrl *c = pool.ctrl;
     if (c->tail) return;
@@ -244,13 +249,13 @@ __global__ void __launch_bounds__(128) k_trace_ext_simple(DevScene sc, Pool pool
         Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, INFINITY};
         Hit h;
         h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
-        TraceResult tr = (kSmemStack && !sc.two_level)
-                             ? traverse<false, SharedStack>(sc.nodes, sc.tris, 0u, r, h, 0u, &sst)
-                             : trace_scene<false>(sc, r, h);
+        TraceResult tr = kTwoLevel    ? traverse_tlas<false>(sc, r, h)
+                         : kSmemStack ? traverse<false, SharedStack>(sc.nodes, sc.tris, 0u, r, h, 0u, &sst)
+                                      : traverse<false>(sc.nodes, sc.tris, 0u, r, h);
         overflow |= tr.overflow;
         if (kCount) { nodes += tr.nodes; tris += tr.tris; }
         pool.hit[q] = make_float4(__uint_as_float(h.prim), h.t, h.b1, h.b2);
-        if (sc.two_level) pool.hit_inst[q] = h.inst;
+        if (kTwoLevel) pool.hit_inst[q] = h.inst;
     }
     if (overflow) atomicOr(&c->overflow, 1u);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&c->ext_rays, (unsigned long long)n);
@@ -260,8 +265,8 @@ __global__ void __launch_bounds__(128) k_trace_ext_simple(DevScene sc, Pool pool
     }
 }
 
-template <bool kCount, bool kSmemStack = false>
-__global__ void __launch_bounds__(128) k_trace_shadow_simple(DevScene sc, Pool pool) {
+template <bool kCount, bool kSmemStack, bool kTwoLevel>
+__global__ void __launch_bounds__(128) k_trace_shadow_simple(DevScene sc, Pool pool, const uint32_t *) {
     Ctrl *c = pool.ctrl;
     if (c->tail) return;
     const uint32_t n = c->n_shadow;
@@ -279,9 +284,9 @@ __global__ void __launch_bounds__(128) k_trace_shadow_simple(DevScene sc, Pool p
         Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, o.w};
         Hit h;
         h.prim = RT_MISS; h.inst = 0; h.t = INFINITY;
-        TraceResult tr = (kSmemStack && !sc.two_level)
-                             ? traverse<true, SharedStack>(sc.nodes, sc.tris, 0u, r, h, 0u, &sst)
-                             : trace_scene<true>(sc, r, h);
+        TraceResult tr = kTwoLevel    ? traverse_tlas<true>(sc, r, h)
+                         : kSmemStack ? traverse<true, SharedStack>(sc.nodes, sc.tris, 0u, r, h, 0u, &sst)
+                                      : traverse<true>(sc.nodes, sc.tris, 0u, r, h);
         overflow |= tr.overflow;
         if (kCount) { nodes += tr.nodes; tris += tr.tris; }
         if (h.prim == RT_MISS) {
@@ -521,7 +526,7 @@ struct UserJob {
     }
 };
 
-template <bool kAny>
+template <bool kAny, bool kTwoLevel>
 __global__ void __launch_bounds__(128) k_trace_user(DevScene sc, rt_rays rays, uint32_t n, rt_hits hits,
                                                     uint32_t *scratch /* [0] fetch counter, [1] overflow */) {
     bool overflow = false;
@@ -534,7 +539,7 @@ __global__ void __launch_bounds__(128) k_trace_user(DevScene sc, rt_rays rays, u
         Ray r = job.load(i);
         Hit h;
         h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
-        TraceResult tr = trace_scene<kAny>(sc, r, h);
+        TraceResult tr = kTwoLevel ? traverse_tlas<kAny>(sc, r, h) : traverse<kAny>(sc.nodes, sc.tris, 0u, r, h);
         overflow |= tr.overflow;
         job.store(i, h);
     }
@@ -701,6 +706,35 @@ int grid_persistent(K kernel, int block, size_t smem) {
 
 inline size_t stack_smem(int block) { return (size_t)kShStack * block * sizeof(uint2); }
 
+// The one-ray-per-thread traversal kernels of one variant (instrumented or
+// not, shared-memory stack or not, one level or two) and their persistent
+// grids, sized by each kernel's own occupancy.
+using TraceFn = void (*)(DevScene, Pool, const uint32_t *);
+struct TraceKernels {
+    TraceFn ext, shadow;
+    int grid_ext, grid_shadow;
+    size_t smem;
+};
+
+template <bool kCount, bool kSmem, bool kTwo>
+TraceKernels trace_kernels_of(int block) {
+    TraceKernels k;
+    k.ext = k_trace_ext_simple<kCount, kSmem, kTwo>;
+    k.shadow = k_trace_shadow_simple<kCount, kSmem, kTwo>;
+    k.smem = kSmem ? (size_t)kSharedEntries * block * sizeof(uint2) : 0;
+    k.grid_ext = grid_persistent(k.ext, block, k.smem);
+    k.grid_shadow = grid_persistent(k.shadow, block, k.smem);
+    return k;
+}
+
+// Two-level scenes always use the thread-local stack.
+inline TraceKernels trace_kernels(bool count, bool smem_stack, bool two_level, int block) {
+    if (two_level) return count ? trace_kernels_of<true, false, true>(block) : trace_kernels_of<false, false, true>(block);
+    if (smem_stack)
+        return count ? trace_kernels_of<true, true, false>(block) : trace_kernels_of<false, true, false>(block);
+    return count ? trace_kernels_of<true, false, false>(block) : trace_kernels_of<false, false, false>(block);
+}
+
 template <class K>
 int grid_for(K kernel, int block, int64_t work) {
     int per_sm = 0;
@@ -719,6 +753,22 @@ struct PoolAlloc {
         if (block) cudaFree(block);
     }
 };
+
+// Device bytes of one path's state in the pool (eight float4 arrays, the
+// sequence index, pixel, instance of the hit and three queue entries).
+constexpr size_t kPoolBytesPerPath = 8 * sizeof(float4) + sizeof(uint2) + 4 + 4 + 3 * 4;
+
+// Pool capacity when the caller leaves it to the library: every requested
+// path at once when that fits, up to 2^27 paths (about 21 GB of state) and a
+// quarter of the free device memory. Large iteration sets pay: the few long
+// paths at the end of a set keep the GPU partly idle, once per set.
+uint32_t default_capacity(uint64_t paths) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)1 << 30;
+    const uint64_t by_mem = (uint64_t)(free_b / 4 / kPoolBytesPerPath);
+    const uint64_t c = std::min<uint64_t>({paths, (uint64_t)1 << 27, by_mem});
+    return (uint32_t)std::max<uint64_t>(c, 32u);
+}
 
 rt_status ensure_pool(PoolAlloc &pa, uint32_t capacity) {
     if (pa.block && pa.capacity >= capacity) return RT_OK;
@@ -815,13 +865,11 @@ extern "C" rt_status rt_trace(const rt_scene *s, const rt_rays *rays, int64_t n,
     cudaStream_t st = (cudaStream_t)stream;
     RT_CUDA_TRY(cudaMemsetAsync(scratch[dev], 0, 2 * sizeof(uint32_t), st));
     const int gb = 128;
-    if (any_hit) {
-        int g = grid_persistent(k_trace_user<true>, gb, 0);
-        k_trace_user<true><<<g, gb, 0, st>>>(s->dev, *rays, (uint32_t)n, *hits, scratch[dev]);
-    } else {
-        int g = grid_persistent(k_trace_user<false>, gb, 0);
-        k_trace_user<false><<<g, gb, 0, st>>>(s->dev, *rays, (uint32_t)n, *hits, scratch[dev]);
-    }
+    using UserFn = void (*)(DevScene, rt_rays, uint32_t, rt_hits, uint32_t *);
+    const UserFn fn = any_hit ? (s->dev.two_level ? (UserFn)k_trace_user<true, true> : (UserFn)k_trace_user<true, false>)
+                              : (s->dev.two_level ? (UserFn)k_trace_user<false, true> : (UserFn)k_trace_user<false, false>);
+    const int g = grid_persistent(fn, gb, 0);
+    fn<<<g, gb, 0, st>>>(s->dev, *rays, (uint32_t)n, *hits, scratch[dev]);
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
 }
@@ -916,7 +964,8 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     RenderCache *rc = cache_of(film);
     const uint32_t W = cam->width, H = cam->height;
     const uint64_t WH = (uint64_t)W * H;
-    uint32_t cap = o.max_paths_in_flight ? o.max_paths_in_flight : (1u << 22);
+    uint32_t cap = o.max_paths_in_flight ? o.max_paths_in_flight
+                                         : default_capacity((film->next_task / WH + (uint64_t)spp) * WH - film->next_task);
     cap = std::max<uint32_t>(cap, 32u);
     rt_status rs = ensure_pool(rc->pool, cap);
     if (rs != RT_OK) return rs;
@@ -967,7 +1016,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         const float alpha = guide_alpha(gd);
         const int gbk = 128;
         const int g_ray = grid_for(k_raygen, 256, cap);
-        const int g_trace = grid_persistent(k_trace_ext_simple<false>, gbk, 0);
+        const TraceKernels tk = trace_kernels(false, false, s->dev.two_level, gbk);
         const int g_shade = grid_persistent(k_shade_guided, gbk, 0);
         const int g_feat = grid_for(k_guide_features, 256, cap);
         rt_stats stats{};
@@ -989,7 +1038,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
             k_raygen<<<g_ray, 256, 0, st>>>(P, gpool, t, n, (uint32_t)WH, 0u);
             stats.kernel_launches += 1;
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
-                k_trace_ext_simple<false><<<g_trace, gbk, 0, st>>>(s->dev, gpool, nullptr);
+                tk.ext<<<tk.grid_ext, gbk, 0, st>>>(s->dev, gpool, nullptr);
                 RT_CUDA_TRY(cudaMemcpyAsync(rc->host_ctrl, gpool.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
                 RT_CUDA_TRY(cudaStreamSynchronize(st));
                 const uint32_t n_ext = rc->host_ctrl->n_ext;
@@ -1001,7 +1050,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
                     stats.kernel_launches += 1 + 12;
                 }
                 k_shade_guided<<<g_shade, gbk, 0, st>>>(P, gpool, raw, a, rc->grec, glo, ghi);
-                k_trace_shadow_simple<false><<<g_trace, gbk, 0, st>>>(s->dev, gpool);
+                tk.shadow<<<tk.grid_shadow, gbk, 0, st>>>(s->dev, gpool, nullptr);
                 k_step_end<<<1, 1, 0, st>>>(gpool);
                 stats.kernel_launches += 4;
                 ++stats.wavefront_steps;
@@ -1044,9 +1093,9 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     const int g_trace = grid_persistent(k_trace_ext<false>, gb, smem);
     const int g_shade = grid_persistent(k_shade, gb, 0);
     const int g_shadow = grid_persistent(k_trace_shadow<false>, gb, smem);
-    const int g_simple = grid_persistent(k_trace_ext_simple<false>, gb, 0);
     const int g_mega = grid_for(k_megakernel, gb, cap);
     const bool prof = o.profile >= 1, count = o.profile >= 2;
+    const TraceKernels tk = trace_kernels(count, o.trace_kernel == 2, s->dev.two_level, gb);
     const uint32_t nmat = s->num_materials;
     const uint32_t nkeys_mat = nmat + 1, nkeys_ray = 8u * 512u;
     const int g_hist = grid_for(k_sort_scatter<RayKey>, 256, cap);
@@ -1070,8 +1119,6 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
                                1.f / fmaxf(s->dev.bb_hi.y - s->dev.bb_lo.y, 1e-20f),
                                1.f / fmaxf(s->dev.bb_hi.z - s->dev.bb_lo.z, 1e-20f));
     MatKey mkey{s->dev, nmat};
-    const size_t smem_stk = (size_t)kSharedEntries * gb * sizeof(uint2);
-    const int g_simple_sm = grid_persistent(k_trace_ext_simple<false, true>, gb, smem_stk);
     // event pairs per timed launch: kind 0 trace, 1 shade, 2 shadow, 3 megakernel, 4 other
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> evs;
     auto mark = [&](int kind) -> cudaEvent_t {
@@ -1115,12 +1162,8 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
                     stats.kernel_launches += 3;
                 }
                 e = mark(0);
-                if (o.trace_kernel == 0) {
-                    if (count) k_trace_ext_simple<true><<<g_simple, gb, 0, st>>>(s->dev, pool, rsorted);
-                    else k_trace_ext_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool, rsorted);
-                } else if (o.trace_kernel == 2) {
-                    if (count) k_trace_ext_simple<true, true><<<g_simple_sm, gb, smem_stk, st>>>(s->dev, pool, rsorted);
-                    else k_trace_ext_simple<false, true><<<g_simple_sm, gb, smem_stk, st>>>(s->dev, pool, rsorted);
+                if (o.trace_kernel != 1) {
+                    tk.ext<<<tk.grid_ext, gb, tk.smem, st>>>(s->dev, pool, rsorted);
                 } else if (count) {
                     k_trace_ext<true><<<g_trace, gb, smem, st>>>(s->dev, pool);
                 } else {
@@ -1142,12 +1185,8 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
                 k_shade<<<g_shade, gb, 0, st>>>(P, pool, sorted);
                 done(e);
                 e = mark(2);
-                if (o.trace_kernel == 0) {
-                    if (count) k_trace_shadow_simple<true><<<g_simple, gb, 0, st>>>(s->dev, pool);
-                    else k_trace_shadow_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool);
-                } else if (o.trace_kernel == 2) {
-                    if (count) k_trace_shadow_simple<true, true><<<g_simple_sm, gb, smem_stk, st>>>(s->dev, pool);
-                    else k_trace_shadow_simple<false, true><<<g_simple_sm, gb, smem_stk, st>>>(s->dev, pool);
+                if (o.trace_kernel != 1) {
+                    tk.shadow<<<tk.grid_shadow, gb, tk.smem, st>>>(s->dev, pool, nullptr);
                 } else if (count) {
                     k_trace_shadow<true><<<g_shadow, gb, smem, st>>>(s->dev, pool);
                 } else {
@@ -1348,7 +1387,7 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
     const int g_trace = grid_persistent(k_trace_ext<false>, gb, smem);
     const int g_shade = grid_persistent(k_shade, gb, 0);
     const int g_shadow = grid_persistent(k_trace_shadow<false>, gb, smem);
-    const int g_simple = grid_persistent(k_trace_ext_simple<false>, gb, 0);
+    const TraceKernels tk = trace_kernels(false, false, s->dev.two_level, gb);
     const int g_mega = grid_for(k_megakernel, gb, cap);
     auto t_start = std::chrono::steady_clock::now();
     uint64_t t = (uint64_t)first_iteration * WH, t_end = t + (uint64_t)spp * WH;
@@ -1369,10 +1408,10 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
         k_raygen<<<g_ray, 256, 0, st>>>(P, pool, t, n, (uint32_t)WH, tail);
         if (!o.megakernel_only) {
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
-                if (o.trace_kernel != 1) k_trace_ext_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool, nullptr);
+                if (o.trace_kernel != 1) tk.ext<<<tk.grid_ext, gb, 0, st>>>(s->dev, pool, nullptr);
                 else k_trace_ext<false><<<g_trace, gb, smem, st>>>(s->dev, pool);
                 k_shade<<<g_shade, gb, 0, st>>>(P, pool, nullptr);
-                if (o.trace_kernel != 1) k_trace_shadow_simple<false><<<g_simple, gb, 0, st>>>(s->dev, pool);
+                if (o.trace_kernel != 1) tk.shadow<<<tk.grid_shadow, gb, 0, st>>>(s->dev, pool, nullptr);
                 else k_trace_shadow<false><<<g_shadow, gb, smem, st>>>(s->dev, pool);
                 k_step_end<<<1, 1, 0, st>>>(pool);
                 stats.kernel_launches += 4;
@@ -1627,7 +1666,7 @@ extern "C" rt_status rt_render_batch(const rt_render_job *jobs, int32_t njobs, c
         total += B.ntask;
     }
     if (total == 0) return RT_OK;
-    const uint32_t cap = std::max<uint32_t>(32u, o.max_paths_in_flight ? o.max_paths_in_flight : (1u << 22));
+    const uint32_t cap = std::max<uint32_t>(32u, o.max_paths_in_flight ? o.max_paths_in_flight : default_capacity(total));
     BatchJob *djobs = nullptr;
     BatchCtl *dctl = nullptr;
     uint32_t *job_of = nullptr;
@@ -1721,7 +1760,7 @@ extern "C" rt_status rt_autotune(const rt_render_job *jobs, int32_t njobs, uint3
     cudaStream_t st = (cudaStream_t)stream;
     struct Cand { uint32_t cap, tail; int32_t tk; };
     std::vector<Cand> cands;
-    const uint32_t caps[4] = {1u << 20, 1u << 21, 1u << 22, 1u << 23};
+    const uint32_t caps[4] = {1u << 20, 1u << 22, 1u << 24, 1u << 26};
     if (njobs == 1) {
         const uint32_t tails[3] = {1u, 8192u, 65536u};   // 1: the megakernel never takes over
         for (uint32_t c : caps)

@@ -502,6 +502,8 @@ def instanced_field(seed: int = BASE_SEED + 3, n_meshes: int = 100, n_instances:
 def random_rays(scene: SceneData, n: int, seed: int, kind: str = "incoherent", cam: Camera = None):
     """n x 8 float32 rays (ox oy oz dx dy dz tmin tmax).
     kind = 'primary': pinhole rays through random film positions;
+    'camera': pinhole rays in scanline pixel order (coherent), one jittered
+    ray per pixel per pass over the image, as many passes as n needs;
     'incoherent': origins on random triangles (slightly off the surface),
     uniformly random directions; 'shadow': segments between two random
     surface points; 'edges': rays aimed exactly at triangle vertices and edge
@@ -528,7 +530,7 @@ def random_rays(scene: SceneData, n: int, seed: int, kind: str = "incoherent", c
         r = np.sqrt(1 - z * z)
         return np.stack([r * np.cos(ph), r * np.sin(ph), z], 1)
 
-    if kind == "primary":
+    if kind in ("primary", "camera"):
         assert cam is not None
         fwd = np.array(cam.look_at, float) - np.array(cam.eye, float)
         fwd /= np.linalg.norm(fwd)
@@ -537,7 +539,13 @@ def random_rays(scene: SceneData, n: int, seed: int, kind: str = "incoherent", c
         up = np.cross(right, fwd)
         th = math.tan(math.radians(cam.vfov_deg) / 2)
         asp = cam.width / cam.height
-        sx, sy = rng.uniform(n, -1, 1), rng.uniform(n, -1, 1)
+        if kind == "primary":
+            sx, sy = rng.uniform(n, -1, 1), rng.uniform(n, -1, 1)
+        else:
+            pix = np.arange(n, dtype=np.int64) % (cam.width * cam.height)
+            fx = (pix % cam.width + rng.uniform(n)) / cam.width
+            fy = (pix // cam.width + rng.uniform(n)) / cam.height
+            sx, sy = 2 * fx - 1, 1 - 2 * fy
         d = fwd + (sx * th * asp)[:, None] * right + (sy * th)[:, None] * up
         d /= np.linalg.norm(d, axis=1, keepdims=True)
         out[:, 0:3] = np.array(cam.eye)

@@ -72,6 +72,17 @@ def test_halton_host_code_matches_oracle_bits():
         assert np.array_equal(a, b)
 
 
+def test_halton_host_code_matches_oracle_bits_1024_dims():
+    # large bases make the fixed-point fast path hand over to the exact
+    # Horner evaluation most often (about n (b - 1) / 2^32 of the values)
+    rng = np.random.default_rng(2)
+    idx = np.concatenate([rng.integers(0, 2**63, 3000, dtype=np.int64).astype(np.uint64) * np.uint64(2) + np.uint64(1),
+                          rng.integers(0, 2**32, 3000, dtype=np.int64).astype(np.uint64)])
+    a = rt.debug_halton_host(1920, 1080, 99, idx, 1024)
+    b = oracle.sample_dims_u32(idx, 1024, 1920, 1080, 99)
+    assert np.array_equal(a, b)
+
+
 def test_sample_index_host_code_matches_oracle():
     for W, H in [(64, 64), (1920, 1080), (7, 5), (1, 1), (333, 100)]:
         k = max(0, (W - 1).bit_length())
