@@ -1301,7 +1301,7 @@ constexpr size_t kStaticU32Bytes = align_up(sizeof(uint32_t) * kStaticMaxPaths);
 constexpr size_t kStaticPixel = kStaticIndex + align_up(sizeof(uint2) * kStaticMaxPaths);
 constexpr size_t kStaticHitInst = kStaticPixel + kStaticU32Bytes;
 constexpr size_t kStaticQueues = kStaticHitInst + kStaticU32Bytes;
-constexpr size_t kStaticBytes = kStaticQueues + 3 * kStaticU32Bytes;   // about 9.6 MB
+constexpr size_t kStaticBytes = kStaticQueues + 3 * kStaticU32Bytes;   // about 9.9 MiB
 
 static __device__ __align__(256) unsigned char g_static_arena[kStaticBytes];
 
