@@ -228,9 +228,10 @@ __global__ void __launch_bounds__(128, 8) k_shade(RenderParams P, Pool pool, con
 // One ray per thread, traced to completion (A/B variant of the above).
 // kTwoLevel selects the instanced (two-level) traversal at compile time: the
 // single-level kernels carry none of its state and need about a third fewer
-// registers, which raises the resident warps per SM from 20 to 32.
+// registers, which raises the resident warps per SM from 20 to 32 (the launch
+// bounds hold them at 64 registers, 8 blocks of 128 per SM).
 template <bool kCount, bool kSmemStack, bool kTwoLevel>
-__global__ void __launch_bounds__(128) k_trace_ext_simple(DevScene sc, Pool pool, const uint32_t *sorted) {
+__global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_ext_simple(DevScene sc, Pool pool, const uint32_t *sorted) {
     Ctrl *c = pool.ctrl;
     if (c->tail) return;
     const uint32_t n = c->n_ext;
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(128) k_trace_ext_simple(DevScene sc, Pool pool
 }
 
 template <bool kCount, bool kSmemStack, bool kTwoLevel>
-__global__ void __launch_bounds__(128) k_trace_shadow_simple(DevScene sc, Pool pool, const uint32_t *) {
+__global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_shadow_simple(DevScene sc, Pool pool, const uint32_t *) {
     Ctrl *c = pool.ctrl;
     if (c->tail) return;
     const uint32_t n = c->n_shadow;
@@ -527,7 +528,7 @@ struct UserJob {
 };
 
 template <bool kAny, bool kTwoLevel>
-__global__ void __launch_bounds__(128) k_trace_user(DevScene sc, rt_rays rays, uint32_t n, rt_hits hits,
+__global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_user(DevScene sc, rt_rays rays, uint32_t n, rt_hits hits,
                                                     uint32_t *scratch /* [0] fetch counter, [1] overflow */) {
     bool overflow = false;
     UserJob job{rays, hits};

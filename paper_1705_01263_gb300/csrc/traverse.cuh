@@ -291,7 +291,9 @@ __device__ __forceinline__ uint32_t intersect_children(const RayPre &rp, uint4 n
     const uint32_t nxl = sx ? n2.z : n2.x, nxh = sx ? n2.w : n2.y, fxl = sx ? n2.x : n2.z, fxh = sx ? n2.y : n2.w;
     const uint32_t nyl = sy ? n3.z : n3.x, nyh = sy ? n3.w : n3.y, fyl = sy ? n3.x : n3.z, fyh = sy ? n3.y : n3.w;
     const uint32_t nzl = sz ? n4.z : n4.x, nzh = sz ? n4.w : n4.y, fzl = sz ? n4.x : n4.z, fzh = sz ? n4.y : n4.w;
-    uint32_t inner = 0, tris = 0;
+    // one hit bit per child slot; the bookkeeping that turns hits into the
+    // internal-child mask and the triangle mask runs once per node below
+    uint32_t hm = 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const uint32_t sel = 0x7540u + (uint32_t)(i & 3);
@@ -307,16 +309,28 @@ __device__ __forceinline__ uint32_t intersect_children(const RayPre &rp, uint4 n
         upk2(fma2(qz, AZ, BZ), nz, fz);
         float t0 = fmaxf(max3(nx, ny, nz), tmin);
         float t1 = fminf(min3(fx, fy, fz), tmax);
-        bool hit = t0 <= t1 * 1.000001f;
-        uint32_t meta = ((i < 4 ? n1.z : n1.w) >> (8 * (i & 3))) & 0xFFu;
-        uint32_t is_inner = (imask >> i) & 1u;
-        uint32_t ib = (hit && meta && is_inner) ? (1u << (24 + (i ^ rp.oct))) : 0u;
-        uint32_t tb = (hit && meta && !is_inner) ? ((meta >> 5) << (meta & 31u)) : 0u;
-        inner |= ib;
-        tris |= tb;
+        if (t0 <= t1 * 1.000001f) hm |= 1u << i;
+    }
+    // Empty slots carry neither an imask bit nor triangles (meta 0), so a
+    // spurious hit on one adds nothing. Internal children: slot s -> bit
+    // 24 + (s ^ oct), i.e. swap bits, bit pairs and nibbles as oct says.
+    uint32_t x = hm & imask;
+    const uint32_t x1 = ((x & 0x55u) << 1) | ((x >> 1) & 0x55u);
+    x = (rp.oct & 1u) ? x1 : x;
+    const uint32_t x2 = ((x & 0x33u) << 2) | ((x >> 2) & 0x33u);
+    x = (rp.oct & 2u) ? x2 : x;
+    const uint32_t x4 = ((x & 0x0Fu) << 4) | ((x >> 4) & 0x0Fu);
+    x = (rp.oct & 4u) ? x4 : x;
+    // leaf children: meta = (unary triangle count << 5) | first triangle bit
+    uint32_t leaves = hm & ~imask, tris = 0;
+    while (leaves) {
+        const uint32_t i = (uint32_t)(__ffs(leaves) - 1);
+        leaves &= leaves - 1u;
+        const uint32_t meta = __byte_perm(i < 4u ? n1.z : n1.w, 0u, 0x4440u | (i & 3u));
+        tris |= (meta >> 5) << (meta & 31u);
     }
     tri_bits = tris;
-    return inner;
+    return x << 24;
 }
 #else
 RT_HD uint32_t intersect_children(const RayPre &rp, uint4 n0, uint4 n1, uint4 n2, uint4 n3, uint4 n4, float tmin,
