@@ -325,7 +325,9 @@ def main():
     ap.add_argument("--spp", type=int, default=SPP)
     ap.add_argument("--out", default=None)
     ap.add_argument("--trace-kernel", type=int, default=0,
-                    help="0 one ray per thread with warp fetch, 1 persistent warps refilling lanes, 2 as 0 with a shared-memory stack")
+                    help="0 closest hit one ray per thread with warp fetch, shadow rays with lane refill; "
+                         "1 persistent warps refilling lanes; 2 one ray per thread with a shared-memory stack; "
+                         "3 lane refill between node visits for both; 4 one ray per thread for both")
     ap.add_argument("--megakernel-only", action="store_true", help="A/B baseline: megakernel per iteration set")
     ap.add_argument("--sort-by-material", action="store_true", help="A/B: material-sorted shading queue")
     ap.add_argument("--sort-rays", action="store_true", help="A/B: reorder extension rays by octant and origin cell")
@@ -463,8 +465,10 @@ def main():
                        "height": cam.height, "spp": args.spp, "max_depth": DEPTH,
                        "paths_per_step": paths_per_step, "l2": "flushed between steps (256 MiB write)",
                        "film": "FP64 sums", "parallelism": f"weak: {world} rank(s), disjoint iteration ranges",
-                       "trace_kernel": ["one ray per thread, warp fetch", "persistent warps, lane refill",
-                                        "one ray per thread, shared-memory stack"][args.trace_kernel],
+                       "trace_kernel": ["closest hit one ray per thread, shadow rays with lane refill",
+                                        "persistent warps, lane refill",
+                                        "one ray per thread, shared-memory stack",
+                                        "lane refill between node visits", "one ray per thread"][args.trace_kernel],
                        "ray_order": "octant + origin cell" if args.sort_rays else "compaction order",
                        "schedule": "megakernel only" if args.megakernel_only else "wavefront + megakernel tail",
                        "shading_queue": "material-sorted" if args.sort_by_material else "compaction order"},

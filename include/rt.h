@@ -148,8 +148,12 @@ typedef struct {
     rt_guide *guide;         /* online path guiding (NULL = off) */
     rt_stats *stats;         /* optional host output */
     int32_t profile;         /* 1: per-kernel event timing; 2: also count traversal work */
-    int32_t trace_kernel;    /* 0: one ray per thread, warps fetch 32 rays at a time; 1: persistent warps
-                              * refilling idle lanes; 2: as 0 with the stack top in shared memory */
+    int32_t trace_kernel;    /* 0: closest hit one ray per thread (warps fetch 32 rays at a time), shadow
+                              * rays with lane refill; 1: persistent warps refilling idle lanes, one node or
+                              * triangle per step; 2: one ray per thread with the stack top in shared
+                              * memory; 3: warps refill idle lanes between node visits (both ray kinds);
+                              * 4: one ray per thread for both. Two-level scenes always use 0's closest-hit
+                              * kernel for both. */
     int32_t sort_rays;       /* 1: reorder extension rays by direction octant and origin cell (A/B) */
 } rt_render_opts;
 

@@ -303,6 +303,81 @@ __global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_shadow_simple(
     }
 }
 
+// One ray per lane with lane refill (A/B variant, single-level scenes): a
+// warp keeps stepping its rays one node visit (with that node's triangles)
+// at a time, and whenever at least kRefillLanes of its lanes are idle it
+// reserves that many queue entries with one atomic and starts new rays on
+// them (dynamic ray fetch, Aila and Laine 2009), so that finished lanes do
+// not wait for the longest ray of the warp. Results equal the one-shot
+// kernels' (same Traversal steps, same tie rule).
+constexpr int kRefillLanes = 8;
+
+template <bool kAnyHit, bool kCount>
+__global__ void __launch_bounds__(128, 8) k_trace_refill(DevScene sc, Pool pool, const uint32_t *sorted) {
+    Ctrl *c = pool.ctrl;
+    if (c->tail) return;
+    const uint32_t n = kAnyHit ? c->n_shadow : c->n_ext;
+    uint32_t *fetch = kAnyHit ? &c->fetch_shadow : &c->fetch_ext;
+    const uint32_t *queue = kAnyHit ? pool.qs : (sorted ? sorted : pool.q[c->cur]);
+    const uint32_t FULL = 0xFFFFFFFFu, lane = lane_id();
+    LocalStack stack;
+    Traversal<kAnyHit> tr;
+    Hit h;
+    h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
+    TraceResult res{false, 0u, 0u};
+    bool active = false, exhausted = false, overflow = false;
+    uint32_t q = 0, nodes = 0, tris = 0;
+    for (;;) {
+        const uint32_t idle = __ballot_sync(FULL, !active);
+        if (!exhausted && __popc(idle) >= kRefillLanes) {
+            const uint32_t cnt = __popc(idle), leader = __ffs(idle) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(fetch, cnt);
+            base = __shfl_sync(FULL, base, leader);
+            if (base + cnt >= n) exhausted = true;
+            if (!active) {
+                const uint32_t i = base + __popc(idle & lanemask_lt());
+                if (i < n) {
+                    q = queue[i];
+                    Ray r;
+                    if (kAnyHit) {
+                        float4 o = pool.sh_o[q], d = pool.sh_d[q];
+                        r = Ray{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, o.w};
+                    } else {
+                        float4 o = pool.ray_o[q], d = pool.ray_d[q];
+                        r = Ray{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, INFINITY};
+                    }
+                    h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
+                    tr.begin(r, h, 0u, 0u);
+                    res = TraceResult{false, 0u, 0u};
+                    active = true;
+                }
+            }
+        }
+        if (__ballot_sync(FULL, active) == 0u) break;
+        if (active && !tr.step(sc.nodes, sc.tris, stack, h, res)) {
+            active = false;
+            overflow |= res.overflow;
+            if (kCount) { nodes += res.nodes; tris += res.tris; }
+            if (kAnyHit) {
+                if (h.prim == RT_MISS) {
+                    float4 cc = pool.sh_c[q], L = pool.L[q];
+                    pool.L[q] = make_float4(L.x + cc.x, L.y + cc.y, L.z + cc.z, 0.f);
+                }
+            } else {
+                pool.hit[q] = make_float4(__uint_as_float(h.prim), h.t, h.b1, h.b2);
+            }
+        }
+    }
+    if (overflow) atomicOr(&c->overflow, 1u);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(kAnyHit ? &c->shadow_rays : &c->ext_rays, (unsigned long long)n);
+    if (kCount) {
+        atomicAdd(kAnyHit ? &c->shadow_nodes : &c->ext_nodes, (unsigned long long)nodes);
+        atomicAdd(kAnyHit ? &c->shadow_tris : &c->ext_tris, (unsigned long long)tris);
+    }
+}
+
 // Counting sorts of the extension queue (A/B options), with one shared
 // atomic per distinct key per warp in the histogram and one global atomic
 // per distinct key per warp in the scatter:
@@ -728,9 +803,33 @@ TraceKernels trace_kernels_of(int block) {
     return k;
 }
 
-// Two-level scenes always use the thread-local stack.
-inline TraceKernels trace_kernels(bool count, bool smem_stack, bool two_level, int block) {
+template <bool kCount>
+TraceKernels refill_kernels(int block) {
+    TraceKernels k;
+    k.ext = k_trace_refill<false, kCount>;
+    k.shadow = k_trace_refill<true, kCount>;
+    k.smem = 0;
+    k.grid_ext = grid_persistent(k.ext, block, 0);
+    k.grid_shadow = grid_persistent(k.shadow, block, 0);
+    return k;
+}
+
+// variant: 0 (default) closest hit one-shot per ray, shadow rays with lane
+// refill (any-hit rays end at very different times, and an occlusion answer
+// does not depend on the order of the traversal); 2 both one-shot with the
+// stack top in shared memory; 3 both with lane refill; 4 both one-shot.
+// Two-level scenes always use the one-shot kernels with a thread-local stack.
+inline TraceKernels trace_kernels(bool count, int variant, bool two_level, int block) {
     if (two_level) return count ? trace_kernels_of<true, false, true>(block) : trace_kernels_of<false, false, true>(block);
+    if (variant == 3) return count ? refill_kernels<true>(block) : refill_kernels<false>(block);
+    if (variant == 0) {
+        TraceKernels k = count ? trace_kernels_of<true, false, false>(block) : trace_kernels_of<false, false, false>(block);
+        const TraceKernels r = count ? refill_kernels<true>(block) : refill_kernels<false>(block);
+        k.shadow = r.shadow;
+        k.grid_shadow = r.grid_shadow;
+        return k;
+    }
+    const bool smem_stack = variant == 2;
     if (smem_stack)
         return count ? trace_kernels_of<true, true, false>(block) : trace_kernels_of<false, true, false>(block);
     return count ? trace_kernels_of<true, false, false>(block) : trace_kernels_of<false, false, false>(block);
@@ -960,6 +1059,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     rt_render_opts o{};
     if (opts_in) o = *opts_in;
     if (spp == 0) return RT_OK;
+    if (o.trace_kernel < 0 || o.trace_kernel > 4) { set_error("rt_render: trace_kernel must be in [0, 4]"); return RT_INVALID_ARG; }
     if (s->dev.two_level) o.trace_kernel = 0;   // the persistent variant is single-level only
     cudaStream_t st = (cudaStream_t)stream;
     RenderCache *rc = cache_of(film);
@@ -1017,7 +1117,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         const float alpha = guide_alpha(gd);
         const int gbk = 128;
         const int g_ray = grid_for(k_raygen, 256, cap);
-        const TraceKernels tk = trace_kernels(false, false, s->dev.two_level, gbk);
+        const TraceKernels tk = trace_kernels(false, 0, s->dev.two_level, gbk);
         const int g_shade = grid_persistent(k_shade_guided, gbk, 0);
         const int g_feat = grid_for(k_guide_features, 256, cap);
         rt_stats stats{};
@@ -1096,7 +1196,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     const int g_shadow = grid_persistent(k_trace_shadow<false>, gb, smem);
     const int g_mega = grid_for(k_megakernel, gb, cap);
     const bool prof = o.profile >= 1, count = o.profile >= 2;
-    const TraceKernels tk = trace_kernels(count, o.trace_kernel == 2, s->dev.two_level, gb);
+    const TraceKernels tk = trace_kernels(count, o.trace_kernel, s->dev.two_level, gb);
     const uint32_t nmat = s->num_materials;
     const uint32_t nkeys_mat = nmat + 1, nkeys_ray = 8u * 512u;
     const int g_hist = grid_for(k_sort_scatter<RayKey>, 256, cap);
@@ -1345,6 +1445,7 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
         return RT_INVALID_ARG;
     }
     if (spp == 0) return RT_OK;
+    if (o.trace_kernel < 0 || o.trace_kernel > 4) { set_error("rt_render_static: trace_kernel must be in [0, 4]"); return RT_INVALID_ARG; }
     if (s->dev.two_level) o.trace_kernel = 0;   // the persistent variant is single-level only
     unsigned char *base = nullptr;
     rt_status rs = static_arena(&base);
@@ -1388,7 +1489,7 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
     const int g_trace = grid_persistent(k_trace_ext<false>, gb, smem);
     const int g_shade = grid_persistent(k_shade, gb, 0);
     const int g_shadow = grid_persistent(k_trace_shadow<false>, gb, smem);
-    const TraceKernels tk = trace_kernels(false, false, s->dev.two_level, gb);
+    const TraceKernels tk = trace_kernels(false, o.trace_kernel == 1 ? 0 : o.trace_kernel, s->dev.two_level, gb);
     const int g_mega = grid_for(k_megakernel, gb, cap);
     auto t_start = std::chrono::steady_clock::now();
     uint64_t t = (uint64_t)first_iteration * WH, t_end = t + (uint64_t)spp * WH;
@@ -1409,10 +1510,10 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
         k_raygen<<<g_ray, 256, 0, st>>>(P, pool, t, n, (uint32_t)WH, tail);
         if (!o.megakernel_only) {
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
-                if (o.trace_kernel != 1) tk.ext<<<tk.grid_ext, gb, 0, st>>>(s->dev, pool, nullptr);
+                if (o.trace_kernel != 1) tk.ext<<<tk.grid_ext, gb, tk.smem, st>>>(s->dev, pool, nullptr);
                 else k_trace_ext<false><<<g_trace, gb, smem, st>>>(s->dev, pool);
                 k_shade<<<g_shade, gb, 0, st>>>(P, pool, nullptr);
-                if (o.trace_kernel != 1) tk.shadow<<<tk.grid_shadow, gb, 0, st>>>(s->dev, pool, nullptr);
+                if (o.trace_kernel != 1) tk.shadow<<<tk.grid_shadow, gb, tk.smem, st>>>(s->dev, pool, nullptr);
                 else k_trace_shadow<false><<<g_shadow, gb, smem, st>>>(s->dev, pool);
                 k_step_end<<<1, 1, 0, st>>>(pool);
                 stats.kernel_launches += 4;

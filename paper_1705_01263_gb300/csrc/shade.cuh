@@ -252,8 +252,7 @@ RT_HD V3 tri_vertex(const DevScene &sc, uint32_t inst, uint32_t prim, int k) {
     return sc.two_level ? xf_point(sc.inst_xf, inst, p) : p;
 }
 
-RT_HD V3 tri_emission(const DevScene &sc, uint32_t prim, float b1, float b2) {
-    uint32_t mid = ldg(sc.tri_material + prim);
+RT_HD V3 tri_emission(const DevScene &sc, uint32_t prim, uint32_t mid, float b1, float b2) {
     float4 e = ldg(sc.mat_b + mid);
     V3 Le = v3(e.x, e.y, e.z);
     int32_t tex = ldg(sc.mat_tex + mid);
@@ -270,6 +269,10 @@ RT_HD V3 tri_emission(const DevScene &sc, uint32_t prim, float b1, float b2) {
     y = y >= sc.tex_h ? sc.tex_h - 1 : y;
     const float *t = sc.textures + 3 * (((size_t)tex * sc.tex_h + y) * sc.tex_w + x);
     return v3(Le.x * ldg(t), Le.y * ldg(t + 1), Le.z * ldg(t + 2));
+}
+
+RT_HD V3 tri_emission(const DevScene &sc, uint32_t prim, float b1, float b2) {
+    return tri_emission(sc, prim, ldg(sc.tri_material + prim), b1, b2);
 }
 
 // Equirectangular texel of a direction (row 0 looks at +y).
@@ -350,7 +353,26 @@ struct Vertex {
 
 RT_HD void setup_vertex(const DevScene &sc, const PathState &s, const Hit &h, Vertex &vx) {
     const uint32_t prim = h.prim;
-    V3 v0 = tri_vertex(sc, h.inst, prim, 0), v1 = tri_vertex(sc, h.inst, prim, 1), v2 = tri_vertex(sc, h.inst, prim, 2);
+    const uint32_t i0 = ldg(sc.indices + 3 * (size_t)prim), i1 = ldg(sc.indices + 3 * (size_t)prim + 1),
+                   i2 = ldg(sc.indices + 3 * (size_t)prim + 2);
+    // positions and vertex normals are independent loads: issued together
+    const float *p0 = sc.vertices + 3 * (size_t)i0, *p1 = sc.vertices + 3 * (size_t)i1,
+                *p2 = sc.vertices + 3 * (size_t)i2;
+    V3 v0 = v3(ldg(p0), ldg(p0 + 1), ldg(p0 + 2)), v1 = v3(ldg(p1), ldg(p1 + 1), ldg(p1 + 2)),
+       v2 = v3(ldg(p2), ldg(p2 + 1), ldg(p2 + 2));
+    V3 m0 = v3(0.f, 0.f, 0.f), m1 = m0, m2 = m0;
+    if (sc.normals) {
+        const float *n0 = sc.normals + 3 * (size_t)i0, *n1 = sc.normals + 3 * (size_t)i1,
+                    *n2 = sc.normals + 3 * (size_t)i2;
+        m0 = v3(ldg(n0), ldg(n0 + 1), ldg(n0 + 2));
+        m1 = v3(ldg(n1), ldg(n1 + 1), ldg(n1 + 2));
+        m2 = v3(ldg(n2), ldg(n2 + 1), ldg(n2 + 2));
+    }
+    if (sc.two_level) {
+        v0 = xf_point(sc.inst_xf, h.inst, v0);
+        v1 = xf_point(sc.inst_xf, h.inst, v1);
+        v2 = xf_point(sc.inst_xf, h.inst, v2);
+    }
     float b0 = 1.f - h.b1 - h.b2;
     vx.x = b0 * v0 + h.b1 * v1 + h.b2 * v2;
     V3 ng = normalize(cross(v1 - v0, v2 - v0));
@@ -359,12 +381,7 @@ RT_HD void setup_vertex(const DevScene &sc, const PathState &s, const Hit &h, Ve
     if (vx.cog < 0.f) ng = -ng;
     V3 ns = ng;
     if (sc.normals) {
-        uint32_t i0 = ldg(sc.indices + 3 * (size_t)prim), i1 = ldg(sc.indices + 3 * (size_t)prim + 1),
-                 i2 = ldg(sc.indices + 3 * (size_t)prim + 2);
-        const float *n0 = sc.normals + 3 * (size_t)i0, *n1 = sc.normals + 3 * (size_t)i1,
-                    *n2 = sc.normals + 3 * (size_t)i2;
-        ns = b0 * v3(ldg(n0), ldg(n0 + 1), ldg(n0 + 2)) + h.b1 * v3(ldg(n1), ldg(n1 + 1), ldg(n1 + 2)) +
-             h.b2 * v3(ldg(n2), ldg(n2 + 1), ldg(n2 + 2));
+        ns = b0 * m0 + h.b1 * m1 + h.b2 * m2;
         if (sc.two_level) ns = xf_normal(sc.inst_xf, h.inst, ns);
         ns = normalize(ns);
         if (dot(ns, ng) < 0.f) ns = -ns;
@@ -410,11 +427,43 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
         return 0;
     }
     const uint32_t prim = h.prim;
+    // Loads that need only the hit record and the sample index go out before
+    // the vertex is set up, so that their latencies overlap with its loads:
+    // the hit triangle's material and light pdf, and the NEE light pick.
+    const uint32_t mid = ldg(sc.tri_material + prim);
+    const float lpa = ldg(sc.tri_light_pdf_area + prim);
+    const int base = 2 + 7 * (int)(v - 1);
+    const bool last = v == P.max_depth + 1;
+    const bool nee = !last && (sc.num_lights > 0 || sc.p_env > 0.f) && mode != 3;
+    float us = 0.f, ua = 0.f, ub = 0.f;
+    uint32_t lt = 0, lmid = 0;
+    float lpa_l = 0.f;
+    V3 l0 = v3(0.f, 0.f, 0.f), l1 = l0, l2 = l0;
+    if (nee) {
+        us = dim_value(P, s.index, base);
+        ua = dim_value(P, s.index, base + 1);
+        ub = dim_value(P, s.index, base + 2);
+        if (!(us < sc.p_env)) {
+            float u2 = (us - sc.p_env) / (1.f - sc.p_env);
+            float xn = u2 * (float)sc.num_lights;
+            uint32_t bin = (uint32_t)xn;
+            if (bin >= sc.num_lights) bin = sc.num_lights - 1;
+            float frac = xn - (float)bin;
+            float2 al = ldg(sc.alias + bin);
+            uint32_t li = frac < al.x ? bin : as_uint(al.y);
+            lt = ldg(sc.light_tri + li);
+            const float4 *LV = sc.light_v + 3 * (size_t)li;
+            l0 = f4xyz(ldg(LV));
+            l1 = f4xyz(ldg(LV + 1));
+            l2 = f4xyz(ldg(LV + 2));
+            lpa_l = ldg(sc.tri_light_pdf_area + lt);
+            lmid = ldg(sc.tri_material + lt);
+        }
+    }
     Vertex vx;
     setup_vertex(sc, s, h, vx);
-    float lpa = ldg(sc.tri_light_pdf_area + prim);
     if (vx.cog > 0.f && lpa > 0.f) {
-        V3 Le = tri_emission(sc, prim, h.b1, h.b2);
+        V3 Le = tri_emission(sc, prim, mid, h.b1, h.b2);
         float w = 1.f;
         if (v > 1) {
             if (mode == 3) w = 1.f;
@@ -423,19 +472,16 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
         }
         s.L = s.L + mul(s.beta, Le) * w;
     }
-    if (v == P.max_depth + 1) return 0;
+    if (last) return 0;
     const V3 x = vx.x, ng = vx.ng, ns = vx.ns, wo = vx.wo;
-    Material m = load_material(sc, ldg(sc.tri_material + prim));
+    Material m = load_material(sc, mid);
     Mixture mix;
     const bool guided = graw != nullptr && alpha > 0.f;
     if (guided) decode_mixture(graw, mix);
-    const int base = 2 + 7 * (int)(v - 1);
     V3 xo = offset_origin(x, ng);
     int ret = 0;
     // next-event estimation
-    if ((sc.num_lights > 0 || sc.p_env > 0.f) && mode != 3) {
-        float us = dim_value(P, s.index, base), ua = dim_value(P, s.index, base + 1),
-              ub = dim_value(P, s.index, base + 2);
+    if (nee) {
         V3 wi = v3(0.f, 0.f, 1.f), Le = v3(0.f, 0.f, 0.f);
         float pdf_l = 0.f, tmax = INFINITY;
         if (us < sc.p_env) {
@@ -444,16 +490,6 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
             Le = v3(e.x, e.y, e.z);
             pdf_l = sc.p_env * e.w;
         } else {
-            float u2 = (us - sc.p_env) / (1.f - sc.p_env);
-            float xn = u2 * (float)sc.num_lights;
-            uint32_t bin = (uint32_t)xn;
-            if (bin >= sc.num_lights) bin = sc.num_lights - 1;
-            float frac = xn - (float)bin;
-            float2 al = ldg(sc.alias + bin);
-            uint32_t li = frac < al.x ? bin : as_uint(al.y);
-            uint32_t lt = ldg(sc.light_tri + li);
-            const float4 *LV = sc.light_v + 3 * (size_t)li;
-            V3 l0 = f4xyz(ldg(LV)), l1 = f4xyz(ldg(LV + 1)), l2 = f4xyz(ldg(LV + 2));
             float sq = sqrtf(ua);
             float lb1 = sq * (1.f - ub), lb2 = sq * ub;
             V3 y = (1.f - sq) * l0 + lb1 * l1 + lb2 * l2;
@@ -464,8 +500,8 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
                 V3 lng = normalize(cross(l1 - l0, l2 - l0));
                 float cl = -dot(wi, lng);
                 if (cl > 0.f) {
-                    pdf_l = ldg(sc.tri_light_pdf_area + lt) * dist * dist / cl;
-                    Le = tri_emission(sc, lt, lb1, lb2);
+                    pdf_l = lpa_l * dist * dist / cl;
+                    Le = tri_emission(sc, lt, lmid, lb1, lb2);
                     tmax = dist * (1.f - kShadowEps);
                 }
             }

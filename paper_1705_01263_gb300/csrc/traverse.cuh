@@ -345,9 +345,6 @@ struct TraceResult {
     uint32_t tris;    // triangles tested
 };
 
-// Closest hit (any_hit = false) or any hit (true) against one BVH.
-// On return hit.prim == RT_MISS if nothing was found; hit.t, b1, b2 valid
-// otherwise. `hit` may hold a previous best (used for two-level scenes).
 // Traversal stack in a thread-local array (registers / local memory).
 struct LocalStack {
     uint2 e[kStackSize];
@@ -367,18 +364,33 @@ struct SharedStack {
 };
 #endif
 
-template <bool kAnyHit, class Stack = LocalStack>
-RT_HD TraceResult traverse(const uint4 *nodes, const float4 *tris, uint32_t root, const Ray &ray, Hit &hit,
-                           uint32_t inst = 0u, Stack *ext_stack = nullptr) {
-    TraceResult res{false, 0u, 0u};
-    RayPre rp = prepare(ray);
-    float tbest = hit.prim == RT_MISS ? ray.tmax : hit.t;
-    Stack own;
-    Stack &stack = ext_stack ? *ext_stack : own;
-    int sp = 0;
-    // a virtual group holding the root as its only internal child (slot 0)
-    uint2 ng = make_uint2(root, (1u << (24 + (0u ^ rp.oct))) | 1u);
-    for (;;) {
+// Traversal of one ray against one BVH as a resumable state: begin() sets it
+// up, each step() visits one node and tests the triangles of its hit leaf
+// children, and returns false once the ray is finished (stack empty, or a hit
+// found in any-hit mode). traverse() runs it to completion; kernels that
+// refill idle lanes between steps drive it themselves. Closest hit: on equal
+// t the lower (instance, primitive) wins.
+template <bool kAnyHit>
+struct Traversal {
+    RayPre rp;
+    float tmin, tmax, tbest;
+    uint2 ng;   // current node group: child base, hit bits 24..31, imask 0..7
+    int sp;
+    uint32_t inst;
+
+    RT_HD void begin(const Ray &ray, const Hit &hit, uint32_t root, uint32_t instance) {
+        rp = prepare(ray);
+        tmin = ray.tmin;
+        tmax = ray.tmax;
+        tbest = hit.prim == RT_MISS ? ray.tmax : hit.t;
+        sp = 0;
+        inst = instance;
+        // a virtual group holding the root as its only internal child (slot 0)
+        ng = make_uint2(root, (1u << (24 + (0u ^ rp.oct))) | 1u);
+    }
+
+    template <class Stack>
+    RT_HD bool step(const uint4 *nodes, const float4 *tris, Stack &stack, Hit &hit, TraceResult &res) {
         uint32_t tbase = 0, tmask = 0;
         if (ng.y & 0xFF000000u) {
             int bit = 31 - clz32(ng.y);
@@ -387,14 +399,14 @@ RT_HD TraceResult traverse(const uint4 *nodes, const float4 *tris, uint32_t root
             uint32_t child = ng.x + rel;
             ng.y &= ~(1u << bit);
             if (ng.y & 0xFF000000u) {
-                if (sp == kStackSize) { res.overflow = true; break; }
+                if (sp == kStackSize) { res.overflow = true; return false; }
                 stack[sp++] = ng;
             }
             const uint4 *N = nodes + 5 * (size_t)child;
             uint4 n0 = ldg(N), n1 = ldg(N + 1), n2 = ldg(N + 2), n3 = ldg(N + 3), n4 = ldg(N + 4);
             ++res.nodes;
             uint32_t tb;
-            uint32_t inner = intersect_children(rp, n0, n1, n2, n3, n4, ray.tmin, tbest, tb);
+            uint32_t inner = intersect_children(rp, n0, n1, n2, n3, n4, tmin, tbest, tb);
             ng = make_uint2(n1.x, inner | (n0.w >> 24));
             tbase = n1.y;
             tmask = tb;
@@ -408,13 +420,12 @@ RT_HD TraceResult traverse(const uint4 *nodes, const float4 *tris, uint32_t root
             float4 a = ldg(T), b = ldg(T + 1), c = ldg(T + 2);
             ++res.tris;
             float t, u, v;
-            if (intersect_tri(rp, f4xyz(a), f4xyz(b), f4xyz(c), ray.tmin, ray.tmax, tbest, t, u, v)) {
+            if (intersect_tri(rp, f4xyz(a), f4xyz(b), f4xyz(c), tmin, tmax, tbest, t, u, v)) {
                 uint32_t prim = as_uint(a.w);
                 if (kAnyHit) {
                     hit.prim = prim; hit.inst = inst; hit.t = t; hit.b1 = u; hit.b2 = v;
-                    return res;
+                    return false;
                 }
-                // equal t: the lower (instance, primitive) wins
                 if (t < tbest || hit.prim == RT_MISS || inst < hit.inst || (inst == hit.inst && prim < hit.prim)) {
                     hit.prim = prim; hit.inst = inst; hit.t = t; hit.b1 = u; hit.b2 = v;
                     tbest = t;
@@ -422,9 +433,26 @@ RT_HD TraceResult traverse(const uint4 *nodes, const float4 *tris, uint32_t root
             }
         }
         if (!(ng.y & 0xFF000000u)) {
-            if (sp == 0) break;
+            if (sp == 0) return false;
             ng = stack[--sp];
         }
+        return true;
+    }
+};
+
+// Closest hit (any_hit = false) or any hit (true) against one BVH.
+// On return hit.prim == RT_MISS if nothing was found; hit.t, b1, b2 valid
+// otherwise. `hit` may hold a previous best (used for two-level scenes).
+// The stack is thread-local unless `ext_stack` is given.
+template <bool kAnyHit, class Stack = LocalStack>
+RT_HD TraceResult traverse(const uint4 *nodes, const float4 *tris, uint32_t root, const Ray &ray, Hit &hit,
+                           uint32_t inst = 0u, Stack *ext_stack = nullptr) {
+    TraceResult res{false, 0u, 0u};
+    Stack own;
+    Stack &stack = ext_stack ? *ext_stack : own;
+    Traversal<kAnyHit> tr;
+    tr.begin(ray, hit, root, inst);
+    while (tr.step(nodes, tris, stack, hit, res)) {
     }
     return res;
 }

@@ -130,10 +130,11 @@ def test_traversal_variants_agree():
     sd, cam = scenes.sphere_field(n_spheres=40, plane_res=(120, 60), env_size=(512, 256), width=160, height=90)
     s = rt.Scene(sd)
     a, _, _ = gpu_render(s, cam, 2, 16, trace_kernel=0)
-    b, _, _ = gpu_render(s, cam, 2, 16, trace_kernel=1)
     sa, _, _ = a.download()
-    sb, _, _ = b.download()
-    assert np.array_equal(sa, sb)
+    for k in (1, 3, 4):
+        b, _, _ = gpu_render(s, cam, 2, 16, trace_kernel=k)
+        sb, _, _ = b.download()
+        assert np.array_equal(sa, sb), k
 
 
 def test_material_sorted_queue_gives_the_same_image():
@@ -145,7 +146,8 @@ def test_material_sorted_queue_gives_the_same_image():
     a, _, _ = gpu_render(s, cam, 4, 16)
     sa, s2a, ca = a.download()
     for kw in (dict(sort_by_material=True), dict(sort_rays=True), dict(trace_kernel=2),
-               dict(sort_rays=True, sort_by_material=True, trace_kernel=2)):
+               dict(sort_rays=True, sort_by_material=True, trace_kernel=2), dict(trace_kernel=3),
+               dict(trace_kernel=3, sort_rays=True), dict(trace_kernel=3, profile=2)):
         b, st, _ = gpu_render(s, cam, 4, 16, **kw)
         sb, s2b, cb = b.download()
         assert np.array_equal(ca, cb) and np.array_equal(sa, sb) and np.array_equal(s2a, s2b), kw
@@ -228,8 +230,28 @@ def test_invalid_arguments():
         rt.rt_render(s, cam, 1, 0, f2)          # max_depth 0
     rt.rt_render(s, cam, 0, 8, f2)              # spp 0 is a no-op
     assert f2.next_iteration() == 0
+    for k in (-1, 5):
+        with pytest.raises(rt.RtError):
+            rt.rt_render(s, cam, 1, 8, f2, rt.make_opts(trace_kernel=k))
+    assert f2.next_iteration() == 0
     bad = scenes.cornell_box()[0]
     bad.indices = bad.indices.copy()
     bad.indices[0, 0] = 10**6
     with pytest.raises(rt.RtError):
         rt.Scene(bad)
+
+
+def test_refill_traversal_does_the_same_work():
+    """Lane refill changes only which rays share a warp: every ray visits the
+    same nodes and tests the same triangles."""
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.sphere_field(n_spheres=40, plane_res=(120, 60), env_size=(512, 256), width=160, height=90)
+    s = rt.Scene(sd)
+    _, a, _ = gpu_render(s, cam, 2, 16, profile=2)
+    _, b, _ = gpu_render(s, cam, 2, 16, profile=2, trace_kernel=4)
+    for f in ("extension_rays", "shadow_rays", "ext_nodes", "ext_tris", "shadow_nodes", "shadow_tris"):
+        assert getattr(a, f) == getattr(b, f), f
+    _, b, _ = gpu_render(s, cam, 2, 16, profile=2, trace_kernel=3)
+    for f in ("extension_rays", "shadow_rays", "ext_nodes", "ext_tris", "shadow_nodes", "shadow_tris"):
+        assert getattr(a, f) == getattr(b, f), f
+    assert a.ext_nodes > 0 and a.shadow_nodes > 0
