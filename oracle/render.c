@@ -19,8 +19,9 @@
  *     4,5: direction, 6: Russian roulette};
  *   - a continuation or light direction below the geometric tangent plane
  *     (seen from wo) carries nothing; the BSDF is zero outside the shading
- *     hemisphere; shadow rays to a triangle stop at (1 - 1e-4) of the
- *     distance; ray origins move off the surface along the geometric normal.
+ *     hemisphere; a shadow ray to a triangle runs from the offset origin to
+ *     the light point and stops at (1 - 1e-4) of that length; ray origins
+ *     move off the surface along the geometric normal.
  */
 #include "oracle.h"
 #include "oracle_internal.h"
@@ -169,10 +170,11 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
         /* next-event estimation */
         if ((has_tris || has_env) && mode != 3) {
             double us = dimv(c, idx, base), ua = dimv(c, idx, base + 1), ub = dimv(c, idx, base + 2);
-            double wi[3], Le[3], pdf_l = 0.0, tmax = INFINITY;
+            double wi[3], Le[3], sdir[3], pdf_l = 0.0, tmax = INFINITY;
             if (us < s->p_env) {
                 double pe;
                 or_env_sample(s, ua, ub, wi, &pe, NULL, NULL);
+                for (int a = 0; a < 3; ++a) sdir[a] = wi[a];
                 or_env_lookup(s, wi, Le);
                 pdf_l = s->p_env * or_env_pdf(s, wi);
             } else {
@@ -194,7 +196,15 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
                     if (cl > 0.0) {
                         pdf_l = s->tri_light_pdf_area[lt] * dist * dist / cl;
                         or_tri_emission(s, lt, lb1, lb2, Le);
-                        tmax = dist * (1.0 - OR_SHADOW_EPS);
+                        /* the shadow segment: offset origin -> light point */
+                        double sv[3] = {y[0] - xo[0], y[1] - xo[1], y[2] - xo[2]};
+                        double sl = sqrt(dot3(sv, sv));
+                        if (sl > 0.0) {
+                            for (int a = 0; a < 3; ++a) sdir[a] = sv[a] / sl;
+                            tmax = sl * (1.0 - OR_SHADOW_EPS);
+                        } else {
+                            pdf_l = 0.0;
+                        }
                     }
                 }
             }
@@ -205,7 +215,7 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
                     double w = mode == 2 ? 1.0 : mis_weight(mode, pdf_l, pdf_b);
                     double ci = dot3(wi, nsa);
                     uint32_t sp; double st, sb1, sb2;
-                    or_trace_one(s, xo, wi, 0.0, tmax, 1, &sp, &st, &sb1, &sb2);
+                    or_trace_one(s, xo, sdir, 0.0, tmax, 1, &sp, &st, &sb1, &sb2);
                     ++*rays;
                     if (sp == OR_MISS)
                         for (int a = 0; a < 3; ++a) L[a] += beta[a] * f[a] * ci * Le[a] * w / pdf_l;

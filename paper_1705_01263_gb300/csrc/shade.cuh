@@ -14,7 +14,8 @@
 //    the environment and triangle emitters exist);
 //  - a direction below the geometric tangent plane carries nothing; the BSDF
 //    vanishes outside the shading hemisphere;
-//  - shadow rays to a triangle stop at (1 - 1e-4) of its distance.
+//  - a shadow ray to a triangle runs from the offset origin and stops at
+//    (1 - 1e-4) of its distance from there.
 #pragma once
 
 #include "guide.cuh"
@@ -482,10 +483,11 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
     int ret = 0;
     // next-event estimation
     if (nee) {
-        V3 wi = v3(0.f, 0.f, 1.f), Le = v3(0.f, 0.f, 0.f);
+        V3 wi = v3(0.f, 0.f, 1.f), Le = v3(0.f, 0.f, 0.f), sdir = wi;
         float pdf_l = 0.f, tmax = INFINITY;
         if (us < sc.p_env) {
             wi = env_sample(sc, ua, ub);
+            sdir = wi;
             float4 e = ldg(sc.env + env_texel(sc, wi));
             Le = v3(e.x, e.y, e.z);
             pdf_l = sc.p_env * e.w;
@@ -502,7 +504,19 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
                 if (cl > 0.f) {
                     pdf_l = lpa_l * dist * dist / cl;
                     Le = tri_emission(sc, lt, lmid, lb1, lb2);
-                    tmax = dist * (1.f - kShadowEps);
+                    // The shadow segment runs from the offset origin: its own
+                    // length bounds the test, so that the sampled triangle
+                    // itself is never reached (from x, a receiver close to the
+                    // emitter at a grazing angle would see the offset eat the
+                    // margin and occlude itself).
+                    V3 sv = y - xo;
+                    float sl = length(sv);
+                    if (sl > 0.f) {
+                        sdir = sv * (1.f / sl);
+                        tmax = sl * (1.f - kShadowEps);
+                    } else {
+                        pdf_l = 0.f;
+                    }
                 }
             }
         }
@@ -515,7 +529,7 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
                 float w = mode == 2 ? 1.f : mis_weight(mode, pdf_l, pdf_b);
                 float k = dot(wi, ns) * w / pdf_l;
                 sh.o = xo;
-                sh.d = wi;
+                sh.d = sdir;
                 sh.tmax = tmax;
                 sh.contrib = mul(mul(s.beta, f), Le) * k;
                 ret |= 2;

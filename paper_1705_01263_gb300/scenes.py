@@ -220,12 +220,16 @@ class _Builder:
 
 
 # ------------------------------------------------------------ Cornell box
-def cornell_box(seed: int = BASE_SEED + 1):
+def cornell_box(seed: int = BASE_SEED + 1, light: str = "down"):
     """Box [0,1]^3 open towards -z: 5 walls (10 triangles), two boxes rotated
     +-17 degrees about y resting 1e-3 above the floor (24 triangles) and a
     0.25 x 0.25 emitter quad
     (2 triangles) 1e-3 below the ceiling facing down, radiance (17, 12, 4).
-    Lambertian albedo in U[0.2, 0.8]^3 per object. 64 x 64 pinhole camera."""
+    Lambertian albedo in U[0.2, 0.8]^3 per object. 64 x 64 pinhole camera.
+    light="up": the same emitter 0.1 below the ceiling facing up, so that the
+    room is lit only through the bright patch it makes on the ceiling (every
+    surface but that patch is lit indirectly; next-event estimation cannot
+    reach the light from them)."""
     rng = Rng(seed)
     b = _Builder()
 
@@ -249,10 +253,13 @@ def cornell_box(seed: int = BASE_SEED + 1):
         v, t = _box(center, size, ang)
         b.add(v, t, mat())
     lm = b.material((0.78, 0.78, 0.78), 0.5, 0.0, (17.0, 12.0, 4.0))
-    y = 1.0 - 1e-3
-    p, t = _oriented_quad((0.375, y, 0.375), (0.625, y, 0.375), (0.625, y, 0.625), (0.375, y, 0.625), (0, -1, 0))
+    if light not in ("down", "up"):
+        raise ValueError(light)
+    y = 1.0 - 1e-3 if light == "down" else 0.9
+    facing = (0, -1, 0) if light == "down" else (0, 1, 0)
+    p, t = _oriented_quad((0.375, y, 0.375), (0.625, y, 0.375), (0.625, y, 0.625), (0.375, y, 0.625), facing)
     b.add(p, t, lm)
-    scene = b.build(name="cornell-36")
+    scene = b.build(name="cornell-36" if light == "down" else "cornell-36-up")
     cam = Camera((0.5, 0.5, -1.4), (0.5, 0.5, 0.0), (0.0, 1.0, 0.0), 40.0, 64, 64)
     return scene, cam
 

@@ -79,6 +79,20 @@ def test_cornell_config_parity():
     assert stats.extension_rays + stats.shadow_rays == pytest.approx(rays, rel=0.01)
 
 
+@pytest.mark.parametrize("mis_mode", [0, 2, 3])
+def test_cornell_light_facing_ceiling_parity(mis_mode):
+    """Emitter 0.1 below the ceiling facing it: the room is lit through the
+    ceiling, and NEE reaches the emitter only from close by at grazing angles."""
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.cornell_box(light="up")
+    film, _, _ = gpu_render(rt.Scene(sd), cam, 64, 8, mis_mode=mis_mode)
+    mg, vg, _ = resolved(film)
+    S, S2, C, _ = oracle.Scene(sd).render(cam, 64, 8, mis_mode=mis_mode)
+    mo, vo = oracle.resolve(S, S2, C)
+    l1, out, n = image_parity(mg, vg, mo, vo)
+    assert l1 <= 0.01 and out <= allowed_4sigma(n), (l1, out, n)
+
+
 @pytest.mark.parametrize("mis_mode", [1, 2, 3])
 def test_cornell_mis_modes_parity(mis_mode):
     from paper_1705_01263_gb300 import rt
