@@ -4,7 +4,8 @@
 // gradients are all expressed as this product with suitably stored operands).
 //
 // One CTA of 128 threads computes a 128 x NT tile (NT <= 256, a multiple of
-// 16) over one split of K: K is walked in chunks of 64; each chunk of A and B
+// 16) over one split of K (several CTAs share an SM, as many as its tensor
+// memory holds): K is walked in chunks of 64; each chunk of A and B
 // is copied from global memory into the canonical no-swizzle K-major shared
 // layout with 16-byte loads, then one thread issues four 128 x NT x 16 MMAs
 // and commits them to an mbarrier that every thread waits on (bounded) before
@@ -25,19 +26,35 @@ struct GemmArgs {
     int M, N, K, lda, ldb, ldc;
     int k_split;        // K elements per split (multiple of 64)
     int nt;             // N columns per CTA (multiple of 16, <= 256)
-    int mode;           // 0 store, 1 atomic add
+    int mode;           // 0 store, 1 atomic add, 2 ReLU backward (below)
     uint32_t *err;      // set to 1 if a tensor-core wait timed out
+    // mode 2: instead of C, dY = bf16(C * (H > 0)) row-major [M][N] (ld N)
+    // and its transpose dYT [N][ldt], H BF16 row-major [M][N]
+    const __nv_bfloat16 *H;
+    __nv_bfloat16 *dY, *dYT;
+    int64_t ldt;
 };
 
 constexpr int kGemmKChunk = 64;
-constexpr int kGemmSmem = 116 * 1024;   // one CTA per SM: its 256 TMEM columns always fit
+constexpr int kGemmSmemMax = 116 * 1024;   // attribute limit of the launch below
+
+// Dynamic shared memory of a launch with `nt` columns per CTA: the A and B
+// chunks and the barrier, raised so that the CTAs that fit on one SM (228 KB
+// of shared memory, 1 KB reserved per CTA) never ask for more than the 512
+// tensor-memory columns an SM has: an allocation then never waits.
+inline int gemm_smem(int nt, uint32_t ncols) {
+    const int need = 16384 + nt * 128 + 64;
+    const int max_ctas = (int)(512u / ncols);
+    const int floor_bytes = 233472 / (max_ctas + 1) - 1024 + 16;
+    return std::min(kGemmSmemMax, std::max(need, floor_bytes));
+}
 
 __global__ void __launch_bounds__(128, 1) k_gemm_bf16(GemmArgs g) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sA = smem;                    // 128 x 64 bf16 = 16 KB
     unsigned char *sB = smem + 16384;            // nt x 64 bf16 <= 32 KB
-    uint64_t *mbar = (uint64_t *)(smem + 16384 + 32768);
-    uint32_t *s_taddr = (uint32_t *)(smem + 16384 + 32768 + 16);
+    uint64_t *mbar = (uint64_t *)(smem + 16384 + g.nt * 128);
+    uint32_t *s_taddr = (uint32_t *)(smem + 16384 + g.nt * 128 + 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * g.nt;
     const int k_begin = blockIdx.z * g.k_split;
@@ -95,7 +112,18 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(GemmArgs g) {
         for (int c0 = 0; c0 < g.nt; c0 += 16) {
             float v[16];
             umma::tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (row < g.M) {
+            if (row < g.M && g.mode == 2) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (col < g.N) {
+                        const size_t i = (size_t)row * g.N + col;
+                        const __nv_bfloat16 b = __float2bfloat16(__bfloat162float(g.H[i]) > 0.f ? v[j] : 0.f);
+                        g.dY[i] = b;
+                        g.dYT[(size_t)col * g.ldt + row] = b;
+                    }
+                }
+            } else if (row < g.M) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     int col = n0 + c0 + j;
@@ -113,10 +141,10 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(GemmArgs g) {
     if (warp == 0) umma::tmem_dealloc(taddr, ncols);
 }
 
-rt_status gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *C, int M, int N, int K, int lda, int ldb,
-                    int ldc, int accumulate, uint32_t *err, cudaStream_t st) {
+static rt_status gemm_launch(GemmArgs g, int accumulate, bool relu_bwd, cudaStream_t st) {
+    const int M = g.M, N = g.N, K = g.K;
     if (M <= 0 || N <= 0 || K <= 0) return RT_OK;
-    if ((K % 8) || (lda % 8) || (ldb % 8) || ((uintptr_t)A % 16) || ((uintptr_t)B % 16)) {
+    if ((K % 8) || (g.lda % 8) || (g.ldb % 8) || ((uintptr_t)g.A % 16) || ((uintptr_t)g.B % 16)) {
         set_error("gemm_bf16: K, lda, ldb must be multiples of 8 and A, B 16-byte aligned");
         return RT_INVALID_ARG;
     }
@@ -124,24 +152,41 @@ rt_status gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *C, in
     int dev = 0;
     RT_CUDA_TRY(cudaGetDevice(&dev));
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        RT_CUDA_TRY(cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
+        RT_CUDA_TRY(cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmemMax));
         attr_set[dev] = true;
     }
-    GemmArgs g{A, B, C, M, N, K, lda, ldb, ldc, 0, 0, 0, err};
     g.nt = std::min(256, (N + 15) / 16 * 16);
     const int mt = (M + 127) / 128, ntiles = (N + g.nt - 1) / g.nt;
-    // split K when the output grid alone cannot fill the machine
+    // split K when the output grid alone cannot fill the machine (not for
+    // the ReLU-backward epilogue, which needs whole sums)
     int splits = 1;
     const int ctas = mt * ntiles;
-    if (ctas < 152 && K > 4 * kGemmKChunk) splits = std::min((K + kGemmKChunk - 1) / kGemmKChunk, (2 * 152 + ctas - 1) / ctas);
+    if (!relu_bwd && ctas < 152 && K > 4 * kGemmKChunk)
+        splits = std::min((K + kGemmKChunk - 1) / kGemmKChunk, (2 * 152 + ctas - 1) / ctas);
     g.k_split = ((K + splits - 1) / splits + kGemmKChunk - 1) / kGemmKChunk * kGemmKChunk;
     splits = (K + g.k_split - 1) / g.k_split;
-    g.mode = (splits > 1 || accumulate) ? 1 : 0;
-    if (g.mode == 1 && !accumulate) RT_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(float) * ((size_t)(M - 1) * ldc + N), st));
+    g.mode = relu_bwd ? 2 : ((splits > 1 || accumulate) ? 1 : 0);
+    if (g.mode == 1 && !accumulate) RT_CUDA_TRY(cudaMemsetAsync(g.C, 0, sizeof(float) * ((size_t)(M - 1) * g.ldc + N), st));
     dim3 grid(mt, ntiles, splits);
-    k_gemm_bf16<<<grid, 128, kGemmSmem, st>>>(g);
+    const uint32_t ncols = g.nt <= 32 ? 32u : (g.nt <= 64 ? 64u : (g.nt <= 128 ? 128u : 256u));
+    k_gemm_bf16<<<grid, 128, gemm_smem(g.nt, ncols), st>>>(g);
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
+}
+
+rt_status gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *C, int M, int N, int K, int lda, int ldb,
+                    int ldc, int accumulate, uint32_t *err, cudaStream_t st) {
+    GemmArgs g{A, B, C, M, N, K, lda, ldb, ldc, 0, 0, 0, err, nullptr, nullptr, nullptr, 0};
+    return gemm_launch(g, accumulate, false, st);
+}
+
+// dY = bf16((A B^T) * (H > 0)) [M][N] and dYT [N][ldt]: the backward step of
+// a ReLU layer fused into the product's epilogue.
+rt_status gemm_bf16_relu_bwd(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int lda, int ldb,
+                             const __nv_bfloat16 *H, __nv_bfloat16 *dY, __nv_bfloat16 *dYT, int64_t ldt, uint32_t *err,
+                             cudaStream_t st) {
+    GemmArgs g{A, B, nullptr, M, N, K, lda, ldb, N, 0, 0, 0, err, H, dY, dYT, ldt};
+    return gemm_launch(g, 0, true, st);
 }
 
 }  // namespace rtg

@@ -12,6 +12,14 @@
 // rows); activations H_l [n][64] BF16 plus their transposes [64][n] for the
 // weight gradients; network outputs [n][48] FP32 (first 40 used, lobe k at
 // 5k: mu xyz, kappa (softplus), logit).
+//
+// Kernels: inference is one fused launch (guide_mlp.cuh); a training step is
+// the fused forward pass with the loss gradient (same file, training mode),
+// then per layer a tcgen05 GEMM for dY_l = (dY_{l+1} W_{l+1}) * relu'(H_l)
+// with the ReLU mask and the transposed copy in its epilogue, one for the
+// weight gradient dW_l = dY_l^T X_{l-1}, and one Adam launch plus the BF16
+// repacking of the weights. gemm_bf16's layer-by-layer forward pass remains
+// as a cross-check of the fused kernel.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -19,12 +27,16 @@
 #include <vector>
 
 #include "guide.cuh"
+#include "guide_mlp.cuh"
 #include "internal.h"
 
 namespace rtg {
 
 rt_status gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *C, int M, int N, int K, int lda, int ldb,
                     int ldc, int accumulate, uint32_t *err, cudaStream_t st);
+rt_status gemm_bf16_relu_bwd(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int lda, int ldb,
+                             const __nv_bfloat16 *H, __nv_bfloat16 *dY, __nv_bfloat16 *dYT, int64_t ldt, uint32_t *err,
+                             cudaStream_t st);
 
 static const int kIn[5] = {kGuideIn, kGuideHid, kGuideHid, kGuideHid, kGuideHid};
 static const int kOut[5] = {kGuideHid, kGuideHid, kGuideHid, kGuideHid, kGuideOut};
@@ -37,66 +49,43 @@ static int64_t param_offset(int l) {
 }
 
 // ------------------------------------------------------------ kernels
+// The activations of the training forward pass and the backward signals are
+// stored twice, row-major [n_pad][C] for the next layer's product and
+// transposed [C][n_pad] for the weight gradients. A block builds a tile of
+// 64 rows in shared memory (row stride C + 2, so that the transposed reads
+// fall in different banks) and writes both copies with coalesced stores.
+constexpr int kTileRows = 64;
+
+template <int C, class F>
+__device__ __forceinline__ void store_tile_and_transpose(int64_t r0, int64_t n_pad, const F &val, __nv_bfloat16 *M,
+                                                         __nv_bfloat16 *MT) {
+    __shared__ __nv_bfloat16 tile[kTileRows * (C + 2)];
+    for (int i = threadIdx.x; i < kTileRows * C; i += blockDim.x) {
+        const int rr = i / C, c = i % C;
+        const __nv_bfloat16 b = __float2bfloat16(val(r0 + rr, c));
+        tile[rr * (C + 2) + c] = b;
+        M[(r0 + rr) * C + c] = b;
+    }
+    if (!MT) return;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTileRows * C; i += blockDim.x) {
+        const int c = i / kTileRows, rr = i % kTileRows;
+        MT[(int64_t)c * n_pad + r0 + rr] = tile[rr * (C + 2) + c];
+    }
+}
+
+// X = one-blob(features) [n_pad][224] (zero rows past n) and X^T.
 __global__ void k_oneblob(const float *feat, int64_t n, int64_t n_pad, __nv_bfloat16 *X, __nv_bfloat16 *XT) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_pad * kGuideIn;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = i / kGuideIn;
-        int c = (int)(i % kGuideIn);
-        float v = 0.f;
-        if (r < n) v = oneblob_bin(feat[r * 7 + c / kGuideBins], c % kGuideBins);
-        __nv_bfloat16 b = __float2bfloat16(v);
-        X[r * kGuideIn + c] = b;
-        if (XT) XT[(int64_t)c * n_pad + r] = b;
-    }
+    const int64_t r0 = (int64_t)blockIdx.x * kTileRows;
+    auto val = [&](int64_t r, int c) { return r < n ? oneblob_bin(feat[r * 7 + c / kGuideBins], c % kGuideBins) : 0.f; };
+    store_tile_and_transpose<kGuideIn>(r0, n_pad, val, X, XT);
 }
 
-// H = bf16(relu(Z)); optional transpose HT [64][n_pad].
-__global__ void k_relu_pack(const float *Z, int64_t n, int64_t n_pad, int cols, __nv_bfloat16 *H, __nv_bfloat16 *HT) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_pad * cols;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = i / cols;
-        int c = (int)(i % cols);
-        float v = r < n ? fmaxf(Z[i], 0.f) : 0.f;
-        __nv_bfloat16 b = __float2bfloat16(v);
-        H[i] = b;
-        if (HT) HT[(int64_t)c * n_pad + r] = b;
-    }
-}
-
-// dY = bf16(dH * (H > 0)) and its transpose.
-__global__ void k_relu_bwd(const float *dH, const __nv_bfloat16 *H, int64_t n_pad, int cols, __nv_bfloat16 *dY,
-                           __nv_bfloat16 *dYT) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_pad * cols;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = i / cols;
-        int c = (int)(i % cols);
-        float v = __bfloat162float(H[i]) > 0.f ? dH[i] : 0.f;
-        __nv_bfloat16 b = __float2bfloat16(v);
-        dY[i] = b;
-        dYT[(int64_t)c * n_pad + r] = b;
-    }
-}
-
-// Loss -weight * log q_mix(wi) / n and its gradient w.r.t. the raw outputs.
-__global__ void k_loss_grad(const float *raw, const float *wi, const float *weight, int64_t n, int64_t n_pad,
-                            float inv_n, __nv_bfloat16 *dY, __nv_bfloat16 *dYT, float *loss_sum) {
-    float local = 0.f;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_pad; r += (int64_t)gridDim.x * blockDim.x) {
-        float g[kGuideOutPad];
-        for (int k = 0; k < kGuideOutPad; ++k) g[k] = 0.f;
-        if (r < n) {
-            float w3[3] = {wi[3 * r], wi[3 * r + 1], wi[3 * r + 2]};
-            float lw = mixture_loss_grad(raw + r * kGuideOutPad, w3, weight[r] * inv_n, g);
-            local += lw;
-        }
-        for (int k = 0; k < kGuideOutPad; ++k) {
-            __nv_bfloat16 b = __float2bfloat16(g[k]);
-            dY[r * kGuideOutPad + k] = b;
-            dYT[(int64_t)k * n_pad + r] = b;
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xFFFFFFFFu, local, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, local);
+// H = bf16(relu(Z)) [n_pad][64] (zero rows past n); optional transpose HT.
+__global__ void k_relu_pack(const float *Z, int64_t n, int64_t n_pad, __nv_bfloat16 *H, __nv_bfloat16 *HT) {
+    const int64_t r0 = (int64_t)blockIdx.x * kTileRows;
+    auto val = [&](int64_t r, int c) { return r < n ? fmaxf(Z[r * kGuideHid + c], 0.f) : 0.f; };
+    store_tile_and_transpose<kGuideHid>(r0, n_pad, val, H, HT);
 }
 
 __global__ void k_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
@@ -127,6 +116,27 @@ __global__ void k_copy_rows(const float *src, int rows, int cols, float *dst) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows * cols; i += gridDim.x * blockDim.x) dst[i] = src[i];
 }
 
+// Fused inference (guide_mlp.cuh) over rows of given features [n][7].
+struct ArrayFeatures {
+    const float *feat;
+    uint32_t n;
+    __device__ uint32_t count() const { return n; }
+    __device__ void operator()(uint32_t row, float f[7]) const {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) f[k] = feat[7 * (size_t)row + k];
+    }
+};
+
+__global__ void __launch_bounds__(512, 1) k_guide_mlp(MlpWeights w, ArrayFeatures feat, float *raw, uint32_t *err) {
+    mlp_infer_tiles(w, feat, raw, err);
+}
+
+// Training forward pass with the loss gradient (guide_mlp.cuh, MlpTrain).
+__global__ void __launch_bounds__(512, 1) k_guide_mlp_train(MlpWeights w, ArrayFeatures feat, MlpTrain tr,
+                                                            uint32_t *err) {
+    mlp_tiles<true>(w, feat, nullptr, err, tr);
+}
+
 static int grid1d(int64_t n, int block = 256) {
     int64_t g = (n + block - 1) / block;
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
@@ -142,9 +152,11 @@ struct rt_guide {
     float *W32 = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
     __nv_bfloat16 *Wb[5] = {nullptr}, *WTb[5] = {nullptr};
     int64_t step = 0;
+    uint64_t sets = 0;   // iteration sets rendered with this guide
     // scratch for a batch of up to cap rows
     int64_t cap = 0;
     __nv_bfloat16 *X0 = nullptr, *X0T = nullptr, *H[4] = {nullptr}, *HT[4] = {nullptr}, *dY = nullptr, *dYT = nullptr;
+    __nv_bfloat16 *dYh[2] = {nullptr, nullptr}, *dYhT[2] = {nullptr, nullptr};   // hidden-layer gradients
     float *Z = nullptr, *raw = nullptr, *dW5 = nullptr, *loss = nullptr;
     uint32_t *err = nullptr;
     std::vector<void *> allocs;
@@ -177,6 +189,7 @@ rt_status ensure_scratch(rt_guide *g, int64_t n) {
     cudaDeviceSynchronize();
     for (void *p : {(void *)g->X0, (void *)g->X0T, (void *)g->H[0], (void *)g->H[1], (void *)g->H[2], (void *)g->H[3],
                     (void *)g->HT[0], (void *)g->HT[1], (void *)g->HT[2], (void *)g->HT[3], (void *)g->dY, (void *)g->dYT,
+                    (void *)g->dYh[0], (void *)g->dYh[1], (void *)g->dYhT[0], (void *)g->dYhT[1],
                     (void *)g->Z, (void *)g->raw}) {
         if (!p) continue;
         cudaFree(p);
@@ -184,7 +197,9 @@ rt_status ensure_scratch(rt_guide *g, int64_t n) {
     }
     rt_status s;
     if ((s = galloc(g, &g->X0, need * kGuideIn)) || (s = galloc(g, &g->X0T, need * kGuideIn)) ||
-        (s = galloc(g, &g->dY, need * kGuideHid)) || (s = galloc(g, &g->dYT, need * kGuideHid)) ||
+        (s = galloc(g, &g->dY, need * kGuideOutPad)) || (s = galloc(g, &g->dYT, need * kGuideOutPad)) ||
+        (s = galloc(g, &g->dYh[0], need * kGuideHid)) || (s = galloc(g, &g->dYhT[0], need * kGuideHid)) ||
+        (s = galloc(g, &g->dYh[1], need * kGuideHid)) || (s = galloc(g, &g->dYhT[1], need * kGuideHid)) ||
         (s = galloc(g, &g->Z, need * kGuideHid)) || (s = galloc(g, &g->raw, need * kGuideOutPad)))
         return s;
     for (int l = 0; l < 4; ++l)
@@ -196,13 +211,13 @@ rt_status ensure_scratch(rt_guide *g, int64_t n) {
 // Forward pass over n rows of features; raw outputs in g->raw [n_pad][48].
 rt_status forward(rt_guide *g, const float *feat, int64_t n, bool keep_transposes, cudaStream_t st) {
     const int64_t n_pad = (n + 127) / 128 * 128;
-    k_oneblob<<<grid1d(n_pad * kGuideIn), 256, 0, st>>>(feat, n, n_pad, g->X0, keep_transposes ? g->X0T : nullptr);
+    const int tiles = (int)(n_pad / kTileRows);
+    k_oneblob<<<tiles, 256, 0, st>>>(feat, n, n_pad, g->X0, keep_transposes ? g->X0T : nullptr);
     const __nv_bfloat16 *x = g->X0;
     for (int l = 0; l < 4; ++l) {
         rt_status s = gemm_bf16(x, g->Wb[l], g->Z, (int)n_pad, kGuideHid, kIn[l], kIn[l], kIn[l], kGuideHid, 0, g->err, st);
         if (s != RT_OK) return s;
-        k_relu_pack<<<grid1d(n_pad * kGuideHid), 256, 0, st>>>(g->Z, n, n_pad, kGuideHid, g->H[l],
-                                                               keep_transposes ? g->HT[l] : nullptr);
+        k_relu_pack<<<tiles, 256, 0, st>>>(g->Z, n, n_pad, g->H[l], keep_transposes ? g->HT[l] : nullptr);
         x = g->H[l];
     }
     rt_status s = gemm_bf16(x, g->Wb[4], g->raw, (int)n_pad, kGuideOutPad, kGuideHid, kGuideHid, kGuideHid,
@@ -212,33 +227,62 @@ rt_status forward(rt_guide *g, const float *feat, int64_t n, bool keep_transpose
     return RT_OK;
 }
 
-// Gradient of the mean loss into g->grad (FP32, layer-major [out][in]).
-rt_status backward(rt_guide *g, const float *wi, const float *weight, int64_t n, cudaStream_t st) {
+// Fused training forward pass: activations, their transposes and the loss
+// gradient dY / dYT for n rows (one launch), loss summed into g->loss.
+rt_status train_forward(rt_guide *g, const float *feat, const float *wi, const float *weight, int64_t n,
+                        cudaStream_t st) {
     const int64_t n_pad = (n + 127) / 128 * 128;
+    rt_status s = mlp_kernel_attr((const void *)k_guide_mlp_train, kMlpSmemTrain);
+    if (s != RT_OK) return s;
     RT_CUDA_TRY(cudaMemsetAsync(g->loss, 0, sizeof(float), st));
-    k_loss_grad<<<grid1d(n_pad), 256, 0, st>>>(g->raw, wi, weight, n, n_pad, 1.f / (float)n, g->dY, g->dYT, g->loss);
+    MlpTrain tr{};
+    tr.wi = wi;
+    tr.weight = weight;
+    tr.inv_n = 1.f / (float)n;
+    tr.n_pad = (uint32_t)n_pad;
+    tr.XT = g->X0T;
+    for (int l = 0; l < 4; ++l) { tr.H[l] = g->H[l]; tr.HT[l] = g->HT[l]; }
+    tr.dY = g->dY;
+    tr.dYT = g->dYT;
+    tr.loss = g->loss;
+    const int grid = (int)std::min<int64_t>(n_pad / kMlpTile, (int64_t)sm_count());
+    k_guide_mlp_train<<<grid, kMlpThreads, kMlpSmemTrain, st>>>(guide_weights(g), ArrayFeatures{feat, (uint32_t)n},
+                                                                 tr, g->err);
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+// Gradient of the mean loss into g->grad (FP32, layer-major [out][in]),
+// from dY / dYT of the training forward pass.
+rt_status backward(rt_guide *g, int64_t n, cudaStream_t st) {
+    const int64_t n_pad = (n + 127) / 128 * 128;
     rt_status s;
-    // layer 5: dW5 [48][64] = dY5^T H4 ; dH4 = dY5 W5
+    // layer 5: dW5 [48][64] = dY5^T H4 ; dY4 = (dY5 W5) * relu'(H4)
     if ((s = gemm_bf16(g->dYT, g->HT[3], g->dW5, kGuideOutPad, kGuideHid, (int)n_pad, (int)n_pad, (int)n_pad,
                        kGuideHid, 0, g->err, st)))
         return s;
     k_copy_rows<<<grid1d(kGuideOut * kGuideHid), 256, 0, st>>>(g->dW5, kGuideOut, kGuideHid, g->grad + param_offset(4));
-    if ((s = gemm_bf16(g->dY, g->WTb[4], g->Z, (int)n_pad, kGuideHid, kGuideOutPad, kGuideOutPad, kGuideOutPad,
-                       kGuideHid, 0, g->err, st)))
-        return s;
+    // the layer-5 gradient lives in the [n_pad][48] dY buffer; the hidden
+    // layers' go to dYh ([n_pad][64], ping-pong with dYh2)
+    const __nv_bfloat16 *dy = g->dY, *dyT = g->dYT;
+    int kdy = kGuideOutPad;
+    __nv_bfloat16 *bufs[2][2] = {{g->dYh[0], g->dYhT[0]}, {g->dYh[1], g->dYhT[1]}};
     for (int l = 3; l >= 0; --l) {
-        // dY_l = dH_l * relu'(H_l)  (dY/dYT buffers hold [n_pad][64])
-        k_relu_bwd<<<grid1d(n_pad * kGuideHid), 256, 0, st>>>(g->Z, g->H[l], n_pad, kGuideHid, g->dY, g->dYT);
+        __nv_bfloat16 *ndy = bufs[l & 1][0], *ndyT = bufs[l & 1][1];
+        // dY_l = (dY_{l+1} W_{l+1}) * relu'(H_l), and its transpose
+        if ((s = gemm_bf16_relu_bwd(dy, g->WTb[l + 1], (int)n_pad, kGuideHid, kdy, kdy, kdy, g->H[l], ndy, ndyT, n_pad,
+                                    g->err, st)))
+            return s;
         // dW_l [64][in] = dY_l^T X_{l-1}
         const __nv_bfloat16 *xT = l == 0 ? g->X0T : g->HT[l - 1];
-        if ((s = gemm_bf16(g->dYT, xT, g->grad + param_offset(l), kGuideHid, kIn[l], (int)n_pad, (int)n_pad,
-                           (int)n_pad, kIn[l], 0, g->err, st)))
+        if ((s = gemm_bf16(ndyT, xT, g->grad + param_offset(l), kGuideHid, kIn[l], (int)n_pad, (int)n_pad, (int)n_pad,
+                           kIn[l], 0, g->err, st)))
             return s;
-        if (l > 0 &&
-            (s = gemm_bf16(g->dY, g->WTb[l], g->Z, (int)n_pad, kGuideHid, kGuideHid, kGuideHid, kGuideHid, kGuideHid,
-                           0, g->err, st)))
-            return s;
+        dy = ndy;
+        dyT = ndyT;
+        kdy = kGuideHid;
     }
+    (void)dyT;
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
 }
@@ -258,8 +302,43 @@ rt_status check_err(rt_guide *g, cudaStream_t st) {
 }  // namespace
 
 namespace rtg {
-// Used by the renderer: raw outputs for n feature rows (device), no sync.
+rt_status guide_check(rt_guide *g, cudaStream_t st) { return check_err(g, st); }
+
+MlpWeights guide_weights(const rt_guide *g) {
+    MlpWeights w;
+    for (int l = 0; l < 5; ++l) w.W[l] = g->Wb[l];
+    return w;
+}
+uint32_t *guide_err(const rt_guide *g) { return g->err; }
+
+// Shared-memory opt-in of a fused network kernel, once per device.
+rt_status mlp_kernel_attr(const void *kernel, uint32_t bytes) {
+    int dev = 0;
+    RT_CUDA_TRY(cudaGetDevice(&dev));
+    static std::vector<std::pair<const void *, int>> done;
+    for (auto &p : done)
+        if (p.first == kernel && p.second == dev) return RT_OK;
+    RT_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    done.push_back({kernel, dev});
+    return RT_OK;
+}
+
+// Raw outputs [n_pad][48] for n feature rows (device), no sync: the fused
+// tensor-core kernel, one launch.
 rt_status guide_infer_async(rt_guide *g, const float *feat, int64_t n, const float **raw_out, cudaStream_t st) {
+    rt_status s = ensure_scratch(g, n);
+    if (s != RT_OK) return s;
+    if ((s = mlp_kernel_attr((const void *)k_guide_mlp, kMlpSmem)) != RT_OK) return s;
+    const int64_t tiles = (n + kMlpTile - 1) / kMlpTile;
+    const int grid = (int)std::min<int64_t>(tiles, (int64_t)sm_count());
+    k_guide_mlp<<<grid, kMlpThreads, kMlpSmem, st>>>(guide_weights(g), ArrayFeatures{feat, (uint32_t)n}, g->raw, g->err);
+    RT_CUDA_TRY(cudaGetLastError());
+    *raw_out = g->raw;
+    return RT_OK;
+}
+
+// The same outputs layer by layer through gemm_bf16 (the training forward).
+rt_status guide_infer_layers_async(rt_guide *g, const float *feat, int64_t n, const float **raw_out, cudaStream_t st) {
     rt_status s = ensure_scratch(g, n);
     if (s != RT_OK) return s;
     s = forward(g, feat, n, false, st);
@@ -272,7 +351,7 @@ rt_status guide_train_async(rt_guide *g, const float *feat, const float *wi, con
     rt_status s = ensure_scratch(g, n);
     if (s != RT_OK) return s;
     for (uint32_t it = 0; it < std::max(1u, g->opts.train_steps); ++it) {
-        if ((s = forward(g, feat, n, true, st)) || (s = backward(g, wi, weight, n, st))) return s;
+        if ((s = train_forward(g, feat, wi, weight, n, st)) || (s = backward(g, n, st))) return s;
         ++g->step;
         float b1 = 0.9f, b2 = 0.999f;
         float c1 = 1.f - (float)std::pow(0.9, (double)g->step), c2 = 1.f - (float)std::pow(0.999, (double)g->step);
@@ -286,6 +365,15 @@ float guide_alpha(const rt_guide *g) { return g->opts.alpha; }
 void guide_bounds(const rt_guide *g, float3 &lo, float3 &hi) { lo = g->bb_lo; hi = g->bb_hi; }
 uint32_t guide_batch(const rt_guide *g) { return g->opts.batch; }
 bool guide_trained(const rt_guide *g) { return g->step > 0; }
+// Training cadence: after every set for the first kGuideWarmSteps steps, then
+// after every train_every-th set.
+constexpr int64_t kGuideWarmSteps = 32;
+bool guide_young(const rt_guide *g) { return g->step < kGuideWarmSteps; }
+bool guide_should_train(rt_guide *g) {
+    const uint64_t k = g->sets++;
+    const uint32_t every = std::max(1u, g->opts.train_every);
+    return g->step < kGuideWarmSteps || k % every == 0;
+}
 }  // namespace rtg
 
 extern "C" int64_t rt_guide_num_params(void) { return kGuideParams; }
@@ -404,6 +492,19 @@ extern "C" rt_status rt_guide_infer(const rt_guide *gc, const float *features, i
     return check_err(g, st);
 }
 
+extern "C" rt_status rt_debug_guide_infer_layers(const rt_guide *gc, const float *features, int64_t n, float *raw,
+                                                 void *stream) {
+    rt_guide *g = const_cast<rt_guide *>(gc);
+    if (!g || (n > 0 && (!features || !raw)) || n < 0) { set_error("rt_debug_guide_infer_layers: invalid argument"); return RT_INVALID_ARG; }
+    if (n == 0) return RT_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const float *r = nullptr;
+    rt_status s = guide_infer_layers_async(g, features, n, &r, st);
+    if (s != RT_OK) return s;
+    RT_CUDA_TRY(cudaMemcpy2DAsync(raw, kGuideOut * 4, r, kGuideOutPad * 4, kGuideOut * 4, n, cudaMemcpyDeviceToDevice, st));
+    return check_err(g, st);
+}
+
 extern "C" rt_status rt_guide_loss_grad(const rt_guide *gc, const float *features, const float *wi, const float *weight,
                                         int64_t n, float *grad, float *loss, void *stream) {
     rt_guide *g = const_cast<rt_guide *>(gc);
@@ -411,7 +512,7 @@ extern "C" rt_status rt_guide_loss_grad(const rt_guide *gc, const float *feature
     cudaStream_t st = (cudaStream_t)stream;
     rt_status s = ensure_scratch(g, n);
     if (s != RT_OK) return s;
-    if ((s = forward(g, features, n, true, st)) || (s = backward(g, wi, weight, n, st))) return s;
+    if ((s = train_forward(g, features, wi, weight, n, st)) || (s = backward(g, n, st))) return s;
     RT_CUDA_TRY(cudaMemcpyAsync(grad, g->grad, g->nparams * 4, cudaMemcpyDeviceToDevice, st));
     if (loss) RT_CUDA_TRY(cudaMemcpyAsync(loss, g->loss, 4, cudaMemcpyDeviceToHost, st));
     return check_err(g, st);

@@ -1,0 +1,250 @@
+// Fused inference of the guiding network on the tensor cores: one persistent
+// CTA of 512 threads per SM keeps all five BF16 weight matrices (58 KB) in
+// shared memory and walks tiles of 128 rows, four threads per row (part p =
+// warp / 4 of row 32 (warp % 4) + lane), so that each SM sub-partition has
+// four warps to switch between. For a tile, the part-0 threads fetch the
+// row's 7 features into shared memory; every thread builds a quarter of the
+// row's one-blob encoding (56 of 224 BF16 values); one elected thread issues
+// the tcgen05.mma of layer 1 (128 x 64 x 224, FP32 accumulator in tensor
+// memory); each warp reads 16 accumulator columns of its 32 rows back with
+// tcgen05.ld (a warp reaches the tensor-memory lanes 32 (warp % 4) + 0..31),
+// applies ReLU, rounds to BF16 and writes them into the next layer's A
+// operand in shared memory; layers 2-4 (64 -> 64) and 5 (64 -> 48, 40 used)
+// follow the same way, and the outputs go straight from tensor memory to
+// global memory. Nothing but the features and the outputs touches global
+// memory, and the whole network is one launch.
+//
+// Operands use the canonical no-swizzle K-major layout of umma.cuh. Every
+// wait on the tensor core is bounded; on a timeout the kernel sets *err and
+// stops. Results equal the layer-by-layer GEMM path (same BF16 inputs, same
+// K order of the accumulation).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "guide.cuh"
+#include "umma.cuh"
+
+namespace rtg {
+
+struct MlpWeights {
+    const __nv_bfloat16 *W[5];   // [out_pad][in] row-major BF16 (layer 5 padded to 48 rows)
+};
+
+// Training forward pass: besides the network outputs, the kernel keeps what
+// the backward pass needs (rows n..n_pad-1 zero): the one-blob input
+// transposed, XT [224][n_pad]; the hidden activations H_l [n_pad][64] and
+// their transposes HT_l [64][n_pad]; and, from the outputs, the gradient of
+// the loss sum_r weight_r * inv_n * -log q(wi_r) with respect to them,
+// dY [n_pad][48] and dYT [48][n_pad] (BF16), the loss summed into *loss.
+struct MlpTrain {
+    const float *wi, *weight;
+    float inv_n;
+    uint32_t n_pad;
+    __nv_bfloat16 *XT, *H[4], *HT[4], *dY, *dYT;
+    float *loss;
+};
+
+constexpr uint32_t kMlpTile = 128;      // rows per tile (the MMA's M)
+constexpr uint32_t kMlpThreads = 512;   // four threads per row
+constexpr uint32_t kMlpW1 = 0;                                            // 64 x 224
+constexpr uint32_t kMlpW2 = kMlpW1 + kGuideHid * kGuideIn * 2;           // 64 x 64
+constexpr uint32_t kMlpW3 = kMlpW2 + kGuideHid * kGuideHid * 2;
+constexpr uint32_t kMlpW4 = kMlpW3 + kGuideHid * kGuideHid * 2;
+constexpr uint32_t kMlpW5 = kMlpW4 + kGuideHid * kGuideHid * 2;          // 48 x 64
+constexpr uint32_t kMlpX = kMlpW5 + kGuideOutPad * kGuideHid * 2;        // 128 x 224
+constexpr uint32_t kMlpH = kMlpX + kMlpTile * kGuideIn * 2;              // 128 x 64
+constexpr uint32_t kMlpF = kMlpH + kMlpTile * kGuideHid * 2;             // 128 x 7 FP32 features
+constexpr uint32_t kMlpBar = kMlpF + kMlpTile * 8 * 4;                   // mbarrier, TMEM address
+constexpr uint32_t kMlpSmem = kMlpBar + 64;                              // 137,280 bytes
+constexpr uint32_t kMlpOut = kMlpSmem;                                   // training: 128 x 48 FP32 outputs
+constexpr uint32_t kMlpSmemTrain = kMlpOut + kMlpTile * kGuideOutPad * 4; // 161,856 bytes
+
+// Row-major [rows][kdim] BF16 from global memory into the canonical layout.
+__device__ __forceinline__ void mlp_stage_rows(unsigned char *dst, const __nv_bfloat16 *src, int rows, int kdim) {
+    const int chunks = kdim / 8;
+    for (int c = threadIdx.x; c < rows * chunks; c += blockDim.x) {
+        const int r = c / chunks, g8 = c % chunks;
+        const uint4 v = *(const uint4 *)(src + (size_t)r * kdim + 8 * g8);
+        *(uint4 *)(dst + umma::kmajor_offset((uint32_t)r, (uint32_t)(8 * g8), (uint32_t)kdim)) = v;
+    }
+}
+
+// Issue one layer: D[128 x n] = A[128 x k] * B[n x k]^T, K in steps of 16.
+__device__ __forceinline__ void mlp_issue(uint32_t taddr, uint32_t a0, uint32_t b0, uint32_t k, uint32_t n,
+                                          uint64_t *bar) {
+    const uint32_t idesc = umma::make_idesc_bf16(kMlpTile, n);
+    const uint32_t sbo = k / 8 * 128;
+    umma::fence_after_sync();
+    for (uint32_t kk = 0; kk < k / 16; ++kk) {
+        const uint64_t ad = umma::make_desc(a0 + kk * 256, 128, sbo);
+        const uint64_t bd = umma::make_desc(b0 + kk * 256, 128, sbo);
+        umma::mma_bf16(taddr, ad, bd, idesc, kk > 0 ? 1u : 0u);
+    }
+    umma::mma_commit(bar);
+}
+
+// Features: `void operator()(uint32_t row, float f[7]) const` (device) and
+// `uint32_t count() const` (rows to infer, read once per launch).
+template <bool kTrain, class Features>
+__device__ void mlp_tiles(const MlpWeights &w, const Features &feat, float *raw, uint32_t *err, const MlpTrain &tr) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *bar = (uint64_t *)(smem + kMlpBar);
+    uint32_t *s_taddr = (uint32_t *)(smem + kMlpBar + 16);
+    float *s_feat = (float *)(smem + kMlpF);
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
+    const uint32_t quarter = warp & 3u, part = warp >> 2;      // rows 32 quarter + lane, part 0..3
+    const uint32_t r = 32u * quarter + lane;                    // this thread's row in the tile
+    const uint32_t n = feat.count();
+    const uint32_t tiles = (n + kMlpTile - 1) / kMlpTile;
+    if (blockIdx.x >= tiles) return;
+    mlp_stage_rows(smem + kMlpW1, w.W[0], kGuideHid, kGuideIn);
+    mlp_stage_rows(smem + kMlpW2, w.W[1], kGuideHid, kGuideHid);
+    mlp_stage_rows(smem + kMlpW3, w.W[2], kGuideHid, kGuideHid);
+    mlp_stage_rows(smem + kMlpW4, w.W[3], kGuideHid, kGuideHid);
+    mlp_stage_rows(smem + kMlpW5, w.W[4], kGuideOutPad, kGuideHid);
+    if (warp == 0) umma::tmem_alloc(s_taddr, 64);
+    if (tid == 0) umma::mbar_init(bar, 1);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t taddr = *s_taddr;
+    const uint32_t lane_addr = taddr + ((32u * quarter) << 16);
+    const uint32_t sbase = umma::smem_addr(smem);
+    uint32_t phase = 0;
+    bool ok = true;
+    // Bounded wait for the layer just issued; the outcome is made uniform
+    // over the block, so that all threads leave (or stay) together.
+    auto wait_layer = [&]() -> bool {
+        const bool done = umma::mbar_wait(bar, phase);
+        phase ^= 1u;
+        return __syncthreads_and(done ? 1 : 0) != 0;
+    };
+    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const uint32_t row = t * kMlpTile + r;
+        if (part == 0) {
+            float f[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (row < n) feat(row, f);
+#pragma unroll
+            for (int k = 0; k < 7; ++k) s_feat[8 * r + k] = f[k];
+        }
+        __syncthreads();
+        // one-blob encoding: this part writes columns 56 part .. 56 part + 55
+        // (feature c / 32, bin c % 32), 8 at a time
+#pragma unroll 1
+        for (uint32_t j = 0; j < 7; ++j) {
+            const uint32_t col = 56u * part + 8u * j;
+            const float fv = s_feat[8 * r + col / kGuideBins];
+            __align__(16) __nv_bfloat16 b[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) b[e] = __float2bfloat16(oneblob_bin(fv, (int)(col % kGuideBins) + e));
+            *(uint4 *)(smem + kMlpX + umma::kmajor_offset(r, col, kGuideIn)) = *(const uint4 *)b;
+            if (kTrain) {
+                const __nv_bfloat16 z = __float2bfloat16(0.f);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) tr.XT[(size_t)(col + e) * tr.n_pad + row] = row < n ? b[e] : z;
+            }
+        }
+        umma::fence_proxy_async();
+        umma::fence_before_sync();
+        __syncthreads();
+        // layers 1..4: MMA, then ReLU -> BF16 -> the next layer's A operand
+#pragma unroll 1
+        for (int l = 0; l < 4; ++l) {
+            if (tid == 0) {
+                const uint32_t a0 = sbase + (l == 0 ? kMlpX : kMlpH);
+                const uint32_t b0 = sbase + (l == 0 ? kMlpW1 : (l == 1 ? kMlpW2 : (l == 2 ? kMlpW3 : kMlpW4)));
+                mlp_issue(taddr, a0, b0, l == 0 ? kGuideIn : kGuideHid, kGuideHid, bar);
+            }
+            if (!(ok = wait_layer())) break;
+            umma::fence_after_sync();
+            {
+                const uint32_t c0 = 16u * part;   // this warp's 16 columns
+                float v[16];
+                umma::tmem_ld16(lane_addr + c0, v);
+                __align__(16) __nv_bfloat16 b[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) b[e] = __float2bfloat16(row < n || !kTrain ? fmaxf(v[e], 0.f) : 0.f);
+                *(uint4 *)(smem + kMlpH + umma::kmajor_offset(r, c0, kGuideHid)) = *(const uint4 *)b;
+                *(uint4 *)(smem + kMlpH + umma::kmajor_offset(r, c0 + 8, kGuideHid)) = *(const uint4 *)(b + 8);
+                if (kTrain) {
+                    uint4 *hr = (uint4 *)(tr.H[l] + (size_t)row * kGuideHid + c0);
+                    hr[0] = *(const uint4 *)b;
+                    hr[1] = *(const uint4 *)(b + 8);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) tr.HT[l][(size_t)(c0 + e) * tr.n_pad + row] = b[e];
+                }
+            }
+            umma::fence_proxy_async();
+            umma::fence_before_sync();
+            __syncthreads();
+        }
+        if (!ok) break;
+        // layer 5: 48 outputs (40 used); parts 0..2 store 16 columns each
+        if (tid == 0) mlp_issue(taddr, sbase + kMlpH, sbase + kMlpW5, kGuideHid, kGuideOutPad, bar);
+        if (!(ok = wait_layer())) break;
+        umma::fence_after_sync();
+        if (part < 3) {
+            const uint32_t c0 = 16u * part;
+            float v[16];
+            umma::tmem_ld16(lane_addr + c0, v);
+            if (kTrain) {
+                float *so = (float *)(smem + kMlpOut) + r * kGuideOutPad + c0;
+#pragma unroll
+                for (int e = 0; e < 16; ++e) so[e] = v[e];
+            } else if (row < n) {
+                float4 *dst = (float4 *)(raw + (size_t)row * kGuideOutPad + c0);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+            }
+        }
+        if (kTrain) {
+            // loss and its gradient per row, from the row's 40 outputs
+            __syncthreads();
+            if (part == 0) {
+                float g[kGuideOutPad];
+#pragma unroll
+                for (int k = 0; k < kGuideOutPad; ++k) g[k] = 0.f;
+                float lw = 0.f;
+                if (row < n) {
+                    const float *so = (const float *)(smem + kMlpOut) + r * kGuideOutPad;
+                    const float w3[3] = {tr.wi[3 * (size_t)row], tr.wi[3 * (size_t)row + 1], tr.wi[3 * (size_t)row + 2]};
+                    lw = mixture_loss_grad(so, w3, tr.weight[row] * tr.inv_n, g);
+                }
+                __align__(16) __nv_bfloat16 b[kGuideOutPad];
+#pragma unroll
+                for (int k = 0; k < kGuideOutPad; ++k) b[k] = __float2bfloat16(g[k]);
+                uint4 *dr = (uint4 *)(tr.dY + (size_t)row * kGuideOutPad);
+#pragma unroll
+                for (int k = 0; k < kGuideOutPad / 8; ++k) dr[k] = ((const uint4 *)b)[k];
+#pragma unroll
+                for (int k = 0; k < kGuideOutPad; ++k) tr.dYT[(size_t)k * tr.n_pad + row] = b[k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) lw += __shfl_xor_sync(0xFFFFFFFFu, lw, o);
+                if (lane == 0) atomicAdd(tr.loss, lw);
+            }
+        }
+        // the accumulator, features, X and H are reused by the next tile
+        umma::fence_before_sync();
+        __syncthreads();
+    }
+    if (!ok) {
+        // the layer in flight may still complete: wait for it once more
+        // (bounded) before the tensor memory is released
+        if (tid == 0) {
+            umma::mbar_wait(bar, phase ^ 1u);
+            atomicExch(err, 1u);
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    if (warp == 0) umma::tmem_dealloc(taddr, 64);
+}
+
+template <class Features>
+__device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, float *raw, uint32_t *err) {
+    mlp_tiles<false>(w, feat, raw, err, MlpTrain{});
+}
+
+}  // namespace rtg

@@ -48,6 +48,14 @@ float guide_alpha(const rt_guide *g);
 void guide_bounds(const rt_guide *g, float3 &lo, float3 &hi);
 uint32_t guide_batch(const rt_guide *g);
 bool guide_trained(const rt_guide *g);
+bool guide_should_train(rt_guide *g);   // advances the set counter
+bool guide_young(const rt_guide *g);    // fewer than its warm-up training steps taken
+struct MlpWeights;
+MlpWeights guide_weights(const rt_guide *g);   // BF16 layers for the fused inference kernel
+uint32_t *guide_err(const rt_guide *g);        // set by a tensor-core wait that timed out
+rt_status guide_check(rt_guide *g, cudaStream_t st);   // RT_TIMEOUT (and clears) if it was set
+rt_status mlp_kernel_attr(const void *kernel, uint32_t bytes);  // shared-memory opt-in of a fused network kernel
+int sm_count();
 uint32_t nth_prime(int dim);
 
 }  // namespace rtg

@@ -19,6 +19,7 @@
 #include "internal.h"
 #include "shade.cuh"
 #include "trace_kernel.cuh"
+#include "guide_mlp.cuh"
 
 namespace rtg {
 
@@ -645,33 +646,47 @@ constexpr uint32_t kRecPending = 0x80000000u;
 
 // Network inputs of every vertex in the extension queue (zeros for misses
 // and for the last vertex, which only adds emission).
-__global__ void k_guide_features(RenderParams P, Pool pool, float *feat, float3 lo, float3 hi) {
-    Ctrl *c = pool.ctrl;
-    const uint32_t n = c->n_ext;
-    const uint32_t *queue = pool.q[c->cur];
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint32_t q = queue[i];
+// Network inputs of the paths in the extension queue (hit point, outgoing
+// direction and shading normal): the fused inference kernel builds them row
+// by row, reading the queue length on the device, so that no host round trip
+// sizes the launch.
+struct PathFeatures {
+    RenderParams P;
+    Pool pool;
+    float3 lo, hi;
+    __device__ uint32_t count() const { return pool.ctrl->n_ext; }
+    __device__ void operator()(uint32_t i, float f[7]) const {
+        const uint32_t q = pool.q[pool.ctrl->cur][i];
         PathState s = load_state(pool, q);
         float4 hv = pool.hit[q];
         Hit h;
         h.prim = __float_as_uint(hv.x); h.inst = P.sc.two_level ? pool.hit_inst[q] : 0u;
         h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
-        float f[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (h.prim != RT_MISS && s.depth <= P.max_depth) {
             Vertex vx;
             setup_vertex(P.sc, s, h, vx);
             guide_features(vx.x, vx.wo, vx.ns, lo, hi, f);
         }
-#pragma unroll
-        for (int k = 0; k < 7; ++k) feat[7 * (size_t)i + k] = f[k];
     }
+};
+
+__global__ void __launch_bounds__(512, 1) k_guide_mlp_paths(MlpWeights w, PathFeatures pf, float *raw, uint32_t *err) {
+    mlp_infer_tiles(w, pf, raw, err);
 }
 
-// Shading with the guided mixture; records (features, wi, throughput) of
-// every continuing vertex and, at the next vertex, the radiance gathered so
-// far, so that the radiance returned through wi is L_end - L_snapshot.
+// Shading with the guided mixture. Every rec_stride-th path of the set (at
+// most `batch` of them, spread over its pixels and passes) records
+// (features, wi, throughput) at every continuing vertex and, at the next
+// vertex, the radiance gathered so far, so that the radiance returned
+// through wi is L_end - L_snapshot; they are the training samples. Record
+// slot of path q: q / rec_stride.
+__device__ __forceinline__ bool recording_path(uint32_t q, uint32_t rec_stride, uint32_t batch) {
+    return q % rec_stride == 0u && q / rec_stride < batch;
+}
+
 __global__ void __launch_bounds__(128) k_shade_guided(RenderParams P, Pool pool, const float *raw, float alpha,
-                                                      float4 *rec, float3 lo, float3 hi) {
+                                                      float4 *rec, uint32_t rec_stride, uint32_t batch, float3 lo,
+                                                      float3 hi) {
     Ctrl *c = pool.ctrl;
     const uint32_t n = c->n_ext;
     const uint32_t cur = c->cur;
@@ -687,10 +702,12 @@ __global__ void __launch_bounds__(128) k_shade_guided(RenderParams P, Pool pool,
         if (valid) {
             q = queue[i];
             PathState s = load_state(pool, q);
-            uint32_t nr = pool.nrec[q];
+            const bool recording = recording_path(q, rec_stride, batch);
+            const uint32_t slot = q / rec_stride;
+            uint32_t nr = recording ? pool.nrec[q] : 0u;
             if (nr & kRecPending) {
                 nr &= ~kRecPending;
-                float4 *R = rec + ((size_t)q * kGuideMaxRec + (nr - 1)) * 4;
+                float4 *R = rec + ((size_t)slot * kGuideMaxRec + (nr - 1)) * 4;
                 R[3] = make_float4(R[3].x, s.L.x, s.L.y, s.L.z);
                 pool.nrec[q] = nr;
             }
@@ -701,7 +718,7 @@ __global__ void __launch_bounds__(128) k_shade_guided(RenderParams P, Pool pool,
             ShadowRay sh;
             GuideRecord gr;
             const uint32_t v = s.depth;
-            const bool want = v <= kGuideMaxRec;
+            const bool want = recording && v <= kGuideMaxRec;
             r = shade(P, s, h, sh, raw ? raw + (size_t)kGuideOutPad * i : nullptr, alpha, want ? &gr : nullptr, lo, hi);
             pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
             if (r & 1) {
@@ -709,7 +726,7 @@ __global__ void __launch_bounds__(128) k_shade_guided(RenderParams P, Pool pool,
                 pool.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);
                 pool.beta[q] = make_float4(s.beta.x, s.beta.y, s.beta.z, __uint_as_float(s.depth));
                 if (want) {
-                    float4 *R = rec + ((size_t)q * kGuideMaxRec + (v - 1)) * 4;
+                    float4 *R = rec + ((size_t)slot * kGuideMaxRec + (v - 1)) * 4;
                     R[0] = make_float4(gr.feat[0], gr.feat[1], gr.feat[2], gr.feat[3]);
                     R[1] = make_float4(gr.feat[4], gr.feat[5], gr.feat[6], gr.wi.x);
                     R[2] = make_float4(gr.wi.y, gr.wi.z, gr.beta.x, gr.beta.y);
@@ -731,15 +748,17 @@ __global__ void __launch_bounds__(128) k_shade_guided(RenderParams P, Pool pool,
 // Training samples of finished paths: weight = luminance of the radiance that
 // came back through wi divided by the throughput on arrival, i.e. the
 // sampled f cos Li / p of that vertex.
-__global__ void k_guide_collect(Pool pool, uint32_t n, const float4 *rec, float *tr_feat, float *tr_wi, float *tr_w,
-                                uint32_t batch) {
+__global__ void k_guide_collect(Pool pool, uint32_t n, const float4 *rec, uint32_t rec_stride, float *tr_feat,
+                                float *tr_wi, float *tr_w, uint32_t batch) {
     Ctrl *c = pool.ctrl;
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const uint32_t slots = min(batch, (n + rec_stride - 1) / rec_stride);
+    for (uint32_t k0 = blockIdx.x * blockDim.x + threadIdx.x; k0 < slots; k0 += gridDim.x * blockDim.x) {
+        const uint32_t q = k0 * rec_stride;
         uint32_t nr = pool.nrec[q];
         uint32_t complete = (nr & kRecPending) ? (nr & ~kRecPending) - 1 : nr;
         float4 L = pool.L[q];
         for (uint32_t k = 0; k < complete; ++k) {
-            const float4 *R = rec + ((size_t)q * kGuideMaxRec + k) * 4;
+            const float4 *R = rec + ((size_t)k0 * kGuideMaxRec + k) * 4;
             float4 r0 = R[0], r1 = R[1], r2 = R[2], r3 = R[3];
             float bx = r2.z, by = r2.w, bz = r3.x;
             float ax = bx > 0.f ? fmaxf(L.x - r3.y, 0.f) / bx : 0.f;
@@ -910,7 +929,8 @@ struct RenderCache {
     uint32_t sort_cap = 0, sort_nkeys = 0;
     // guided rendering
     uint32_t gcap = 0, gbatch = 0;
-    float *gfeat = nullptr, *tr_feat = nullptr, *tr_wi = nullptr, *tr_w = nullptr;
+    float *gfeat = nullptr;   // network outputs [cap][48] of one bounce step
+    float *tr_feat = nullptr, *tr_wi = nullptr, *tr_w = nullptr;
     float4 *grec = nullptr;
     uint32_t *gnrec = nullptr;
     ~RenderCache() {
@@ -930,8 +950,8 @@ static rt_status ensure_guided(RenderCache *rc, uint32_t cap, uint32_t batch) {
     rc->gfeat = rc->tr_feat = rc->tr_wi = rc->tr_w = nullptr;
     rc->grec = nullptr;
     rc->gnrec = nullptr;
-    if (cudaMalloc(&rc->gfeat, (size_t)cap * 7 * 4) != cudaSuccess ||
-        cudaMalloc(&rc->grec, (size_t)cap * kGuideMaxRec * 4 * sizeof(float4)) != cudaSuccess ||
+    if (cudaMalloc(&rc->gfeat, (size_t)cap * kGuideOutPad * 4) != cudaSuccess ||
+        cudaMalloc(&rc->grec, (size_t)std::min(cap, batch) * kGuideMaxRec * 4 * sizeof(float4)) != cudaSuccess ||
         cudaMalloc(&rc->gnrec, (size_t)cap * 4) != cudaSuccess ||
         cudaMalloc(&rc->tr_feat, (size_t)batch * 7 * 4) != cudaSuccess ||
         cudaMalloc(&rc->tr_wi, (size_t)batch * 3 * 4) != cudaSuccess ||
@@ -1105,10 +1125,15 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         // step the proposal is BSDF-only.
         rt_guide *gd = o.guide;
         const uint32_t batch = guide_batch(gd);
-        // one iteration set per training batch: the proposal improves every
-        // `batch` paths (2^16 by default)
+        // Iteration sets: while the proposal is young (fewer than 32 training
+        // steps) one training batch of paths per set, so that it learns
+        // fast; then 16 batches (2^20 paths by default; max_paths_in_flight
+        // overrides both), so that the per-set launches and the host round
+        // trip are spread over many paths. Each set ends with a training step
+        // on `batch` of its samples.
         const uint32_t cap_full = cap;
-        cap = std::min(cap, std::max(batch, 32u));
+        if (!o.max_paths_in_flight) cap = std::min<uint64_t>(cap, 16ull * std::max(batch, 32u));
+        const uint32_t cap_young = o.max_paths_in_flight ? cap : std::min(cap, std::max(batch, 32u));
         if ((rs = ensure_guided(rc, cap_full, batch)) != RT_OK) return rs;
         rc->pool.view.nrec = rc->gnrec;
         Pool gpool = rc->pool.view;
@@ -1119,38 +1144,39 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         const int g_ray = grid_for(k_raygen, 256, cap);
         const TraceKernels tk = trace_kernels(false, 0, s->dev.two_level, gbk);
         const int g_shade = grid_persistent(k_shade_guided, gbk, 0);
-        const int g_feat = grid_for(k_guide_features, 256, cap);
+        if ((rs = mlp_kernel_attr((const void *)k_guide_mlp_paths, kMlpSmem)) != RT_OK) return rs;
+        const PathFeatures pf{P, gpool, glo, ghi};
         rt_stats stats{};
         auto t_start = std::chrono::steady_clock::now();
         uint64_t t = film->next_task, t_end = (film->next_task / WH + (uint64_t)spp) * WH;
         rt_status result = RT_OK;
         while (t < t_end) {
+            const uint32_t cset = guide_young(gd) ? cap_young : cap;
             uint64_t n64;
             uint32_t passes = 0;
-            if (t % WH != 0 || WH > cap) {
-                n64 = std::min<uint64_t>({t_end - t, WH - t % WH, (uint64_t)cap});
+            if (t % WH != 0 || WH > cset) {
+                n64 = std::min<uint64_t>({t_end - t, WH - t % WH, (uint64_t)cset});
             } else {
-                uint64_t full = std::min<uint64_t>((t_end - t) / WH, cap / WH);
+                uint64_t full = std::min<uint64_t>((t_end - t) / WH, cset / WH);
                 if (full >= 1) { passes = (uint32_t)full; n64 = full * WH; }
-                else n64 = std::min<uint64_t>(t_end - t, cap);
+                else n64 = std::min<uint64_t>(t_end - t, cset);
             }
             uint32_t n = (uint32_t)n64;
             const float a = guide_trained(gd) ? alpha : 0.f;
+            const uint32_t rec_stride = std::max(1u, n / std::max(batch, 1u));
             k_raygen<<<g_ray, 256, 0, st>>>(P, gpool, t, n, (uint32_t)WH, 0u);
             stats.kernel_launches += 1;
+            // every bounce step runs on the device-side queue lengths: no
+            // host round trip until the set is done
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
                 tk.ext<<<tk.grid_ext, gbk, 0, st>>>(s->dev, gpool, nullptr);
-                RT_CUDA_TRY(cudaMemcpyAsync(rc->host_ctrl, gpool.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-                RT_CUDA_TRY(cudaStreamSynchronize(st));
-                const uint32_t n_ext = rc->host_ctrl->n_ext;
-                if (n_ext == 0) break;
-                const float *raw = nullptr;
                 if (a > 0.f) {
-                    k_guide_features<<<g_feat, 256, 0, st>>>(P, gpool, rc->gfeat, glo, ghi);
-                    if ((rs = guide_infer_async(gd, rc->gfeat, n_ext, &raw, st)) != RT_OK) return rs;
-                    stats.kernel_launches += 1 + 12;
+                    k_guide_mlp_paths<<<sm_count(), kMlpThreads, kMlpSmem, st>>>(guide_weights(gd), pf, rc->gfeat,
+                                                                            guide_err(gd));
+                    stats.kernel_launches += 1;
                 }
-                k_shade_guided<<<g_shade, gbk, 0, st>>>(P, gpool, raw, a, rc->grec, glo, ghi);
+                k_shade_guided<<<g_shade, gbk, 0, st>>>(P, gpool, a > 0.f ? rc->gfeat : nullptr, a, rc->grec,
+                                                        rec_stride, batch, glo, ghi);
                 tk.shadow<<<tk.grid_shadow, gbk, 0, st>>>(s->dev, gpool, nullptr);
                 k_step_end<<<1, 1, 0, st>>>(gpool);
                 stats.kernel_launches += 4;
@@ -1158,8 +1184,8 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
             }
             int g_film = grid_for(k_film, 256, passes ? WH : n);
             k_film<<<g_film, 256, 0, st>>>(gpool, film->sum, film->sum2, film->count, t, n, (uint32_t)WH, passes);
-            k_guide_collect<<<grid_for(k_guide_collect, 256, n), 256, 0, st>>>(gpool, n, rc->grec, rc->tr_feat,
-                                                                               rc->tr_wi, rc->tr_w, batch);
+            k_guide_collect<<<grid_for(k_guide_collect, 256, std::min(n, batch)), 256, 0, st>>>(
+                gpool, n, rc->grec, rec_stride, rc->tr_feat, rc->tr_wi, rc->tr_w, batch);
             stats.kernel_launches += 2;
             RT_CUDA_TRY(cudaGetLastError());
             RT_CUDA_TRY(cudaMemcpyAsync(rc->host_ctrl, gpool.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
@@ -1169,8 +1195,9 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
             stats.paths += n;
             ++stats.waves;
             if (rc->host_ctrl->overflow) { set_error("BVH traversal stack overflow"); result = RT_STACK_OVERFLOW; break; }
+            if ((rs = guide_check(gd, st)) != RT_OK) return rs;
             const uint32_t n_train = std::min(rc->host_ctrl->n_train, batch);
-            if (n_train >= 256) {
+            if (n_train >= 256 && guide_should_train(gd)) {
                 if ((rs = guide_train_async(gd, rc->tr_feat, rc->tr_wi, rc->tr_w, n_train, st)) != RT_OK) return rs;
                 stats.kernel_launches += 40;
             }

@@ -80,7 +80,7 @@ class rt_render_job(C.Structure):
 
 class rt_guide_opts(C.Structure):
     _fields_ = [("batch", C.c_uint32), ("learning_rate", C.c_float), ("alpha", C.c_float),
-                ("train_steps", C.c_uint32), ("seed", C.c_uint64)]
+                ("train_steps", C.c_uint32), ("seed", C.c_uint64), ("train_every", C.c_uint32)]
 
 
 _lib = None
@@ -136,6 +136,7 @@ def _declare(L):
         "rt_debug_render_host": [vp, C.POINTER(rt_camera), u32, C.POINTER(rt_render_opts), vp, vp, vp, i64, vp],
         "rt_debug_halton_host": [u32, u32, u64, vp, i64, i32, vp],
         "rt_debug_sample_index_host": [u32, u32, u32, u32, u32, C.POINTER(u64)],
+        "rt_debug_guide_infer_layers": [vp, vp, i64, vp, vp],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -463,8 +464,8 @@ def rt_gemm_bf16(A, B, C=None, accumulate=False, stream=None):
 class Guide:
     """Online path-guiding network (rt_guide_*)."""
 
-    def __init__(self, scene=None, batch=0, lr=0.0, alpha=0.0, train_steps=0, seed=0):
-        o = rt_guide_opts(batch, lr, alpha, train_steps, seed)
+    def __init__(self, scene=None, batch=0, lr=0.0, alpha=0.0, train_steps=0, seed=0, train_every=0):
+        o = rt_guide_opts(batch, lr, alpha, train_steps, seed, train_every)
         h = C.c_void_p()
         check(lib().rt_guide_create(scene.handle if scene is not None else None, C.byref(o), C.byref(h)))
         self.handle = h
@@ -498,6 +499,15 @@ class Guide:
         n = features.shape[0]
         raw = torch.empty((n, 40), dtype=torch.float32, device=features.device)
         check(lib().rt_guide_infer(self.handle, features.data_ptr(), n, raw.data_ptr(), _stream(stream)))
+        return raw
+
+    def infer_layers(self, features, stream=None):
+        """Test hook: the same outputs layer by layer through the GEMM path
+        the training forward pass uses (rt_guide_infer runs the fused kernel)."""
+        import torch
+        n = features.shape[0]
+        raw = torch.empty((n, 40), dtype=torch.float32, device=features.device)
+        check(lib().rt_debug_guide_infer_layers(self.handle, features.data_ptr(), n, raw.data_ptr(), _stream(stream)))
         return raw
 
     def loss_grad(self, features, wi, weight, stream=None):

@@ -71,6 +71,29 @@ def test_forward_matches_oracle():
     assert np.isfinite(raw).all()
 
 
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 5000, 70000])
+def test_fused_inference_equals_layer_by_layer(n):
+    """The fused kernel (one launch, weights and activations in shared and
+    tensor memory) and the GEMM path of the training forward pass take the
+    same BF16 operands and accumulate in the same K order, for ragged tiles
+    and for more tiles than SMs."""
+    from paper_1705_01263_gb300 import rt
+    guide = rt.Guide(seed=12)
+    x = torch.tensor(features(n, 2), dtype=torch.float32, device="cuda")
+    a = guide.infer(x).cpu().numpy()
+    b = guide.infer_layers(x).cpu().numpy()
+    assert np.isfinite(a).all()
+    assert np.abs(a - b).max() <= 1e-5 * max(1.0, np.abs(b).max()), np.abs(a - b).max()
+    # after training steps the weights the fused kernel stages change too
+    wi = torch.nn.functional.normalize(torch.randn(n, 3, device="cuda"), dim=1)
+    w = torch.rand(n, device="cuda")
+    guide.train_step(x, wi, w)
+    a2 = guide.infer(x).cpu().numpy()
+    b2 = guide.infer_layers(x).cpu().numpy()
+    assert np.abs(a2 - b2).max() <= 1e-5 * max(1.0, np.abs(b2).max())
+    assert np.abs(a2 - a).max() > 0
+
+
 def test_gradients_match_oracle():
     from paper_1705_01263_gb300 import rt
     guide = rt.Guide(seed=12)
