@@ -128,28 +128,34 @@ def cpu_baseline_oracle(sd, cam):
             "mrays_per_s": rays / dt / 1e6}
 
 
-def guided_vs_plain(target_spp=256, chunk=16, max_spp=1024, seed=5):
-    """Time to equal RMSE on the Cornell configuration (64 x 64, depth 8):
-    RMSE against the stored FP64 oracle reference (2^15 spp) after every
-    iteration set of `chunk` spp; the target is the plain tracer's RMSE at
-    `target_spp`; guided time includes its inference and training."""
+def guided_vs_plain(light="down", target_spp=16384, chunk=512, max_factor=2, seed=5):
+    """Time to equal RMSE, guided vs plain, on the Cornell configuration (64 x
+    64, depth 8): light "down" is the configuration itself; "up" turns the
+    emitter to face the ceiling, so that the room is lit through the bright
+    patch it makes there (the case a guide is for; on "down" the pixel error
+    is almost all direct light, which next-event estimation already samples).
+    RMSE against the stored FP64 oracle reference (2^15 spp from a disjoint
+    part of the sample sequence) after every call of `chunk` spp; the target
+    is the plain tracer's RMSE at `target_spp`; guided time includes its
+    inference and training from an untrained network."""
     import torch
     from paper_1705_01263_gb300 import rt, scenes
-    ref_path = os.path.join(ROOT, "tests", "golden", "cornell_64_depth8_ref.npz")
+    name = "cornell_64_depth8_ref.npz" if light == "down" else "cornell_up_64_depth8_ref.npz"
+    ref_path = os.path.join(ROOT, "tests", "golden", name)
     if not os.path.exists(ref_path):
         return None
     ref = np.load(ref_path)["mean"]
-    sd, cam = scenes.cornell_box()
+    sd, cam = scenes.cornell_box(light=light)
     scene = rt.Scene(sd)
     mean = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
 
-    def curve(guided):
+    def curve(guided, stop_rmse=None, max_spp=target_spp):
         film = rt.Film(cam.width, cam.height)
-        guide = rt.Guide(scene, seed=seed) if guided else None
         # warm-up of the code path on a scratch film (not timed)
         scratch = rt.Film(cam.width, cam.height)
         rt.rt_render(scene, cam, chunk, 8, scratch, rt.make_opts(guide=rt.Guide(scene, seed=seed + 1) if guided else None))
         torch.cuda.synchronize()
+        guide = rt.Guide(scene, seed=seed) if guided else None
         pts = []
         t0 = time.perf_counter()
         spp = 0
@@ -161,24 +167,28 @@ def guided_vs_plain(target_spp=256, chunk=16, max_spp=1024, seed=5):
             el = time.perf_counter() - t0
             img = mean.cpu().numpy().astype(np.float64)
             pts.append((spp, el, float(np.sqrt(np.mean((img - ref) ** 2)))))
-            if not guided and spp >= target_spp:
+            if stop_rmse is not None and pts[-1][2] <= stop_rmse:
                 break
         return pts
 
     plain = curve(False)
     target = plain[-1][2]
     t_plain = plain[-1][1]
-    guided = curve(True)
+    guided = curve(True, stop_rmse=target, max_spp=max_factor * target_spp)
     t_guided, spp_guided = None, None
     for spp, el, r in guided:
         if r <= target:
             t_guided, spp_guided = el, spp
             break
-    return {"scene": "cornell 64x64, depth 8", "reference": "FP64 oracle, 32768 spp", "target_rmse": target,
+    same = {p[0]: p[2] for p in plain}
+    per_sample = [(spp, same[spp], r) for spp, _, r in guided if spp in same]
+    return {"scene": f"cornell 64x64, depth 8, emitter {'under the ceiling facing down' if light == 'down' else 'facing the ceiling'}",
+            "reference": "FP64 oracle, 32768 spp from sequence iteration 2^20", "target_rmse": target,
             "target": f"plain RMSE at {target_spp} spp", "plain_seconds": t_plain, "plain_spp": plain[-1][0],
             "guided_seconds": t_guided, "guided_spp": spp_guided,
             "guided_speedup": (t_plain / t_guided) if t_guided else None,
-            "plain_curve": plain, "guided_curve": guided[:40]}
+            "rmse_at_equal_spp": per_sample[-4:],
+            "plain_curve": plain[::4], "guided_curve": guided[::4]}
 
 
 def many_lights(spp=4, depth=12):
@@ -441,7 +451,7 @@ def main():
     e2e_value = paths_per_step * world / (statistics.mean(e2e_ms) / 1e3) / 1e6
     gvp = None
     if rank == 0 and not args.no_guided:
-        gvp = guided_vs_plain()
+        gvp = {"indirect_lit": guided_vs_plain("up"), "config": guided_vs_plain("down")}
     ml = None
     if rank == 0 and not args.no_many_lights:
         ml = many_lights()

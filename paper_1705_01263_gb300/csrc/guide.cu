@@ -245,7 +245,8 @@ rt_status train_forward(rt_guide *g, const float *feat, const float *wi, const f
     tr.dY = g->dY;
     tr.dYT = g->dYT;
     tr.loss = g->loss;
-    const int grid = (int)std::min<int64_t>(n_pad / kMlpTile, (int64_t)sm_count());
+    const int grid = (int)std::min<int64_t>((n_pad + kMlpGroup * kMlpTile - 1) / (kMlpGroup * kMlpTile),
+                                            (int64_t)sm_count());
     k_guide_mlp_train<<<grid, kMlpThreads, kMlpSmemTrain, st>>>(guide_weights(g), ArrayFeatures{feat, (uint32_t)n},
                                                                  tr, g->err);
     RT_CUDA_TRY(cudaGetLastError());
@@ -329,8 +330,8 @@ rt_status guide_infer_async(rt_guide *g, const float *feat, int64_t n, const flo
     rt_status s = ensure_scratch(g, n);
     if (s != RT_OK) return s;
     if ((s = mlp_kernel_attr((const void *)k_guide_mlp, kMlpSmem)) != RT_OK) return s;
-    const int64_t tiles = (n + kMlpTile - 1) / kMlpTile;
-    const int grid = (int)std::min<int64_t>(tiles, (int64_t)sm_count());
+    const int64_t groups = (n + kMlpGroup * kMlpTile - 1) / (kMlpGroup * kMlpTile);
+    const int grid = (int)std::min<int64_t>(groups, (int64_t)sm_count());
     k_guide_mlp<<<grid, kMlpThreads, kMlpSmem, st>>>(guide_weights(g), ArrayFeatures{feat, (uint32_t)n}, g->raw, g->err);
     RT_CUDA_TRY(cudaGetLastError());
     *raw_out = g->raw;

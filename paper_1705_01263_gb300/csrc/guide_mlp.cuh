@@ -2,8 +2,10 @@
 // CTA of 512 threads per SM keeps all five BF16 weight matrices (58 KB) in
 // shared memory and walks tiles of 128 rows, four threads per row (part p =
 // warp / 4 of row 32 (warp % 4) + lane), so that each SM sub-partition has
-// four warps to switch between. For a tile, the part-0 threads fetch the
-// row's 7 features into shared memory; every thread builds a quarter of the
+// four warps to switch between. The CTA gathers the 7 features of four
+// tiles at once (one row per thread, so that the dependent loads behind a
+// feature overlap across 512 rows), then runs the tiles. For a tile, every
+// thread builds a quarter of the
 // row's one-blob encoding (56 of 224 BF16 values); one elected thread issues
 // the tcgen05.mma of layer 1 (128 x 64 x 224, FP32 accumulator in tensor
 // memory); each warp reads 16 accumulator columns of its 32 rows back with
@@ -54,11 +56,12 @@ constexpr uint32_t kMlpW4 = kMlpW3 + kGuideHid * kGuideHid * 2;
 constexpr uint32_t kMlpW5 = kMlpW4 + kGuideHid * kGuideHid * 2;          // 48 x 64
 constexpr uint32_t kMlpX = kMlpW5 + kGuideOutPad * kGuideHid * 2;        // 128 x 224
 constexpr uint32_t kMlpH = kMlpX + kMlpTile * kGuideIn * 2;              // 128 x 64
-constexpr uint32_t kMlpF = kMlpH + kMlpTile * kGuideHid * 2;             // 128 x 7 FP32 features
-constexpr uint32_t kMlpBar = kMlpF + kMlpTile * 8 * 4;                   // mbarrier, TMEM address
-constexpr uint32_t kMlpSmem = kMlpBar + 64;                              // 137,280 bytes
+constexpr uint32_t kMlpGroup = 4;                                        // tiles whose features are gathered together
+constexpr uint32_t kMlpF = kMlpH + kMlpTile * kGuideHid * 2;             // 512 x 8 FP32 features
+constexpr uint32_t kMlpBar = kMlpF + kMlpGroup * kMlpTile * 8 * 4;       // mbarrier, TMEM address
+constexpr uint32_t kMlpSmem = kMlpBar + 64;                              // 149,568 bytes
 constexpr uint32_t kMlpOut = kMlpSmem;                                   // training: 128 x 48 FP32 outputs
-constexpr uint32_t kMlpSmemTrain = kMlpOut + kMlpTile * kGuideOutPad * 4; // 161,856 bytes
+constexpr uint32_t kMlpSmemTrain = kMlpOut + kMlpTile * kGuideOutPad * 4; // 174,144 bytes
 
 // Row-major [rows][kdim] BF16 from global memory into the canonical layout.
 __device__ __forceinline__ void mlp_stage_rows(unsigned char *dst, const __nv_bfloat16 *src, int rows, int kdim) {
@@ -97,7 +100,8 @@ __device__ void mlp_tiles(const MlpWeights &w, const Features &feat, float *raw,
     const uint32_t r = 32u * quarter + lane;                    // this thread's row in the tile
     const uint32_t n = feat.count();
     const uint32_t tiles = (n + kMlpTile - 1) / kMlpTile;
-    if (blockIdx.x >= tiles) return;
+    const uint32_t groups = (tiles + kMlpGroup - 1) / kMlpGroup;
+    if (blockIdx.x >= groups) return;
     mlp_stage_rows(smem + kMlpW1, w.W[0], kGuideHid, kGuideIn);
     mlp_stage_rows(smem + kMlpW2, w.W[1], kGuideHid, kGuideHid);
     mlp_stage_rows(smem + kMlpW3, w.W[2], kGuideHid, kGuideHid);
@@ -120,21 +124,28 @@ __device__ void mlp_tiles(const MlpWeights &w, const Features &feat, float *raw,
         phase ^= 1u;
         return __syncthreads_and(done ? 1 : 0) != 0;
     };
-    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const uint32_t row = t * kMlpTile + r;
-        if (part == 0) {
-            float f[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (row < n) feat(row, f);
+    for (uint32_t gi = blockIdx.x; gi < groups; gi += gridDim.x) {
+      {
+        // features of the group's 512 rows, one per thread
+        const uint32_t grow = gi * kMlpGroup * kMlpTile + tid;
+        float f[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (grow < n) feat(grow, f);
+        __syncthreads();   // the previous group's last tile is done with s_feat
 #pragma unroll
-            for (int k = 0; k < 7; ++k) s_feat[8 * r + k] = f[k];
-        }
+        for (int k = 0; k < 7; ++k) s_feat[8 * tid + k] = f[k];
         __syncthreads();
+      }
+      for (uint32_t sub = 0; sub < kMlpGroup; ++sub) {
+        const uint32_t t = gi * kMlpGroup + sub;
+        if (t >= tiles) break;
+        const uint32_t row = t * kMlpTile + r;
+        const float *frow = s_feat + 8 * (sub * kMlpTile + r);
         // one-blob encoding: this part writes columns 56 part .. 56 part + 55
         // (feature c / 32, bin c % 32), 8 at a time
 #pragma unroll 1
         for (uint32_t j = 0; j < 7; ++j) {
             const uint32_t col = 56u * part + 8u * j;
-            const float fv = s_feat[8 * r + col / kGuideBins];
+            const float fv = frow[col / kGuideBins];
             __align__(16) __nv_bfloat16 b[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) b[e] = __float2bfloat16(oneblob_bin(fv, (int)(col % kGuideBins) + e));
@@ -224,9 +235,11 @@ __device__ void mlp_tiles(const MlpWeights &w, const Features &feat, float *raw,
                 if (lane == 0) atomicAdd(tr.loss, lw);
             }
         }
-        // the accumulator, features, X and H are reused by the next tile
+        // the accumulator, X and H are reused by the next tile
         umma::fence_before_sync();
         __syncthreads();
+      }
+      if (!ok) break;
     }
     if (!ok) {
         // the layer in flight may still complete: wait for it once more
