@@ -36,8 +36,8 @@ SPP, DEPTH = 64, 16
 # DRAM bytes (read + write) per extension ray of k_trace_ext_simple, measured
 # with ncu (dram__bytes_read.sum + dram__bytes_write.sum) over all 17 launches
 # of one 4-spp render of the same scene, caches as the program left them:
-# 1,893.6 MB for 19,024,330 rays.
-TRACE_EXT_DRAM_BYTES_PER_RAY = 99.5
+# 1,967.2 MB for 19,024,373 rays.
+TRACE_EXT_DRAM_BYTES_PER_RAY = 103.4
 
 
 def env_rank():
@@ -332,6 +332,10 @@ def main():
     ap.add_argument("--tail", type=int, default=0, help="live-path count below which the megakernel finishes a set (0 = default)")
     ap.add_argument("--render-once", action="store_true",
                     help="profiling aid: one untimed render of --spp, print its ray and launch counts, exit")
+    ap.add_argument("--scene", default="field", choices=["field", "cornell", "cornell-up"],
+                    help="scene of --render-once (cornell-up: emitter facing the ceiling)")
+    ap.add_argument("--guided", action="store_true",
+                    help="--render-once with the guiding network: three calls of --spp (the first trains it)")
     ap.add_argument("--spp", type=int, default=SPP)
     ap.add_argument("--out", default=None)
     ap.add_argument("--trace-kernel", type=int, default=0,
@@ -374,9 +378,19 @@ def main():
     film.seek(base_iter)
     if args.render_once:
         st = rt.rt_stats()
-        render_step(st)
+        what = WORKLOAD.replace("64 spp", f"{args.spp} spp")
+        if args.scene != "field" or args.guided:
+            csd, ccam = scenes.cornell_box(light="up" if args.scene == "cornell-up" else "down")
+            cscene = rt.Scene(csd)
+            cfilm = rt.Film(ccam.width, ccam.height)
+            guide = rt.Guide(cscene, seed=5) if args.guided else None
+            for _ in range(3 if args.guided else 1):
+                rt.rt_render(cscene, ccam, args.spp, 8, cfilm, rt.make_opts(guide=guide, stats=st))
+            what = f"{args.scene} 64x64, {args.spp} spp, depth 8" + (", guided, 3 calls" if args.guided else "")
+        else:
+            render_step(st)
         torch.cuda.synchronize()
-        print(json.dumps({"render_once": WORKLOAD.replace("64 spp", f"{args.spp} spp"), "paths": st.paths,
+        print(json.dumps({"render_once": what, "paths": st.paths,
                           "extension_rays": st.extension_rays, "shadow_rays": st.shadow_rays,
                           "trace_launches": st.trace_launches, "wavefront_steps": st.wavefront_steps}), flush=True)
         return 0
