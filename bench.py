@@ -105,6 +105,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def cpu_model():
+    """Host CPU model from /proc/cpuinfo (x86 "model name", Arm implementer /
+    part), or "unknown"."""
+    try:
+        txt = open("/proc/cpuinfo").read()
+    except OSError:
+        return "unknown"
+    for line in txt.splitlines():
+        if line.lower().startswith("model name"):
+            return line.split(":", 1)[1].strip()
+    impl = [l.split(":", 1)[1].strip() for l in txt.splitlines() if l.startswith("CPU implementer")]
+    part = [l.split(":", 1)[1].strip() for l in txt.splitlines() if l.startswith("CPU part")]
+    if impl and part:
+        return f"Arm implementer {impl[0]} part {part[0]}"
+    return "unknown"
+
+
 def cpu_baseline_oracle(sd, cam):
     """The FP64 oracle as it stands, on all host cores, on a bounded sample of
     the workload: the full scene and image at 8 of the 64 spp (about 10-20 s
@@ -125,7 +142,7 @@ def cpu_baseline_oracle(sd, cam):
     return {"value": paths / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{W}x{H} px x {spp} spp of the same scene and camera (depth {DEPTH}), "
                       f"{paths} paths in {dt:.1f} s; oracle BVH build {build_s:.1f} s not timed",
-            "mrays_per_s": rays / dt / 1e6}
+            "mrays_per_s": rays / dt / 1e6, "cpu": cpu_model()}
 
 
 def guided_vs_plain(light="down", target_spp=16384, chunk=512, max_factor=2, seed=5):
@@ -310,7 +327,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "reference_sample": f"{W}x{H} px, 1 spp per step"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                              "sample": f"{W}x{H} px x 1 spp per step of the same scene/camera, depth {DEPTH}"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
