@@ -84,6 +84,7 @@ def _declare(L):
         "or_filter_offset": (None, [f64, f64, f64, vp, vp]),
         "or_render": (None, [vp, C.POINTER(_Cam), u32, u32, u32, C.POINTER(_Opts), vp, vp, vp, vp]),
         "or_render_pixels": (None, [vp, C.POINTER(_Cam), vp, vp, vp, i64, u32, C.POINTER(_Opts), vp]),
+        "or_render_probes": (None, [vp, vp, vp, u32, u32, u32, u32, C.POINTER(_Opts), vp, vp, vp, vp]),
         "or_vmf_pdf": (f64, [f64, vp, vp]),
         "or_vmf_sample": (None, [f64, vp, f64, f64, vp]),
         "or_oneblob": (None, [vp, vp]),
@@ -239,6 +240,21 @@ class Scene:
         lib().or_render_pixels(self.handle, C.byref(c), _p(px), _p(py), _p(sj), px.size, max_depth,
                                C.byref(o), _p(L))
         return L
+
+    def render_probes(self, pos, nrm, spp: int, max_depth: int, iter0: int = 0, mis_mode: int = 0,
+                      seed: int = 0, rr: bool = False):
+        """Irradiance probes (Sec. 4.2): per probe the sums of E, E^2 and the
+        sample count over iterations [iter0, iter0 + spp)."""
+        pos = np.ascontiguousarray(pos, np.float64).reshape(-1, 3)
+        nrm = np.ascontiguousarray(nrm, np.float64).reshape(-1, 3)
+        n = pos.shape[0]
+        o = _Opts(0.5, int(rr), mis_mode, seed, 1)
+        S, S2 = np.zeros((n, 3)), np.zeros((n, 3))
+        cnt = np.zeros(n, np.uint32)
+        rays = np.zeros(1, np.uint64)
+        lib().or_render_probes(self.handle, _p(pos), _p(nrm), n, iter0, spp, max_depth, C.byref(o), _p(S), _p(S2),
+                               _p(cnt), _p(rays))
+        return S, S2, cnt, int(rays[0])
 
 
 def _camera(cam) -> _Cam:

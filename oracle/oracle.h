@@ -140,6 +140,11 @@ void or_render_pixels(const or_scene *s, const or_camera *cam,
                       const uint32_t *px, const uint32_t *py,
                       const uint32_t *sample_j, int64_t n, uint32_t max_depth,
                       const or_render_opts *opts, double *L /* n x 3 */);
+/* Irradiance probes (see render.c): sums of E = pi L per probe. */
+void or_render_probes(const or_scene *s, const double *pos, const double *nrm, uint32_t n,
+                      uint32_t iter0, uint32_t spp, uint32_t max_depth,
+                      const or_render_opts *opts, double *sum, double *sum2,
+                      uint32_t *count, uint64_t *rays_traced);
 
 /* ----------------------------------------------------------------- guide.c */
 #define OR_GUIDE_BINS 32

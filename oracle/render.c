@@ -99,23 +99,36 @@ static double dimv(const ctx_t *c, uint64_t idx, int dim) {
     return or_sample_dim(idx, dim, c->k, c->l, c->factors);
 }
 
-/* Radiance of one camera path (sequence index idx through pixel px, py). */
+/* Radiance of one camera path (sequence index idx through pixel px, py), or,
+ * with probe_x and probe_n given, the irradiance estimate of one probe path
+ * (Sec. 4.2, alternate outputs: irradiance at a point from the hemisphere
+ * around a normal). Reading: the probe is vertex 1, a virtual white
+ * Lambertian surface point (albedo 1, geometric and shading normal probe_n,
+ * wo = probe_n) that emits nothing; its outgoing radiance is E / pi, so the
+ * path's radiance times pi estimates E. The vertices after it are those of a
+ * camera path, with the same dimension allocation. */
 static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
-                          uint32_t py, double L[3], uint64_t *rays) {
+                          uint32_t py, const double *probe_x, const double *probe_n,
+                          double L[3], uint64_t *rays) {
     const or_scene *s = c->s;
     int mode = c->opts->mis_mode;
     L[0] = L[1] = L[2] = 0.0;
-    double dx, dy;
-    or_filter_offset(c->opts->filter_sigma, dimv(c, idx, 0), dimv(c, idx, 1), &dx, &dy);
-    double o[3], d[3];
-    or_camera_ray(c->cam, (double)px + 0.5 + dx, (double)py + 0.5 + dy, o, d);
+    double o[3] = {0.0, 0.0, 0.0}, d[3] = {0.0, 0.0, 1.0};
+    if (!probe_x) {
+        double dx, dy;
+        or_filter_offset(c->opts->filter_sigma, dimv(c, idx, 0), dimv(c, idx, 1), &dx, &dy);
+        or_camera_ray(c->cam, (double)px + 0.5 + dx, (double)py + 0.5 + dy, o, d);
+    }
     double beta[3] = {1.0, 1.0, 1.0};
     double prev_pdf = 0.0;
     int has_tris = s->nlights > 0, has_env = s->p_env > 0.0;
     for (uint32_t v = 1; v <= c->D + 1; ++v) {
-        uint32_t prim; double t, b1, b2;
-        or_trace_one(s, o, d, 0.0, INFINITY, 0, &prim, &t, &b1, &b2);
-        ++*rays;
+        const int at_probe = probe_x && v == 1;
+        uint32_t prim = 0; double t = 0.0, b1 = 0.0, b2 = 0.0;
+        if (!at_probe) {
+            or_trace_one(s, o, d, 0.0, INFINITY, 0, &prim, &t, &b1, &b2);
+            ++*rays;
+        }
         if (prim == OR_MISS) {
             if (s->d.env) {
                 double Le[3];
@@ -130,15 +143,19 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
             }
             break;
         }
-        const double *vv = s->v64 + 9 * (size_t)prim;
+        double x[3], ng[3], wo[3], cog;
         double b0 = 1.0 - b1 - b2;
-        double x[3];
-        for (int a = 0; a < 3; ++a) x[a] = b0 * vv[a] + b1 * vv[3 + a] + b2 * vv[6 + a];
-        double ng[3] = {s->ng[3 * prim], s->ng[3 * prim + 1], s->ng[3 * prim + 2]};
-        double wo[3] = {-d[0], -d[1], -d[2]};
-        double cog = dot3(wo, ng);
-        uint32_t m = s->d.tri_material[prim];
-        if (cog > 0.0 && s->tri_light_pdf_area[prim] > 0.0) {
+        if (at_probe) {
+            for (int a = 0; a < 3; ++a) { x[a] = probe_x[a]; ng[a] = probe_n[a]; wo[a] = probe_n[a]; }
+            cog = 1.0;
+        } else {
+            const double *vv = s->v64 + 9 * (size_t)prim;
+            for (int a = 0; a < 3; ++a) x[a] = b0 * vv[a] + b1 * vv[3 + a] + b2 * vv[6 + a];
+            for (int a = 0; a < 3; ++a) { ng[a] = s->ng[3 * prim + a]; wo[a] = -d[a]; }
+            cog = dot3(wo, ng);
+        }
+        uint32_t m = at_probe ? 0u : s->d.tri_material[prim];
+        if (!at_probe && cog > 0.0 && s->tri_light_pdf_area[prim] > 0.0) {
             double Le[3];
             or_tri_emission(s, prim, b1, b2, Le);
             double w = 1.0;
@@ -152,7 +169,7 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
         if (v == c->D + 1) break;
         if (cog < 0.0) { ng[0] = -ng[0]; ng[1] = -ng[1]; ng[2] = -ng[2]; }
         double ns[3] = {ng[0], ng[1], ng[2]};
-        if (s->d.normals) {
+        if (s->d.normals && !at_probe) {
             const uint32_t *id = s->d.indices + 3 * (size_t)prim;
             for (int a = 0; a < 3; ++a)
                 ns[a] = b0 * s->d.normals[3 * (size_t)id[0] + a] + b1 * s->d.normals[3 * (size_t)id[1] + a] +
@@ -164,6 +181,7 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
         or_adapt_shading_normal(ns, ng, wo, nsa);
         double albedo[3] = {s->d.albedo[3 * m], s->d.albedo[3 * m + 1], s->d.albedo[3 * m + 2]};
         double rough = s->d.roughness[m], gw = s->d.ggx_weight[m];
+        if (at_probe) { albedo[0] = albedo[1] = albedo[2] = 1.0; gw = 0.0; }
         int base = 2 + 7 * (int)(v - 1);
         double xo[3];
         offset_origin(x, ng, xo);
@@ -275,7 +293,7 @@ static void *render_rows(void *arg) {
             for (uint32_t s = j->iter0; s < j->iter0 + j->spp; ++s) {
                 uint64_t idx = i0 + (uint64_t)s * p2 * p3;
                 double L[3];
-                path_radiance(c, idx, x, y, L, &j->rays);
+                path_radiance(c, idx, x, y, NULL, NULL, L, &j->rays);
                 for (int a = 0; a < 3; ++a) {
                     j->sum[3 * p + a] += L[a];
                     j->sum2[3 * p + a] += L[a] * L[a];
@@ -324,7 +342,41 @@ void or_render_pixels(const or_scene *s, const or_camera *cam,
     uint64_t rays = 0;
     for (int64_t r = 0; r < n; ++r) {
         uint64_t i0 = or_pixel_base_index(cam->width, cam->height, px[r], py[r]);
-        path_radiance(&c, i0 + (uint64_t)sample_j[r] * p2 * p3, px[r], py[r], L + 3 * r, &rays);
+        path_radiance(&c, i0 + (uint64_t)sample_j[r] * p2 * p3, px[r], py[r], NULL, NULL, L + 3 * r, &rays);
     }
+    free(c.factors);
+}
+
+/* Irradiance probes: probe p (position pos[3p..], unit normal nrm[3p..]) is
+ * the pixel (p, 0) of an n x 1 image for the sample enumeration; iterations
+ * [iter0, iter0 + spp); per probe the sums of E = pi L, of E^2 and the
+ * sample count. */
+void or_render_probes(const or_scene *s, const double *pos, const double *nrm, uint32_t n,
+                      uint32_t iter0, uint32_t spp, uint32_t max_depth,
+                      const or_render_opts *opts, double *sum, double *sum2,
+                      uint32_t *count, uint64_t *rays_traced) {
+    or_camera cam;
+    memset(&cam, 0, sizeof cam);
+    cam.width = n;
+    cam.height = 1;
+    ctx_t c;
+    ctx_init(&c, s, &cam, max_depth, opts);
+    uint32_t k, l; uint64_t p2, p3;
+    or_enum_params(n, 1, &k, &l, &p2, &p3);
+    uint64_t rays = 0;
+    for (uint32_t p = 0; p < n; ++p) {
+        uint64_t i0 = or_pixel_base_index(n, 1, p, 0);
+        for (uint32_t j = iter0; j < iter0 + spp; ++j) {
+            double L[3];
+            path_radiance(&c, i0 + (uint64_t)j * p2 * p3, p, 0, pos + 3 * (size_t)p, nrm + 3 * (size_t)p, L, &rays);
+            for (int a = 0; a < 3; ++a) {
+                double e = OR_PI * L[a];
+                sum[3 * (size_t)p + a] += e;
+                sum2[3 * (size_t)p + a] += e * e;
+            }
+            count[p] += 1;
+        }
+    }
+    if (rays_traced) *rays_traced = rays;
     free(c.factors);
 }
