@@ -209,6 +209,24 @@ rt_status rt_film_resolve(const rt_film *film, float *mean, float *var, void *st
 rt_status rt_render(const rt_scene *scene, const rt_camera *camera, uint32_t spp,
                     uint32_t max_depth, rt_film *film, const rt_render_opts *opts, void *stream);
 
+/* Irradiance probes (Sec. 4.2, alternate outputs): instead of camera rays,
+ * n probe points with normals; each probe's film pixel accumulates estimates
+ * of the irradiance E = integral over the hemisphere around its normal of
+ * L cos(theta), sampled progressively like a pixel (probe p is the pixel
+ * (p, 0) of an n x 1 image for the sample enumeration). A probe path starts
+ * at a virtual white Lambertian point (vertex 1: NEE and a cosine-sampled
+ * continuation, no emission) and continues as a camera path; max_depth counts
+ * the probe as vertex 1, so 1 = direct irradiance.
+ *   pos, nrm: DEVICE float arrays [n][3] (normals need not be unit length;
+ *             caller-owned, read during the call)
+ *   film:     created as rt_film_create(n, 1); iterations continue from its
+ *             next iteration like rt_render; resolve gives E per probe
+ *   opts:     as rt_render (guide must be NULL: RT_NOT_SUPPORTED)
+ * Errors: RT_INVALID_ARG (null pointers, film not n x 1, max_depth out of
+ * [1, 64]), RT_TIMEOUT (time budget / abort flag: resumable), as rt_render. */
+rt_status rt_render_probes(const rt_scene *scene, const float *pos, const float *nrm, uint32_t n, uint32_t spp,
+                           uint32_t max_depth, rt_film *film, const rt_render_opts *opts, void *stream);
+
 /* Rendering that allocates nothing (the paper has no counterpart).
  * For callers that cannot call cudaMalloc or let a library do so - code
  * inside a host framework that owns all device memory through its own

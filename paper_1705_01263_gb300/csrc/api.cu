@@ -225,6 +225,68 @@ extern "C" rt_status rt_debug_render_host(const rt_scene *s, const rt_camera *ca
     return RT_OK;
 }
 
+/* Host execution of irradiance-probe paths (same code as the kernels):
+ * E of sample j[i] of probe p[i] of the n probes pos/nrm (host arrays). */
+extern "C" rt_status rt_debug_render_probes_host(const rt_scene *s, const float *pos, const float *nrm, uint32_t n,
+                                                 uint32_t max_depth, const rt_render_opts *opts, const uint32_t *p,
+                                                 const uint32_t *j, int64_t count, float *E) {
+    if (!s || !s->host_only || !pos || !nrm || n == 0) {
+        set_error("rt_debug_render_probes_host: needs a host-only scene and probes");
+        return RT_INVALID_ARG;
+    }
+    rt_render_opts o{};
+    if (opts) o = *opts;
+    std::vector<HaltonDim> dims = make_dims(o.seed, 2 + 7 * (int)(max_depth + 1));
+    rt_camera cam{};
+    cam.width = n;
+    cam.height = 1;
+    cam.look_at[2] = 1.f;
+    cam.up[1] = 1.f;
+    cam.vfov_deg = 45.f;
+    RenderParams P;
+    P.sc = s->host;
+    P.cam = make_camera(cam);
+    P.en = make_enum(n, 1);
+    P.dims = dims.data();
+    P.max_depth = max_depth;
+    P.sigma = 0.5f;
+    P.mis_mode = o.mis_mode;
+    P.rr = o.rr_enable;
+    const DevScene *sc = &s->host;
+    auto closest = [sc](V3 oo, V3 dd, Hit &h) {
+        Ray r{oo, dd, 0.f, INFINITY};
+        h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
+        trace_scene<false>(*sc, r, h);
+    };
+    auto any = [sc](V3 oo, V3 dd, float tmax) {
+        Ray r{oo, dd, 0.f, tmax};
+        Hit h;
+        h.prim = RT_MISS; h.inst = 0; h.t = INFINITY;
+        trace_scene<true>(*sc, r, h);
+        return h.prim != RT_MISS;
+    };
+    for (int64_t i = 0; i < count; ++i) {
+        if (p[i] >= n) { set_error("rt_debug_render_probes_host: probe index out of range"); return RT_INVALID_ARG; }
+        PathState st;
+        st.index = pixel_base_index(P.en, p[i], 0) + (uint64_t)j[i] * P.en.period;
+        st.pixel = p[i];
+        st.depth = 1;
+        st.beta = v3(kPi, kPi, kPi);
+        st.L = v3(0.f, 0.f, 0.f);
+        st.prev_pdf = 0.f;
+        st.o = st.d = v3(0.f, 0.f, 0.f);
+        const V3 x = v3(pos[3 * (size_t)p[i]], pos[3 * (size_t)p[i] + 1], pos[3 * (size_t)p[i] + 2]);
+        const V3 nn = normalize(v3(nrm[3 * (size_t)p[i]], nrm[3 * (size_t)p[i] + 1], nrm[3 * (size_t)p[i] + 2]));
+        ShadowRay sh;
+        int r = probe_vertex(P, st, x, nn, sh);
+        if ((r & 2) && !any(sh.o, sh.d, sh.tmax)) st.L = st.L + sh.contrib;
+        uint32_t e = 0, shc = 0;
+        if (r & 1) finish_path(P, st, closest, any, e, shc);
+        E[3 * i] = st.L.x; E[3 * i + 1] = st.L.y; E[3 * i + 2] = st.L.z;
+    }
+    return RT_OK;
+}
+
 /* Host execution of the Halton routine (same code as the kernels). */
 extern "C" rt_status rt_debug_halton_host(uint32_t W, uint32_t H, uint64_t seed, const uint64_t *idx, int64_t n,
                                           int32_t ndims, uint32_t *out) {

@@ -549,6 +549,67 @@ __global__ void __launch_bounds__(128) k_megakernel(RenderParams P, Pool pool) {
 // Film accumulation, owner-exclusive per pixel (deterministic order).
 // passes > 0: the wave holds `passes` whole passes, slot = pass * WH + pixel.
 // passes == 0: the wave holds n <= WH distinct consecutive pixels from t0.
+// Irradiance probes (Sec. 4.2). Task t is sample t / n of probe t % n, the
+// pixel (p, 0) of an n x 1 image for the sample enumeration. The probe
+// vertex (vertex 1) is shaded here with throughput pi (its radiance times pi
+// is the irradiance); every path continues into the extension queue, NEE
+// shadow rays go to the shadow queue. The counters are set by k_probe_reset.
+__global__ void k_probe_reset(Pool pool) {
+    Ctrl *c = pool.ctrl;
+    c->n_ext = 0;
+    c->n_next = 0;
+    c->n_shadow = 0;
+    c->cur = 0;
+    c->fetch_ext = 0;
+    c->fetch_shadow = 0;
+    c->fetch_shade = 0;
+    c->n_train = 0;
+    c->tail_threshold = 0;
+    c->tail = 0;
+}
+
+__global__ void k_probe_start(RenderParams P, Pool pool, const float *pos, const float *nrm, uint64_t t0, uint32_t n,
+                              uint32_t WH) {
+    Ctrl *c = pool.ctrl;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t b = blockIdx.x * blockDim.x; b < n; b += stride) {   // uniform per warp (warp_append)
+        const uint32_t q = b + threadIdx.x;
+        const bool valid = q < n;
+        int r = 0;
+        if (valid) {
+            const uint64_t t = t0 + q;
+            const uint32_t p = (uint32_t)(t % WH), j = (uint32_t)(t / WH);
+            PathState s;
+            s.index = pixel_base_index(P.en, p, 0) + (uint64_t)j * P.en.period;
+            s.pixel = p;
+            s.depth = 1;
+            s.beta = v3(kPi, kPi, kPi);
+            s.L = v3(0.f, 0.f, 0.f);
+            s.prev_pdf = 0.f;
+            s.o = s.d = v3(0.f, 0.f, 0.f);
+            const V3 x = v3(pos[3 * (size_t)p], pos[3 * (size_t)p + 1], pos[3 * (size_t)p + 2]);
+            const V3 nn = normalize(v3(nrm[3 * (size_t)p], nrm[3 * (size_t)p + 1], nrm[3 * (size_t)p + 2]));
+            ShadowRay sh;
+            r = probe_vertex(P, s, x, nn, sh);
+            store_state(pool, q, s);
+            if (r & 2) {
+                pool.sh_o[q] = make_float4(sh.o.x, sh.o.y, sh.o.z, sh.tmax);
+                pool.sh_d[q] = make_float4(sh.d.x, sh.d.y, sh.d.z, 0.f);
+                pool.sh_c[q] = make_float4(sh.contrib.x, sh.contrib.y, sh.contrib.z, 0.f);
+            }
+        }
+        warp_append(pool.q[0], &c->n_ext, valid && (r & 1), q);
+        warp_append(pool.qs, &c->n_shadow, valid && (r & 2), q);
+    }
+}
+
+// After the probe vertex's shadow rays are traced: an empty shadow queue.
+__global__ void k_probe_shadow_done(Pool pool) {
+    Ctrl *c = pool.ctrl;
+    c->n_shadow = 0;
+    c->fetch_shadow = 0;
+}
+
 __global__ void k_film(Pool pool, double *sum, double *sum2, uint32_t *count, uint64_t t0, uint32_t n, uint32_t WH,
                        uint32_t passes) {
     uint32_t m = passes ? WH : n;
@@ -1453,6 +1514,111 @@ static rt_status static_arena(unsigned char **out) {
 }
 
 }  // namespace rtg
+
+extern "C" rt_status rt_render_probes(const rt_scene *s, const float *pos, const float *nrm, uint32_t n,
+                                      uint32_t spp, uint32_t max_depth, rt_film *film, const rt_render_opts *opts_in,
+                                      void *stream) {
+    if (!s || !film || (n > 0 && (!pos || !nrm))) { set_error("rt_render_probes: null argument"); return RT_INVALID_ARG; }
+    if (s->host_only) { set_error("rt_render_probes: scene has no device copy"); return RT_INVALID_ARG; }
+    if (n == 0 || film->W != n || film->H != 1) {
+        set_error("rt_render_probes: the film must be n x 1 for n > 0 probes");
+        return RT_INVALID_ARG;
+    }
+    if (max_depth < 1 || max_depth > (uint32_t)kMaxDepth) { set_error("rt_render_probes: max_depth must be in [1, 64]"); return RT_INVALID_ARG; }
+    rt_render_opts o{};
+    if (opts_in) o = *opts_in;
+    if (o.guide) { set_error("rt_render_probes: guiding needs rt_render"); return RT_NOT_SUPPORTED; }
+    if (spp == 0) return RT_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    RenderCache *rc = cache_of(film);
+    const uint64_t WH = n;
+    uint32_t cap = o.max_paths_in_flight ? o.max_paths_in_flight
+                                         : default_capacity((film->next_task / WH + (uint64_t)spp) * WH - film->next_task);
+    cap = std::max<uint32_t>(cap, 32u);
+    rt_status rs = ensure_pool(rc->pool, cap);
+    if (rs != RT_OK) return rs;
+    const int ndims = 2 + 7 * (int)(max_depth + 1);
+    if (!rc->dims || rc->dims_seed != o.seed || rc->dims_n < ndims) {
+        std::vector<HaltonDim> d = make_dims(o.seed, ndims);
+        if (rc->dims) cudaFree(rc->dims);
+        RT_CUDA_TRY(cudaMalloc(&rc->dims, d.size() * sizeof(HaltonDim)));
+        RT_CUDA_TRY(cudaMemcpy(rc->dims, d.data(), d.size() * sizeof(HaltonDim), cudaMemcpyHostToDevice));
+        rc->dims_seed = o.seed;
+        rc->dims_n = ndims;
+    }
+    rt_camera cam{};
+    cam.width = n;
+    cam.height = 1;
+    cam.look_at[2] = 1.f;
+    cam.up[1] = 1.f;
+    cam.vfov_deg = 45.f;
+    RenderParams P;
+    P.sc = s->dev;
+    P.cam = make_camera(cam);
+    P.en = make_enum(n, 1);
+    P.dims = rc->dims;
+    P.max_depth = max_depth;
+    P.sigma = 0.5f;
+    P.mis_mode = o.mis_mode;
+    P.rr = o.rr_enable;
+    Pool pool = rc->pool.view;
+    RT_CUDA_TRY(cudaMemsetAsync(pool.ctrl, 0, sizeof(Ctrl), st));
+    const int gb = 128;
+    const TraceKernels tk = trace_kernels(false, 0, s->dev.two_level, gb);
+    const int g_start = grid_for(k_probe_start, 256, cap);
+    const int g_shade = grid_persistent(k_shade, gb, 0);
+    rt_stats stats{};
+    Ctrl host_ctrl{};
+    auto t_start = std::chrono::steady_clock::now();
+    uint64_t t = film->next_task, t_end = (film->next_task / WH + (uint64_t)spp) * WH;
+    rt_status result = RT_OK;
+    while (t < t_end) {
+        uint64_t n64;
+        uint32_t passes = 0;
+        if (t % WH != 0 || WH > cap) {
+            n64 = std::min<uint64_t>({t_end - t, WH - t % WH, (uint64_t)cap});
+        } else {
+            uint64_t full = std::min<uint64_t>((t_end - t) / WH, cap / WH);
+            if (full >= 1) { passes = (uint32_t)full; n64 = full * WH; }
+            else n64 = std::min<uint64_t>(t_end - t, cap);
+        }
+        const uint32_t ns = (uint32_t)n64;
+        k_probe_reset<<<1, 1, 0, st>>>(pool);
+        k_probe_start<<<g_start, 256, 0, st>>>(P, pool, pos, nrm, t, ns, (uint32_t)WH);
+        tk.shadow<<<tk.grid_shadow, gb, tk.smem, st>>>(s->dev, pool, nullptr);
+        k_probe_shadow_done<<<1, 1, 0, st>>>(pool);
+        stats.kernel_launches += 4;
+        for (uint32_t v = 2; v <= max_depth + 1; ++v) {
+            tk.ext<<<tk.grid_ext, gb, tk.smem, st>>>(s->dev, pool, nullptr);
+            k_shade<<<g_shade, gb, 0, st>>>(P, pool, nullptr);
+            tk.shadow<<<tk.grid_shadow, gb, tk.smem, st>>>(s->dev, pool, nullptr);
+            k_step_end<<<1, 1, 0, st>>>(pool);
+            stats.kernel_launches += 4;
+            ++stats.wavefront_steps;
+        }
+        const int g_film = grid_for(k_film, 256, passes ? WH : ns);
+        k_film<<<g_film, 256, 0, st>>>(pool, film->sum, film->sum2, film->count, t, ns, (uint32_t)WH, passes);
+        stats.kernel_launches += 1;
+        RT_CUDA_TRY(cudaGetLastError());
+        RT_CUDA_TRY(cudaMemcpyAsync(&host_ctrl, pool.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+        RT_CUDA_TRY(cudaStreamSynchronize(st));
+        t += ns;
+        film->next_task = t;
+        stats.paths += ns;
+        ++stats.waves;
+        if (host_ctrl.overflow) { set_error("BVH traversal stack overflow"); result = RT_STACK_OVERFLOW; break; }
+        double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        if (t < t_end && ((o.abort_flag && *o.abort_flag) || (o.time_budget_ms > 0 && ms >= o.time_budget_ms))) {
+            set_error("rt_render_probes: stopped by time budget or abort flag (resumable)");
+            result = RT_TIMEOUT;
+            break;
+        }
+    }
+    stats.extension_rays = host_ctrl.ext_rays;
+    stats.shadow_rays = host_ctrl.shadow_rays;
+    if (o.stats) *o.stats = stats;
+    return result;
+}
 
 extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, uint32_t spp, uint32_t max_depth,
                                       uint32_t first_iteration, double *sum, double *sum2, uint32_t *count,

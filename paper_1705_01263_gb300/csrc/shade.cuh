@@ -400,82 +400,58 @@ struct GuideRecord {
     V3 beta;
 };
 
-// Shade the hit of the pending ray of `s`. Returns bit 0 when the path
-// continues (new pending ray in s.o, s.d) and bit 1 when `sh` holds a shadow
-// ray whose unoccluded contribution must be added to s.L. With `graw` (the
-// guiding network's 40 outputs for this vertex) the continuation is drawn
-// from the one-sample MIS mixture alpha * vMF-mixture + (1 - alpha) * BSDF
-// and every pdf used for MIS is that mixture's; with `rec` the vertex's
-// training record is filled when the path continues.
-RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh, const float *graw = nullptr,
-                float alpha = 0.f, GuideRecord *rec = nullptr, float3 glo = float3{0.f, 0.f, 0.f},
-                float3 ghi = float3{1.f, 1.f, 1.f}) {
+// NEE light pick of a vertex: the sample's light-selection and light-point
+// dimensions and, for a triangle emitter, its world-space vertices, material
+// and light pdf. It needs only the sample index, so the shading kernels issue
+// its loads before the vertex is set up, overlapping their latencies.
+struct NeePick {
+    float us, ua, ub;
+    uint32_t lt, lmid;
+    float lpa;
+    V3 l0, l1, l2;
+};
+
+RT_HD NeePick nee_pick(const RenderParams &P, uint64_t index, int base) {
+    const DevScene &sc = P.sc;
+    NeePick k;
+    k.us = dim_value(P, index, base);
+    k.ua = dim_value(P, index, base + 1);
+    k.ub = dim_value(P, index, base + 2);
+    k.lt = 0;
+    k.lmid = 0;
+    k.lpa = 0.f;
+    k.l0 = k.l1 = k.l2 = v3(0.f, 0.f, 0.f);
+    if (!(k.us < sc.p_env)) {
+        float u2 = (k.us - sc.p_env) / (1.f - sc.p_env);
+        float xn = u2 * (float)sc.num_lights;
+        uint32_t bin = (uint32_t)xn;
+        if (bin >= sc.num_lights) bin = sc.num_lights - 1;
+        float frac = xn - (float)bin;
+        float2 al = ldg(sc.alias + bin);
+        uint32_t li = frac < al.x ? bin : as_uint(al.y);
+        k.lt = ldg(sc.light_tri + li);
+        const float4 *LV = sc.light_v + 3 * (size_t)li;
+        k.l0 = f4xyz(ldg(LV));
+        k.l1 = f4xyz(ldg(LV + 1));
+        k.l2 = f4xyz(ldg(LV + 2));
+        k.lpa = ldg(sc.tri_light_pdf_area + k.lt);
+        k.lmid = ldg(sc.tri_material + k.lt);
+    }
+    return k;
+}
+
+// Next-event estimation and the continuation of vertex `vx` (material m) of
+// path s, vertex number s.depth: the scattering half of shade(), shared with
+// the probe vertex. Returns bit 0 when the path continues and bit 1 when `sh`
+// holds a shadow ray (see shade()).
+RT_HD int scatter(const RenderParams &P, PathState &s, const Vertex &vx, const Material &m, bool nee,
+                  const NeePick &pk, ShadowRay &sh, const float *graw, float alpha, GuideRecord *rec, float3 glo,
+                  float3 ghi) {
     const DevScene &sc = P.sc;
     const int mode = P.mis_mode;
     const uint32_t v = s.depth;
-    if (h.prim == RT_MISS) {
-        if (sc.env_w > 0) {
-            int tx = env_texel(sc, s.d);
-            float4 e = ldg(sc.env + tx);
-            float w = 1.f;
-            if (v > 1) {
-                if (mode == 3) w = 1.f;
-                else if (mode == 2) w = 0.f;
-                else w = sc.p_env > 0.f ? mis_weight(mode, s.prev_pdf, sc.p_env * e.w) : 1.f;
-            }
-            s.L = s.L + mul(s.beta, v3(e.x, e.y, e.z)) * w;
-        }
-        return 0;
-    }
-    const uint32_t prim = h.prim;
-    // Loads that need only the hit record and the sample index go out before
-    // the vertex is set up, so that their latencies overlap with its loads:
-    // the hit triangle's material and light pdf, and the NEE light pick.
-    const uint32_t mid = ldg(sc.tri_material + prim);
-    const float lpa = ldg(sc.tri_light_pdf_area + prim);
     const int base = 2 + 7 * (int)(v - 1);
-    const bool last = v == P.max_depth + 1;
-    const bool nee = !last && (sc.num_lights > 0 || sc.p_env > 0.f) && mode != 3;
-    float us = 0.f, ua = 0.f, ub = 0.f;
-    uint32_t lt = 0, lmid = 0;
-    float lpa_l = 0.f;
-    V3 l0 = v3(0.f, 0.f, 0.f), l1 = l0, l2 = l0;
-    if (nee) {
-        us = dim_value(P, s.index, base);
-        ua = dim_value(P, s.index, base + 1);
-        ub = dim_value(P, s.index, base + 2);
-        if (!(us < sc.p_env)) {
-            float u2 = (us - sc.p_env) / (1.f - sc.p_env);
-            float xn = u2 * (float)sc.num_lights;
-            uint32_t bin = (uint32_t)xn;
-            if (bin >= sc.num_lights) bin = sc.num_lights - 1;
-            float frac = xn - (float)bin;
-            float2 al = ldg(sc.alias + bin);
-            uint32_t li = frac < al.x ? bin : as_uint(al.y);
-            lt = ldg(sc.light_tri + li);
-            const float4 *LV = sc.light_v + 3 * (size_t)li;
-            l0 = f4xyz(ldg(LV));
-            l1 = f4xyz(ldg(LV + 1));
-            l2 = f4xyz(ldg(LV + 2));
-            lpa_l = ldg(sc.tri_light_pdf_area + lt);
-            lmid = ldg(sc.tri_material + lt);
-        }
-    }
-    Vertex vx;
-    setup_vertex(sc, s, h, vx);
-    if (vx.cog > 0.f && lpa > 0.f) {
-        V3 Le = tri_emission(sc, prim, mid, h.b1, h.b2);
-        float w = 1.f;
-        if (v > 1) {
-            if (mode == 3) w = 1.f;
-            else if (mode == 2) w = 0.f;
-            else w = mis_weight(mode, s.prev_pdf, lpa * h.t * h.t / vx.cog);
-        }
-        s.L = s.L + mul(s.beta, Le) * w;
-    }
-    if (last) return 0;
     const V3 x = vx.x, ng = vx.ng, ns = vx.ns, wo = vx.wo;
-    Material m = load_material(sc, mid);
     Mixture mix;
     const bool guided = graw != nullptr && alpha > 0.f;
     if (guided) decode_mixture(graw, mix);
@@ -483,6 +459,8 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
     int ret = 0;
     // next-event estimation
     if (nee) {
+        const float us = pk.us, ua = pk.ua, ub = pk.ub;
+        const V3 l0 = pk.l0, l1 = pk.l1, l2 = pk.l2;
         V3 wi = v3(0.f, 0.f, 1.f), Le = v3(0.f, 0.f, 0.f), sdir = wi;
         float pdf_l = 0.f, tmax = INFINITY;
         if (us < sc.p_env) {
@@ -502,8 +480,8 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
                 V3 lng = normalize(cross(l1 - l0, l2 - l0));
                 float cl = -dot(wi, lng);
                 if (cl > 0.f) {
-                    pdf_l = lpa_l * dist * dist / cl;
-                    Le = tri_emission(sc, lt, lmid, lb1, lb2);
+                    pdf_l = pk.lpa * dist * dist / cl;
+                    Le = tri_emission(sc, pk.lt, pk.lmid, lb1, lb2);
                     // The shadow segment runs from the offset origin: its own
                     // length bounds the test, so that the sampled triangle
                     // itself is never reached (from x, a receiver close to the
@@ -575,6 +553,84 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
     s.d = wi;
     s.depth = v + 1;
     return ret | 1;
+}
+
+
+// Shade the hit of the pending ray of `s`. Returns bit 0 when the path
+// continues (new pending ray in s.o, s.d) and bit 1 when `sh` holds a shadow
+// ray whose unoccluded contribution must be added to s.L. With `graw` (the
+// guiding network's 40 outputs for this vertex) the continuation is drawn
+// from the one-sample MIS mixture alpha * vMF-mixture + (1 - alpha) * BSDF
+// and every pdf used for MIS is that mixture's; with `rec` the vertex's
+// training record is filled when the path continues.
+RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh, const float *graw = nullptr,
+                float alpha = 0.f, GuideRecord *rec = nullptr, float3 glo = float3{0.f, 0.f, 0.f},
+                float3 ghi = float3{1.f, 1.f, 1.f}) {
+    const DevScene &sc = P.sc;
+    const int mode = P.mis_mode;
+    const uint32_t v = s.depth;
+    if (h.prim == RT_MISS) {
+        if (sc.env_w > 0) {
+            int tx = env_texel(sc, s.d);
+            float4 e = ldg(sc.env + tx);
+            float w = 1.f;
+            if (v > 1) {
+                if (mode == 3) w = 1.f;
+                else if (mode == 2) w = 0.f;
+                else w = sc.p_env > 0.f ? mis_weight(mode, s.prev_pdf, sc.p_env * e.w) : 1.f;
+            }
+            s.L = s.L + mul(s.beta, v3(e.x, e.y, e.z)) * w;
+        }
+        return 0;
+    }
+    const uint32_t prim = h.prim;
+    // Loads that need only the hit record and the sample index go out before
+    // the vertex is set up, so that their latencies overlap with its loads:
+    // the hit triangle's material and light pdf, and the NEE light pick.
+    const uint32_t mid = ldg(sc.tri_material + prim);
+    const float lpa = ldg(sc.tri_light_pdf_area + prim);
+    const bool last = v == P.max_depth + 1;
+    const bool nee = !last && (sc.num_lights > 0 || sc.p_env > 0.f) && mode != 3;
+    NeePick pk;
+    if (nee) pk = nee_pick(P, s.index, 2 + 7 * (int)(v - 1));
+    Vertex vx;
+    setup_vertex(sc, s, h, vx);
+    if (vx.cog > 0.f && lpa > 0.f) {
+        V3 Le = tri_emission(sc, prim, mid, h.b1, h.b2);
+        float w = 1.f;
+        if (v > 1) {
+            if (mode == 3) w = 1.f;
+            else if (mode == 2) w = 0.f;
+            else w = mis_weight(mode, s.prev_pdf, lpa * h.t * h.t / vx.cog);
+        }
+        s.L = s.L + mul(s.beta, Le) * w;
+    }
+    if (last) return 0;
+    const Material m = load_material(sc, mid);
+    return scatter(P, s, vx, m, nee, pk, sh, graw, alpha, rec, glo, ghi);
+}
+
+// Vertex 1 of an irradiance-probe path (Sec. 4.2): a virtual white
+// Lambertian point at `pos` facing `nrm` (albedo 1, geometric and shading
+// normal nrm, wo = nrm) that emits nothing, so its outgoing radiance is E / pi;
+// the caller starts the path with throughput pi, so that the path's radiance
+// estimates the irradiance E. Everything after it is a camera path's.
+RT_HD int probe_vertex(const RenderParams &P, PathState &s, V3 pos, V3 nrm, ShadowRay &sh) {
+    const DevScene &sc = P.sc;
+    const bool nee = (sc.num_lights > 0 || sc.p_env > 0.f) && P.mis_mode != 3;
+    NeePick pk;
+    if (nee) pk = nee_pick(P, s.index, 2 + 7 * (int)(s.depth - 1));
+    Vertex vx;
+    vx.x = pos;
+    vx.ng = nrm;
+    vx.ns = nrm;
+    vx.wo = nrm;
+    vx.cog = 1.f;
+    Material m;
+    m.albedo = v3(1.f, 1.f, 1.f);
+    m.alpha = 1.f;
+    m.w = 0.f;
+    return scatter(P, s, vx, m, nee, pk, sh, nullptr, 0.f, nullptr, float3{0.f, 0.f, 0.f}, float3{1.f, 1.f, 1.f});
 }
 
 // Whole path in one thread: the megakernel body (Sec. 3.1 hybrid scheme)

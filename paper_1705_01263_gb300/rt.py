@@ -91,7 +91,7 @@ EXPORTED = [
     "rt_render_static", "rt_render_batch", "rt_autotune", "rt_sample_index", "rt_halton", "rt_divide_u64_host", "rt_guide_create", "rt_guide_destroy",
     "rt_guide_num_params", "rt_guide_get_params", "rt_guide_set_params", "rt_guide_state_size", "rt_guide_save",
     "rt_guide_load", "rt_guide_infer", "rt_guide_loss_grad", "rt_guide_train_step", "rt_last_error",
-    "rt_status_string", "rt_gemm_bf16",
+    "rt_status_string", "rt_gemm_bf16", "rt_render_probes",
 ]
 
 
@@ -137,6 +137,8 @@ def _declare(L):
         "rt_debug_halton_host": [u32, u32, u64, vp, i64, i32, vp],
         "rt_debug_sample_index_host": [u32, u32, u32, u32, u32, C.POINTER(u64)],
         "rt_debug_guide_infer_layers": [vp, vp, i64, vp, vp],
+        "rt_debug_render_probes_host": [vp, vp, vp, u32, u32, C.POINTER(rt_render_opts), vp, vp, i64, vp],
+        "rt_render_probes": [vp, vp, vp, u32, u32, u32, vp, C.POINTER(rt_render_opts), vp],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -560,6 +562,35 @@ def debug_render_host(scene: Scene, cam, max_depth, px, py, j, opts: Optional[rt
     check(lib().rt_debug_render_host(scene.handle, C.byref(c), max_depth, C.byref(o), px.ctypes.data,
                                      py.ctypes.data, j.ctypes.data, px.size, L.ctypes.data))
     return L
+
+
+def rt_render_probes(scene: Scene, pos, nrm, spp: int, max_depth: int, film: "Film",
+                     opts: Optional[rt_render_opts] = None, stream=None, allow_timeout: bool = False) -> int:
+    """Irradiance probes (rt_render_probes): pos, nrm torch CUDA float32 [n][3];
+    film = Film(n, 1). Returns the status (RT_TIMEOUT only with allow_timeout)."""
+    pos = pos.contiguous()
+    nrm = nrm.contiguous()
+    n = pos.shape[0]
+    o = opts if opts is not None else make_opts()
+    st = lib().rt_render_probes(scene.handle, pos.data_ptr(), nrm.data_ptr(), n, spp, max_depth, film.handle,
+                                C.byref(o), _stream(stream))
+    if st == RT_TIMEOUT and allow_timeout:
+        return st
+    check(st)
+    return st
+
+
+def debug_render_probes_host(scene: Scene, pos, nrm, max_depth, p, j, opts: Optional[rt_render_opts] = None):
+    """Host execution of probe paths (test hook): E of sample j[i] of probe p[i]."""
+    pos = np.ascontiguousarray(pos, np.float32).reshape(-1, 3)
+    nrm = np.ascontiguousarray(nrm, np.float32).reshape(-1, 3)
+    p = np.ascontiguousarray(p, np.uint32)
+    j = np.ascontiguousarray(j, np.uint32)
+    o = opts if opts is not None else make_opts()
+    E = np.zeros((p.size, 3), np.float32)
+    check(lib().rt_debug_render_probes_host(scene.handle, pos.ctypes.data, nrm.ctypes.data, pos.shape[0], max_depth,
+                                            C.byref(o), p.ctypes.data, j.ctypes.data, p.size, E.ctypes.data))
+    return E
 
 
 def debug_halton_host(width, height, seed, indices, ndims):

@@ -179,3 +179,39 @@ def test_path_code_host_matches_oracle_per_sample(small_field, which):
     close = d <= rel * np.maximum(np.abs(Lo).sum(1), 1e-3)
     assert close.mean() >= 0.99
     assert np.abs(Lg.mean(0) - Lo.mean(0)).max() <= 1e-2 * np.abs(Lo.mean(0)).max()
+
+
+@pytest.mark.parametrize("scene_kind", ["cornell", "cornell_up", "furnace"])
+def test_probe_code_host_matches_oracle_per_sample(scene_kind):
+    """Irradiance probes (Sec. 4.2): the library's probe paths, run on the
+    host, against the oracle sample by sample (same sequence indices)."""
+    if scene_kind == "furnace":
+        sd, _ = scenes.furnace_sphere(res=16)
+        pos = np.array([[0.0, 3.0, 0.0], [2.5, 0.3, -0.4], [-1.2, -1.5, 2.0]])
+        nrm = np.array([[0.0, -1.0, 0.0], [-1.0, 0.0, 0.0], [0.6, 0.0, -0.8]])
+        D = 3
+    else:
+        sd, _ = scenes.cornell_box(light="up" if scene_kind == "cornell_up" else "down")
+        pos = np.array([[0.5, 1e-3, 0.5], [0.2, 0.5, 0.999], [0.99, 0.3, 0.3], [0.5, 0.5, 0.5]])
+        nrm = np.array([[0.0, 1.0, 0.0], [0.0, 0.0, -1.0], [-1.0, 0.0, 0.0], [0.0, 0.7, 0.7]])
+        D = 8
+    nrm = nrm / np.linalg.norm(nrm, axis=1, keepdims=True)
+    s, o = rt.Scene(sd, host_only=True), oracle.Scene(sd)
+    rng = np.random.default_rng(4)
+    m = 3000
+    p = rng.integers(0, len(pos), m)
+    j = rng.integers(0, 256, m)
+    Eg = rt.debug_render_probes_host(s, pos, nrm, D, p, j)
+    # the oracle at the same (probe, sample) pairs: all probes of one
+    # iteration per call, the same FP32-rounded probe positions and normals
+    pos64, nrm64 = pos.astype(np.float32).astype(np.float64), nrm.astype(np.float32).astype(np.float64)
+    Eo2 = np.zeros((m, 3))
+    for jj in np.unique(j):
+        S, _, _, _ = o.render_probes(pos64, nrm64, 1, D, iter0=int(jj))
+        sel = np.where(j == jj)[0]
+        Eo2[sel] = S[p[sel]]
+    d = np.abs(Eg - Eo2).sum(1)
+    rel = 1e-2 if scene_kind == "cornell_up" else 1e-3
+    close = d <= rel * np.maximum(np.abs(Eo2).sum(1), 1e-3)
+    assert close.mean() >= 0.99, close.mean()
+    assert np.abs(Eg.mean(0) - Eo2.mean(0)).max() <= 1e-2 * np.abs(Eo2.mean(0)).max()
