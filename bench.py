@@ -297,6 +297,40 @@ def traversal_only(sd, cam, scene, n=1 << 22, reps=5):
     return out
 
 
+def probes(sd, scene, n_side=64, spp=256, depth=16):
+    """Irradiance probes (Sec. 4.2) in the main scene: an n_side x n_side grid
+    over the middle half of the scene at a fifth of its height (between and
+    through the spheres, like a grid of probes at desk height in a room),
+    normals up, `spp` samples each, depth 16 (device time, Mpaths/s)."""
+    import torch
+    from paper_1705_01263_gb300 import rt
+    V = sd.vertices
+    lo, hi = V.min(0), V.max(0)
+    xs = np.linspace(lo[0] + 0.25 * (hi[0] - lo[0]), hi[0] - 0.25 * (hi[0] - lo[0]), n_side)
+    zs = np.linspace(lo[2] + 0.25 * (hi[2] - lo[2]), hi[2] - 0.25 * (hi[2] - lo[2]), n_side)
+    X, Z = np.meshgrid(xs, zs)
+    y = lo[1] + 0.2 * (hi[1] - lo[1])
+    pos = np.stack([X.ravel(), np.full(X.size, y), Z.ravel()], 1).astype(np.float32)
+    nrm = np.tile(np.array([[0.0, 1.0, 0.0]], np.float32), (X.size, 1))
+    pd, nd = torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda()
+    film = rt.Film(X.size, 1)
+    rt.rt_render_probes(scene, pd, nd, 4, depth, film)
+    torch.cuda.synchronize()
+    st = rt.rt_stats()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    rt.rt_render_probes(scene, pd, nd, spp, depth, film, rt.make_opts(stats=st))
+    ev1.record()
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    mean = torch.empty((1, X.size, 3), dtype=torch.float32, device="cuda")
+    film.resolve(mean)
+    E = mean.cpu().numpy()
+    return {"workload": f"{X.size} irradiance probes (grid over the ground, normals up), {spp} spp, depth {depth}",
+            "Mpaths_per_s": st.paths / ms / 1e3, "Mrays_per_s": (st.extension_rays + st.shadow_rays) / ms / 1e3,
+            "ms": ms, "irradiance_mean_rgb": [float(x) for x in E.reshape(-1, 3).mean(0)]}
+
+
 def C_pointer(x):
     import ctypes
     return ctypes.pointer(x)
@@ -345,6 +379,7 @@ def main():
     ap.add_argument("--no-many-lights", action="store_true", help="skip the instanced many-light workload")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-scene batched workload")
     ap.add_argument("--no-traversal", action="store_true", help="skip the traversal-only ray batches")
+    ap.add_argument("--no-probes", action="store_true", help="skip the irradiance-probe workload")
     ap.add_argument("--pool", type=int, default=0, help="paths in flight per iteration set (0 = library default)")
     ap.add_argument("--tail", type=int, default=0, help="live-path count below which the megakernel finishes a set (0 = default)")
     ap.add_argument("--render-once", action="store_true",
@@ -489,6 +524,9 @@ def main():
     trv = None
     if rank == 0 and not args.no_traversal:
         trv = traversal_only(sd, cam, scene)
+    prb = None
+    if rank == 0 and not args.no_probes:
+        prb = probes(sd, scene)
     bt = None
     if rank == 0 and not args.no_batched:
         bt = batched()
@@ -535,6 +573,7 @@ def main():
             "many_lights": ml,
             "batched": bt,
             "traversal_only": trv,
+            "probes": prb,
             "wall_s": t_wall,
         }
         s = json.dumps(line)
