@@ -41,6 +41,7 @@ class _Desc(C.Structure):
         ("ggx_weight", C.c_void_p), ("emission", C.c_void_p), ("emission_tex", C.c_void_p),
         ("ntex", C.c_int32), ("tex_w", C.c_int32), ("tex_h", C.c_int32), ("textures", C.c_void_p),
         ("env_w", C.c_int32), ("env_h", C.c_int32), ("env", C.c_void_p),
+        ("env_plain", C.c_int32),
     ]
 
 
@@ -85,6 +86,10 @@ def _declare(L):
         "or_render": (None, [vp, C.POINTER(_Cam), u32, u32, u32, C.POINTER(_Opts), vp, vp, vp, vp]),
         "or_render_pixels": (None, [vp, C.POINTER(_Cam), vp, vp, vp, i64, u32, C.POINTER(_Opts), vp]),
         "or_render_probes": (None, [vp, vp, vp, u32, u32, u32, u32, C.POINTER(_Opts), vp, vp, vp, vp]),
+        "or_env_normal_cell": (C.c_int, [vp]),
+        "or_env_sample_n": (None, [vp, vp, f64, f64, vp, vp]),
+        "or_env_pdf_n": (f64, [vp, vp, vp]),
+        "or_env_texel_probs_n": (None, [vp, C.c_int, vp]),
         "or_vmf_pdf": (f64, [f64, vp, vp]),
         "or_vmf_sample": (None, [f64, vp, f64, f64, vp]),
         "or_oneblob": (None, [vp, vp]),
@@ -174,6 +179,7 @@ class Scene:
         if env is not None:
             d.env_h, d.env_w = env.shape[0], env.shape[1]
             d.env = env.ctypes.data
+        d.env_plain = int(getattr(sd, "env_plain", False))
         self._desc = d
         self.handle = lib().or_scene_create(C.byref(d))
 
@@ -241,6 +247,25 @@ class Scene:
                                C.byref(o), _p(L))
         return L
 
+    def env_sample_n(self, ng, u: float, v: float):
+        """Environment direction for a shading point of geometric normal ng
+        (normal-oriented top levels) and its solid-angle pdf."""
+        n = np.ascontiguousarray(ng, np.float64)
+        wi = np.zeros(3)
+        pdf = np.zeros(1)
+        lib().or_env_sample_n(self.handle, _p(n), u, v, _p(wi), _p(pdf))
+        return wi, float(pdf[0])
+
+    def env_pdf_n(self, ng, wi) -> float:
+        n = np.ascontiguousarray(ng, np.float64)
+        w = np.ascontiguousarray(wi, np.float64)
+        return lib().or_env_pdf_n(self.handle, _p(n), _p(w))
+
+    def env_texel_probs_n(self, cell: int, W: int, H: int):
+        out = np.zeros((H, W))
+        lib().or_env_texel_probs_n(self.handle, cell, _p(out))
+        return out
+
     def render_probes(self, pos, nrm, spp: int, max_depth: int, iter0: int = 0, mis_mode: int = 0,
                       seed: int = 0, rr: bool = False):
         """Irradiance probes (Sec. 4.2): per probe the sums of E, E^2 and the
@@ -255,6 +280,13 @@ class Scene:
         lib().or_render_probes(self.handle, _p(pos), _p(nrm), n, iter0, spp, max_depth, C.byref(o), _p(S), _p(S2),
                                _p(cnt), _p(rays))
         return S, S2, cnt, int(rays[0])
+
+
+def env_normal_cell(n) -> int:
+    """Cell of a normal in the 8 x 8 octahedral map of the normal-oriented
+    environment levels."""
+    a = np.ascontiguousarray(n, np.float64)
+    return lib().or_env_normal_cell(_p(a))
 
 
 def _camera(cam) -> _Cam:

@@ -108,6 +108,148 @@ static double envw(const or_scene *s, int l, int32_t x, int32_t y) {
     return s->env_w[l][(size_t)y * s->env_lw[l] + x];
 }
 
+/* ------------------------------------- normal-oriented top levels (2.1.2) */
+#define OR_ENV_CELL_SIDE 8        /* 8 x 8 octahedral cells of the normal */
+#define OR_ENV_NORMAL_LEVELS 5    /* reweighted top levels of the pyramid */
+
+static void or_normalize(double a[3]) {
+    double l = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    if (l > 0.0) { a[0] /= l; a[1] /= l; a[2] /= l; }
+}
+
+static double angle_between(const double a[3], const double b[3]) {
+    double c = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+    if (c > 1.0) c = 1.0;
+    if (c < -1.0) c = -1.0;
+    return acos(c);
+}
+
+/* Octahedral map of the unit sphere onto [-1, 1]^2 (plane x, z; the lower
+ * hemisphere y < 0 folded over the diagonals) and back. */
+static void oct_decode(double px, double pz, double n[3]) {
+    double y = 1.0 - fabs(px) - fabs(pz);
+    if (y < 0.0) {
+        double ox = (1.0 - fabs(pz)) * (px >= 0.0 ? 1.0 : -1.0);
+        double oz = (1.0 - fabs(px)) * (pz >= 0.0 ? 1.0 : -1.0);
+        px = ox; pz = oz;
+    }
+    n[0] = px; n[1] = y; n[2] = pz;
+    or_normalize(n);
+}
+
+int or_env_normal_cell(const double n[3]) {
+    double sum = fabs(n[0]) + fabs(n[1]) + fabs(n[2]);
+    if (!(sum > 0.0)) return 0;
+    double px = n[0] / sum, pz = n[2] / sum;
+    if (n[1] < 0.0) {
+        double ox = (1.0 - fabs(pz)) * (px >= 0.0 ? 1.0 : -1.0);
+        double oz = (1.0 - fabs(px)) * (pz >= 0.0 ? 1.0 : -1.0);
+        px = ox; pz = oz;
+    }
+    int i = (int)floor((px + 1.0) * 0.5 * OR_ENV_CELL_SIDE);
+    int j = (int)floor((pz + 1.0) * 0.5 * OR_ENV_CELL_SIDE);
+    if (i < 0) i = 0;
+    if (i >= OR_ENV_CELL_SIDE) i = OR_ENV_CELL_SIDE - 1;
+    if (j < 0) j = 0;
+    if (j >= OR_ENV_CELL_SIDE) j = OR_ENV_CELL_SIDE - 1;
+    return j * OR_ENV_CELL_SIDE + i;
+}
+
+/* Centre direction of a set given on a 17 x 17 parameter grid and the
+ * largest angle from it to the set: the largest angle to a grid point plus
+ * the largest angle across a grid square's diagonal (every point of the set
+ * lies within that of a grid point). */
+static void cone_of_grid(double pts[17][17][3], double centre[3], double *radius) {
+    double far = 0.0, step = 0.0;
+    for (int a = 0; a < 17; ++a)
+        for (int b = 0; b < 17; ++b) {
+            double t = angle_between(centre, pts[a][b]);
+            if (t > far) far = t;
+            if (a < 16 && b < 16) {
+                double d1 = angle_between(pts[a][b], pts[a + 1][b + 1]);
+                double d2 = angle_between(pts[a + 1][b], pts[a][b + 1]);
+                if (d1 > step) step = d1;
+                if (d2 > step) step = d2;
+            }
+        }
+    *radius = far + step;
+}
+
+static void cell_cone(int cell, double centre[3], double *radius) {
+    int i = cell % OR_ENV_CELL_SIDE, j = cell / OR_ENV_CELL_SIDE;
+    double pts[17][17][3];
+    for (int a = 0; a < 17; ++a)
+        for (int b = 0; b < 17; ++b) {
+            double u = (i + a / 16.0) / OR_ENV_CELL_SIDE, v = (j + b / 16.0) / OR_ENV_CELL_SIDE;
+            oct_decode(2.0 * u - 1.0, 2.0 * v - 1.0, pts[a][b]);
+        }
+    oct_decode(2.0 * (i + 0.5) / OR_ENV_CELL_SIDE - 1.0, 2.0 * (j + 0.5) / OR_ENV_CELL_SIDE - 1.0, centre);
+    cone_of_grid(pts, centre, radius);
+}
+
+static void dir_of(double theta, double phi, double d[3]) {
+    d[0] = sin(theta) * cos(phi); d[1] = cos(theta); d[2] = sin(theta) * sin(phi);
+}
+
+/* Region (x, y) of a level of lw x lh nodes: phi in [2 pi x / lw, ...),
+ * theta in [pi y / lh, ...). */
+static void region_cone(int32_t lw, int32_t lh, int32_t x, int32_t y, double centre[3], double *radius) {
+    double pts[17][17][3];
+    double t0 = OR_PI * y / lh, t1 = OR_PI * (y + 1) / lh;
+    double p0 = 2.0 * OR_PI * x / lw, p1 = 2.0 * OR_PI * (x + 1) / lw;
+    for (int a = 0; a < 17; ++a)
+        for (int b = 0; b < 17; ++b) dir_of(t0 + (t1 - t0) * a / 16.0, p0 + (p1 - p0) * b / 16.0, pts[a][b]);
+    dir_of(0.5 * (t0 + t1), 0.5 * (p0 + p1), centre);
+    cone_of_grid(pts, centre, radius);
+}
+
+/* Per normal cell, the finest reweighted level holds w x kappa, kappa the
+ * cone bound of the clamped cosine between the cell's normals and the
+ * region's directions (1 when the cones overlap, 0 when every pair is at
+ * least 90 degrees apart); the coarser reweighted levels are sums of their
+ * children, so the descent is proportional to the reweighted energy below. */
+static void build_env_normal_levels(or_scene *s) {
+    s->env_nw = NULL;
+    if (!s->d.env || s->d.env_plain || !(s->env_wsum > 0.0)) return;
+    int top = s->env_levels - 1;
+    int nl = OR_ENV_NORMAL_LEVELS < s->env_levels ? OR_ENV_NORMAL_LEVELS : s->env_levels;
+    s->env_lstar = top - nl + 1;
+    int64_t off = 0;
+    for (int l = top; l >= s->env_lstar; --l) {
+        s->env_noff[l] = off;
+        off += (int64_t)s->env_lw[l] * s->env_lh[l];
+    }
+    s->env_nstride = off;
+    int ncell = OR_ENV_CELL_SIDE * OR_ENV_CELL_SIDE;
+    s->env_nw = (double *)calloc((size_t)ncell * (size_t)off, sizeof(double));
+    const int ls = s->env_lstar;
+    const int32_t lw = s->env_lw[ls], lh = s->env_lh[ls];
+    double *rc = (double *)malloc(sizeof(double) * 3 * (size_t)lw * lh);
+    double *rb = (double *)malloc(sizeof(double) * (size_t)lw * lh);
+    for (int32_t y = 0; y < lh; ++y)
+        for (int32_t x = 0; x < lw; ++x) region_cone(lw, lh, x, y, rc + 3 * ((size_t)y * lw + x), rb + (size_t)y * lw + x);
+    for (int c = 0; c < ncell; ++c) {
+        double nc[3], alpha;
+        cell_cone(c, nc, &alpha);
+        double *blk = s->env_nw + (size_t)c * (size_t)off;
+        for (int32_t y = 0; y < lh; ++y)
+            for (int32_t x = 0; x < lw; ++x) {
+                size_t i = (size_t)y * lw + x;
+                double ang = angle_between(nc, rc + 3 * i) - alpha - rb[i];
+                double kappa = ang <= 0.0 ? 1.0 : (ang >= 0.5 * OR_PI ? 0.0 : cos(ang));
+                blk[s->env_noff[ls] + i] = s->env_w[ls][i] * kappa;
+            }
+        for (int l = ls + 1; l <= top; ++l) {
+            int32_t pw = s->env_lw[l - 1], ph = s->env_lh[l - 1], qw = s->env_lw[l];
+            for (int32_t y = 0; y < ph; ++y)
+                for (int32_t x = 0; x < pw; ++x)
+                    blk[s->env_noff[l] + (size_t)(y / 2) * qw + x / 2] += blk[s->env_noff[l - 1] + (size_t)y * pw + x];
+        }
+    }
+    free(rc);
+    free(rb);
+}
+
 void or_env_lookup(const or_scene *s, const double wi[3], double L[3]) {
     L[0] = L[1] = L[2] = 0.0;
     if (!s->d.env) return;
@@ -162,6 +304,96 @@ void or_env_sample(const or_scene *s, double u, double v, double wi[3],
     *pdf = or_luminance(L) / s->env_wsum;
     if (tx) *tx = x;
     if (ty) *ty = y;
+}
+
+/* Weight of node (x, y) of level l for normal cell c: reweighted at the
+ * normal-oriented levels, plain below them. */
+static double envw_n(const or_scene *s, int c, int l, int32_t x, int32_t y) {
+    if (!s->env_nw || l < s->env_lstar) return envw(s, l, x, y);
+    return s->env_nw[(size_t)c * (size_t)s->env_nstride + (size_t)s->env_noff[l] + (size_t)y * s->env_lw[l] + x];
+}
+
+static int choose_p(double p, double *u) {
+    if (*u < p) { *u = *u / p; return 0; }
+    *u = (*u - p) / (1.0 - p);
+    if (*u >= 1.0) *u = nextafter(1.0, 0.0);
+    return 1;
+}
+
+/* Solid-angle pdf of a direction in finest texel (x0, y0) for normal cell c.
+ * The descent reaches region R of the finest reweighted level with
+ * probability W_c(R) / W_c(total) and then the texel with the plain share
+ * w(texel) / w(R); with W_c(R) = w(R) kappa_c(R) this is kappa_c(R) w(texel)
+ * / W_c(total), over the texel's solid angle. A cell whose reweighted total
+ * vanishes (nothing lit above any of its normals) uses the plain pyramid. */
+static double texel_pdf_n(const or_scene *s, int c, int32_t x0, int32_t y0) {
+    int top = s->env_levels - 1;
+    int32_t W = s->d.env_w, H = s->d.env_h;
+    double total = envw_n(s, c, top, 0, 0) + envw_n(s, c, top, 1, 0);
+    if (!(total > 0.0)) return envw(s, 0, x0, y0) / s->env_wsum / texel_solid_angle(W, H, y0);
+    int ls = s->env_lstar;
+    double region = envw(s, ls, x0 >> ls, y0 >> ls);
+    if (!(region > 0.0)) return 0.0;
+    double P = envw_n(s, c, ls, x0 >> ls, y0 >> ls) / total;
+    return P * envw(s, 0, x0, y0) / region / texel_solid_angle(W, H, y0);
+}
+
+static void env_texel_of(const or_scene *s, const double wi[3], int32_t *x, int32_t *y) {
+    int32_t W = s->d.env_w, H = s->d.env_h;
+    double cy = fmax(-1.0, fmin(1.0, wi[1]));
+    double theta = acos(cy);
+    double phi = atan2(wi[2], wi[0]);
+    if (phi < 0.0) phi += 2.0 * OR_PI;
+    *x = (int32_t)floor(phi / (2.0 * OR_PI) * W);
+    *y = (int32_t)floor(theta / OR_PI * H);
+    if (*x >= W) *x = W - 1;
+    if (*x < 0) *x = 0;
+    if (*y >= H) *y = H - 1;
+    if (*y < 0) *y = 0;
+}
+
+double or_env_pdf_n(const or_scene *s, const double ng[3], const double wi[3]) {
+    if (!s->env_nw) return or_env_pdf(s, wi);
+    int32_t x, y;
+    env_texel_of(s, wi, &x, &y);
+    return texel_pdf_n(s, or_env_normal_cell(ng), x, y);
+}
+
+void or_env_sample_n(const or_scene *s, const double ng[3], double u, double v, double wi[3], double *pdf) {
+    int c = or_env_normal_cell(ng);
+    int top = s->env_levels - 1;
+    if (!s->env_nw || !(envw_n(s, c, top, 0, 0) + envw_n(s, c, top, 1, 0) > 0.0)) {
+        or_env_sample(s, u, v, wi, pdf, NULL, NULL);
+        if (s->env_nw) *pdf = or_env_pdf_n(s, ng, wi);
+        return;
+    }
+    /* reweighted choices down to the finest reweighted level, plain below */
+    double a = envw_n(s, c, top, 0, 0), b = envw_n(s, c, top, 1, 0);
+    int32_t x = choose_p(a / (a + b), &u), y = 0;
+    for (int l = top - 1; l >= 0; --l) {
+        double ln = envw_n(s, c, l, 2 * x, 2 * y) + envw_n(s, c, l, 2 * x, 2 * y + 1);
+        double rn = envw_n(s, c, l, 2 * x + 1, 2 * y) + envw_n(s, c, l, 2 * x + 1, 2 * y + 1);
+        x = 2 * x + choose_p(ln / (ln + rn), &u);
+        double t0 = envw_n(s, c, l, x, 2 * y), t1 = envw_n(s, c, l, x, 2 * y + 1);
+        y = 2 * y + choose_p(t0 / (t0 + t1), &v);
+    }
+    int32_t W = s->d.env_w, H = s->d.env_h;
+    double phi = 2.0 * OR_PI * ((double)x + u) / (double)W;
+    double c0 = cos(OR_PI * (double)y / (double)H), c1 = cos(OR_PI * (double)(y + 1) / (double)H);
+    double ct = c0 - v * (c0 - c1);
+    double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    wi[0] = st * cos(phi); wi[1] = ct; wi[2] = st * sin(phi);
+    *pdf = texel_pdf_n(s, c, x, y);
+}
+
+void or_env_texel_probs_n(const or_scene *s, int cell, double *texel_prob) {
+    int32_t W = s->d.env_w, H = s->d.env_h;
+    for (int32_t y = 0; y < H; ++y)
+        for (int32_t x = 0; x < W; ++x) {
+            double pdf = s->env_nw ? texel_pdf_n(s, cell, x, y)
+                                   : envw(s, 0, x, y) / s->env_wsum / texel_solid_angle(W, H, y);
+            texel_prob[(size_t)y * W + x] = pdf * texel_solid_angle(W, H, y);
+        }
 }
 
 /* Probability of every finest texel under the descent: the product of the
@@ -367,6 +599,7 @@ or_scene *or_scene_create(const or_scene_desc *d) {
     }
     or_build_bvh(s);
     build_env(s);
+    build_env_normal_levels(s);
     if (d->tri_material) or_build_lights(s);
     return s;
 }
@@ -377,6 +610,6 @@ void or_scene_destroy(or_scene *s) {
     free(s->light_tri); free(s->light_prob); free(s->alias_prob); free(s->alias_idx);
     free(s->tri_light_pdf_area);
     for (int l = 0; l < s->env_levels; ++l) free(s->env_w[l]);
-    free(s->env_w); free(s->env_lw); free(s->env_lh);
+    free(s->env_w); free(s->env_lw); free(s->env_lh); free(s->env_nw);
     free(s);
 }

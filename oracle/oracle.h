@@ -69,6 +69,9 @@ typedef struct {
     /* environment: env_h x env_w x 3 equirect, or NULL */
     int32_t env_w, env_h;
     const float *env;
+    /* 1: NEE samples the environment from the plain pyramid only (no
+     * normal-oriented top levels) */
+    int32_t env_plain;
 } or_scene_desc;
 
 or_scene *or_scene_create(const or_scene_desc *d);
@@ -109,6 +112,15 @@ void   or_env_pyramid_probs(const float *env, int32_t W, int32_t H,
 void   or_env_sample(const or_scene *s, double u, double v, double wi[3],
                      double *pdf, int32_t *tx, int32_t *ty);
 double or_env_pdf(const or_scene *s, const double wi[3]);
+/* Normal-oriented top levels of the environment pyramid (Sec. 2.1.2): the
+ * geometric normal's cell (64 cells of an 8 x 8 octahedral map); sampling and
+ * pdf for a shading point of that normal (equal to or_env_sample /
+ * or_env_pdf when the scene has env_plain set). */
+int    or_env_normal_cell(const double n[3]);
+void   or_env_sample_n(const or_scene *s, const double ng[3], double u, double v, double wi[3], double *pdf);
+double or_env_pdf_n(const or_scene *s, const double ng[3], const double wi[3]);
+/* probability of every finest texel (W x H) for normal cell `cell` */
+void   or_env_texel_probs_n(const or_scene *s, int cell, double *texel_prob);
 void   or_env_lookup(const or_scene *s, const double wi[3], double L[3]);
 double or_scene_light_pdf_area(const or_scene *s, uint32_t prim);
 double or_scene_env_select_prob(const or_scene *s);

@@ -27,6 +27,13 @@ struct or_scene {
     int32_t *env_lw, *env_lh;
     double env_wsum;
     double p_env;            /* probability of choosing the environment in NEE */
+    /* normal-oriented top levels: levels env_lstar .. top, per normal cell,
+     * weights w x kappa (kappa: bound of the clamped cosine between the
+     * cell's normals and the region's directions); NULL when plain */
+    int32_t env_lstar;
+    double *env_nw;          /* 64 cells x env_nstride */
+    int64_t env_noff[32];    /* offset of level l inside a cell's block */
+    int64_t env_nstride;
 };
 
 void or_build_bvh(or_scene *s);

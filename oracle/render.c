@@ -121,6 +121,7 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
     }
     double beta[3] = {1.0, 1.0, 1.0};
     double prev_pdf = 0.0;
+    double prev_ng[3] = {0.0, 1.0, 0.0};   /* geometric normal of the previous vertex (env pdf) */
     int has_tris = s->nlights > 0, has_env = s->p_env > 0.0;
     for (uint32_t v = 1; v <= c->D + 1; ++v) {
         const int at_probe = probe_x && v == 1;
@@ -137,7 +138,7 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
                 if (v > 1) {
                     if (mode == 3) w = 1.0;
                     else if (mode == 2) w = 0.0;
-                    else w = has_env ? mis_weight(mode, prev_pdf, s->p_env * or_env_pdf(s, d)) : 1.0;
+                    else w = has_env ? mis_weight(mode, prev_pdf, s->p_env * or_env_pdf_n(s, prev_ng, d)) : 1.0;
                 }
                 for (int a = 0; a < 3; ++a) L[a] += beta[a] * Le[a] * w;
             }
@@ -191,10 +192,10 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
             double wi[3], Le[3], sdir[3], pdf_l = 0.0, tmax = INFINITY;
             if (us < s->p_env) {
                 double pe;
-                or_env_sample(s, ua, ub, wi, &pe, NULL, NULL);
+                or_env_sample_n(s, ng, ua, ub, wi, &pe);
                 for (int a = 0; a < 3; ++a) sdir[a] = wi[a];
                 or_env_lookup(s, wi, Le);
-                pdf_l = s->p_env * or_env_pdf(s, wi);
+                pdf_l = s->p_env * or_env_pdf_n(s, ng, wi);
             } else {
                 double u2 = (us - s->p_env) / (1.0 - s->p_env);
                 if (u2 >= 1.0) u2 = nextafter(1.0, 0.0);
@@ -256,7 +257,7 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
         }
         if (beta[0] == 0.0 && beta[1] == 0.0 && beta[2] == 0.0) break;
         prev_pdf = pdf;
-        for (int a = 0; a < 3; ++a) { o[a] = xo[a]; d[a] = wi[a]; }
+        for (int a = 0; a < 3; ++a) { o[a] = xo[a]; d[a] = wi[a]; prev_ng[a] = ng[a]; }
     }
 }
 

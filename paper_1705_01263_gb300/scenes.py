@@ -83,6 +83,7 @@ class SceneData:
     uvs: Optional[np.ndarray] = None     # V x 2 float32
     textures: Optional[np.ndarray] = None  # K x th x tw x 3 float32
     env: Optional[np.ndarray] = None     # H x W x 3 float32
+    env_plain: bool = False              # NEE from the plain environment pyramid only
     # two-level scenes: per-instance mesh id and 3x4 object-to-world transform
     mesh_tri_offset: Optional[np.ndarray] = None   # meshes + 1 (prefix into indices)
     instance_mesh: Optional[np.ndarray] = None     # I uint32
