@@ -47,7 +47,8 @@ def test_white_furnace_with_mis_converges_to_one():
     S, S2, cnt, _ = s.render(cam, 64, 4)
     mean, var = oracle.resolve(S, S2, cnt)
     assert abs(mean.mean() - 1.0) < 1e-3
-    assert np.all(np.abs(mean - 1.0) < 0.05)
+    # every pixel within five of its own standard errors (64 samples)
+    assert np.all(np.abs(mean - 1.0) < 5.0 * np.sqrt(var) + 1e-3)
 
 
 def corner_form_factor(A, B):
