@@ -331,6 +331,47 @@ def probes(sd, scene, n_side=64, spp=256, depth=16):
             "ms": ms, "irradiance_mean_rgb": [float(x) for x in E.reshape(-1, 3).mean(0)]}
 
 
+def env_normal_vs_plain(sd, cam, scene, spp=16, ref_spp=1024, reps=3):
+    """Environment NEE through the normal-oriented top pyramid levels (Sec.
+    2.1.2; the default) against the plain pyramid (env_plain) in the main
+    scene at equal spp: RMSE of `spp`-sample images against a `ref_spp`
+    reference of disjoint iterations, and device time per image. efficiency
+    = (RMSE^2 x time) of plain over that of normal-oriented (above 1: the
+    normal-oriented levels reach equal error sooner)."""
+    import dataclasses
+    import torch
+    from paper_1705_01263_gb300 import rt
+    plain = rt.Scene(dataclasses.replace(sd, env_plain=True))
+    film = rt.Film(cam.width, cam.height)
+
+    def render(sc, first, n):
+        film.clear()
+        film.seek(first)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        rt.rt_render(sc, cam, n, DEPTH, film)
+        ev1.record()
+        ev1.synchronize()
+        mean, _ = film.resolve()
+        return mean, ev0.elapsed_time(ev1)
+
+    ref, _ = render(scene, 1 << 22, ref_spp)
+    out = {"workload": f"{WORKLOAD.replace('64 spp', f'{spp} spp')}, reference {ref_spp} spp of disjoint iterations"}
+    for name, sc in (("normal_oriented", scene), ("plain", plain)):
+        render(sc, 0, spp)   # warm-up
+        err, ms = [], []
+        for r in range(reps):
+            m, t = render(sc, r * spp, spp)
+            err.append(float((m - ref).double().pow(2).mean().sqrt()))
+            ms.append(t)
+        out[name] = {"rmse": statistics.mean(err), "ms": statistics.median(ms)}
+    n, p = out["normal_oriented"], out["plain"]
+    out["efficiency"] = (p["rmse"] ** 2 * p["ms"]) / (n["rmse"] ** 2 * n["ms"])
+    film.close()
+    del plain
+    return out
+
+
 def C_pointer(x):
     import ctypes
     return ctypes.pointer(x)
@@ -380,6 +421,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-scene batched workload")
     ap.add_argument("--no-traversal", action="store_true", help="skip the traversal-only ray batches")
     ap.add_argument("--no-probes", action="store_true", help="skip the irradiance-probe workload")
+    ap.add_argument("--no-env-ab", action="store_true",
+                    help="skip the normal-oriented vs plain environment-sampling comparison")
     ap.add_argument("--pool", type=int, default=0, help="paths in flight per iteration set (0 = library default)")
     ap.add_argument("--tail", type=int, default=0, help="live-path count below which the megakernel finishes a set (0 = default)")
     ap.add_argument("--render-once", action="store_true",
@@ -527,6 +570,9 @@ def main():
     prb = None
     if rank == 0 and not args.no_probes:
         prb = probes(sd, scene)
+    env_ab = None
+    if rank == 0 and not args.no_env_ab:
+        env_ab = env_normal_vs_plain(sd, cam, scene)
     bt = None
     if rank == 0 and not args.no_batched:
         bt = batched()
@@ -574,6 +620,7 @@ def main():
             "batched": bt,
             "traversal_only": trv,
             "probes": prb,
+            "env_normal_vs_plain": env_ab,
             "wall_s": t_wall,
         }
         s = json.dumps(line)

@@ -91,6 +91,11 @@ typedef struct {
     int32_t num_instances;
     const uint32_t *instance_mesh;   /* num_instances */
     const float *instance_xform;     /* num_instances x 12 */
+    /* 1: NEE samples the environment from the plain pyramid only; 0: the
+     * top pyramid levels are reweighted per geometric-normal cell (Sec.
+     * 2.1.2: 64 octahedral cells, finest of the top five levels weighted by a
+     * bound of the clamped cosine, coarser ones summed) */
+    int32_t env_plain;
 } rt_scene_desc;
 
 /* Rays and hits for rt_trace: structure-of-arrays of DEVICE pointers, n

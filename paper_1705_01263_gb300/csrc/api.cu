@@ -184,6 +184,27 @@ extern "C" rt_status rt_debug_trace_host(const rt_scene *s, const float *rays, i
     return RT_OK;
 }
 
+/* Host execution of the environment's NEE sampling (Sec. 2.1.2): for n
+ * vertices with geometric normals ng (n x 3) and sample pairs (u, v), the
+ * direction drawn for the normal's cell (wi, n x 3), the normal cell, and the
+ * solid-angle pdf of that direction for the cell (the environment's share
+ * p_env not included). */
+extern "C" rt_status rt_debug_env_sample_host(const rt_scene *s, const float *ng, const float *u, const float *v,
+                                              int64_t n, float *wi, uint32_t *cell, float *pdf) {
+    if (!s || !s->host_only || n < 0) { set_error("rt_debug_env_sample_host: needs a host-only scene"); return RT_INVALID_ARG; }
+    const DevScene &sc = s->host;
+    if (sc.env_w <= 0) { set_error("rt_debug_env_sample_host: the scene has no environment"); return RT_INVALID_ARG; }
+    for (int64_t i = 0; i < n; ++i) {
+        const uint32_t c = env_cell(v3(ng[3 * i], ng[3 * i + 1], ng[3 * i + 2]));
+        const V3 d = env_sample_cell(sc, c, u[i], v[i]);
+        const int tx = env_texel(sc, d);
+        wi[3 * i] = d.x; wi[3 * i + 1] = d.y; wi[3 * i + 2] = d.z;
+        cell[i] = c;
+        pdf[i] = sc.env[tx].w * env_cell_factor(sc, c, tx);
+    }
+    return RT_OK;
+}
+
 /* Host execution of the per-sample path (the megakernel body) for samples
  * (px, py, j): radiance into L (n x 3 floats). */
 extern "C" rt_status rt_debug_render_host(const rt_scene *s, const rt_camera *cam, uint32_t max_depth,
@@ -274,6 +295,7 @@ extern "C" rt_status rt_debug_render_probes_host(const rt_scene *s, const float 
         st.beta = v3(kPi, kPi, kPi);
         st.L = v3(0.f, 0.f, 0.f);
         st.prev_pdf = 0.f;
+        st.prev_cell = 0;
         st.o = st.d = v3(0.f, 0.f, 0.f);
         const V3 x = v3(pos[3 * (size_t)p[i]], pos[3 * (size_t)p[i] + 1], pos[3 * (size_t)p[i] + 2]);
         const V3 nn = normalize(v3(nrm[3 * (size_t)p[i]], nrm[3 * (size_t)p[i] + 1], nrm[3 * (size_t)p[i] + 2]));

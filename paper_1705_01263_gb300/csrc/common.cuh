@@ -81,6 +81,20 @@ struct DevScene {
     const int64_t *env_off;    // level offsets into env_pyr (device copy)
     int64_t env_off_h[16];     // same offsets, by value
     float p_env;               // probability of choosing the environment in NEE
+    // normal-oriented top levels (null env_nw: plain pyramid only): per cell
+    // of the geometric normal, levels env_lstar..top of reweighted weights,
+    // level l at env_noff_h[l] inside a cell's block of env_nstride floats;
+    // env_nscale[c] = sum of plain weights / sum of cell c's weights (0: the
+    // cell uses the plain pyramid); env_nfac[c * env_nregions + R] = the
+    // cell's pdf over the plain pdf in region R of level env_lstar (the
+    // cosine bound times env_nscale[c]; 1 for a plain cell)
+    const float *env_nw;
+    const float *env_nscale;
+    const float *env_nfac;
+    int32_t env_nregions;
+    int32_t env_lstar;
+    int64_t env_nstride;
+    int64_t env_noff_h[16];
     float3 bb_lo, bb_hi;       // scene bounds (guiding features)
 };
 

@@ -52,7 +52,7 @@ struct Pool {
 };
 
 RT_D void store_state(const Pool &p, uint32_t q, const PathState &s) {
-    p.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, 0.f);
+    p.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
     p.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);
     p.beta[q] = make_float4(s.beta.x, s.beta.y, s.beta.z, __uint_as_float(s.depth));
     p.L[q] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
@@ -65,6 +65,7 @@ RT_D PathState load_state(const Pool &p, uint32_t q) {
     float4 o = p.ray_o[q], d = p.ray_d[q], b = p.beta[q], L = p.L[q];
     uint2 ix = p.index[q];
     s.o = v3(o.x, o.y, o.z);
+    s.prev_cell = __float_as_uint(o.w);
     s.d = v3(d.x, d.y, d.z);
     s.prev_pdf = d.w;
     s.beta = v3(b.x, b.y, b.z);
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(128, 8) k_shade(RenderParams P, Pool pool, con
             r = shade(P, s, h, sh);
             pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
             if (r & 1) {
-                pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, 0.f);
+                pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
                 pool.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);
                 pool.beta[q] = make_float4(s.beta.x, s.beta.y, s.beta.z, __uint_as_float(s.depth));
             }
@@ -586,6 +587,7 @@ __global__ void k_probe_start(RenderParams P, Pool pool, const float *pos, const
             s.beta = v3(kPi, kPi, kPi);
             s.L = v3(0.f, 0.f, 0.f);
             s.prev_pdf = 0.f;
+            s.prev_cell = 0;
             s.o = s.d = v3(0.f, 0.f, 0.f);
             const V3 x = v3(pos[3 * (size_t)p], pos[3 * (size_t)p + 1], pos[3 * (size_t)p + 2]);
             const V3 nn = normalize(v3(nrm[3 * (size_t)p], nrm[3 * (size_t)p + 1], nrm[3 * (size_t)p + 2]));
@@ -783,7 +785,7 @@ __global__ void __launch_bounds__(128) k_shade_guided(RenderParams P, Pool pool,
             r = shade(P, s, h, sh, raw ? raw + (size_t)kGuideOutPad * i : nullptr, alpha, want ? &gr : nullptr, lo, hi);
             pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
             if (r & 1) {
-                pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, 0.f);
+                pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
                 pool.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);
                 pool.beta[q] = make_float4(s.beta.x, s.beta.y, s.beta.z, __uint_as_float(s.depth));
                 if (want) {
@@ -1859,7 +1861,7 @@ __global__ void __launch_bounds__(128) k_batch_shade(const BatchJob *jobs, Pool 
             r = shade(P, s, h, sh);
             pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
             if (r & 1) {
-                pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, 0.f);
+                pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
                 pool.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);
                 pool.beta[q] = make_float4(s.beta.x, s.beta.y, s.beta.z, __uint_as_float(s.depth));
             }

@@ -46,6 +46,128 @@ rt_status upload(rt_scene *s, const T *host, size_t count, const T **dev_out, co
 
 double lum3(const float *c) { return 0.2126 * c[0] + 0.7152 * c[1] + 0.0722 * c[2]; }
 
+// ---- normal-oriented top levels of the environment pyramid (Sec. 2.1.2)
+struct Dir3 {
+    double x, y, z;
+};
+
+Dir3 unit3(double x, double y, double z) {
+    double l = std::sqrt(x * x + y * y + z * z);
+    return l > 0.0 ? Dir3{x / l, y / l, z / l} : Dir3{x, y, z};
+}
+
+double angle3(const Dir3 &a, const Dir3 &b) {
+    return std::acos(std::min(1.0, std::max(-1.0, a.x * b.x + a.y * b.y + a.z * b.z)));
+}
+
+// Point (px, pz) of the octahedral square [-1, 1]^2 on the unit sphere: the
+// upper hemisphere over the inner diamond, the lower one folded outside it.
+Dir3 octahedral_dir(double px, double pz) {
+    double y = 1.0 - std::fabs(px) - std::fabs(pz);
+    if (y < 0.0) {
+        double fx = (1.0 - std::fabs(pz)) * (px >= 0.0 ? 1.0 : -1.0);
+        double fz = (1.0 - std::fabs(px)) * (pz >= 0.0 ? 1.0 : -1.0);
+        px = fx;
+        pz = fz;
+    }
+    return unit3(px, y, pz);
+}
+
+// Direction at polar angle theta from +y and azimuth phi from +x towards +z.
+Dir3 polar_dir(double theta, double phi) {
+    return Dir3{std::sin(theta) * std::cos(phi), std::cos(theta), std::sin(theta) * std::sin(phi)};
+}
+
+// Angular radius about `centre` of a patch of the sphere given by its map
+// f(s, t), s, t in [0, 1]: the largest angle from the centre to the points of
+// a 17 x 17 grid, plus the longest diagonal of a grid square so that the
+// points between grid points are covered too.
+template <class F>
+double patch_radius(const Dir3 &centre, F f) {
+    constexpr int G = 16;
+    Dir3 g[G + 1][G + 1];
+    for (int a = 0; a <= G; ++a)
+        for (int b = 0; b <= G; ++b) g[a][b] = f((double)a / G, (double)b / G);
+    double far = 0.0, diag = 0.0;
+    for (int a = 0; a <= G; ++a)
+        for (int b = 0; b <= G; ++b) {
+            far = std::max(far, angle3(centre, g[a][b]));
+            if (a < G && b < G)
+                diag = std::max(diag, std::max(angle3(g[a][b], g[a + 1][b + 1]), angle3(g[a + 1][b], g[a][b + 1])));
+        }
+    return far + diag;
+}
+
+struct EnvNormalTables {
+    int lstar = 0, nregions = 0;
+    int64_t stride = 0;
+    int64_t off[16] = {};
+    std::vector<float> nw, scale, fac;
+};
+
+// Per normal cell: level lstar = the finest of the top kEnvNormalLevels
+// levels holds w(R) x kappa_c(R), kappa the clamped cosine at the smallest
+// angle between a normal of the cell's cone and a direction of region R's
+// cone (1 where the cones overlap, 0 beyond 90 degrees); coarser levels are
+// sums of their children. lv[l] = plain weights of level l (W >> l columns).
+void build_env_normal_tables(const std::vector<std::vector<double>> &lv, int32_t W, int32_t H, int levels,
+                             double env_sum, EnvNormalTables &t) {
+    constexpr int side = 8, cells = side * side, kLevels = 5;
+    const double pi = M_PI;
+    const int top = levels - 1;
+    t.lstar = std::max(0, top - kLevels + 1);
+    auto lw = [&](int l) { return W >> l; };
+    auto lh = [&](int l) { return std::max(1, H >> l); };
+    t.stride = 0;
+    for (int l = top; l >= t.lstar; --l) {
+        t.off[l] = t.stride;
+        t.stride += (int64_t)lw(l) * lh(l);
+    }
+    const int ls = t.lstar, rw = lw(ls), rh = lh(ls);
+    t.nregions = rw * rh;
+    std::vector<Dir3> rc(t.nregions);
+    std::vector<double> rb(t.nregions);
+    for (int y = 0; y < rh; ++y)
+        for (int x = 0; x < rw; ++x) {
+            const double th0 = pi * y / rh, th1 = pi * (y + 1) / rh;
+            const double ph0 = 2.0 * pi * x / rw, ph1 = 2.0 * pi * (x + 1) / rw;
+            const int r = y * rw + x;
+            rc[r] = polar_dir(0.5 * (th0 + th1), 0.5 * (ph0 + ph1));
+            rb[r] = patch_radius(rc[r], [&](double s_, double t_) {
+                return polar_dir(th0 + (th1 - th0) * s_, ph0 + (ph1 - ph0) * t_);
+            });
+        }
+    t.nw.assign((size_t)cells * t.stride, 0.f);
+    t.scale.assign(cells, 0.f);
+    t.fac.assign((size_t)cells * t.nregions, 1.f);
+    std::vector<double> blk(t.stride), kap(t.nregions);
+    for (int c = 0; c < cells; ++c) {
+        const int ci = c % side, cj = c / side;
+        auto cell_point = [&](double s_, double t_) {
+            return octahedral_dir(2.0 * (ci + s_) / side - 1.0, 2.0 * (cj + t_) / side - 1.0);
+        };
+        const Dir3 nc = cell_point(0.5, 0.5);
+        const double alpha = patch_radius(nc, cell_point);
+        std::fill(blk.begin(), blk.end(), 0.0);
+        double total = 0.0;
+        for (int r = 0; r < t.nregions; ++r) {
+            const double gap = angle3(nc, rc[r]) - alpha - rb[r];
+            kap[r] = gap <= 0.0 ? 1.0 : (gap >= 0.5 * pi ? 0.0 : std::cos(gap));
+            blk[t.off[ls] + r] = lv[ls][r] * kap[r];
+            total += blk[t.off[ls] + r];
+        }
+        for (int l = ls + 1; l <= top; ++l)
+            for (int y = 0; y < lh(l - 1); ++y)
+                for (int x = 0; x < lw(l - 1); ++x)
+                    blk[t.off[l] + (int64_t)(y / 2) * lw(l) + x / 2] += blk[t.off[l - 1] + (int64_t)y * lw(l - 1) + x];
+        for (int64_t i = 0; i < t.stride; ++i) t.nw[(size_t)c * t.stride + i] = (float)blk[i];
+        if (total > 0.0) {
+            t.scale[c] = (float)(env_sum / total);
+            for (int r = 0; r < t.nregions; ++r) t.fac[(size_t)c * t.nregions + r] = (float)(kap[r] * env_sum / total);
+        }
+    }
+}
+
 // Mean luminance of a textured emitter over its triangle, by stratified
 // supersampling of the UV footprint (16 x 16 strata, nearest texel).
 double textured_mean(const rt_scene_desc *d, int64_t t, int32_t tex) {
@@ -343,6 +465,17 @@ rt_status rtg::scene_create(const rt_scene_desc *d, rt_scene **out, bool host_on
         if ((st = upload(s, env4.data(), env4.size(), &D.env, &Hs.env)) != RT_OK) return fail(st);
         if ((st = upload(s, pyr.data(), pyr.size(), &D.env_pyr, &Hs.env_pyr)) != RT_OK) return fail(st);
         if ((st = upload(s, off.data(), off.size(), &D.env_off, &Hs.env_off)) != RT_OK) return fail(st);
+        if (!d->env_plain && env_sum > 0.0) {
+            EnvNormalTables nt;
+            build_env_normal_tables(lv, W, H, levels, env_sum, nt);
+            D.env_lstar = Hs.env_lstar = nt.lstar;
+            D.env_nregions = Hs.env_nregions = nt.nregions;
+            D.env_nstride = Hs.env_nstride = nt.stride;
+            for (int l = 0; l < 16; ++l) D.env_noff_h[l] = Hs.env_noff_h[l] = nt.off[l];
+            if ((st = upload(s, nt.nw.data(), nt.nw.size(), &D.env_nw, &Hs.env_nw)) != RT_OK) return fail(st);
+            if ((st = upload(s, nt.scale.data(), nt.scale.size(), &D.env_nscale, &Hs.env_nscale)) != RT_OK) return fail(st);
+            if ((st = upload(s, nt.fac.data(), nt.fac.size(), &D.env_nfac, &Hs.env_nfac)) != RT_OK) return fail(st);
+        }
     }
 
     // ---- emitters: mean luminance per triangle; one emitter per emissive

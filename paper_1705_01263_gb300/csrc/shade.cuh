@@ -52,6 +52,7 @@ struct PathState {
     uint64_t index;   // QMC sequence index
     uint32_t pixel;
     uint32_t depth;   // vertex number the pending ray will create (1 = camera ray)
+    uint32_t prev_cell;  // normal cell of the vertex that emitted the pending ray (environment pdf)
 };
 
 struct ShadowRay {
@@ -100,6 +101,7 @@ RT_HD void raygen(const RenderParams &P, uint32_t pixel, uint32_t j, PathState &
     s.index = idx;
     s.pixel = pixel;
     s.depth = 1;
+    s.prev_cell = 0;
 }
 
 // ------------------------------------------------------------------ BSDF
@@ -326,6 +328,73 @@ RT_HD V3 env_sample(const DevScene &sc, float u, float v) {
     return v3(st * cp, ct, st * sp);
 }
 
+// Normal-oriented top levels of the pyramid (Sec. 2.1.2). The unit sphere of
+// geometric normals is cut into kEnvCellSide^2 cells of the octahedral map
+// (plane (x, z); the lower hemisphere folded over the diagonals); for each
+// cell the scene holds its own copy of the top pyramid levels, built on the
+// host: the finest of them weights each region by a bound of the clamped
+// cosine between the cell's normals and the region's directions, the coarser
+// ones are sums. A descent for a vertex of cell c follows that copy down to
+// the finest reweighted level and the plain pyramid below it.
+constexpr int kEnvCellSide = 8;
+constexpr int kEnvCells = kEnvCellSide * kEnvCellSide;
+constexpr int kEnvNormalLevels = 5;
+
+RT_HD uint32_t env_cell(V3 n) {
+    float a = fabsf(n.x) + fabsf(n.y) + fabsf(n.z);
+    if (!(a > 0.f)) return 0u;
+    float px = n.x / a, pz = n.z / a;
+    if (n.y < 0.f) {
+        float fx = (1.f - fabsf(pz)) * (px >= 0.f ? 1.f : -1.f);
+        float fz = (1.f - fabsf(px)) * (pz >= 0.f ? 1.f : -1.f);
+        px = fx;
+        pz = fz;
+    }
+    int i = (int)floorf((px + 1.f) * (0.5f * kEnvCellSide));
+    int j = (int)floorf((pz + 1.f) * (0.5f * kEnvCellSide));
+    i = i < 0 ? 0 : (i >= kEnvCellSide ? kEnvCellSide - 1 : i);
+    j = j < 0 ? 0 : (j >= kEnvCellSide ? kEnvCellSide - 1 : j);
+    return (uint32_t)(j * kEnvCellSide + i);
+}
+
+// Solid-angle pdf factor of finest texel `tx` for normal cell `cell`
+// relative to the plain pyramid's pdf (texel luminance / total weight).
+RT_HD float env_cell_factor(const DevScene &sc, uint32_t cell, int tx) {
+    if (!sc.env_nw) return 1.f;
+    const int x = tx % sc.env_w, y = tx / sc.env_w, ls = sc.env_lstar;
+    return ldg(sc.env_nfac + (size_t)cell * (size_t)sc.env_nregions + (size_t)((y >> ls) * (sc.env_w >> ls) + (x >> ls)));
+}
+
+// Descent for a vertex of normal cell `cell`; a cell whose reweighted total
+// vanishes (env_nscale 0) descends the plain pyramid.
+RT_HD V3 env_sample_cell(const DevScene &sc, uint32_t cell, float u, float v) {
+    if (!sc.env_nw || !(ldg(sc.env_nscale + cell) > 0.f)) return env_sample(sc, u, v);
+    const float *blk = sc.env_nw + (size_t)cell * (size_t)sc.env_nstride;
+    const int top = sc.env_levels - 1, ls = sc.env_lstar;
+    auto w = [&](int l, int x, int y) -> float {
+        if (l < ls) return envw(sc, l, x, y);
+        return ldg(blk + sc.env_noff_h[l] + (int64_t)y * (sc.env_w >> l) + x);
+    };
+    int x = choose2(w(top, 0, 0), w(top, 1, 0), u), y = 0;
+    for (int l = top - 1; l >= 0; --l) {
+        float left = w(l, 2 * x, 2 * y) + w(l, 2 * x, 2 * y + 1);
+        float right = w(l, 2 * x + 1, 2 * y) + w(l, 2 * x + 1, 2 * y + 1);
+        x = 2 * x + choose2(left, right, u);
+        y = 2 * y + choose2(w(l, x, 2 * y), w(l, x, 2 * y + 1), v);
+    }
+    float phi = 2.f * kPi * ((float)x + u) / (float)sc.env_w;
+    float c0 = cosf(kPi * (float)y / (float)sc.env_h), c1 = cosf(kPi * (float)(y + 1) / (float)sc.env_h);
+    float ct = c0 - v * (c0 - c1);
+    float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
+    float sp, cp;
+#ifdef __CUDA_ARCH__
+    sincosf(phi, &sp, &cp);
+#else
+    sp = sinf(phi); cp = cosf(phi);
+#endif
+    return v3(st * cp, ct, st * sp);
+}
+
 // Ray origin moved off the surface along n by an offset that grows with the
 // magnitude of the position (integer-ULP offset as in Waechter and Binder,
 // "A fast and robust method for avoiding self-intersection", 2019).
@@ -464,11 +533,13 @@ RT_HD int scatter(const RenderParams &P, PathState &s, const Vertex &vx, const M
         V3 wi = v3(0.f, 0.f, 1.f), Le = v3(0.f, 0.f, 0.f), sdir = wi;
         float pdf_l = 0.f, tmax = INFINITY;
         if (us < sc.p_env) {
-            wi = env_sample(sc, ua, ub);
+            const uint32_t cell = env_cell(ng);
+            wi = env_sample_cell(sc, cell, ua, ub);
             sdir = wi;
-            float4 e = ldg(sc.env + env_texel(sc, wi));
+            const int tx = env_texel(sc, wi);
+            float4 e = ldg(sc.env + tx);
             Le = v3(e.x, e.y, e.z);
-            pdf_l = sc.p_env * e.w;
+            pdf_l = sc.p_env * e.w * env_cell_factor(sc, cell, tx);
         } else {
             float sq = sqrtf(ua);
             float lb1 = sq * (1.f - ub), lb2 = sq * ub;
@@ -549,6 +620,7 @@ RT_HD int scatter(const RenderParams &P, PathState &s, const Vertex &vx, const M
         rec->beta = beta_in;
     }
     s.prev_pdf = pdf;
+    s.prev_cell = env_cell(ng);
     s.o = xo;
     s.d = wi;
     s.depth = v + 1;
@@ -577,7 +649,9 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
             if (v > 1) {
                 if (mode == 3) w = 1.f;
                 else if (mode == 2) w = 0.f;
-                else w = sc.p_env > 0.f ? mis_weight(mode, s.prev_pdf, sc.p_env * e.w) : 1.f;
+                else w = sc.p_env > 0.f
+                             ? mis_weight(mode, s.prev_pdf, sc.p_env * e.w * env_cell_factor(sc, s.prev_cell, tx))
+                             : 1.f;
             }
             s.L = s.L + mul(s.beta, v3(e.x, e.y, e.z)) * w;
         }

@@ -39,6 +39,7 @@ class rt_scene_desc(C.Structure):
         ("env_width", C.c_int32), ("env_height", C.c_int32), ("env", C.c_void_p),
         ("num_meshes", C.c_int32), ("mesh_tri_offset", C.c_void_p),
         ("num_instances", C.c_int32), ("instance_mesh", C.c_void_p), ("instance_xform", C.c_void_p),
+        ("env_plain", C.c_int32),
     ]
 
 
@@ -133,6 +134,7 @@ def _declare(L):
         "rt_divide_u64_host": [vp, i64, u32, vp],
         "rt_gemm_bf16": [vp, vp, vp, i32, i32, i32, i32, i32, i32, i32, vp],
         "rt_debug_trace_host": [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp],
+        "rt_debug_env_sample_host": [vp, vp, vp, vp, i64, vp, vp, vp],
         "rt_debug_render_host": [vp, C.POINTER(rt_camera), u32, C.POINTER(rt_render_opts), vp, vp, vp, i64, vp],
         "rt_debug_halton_host": [u32, u32, u64, vp, i64, i32, vp],
         "rt_debug_sample_index_host": [u32, u32, u32, u32, u32, C.POINTER(u64)],
@@ -224,6 +226,7 @@ class Scene:
         if sd.env is not None:
             d.env_height, d.env_width = int(sd.env.shape[0]), int(sd.env.shape[1])
             d.env = arr(sd.env, np.float32)
+            d.env_plain = 1 if getattr(sd, "env_plain", False) else 0
         if getattr(sd, "instance_mesh", None) is not None:
             d.num_meshes = int(len(sd.mesh_tri_offset) - 1)
             d.mesh_tri_offset = arr(sd.mesh_tri_offset, np.int64)
@@ -550,6 +553,23 @@ def debug_trace_host(scene: Scene, rays: np.ndarray, any_hit: bool = False, retu
     if return_inst:
         return prim, t, u, v, nodes, inst
     return prim, t, u, v, nodes
+
+
+def debug_env_sample_host(scene: Scene, ng, u, v):
+    """(wi, cell, pdf) of the environment's NEE sampling for geometric
+    normals ng and sample pairs (u, v), run on the host."""
+    ng = np.ascontiguousarray(ng, np.float32).reshape(-1, 3)
+    u = np.ascontiguousarray(u, np.float32)
+    v = np.ascontiguousarray(v, np.float32)
+    n = ng.shape[0]
+    if u.size != n or v.size != n:
+        raise ValueError("debug_env_sample_host: ng, u and v must have the same length")
+    wi = np.zeros((n, 3), np.float32)
+    cell = np.zeros(n, np.uint32)
+    pdf = np.zeros(n, np.float32)
+    check(lib().rt_debug_env_sample_host(scene.handle, ng.ctypes.data, u.ctypes.data, v.ctypes.data, n,
+                                         wi.ctypes.data, cell.ctypes.data, pdf.ctypes.data))
+    return wi, cell, pdf
 
 
 def debug_render_host(scene: Scene, cam, max_depth, px, py, j, opts: Optional[rt_render_opts] = None):
