@@ -41,7 +41,7 @@ class _Desc(C.Structure):
         ("ggx_weight", C.c_void_p), ("emission", C.c_void_p), ("emission_tex", C.c_void_p),
         ("ntex", C.c_int32), ("tex_w", C.c_int32), ("tex_h", C.c_int32), ("textures", C.c_void_p),
         ("env_w", C.c_int32), ("env_h", C.c_int32), ("env", C.c_void_p),
-        ("env_plain", C.c_int32),
+        ("env_plain", C.c_int32), ("light_bvh", C.c_int32),
     ]
 
 
@@ -90,6 +90,14 @@ def _declare(L):
         "or_env_sample_n": (None, [vp, vp, f64, f64, vp, vp]),
         "or_env_pdf_n": (f64, [vp, vp, vp]),
         "or_env_texel_probs_n": (None, [vp, C.c_int, vp]),
+        "or_lb_sample": (i64, [vp, vp, vp, f64, vp]),
+        "or_lb_prob": (f64, [vp, vp, vp, i64]),
+        "or_lb_estimate": (f64, [vp, C.c_int32, vp, vp]),
+        "or_lb_p_left": (f64, [vp, C.c_int32, vp, vp]),
+        "or_lb_num_nodes": (C.c_int32, [vp]),
+        "or_lb_node_info": (None, [vp, C.c_int32, vp, vp, vp, vp]),
+        "or_lb_region": (C.c_int, [vp]),
+        "or_lb_light_of_tri": (i64, [vp, i64]),
         "or_vmf_pdf": (f64, [f64, vp, vp]),
         "or_vmf_sample": (None, [f64, vp, f64, f64, vp]),
         "or_oneblob": (None, [vp, vp]),
@@ -180,6 +188,7 @@ class Scene:
             d.env_h, d.env_w = env.shape[0], env.shape[1]
             d.env = env.ctypes.data
         d.env_plain = int(getattr(sd, "env_plain", False))
+        d.light_bvh = int(getattr(sd, "light_bvh", False))
         self._desc = d
         self.handle = lib().or_scene_create(C.byref(d))
 
@@ -266,6 +275,35 @@ class Scene:
         lib().or_env_texel_probs_n(self.handle, cell, _p(out))
         return out
 
+    # ---- probabilistic light hierarchy (light_bvh scenes, Sec. 2.1.1)
+    def lb_sample(self, x, n, u: float):
+        """(emitter index, its probability) drawn with u for point x, normal n."""
+        prob = np.zeros(1)
+        e = lib().or_lb_sample(self.handle, _p(_f64(x, 3)), _p(_f64(n, 3)), u, _p(prob))
+        return int(e), float(prob[0])
+
+    def lb_prob(self, x, n, e: int) -> float:
+        return lib().or_lb_prob(self.handle, _p(_f64(x, 3)), _p(_f64(n, 3)), e)
+
+    def lb_estimate(self, node: int, x, n) -> float:
+        return lib().or_lb_estimate(self.handle, node, _p(_f64(x, 3)), _p(_f64(n, 3)))
+
+    def lb_p_left(self, node: int, x, n) -> float:
+        return lib().or_lb_p_left(self.handle, node, _p(_f64(x, 3)), _p(_f64(n, 3)))
+
+    def lb_num_nodes(self) -> int:
+        return lib().or_lb_num_nodes(self.handle)
+
+    def lb_node(self, node: int):
+        box, I, flux = np.zeros(6), np.zeros(6), np.zeros(1)
+        links = np.zeros(4, np.int32)
+        lib().or_lb_node_info(self.handle, node, _p(box), _p(I), _p(flux), links.ctypes.data)
+        return {"lo": box[:3], "hi": box[3:], "I": I, "flux": float(flux[0]), "left": int(links[0]),
+                "right": int(links[1]), "parent": int(links[2]), "count": int(links[3])}
+
+    def lb_light_of_tri(self, t: int) -> int:
+        return lib().or_lb_light_of_tri(self.handle, t)
+
     def render_probes(self, pos, nrm, spp: int, max_depth: int, iter0: int = 0, mis_mode: int = 0,
                       seed: int = 0, rr: bool = False):
         """Irradiance probes (Sec. 4.2): per probe the sums of E, E^2 and the
@@ -280,6 +318,11 @@ class Scene:
         lib().or_render_probes(self.handle, _p(pos), _p(nrm), n, iter0, spp, max_depth, C.byref(o), _p(S), _p(S2),
                                _p(cnt), _p(rays))
         return S, S2, cnt, int(rays[0])
+
+
+def lb_region(w) -> int:
+    """Cube-face region of a direction (0..5 = +x, -x, +y, -y, +z, -z)."""
+    return lib().or_lb_region(_p(_f64(w, 3)))
 
 
 def env_normal_cell(n) -> int:

@@ -557,6 +557,11 @@ void or_build_lights(or_scene *s) {
     }
     s->nlights = nl;
     s->flux_sum = total;
+    s->light_flux = (double *)malloc(sizeof(double) * (size_t)(nl > 0 ? nl : 1));
+    for (int64_t i = 0; i < nl; ++i) s->light_flux[i] = flux[i];
+    s->light_of_tri = (int64_t *)malloc(sizeof(int64_t) * (size_t)(s->nt > 0 ? s->nt : 1));
+    for (int64_t t = 0; t < s->nt; ++t) s->light_of_tri[t] = -1;
+    for (int64_t i = 0; i < nl; ++i) s->light_of_tri[ids[i]] = i;
     s->light_tri = ids;
     s->light_prob = flux;
     s->alias_prob = (double *)malloc(sizeof(double) * (size_t)(nl > 0 ? nl : 1));
@@ -600,7 +605,10 @@ or_scene *or_scene_create(const or_scene_desc *d) {
     or_build_bvh(s);
     build_env(s);
     build_env_normal_levels(s);
-    if (d->tri_material) or_build_lights(s);
+    if (d->tri_material) {
+        or_build_lights(s);
+        or_build_light_bvh(s);
+    }
     return s;
 }
 
@@ -609,6 +617,8 @@ void or_scene_destroy(or_scene *s) {
     free(s->v64); free(s->ng); free(s->area); free(s->nodes); free(s->bvh_prims);
     free(s->light_tri); free(s->light_prob); free(s->alias_prob); free(s->alias_idx);
     free(s->tri_light_pdf_area);
+    free(s->light_flux); free(s->light_of_tri);
+    free(s->lb_nodes); free(s->lb_perm); free(s->lb_leaf_of);
     for (int l = 0; l < s->env_levels; ++l) free(s->env_w[l]);
     free(s->env_w); free(s->env_lw); free(s->env_lh); free(s->env_nw);
     free(s);

@@ -72,6 +72,9 @@ typedef struct {
     /* 1: NEE samples the environment from the plain pyramid only (no
      * normal-oriented top levels) */
     int32_t env_plain;
+    /* 1: NEE picks triangle emitters through the probabilistic light
+     * hierarchy (Sec. 2.1.1) instead of the alias table */
+    int32_t light_bvh;
 } or_scene_desc;
 
 or_scene *or_scene_create(const or_scene_desc *d);
@@ -116,6 +119,22 @@ double or_env_pdf(const or_scene *s, const double wi[3]);
  * geometric normal's cell (64 cells of an 8 x 8 octahedral map); sampling and
  * pdf for a shading point of that normal (equal to or_env_sample /
  * or_env_pdf when the scene has env_plain set). */
+/* Probabilistic light hierarchy (Sec. 2.1.1; light_bvh scenes): the emitter
+ * drawn with u for a shading point x of geometric normal n and its
+ * probability; the probability of emitter e by the deterministic traversal
+ * of its path; one node's estimate and left-child probability; node data
+ * (box lo/hi, six directional values, flux, links {left, right, parent,
+ * emitter count (0: internal)}); the cube-face region of a direction; the
+ * emitter index of a triangle (-1 if none). */
+int64_t or_lb_sample(const or_scene *s, const double x[3], const double n[3], double u, double *prob);
+double  or_lb_prob(const or_scene *s, const double x[3], const double n[3], int64_t e);
+double  or_lb_estimate(const or_scene *s, int32_t id, const double x[3], const double n[3]);
+double  or_lb_p_left(const or_scene *s, int32_t id, const double x[3], const double n[3]);
+int32_t or_lb_num_nodes(const or_scene *s);
+void    or_lb_node_info(const or_scene *s, int32_t id, double box[6], double I[6], double *flux, int32_t links[4]);
+int     or_lb_region(const double w[3]);
+int64_t or_lb_light_of_tri(const or_scene *s, int64_t t);
+
 int    or_env_normal_cell(const double n[3]);
 void   or_env_sample_n(const or_scene *s, const double ng[3], double u, double v, double wi[3], double *pdf);
 double or_env_pdf_n(const or_scene *s, const double ng[3], const double wi[3]);

@@ -21,6 +21,15 @@ struct or_scene {
     int64_t *alias_idx;      /* nlights */
     double *tri_light_pdf_area; /* nt: P(select tri) / area, 0 if not an emitter */
     double flux_sum;
+    double *light_flux;      /* nlights: luminance x area */
+    int64_t *light_of_tri;   /* nt: emitter index of a triangle, -1 if none */
+    /* probabilistic light hierarchy (light_bvh scenes): binary tree, node 0
+     * the root; lb_perm orders the emitters so that every node covers a
+     * contiguous range; lb_leaf_of = leaf of each emitter */
+    struct or_lb_node *lb_nodes;
+    int32_t lb_n;
+    int64_t *lb_perm;
+    int32_t *lb_leaf_of;
     /* environment pyramid */
     int32_t env_levels;      /* number of levels, finest first */
     double **env_w;          /* per level: weights (lum x solid angle), finest first */
@@ -36,6 +45,20 @@ struct or_scene {
     int64_t env_nstride;
 };
 
+#define OR_LB_LEAF 4       /* emitters per leaf of the light hierarchy, at most */
+#define OR_LB_PMIN 0.1     /* clamp of a child's probability */
+
+typedef struct or_lb_node {
+    double lo[3], hi[3];   /* bounds of the emitters' vertices */
+    double c[3], r;        /* box centre and half diagonal */
+    double flux;           /* sum of emitter fluxes */
+    double I[6];           /* directional values per cube-face region */
+    int32_t left, right;   /* children (internal nodes), -1 in a leaf */
+    int32_t parent;        /* -1 at the root */
+    int64_t first, count;  /* leaf: range of lb_perm; internal: count 0 */
+} or_lb_node;
+
+void or_build_light_bvh(or_scene *s);
 void or_build_bvh(or_scene *s);
 void or_build_lights(or_scene *s);
 void or_trace_one(const or_scene *s, const double o[3], const double d[3],

@@ -163,7 +163,14 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
             if (v > 1) {
                 if (mode == 3) w = 1.0;
                 else if (mode == 2) w = 0.0;
-                else w = mis_weight(mode, prev_pdf, s->tri_light_pdf_area[prim] * t * t / cog);
+                else {
+                    /* the light hierarchy's probability of this emitter from
+                     * the previous vertex (its offset origin o and normal) */
+                    double pa = s->lb_nodes ? (1.0 - s->p_env) * or_lb_prob(s, o, prev_ng, s->light_of_tri[prim]) /
+                                                  s->area[prim]
+                                            : s->tri_light_pdf_area[prim];
+                    w = mis_weight(mode, prev_pdf, pa * t * t / cog);
+                }
             }
             for (int a = 0; a < 3; ++a) L[a] += beta[a] * Le[a] * w;
         }
@@ -199,7 +206,9 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
             } else {
                 double u2 = (us - s->p_env) / (1.0 - s->p_env);
                 if (u2 >= 1.0) u2 = nextafter(1.0, 0.0);
-                int64_t li = or_alias_sample(s->alias_prob, s->alias_idx, s->nlights, u2);
+                double psel = 0.0;
+                int64_t li = s->lb_nodes ? or_lb_sample(s, xo, ng, u2, &psel)
+                                         : or_alias_sample(s->alias_prob, s->alias_idx, s->nlights, u2);
                 uint32_t lt = (uint32_t)s->light_tri[li];
                 const double *lv = s->v64 + 9 * (size_t)lt;
                 double sq = sqrt(ua);
@@ -213,7 +222,8 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
                     const double *lng = s->ng + 3 * (size_t)lt;
                     double cl = -dot3(wi, lng);
                     if (cl > 0.0) {
-                        pdf_l = s->tri_light_pdf_area[lt] * dist * dist / cl;
+                        double pa = s->lb_nodes ? (1.0 - s->p_env) * psel / s->area[lt] : s->tri_light_pdf_area[lt];
+                        pdf_l = pa * dist * dist / cl;
                         or_tri_emission(s, lt, lb1, lb2, Le);
                         /* the shadow segment: offset origin -> light point */
                         double sv[3] = {y[0] - xo[0], y[1] - xo[1], y[2] - xo[2]};

@@ -84,6 +84,7 @@ class SceneData:
     textures: Optional[np.ndarray] = None  # K x th x tw x 3 float32
     env: Optional[np.ndarray] = None     # H x W x 3 float32
     env_plain: bool = False              # NEE from the plain environment pyramid only
+    light_bvh: bool = False              # NEE picks emitters through the light hierarchy
     # two-level scenes: per-instance mesh id and 3x4 object-to-world transform
     mesh_tri_offset: Optional[np.ndarray] = None   # meshes + 1 (prefix into indices)
     instance_mesh: Optional[np.ndarray] = None     # I uint32
@@ -445,6 +446,45 @@ def parallel_emitter(h: float = 1.0, a: float = 0.5, b_: float = 0.75, L: float 
 
 
 # ----------------------------------------------------------- many lights
+def many_emitters(seed: int = BASE_SEED + 5, n_lights: int = 256, res: int = 64, light_bvh: bool = True):
+    """A 20 x 20 Lambertian floor (albedo 0.7) under `n_lights` small emitter
+    triangles (edge ~0.2) scattered over it at heights in [0.3, 3], each facing
+    a random direction of the lower hemisphere, radiance lognormal(1, 1) times
+    a random RGB tint; three boxes on the floor cast shadows. The lights are
+    spread out, so at any floor point a few of them dominate: the case the
+    light hierarchy is for. res x res pinhole camera looking down at the
+    floor from 14 above."""
+    rng = Rng(seed)
+    b = _Builder()
+    p, t = _oriented_quad((-10, 0, -10), (10, 0, -10), (10, 0, 10), (-10, 0, 10), (0, 1, 0))
+    b.add(p, t, b.material((0.7, 0.7, 0.7), 0.5, 0.0))
+    for center, size, ang in (((-3.0, 0.5, 2.0), (1.0, 1.0, 1.0), 20.0), ((4.0, 1.0, -3.0), (1.5, 2.0, 1.0), -35.0),
+                              ((0.5, 0.4, -6.0), (3.0, 0.8, 0.6), 5.0)):
+        v, tt = _box(center, size, ang)
+        b.add(v, tt, b.material((0.5, 0.6, 0.4), 0.4, 0.3))
+    pos = np.stack([rng.uniform(n_lights, -9.5, 9.5), rng.uniform(n_lights, 0.3, 3.0),
+                    rng.uniform(n_lights, -9.5, 9.5)], 1)
+    nrm = rng.normal(3 * n_lights).reshape(n_lights, 3)
+    nrm[:, 1] = -np.abs(nrm[:, 1])
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    radiance = np.exp(1.0 + rng.normal(n_lights))
+    tint = rng.uniform(3 * n_lights, 0.3, 1.0).reshape(n_lights, 3)
+    for k in range(n_lights):
+        n = nrm[k]
+        a = np.cross(n, (0.0, 0.0, 1.0) if abs(n[2]) < 0.9 else (1.0, 0.0, 0.0))
+        a /= np.linalg.norm(a)
+        c = np.cross(n, a)
+        q = pos[k] + 0.12 * np.array([a, np.cos(2.1) * a + np.sin(2.1) * c, np.cos(4.2) * a + np.sin(4.2) * c])
+        tri = np.array([[0, 1, 2]], np.uint32)
+        if np.dot(np.cross(q[1] - q[0], q[2] - q[0]), n) < 0:
+            tri = np.array([[0, 2, 1]], np.uint32)
+        b.add(q, tri, b.material((0.5, 0.5, 0.5), 0.5, 0.0, tuple(radiance[k] * tint[k])))
+    scene = b.build(name=f"many-emitters-{n_lights}")
+    scene.light_bvh = light_bvh
+    cam = Camera((0.0, 14.0, 6.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 60.0, res, res)
+    return scene, cam
+
+
 def instanced_field(seed: int = BASE_SEED + 3, n_meshes: int = 100, n_instances: int = 1000,
                     total_tris: int = 10_000_000, n_emissive: int = 100_000, n_textures: int = 16,
                     tex_size: int = 64, width: int = 1920, height: int = 1080,
