@@ -208,29 +208,52 @@ def guided_vs_plain(light="down", target_spp=16384, chunk=512, max_factor=2, see
             "plain_curve": plain[::4], "guided_curve": guided[::4]}
 
 
-def many_lights(spp=4, depth=12):
+def many_lights(spp=4, depth=12, ref_spp=128):
     """Secondary workload: 1000 instances of 100 meshes (10M instanced
-    triangles), 100k textured emitters selected by the alias table, 1920 x
-    1080 at `spp` of its 256 spp, depth 12 (throughput only)."""
+    triangles), 100k textured emitters, 1920 x 1080 at `spp` of its 256 spp,
+    depth 12. NEE picks emitters by the alias table and by the probabilistic
+    light hierarchy (Sec. 2.1.1); for each, device time and paths/s, and the
+    RMSE of the `spp` image against a `ref_spp` hierarchy reference of
+    disjoint iterations. efficiency = (RMSE^2 x time) of the alias table over
+    that of the hierarchy (above 1: the hierarchy reaches equal error
+    sooner)."""
     import torch
     from paper_1705_01263_gb300 import rt, scenes
     sd, cam = scenes.instanced_field()
-    s = rt.Scene(sd)
     film = rt.Film(cam.width, cam.height)
-    rt.rt_render(s, cam, 1, depth, film)
-    torch.cuda.synchronize()
-    st = rt.rt_stats()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    rt.rt_render(s, cam, spp, depth, film, rt.make_opts(stats=st))
-    ev1.record()
-    ev1.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    info = s.info()
-    return {"workload": "instanced field: 1000 instances of 100 meshes, 10M instanced tris, 100k textured emitters, "
-                        f"1920x1080, {spp} spp, depth {depth}",
-            "Mpaths_per_s": st.paths / ms / 1e3, "Mrays_per_s": (st.extension_rays + st.shadow_rays) / ms / 1e3,
-            "ms": ms, "bvh_nodes": info["nodes"], "unique_tris": info["leaf_tris"], "device_bytes": info["device_bytes"]}
+
+    def run(scene, first, n, stats=None):
+        film.clear()
+        film.seek(first)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        rt.rt_render(scene, cam, n, depth, film, rt.make_opts(stats=stats))
+        ev1.record()
+        ev1.synchronize()
+        return film.resolve()[0], ev0.elapsed_time(ev1)
+
+    out = {"workload": "instanced field: 1000 instances of 100 meshes, 10M instanced tris, 100k textured emitters, "
+                       f"1920x1080, {spp} spp, depth {depth}; RMSE against {ref_spp} spp of disjoint iterations"}
+    ref = None
+    for name, bvh in (("light_hierarchy", True), ("alias_table", False)):
+        sd.light_bvh = bvh
+        s = rt.Scene(sd)
+        if ref is None:
+            ref, _ = run(s, 1 << 20, ref_spp)
+            ref = ref.clone()
+        run(s, 0, 1)   # warm-up
+        st = rt.rt_stats()
+        m, ms = run(s, 0, spp, st)
+        info = s.info()
+        out[name] = {"Mpaths_per_s": st.paths / ms / 1e3, "Mrays_per_s": (st.extension_rays + st.shadow_rays) / ms / 1e3,
+                     "ms": ms, "rmse": float((m - ref).double().pow(2).mean().sqrt()),
+                     "device_bytes": info["device_bytes"]}
+        del s
+    h, a = out["light_hierarchy"], out["alias_table"]
+    out["efficiency"] = (a["rmse"] ** 2 * a["ms"]) / (h["rmse"] ** 2 * h["ms"])
+    out["bvh_nodes"], out["unique_tris"] = info["nodes"], info["leaf_tris"]
+    film.close()
+    return out
 
 
 def batched(spp_divisor=16):

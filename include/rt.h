@@ -96,6 +96,13 @@ typedef struct {
      * 2.1.2: 64 octahedral cells, finest of the top five levels weighted by a
      * bound of the clamped cosine, coarser ones summed) */
     int32_t env_plain;
+    /* 1: NEE picks triangle emitters through the probabilistic light
+     * hierarchy (Sec. 2.1.1: a binary BVH over the emitters traversed with
+     * branch probabilities from each child's estimated contribution to the
+     * shading point, clamped to [0.1, 0.9]; by flux inside a leaf of at most
+     * four); 0: the alias table over the emitter fluxes. RT_INVALID_ARG when
+     * an instance transform makes one of its mesh's emitters degenerate. */
+    int32_t light_bvh;
 } rt_scene_desc;
 
 /* Rays and hits for rt_trace: structure-of-arrays of DEVICE pointers, n

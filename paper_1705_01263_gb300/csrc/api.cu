@@ -205,6 +205,26 @@ extern "C" rt_status rt_debug_env_sample_host(const rt_scene *s, const float *ng
     return RT_OK;
 }
 
+/* Host execution of the light hierarchy (Sec. 2.1.1): for n shading points
+ * x (n x 3) with geometric normals nrm (n x 3) and numbers u, the emitter
+ * drawn (emitter index, the order of the alias table), the probability the
+ * descent reports and the probability of that emitter by re-traversal. */
+extern "C" rt_status rt_debug_light_bvh_host(const rt_scene *s, const float *x, const float *nrm, const float *u,
+                                             int64_t n, uint32_t *emitter, float *p_sample, float *p_retraverse) {
+    if (!s || !s->host_only || n < 0) { set_error("rt_debug_light_bvh_host: needs a host-only scene"); return RT_INVALID_ARG; }
+    const DevScene &sc = s->host;
+    if (!sc.lb_nodes) { set_error("rt_debug_light_bvh_host: the scene has no light hierarchy"); return RT_INVALID_ARG; }
+    for (int64_t i = 0; i < n; ++i) {
+        const V3 p = v3(x[3 * i], x[3 * i + 1], x[3 * i + 2]), nn = v3(nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]);
+        float P;
+        const uint32_t e = lb_sample(sc, p, nn, u[i], P);
+        emitter[i] = e;
+        p_sample[i] = P;
+        p_retraverse[i] = lb_prob(sc, p, nn, e);
+    }
+    return RT_OK;
+}
+
 /* Host execution of the per-sample path (the megakernel body) for samples
  * (px, py, j): radiance into L (n x 3 floats). */
 extern "C" rt_status rt_debug_render_host(const rt_scene *s, const rt_camera *cam, uint32_t max_depth,
@@ -296,6 +316,7 @@ extern "C" rt_status rt_debug_render_probes_host(const rt_scene *s, const float 
         st.L = v3(0.f, 0.f, 0.f);
         st.prev_pdf = 0.f;
         st.prev_cell = 0;
+        st.prev_n = 0;
         st.o = st.d = v3(0.f, 0.f, 0.f);
         const V3 x = v3(pos[3 * (size_t)p[i]], pos[3 * (size_t)p[i] + 1], pos[3 * (size_t)p[i] + 2]);
         const V3 nn = normalize(v3(nrm[3 * (size_t)p[i]], nrm[3 * (size_t)p[i] + 1], nrm[3 * (size_t)p[i] + 2]));

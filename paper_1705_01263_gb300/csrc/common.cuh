@@ -74,6 +74,18 @@ struct DevScene {
     const uint32_t *light_tri; // emitter -> triangle id
     const uint32_t *light_inst;// emitter -> instance id (two-level scenes)
     const float4 *light_v;     // emitter -> three world-space vertices
+    // probabilistic light hierarchy (Sec. 2.1.1; null lb_nodes: the alias
+    // table picks emitters). Node i = lb_nodes[4i .. 4i+3]: (box centre, half
+    // diagonal), (I0..I3), (I4, I5, flux, 0) with I_k the directional value
+    // of cube-face region k (+x, -x, +y, -y, +z, -z), and the links as int
+    // bits (left, right, parent, leaf word): internal nodes have leaf word 0,
+    // leaves left = right = -1 and leaf word = first slot << 3 | count.
+    const float4 *lb_nodes;
+    const uint32_t *lb_perm;      // leaf slot -> emitter
+    const uint32_t *lb_leaf;      // emitter -> its leaf node
+    const float *lb_eflux;        // emitter -> flux (luminance x area)
+    const uint32_t *lb_tri_rank;  // triangle -> rank among its mesh's emitters
+    const uint32_t *lb_inst_base; // instance -> index of its first emitter
     // environment
     int32_t env_w, env_h, env_levels;
     const float4 *env;         // finest level: rgb + pdf (lum / sum w)

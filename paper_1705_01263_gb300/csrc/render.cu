@@ -55,7 +55,7 @@ RT_D void store_state(const Pool &p, uint32_t q, const PathState &s) {
     p.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
     p.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);
     p.beta[q] = make_float4(s.beta.x, s.beta.y, s.beta.z, __uint_as_float(s.depth));
-    p.L[q] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
+    p.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
     p.index[q] = make_uint2((uint32_t)s.index, (uint32_t)(s.index >> 32));
     p.pixel[q] = s.pixel;
 }
@@ -71,6 +71,7 @@ RT_D PathState load_state(const Pool &p, uint32_t q) {
     s.beta = v3(b.x, b.y, b.z);
     s.depth = __float_as_uint(b.w);
     s.L = v3(L.x, L.y, L.z);
+    s.prev_n = __float_as_uint(L.w);
     s.index = (uint64_t)ix.x | ((uint64_t)ix.y << 32);
     s.pixel = p.pixel[q];
     return s;
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(128, 8) k_shade(RenderParams P, Pool pool, con
             h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
             ShadowRay sh;
             r = shade(P, s, h, sh);
-            pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
+            pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
             if (r & 1) {
                 pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
                 pool.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_shadow_simple(
         if (kCount) { nodes += tr.nodes; tris += tr.tris; }
         if (h.prim == RT_MISS) {
             float4 cc = pool.sh_c[q], L = pool.L[q];
-            pool.L[q] = make_float4(L.x + cc.x, L.y + cc.y, L.z + cc.z, 0.f);
+            pool.L[q] = make_float4(L.x + cc.x, L.y + cc.y, L.z + cc.z, L.w);
         }
     }
     if (overflow) atomicOr(&c->overflow, 1u);
@@ -364,7 +365,7 @@ __global__ void __launch_bounds__(128, 8) k_trace_refill(DevScene sc, Pool pool,
             if (kAnyHit) {
                 if (h.prim == RT_MISS) {
                     float4 cc = pool.sh_c[q], L = pool.L[q];
-                    pool.L[q] = make_float4(L.x + cc.x, L.y + cc.y, L.z + cc.z, 0.f);
+                    pool.L[q] = make_float4(L.x + cc.x, L.y + cc.y, L.z + cc.z, L.w);
                 }
             } else {
                 pool.hit[q] = make_float4(__uint_as_float(h.prim), h.t, h.b1, h.b2);
@@ -491,7 +492,7 @@ struct ShadowJob {
         if (h.prim != RT_MISS) return;
         uint32_t q = qs[i];
         float4 cc = sh_c[q], l = L[q];
-        L[q] = make_float4(l.x + cc.x, l.y + cc.y, l.z + cc.z, 0.f);
+        L[q] = make_float4(l.x + cc.x, l.y + cc.y, l.z + cc.z, l.w);
     }
 };
 
@@ -540,7 +541,7 @@ __global__ void __launch_bounds__(128) k_megakernel(RenderParams P, Pool pool) {
         uint32_t q = queue[i];
         PathState s = load_state(pool, q);
         finish_path(P, s, closest, any, ext, shadow);
-        pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
+        pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
     }
     if (ext) atomicAdd(&c->ext_rays, (unsigned long long)ext);
     if (shadow) atomicAdd(&c->shadow_rays, (unsigned long long)shadow);
@@ -588,6 +589,7 @@ __global__ void k_probe_start(RenderParams P, Pool pool, const float *pos, const
             s.L = v3(0.f, 0.f, 0.f);
             s.prev_pdf = 0.f;
             s.prev_cell = 0;
+            s.prev_n = 0;
             s.o = s.d = v3(0.f, 0.f, 0.f);
             const V3 x = v3(pos[3 * (size_t)p], pos[3 * (size_t)p + 1], pos[3 * (size_t)p + 2]);
             const V3 nn = normalize(v3(nrm[3 * (size_t)p], nrm[3 * (size_t)p + 1], nrm[3 * (size_t)p + 2]));
@@ -783,7 +785,7 @@ __global__ void __launch_bounds__(128) k_shade_guided(RenderParams P, Pool pool,
             const uint32_t v = s.depth;
             const bool want = recording && v <= kGuideMaxRec;
             r = shade(P, s, h, sh, raw ? raw + (size_t)kGuideOutPad * i : nullptr, alpha, want ? &gr : nullptr, lo, hi);
-            pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
+            pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
             if (r & 1) {
                 pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
                 pool.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);
@@ -1826,7 +1828,7 @@ __global__ void __launch_bounds__(128) k_batch_trace(const BatchJob *jobs, Pool 
         if (kAny) {
             if (h.prim == RT_MISS) {
                 float4 cc = pool.sh_c[q], L = pool.L[q];
-                pool.L[q] = make_float4(L.x + cc.x, L.y + cc.y, L.z + cc.z, 0.f);
+                pool.L[q] = make_float4(L.x + cc.x, L.y + cc.y, L.z + cc.z, L.w);
             }
         } else {
             pool.hit[q] = make_float4(__uint_as_float(h.prim), h.t, h.b1, h.b2);
@@ -1859,7 +1861,7 @@ __global__ void __launch_bounds__(128) k_batch_shade(const BatchJob *jobs, Pool 
             h.prim = __float_as_uint(hv.x); h.inst = pool.hit_inst[q]; h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
             ShadowRay sh;
             r = shade(P, s, h, sh);
-            pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
+            pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
             if (r & 1) {
                 pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
                 pool.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "traverse.cuh"
 
 namespace rtg {
 namespace {
@@ -165,6 +166,101 @@ void build_env_normal_tables(const std::vector<std::vector<double>> &lv, int32_t
             t.scale[c] = (float)(env_sum / total);
             for (int r = 0; r < t.nregions; ++r) t.fac[(size_t)c * t.nregions + r] = (float)(kap[r] * env_sum / total);
         }
+    }
+}
+
+// ---- probabilistic light hierarchy (Sec. 2.1.1)
+struct LightBvh {
+    std::vector<float4> nodes;   // 4 float4 per node (see DevScene::lb_nodes)
+    std::vector<uint32_t> perm;  // leaf slot -> emitter
+    std::vector<uint32_t> leaf;  // emitter -> leaf node
+};
+
+// Binary tree over the emitters (three world-space vertices each in lv,
+// fluxes in flux): leaves of at most kLeaf emitters; a larger set is ordered
+// by centroid along the longest axis of its centroid bounds (ties: the lower
+// axis, then the lower emitter index) and split at count / 2. Per node: box
+// centre and half diagonal, flux, and per cube-face region k the sum over
+// its emitters of flux x (the largest clamped cosine between the emitter's
+// normal and the directions of a cone around face axis k that holds the
+// region).
+void build_light_bvh(const std::vector<float4> &lv, const std::vector<double> &flux, LightBvh &out) {
+    constexpr int kLeaf = 4;
+    const size_t n = flux.size();
+    const double face_half_angle = std::acos(1.0 / std::sqrt(3.0));
+    std::vector<Dir3> nrm(n);
+    std::vector<double> cen(3 * n);
+    for (size_t e = 0; e < n; ++e) {
+        const float4 a = lv[3 * e], b = lv[3 * e + 1], c = lv[3 * e + 2];
+        const double ex = (double)b.x - a.x, ey = (double)b.y - a.y, ez = (double)b.z - a.z;
+        const double fx = (double)c.x - a.x, fy = (double)c.y - a.y, fz = (double)c.z - a.z;
+        nrm[e] = unit3(ey * fz - ez * fy, ez * fx - ex * fz, ex * fy - ey * fx);
+        cen[3 * e] = ((double)a.x + b.x + c.x) / 3.0;
+        cen[3 * e + 1] = ((double)a.y + b.y + c.y) / 3.0;
+        cen[3 * e + 2] = ((double)a.z + b.z + c.z) / 3.0;
+    }
+    auto kappa = [](double g) { return g <= 0.0 ? 1.0 : (g >= 0.5 * M_PI ? 0.0 : std::cos(g)); };
+    std::vector<double> lobe(6 * n);   // per emitter and region: flux x bound of its cosine lobe
+    for (size_t e = 0; e < n; ++e)
+        for (int k = 0; k < 6; ++k) {
+            Dir3 ax{0.0, 0.0, 0.0};
+            (k / 2 == 0 ? ax.x : (k / 2 == 1 ? ax.y : ax.z)) = (k & 1) ? -1.0 : 1.0;
+            lobe[6 * e + k] = flux[e] * kappa(angle3(nrm[e], ax) - face_half_angle);
+        }
+    out.perm.resize(n);
+    out.leaf.assign(n, 0u);
+    for (size_t e = 0; e < n; ++e) out.perm[e] = (uint32_t)e;
+    out.nodes.clear();
+    out.nodes.reserve(4 * (2 * n));
+    struct Item { size_t first, count; int32_t parent; bool is_left; };
+    std::vector<Item> todo{{0, n, -1, false}};
+    while (!todo.empty()) {
+        Item it = todo.back();
+        todo.pop_back();
+        const int32_t id = (int32_t)(out.nodes.size() / 4);
+        if (it.parent >= 0) {
+            float4 &links = out.nodes[4 * (size_t)it.parent + 3];
+            (it.is_left ? links.x : links.y) = as_float((uint32_t)id);
+        }
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        double clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        double F = 0.0, I[6] = {0, 0, 0, 0, 0, 0};
+        for (size_t i = it.first; i < it.first + it.count; ++i) {
+            const uint32_t e = out.perm[i];
+            for (int v = 0; v < 3; ++v) {
+                const float4 p = lv[3 * (size_t)e + v];
+                const double q[3] = {p.x, p.y, p.z};
+                for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], q[a]); hi[a] = std::max(hi[a], q[a]); }
+            }
+            for (int a = 0; a < 3; ++a) {
+                clo[a] = std::min(clo[a], cen[3 * (size_t)e + a]);
+                chi[a] = std::max(chi[a], cen[3 * (size_t)e + a]);
+            }
+            F += flux[e];
+            for (int k = 0; k < 6; ++k) I[k] += lobe[6 * (size_t)e + k];
+        }
+        const double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+        out.nodes.push_back(make_float4((float)(0.5 * (lo[0] + hi[0])), (float)(0.5 * (lo[1] + hi[1])),
+                                        (float)(0.5 * (lo[2] + hi[2])), (float)(0.5 * std::sqrt(dx * dx + dy * dy + dz * dz))));
+        out.nodes.push_back(make_float4((float)I[0], (float)I[1], (float)I[2], (float)I[3]));
+        out.nodes.push_back(make_float4((float)I[4], (float)I[5], (float)F, 0.f));
+        out.nodes.push_back(make_float4(as_float(0xffffffffu), as_float(0xffffffffu), as_float((uint32_t)it.parent), 0.f));
+        if (it.count <= (size_t)kLeaf) {
+            out.nodes.back().w = as_float((uint32_t)(it.first << 3) | (uint32_t)it.count);
+            for (size_t i = it.first; i < it.first + it.count; ++i) out.leaf[out.perm[i]] = (uint32_t)id;
+            continue;
+        }
+        int axis = 0;
+        for (int a = 1; a < 3; ++a)
+            if (chi[a] - clo[a] > chi[axis] - clo[axis]) axis = a;
+        std::sort(out.perm.begin() + it.first, out.perm.begin() + it.first + it.count, [&](uint32_t a, uint32_t b) {
+            const double ca = cen[3 * (size_t)a + axis], cb = cen[3 * (size_t)b + axis];
+            return ca < cb || (ca == cb && a < b);
+        });
+        const size_t half = it.count / 2;
+        // right pushed first so that the left subtree is numbered first
+        todo.push_back({it.first + half, it.count - half, id, false});
+        todo.push_back({it.first, half, id, true});
     }
 }
 
@@ -542,6 +638,34 @@ rt_status rtg::scene_create(const rt_scene_desc *d, rt_scene **out, bool host_on
         if ((st = upload(s, light_tri.data(), light_tri.size(), &D.light_tri, &Hs.light_tri)) != RT_OK) return fail(st);
         if ((st = upload(s, light_inst.data(), light_inst.size(), &D.light_inst, &Hs.light_inst)) != RT_OK) return fail(st);
         if ((st = upload(s, light_v.data(), light_v.size(), &D.light_v, &Hs.light_v)) != RT_OK) return fail(st);
+        if (d->light_bvh) {
+            // emitter of a hit (instance, triangle): the instance's first
+            // emitter plus the triangle's rank among its mesh's emitters
+            const int32_t I = std::max<int32_t>(1, d->num_instances);
+            std::vector<uint32_t> base(I, 0u), rank((size_t)std::max<int64_t>(T, 1), 0xffffffffu);
+            std::vector<uint8_t> seen(I, 0);
+            for (size_t e = 0; e < flux.size(); ++e) {
+                const uint32_t k = light_inst[e];
+                if (!seen[k]) { seen[k] = 1; base[k] = (uint32_t)e; }
+                const uint32_t r = (uint32_t)e - base[k];
+                uint32_t &slot = rank[light_tri[e]];
+                if (slot != 0xffffffffu && slot != r) {
+                    set_error("rt_scene_create: light_bvh needs every instance to keep all of its mesh's emitters "
+                              "(an instance transform made one degenerate)");
+                    return fail(RT_INVALID_ARG);
+                }
+                slot = r;
+            }
+            LightBvh lb;
+            build_light_bvh(light_v, flux, lb);
+            if ((st = upload(s, lb.nodes.data(), lb.nodes.size(), &D.lb_nodes, &Hs.lb_nodes)) != RT_OK) return fail(st);
+            if ((st = upload(s, lb.perm.data(), lb.perm.size(), &D.lb_perm, &Hs.lb_perm)) != RT_OK) return fail(st);
+            if ((st = upload(s, lb.leaf.data(), lb.leaf.size(), &D.lb_leaf, &Hs.lb_leaf)) != RT_OK) return fail(st);
+            std::vector<float> ef(flux.begin(), flux.end());
+            if ((st = upload(s, ef.data(), ef.size(), &D.lb_eflux, &Hs.lb_eflux)) != RT_OK) return fail(st);
+            if ((st = upload(s, rank.data(), rank.size(), &D.lb_tri_rank, &Hs.lb_tri_rank)) != RT_OK) return fail(st);
+            if ((st = upload(s, base.data(), base.size(), &D.lb_inst_base, &Hs.lb_inst_base)) != RT_OK) return fail(st);
+        }
     }
     *out = s;
     return RT_OK;

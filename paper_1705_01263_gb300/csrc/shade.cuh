@@ -53,6 +53,7 @@ struct PathState {
     uint32_t pixel;
     uint32_t depth;   // vertex number the pending ray will create (1 = camera ray)
     uint32_t prev_cell;  // normal cell of the vertex that emitted the pending ray (environment pdf)
+    uint32_t prev_n;     // its geometric normal, octahedral 16:16 code (light hierarchy pdf)
 };
 
 struct ShadowRay {
@@ -102,6 +103,7 @@ RT_HD void raygen(const RenderParams &P, uint32_t pixel, uint32_t j, PathState &
     s.pixel = pixel;
     s.depth = 1;
     s.prev_cell = 0;
+    s.prev_n = 0;
 }
 
 // ------------------------------------------------------------------ BSDF
@@ -469,6 +471,145 @@ struct GuideRecord {
     V3 beta;
 };
 
+// ------------------------------------------------------- light hierarchy
+// Octahedral 16:16 code of a unit vector (plane (x, y), lower hemisphere
+// folded over the diagonals, 16 bits per coordinate) and back: the path
+// state keeps the previous vertex's geometric normal in one 32-bit word.
+RT_HD uint32_t oct_encode(V3 n) {
+    float a = fabsf(n.x) + fabsf(n.y) + fabsf(n.z);
+    float px = a > 0.f ? n.x / a : 0.f, py = a > 0.f ? n.y / a : 0.f;
+    if (n.z < 0.f) {
+        float fx = (1.f - fabsf(py)) * (px >= 0.f ? 1.f : -1.f);
+        float fy = (1.f - fabsf(px)) * (py >= 0.f ? 1.f : -1.f);
+        px = fx;
+        py = fy;
+    }
+    uint32_t ux = (uint32_t)rintf(fminf(fmaxf(px * 0.5f + 0.5f, 0.f), 1.f) * 65535.f);
+    uint32_t uy = (uint32_t)rintf(fminf(fmaxf(py * 0.5f + 0.5f, 0.f), 1.f) * 65535.f);
+    return ux | (uy << 16);
+}
+
+RT_HD V3 oct_decode(uint32_t c) {
+    float px = (float)(c & 0xffffu) * (2.f / 65535.f) - 1.f, py = (float)(c >> 16) * (2.f / 65535.f) - 1.f;
+    float z = 1.f - fabsf(px) - fabsf(py);
+    if (z < 0.f) {
+        float fx = (1.f - fabsf(py)) * (px >= 0.f ? 1.f : -1.f);
+        float fy = (1.f - fabsf(px)) * (py >= 0.f ? 1.f : -1.f);
+        px = fx;
+        py = fy;
+    }
+    return normalize(v3(px, py, z));
+}
+
+// Estimated contribution of light-hierarchy node `id` to point x of normal
+// n (Sec. 2.1.1): its directional value for the region the point lies in,
+// seen from the box centre, times a bound of the surface cosine over the
+// box's bounding sphere, over the squared distance to the centre; inside the
+// sphere the largest directional value over the squared radius. `flux`
+// returns the node's flux.
+RT_HD float lb_estimate(const DevScene &sc, uint32_t id, V3 x, V3 n, float &flux) {
+    const float4 *N = sc.lb_nodes + 4 * (size_t)id;
+    const float4 a = ldg(N), b = ldg(N + 1), c = ldg(N + 2);
+    flux = c.z;
+    if (!(c.z > 0.f)) return 0.f;
+    const V3 v = x - v3(a.x, a.y, a.z);
+    const float d2 = dot(v, v), r = a.w;
+    if (d2 <= r * r) return fmaxf(fmaxf(fmaxf(b.x, b.y), fmaxf(b.z, b.w)), fmaxf(c.x, c.y)) / (r * r);
+    const float d = sqrtf(d2);
+    const V3 w = v * (1.f / d);
+    const float ax = fabsf(w.x), ay = fabsf(w.y), az = fabsf(w.z);
+    float I;
+    if (az > fmaxf(ax, ay)) I = w.z < 0.f ? c.y : c.x;
+    else if (ay > ax) I = w.y < 0.f ? b.w : b.z;
+    else I = w.x < 0.f ? b.y : b.x;
+    // kappa(angle(n, -w) - asin(r / d)) through cosines: 1 inside the cone,
+    // cos of the gap up to 90 degrees, 0 beyond
+    const float ca = -dot(n, w), sa = sqrtf(fmaxf(0.f, 1.f - ca * ca));
+    const float sb = r / d, cb = sqrtf(fmaxf(0.f, 1.f - sb * sb));
+    const float cs = ca >= cb ? 1.f : fmaxf(0.f, ca * cb + sa * sb);
+    return I * cs / d2;
+}
+
+// Probability of the left child: a child without flux is never chosen, else
+// the share of the estimates (of the fluxes when both vanish) clamped to
+// [0.1, 0.9].
+RT_HD float lb_p_left(const DevScene &sc, uint32_t left, uint32_t right, V3 x, V3 n) {
+    float fl, fr;
+    const float el = lb_estimate(sc, left, x, n, fl), er = lb_estimate(sc, right, x, n, fr);
+    if (!(fl > 0.f)) return 0.f;
+    if (!(fr > 0.f)) return 1.f;
+    const float p = el + er > 0.f ? el / (el + er) : fl / (fl + fr);
+    return fminf(fmaxf(p, 0.1f), 0.9f);
+}
+
+constexpr int kLbMaxDepth = 64;
+
+// Emitter drawn with u from point x of normal n, and its probability P (0
+// when the descent does not end in a leaf within kLbMaxDepth levels). Not
+// inlined, like lb_prob: the shading kernels then keep the registers of the
+// scenes without a hierarchy.
+RT_HD __noinline__ uint32_t lb_sample(const DevScene &sc, V3 x, V3 n, float u, float &P) {
+    uint32_t id = 0;
+    P = 1.f;
+    for (int depth = 0; depth < kLbMaxDepth; ++depth) {
+        const float4 L = ldg(sc.lb_nodes + 4 * (size_t)id + 3);
+        const uint32_t leaf = as_uint(L.w);
+        if (leaf) {
+            const uint32_t first = leaf >> 3, count = leaf & 7u;
+            const float target = u * ldg(sc.lb_nodes + 4 * (size_t)id + 2).z;
+            float cum = 0.f;
+            uint32_t pick = ldg(sc.lb_perm + first + count - 1);
+            float fpick = 0.f;
+            for (uint32_t i = 0; i < count; ++i) {
+                const uint32_t e = ldg(sc.lb_perm + first + i);
+                const float f = ldg(sc.lb_eflux + e);
+                cum += f;
+                if (target < cum || i + 1 == count) { pick = e; fpick = f; break; }
+            }
+            P *= fpick / ldg(sc.lb_nodes + 4 * (size_t)id + 2).z;
+            return pick;
+        }
+        const uint32_t l = as_uint(L.x), r = as_uint(L.y);
+        const float p = lb_p_left(sc, l, r, x, n);
+        if (u < p) {
+            u = u / p;
+            P *= p;
+            id = l;
+        } else {
+            u = (u - p) / (1.f - p);
+            if (u >= 1.f) u = 0.99999994f;
+            P *= 1.f - p;
+            id = r;
+        }
+    }
+    P = 0.f;
+    return 0u;
+}
+
+// Probability that the descent from x (normal n) draws emitter e: the same
+// branch probabilities along the path from e's leaf up to the root.
+RT_HD __noinline__ float lb_prob(const DevScene &sc, V3 x, V3 n, uint32_t e) {
+    uint32_t id = ldg(sc.lb_leaf + e);
+    float P = ldg(sc.lb_eflux + e) / ldg(sc.lb_nodes + 4 * (size_t)id + 2).z;
+    for (int depth = 0; depth < kLbMaxDepth; ++depth) {
+        const uint32_t par = as_uint(ldg(sc.lb_nodes + 4 * (size_t)id + 3).z);
+        if (par == 0xffffffffu) break;
+        const float4 PL = ldg(sc.lb_nodes + 4 * (size_t)par + 3);
+        const uint32_t l = as_uint(PL.x), r = as_uint(PL.y);
+        const float p = lb_p_left(sc, l, r, x, n);
+        P *= l == id ? p : 1.f - p;
+        id = par;
+    }
+    return P;
+}
+
+// Area of emitter e (world space).
+RT_HD float emitter_area(const DevScene &sc, uint32_t e) {
+    const float4 *LV = sc.light_v + 3 * (size_t)e;
+    const V3 a = f4xyz(ldg(LV)), b = f4xyz(ldg(LV + 1)), c = f4xyz(ldg(LV + 2));
+    return 0.5f * length(cross(b - a, c - a));
+}
+
 // NEE light pick of a vertex: the sample's light-selection and light-point
 // dimensions and, for a triangle emitter, its world-space vertices, material
 // and light pdf. It needs only the sample index, so the shading kernels issue
@@ -490,7 +631,7 @@ RT_HD NeePick nee_pick(const RenderParams &P, uint64_t index, int base) {
     k.lmid = 0;
     k.lpa = 0.f;
     k.l0 = k.l1 = k.l2 = v3(0.f, 0.f, 0.f);
-    if (!(k.us < sc.p_env)) {
+    if (!(k.us < sc.p_env) && !sc.lb_nodes) {
         float u2 = (k.us - sc.p_env) / (1.f - sc.p_env);
         float xn = u2 * (float)sc.num_lights;
         uint32_t bin = (uint32_t)xn;
@@ -529,7 +670,6 @@ RT_HD int scatter(const RenderParams &P, PathState &s, const Vertex &vx, const M
     // next-event estimation
     if (nee) {
         const float us = pk.us, ua = pk.ua, ub = pk.ub;
-        const V3 l0 = pk.l0, l1 = pk.l1, l2 = pk.l2;
         V3 wi = v3(0.f, 0.f, 1.f), Le = v3(0.f, 0.f, 0.f), sdir = wi;
         float pdf_l = 0.f, tmax = INFINITY;
         if (us < sc.p_env) {
@@ -541,6 +681,23 @@ RT_HD int scatter(const RenderParams &P, PathState &s, const Vertex &vx, const M
             Le = v3(e.x, e.y, e.z);
             pdf_l = sc.p_env * e.w * env_cell_factor(sc, cell, tx);
         } else {
+            V3 l0 = pk.l0, l1 = pk.l1, l2 = pk.l2;
+            uint32_t lt = pk.lt, lmid = pk.lmid;
+            float lpa = pk.lpa;
+            if (sc.lb_nodes) {
+                // the light hierarchy draws the emitter from the offset
+                // origin and the normal as the path state keeps it, so that
+                // an emitter hit by the continuation gets the same number
+                float P;
+                const uint32_t li = lb_sample(sc, xo, oct_decode(oct_encode(ng)), (us - sc.p_env) / (1.f - sc.p_env), P);
+                const float4 *LV = sc.light_v + 3 * (size_t)li;
+                l0 = f4xyz(ldg(LV));
+                l1 = f4xyz(ldg(LV + 1));
+                l2 = f4xyz(ldg(LV + 2));
+                lt = ldg(sc.light_tri + li);
+                lmid = ldg(sc.tri_material + lt);
+                lpa = (1.f - sc.p_env) * P / (0.5f * length(cross(l1 - l0, l2 - l0)));
+            }
             float sq = sqrtf(ua);
             float lb1 = sq * (1.f - ub), lb2 = sq * ub;
             V3 y = (1.f - sq) * l0 + lb1 * l1 + lb2 * l2;
@@ -551,8 +708,8 @@ RT_HD int scatter(const RenderParams &P, PathState &s, const Vertex &vx, const M
                 V3 lng = normalize(cross(l1 - l0, l2 - l0));
                 float cl = -dot(wi, lng);
                 if (cl > 0.f) {
-                    pdf_l = pk.lpa * dist * dist / cl;
-                    Le = tri_emission(sc, pk.lt, pk.lmid, lb1, lb2);
+                    pdf_l = lpa * dist * dist / cl;
+                    Le = tri_emission(sc, lt, lmid, lb1, lb2);
                     // The shadow segment runs from the offset origin: its own
                     // length bounds the test, so that the sampled triangle
                     // itself is never reached (from x, a receiver close to the
@@ -621,6 +778,7 @@ RT_HD int scatter(const RenderParams &P, PathState &s, const Vertex &vx, const M
     }
     s.prev_pdf = pdf;
     s.prev_cell = env_cell(ng);
+    s.prev_n = oct_encode(ng);
     s.o = xo;
     s.d = wi;
     s.depth = v + 1;
@@ -675,7 +833,16 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
         if (v > 1) {
             if (mode == 3) w = 1.f;
             else if (mode == 2) w = 0.f;
-            else w = mis_weight(mode, s.prev_pdf, lpa * h.t * h.t / vx.cog);
+            else {
+                float pa = lpa;
+                if (sc.lb_nodes) {
+                    // the hierarchy's probability of this emitter from the
+                    // previous vertex (offset origin s.o, its stored normal)
+                    const uint32_t li = ldg(sc.lb_inst_base + h.inst) + ldg(sc.lb_tri_rank + prim);
+                    pa = (1.f - sc.p_env) * lb_prob(sc, s.o, oct_decode(s.prev_n), li) / emitter_area(sc, li);
+                }
+                w = mis_weight(mode, s.prev_pdf, pa * h.t * h.t / vx.cog);
+            }
         }
         s.L = s.L + mul(s.beta, Le) * w;
     }

@@ -39,7 +39,7 @@ class rt_scene_desc(C.Structure):
         ("env_width", C.c_int32), ("env_height", C.c_int32), ("env", C.c_void_p),
         ("num_meshes", C.c_int32), ("mesh_tri_offset", C.c_void_p),
         ("num_instances", C.c_int32), ("instance_mesh", C.c_void_p), ("instance_xform", C.c_void_p),
-        ("env_plain", C.c_int32),
+        ("env_plain", C.c_int32), ("light_bvh", C.c_int32),
     ]
 
 
@@ -135,6 +135,7 @@ def _declare(L):
         "rt_gemm_bf16": [vp, vp, vp, i32, i32, i32, i32, i32, i32, i32, vp],
         "rt_debug_trace_host": [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp],
         "rt_debug_env_sample_host": [vp, vp, vp, vp, i64, vp, vp, vp],
+        "rt_debug_light_bvh_host": [vp, vp, vp, vp, i64, vp, vp, vp],
         "rt_debug_render_host": [vp, C.POINTER(rt_camera), u32, C.POINTER(rt_render_opts), vp, vp, vp, i64, vp],
         "rt_debug_halton_host": [u32, u32, u64, vp, i64, i32, vp],
         "rt_debug_sample_index_host": [u32, u32, u32, u32, u32, C.POINTER(u64)],
@@ -227,6 +228,7 @@ class Scene:
             d.env_height, d.env_width = int(sd.env.shape[0]), int(sd.env.shape[1])
             d.env = arr(sd.env, np.float32)
             d.env_plain = 1 if getattr(sd, "env_plain", False) else 0
+        d.light_bvh = 1 if getattr(sd, "light_bvh", False) else 0
         if getattr(sd, "instance_mesh", None) is not None:
             d.num_meshes = int(len(sd.mesh_tri_offset) - 1)
             d.mesh_tri_offset = arr(sd.mesh_tri_offset, np.int64)
@@ -570,6 +572,23 @@ def debug_env_sample_host(scene: Scene, ng, u, v):
     check(lib().rt_debug_env_sample_host(scene.handle, ng.ctypes.data, u.ctypes.data, v.ctypes.data, n,
                                          wi.ctypes.data, cell.ctypes.data, pdf.ctypes.data))
     return wi, cell, pdf
+
+
+def debug_light_bvh_host(scene: Scene, x, nrm, u):
+    """(emitter, probability from the descent, probability by re-traversal)
+    of the light hierarchy for points x, normals nrm and numbers u, run on
+    the host."""
+    x = np.ascontiguousarray(x, np.float32).reshape(-1, 3)
+    nrm = np.ascontiguousarray(nrm, np.float32).reshape(-1, 3)
+    u = np.ascontiguousarray(u, np.float32)
+    n = x.shape[0]
+    if nrm.shape[0] != n or u.size != n:
+        raise ValueError("debug_light_bvh_host: x, nrm and u must have the same length")
+    e = np.zeros(n, np.uint32)
+    ps, pr = np.zeros(n, np.float32), np.zeros(n, np.float32)
+    check(lib().rt_debug_light_bvh_host(scene.handle, x.ctypes.data, nrm.ctypes.data, u.ctypes.data, n,
+                                        e.ctypes.data, ps.ctypes.data, pr.ctypes.data))
+    return e, ps, pr
 
 
 def debug_render_host(scene: Scene, cam, max_depth, px, py, j, opts: Optional[rt_render_opts] = None):
