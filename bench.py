@@ -145,7 +145,7 @@ def cpu_baseline_oracle(sd, cam):
             "mrays_per_s": rays / dt / 1e6, "cpu": cpu_model()}
 
 
-def guided_vs_plain(light="down", target_spp=16384, chunk=512, max_factor=2, seed=5):
+def guided_vs_plain(light="down", target_spp=16384, chunk=512, max_factor=2, seed=5, guide_kw=None, opts_kw=None):
     """Time to equal RMSE, guided vs plain, on the Cornell configuration (64 x
     64, depth 8): light "down" is the configuration itself; "up" turns the
     emitter to face the ceiling, so that the room is lit through the bright
@@ -170,14 +170,16 @@ def guided_vs_plain(light="down", target_spp=16384, chunk=512, max_factor=2, see
         film = rt.Film(cam.width, cam.height)
         # warm-up of the code path on a scratch film (not timed)
         scratch = rt.Film(cam.width, cam.height)
-        rt.rt_render(scene, cam, chunk, 8, scratch, rt.make_opts(guide=rt.Guide(scene, seed=seed + 1) if guided else None))
+        gk = guide_kw or {}
+        rt.rt_render(scene, cam, chunk, 8, scratch,
+                     rt.make_opts(guide=rt.Guide(scene, seed=seed + 1, **gk) if guided else None))
         torch.cuda.synchronize()
-        guide = rt.Guide(scene, seed=seed) if guided else None
+        guide = rt.Guide(scene, seed=seed, **gk) if guided else None
         pts = []
         t0 = time.perf_counter()
         spp = 0
         while spp < max_spp:
-            rt.rt_render(scene, cam, chunk, 8, film, rt.make_opts(guide=guide))
+            rt.rt_render(scene, cam, chunk, 8, film, rt.make_opts(guide=guide, **((opts_kw or {}) if guided else {})))
             spp += chunk
             film.resolve(mean)
             torch.cuda.synchronize()
@@ -584,6 +586,17 @@ def main():
     gvp = None
     if rank == 0 and not args.no_guided:
         gvp = {"indirect_lit": guided_vs_plain("up"), "config": guided_vs_plain("down")}
+        # the same comparison with the network guiding only the first one or
+        # two vertices, 8 warm-up steps and training after every 4th set
+        variants = []
+        for gd in (1, 2):
+            kw = dict(guide_depth=gd, warm_steps=8, train_every=4)
+            for key, light in (("indirect_lit", "up"), ("config", "down")):
+                r = guided_vs_plain(light, guide_kw=kw)
+                if r:
+                    variants.append({"scene": key, **kw, "guided_speedup": r["guided_speedup"],
+                                     "guided_spp": r["guided_spp"], "plain_spp": r["plain_spp"]})
+        gvp["variants"] = variants
     ml = None
     if rank == 0 and not args.no_many_lights:
         ml = many_lights()

@@ -308,17 +308,22 @@ rt_status rt_divide_u64_host(const uint64_t *n, int64_t count, uint32_t d, uint6
  * accumulation on the tensor cores -> 8-lobe von Mises-Fisher mixture,
  * combined with BSDF sampling by one-sample MIS (mixture probability
  * `alpha`). Trained with Adam on up to `batch` radiance samples after each
- * iteration set. For its first 32 steps a set renders `batch` paths and every
- * set is followed by training; after that a set renders 16 x `batch` paths
- * (rt_render_opts.max_paths_in_flight overrides both) and training follows
- * every `train_every`-th set. */
+ * iteration set. For its first `warm_steps` steps a set renders `batch` paths
+ * (at most; fewer if rt_render_opts.max_paths_in_flight is smaller) and
+ * every set is followed by training; after that a set renders 16 x `batch`
+ * paths (rt_render_opts.max_paths_in_flight sets this size) and training
+ * follows every `train_every`-th set. */
 typedef struct {
     uint32_t batch;          /* training samples per pass (0 = 65536) */
     float learning_rate;     /* Adam lr (0 = 1e-2) */
     float alpha;             /* guide-vs-BSDF selection probability (0 = 0.5) */
     uint32_t train_steps;    /* Adam steps per pass (0 = 1) */
     uint64_t seed;           /* weight initialisation seed */
-    uint32_t train_every;    /* after 32 steps, train after every train_every-th set (0 = 1) */
+    uint32_t train_every;    /* after the warm-up steps, train after every train_every-th set (0 = 1) */
+    uint32_t guide_depth;    /* guide the continuation of vertices 1..guide_depth only, BSDF
+                              * sampling beyond (0 = every vertex); training records still
+                              * come from every vertex */
+    uint32_t warm_steps;     /* training steps taken with small sets before the large ones (0 = 32) */
 } rt_guide_opts;
 
 rt_status rt_guide_create(const rt_scene *scene, const rt_guide_opts *opts, rt_guide **out);

@@ -366,14 +366,14 @@ float guide_alpha(const rt_guide *g) { return g->opts.alpha; }
 void guide_bounds(const rt_guide *g, float3 &lo, float3 &hi) { lo = g->bb_lo; hi = g->bb_hi; }
 uint32_t guide_batch(const rt_guide *g) { return g->opts.batch; }
 bool guide_trained(const rt_guide *g) { return g->step > 0; }
-// Training cadence: after every set for the first kGuideWarmSteps steps, then
+uint32_t guide_depth(const rt_guide *g) { return g->opts.guide_depth; }
+// Training cadence: after every set for the first warm_steps steps, then
 // after every train_every-th set.
-constexpr int64_t kGuideWarmSteps = 32;
-bool guide_young(const rt_guide *g) { return g->step < kGuideWarmSteps; }
+bool guide_young(const rt_guide *g) { return g->step < (int64_t)g->opts.warm_steps; }
 bool guide_should_train(rt_guide *g) {
     const uint64_t k = g->sets++;
     const uint32_t every = std::max(1u, g->opts.train_every);
-    return g->step < kGuideWarmSteps || k % every == 0;
+    return guide_young(g) || k % every == 0;
 }
 }  // namespace rtg
 
@@ -389,6 +389,7 @@ extern "C" rt_status rt_guide_create(const rt_scene *scene, const rt_guide_opts 
     if (!(g->opts.alpha > 0.f)) g->opts.alpha = 0.5f;
     if (g->opts.alpha > 1.f) { delete g; set_error("rt_guide_create: alpha must be in (0, 1]"); return RT_INVALID_ARG; }
     if (!g->opts.train_steps) g->opts.train_steps = 1;
+    if (!g->opts.warm_steps) g->opts.warm_steps = 32;
     g->nparams = kGuideParams;
     if (scene) { g->bb_lo = scene->dev.bb_lo; g->bb_hi = scene->dev.bb_hi; }
     else { g->bb_lo = make_float3(0.f, 0.f, 0.f); g->bb_hi = make_float3(1.f, 1.f, 1.f); }

@@ -48,6 +48,7 @@ float guide_alpha(const rt_guide *g);
 void guide_bounds(const rt_guide *g, float3 &lo, float3 &hi);
 uint32_t guide_batch(const rt_guide *g);
 bool guide_trained(const rt_guide *g);
+uint32_t guide_depth(const rt_guide *g);   // last guided vertex (0 = all)
 bool guide_should_train(rt_guide *g);   // advances the set counter
 bool guide_young(const rt_guide *g);    // fewer than its warm-up training steps taken
 struct MlpWeights;

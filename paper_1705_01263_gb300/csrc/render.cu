@@ -1190,15 +1190,15 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         // step the proposal is BSDF-only.
         rt_guide *gd = o.guide;
         const uint32_t batch = guide_batch(gd);
-        // Iteration sets: while the proposal is young (fewer than 32 training
-        // steps) one training batch of paths per set, so that it learns
-        // fast; then 16 batches (2^20 paths by default; max_paths_in_flight
-        // overrides both), so that the per-set launches and the host round
-        // trip are spread over many paths. Each set ends with a training step
-        // on `batch` of its samples.
+        // Iteration sets: while the proposal is young (fewer than its warm-up
+        // training steps) at most one training batch of paths per set, so
+        // that it learns fast; then 16 batches (2^20 paths by default;
+        // max_paths_in_flight sets this size), so that the per-set launches
+        // and the host round trip are spread over many paths. Training
+        // follows a set on `batch` of its samples.
         const uint32_t cap_full = cap;
         if (!o.max_paths_in_flight) cap = std::min<uint64_t>(cap, 16ull * std::max(batch, 32u));
-        const uint32_t cap_young = o.max_paths_in_flight ? cap : std::min(cap, std::max(batch, 32u));
+        const uint32_t cap_young = std::min(cap, std::max(batch, 32u));
         if ((rs = ensure_guided(rc, cap_full, batch)) != RT_OK) return rs;
         rc->pool.view.nrec = rc->gnrec;
         Pool gpool = rc->pool.view;
@@ -1233,14 +1233,18 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
             stats.kernel_launches += 1;
             // every bounce step runs on the device-side queue lengths: no
             // host round trip until the set is done
+            const uint32_t gdepth = guide_depth(gd) ? std::min(guide_depth(gd), max_depth) : max_depth;
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
                 tk.ext<<<tk.grid_ext, gbk, 0, st>>>(s->dev, gpool, nullptr);
-                if (a > 0.f) {
+                // the network runs only where a continuation is guided: not
+                // at the last vertex (it only adds emission) nor past gdepth
+                const float av = v <= gdepth ? a : 0.f;
+                if (av > 0.f) {
                     k_guide_mlp_paths<<<sm_count(), kMlpThreads, kMlpSmem, st>>>(guide_weights(gd), pf, rc->gfeat,
                                                                             guide_err(gd));
                     stats.kernel_launches += 1;
                 }
-                k_shade_guided<<<g_shade, gbk, 0, st>>>(P, gpool, a > 0.f ? rc->gfeat : nullptr, a, rc->grec,
+                k_shade_guided<<<g_shade, gbk, 0, st>>>(P, gpool, av > 0.f ? rc->gfeat : nullptr, av, rc->grec,
                                                         rec_stride, batch, glo, ghi);
                 tk.shadow<<<tk.grid_shadow, gbk, 0, st>>>(s->dev, gpool, nullptr);
                 k_step_end<<<1, 1, 0, st>>>(gpool);

@@ -29,14 +29,15 @@ def reference(light="down"):
     return oracle.resolve(S, S2, C)
 
 
-@pytest.mark.parametrize("pool", [0, 65536])
-def test_guided_render_is_consistent_with_the_oracle(pool):
+@pytest.mark.parametrize("pool,gdepth,warm", [(0, 0, 0), (65536, 0, 0), (0, 1, 8), (0, 2, 0)])
+def test_guided_render_is_consistent_with_the_oracle(pool, gdepth, warm):
     """pool 0: the library's iteration sets; 65536: 16 spp per set, so that
-    a training step follows every set."""
+    a training step follows every set; gdepth 1 or 2: only the first vertices
+    guided (BSDF sampling and its MIS weights beyond them)."""
     from paper_1705_01263_gb300 import rt
     sd, cam = scenes.cornell_box()
     scene = rt.Scene(sd)
-    guide = rt.Guide(scene, seed=5)
+    guide = rt.Guide(scene, seed=5, guide_depth=gdepth, warm_steps=warm)
     p0 = guide.get_params()
     film = rt.Film(cam.width, cam.height)
     stats = rt.rt_stats()
