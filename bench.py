@@ -397,6 +397,59 @@ def env_normal_vs_plain(sd, cam, scene, spp=16, ref_spp=1024, reps=3):
     return out
 
 
+# FLOPs of one row of the guiding network: 224->64->64->64->64->40
+GUIDE_FLOP_PER_ROW = 2 * (224 * 64 + 3 * 64 * 64 + 64 * 40)
+
+
+def guide_mlp(n=1 << 20, reps=10):
+    """Guiding-network throughput on the tensor cores: the fused inference
+    kernel through rt_guide_infer on n rows of uniform features already on
+    the device (median of `reps`, CUDA events, L2 flushed between calls),
+    against the measured dense BF16 peak; and one fused training step
+    (forward with the loss gradient, backward, Adam) on 2^16 samples."""
+    import torch
+    from paper_1705_01263_gb300 import rt
+    hbm, tflops, src = peaks()
+    g = rt.Guide(None, seed=3)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(11)
+    feat = torch.rand((n, 7), device="cuda", generator=gen)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    g.infer(feat)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        g.infer(feat)
+        ev1.record()
+        ev1.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+    med = statistics.median(ms)
+    achieved = GUIDE_FLOP_PER_ROW * n / med / 1e9
+    m = 1 << 16
+    wi = torch.nn.functional.normalize(torch.randn((m, 3), device="cuda", generator=gen), dim=1)
+    wt = torch.rand(m, device="cuda", generator=gen)
+    g.train_step(feat[:m], wi, wt)
+    torch.cuda.synchronize()
+    tms = []
+    for _ in range(reps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        g.train_step(feat[:m], wi, wt)
+        ev1.record()
+        ev1.synchronize()
+        tms.append(ev0.elapsed_time(ev1))
+    g.close()
+    return {"workload": f"fused inference of {n} rows (224-64-64-64-64-40, BF16 weights, FP32 accumulation)",
+            "kernel": "k_guide_mlp (tcgen05)", "ms": med, "Mrows_per_s": n / med / 1e3,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": tflops, "unit": "TFLOP/s",
+                         "frac": achieved / tflops, "flop_per_row": GUIDE_FLOP_PER_ROW,
+                         "peak_source": f"{src} bf16_tflops (burst)"},
+            "train_step_ms_65536": statistics.median(tms)}
+
+
 def C_pointer(x):
     import ctypes
     return ctypes.pointer(x)
@@ -446,6 +499,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-scene batched workload")
     ap.add_argument("--no-traversal", action="store_true", help="skip the traversal-only ray batches")
     ap.add_argument("--no-probes", action="store_true", help="skip the irradiance-probe workload")
+    ap.add_argument("--mlp-once", action="store_true",
+                    help="run only the guiding-network throughput measurement and print it (profile captures)")
     ap.add_argument("--no-env-ab", action="store_true",
                     help="skip the normal-oriented vs plain environment-sampling comparison")
     ap.add_argument("--pool", type=int, default=0, help="paths in flight per iteration set (0 = library default)")
@@ -496,6 +551,9 @@ def main():
         rt.rt_render(scene, cam, args.spp, DEPTH, film, o)
 
     film.seek(base_iter)
+    if args.mlp_once:
+        print(json.dumps(guide_mlp(reps=3)), flush=True)
+        return 0
     if args.render_once:
         st = rt.rt_stats()
         what = WORKLOAD.replace("64 spp", f"{args.spp} spp")
@@ -606,6 +664,9 @@ def main():
     prb = None
     if rank == 0 and not args.no_probes:
         prb = probes(sd, scene)
+    gmlp = None
+    if rank == 0 and not args.no_guided:
+        gmlp = guide_mlp()
     env_ab = None
     if rank == 0 and not args.no_env_ab:
         env_ab = env_normal_vs_plain(sd, cam, scene)
@@ -652,6 +713,7 @@ def main():
             "clocks": clocks,
             "cpu_baseline": cpu,
             "guided_vs_plain": gvp,
+            "guide_mlp": gmlp,
             "many_lights": ml,
             "batched": bt,
             "traversal_only": trv,

@@ -326,15 +326,14 @@ rt_status mlp_kernel_attr(const void *kernel, uint32_t bytes) {
 
 // Raw outputs [n_pad][48] for n feature rows (device), no sync: the fused
 // tensor-core kernel, one launch.
-rt_status guide_infer_async(rt_guide *g, const float *feat, int64_t n, const float **raw_out, cudaStream_t st) {
-    rt_status s = ensure_scratch(g, n);
-    if (s != RT_OK) return s;
-    if ((s = mlp_kernel_attr((const void *)k_guide_mlp, kMlpSmem)) != RT_OK) return s;
-    const int64_t groups = (n + kMlpGroup * kMlpTile - 1) / (kMlpGroup * kMlpTile);
-    const int grid = (int)std::min<int64_t>(groups, (int64_t)sm_count());
-    k_guide_mlp<<<grid, kMlpThreads, kMlpSmem, st>>>(guide_weights(g), ArrayFeatures{feat, (uint32_t)n}, g->raw, g->err);
+rt_status guide_infer_async(rt_guide *g, const float *feat, int64_t n, float *out, cudaStream_t st) {
+    rt_status s;
+    if ((s = mlp_kernel_attr((const void *)k_guide_mlp, kMlpInferSmem)) != RT_OK) return s;
+    const int64_t per_cta = 2 * kMiRows;   // two groups of two tiles
+    const int grid = (int)std::min<int64_t>((n + per_cta - 1) / per_cta, (int64_t)sm_count());
+    k_guide_mlp<<<grid, kMlpThreads, kMlpInferSmem, st>>>(guide_weights(g), ArrayFeatures{feat, (uint32_t)n}, out,
+                                                           g->err);
     RT_CUDA_TRY(cudaGetLastError());
-    *raw_out = g->raw;
     return RT_OK;
 }
 
@@ -487,10 +486,8 @@ extern "C" rt_status rt_guide_infer(const rt_guide *gc, const float *features, i
     if (!g || (n > 0 && (!features || !raw)) || n < 0) { set_error("rt_guide_infer: invalid argument"); return RT_INVALID_ARG; }
     if (n == 0) return RT_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const float *r = nullptr;
-    rt_status s = guide_infer_async(g, features, n, &r, st);
+    rt_status s = guide_infer_async(g, features, n, raw, st);
     if (s != RT_OK) return s;
-    RT_CUDA_TRY(cudaMemcpy2DAsync(raw, kGuideOut * 4, r, kGuideOutPad * 4, kGuideOut * 4, n, cudaMemcpyDeviceToDevice, st));
     return check_err(g, st);
 }
 

@@ -51,6 +51,7 @@ struct Mixture {
     V3 mu[kGuideLobes];
     float kappa[kGuideLobes];
     float w[kGuideLobes];
+    float c[kGuideLobes];   // w kappa / (2 pi (1 - e^{-2 kappa})): the weighted lobe's normalisation
 };
 
 RT_HD void decode_mixture(const float *raw, Mixture &m) {
@@ -65,7 +66,10 @@ RT_HD void decode_mixture(const float *raw, Mixture &m) {
         m.w[k] = expf(r[4] - mx);
         z += m.w[k];
     }
-    for (int k = 0; k < kGuideLobes; ++k) m.w[k] /= z;
+    for (int k = 0; k < kGuideLobes; ++k) {
+        m.w[k] /= z;
+        m.c[k] = m.w[k] * m.kappa[k] / (2.f * kPi * -expm1f(-2.f * m.kappa[k]));
+    }
 }
 
 RT_HD float vmf_pdf(float kappa, V3 mu, V3 w) {
@@ -74,7 +78,7 @@ RT_HD float vmf_pdf(float kappa, V3 mu, V3 w) {
 
 RT_HD float mixture_pdf(const Mixture &m, V3 w) {
     float p = 0.f;
-    for (int k = 0; k < kGuideLobes; ++k) p += m.w[k] * vmf_pdf(m.kappa[k], m.mu[k], w);
+    for (int k = 0; k < kGuideLobes; ++k) p += m.c[k] * expf(m.kappa[k] * (dot(m.mu[k], w) - 1.f));
     return p;
 }
 
@@ -86,12 +90,12 @@ RT_HD V3 mixture_sample(const Mixture &m, float u_sel, float u1, float u2) {
         if (u_sel < acc + m.w[k]) break;
         acc += m.w[k];
     }
-    float kap = m.kappa[k];
+    const float kap = m.kappa[k];
+    const V3 n = m.mu[k];
     float ct = 1.f + logf(u1 + (1.f - u1) * expf(-2.f * kap)) / kap;
     ct = fminf(1.f, fmaxf(-1.f, ct));
     float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
     float phi = 2.f * kPi * u2;
-    V3 n = m.mu[k];
     float sign = n.z >= 0.f ? 1.f : -1.f;
     float a = -1.f / (sign + n.z);
     float bb = n.x * n.y * a;

@@ -1,5 +1,7 @@
-// Fused inference of the guiding network on the tensor cores: one persistent
-// CTA of 512 threads per SM keeps all five BF16 weight matrices (58 KB) in
+// Fused forward pass of the guiding network on the tensor cores. The
+// training forward (mlp_tiles<true>) works as follows; the inference kernel
+// (mlp_infer_tiles, below) keeps two tiles in flight instead of one. One
+// persistent CTA of 512 threads per SM keeps all five BF16 weight matrices (58 KB) in
 // shared memory and walks tiles of 128 rows, four threads per row (part p =
 // warp / 4 of row 32 (warp % 4) + lane), so that each SM sub-partition has
 // four warps to switch between. The CTA gathers the 7 features of four
@@ -255,9 +257,166 @@ __device__ void mlp_tiles(const MlpWeights &w, const Features &feat, float *raw,
     if (warp == 0) umma::tmem_dealloc(taddr, 64);
 }
 
+// ---------------------------------------------------------------- inference
+// Two tiles in flight: the 512 threads form two independent groups of 256
+// (eight warps), each with its own one-blob and activation buffers, feature
+// buffer, 64 tensor-memory columns and mbarrier, sharing the weights; while
+// one group waits for its tensor-core product the other encodes, reads back
+// or stores. In a group, two threads serve a row (half h of the columns:
+// warp w of the group reaches tensor-memory lanes 32 (w % 4) + 0..31, rows
+// 32 (w % 4) + lane, h = w / 4), and the group gathers the features of two
+// tiles at once. The group synchronises on its own named barrier (ids 1, 2),
+// so a wait that times out in one group leaves the other running. Outputs:
+// 40 floats per row (row stride kGuideOut).
+constexpr uint32_t kMiRows = 2 * kMlpTile;                                 // rows gathered per group
+constexpr uint32_t kMiX = 0;                                                // 128 x 224 BF16
+constexpr uint32_t kMiH = kMiX + kMlpTile * kGuideIn * 2;                   // 128 x 64 BF16
+constexpr uint32_t kMiF = kMiH + kMlpTile * kGuideHid * 2;                  // 256 x 8 FP32 features
+constexpr uint32_t kMiGroupBytes = kMiF + kMiRows * 8 * 4;                  // 81,920
+constexpr uint32_t kMiGroup0 = kMlpX;                                       // after the weights (59,392)
+constexpr uint32_t kMiBar = kMiGroup0 + 2 * kMiGroupBytes;                  // 2 mbarriers, TMEM address
+constexpr uint32_t kMlpInferSmem = kMiBar + 64;                             // 223,296 bytes
+
+__device__ __forceinline__ void group_sync(uint32_t id) {
+    asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory");
+}
+// Barrier of the group that also returns whether pred held in all its threads.
+__device__ __forceinline__ bool group_all(uint32_t id, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(pred ? 1u : 0u), "r"(id)
+        : "memory");
+    return r != 0;
+}
+
 template <class Features>
-__device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, float *raw, uint32_t *err) {
-    mlp_tiles<false>(w, feat, raw, err, MlpTrain{});
+__device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, float *out, uint32_t *err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
+    const uint32_t g = warp >> 3, gtid = tid & 255u, gw = warp & 7u;
+    const uint32_t quarter = gw & 3u, half = gw >> 2;
+    const uint32_t r = 32u * quarter + lane;                     // this thread's row in the tile
+    const uint32_t bar_id = 1u + g;
+    uint64_t *bar = (uint64_t *)(smem + kMiBar) + g;
+    uint32_t *s_taddr = (uint32_t *)(smem + kMiBar + 16);
+    unsigned char *gs = smem + kMiGroup0 + g * kMiGroupBytes;
+    float *s_feat = (float *)(gs + kMiF);
+    const uint32_t n = feat.count();
+    const uint32_t tiles = (n + kMlpTile - 1) / kMlpTile;
+    const uint32_t units = (tiles + 1) / 2;                      // two tiles per gather
+    if (2 * blockIdx.x >= units) return;
+    mlp_stage_rows(smem + kMlpW1, w.W[0], kGuideHid, kGuideIn);
+    mlp_stage_rows(smem + kMlpW2, w.W[1], kGuideHid, kGuideHid);
+    mlp_stage_rows(smem + kMlpW3, w.W[2], kGuideHid, kGuideHid);
+    mlp_stage_rows(smem + kMlpW4, w.W[3], kGuideHid, kGuideHid);
+    mlp_stage_rows(smem + kMlpW5, w.W[4], kGuideOutPad, kGuideHid);
+    if (warp == 0) umma::tmem_alloc(s_taddr, 128);
+    if (tid == 0) {
+        umma::mbar_init((uint64_t *)(smem + kMiBar), 1);
+        umma::mbar_init((uint64_t *)(smem + kMiBar) + 1, 1);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t taddr = *s_taddr + 64u * g;                   // this group's 64 columns
+    const uint32_t lane_addr = taddr + ((32u * quarter) << 16);
+    const uint32_t sbase = umma::smem_addr(smem), gbase = umma::smem_addr(gs);
+    uint32_t phase = 0;
+    bool ok = true;
+    auto wait_layer = [&]() -> bool {
+        const bool done = umma::mbar_wait(bar, phase);
+        phase ^= 1u;
+        return group_all(bar_id, done);
+    };
+    for (uint32_t u = 2 * blockIdx.x + g; u < units && ok; u += 2 * gridDim.x) {
+        {
+            const uint32_t grow = u * kMiRows + gtid;
+            float f[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (grow < n) feat(grow, f);
+            group_sync(bar_id);   // the previous unit's last tile is done with s_feat
+#pragma unroll
+            for (int k = 0; k < 7; ++k) s_feat[8 * gtid + k] = f[k];
+            group_sync(bar_id);
+        }
+        for (uint32_t sub = 0; sub < 2; ++sub) {
+            const uint32_t t = 2 * u + sub;
+            if (t >= tiles) break;
+            const uint32_t row = t * kMlpTile + r;
+            const float *frow = s_feat + 8 * (sub * kMlpTile + r);
+            // one-blob encoding: this half writes columns 112 half .. + 111
+#pragma unroll 1
+            for (uint32_t j = 0; j < 14; ++j) {
+                const uint32_t col = 112u * half + 8u * j;
+                const float fv = frow[col / kGuideBins];
+                __align__(16) __nv_bfloat16 b[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) b[e] = __float2bfloat16(oneblob_bin(fv, (int)(col % kGuideBins) + e));
+                *(uint4 *)(gs + kMiX + umma::kmajor_offset(r, col, kGuideIn)) = *(const uint4 *)b;
+            }
+            umma::fence_proxy_async();
+            umma::fence_before_sync();
+            group_sync(bar_id);
+#pragma unroll 1
+            for (int l = 0; l < 4; ++l) {
+                if (gtid == 0) {
+                    const uint32_t a0 = l == 0 ? gbase + kMiX : gbase + kMiH;
+                    const uint32_t b0 = sbase + (l == 0 ? kMlpW1 : (l == 1 ? kMlpW2 : (l == 2 ? kMlpW3 : kMlpW4)));
+                    mlp_issue(taddr, a0, b0, l == 0 ? kGuideIn : kGuideHid, kGuideHid, bar);
+                }
+                if (!(ok = wait_layer())) break;
+                umma::fence_after_sync();
+#pragma unroll
+                for (uint32_t c = 0; c < 2; ++c) {
+                    const uint32_t c0 = 32u * half + 16u * c;
+                    float v[16];
+                    umma::tmem_ld16(lane_addr + c0, v);
+                    __align__(16) __nv_bfloat16 b[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) b[e] = __float2bfloat16(fmaxf(v[e], 0.f));
+                    *(uint4 *)(gs + kMiH + umma::kmajor_offset(r, c0, kGuideHid)) = *(const uint4 *)b;
+                    *(uint4 *)(gs + kMiH + umma::kmajor_offset(r, c0 + 8, kGuideHid)) = *(const uint4 *)(b + 8);
+                }
+                umma::fence_proxy_async();
+                umma::fence_before_sync();
+                group_sync(bar_id);
+            }
+            if (!ok) break;
+            if (gtid == 0) mlp_issue(taddr, gbase + kMiH, sbase + kMlpW5, kGuideHid, kGuideOutPad, bar);
+            if (!(ok = wait_layer())) break;
+            umma::fence_after_sync();
+            // outputs 0..39: half 0 columns 0..31, half 1 columns 32..39
+#pragma unroll
+            for (uint32_t c = 0; c < 2; ++c) {
+                if (half == 1 && c == 1) break;
+                const uint32_t c0 = 32u * half + 16u * c;
+                float v[16];
+                umma::tmem_ld16(lane_addr + c0, v);
+                if (row < n) {
+                    float4 *dst = (float4 *)(out + (size_t)row * kGuideOut + c0);
+                    const int nv = c0 + 16 <= (uint32_t)kGuideOut ? 4 : 2;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (e < nv) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+                }
+            }
+            // the accumulator, X and H are reused by the next tile
+            umma::fence_before_sync();
+            group_sync(bar_id);
+        }
+    }
+    if (!ok && gtid == 0) {
+        // the layer in flight may still complete: wait for it once more
+        // (bounded) before the tensor memory is released
+        umma::mbar_wait(bar, phase ^ 1u);
+        atomicExch(err, 1u);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    if (warp == 0) umma::tmem_dealloc(*s_taddr, 128);
 }
 
 }  // namespace rtg

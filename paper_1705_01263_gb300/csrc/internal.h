@@ -41,7 +41,7 @@ rt_status cuda_status(cudaError_t e, const char *what);
 std::vector<HaltonDim> make_dims(uint64_t seed, int ndims);
 
 // guiding network (guide.cu)
-rt_status guide_infer_async(rt_guide *g, const float *feat, int64_t n, const float **raw_out, cudaStream_t st);
+rt_status guide_infer_async(rt_guide *g, const float *feat, int64_t n, float *out, cudaStream_t st);   // out: n x 40
 rt_status guide_train_async(rt_guide *g, const float *feat, const float *wi, const float *weight, int64_t n,
                             cudaStream_t st);
 float guide_alpha(const rt_guide *g);

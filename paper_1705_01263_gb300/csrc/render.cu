@@ -784,7 +784,7 @@ __global__ void __launch_bounds__(128) k_shade_guided(RenderParams P, Pool pool,
             GuideRecord gr;
             const uint32_t v = s.depth;
             const bool want = recording && v <= kGuideMaxRec;
-            r = shade(P, s, h, sh, raw ? raw + (size_t)kGuideOutPad * i : nullptr, alpha, want ? &gr : nullptr, lo, hi);
+            r = shade(P, s, h, sh, raw ? raw + (size_t)kGuideOut * i : nullptr, alpha, want ? &gr : nullptr, lo, hi);
             pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
             if (r & 1) {
                 pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
@@ -1015,7 +1015,7 @@ static rt_status ensure_guided(RenderCache *rc, uint32_t cap, uint32_t batch) {
     rc->gfeat = rc->tr_feat = rc->tr_wi = rc->tr_w = nullptr;
     rc->grec = nullptr;
     rc->gnrec = nullptr;
-    if (cudaMalloc(&rc->gfeat, (size_t)cap * kGuideOutPad * 4) != cudaSuccess ||
+    if (cudaMalloc(&rc->gfeat, (size_t)cap * kGuideOut * 4) != cudaSuccess ||
         cudaMalloc(&rc->grec, (size_t)std::min(cap, batch) * kGuideMaxRec * 4 * sizeof(float4)) != cudaSuccess ||
         cudaMalloc(&rc->gnrec, (size_t)cap * 4) != cudaSuccess ||
         cudaMalloc(&rc->tr_feat, (size_t)batch * 7 * 4) != cudaSuccess ||
@@ -1209,7 +1209,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         const int g_ray = grid_for(k_raygen, 256, cap);
         const TraceKernels tk = trace_kernels(false, 0, s->dev.two_level, gbk);
         const int g_shade = grid_persistent(k_shade_guided, gbk, 0);
-        if ((rs = mlp_kernel_attr((const void *)k_guide_mlp_paths, kMlpSmem)) != RT_OK) return rs;
+        if ((rs = mlp_kernel_attr((const void *)k_guide_mlp_paths, kMlpInferSmem)) != RT_OK) return rs;
         const PathFeatures pf{P, gpool, glo, ghi};
         rt_stats stats{};
         auto t_start = std::chrono::steady_clock::now();
@@ -1240,7 +1240,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
                 // at the last vertex (it only adds emission) nor past gdepth
                 const float av = v <= gdepth ? a : 0.f;
                 if (av > 0.f) {
-                    k_guide_mlp_paths<<<sm_count(), kMlpThreads, kMlpSmem, st>>>(guide_weights(gd), pf, rc->gfeat,
+                    k_guide_mlp_paths<<<sm_count(), kMlpThreads, kMlpInferSmem, st>>>(guide_weights(gd), pf, rc->gfeat,
                                                                             guide_err(gd));
                     stats.kernel_launches += 1;
                 }
