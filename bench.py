@@ -201,12 +201,26 @@ def guided_vs_plain(light="down", target_spp=16384, chunk=512, max_factor=2, see
             break
     same = {p[0]: p[2] for p in plain}
     per_sample = [(spp, same[spp], r) for spp, _, r in guided if spp in same]
+    # the survey's short target: the plain tracer's RMSE at 256 spp (one
+    # render of 256 spp, timed alike); guided reaches it within its first
+    # call or later
+    film = rt.Film(cam.width, cam.height)
+    t0 = time.perf_counter()
+    rt.rt_render(scene, cam, 256, 8, film, rt.make_opts())
+    film.resolve(mean)
+    torch.cuda.synchronize()
+    t256 = time.perf_counter() - t0
+    r256 = float(np.sqrt(np.mean((mean.cpu().numpy().astype(np.float64) - ref) ** 2)))
+    g256 = next(((spp, el) for spp, el, r in guided if r <= r256), None)
+    short = {"target_rmse": r256, "plain_seconds": t256, "plain_spp": 256,
+             "guided_seconds": g256[1] if g256 else None, "guided_spp": g256[0] if g256 else None,
+             "guided_speedup": (t256 / g256[1]) if g256 else None}
     return {"scene": f"cornell 64x64, depth 8, emitter {'under the ceiling facing down' if light == 'down' else 'facing the ceiling'}",
             "reference": "FP64 oracle, 32768 spp from sequence iteration 2^20", "target_rmse": target,
             "target": f"plain RMSE at {target_spp} spp", "plain_seconds": t_plain, "plain_spp": plain[-1][0],
             "guided_seconds": t_guided, "guided_spp": spp_guided,
             "guided_speedup": (t_plain / t_guided) if t_guided else None,
-            "rmse_at_equal_spp": per_sample[-4:],
+            "rmse_at_equal_spp": per_sample[-4:], "target_256spp": short,
             "plain_curve": plain[::4], "guided_curve": guided[::4]}
 
 

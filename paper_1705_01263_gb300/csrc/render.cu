@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(128) k_trace_ext(DevScene sc, Pool pool) {
 
 // Capped at 64 registers (8 blocks of 128 per SM): the kernel is latency
 // bound, and the extra resident warps outweigh a few spilled registers.
+template <bool kLb>
 __global__ void __launch_bounds__(128, 8) k_shade(RenderParams P, Pool pool, const uint32_t *sorted) {
     Ctrl *c = pool.ctrl;
     if (c->tail) return;
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(128, 8) k_shade(RenderParams P, Pool pool, con
             h.prim = __float_as_uint(hv.x); h.inst = P.sc.two_level ? pool.hit_inst[q] : 0u;
             h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
             ShadowRay sh;
-            r = shade(P, s, h, sh);
+            r = shade<kLb>(P, s, h, sh);
             pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
             if (r & 1) {
                 pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
@@ -1288,7 +1289,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     const int g_ray = grid_for(k_raygen, 256, cap);
     const size_t smem = stack_smem(gb);
     const int g_trace = grid_persistent(k_trace_ext<false>, gb, smem);
-    const int g_shade = grid_persistent(k_shade, gb, 0);
+    const int g_shade = grid_persistent(k_shade<true>, gb, 0);
     const int g_shadow = grid_persistent(k_trace_shadow<false>, gb, smem);
     const int g_mega = grid_for(k_megakernel, gb, cap);
     const bool prof = o.profile >= 1, count = o.profile >= 2;
@@ -1379,7 +1380,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
                     stats.kernel_launches += 3;
                 }
                 e = mark(1);
-                k_shade<<<g_shade, gb, 0, st>>>(P, pool, sorted);
+                (s->dev.lb_nodes ? k_shade<true> : k_shade<false>)<<<g_shade, gb, 0, st>>>(P, pool, sorted);
                 done(e);
                 e = mark(2);
                 if (o.trace_kernel != 1) {
@@ -1574,7 +1575,7 @@ extern "C" rt_status rt_render_probes(const rt_scene *s, const float *pos, const
     const int gb = 128;
     const TraceKernels tk = trace_kernels(false, 0, s->dev.two_level, gb);
     const int g_start = grid_for(k_probe_start, 256, cap);
-    const int g_shade = grid_persistent(k_shade, gb, 0);
+    const int g_shade = grid_persistent(k_shade<true>, gb, 0);
     rt_stats stats{};
     Ctrl host_ctrl{};
     auto t_start = std::chrono::steady_clock::now();
@@ -1598,7 +1599,7 @@ extern "C" rt_status rt_render_probes(const rt_scene *s, const float *pos, const
         stats.kernel_launches += 4;
         for (uint32_t v = 2; v <= max_depth + 1; ++v) {
             tk.ext<<<tk.grid_ext, gb, tk.smem, st>>>(s->dev, pool, nullptr);
-            k_shade<<<g_shade, gb, 0, st>>>(P, pool, nullptr);
+            (s->dev.lb_nodes ? k_shade<true> : k_shade<false>)<<<g_shade, gb, 0, st>>>(P, pool, nullptr);
             tk.shadow<<<tk.grid_shadow, gb, tk.smem, st>>>(s->dev, pool, nullptr);
             k_step_end<<<1, 1, 0, st>>>(pool);
             stats.kernel_launches += 4;
@@ -1688,7 +1689,7 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
     const size_t smem = stack_smem(gb);
     const int g_ray = grid_for(k_raygen, 256, cap);
     const int g_trace = grid_persistent(k_trace_ext<false>, gb, smem);
-    const int g_shade = grid_persistent(k_shade, gb, 0);
+    const int g_shade = grid_persistent(k_shade<true>, gb, 0);
     const int g_shadow = grid_persistent(k_trace_shadow<false>, gb, smem);
     const TraceKernels tk = trace_kernels(false, o.trace_kernel == 1 ? 0 : o.trace_kernel, s->dev.two_level, gb);
     const int g_mega = grid_for(k_megakernel, gb, cap);
@@ -1713,7 +1714,7 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
                 if (o.trace_kernel != 1) tk.ext<<<tk.grid_ext, gb, tk.smem, st>>>(s->dev, pool, nullptr);
                 else k_trace_ext<false><<<g_trace, gb, smem, st>>>(s->dev, pool);
-                k_shade<<<g_shade, gb, 0, st>>>(P, pool, nullptr);
+                (s->dev.lb_nodes ? k_shade<true> : k_shade<false>)<<<g_shade, gb, 0, st>>>(P, pool, nullptr);
                 if (o.trace_kernel != 1) tk.shadow<<<tk.grid_shadow, gb, tk.smem, st>>>(s->dev, pool, nullptr);
                 else k_trace_shadow<false><<<g_shadow, gb, smem, st>>>(s->dev, pool);
                 k_step_end<<<1, 1, 0, st>>>(pool);

@@ -621,6 +621,8 @@ struct NeePick {
     V3 l0, l1, l2;
 };
 
+// kLb false: compiled without the light hierarchy (scenes that have none).
+template <bool kLb = true>
 RT_HD NeePick nee_pick(const RenderParams &P, uint64_t index, int base) {
     const DevScene &sc = P.sc;
     NeePick k;
@@ -631,7 +633,7 @@ RT_HD NeePick nee_pick(const RenderParams &P, uint64_t index, int base) {
     k.lmid = 0;
     k.lpa = 0.f;
     k.l0 = k.l1 = k.l2 = v3(0.f, 0.f, 0.f);
-    if (!(k.us < sc.p_env) && !sc.lb_nodes) {
+    if (!(k.us < sc.p_env) && !(kLb && sc.lb_nodes)) {
         float u2 = (k.us - sc.p_env) / (1.f - sc.p_env);
         float xn = u2 * (float)sc.num_lights;
         uint32_t bin = (uint32_t)xn;
@@ -654,6 +656,7 @@ RT_HD NeePick nee_pick(const RenderParams &P, uint64_t index, int base) {
 // path s, vertex number s.depth: the scattering half of shade(), shared with
 // the probe vertex. Returns bit 0 when the path continues and bit 1 when `sh`
 // holds a shadow ray (see shade()).
+template <bool kLb = true>
 RT_HD int scatter(const RenderParams &P, PathState &s, const Vertex &vx, const Material &m, bool nee,
                   const NeePick &pk, ShadowRay &sh, const float *graw, float alpha, GuideRecord *rec, float3 glo,
                   float3 ghi) {
@@ -684,7 +687,7 @@ RT_HD int scatter(const RenderParams &P, PathState &s, const Vertex &vx, const M
             V3 l0 = pk.l0, l1 = pk.l1, l2 = pk.l2;
             uint32_t lt = pk.lt, lmid = pk.lmid;
             float lpa = pk.lpa;
-            if (sc.lb_nodes) {
+            if (kLb && sc.lb_nodes) {
                 // the light hierarchy draws the emitter from the offset
                 // origin and the normal as the path state keeps it, so that
                 // an emitter hit by the continuation gets the same number
@@ -793,6 +796,7 @@ RT_HD int scatter(const RenderParams &P, PathState &s, const Vertex &vx, const M
 // from the one-sample MIS mixture alpha * vMF-mixture + (1 - alpha) * BSDF
 // and every pdf used for MIS is that mixture's; with `rec` the vertex's
 // training record is filled when the path continues.
+template <bool kLb = true>
 RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh, const float *graw = nullptr,
                 float alpha = 0.f, GuideRecord *rec = nullptr, float3 glo = float3{0.f, 0.f, 0.f},
                 float3 ghi = float3{1.f, 1.f, 1.f}) {
@@ -824,7 +828,7 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
     const bool last = v == P.max_depth + 1;
     const bool nee = !last && (sc.num_lights > 0 || sc.p_env > 0.f) && mode != 3;
     NeePick pk;
-    if (nee) pk = nee_pick(P, s.index, 2 + 7 * (int)(v - 1));
+    if (nee) pk = nee_pick<kLb>(P, s.index, 2 + 7 * (int)(v - 1));
     Vertex vx;
     setup_vertex(sc, s, h, vx);
     if (vx.cog > 0.f && lpa > 0.f) {
@@ -835,7 +839,7 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
             else if (mode == 2) w = 0.f;
             else {
                 float pa = lpa;
-                if (sc.lb_nodes) {
+                if (kLb && sc.lb_nodes) {
                     // the hierarchy's probability of this emitter from the
                     // previous vertex (offset origin s.o, its stored normal)
                     const uint32_t li = ldg(sc.lb_inst_base + h.inst) + ldg(sc.lb_tri_rank + prim);
@@ -848,7 +852,7 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
     }
     if (last) return 0;
     const Material m = load_material(sc, mid);
-    return scatter(P, s, vx, m, nee, pk, sh, graw, alpha, rec, glo, ghi);
+    return scatter<kLb>(P, s, vx, m, nee, pk, sh, graw, alpha, rec, glo, ghi);
 }
 
 // Vertex 1 of an irradiance-probe path (Sec. 4.2): a virtual white
