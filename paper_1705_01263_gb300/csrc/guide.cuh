@@ -21,10 +21,28 @@ constexpr int kGuideLobes = 8;
 constexpr int64_t kGuideParams = (int64_t)kGuideIn * kGuideHid + 3 * kGuideHid * kGuideHid + kGuideHid * kGuideOut;
 constexpr float kKappaMin = 1e-2f, kKappaMax = 1e4f;
 
-RT_HD float oneblob_bin(float s, int c) {
+// One-blob bins c0 .. c0 + 7 (c0 a multiple of 8) of scalar s, the Gaussian
+// exp(-(s - (c + 1/2) / 32)^2 / (2 sigma^2)) with sigma = 1/32: bin c0 by one
+// exponential, its neighbours by the ratio of consecutive bins,
+// g(c + 1) = g(c) r_c with r_c = exp(32 (s - (c + 1/2) / 32) - 1/2) and
+// r_{c+1} = r_c / e (two exponentials per eight bins instead of eight).
+RT_HD void oneblob_chunk(float s, int c0, float *g8) {
     const float sig = 1.f / kGuideBins;
-    float d = s - ((float)c + 0.5f) / kGuideBins;
-    return expf(-d * d / (2.f * sig * sig));
+    const float d = s - ((float)c0 + 0.5f) / kGuideBins;
+    float g = expf(-d * d / (2.f * sig * sig));
+    float r = expf((float)kGuideBins * d - 0.5f);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        g8[e] = g;
+        g *= r;
+        r *= 0.36787944117144233f;   // 1 / e
+    }
+}
+
+RT_HD float oneblob_bin(float s, int c) {
+    float g8[8];
+    oneblob_chunk(s, c & ~7, g8);
+    return g8[c & 7];
 }
 
 // Features in [0,1]: position in the scene box (3), outgoing direction and

@@ -149,8 +149,10 @@ __device__ void mlp_tiles(const MlpWeights &w, const Features &feat, float *raw,
             const uint32_t col = 56u * part + 8u * j;
             const float fv = frow[col / kGuideBins];
             __align__(16) __nv_bfloat16 b[8];
+            float g8[8];
+            oneblob_chunk(fv, (int)(col % kGuideBins), g8);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) b[e] = __float2bfloat16(oneblob_bin(fv, (int)(col % kGuideBins) + e));
+            for (int e = 0; e < 8; ++e) b[e] = __float2bfloat16(g8[e]);
             *(uint4 *)(smem + kMlpX + umma::kmajor_offset(r, col, kGuideIn)) = *(const uint4 *)b;
             if (kTrain) {
                 const __nv_bfloat16 z = __float2bfloat16(0.f);
@@ -352,8 +354,10 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, float
                 const uint32_t col = 112u * half + 8u * j;
                 const float fv = frow[col / kGuideBins];
                 __align__(16) __nv_bfloat16 b[8];
+                float g8[8];
+                oneblob_chunk(fv, (int)(col % kGuideBins), g8);
 #pragma unroll
-                for (int e = 0; e < 8; ++e) b[e] = __float2bfloat16(oneblob_bin(fv, (int)(col % kGuideBins) + e));
+                for (int e = 0; e < 8; ++e) b[e] = __float2bfloat16(g8[e]);
                 *(uint4 *)(gs + kMiX + umma::kmajor_offset(r, col, kGuideIn)) = *(const uint4 *)b;
             }
             umma::fence_proxy_async();
