@@ -100,6 +100,19 @@ struct DevScene {
     // cell uses the plain pyramid); env_nfac[c * env_nregions + R] = the
     // cell's pdf over the plain pdf in region R of level env_lstar (the
     // cosine bound times env_nscale[c]; 1 for a plain cell)
+    // the descent reads two levels per load: for a node of level l >= 2 five
+    // float4 at env_dq + env_dqoff_h[l] + 5 * node (its children's weights as
+    // the quad (x0 y0, x1 y0, x0 y1, x1 y1), then each child's own children
+    // quad, in that order); for a node of level 1 one float4 (its children
+    // quad) at env_dq + env_dqoff_h[1] + node. env_ndq: the same blocks per
+    // normal cell for the levels whose children are reweighted, a cell's
+    // blocks env_ndqstride float4 apart, offsets env_ndqoff_h[l] (-1: the
+    // level's blocks come from env_dq)
+    const float4 *env_dq;
+    int64_t env_dqoff_h[16];
+    const float4 *env_ndq;
+    int64_t env_ndqoff_h[16];
+    int64_t env_ndqstride;
     const float *env_nw;
     const float *env_nscale;
     const float *env_nfac;

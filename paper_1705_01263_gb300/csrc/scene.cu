@@ -561,9 +561,53 @@ rt_status rtg::scene_create(const rt_scene_desc *d, rt_scene **out, bool host_on
         if ((st = upload(s, env4.data(), env4.size(), &D.env, &Hs.env)) != RT_OK) return fail(st);
         if ((st = upload(s, pyr.data(), pyr.size(), &D.env_pyr, &Hs.env_pyr)) != RT_OK) return fail(st);
         if ((st = upload(s, off.data(), off.size(), &D.env_off, &Hs.env_off)) != RT_OK) return fail(st);
+        // descent blocks: per node of level l >= 1, its children quad and,
+        // from level 2 on, its children's quads (weights as stored above)
+        auto quad_of = [&](auto &&wt, int l, int32_t x, int32_t y) {
+            return make_float4(wt(l, 2 * x, 2 * y), wt(l, 2 * x + 1, 2 * y), wt(l, 2 * x, 2 * y + 1),
+                               wt(l, 2 * x + 1, 2 * y + 1));
+        };
+        auto blocks_of = [&](auto &&wt, int l, std::vector<float4> &out) {
+            const int32_t wl = W >> l, hl = std::max(1, H >> l);
+            for (int32_t y = 0; y < hl; ++y)
+                for (int32_t x = 0; x < wl; ++x) {
+                    out.push_back(quad_of(wt, l - 1, x, y));
+                    if (l >= 2)
+                        for (int k = 0; k < 4; ++k) out.push_back(quad_of(wt, l - 2, 2 * x + (k & 1), 2 * y + (k >> 1)));
+                }
+        };
+        auto plain_w = [&](int l, int32_t x, int32_t y) { return pyr[off[l] + (int64_t)y * (W >> l) + x]; };
+        std::vector<float4> dq;
+        for (int l = 0; l < 16; ++l) D.env_dqoff_h[l] = Hs.env_dqoff_h[l] = -1;
+        for (int l = 1; l < levels; ++l) {
+            D.env_dqoff_h[l] = Hs.env_dqoff_h[l] = (int64_t)dq.size();
+            blocks_of(plain_w, l, dq);
+        }
+        for (int l = 0; l < 16; ++l) D.env_ndqoff_h[l] = Hs.env_ndqoff_h[l] = -1;
+        if (!dq.empty() && (st = upload(s, dq.data(), dq.size(), &D.env_dq, &Hs.env_dq)) != RT_OK) return fail(st);
         if (!d->env_plain && env_sum > 0.0) {
             EnvNormalTables nt;
             build_env_normal_tables(lv, W, H, levels, env_sum, nt);
+            // per cell, the blocks of the levels whose children are reweighted
+            std::vector<float4> ndq;
+            int64_t stride = 0, noff[16];
+            for (int l = 0; l < 16; ++l) noff[l] = -1;
+            for (int c = 0; c < 64; ++c) {
+                auto cell_w = [&](int l, int32_t x, int32_t y) {
+                    return l >= nt.lstar ? nt.nw[(size_t)c * nt.stride + nt.off[l] + (int64_t)y * (W >> l) + x]
+                                         : plain_w(l, x, y);
+                };
+                const size_t start = ndq.size();
+                for (int l = levels - 1; l >= 1 && l - 1 >= nt.lstar; --l) {
+                    if (c == 0) noff[l] = (int64_t)(ndq.size() - start);
+                    blocks_of(cell_w, l, ndq);
+                }
+                if (c == 0) stride = (int64_t)(ndq.size() - start);
+            }
+            for (int l = 0; l < 16; ++l) D.env_ndqoff_h[l] = Hs.env_ndqoff_h[l] = noff[l];
+            D.env_ndqstride = Hs.env_ndqstride = stride;
+            if (!ndq.empty() && (st = upload(s, ndq.data(), ndq.size(), &D.env_ndq, &Hs.env_ndq)) != RT_OK)
+                return fail(st);
             D.env_lstar = Hs.env_lstar = nt.lstar;
             D.env_nregions = Hs.env_nregions = nt.nregions;
             D.env_nstride = Hs.env_nstride = nt.stride;

@@ -307,16 +307,48 @@ RT_HD int choose2(float a, float b, float &u) {
 }
 
 // Pyramid descent (Sec. 2.1.2): column by u then row by v at each level,
-// then a uniform direction in (phi, cos theta) inside the texel.
-RT_HD V3 env_sample(const DevScene &sc, float u, float v) {
-    int top = sc.env_levels - 1;
-    int x = choose2(envw(sc, top, 0, 0), envw(sc, top, 1, 0), u), y = 0;
-    for (int l = top - 1; l >= 0; --l) {
-        float left = envw(sc, l, 2 * x, 2 * y) + envw(sc, l, 2 * x, 2 * y + 1);
-        float right = envw(sc, l, 2 * x + 1, 2 * y) + envw(sc, l, 2 * x + 1, 2 * y + 1);
-        x = 2 * x + choose2(left, right, u);
-        y = 2 * y + choose2(envw(sc, l, x, 2 * y), envw(sc, l, x, 2 * y + 1), v);
+// rescaling each, from the top pair down to a texel. The weights come in
+// blocks of two levels (DevScene::env_dq; a normal cell's own blocks where
+// its children are reweighted, cellq non-null), so one load serves two
+// choices; the choices and the values they use are those of a level-by-level
+// walk over the stored weights.
+RT_HD void env_descend(const DevScene &sc, const float4 *cellq, float top0, float top1, float &u, float &v, int &x,
+                       int &y) {
+    int l = sc.env_levels - 1;
+    x = choose2(top0, top1, u);
+    y = 0;
+    while (l >= 1) {
+        const int64_t node = (int64_t)y * (sc.env_w >> l) + x;
+        const bool own = cellq && sc.env_ndqoff_h[l] >= 0;
+        const float4 *B = own ? cellq + sc.env_ndqoff_h[l] : sc.env_dq + sc.env_dqoff_h[l];
+        if (l >= 2) {
+            B += 5 * node;
+            const float4 q = ldg(B), g0 = ldg(B + 1), g1 = ldg(B + 2), g2 = ldg(B + 3), g3 = ldg(B + 4);
+            int dx = choose2(q.x + q.z, q.y + q.w, u);
+            int dy = choose2(dx ? q.y : q.x, dx ? q.w : q.z, v);
+            x = 2 * x + dx;
+            y = 2 * y + dy;
+            const int k = 2 * dy + dx;
+            const float4 g = k == 0 ? g0 : (k == 1 ? g1 : (k == 2 ? g2 : g3));
+            dx = choose2(g.x + g.z, g.y + g.w, u);
+            dy = choose2(dx ? g.y : g.x, dx ? g.w : g.z, v);
+            x = 2 * x + dx;
+            y = 2 * y + dy;
+            l -= 2;
+        } else {
+            const float4 q = ldg(B + node);
+            const int dx = choose2(q.x + q.z, q.y + q.w, u);
+            const int dy = choose2(dx ? q.y : q.x, dx ? q.w : q.z, v);
+            x = 2 * x + dx;
+            y = 2 * y + dy;
+            l -= 1;
+        }
     }
+}
+
+// Direction uniform in (phi, cos theta) inside texel (x, y), by the
+// remaining fractions u, v.
+RT_HD V3 env_texel_dir(const DevScene &sc, int x, int y, float u, float v) {
     float phi = 2.f * kPi * ((float)x + u) / (float)sc.env_w;
     float c0 = cosf(kPi * (float)y / (float)sc.env_h), c1 = cosf(kPi * (float)(y + 1) / (float)sc.env_h);
     float ct = c0 - v * (c0 - c1);
@@ -328,6 +360,13 @@ RT_HD V3 env_sample(const DevScene &sc, float u, float v) {
     sp = sinf(phi); cp = cosf(phi);
 #endif
     return v3(st * cp, ct, st * sp);
+}
+
+RT_HD V3 env_sample(const DevScene &sc, float u, float v) {
+    const int top = sc.env_levels - 1;
+    int x, y;
+    env_descend(sc, nullptr, envw(sc, top, 0, 0), envw(sc, top, 1, 0), u, v, x, y);
+    return env_texel_dir(sc, x, y, u, v);
 }
 
 // Normal-oriented top levels of the pyramid (Sec. 2.1.2). The unit sphere of
@@ -372,29 +411,11 @@ RT_HD float env_cell_factor(const DevScene &sc, uint32_t cell, int tx) {
 RT_HD V3 env_sample_cell(const DevScene &sc, uint32_t cell, float u, float v) {
     if (!sc.env_nw || !(ldg(sc.env_nscale + cell) > 0.f)) return env_sample(sc, u, v);
     const float *blk = sc.env_nw + (size_t)cell * (size_t)sc.env_nstride;
-    const int top = sc.env_levels - 1, ls = sc.env_lstar;
-    auto w = [&](int l, int x, int y) -> float {
-        if (l < ls) return envw(sc, l, x, y);
-        return ldg(blk + sc.env_noff_h[l] + (int64_t)y * (sc.env_w >> l) + x);
-    };
-    int x = choose2(w(top, 0, 0), w(top, 1, 0), u), y = 0;
-    for (int l = top - 1; l >= 0; --l) {
-        float left = w(l, 2 * x, 2 * y) + w(l, 2 * x, 2 * y + 1);
-        float right = w(l, 2 * x + 1, 2 * y) + w(l, 2 * x + 1, 2 * y + 1);
-        x = 2 * x + choose2(left, right, u);
-        y = 2 * y + choose2(w(l, x, 2 * y), w(l, x, 2 * y + 1), v);
-    }
-    float phi = 2.f * kPi * ((float)x + u) / (float)sc.env_w;
-    float c0 = cosf(kPi * (float)y / (float)sc.env_h), c1 = cosf(kPi * (float)(y + 1) / (float)sc.env_h);
-    float ct = c0 - v * (c0 - c1);
-    float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
-    float sp, cp;
-#ifdef __CUDA_ARCH__
-    sincosf(phi, &sp, &cp);
-#else
-    sp = sinf(phi); cp = cosf(phi);
-#endif
-    return v3(st * cp, ct, st * sp);
+    const int top = sc.env_levels - 1;
+    int x, y;
+    env_descend(sc, sc.env_ndq + (size_t)cell * (size_t)sc.env_ndqstride, ldg(blk + sc.env_noff_h[top]),
+                ldg(blk + sc.env_noff_h[top] + 1), u, v, x, y);
+    return env_texel_dir(sc, x, y, u, v);
 }
 
 // Ray origin moved off the surface along n by an offset that grows with the
