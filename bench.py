@@ -201,7 +201,7 @@ def guided_vs_plain(light="down", target_spp=16384, chunk=512, max_factor=2, see
             break
     same = {p[0]: p[2] for p in plain}
     per_sample = [(spp, same[spp], r) for spp, _, r in guided if spp in same]
-    # the survey's short target: the plain tracer's RMSE at 256 spp (one
+    # a short target as well: the plain tracer's RMSE at 256 spp (one
     # render of 256 spp, timed alike); guided reaches it within its first
     # call or later
     film = rt.Film(cam.width, cam.height)
