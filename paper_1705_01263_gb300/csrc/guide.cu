@@ -329,7 +329,7 @@ rt_status mlp_kernel_attr(const void *kernel, uint32_t bytes) {
 rt_status guide_infer_async(rt_guide *g, const float *feat, int64_t n, float *out, cudaStream_t st) {
     rt_status s;
     if ((s = mlp_kernel_attr((const void *)k_guide_mlp, kMlpInferSmem)) != RT_OK) return s;
-    const int64_t per_cta = 2 * kMiRows;   // two groups of two tiles
+    const int64_t per_cta = kMiGroups * kMlpTile;   // four groups, one tile each
     const int grid = (int)std::min<int64_t>((n + per_cta - 1) / per_cta, (int64_t)sm_count());
     k_guide_mlp<<<grid, kMlpThreads, kMlpInferSmem, st>>>(guide_weights(g), ArrayFeatures{feat, (uint32_t)n}, out,
                                                            g->err);

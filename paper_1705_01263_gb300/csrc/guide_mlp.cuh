@@ -1,6 +1,6 @@
 // Fused forward pass of the guiding network on the tensor cores. The
 // training forward (mlp_tiles<true>) works as follows; the inference kernel
-// (mlp_infer_tiles, below) keeps two tiles in flight instead of one. One
+// (mlp_infer_tiles, below) keeps four tiles in flight instead of one. One
 // persistent CTA of 512 threads per SM keeps all five BF16 weight matrices (58 KB) in
 // shared memory and walks tiles of 128 rows, four threads per row (part p =
 // warp / 4 of row 32 (warp % 4) + lane), so that each SM sub-partition has
@@ -260,72 +260,79 @@ __device__ void mlp_tiles(const MlpWeights &w, const Features &feat, float *raw,
 }
 
 // ---------------------------------------------------------------- inference
-// Two tiles in flight: the 512 threads form two independent groups of 256
-// (eight warps), each with its own one-blob and activation buffers, feature
-// buffer, 64 tensor-memory columns and mbarrier, sharing the weights; while
-// one group waits for its tensor-core product the other encodes, reads back
-// or stores. In a group, two threads serve a row (half h of the columns:
-// warp w of the group reaches tensor-memory lanes 32 (w % 4) + 0..31, rows
-// 32 (w % 4) + lane, h = w / 4), and the group gathers the features of two
-// tiles at once. The group synchronises on its own named barrier (ids 1, 2),
-// so a wait that times out in one group leaves the other running. Outputs:
-// 40 floats per row (row stride kGuideOut).
-constexpr uint32_t kMiRows = 2 * kMlpTile;                                 // rows gathered per group
-constexpr uint32_t kMiX = 0;                                                // 128 x 224 BF16
-constexpr uint32_t kMiH = kMiX + kMlpTile * kGuideIn * 2;                   // 128 x 64 BF16
-constexpr uint32_t kMiF = kMiH + kMlpTile * kGuideHid * 2;                  // 256 x 8 FP32 features
-constexpr uint32_t kMiGroupBytes = kMiF + kMiRows * 8 * 4;                  // 81,920
-constexpr uint32_t kMiGroup0 = kMlpX;                                       // after the weights (59,392)
-constexpr uint32_t kMiBar = kMiGroup0 + 2 * kMiGroupBytes;                  // 2 mbarriers, TMEM address
-constexpr uint32_t kMlpInferSmem = kMiBar + 64;                             // 223,296 bytes
+// Four tiles in flight: the 512 threads form four independent groups of 128
+// (four warps), one thread per row (warp w of a group reaches tensor-memory
+// lanes 32 (w % 4) + 0..31, its rows), each group with its own 64
+// tensor-memory columns, mbarrier and named barrier (ids 1..4), sharing the
+// weights. A group's shared buffer is 128 x 112 BF16: layer 1 runs in two K
+// halves, the one-blob columns 0..111 then 112..223 encoded into the same
+// buffer (the second after the first product has completed, the products
+// accumulating in tensor memory), and the hidden activations (128 x 64) then
+// overlay it. While one group waits on its tensor-core product the others
+// encode, read back or store. Outputs: 40 floats per row (row stride
+// kGuideOut).
+constexpr uint32_t kMiHalfK = kGuideIn / 2;                                // 112
+constexpr uint32_t kMiBuf = kMlpTile * kMiHalfK * 2;                       // 28,672 bytes
+constexpr uint32_t kMiGroup0 = kMlpX;                                      // after the weights (59,392)
+constexpr uint32_t kMiGroups = 4;
+constexpr uint32_t kMiBar = kMiGroup0 + kMiGroups * kMiBuf;                // 4 mbarriers, TMEM address
+constexpr uint32_t kMlpInferSmem = kMiBar + 64;                            // 174,144 bytes
 
 __device__ __forceinline__ void group_sync(uint32_t id) {
-    asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory");
+    asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
 }
 // Barrier of the group that also returns whether pred held in all its threads.
 __device__ __forceinline__ bool group_all(uint32_t id, bool pred) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, %2, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        "bar.red.and.pred q, %2, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
         : "r"(pred ? 1u : 0u), "r"(id)
         : "memory");
     return r != 0;
 }
 
+// Layer-1 product over one K half: D (+)= A[128 x 112] * W1[:, k0 .. k0 + 111]^T.
+__device__ __forceinline__ void mlp_issue_half(uint32_t taddr, uint32_t a0, uint32_t w1, uint32_t half, uint64_t *bar) {
+    const uint32_t idesc = umma::make_idesc_bf16(kMlpTile, kGuideHid);
+    const uint32_t sbo_a = kMiHalfK / 8 * 128, sbo_b = kGuideIn / 8 * 128;
+    const uint32_t b0 = w1 + half * (kMiHalfK / 8) * 128;
+    umma::fence_after_sync();
+    for (uint32_t kk = 0; kk < kMiHalfK / 16; ++kk) {
+        const uint64_t ad = umma::make_desc(a0 + kk * 256, 128, sbo_a);
+        const uint64_t bd = umma::make_desc(b0 + kk * 256, 128, sbo_b);
+        umma::mma_bf16(taddr, ad, bd, idesc, (half > 0 || kk > 0) ? 1u : 0u);
+    }
+    umma::mma_commit(bar);
+}
+
 template <class Features>
 __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, float *out, uint32_t *err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
-    const uint32_t g = warp >> 3, gtid = tid & 255u, gw = warp & 7u;
-    const uint32_t quarter = gw & 3u, half = gw >> 2;
+    const uint32_t g = warp >> 2, quarter = warp & 3u, gtid = tid & 127u;
     const uint32_t r = 32u * quarter + lane;                     // this thread's row in the tile
     const uint32_t bar_id = 1u + g;
     uint64_t *bar = (uint64_t *)(smem + kMiBar) + g;
-    uint32_t *s_taddr = (uint32_t *)(smem + kMiBar + 16);
-    unsigned char *gs = smem + kMiGroup0 + g * kMiGroupBytes;
-    float *s_feat = (float *)(gs + kMiF);
+    uint32_t *s_taddr = (uint32_t *)(smem + kMiBar + 32);
+    unsigned char *buf = smem + kMiGroup0 + g * kMiBuf;
     const uint32_t n = feat.count();
     const uint32_t tiles = (n + kMlpTile - 1) / kMlpTile;
-    const uint32_t units = (tiles + 1) / 2;                      // two tiles per gather
-    if (2 * blockIdx.x >= units) return;
+    if (kMiGroups * blockIdx.x >= tiles) return;
     mlp_stage_rows(smem + kMlpW1, w.W[0], kGuideHid, kGuideIn);
     mlp_stage_rows(smem + kMlpW2, w.W[1], kGuideHid, kGuideHid);
     mlp_stage_rows(smem + kMlpW3, w.W[2], kGuideHid, kGuideHid);
     mlp_stage_rows(smem + kMlpW4, w.W[3], kGuideHid, kGuideHid);
     mlp_stage_rows(smem + kMlpW5, w.W[4], kGuideOutPad, kGuideHid);
-    if (warp == 0) umma::tmem_alloc(s_taddr, 128);
-    if (tid == 0) {
-        umma::mbar_init((uint64_t *)(smem + kMiBar), 1);
-        umma::mbar_init((uint64_t *)(smem + kMiBar) + 1, 1);
-    }
+    if (warp == 0) umma::tmem_alloc(s_taddr, 256);
+    if (tid < kMiGroups) umma::mbar_init((uint64_t *)(smem + kMiBar) + tid, 1);
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
     const uint32_t taddr = *s_taddr + 64u * g;                   // this group's 64 columns
     const uint32_t lane_addr = taddr + ((32u * quarter) << 16);
-    const uint32_t sbase = umma::smem_addr(smem), gbase = umma::smem_addr(gs);
+    const uint32_t sbase = umma::smem_addr(smem), bbase = umma::smem_addr(buf);
     uint32_t phase = 0;
     bool ok = true;
     auto wait_layer = [&]() -> bool {
@@ -333,86 +340,77 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, float
         phase ^= 1u;
         return group_all(bar_id, done);
     };
-    for (uint32_t u = 2 * blockIdx.x + g; u < units && ok; u += 2 * gridDim.x) {
-        {
-            const uint32_t grow = u * kMiRows + gtid;
-            float f[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (grow < n) feat(grow, f);
-            group_sync(bar_id);   // the previous unit's last tile is done with s_feat
-#pragma unroll
-            for (int k = 0; k < 7; ++k) s_feat[8 * gtid + k] = f[k];
-            group_sync(bar_id);
-        }
-        for (uint32_t sub = 0; sub < 2; ++sub) {
-            const uint32_t t = 2 * u + sub;
-            if (t >= tiles) break;
-            const uint32_t row = t * kMlpTile + r;
-            const float *frow = s_feat + 8 * (sub * kMlpTile + r);
-            // one-blob encoding: this half writes columns 112 half .. + 111
+    // one-blob columns [c0, c0 + 112) of this row into the buffer (kdim 112)
+    auto encode_half = [&](const float *f, uint32_t c0) {
 #pragma unroll 1
-            for (uint32_t j = 0; j < 14; ++j) {
-                const uint32_t col = 112u * half + 8u * j;
-                const float fv = frow[col / kGuideBins];
-                __align__(16) __nv_bfloat16 b[8];
-                float g8[8];
-                oneblob_chunk(fv, (int)(col % kGuideBins), g8);
+        for (uint32_t j = 0; j < kMiHalfK / 8; ++j) {
+            const uint32_t col = c0 + 8u * j;
+            float g8[8];
+            oneblob_chunk(f[col / kGuideBins], (int)(col % kGuideBins), g8);
+            __align__(16) __nv_bfloat16 b[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) b[e] = __float2bfloat16(g8[e]);
-                *(uint4 *)(gs + kMiX + umma::kmajor_offset(r, col, kGuideIn)) = *(const uint4 *)b;
+            for (int e = 0; e < 8; ++e) b[e] = __float2bfloat16(g8[e]);
+            *(uint4 *)(buf + umma::kmajor_offset(r, 8u * j, kMiHalfK)) = *(const uint4 *)b;
+        }
+        umma::fence_proxy_async();
+        umma::fence_before_sync();
+        group_sync(bar_id);
+    };
+    for (uint32_t t = kMiGroups * blockIdx.x + g; t < tiles && ok; t += kMiGroups * gridDim.x) {
+        const uint32_t row = t * kMlpTile + r;
+        float f[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (row < n) feat(row, f);
+        encode_half(f, 0u);
+        if (gtid == 0) mlp_issue_half(taddr, bbase, sbase + kMlpW1, 0u, bar);
+        if (!(ok = wait_layer())) break;
+        encode_half(f, kMiHalfK);
+        if (gtid == 0) mlp_issue_half(taddr, bbase, sbase + kMlpW1, 1u, bar);
+        if (!(ok = wait_layer())) break;
+        // layers 2..5: read back, ReLU -> BF16 -> the activation buffer
+        // (overlaying the one-blob buffer), next product
+#pragma unroll 1
+        for (int l = 1; l < 5; ++l) {
+            umma::fence_after_sync();
+#pragma unroll 1
+            for (uint32_t c0 = 0; c0 < (uint32_t)kGuideHid; c0 += 16) {
+                float v[16];
+                umma::tmem_ld16(lane_addr + c0, v);
+                __align__(16) __nv_bfloat16 b[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) b[e] = __float2bfloat16(fmaxf(v[e], 0.f));
+                *(uint4 *)(buf + umma::kmajor_offset(r, c0, kGuideHid)) = *(const uint4 *)b;
+                *(uint4 *)(buf + umma::kmajor_offset(r, c0 + 8, kGuideHid)) = *(const uint4 *)(b + 8);
             }
             umma::fence_proxy_async();
             umma::fence_before_sync();
             group_sync(bar_id);
-#pragma unroll 1
-            for (int l = 0; l < 4; ++l) {
-                if (gtid == 0) {
-                    const uint32_t a0 = l == 0 ? gbase + kMiX : gbase + kMiH;
-                    const uint32_t b0 = sbase + (l == 0 ? kMlpW1 : (l == 1 ? kMlpW2 : (l == 2 ? kMlpW3 : kMlpW4)));
-                    mlp_issue(taddr, a0, b0, l == 0 ? kGuideIn : kGuideHid, kGuideHid, bar);
-                }
-                if (!(ok = wait_layer())) break;
-                umma::fence_after_sync();
-#pragma unroll
-                for (uint32_t c = 0; c < 2; ++c) {
-                    const uint32_t c0 = 32u * half + 16u * c;
-                    float v[16];
-                    umma::tmem_ld16(lane_addr + c0, v);
-                    __align__(16) __nv_bfloat16 b[16];
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) b[e] = __float2bfloat16(fmaxf(v[e], 0.f));
-                    *(uint4 *)(gs + kMiH + umma::kmajor_offset(r, c0, kGuideHid)) = *(const uint4 *)b;
-                    *(uint4 *)(gs + kMiH + umma::kmajor_offset(r, c0 + 8, kGuideHid)) = *(const uint4 *)(b + 8);
-                }
-                umma::fence_proxy_async();
-                umma::fence_before_sync();
-                group_sync(bar_id);
+            if (gtid == 0) {
+                const uint32_t b0 = sbase + (l == 1 ? kMlpW2 : (l == 2 ? kMlpW3 : (l == 3 ? kMlpW4 : kMlpW5)));
+                mlp_issue(taddr, bbase, b0, kGuideHid, l == 4 ? kGuideOutPad : kGuideHid, bar);
             }
-            if (!ok) break;
-            if (gtid == 0) mlp_issue(taddr, gbase + kMiH, sbase + kMlpW5, kGuideHid, kGuideOutPad, bar);
             if (!(ok = wait_layer())) break;
-            umma::fence_after_sync();
-            // outputs 0..39: half 0 columns 0..31, half 1 columns 32..39
-#pragma unroll
-            for (uint32_t c = 0; c < 2; ++c) {
-                if (half == 1 && c == 1) break;
-                const uint32_t c0 = 32u * half + 16u * c;
-                float v[16];
-                umma::tmem_ld16(lane_addr + c0, v);
-                if (row < n) {
-                    float4 *dst = (float4 *)(out + (size_t)row * kGuideOut + c0);
-                    const int nv = c0 + 16 <= (uint32_t)kGuideOut ? 4 : 2;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (e < nv) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
-                }
-            }
-            // the accumulator, X and H are reused by the next tile
-            umma::fence_before_sync();
-            group_sync(bar_id);
         }
+        if (!ok) break;
+        umma::fence_after_sync();
+        // outputs 0..39
+#pragma unroll 1
+        for (uint32_t c0 = 0; c0 < (uint32_t)kGuideOutPad; c0 += 16) {
+            float v[16];
+            umma::tmem_ld16(lane_addr + c0, v);
+            if (row < n) {
+                float4 *dst = (float4 *)(out + (size_t)row * kGuideOut + c0);
+                const int nv = c0 + 16 <= (uint32_t)kGuideOut ? 4 : 2;
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (e < nv) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+            }
+        }
+        // the accumulator and the buffer are reused by the next tile
+        umma::fence_before_sync();
+        group_sync(bar_id);
     }
     if (!ok && gtid == 0) {
-        // the layer in flight may still complete: wait for it once more
+        // the product in flight may still complete: wait for it once more
         // (bounded) before the tensor memory is released
         umma::mbar_wait(bar, phase ^ 1u);
         atomicExch(err, 1u);
@@ -420,7 +418,7 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, float
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
-    if (warp == 0) umma::tmem_dealloc(*s_taddr, 128);
+    if (warp == 0) umma::tmem_dealloc(*s_taddr, 256);
 }
 
 }  // namespace rtg
