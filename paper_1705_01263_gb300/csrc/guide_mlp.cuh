@@ -293,6 +293,16 @@ __device__ __forceinline__ bool group_all(uint32_t id, bool pred) {
     return r != 0;
 }
 
+// Two floats to a packed BF16 pair (round to nearest even), the first in the
+// low half; with kRelu, negative values become zero (one instruction).
+template <bool kRelu>
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t d;
+    if (kRelu) asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    else asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
 // Layer-1 product over one K half: D (+)= A[128 x 112] * W1[:, k0 .. k0 + 111]^T.
 __device__ __forceinline__ void mlp_issue_half(uint32_t taddr, uint32_t a0, uint32_t w1, uint32_t half, uint64_t *bar) {
     const uint32_t idesc = umma::make_idesc_bf16(kMlpTile, kGuideHid);
@@ -347,10 +357,9 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, float
             const uint32_t col = c0 + 8u * j;
             float g8[8];
             oneblob_chunk(f[col / kGuideBins], (int)(col % kGuideBins), g8);
-            __align__(16) __nv_bfloat16 b[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) b[e] = __float2bfloat16(g8[e]);
-            *(uint4 *)(buf + umma::kmajor_offset(r, 8u * j, kMiHalfK)) = *(const uint4 *)b;
+            *(uint4 *)(buf + umma::kmajor_offset(r, 8u * j, kMiHalfK)) =
+                make_uint4(pack_bf16x2<false>(g8[0], g8[1]), pack_bf16x2<false>(g8[2], g8[3]),
+                           pack_bf16x2<false>(g8[4], g8[5]), pack_bf16x2<false>(g8[6], g8[7]));
         }
         umma::fence_proxy_async();
         umma::fence_before_sync();
@@ -375,11 +384,12 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, float
             for (uint32_t c0 = 0; c0 < (uint32_t)kGuideHid; c0 += 16) {
                 float v[16];
                 umma::tmem_ld16(lane_addr + c0, v);
-                __align__(16) __nv_bfloat16 b[16];
-#pragma unroll
-                for (int e = 0; e < 16; ++e) b[e] = __float2bfloat16(fmaxf(v[e], 0.f));
-                *(uint4 *)(buf + umma::kmajor_offset(r, c0, kGuideHid)) = *(const uint4 *)b;
-                *(uint4 *)(buf + umma::kmajor_offset(r, c0 + 8, kGuideHid)) = *(const uint4 *)(b + 8);
+                *(uint4 *)(buf + umma::kmajor_offset(r, c0, kGuideHid)) =
+                    make_uint4(pack_bf16x2<true>(v[0], v[1]), pack_bf16x2<true>(v[2], v[3]),
+                               pack_bf16x2<true>(v[4], v[5]), pack_bf16x2<true>(v[6], v[7]));
+                *(uint4 *)(buf + umma::kmajor_offset(r, c0 + 8, kGuideHid)) =
+                    make_uint4(pack_bf16x2<true>(v[8], v[9]), pack_bf16x2<true>(v[10], v[11]),
+                               pack_bf16x2<true>(v[12], v[13]), pack_bf16x2<true>(v[14], v[15]));
             }
             umma::fence_proxy_async();
             umma::fence_before_sync();
