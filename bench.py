@@ -297,11 +297,32 @@ def batched(spp_divisor=16):
     ev1.record()
     ev1.synchronize()
     ms = ev0.elapsed_time(ev1)
+    # the same batch with a guiding network on every 8th job (each trained
+    # from scratch during the call, rendered through the guided path)
+    for f in films:
+        f.clear()
+    guides = [rt.Guide(s, seed=7 + k) if k % 8 == 0 else None for k, (s, _, _, _, _) in enumerate(jobs)]
+    gjobs = [j + (g,) for j, g in zip(jobs, guides)]
+    go = rt.make_opts(tail_threshold=o.tail_threshold, trace_kernel=o.trace_kernel)
+    gst = rt.rt_stats()
+    go.stats = C_pointer(gst)
+    torch.cuda.synchronize()
+    ev0.record()
+    rt.rt_render_batch(gjobs, go)
+    ev1.record()
+    ev1.synchronize()
+    gms = ev0.elapsed_time(ev1)
+    for g in guides:
+        if g is not None:
+            g.close()
     return {"workload": f"64 seeded scenes ({sum(sd.num_triangles for sd, _, _, _ in specs)} triangles in all), "
                         f"spp / {spp_divisor}, one batched wavefront replayed as a CUDA graph",
             "paths": st.paths, "Mpaths_per_s": st.paths / ms / 1e3,
             "Mrays_per_s": (st.extension_rays + st.shadow_rays) / ms / 1e3, "ms": ms,
-            "graph_replays": st.waves, "autotuned_pool": o.max_paths_in_flight, "scene_setup_s": setup_s}
+            "graph_replays": st.waves, "autotuned_pool": o.max_paths_in_flight, "scene_setup_s": setup_s,
+            "with_guides": {"guided_jobs": sum(g is not None for g in guides), "ms": gms,
+                            "Mpaths_per_s": gst.paths / gms / 1e3,
+                            "note": "guided jobs rendered after the shared wavefront, each with its own network"}}
 
 
 def traversal_only(sd, cam, scene, n=1 << 22, reps=5):

@@ -269,20 +269,26 @@ rt_status rt_render_static(const rt_scene *scene, const rt_camera *camera, uint3
  * accumulates iterations [film next, + spp) into its own film (FP64 atomic
  * additions: equal to rt_render up to FP64 addition order). Blocking;
  * RT_TIMEOUT when the abort flag or time budget stopped it between sets
- * (films hold the completed tasks). Guiding is per rt_render call. */
+ * (films hold the completed tasks). A job may carry its own guiding network
+ * (`guide`, or NULL): such jobs are rendered inside the call after the
+ * shared wavefront, one after another through the guided path (each needs its
+ * own network in its inference and training launches); opts->guide must be
+ * NULL. */
 typedef struct {
     const rt_scene *scene;
     rt_camera camera;
     uint32_t spp;
     uint32_t max_depth;
     rt_film *film;
+    rt_guide *guide;       /* this job's guiding network, or NULL */
 } rt_render_job;
 rt_status rt_render_batch(const rt_render_job *jobs, int32_t njobs, const rt_render_opts *opts, void *stream);
 
 /* Autotuner (not in the paper): renders `sample_spp` of each job with every
  * candidate of path-pool capacity, tail threshold and traversal variant and
  * writes the fastest into *opts (max_paths_in_flight, tail_threshold,
- * trace_kernel). The films receive those samples; callers clear them. */
+ * trace_kernel). The films receive those samples; callers clear them. Jobs
+ * with a guide are rejected (RT_NOT_SUPPORTED). */
 rt_status rt_autotune(const rt_render_job *jobs, int32_t njobs, uint32_t sample_spp, rt_render_opts *opts,
                       void *stream);
 

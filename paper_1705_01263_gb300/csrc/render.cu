@@ -1916,12 +1916,51 @@ __global__ void k_batch_advance(BatchCtl *bc) { bc->t0 += bc->n; }
 
 }  // namespace rtg
 
+static rt_status render_batch_shared(const rt_render_job *jobs, int32_t njobs, const rt_render_opts *opts_in,
+                                     void *stream);
+
 extern "C" rt_status rt_render_batch(const rt_render_job *jobs, int32_t njobs, const rt_render_opts *opts_in,
                                      void *stream) {
     if (!jobs || njobs <= 0) { set_error("rt_render_batch: no jobs"); return RT_INVALID_ARG; }
+    if (opts_in && opts_in->guide) {
+        set_error("rt_render_batch: guiding networks go with the jobs (rt_render_job.guide)");
+        return RT_NOT_SUPPORTED;
+    }
+    std::vector<rt_render_job> shared, guided;
+    for (int32_t j = 0; j < njobs; ++j) (jobs[j].guide ? guided : shared).push_back(jobs[j]);
+    rt_status rs = RT_OK;
+    if (!shared.empty()) rs = render_batch_shared(shared.data(), (int32_t)shared.size(), opts_in, stream);
+    if (rs != RT_OK) return rs;
+    // guided jobs: one guided render each (their networks differ)
     rt_render_opts o{};
     if (opts_in) o = *opts_in;
-    if (o.guide) { set_error("rt_render_batch: guiding is per rt_render call"); return RT_NOT_SUPPORTED; }
+    rt_stats total{};
+    rt_stats *user_stats = o.stats;
+    if (user_stats && !shared.empty()) total = *user_stats;
+    for (const rt_render_job &J : guided) {
+        rt_render_opts oj = o;
+        rt_stats sj{};
+        oj.guide = J.guide;
+        oj.stats = user_stats ? &sj : nullptr;
+        rs = rt_render(J.scene, &J.camera, J.spp, J.max_depth, J.film, &oj, stream);
+        if (user_stats) {
+            total.paths += sj.paths;
+            total.extension_rays += sj.extension_rays;
+            total.shadow_rays += sj.shadow_rays;
+            total.waves += sj.waves;
+            total.wavefront_steps += sj.wavefront_steps;
+            total.kernel_launches += sj.kernel_launches;
+        }
+        if (rs != RT_OK) break;
+    }
+    if (user_stats && !guided.empty()) *user_stats = total;
+    return rs;
+}
+
+static rt_status render_batch_shared(const rt_render_job *jobs, int32_t njobs, const rt_render_opts *opts_in,
+                                     void *stream) {
+    rt_render_opts o{};
+    if (opts_in) o = *opts_in;
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<BatchJob> hj((size_t)njobs);
     uint64_t total = 0;
@@ -2061,6 +2100,8 @@ extern "C" rt_status rt_render_batch(const rt_render_job *jobs, int32_t njobs, c
 extern "C" rt_status rt_autotune(const rt_render_job *jobs, int32_t njobs, uint32_t sample_spp, rt_render_opts *opts,
                                  void *stream) {
     if (!jobs || njobs <= 0 || !opts || sample_spp == 0) { set_error("rt_autotune: invalid argument"); return RT_INVALID_ARG; }
+    for (int32_t j = 0; j < njobs; ++j)
+        if (jobs[j].guide) { set_error("rt_autotune: jobs with a guiding network are not tuned"); return RT_NOT_SUPPORTED; }
     cudaStream_t st = (cudaStream_t)stream;
     struct Cand { uint32_t cap, tail; int32_t tk; };
     std::vector<Cand> cands;

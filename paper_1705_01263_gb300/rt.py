@@ -76,7 +76,7 @@ class rt_render_opts(C.Structure):
 
 class rt_render_job(C.Structure):
     _fields_ = [("scene", C.c_void_p), ("camera", rt_camera), ("spp", C.c_uint32), ("max_depth", C.c_uint32),
-                ("film", C.c_void_p)]
+                ("film", C.c_void_p), ("guide", C.c_void_p)]
 
 
 class rt_guide_opts(C.Structure):
@@ -398,10 +398,13 @@ def rt_render(scene: Scene, cam, spp: int, max_depth: int, film: Film, opts: Opt
 
 
 def _jobs(jobs):
-    """jobs: list of (Scene, camera, spp, max_depth, Film)."""
+    """jobs: list of (Scene, camera, spp, max_depth, Film[, Guide or None])."""
     arr = (rt_render_job * len(jobs))()
-    for k, (sc, cam, spp, depth, film) in enumerate(jobs):
+    for k, job in enumerate(jobs):
+        sc, cam, spp, depth, film = job[:5]
+        guide = job[5] if len(job) > 5 else None
         arr[k].scene, arr[k].camera, arr[k].spp, arr[k].max_depth, arr[k].film = sc.handle, make_camera(cam), spp, depth, film.handle
+        arr[k].guide = guide.handle if guide is not None else None
     return arr
 
 

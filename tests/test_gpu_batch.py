@@ -94,3 +94,42 @@ def test_autotune_picks_a_candidate_and_renders():
     torch.cuda.synchronize()
     for f, (_, _, spp, _) in zip(films, jobs):
         assert np.all(f.download()[2] == spp)
+
+
+def test_batch_with_per_job_guides():
+    """Jobs carrying their own guiding network: each is rendered with its
+    network (which trains during the call) and converges to the oracle's
+    reference; the jobs without one equal their individual renders."""
+    from paper_1705_01263_gb300 import rt
+    from helpers import allowed_4sigma
+    jobs = make_jobs()
+    ref = individual(jobs)
+    sd, cam = scenes.cornell_box()
+    cscene = rt.Scene(sd)
+    guides = [rt.Guide(cscene, seed=5), rt.Guide(cscene, seed=6)]
+    p0 = [g.get_params() for g in guides]
+    gfilms = [rt.Film(cam.width, cam.height) for _ in guides]
+    films = [rt.Film(c.width, c.height) for _, c, _, _ in jobs]
+    spec = [(s, c, spp, d, f) for (s, c, spp, d), f in zip(jobs, films)]
+    spec += [(cscene, cam, 1024, 8, f, g) for f, g in zip(gfilms, guides)]
+    stats = rt.rt_stats()
+    rt.rt_render_batch(spec, rt.make_opts(stats=stats))
+    torch.cuda.synchronize()
+    total = sum(c.width * c.height * spp for _, c, spp, _ in jobs) + 2 * cam.width * cam.height * 1024
+    assert stats.paths == total
+    for (s_ref, s2_ref, c_ref), f in zip(ref, films):
+        s, s2, c = f.download()
+        assert np.array_equal(c, c_ref)
+        assert np.allclose(s, s_ref, rtol=1e-5, atol=1e-9)
+    import os
+    d = np.load(os.path.join(os.path.dirname(__file__), "golden", "cornell_64_depth8_ref.npz"))
+    mr, vr = d["mean"], d["var"]   # FP64 oracle, 2^15 spp from iteration 2^20
+    for g, q0, f in zip(guides, p0, gfilms):
+        assert not np.array_equal(q0, g.get_params())
+        s, s2, c = f.download()
+        assert np.all(c == 1024)
+        mg, vg = oracle.resolve(s, s2, c)
+        out = int((np.abs(mg - mr) > 4 * np.sqrt(vg + vr) + 1e-6).sum())
+        assert out <= allowed_4sigma(mg.size), out
+    with pytest.raises(rt.RtError):
+        rt.rt_autotune(spec, 1)
