@@ -26,7 +26,8 @@ struct GemmArgs {
     int M, N, K, lda, ldb, ldc;
     int k_split;        // K elements per split (multiple of 64)
     int nt;             // N columns per CTA (multiple of 16, <= 256)
-    int mode;           // 0 store, 1 atomic add, 2 ReLU backward (below)
+    int mode;           // 0 store, 1 atomic add, 2 ReLU backward (below), 3 partial of split blockIdx.z
+    float *part;        // mode 3: partial sums, split z at part + z * M * N (row-major, ld N)
     uint32_t *err;      // set to 1 if a tensor-core wait timed out
     // mode 2: instead of C, dY = bf16(C * (H > 0)) row-major [M][N] (ld N)
     // and its transpose dYT [N][ldt], H BF16 row-major [M][N]
@@ -112,7 +113,22 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(GemmArgs g) {
         for (int c0 = 0; c0 < g.nt; c0 += 16) {
             float v[16];
             umma::tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (row < g.M && g.mode == 2) {
+            if (row < g.M && g.mode == 2 && (g.N % 16) == 0 && n0 + c0 + 16 <= g.N) {
+                // whole 16-column chunk: the row's 32 bytes of H and dY in
+                // two 16-byte accesses, dYT column by column (coalesced over
+                // the warp's consecutive rows)
+                const size_t i0 = (size_t)row * g.N + n0 + c0;
+                const uint4 h0 = *(const uint4 *)(g.H + i0), h1 = *(const uint4 *)(g.H + i0 + 8);
+                __align__(16) __nv_bfloat16 hb[16], b[16];
+                *(uint4 *)hb = h0;
+                *(uint4 *)(hb + 8) = h1;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) b[j] = __float2bfloat16(__bfloat162float(hb[j]) > 0.f ? v[j] : 0.f);
+                *(uint4 *)(g.dY + i0) = *(const uint4 *)b;
+                *(uint4 *)(g.dY + i0 + 8) = *(const uint4 *)(b + 8);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) g.dYT[(size_t)(n0 + c0 + j) * g.ldt + row] = b[j];
+            } else if (row < g.M && g.mode == 2) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int col = n0 + c0 + j;
@@ -121,6 +137,19 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(GemmArgs g) {
                         const __nv_bfloat16 b = __float2bfloat16(__bfloat162float(g.H[i]) > 0.f ? v[j] : 0.f);
                         g.dY[i] = b;
                         g.dYT[(size_t)col * g.ldt + row] = b;
+                    }
+                }
+            } else if (row < g.M && g.mode == 3) {
+                float *dst = g.part + (size_t)blockIdx.z * g.M * g.N + (size_t)row * g.N;
+                if ((g.N % 4) == 0 && n0 + c0 + 16 <= g.N) {
+                    float4 *d4 = (float4 *)(dst + n0 + c0);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) d4[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = n0 + c0 + j;
+                        if (col < g.N) dst[col] = v[j];
                     }
                 }
             } else if (row < g.M) {
@@ -139,6 +168,40 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(GemmArgs g) {
     umma::fence_before_sync();
     __syncthreads();
     if (warp == 0) umma::tmem_dealloc(taddr, ncols);
+}
+
+// C (+)= the sum of the splits' partial products (one thread per element).
+__global__ void k_sum_splits(const float *part, int splits, int M, int N, float *C, int ldc, int accumulate) {
+    const int64_t n = (int64_t)M * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int z = 0; z < splits; ++z) acc += part[(size_t)z * n + i];
+        float *dst = C + (i / N) * ldc + (i % N);
+        *dst = accumulate ? *dst + acc : acc;
+    }
+}
+
+// Partial-sum workspace of the split-K products, one per device, grown on
+// demand and kept for the life of the process (like a GEMM library's
+// workspace).
+static float *split_workspace(size_t floats, rt_status &st) {
+    static float *buf[64] = {nullptr};
+    static size_t cap[64] = {0};
+    int dev = 0;
+    st = RT_OK;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { st = RT_CUDA_ERROR; return nullptr; }
+    if (cap[dev] < floats) {
+        if (buf[dev]) cudaFree(buf[dev]);
+        buf[dev] = nullptr;
+        cap[dev] = 0;
+        if (cudaMalloc(&buf[dev], floats * sizeof(float)) != cudaSuccess) {
+            set_error("gemm_bf16: split-K workspace allocation failed");
+            st = RT_OOM;
+            return nullptr;
+        }
+        cap[dev] = floats;
+    }
+    return buf[dev];
 }
 
 static rt_status gemm_launch(GemmArgs g, int accumulate, bool relu_bwd, cudaStream_t st) {
@@ -165,18 +228,30 @@ static rt_status gemm_launch(GemmArgs g, int accumulate, bool relu_bwd, cudaStre
         splits = std::min((K + kGemmKChunk - 1) / kGemmKChunk, (2 * 152 + ctas - 1) / ctas);
     g.k_split = ((K + splits - 1) / splits + kGemmKChunk - 1) / kGemmKChunk * kGemmKChunk;
     splits = (K + g.k_split - 1) / g.k_split;
-    g.mode = relu_bwd ? 2 : ((splits > 1 || accumulate) ? 1 : 0);
-    if (g.mode == 1 && !accumulate) RT_CUDA_TRY(cudaMemsetAsync(g.C, 0, sizeof(float) * ((size_t)(M - 1) * g.ldc + N), st));
+    // split K: each split stores its partial product and one pass sums them
+    // (no atomics on the same addresses from every split)
+    g.mode = relu_bwd ? 2 : (splits > 1 ? 3 : (accumulate ? 1 : 0));
+    if (g.mode == 3) {
+        rt_status ws;
+        g.part = split_workspace((size_t)splits * M * N, ws);
+        if (ws != RT_OK) return ws;
+    }
     dim3 grid(mt, ntiles, splits);
     const uint32_t ncols = g.nt <= 32 ? 32u : (g.nt <= 64 ? 64u : (g.nt <= 128 ? 128u : 256u));
     k_gemm_bf16<<<grid, 128, gemm_smem(g.nt, ncols), st>>>(g);
     RT_CUDA_TRY(cudaGetLastError());
+    if (g.mode == 3) {
+        const int64_t n = (int64_t)M * N;
+        const int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
+        k_sum_splits<<<blocks, 256, 0, st>>>(g.part, splits, M, N, g.C, g.ldc, accumulate);
+        RT_CUDA_TRY(cudaGetLastError());
+    }
     return RT_OK;
 }
 
 rt_status gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *C, int M, int N, int K, int lda, int ldb,
                     int ldc, int accumulate, uint32_t *err, cudaStream_t st) {
-    GemmArgs g{A, B, C, M, N, K, lda, ldb, ldc, 0, 0, 0, err, nullptr, nullptr, nullptr, 0};
+    GemmArgs g{A, B, C, M, N, K, lda, ldb, ldc, 0, 0, 0, nullptr, err, nullptr, nullptr, nullptr, 0};
     return gemm_launch(g, accumulate, false, st);
 }
 
@@ -185,7 +260,7 @@ rt_status gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *C, in
 rt_status gemm_bf16_relu_bwd(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int lda, int ldb,
                              const __nv_bfloat16 *H, __nv_bfloat16 *dY, __nv_bfloat16 *dYT, int64_t ldt, uint32_t *err,
                              cudaStream_t st) {
-    GemmArgs g{A, B, nullptr, M, N, K, lda, ldb, N, 0, 0, 0, err, H, dY, dYT, ldt};
+    GemmArgs g{A, B, nullptr, M, N, K, lda, ldb, N, 0, 0, 0, nullptr, err, H, dY, dYT, ldt};
     return gemm_launch(g, 0, true, st);
 }
 

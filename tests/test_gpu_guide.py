@@ -137,3 +137,20 @@ def test_training_lowers_loss_and_checkpoint_roundtrip():
     other.load(blob)
     out_b = other.infer(f[:256]).cpu().numpy()
     assert np.array_equal(out_a, out_b)
+
+
+def test_gemm_split_k_accumulate_into_strided_c():
+    """K long enough to be split across CTAs (partial products summed in a
+    second pass), accumulating into a column slice of a wider C."""
+    from paper_1705_01263_gb300 import rt
+    g = torch.Generator().manual_seed(5)
+    A = torch.randn(64, 8192, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(48, 8192, generator=g).to(torch.bfloat16).cuda()
+    big = torch.full((64, 80), 2.0, device="cuda")
+    C = big[:, 16:64]
+    rt.rt_gemm_bf16(A, B, C, accumulate=True)
+    torch.cuda.synchronize()
+    ref = 2.0 + A.double().cpu() @ B.double().cpu().T
+    scale = (A.double().cpu().abs() @ B.double().cpu().abs().T).max().item()
+    assert (C.cpu().double() - ref).abs().max().item() <= 1e-5 * scale + 1e-4
+    assert torch.all(big[:, :16] == 2.0) and torch.all(big[:, 64:] == 2.0)
