@@ -8,6 +8,8 @@
 // softmax(logits).
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace rtg {
@@ -72,16 +74,23 @@ struct Mixture {
     float c[kGuideLobes];   // w kappa / (2 pi (1 - e^{-2 kappa})): the weighted lobe's normalisation
 };
 
-RT_HD void decode_mixture(const float *raw, Mixture &m) {
+RT_HD float raw_value(float v) { return v; }
+RT_HD float raw_value(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Raw outputs in FP32 (training, the API) or BF16 (the rows the guided
+// render writes and reads back).
+template <class T>
+RT_HD void decode_mixture(const T *raw, Mixture &m) {
     float mx = -INFINITY;
-    for (int k = 0; k < kGuideLobes; ++k) mx = fmaxf(mx, raw[5 * k + 4]);
+    for (int k = 0; k < kGuideLobes; ++k) mx = fmaxf(mx, raw_value(raw[5 * k + 4]));
     float z = 0.f;
     for (int k = 0; k < kGuideLobes; ++k) {
-        const float *r = raw + 5 * k;
+        const T *rr = raw + 5 * k;
+        const float r[4] = {raw_value(rr[0]), raw_value(rr[1]), raw_value(rr[2]), raw_value(rr[3])};
         float l = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
         m.mu[k] = l > 0.f ? v3(r[0] / l, r[1] / l, r[2] / l) : v3(0.f, 0.f, 1.f);
         m.kappa[k] = fminf(kKappaMax, fmaxf(kKappaMin, softplusf(r[3])));
-        m.w[k] = expf(r[4] - mx);
+        m.w[k] = expf(raw_value(rr[4]) - mx);
         z += m.w[k];
     }
     for (int k = 0; k < kGuideLobes; ++k) {

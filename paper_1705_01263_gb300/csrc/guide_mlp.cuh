@@ -317,8 +317,10 @@ __device__ __forceinline__ void mlp_issue_half(uint32_t taddr, uint32_t a0, uint
     umma::mma_commit(bar);
 }
 
-template <class Features>
-__device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, float *out, uint32_t *err) {
+// Out: float (the API's n x 40 rows) or __nv_bfloat16 (the guided render's
+// rows, 80 bytes each).
+template <class Out, class Features>
+__device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, Out *out, uint32_t *err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
     const uint32_t g = warp >> 2, quarter = warp & 3u, gtid = tid & 127u;
@@ -408,11 +410,20 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, float
             float v[16];
             umma::tmem_ld16(lane_addr + c0, v);
             if (row < n) {
-                float4 *dst = (float4 *)(out + (size_t)row * kGuideOut + c0);
-                const int nv = c0 + 16 <= (uint32_t)kGuideOut ? 4 : 2;
+                const int nv = c0 + 16 <= (uint32_t)kGuideOut ? 4 : 2;   // groups of four columns
+                if constexpr (sizeof(Out) == 4) {
+                    float4 *dst = (float4 *)(out + (size_t)row * kGuideOut + c0);
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (e < nv) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+                    for (int e = 0; e < 4; ++e)
+                        if (e < nv) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+                } else {
+                    uint2 *dst = (uint2 *)(out + (size_t)row * kGuideOut + c0);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (e < nv)
+                            dst[e] = make_uint2(pack_bf16x2<false>(v[4 * e], v[4 * e + 1]),
+                                                pack_bf16x2<false>(v[4 * e + 2], v[4 * e + 3]));
+                }
             }
         }
         // the accumulator and the buffer are reused by the next tile

@@ -736,7 +736,8 @@ struct PathFeatures {
     }
 };
 
-__global__ void __launch_bounds__(512, 1) k_guide_mlp_paths(MlpWeights w, PathFeatures pf, float *raw, uint32_t *err) {
+__global__ void __launch_bounds__(512, 1) k_guide_mlp_paths(MlpWeights w, PathFeatures pf, __nv_bfloat16 *raw,
+                                                            uint32_t *err) {
     mlp_infer_tiles(w, pf, raw, err);
 }
 
@@ -750,7 +751,7 @@ __device__ __forceinline__ bool recording_path(uint32_t q, uint32_t rec_stride, 
     return q % rec_stride == 0u && q / rec_stride < batch;
 }
 
-__global__ void __launch_bounds__(128) k_shade_guided(RenderParams P, Pool pool, const float *raw, float alpha,
+__global__ void __launch_bounds__(128) k_shade_guided(RenderParams P, Pool pool, const __nv_bfloat16 *raw, float alpha,
                                                       float4 *rec, uint32_t rec_stride, uint32_t batch, float3 lo,
                                                       float3 hi) {
     Ctrl *c = pool.ctrl;
@@ -995,7 +996,7 @@ struct RenderCache {
     uint32_t sort_cap = 0, sort_nkeys = 0;
     // guided rendering
     uint32_t gcap = 0, gbatch = 0;
-    float *gfeat = nullptr;   // network outputs [cap][48] of one bounce step
+    __nv_bfloat16 *gfeat = nullptr;   // network outputs [cap][40] (BF16) of one bounce step
     float *tr_feat = nullptr, *tr_wi = nullptr, *tr_w = nullptr;
     float4 *grec = nullptr;
     uint32_t *gnrec = nullptr;
@@ -1013,10 +1014,11 @@ static rt_status ensure_guided(RenderCache *rc, uint32_t cap, uint32_t batch) {
     for (void *p : {(void *)rc->gfeat, (void *)rc->tr_feat, (void *)rc->tr_wi, (void *)rc->tr_w, (void *)rc->grec,
                     (void *)rc->gnrec})
         if (p) cudaFree(p);
-    rc->gfeat = rc->tr_feat = rc->tr_wi = rc->tr_w = nullptr;
+    rc->gfeat = nullptr;
+    rc->tr_feat = rc->tr_wi = rc->tr_w = nullptr;
     rc->grec = nullptr;
     rc->gnrec = nullptr;
-    if (cudaMalloc(&rc->gfeat, (size_t)cap * kGuideOut * 4) != cudaSuccess ||
+    if (cudaMalloc(&rc->gfeat, (size_t)cap * kGuideOut * sizeof(__nv_bfloat16)) != cudaSuccess ||
         cudaMalloc(&rc->grec, (size_t)std::min(cap, batch) * kGuideMaxRec * 4 * sizeof(float4)) != cudaSuccess ||
         cudaMalloc(&rc->gnrec, (size_t)cap * 4) != cudaSuccess ||
         cudaMalloc(&rc->tr_feat, (size_t)batch * 7 * 4) != cudaSuccess ||

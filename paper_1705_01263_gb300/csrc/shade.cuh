@@ -679,7 +679,7 @@ RT_HD NeePick nee_pick(const RenderParams &P, uint64_t index, int base) {
 // holds a shadow ray (see shade()).
 template <bool kLb = true>
 RT_HD int scatter(const RenderParams &P, PathState &s, const Vertex &vx, const Material &m, bool nee,
-                  const NeePick &pk, ShadowRay &sh, const float *graw, float alpha, GuideRecord *rec, float3 glo,
+                  const NeePick &pk, ShadowRay &sh, const __nv_bfloat16 *graw, float alpha, GuideRecord *rec, float3 glo,
                   float3 ghi) {
     const DevScene &sc = P.sc;
     const int mode = P.mis_mode;
@@ -813,12 +813,12 @@ RT_HD int scatter(const RenderParams &P, PathState &s, const Vertex &vx, const M
 // Shade the hit of the pending ray of `s`. Returns bit 0 when the path
 // continues (new pending ray in s.o, s.d) and bit 1 when `sh` holds a shadow
 // ray whose unoccluded contribution must be added to s.L. With `graw` (the
-// guiding network's 40 outputs for this vertex) the continuation is drawn
+// guiding network's 40 outputs for this vertex, BF16) the continuation is drawn
 // from the one-sample MIS mixture alpha * vMF-mixture + (1 - alpha) * BSDF
 // and every pdf used for MIS is that mixture's; with `rec` the vertex's
 // training record is filled when the path continues.
 template <bool kLb = true>
-RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh, const float *graw = nullptr,
+RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh, const __nv_bfloat16 *graw = nullptr,
                 float alpha = 0.f, GuideRecord *rec = nullptr, float3 glo = float3{0.f, 0.f, 0.f},
                 float3 ghi = float3{1.f, 1.f, 1.f}) {
     const DevScene &sc = P.sc;
