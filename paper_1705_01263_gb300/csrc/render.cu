@@ -751,7 +751,7 @@ __device__ __forceinline__ bool recording_path(uint32_t q, uint32_t rec_stride, 
     return q % rec_stride == 0u && q / rec_stride < batch;
 }
 
-__global__ void __launch_bounds__(128) k_shade_guided(RenderParams P, Pool pool, const __nv_bfloat16 *raw, float alpha,
+__global__ void __launch_bounds__(128, 6) k_shade_guided(RenderParams P, Pool pool, const __nv_bfloat16 *raw, float alpha,
                                                       float4 *rec, uint32_t rec_stride, uint32_t batch, float3 lo,
                                                       float3 hi) {
     Ctrl *c = pool.ctrl;
