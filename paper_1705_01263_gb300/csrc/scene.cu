@@ -106,7 +106,7 @@ struct EnvNormalTables {
     std::vector<float> nw, scale, fac;
 };
 
-// Per normal cell: level lstar = the finest of the top kEnvNormalLevels
+// Per normal cell: level lstar = the finest of the top kLevels (five)
 // levels holds w(R) x kappa_c(R), kappa the clamped cosine at the smallest
 // angle between a normal of the cell's cone and a direction of region R's
 // cone (1 where the cones overlap, 0 beyond 90 degrees); coarser levels are

@@ -377,9 +377,7 @@ RT_HD V3 env_sample(const DevScene &sc, float u, float v) {
 // cosine between the cell's normals and the region's directions, the coarser
 // ones are sums. A descent for a vertex of cell c follows that copy down to
 // the finest reweighted level and the plain pyramid below it.
-constexpr int kEnvCellSide = 8;
-constexpr int kEnvCells = kEnvCellSide * kEnvCellSide;
-constexpr int kEnvNormalLevels = 5;
+constexpr int kEnvCellSide = 8;   // the scene's tables hold the top five levels for each of the 64 cells
 
 RT_HD uint32_t env_cell(V3 n) {
     float a = fabsf(n.x) + fabsf(n.y) + fabsf(n.z);
