@@ -303,7 +303,7 @@ def batched(spp_divisor=16):
         f.clear()
     guides = [rt.Guide(s, seed=7 + k) if k % 8 == 0 else None for k, (s, _, _, _, _) in enumerate(jobs)]
     gjobs = [j + (g,) for j, g in zip(jobs, guides)]
-    go = rt.make_opts(tail_threshold=o.tail_threshold, trace_kernel=o.trace_kernel)
+    go = rt.make_opts(tail_threshold=o.tail_threshold, trace_kernel=o.trace_kernel, block_size=o.block_size)
     gst = rt.rt_stats()
     go.stats = C_pointer(gst)
     torch.cuda.synchronize()
@@ -319,7 +319,8 @@ def batched(spp_divisor=16):
                         f"spp / {spp_divisor}, one batched wavefront replayed as a CUDA graph",
             "paths": st.paths, "Mpaths_per_s": st.paths / ms / 1e3,
             "Mrays_per_s": (st.extension_rays + st.shadow_rays) / ms / 1e3, "ms": ms,
-            "graph_replays": st.waves, "autotuned_pool": o.max_paths_in_flight, "scene_setup_s": setup_s,
+            "graph_replays": st.waves, "autotuned_pool": o.max_paths_in_flight, "autotuned_block": o.block_size,
+            "scene_setup_s": setup_s,
             "with_guides": {"guided_jobs": sum(g is not None for g in guides), "ms": gms,
                             "Mpaths_per_s": gst.paths / gms / 1e3,
                             "note": "guided jobs rendered after the shared wavefront, each with its own network"}}

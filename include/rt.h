@@ -155,7 +155,8 @@ typedef struct {
     int32_t megakernel_only; /* 1: one megakernel per iteration set (A/B baseline) */
     int32_t sort_by_material;/* 1: material-sorted shading queue */
     uint32_t tail_threshold; /* live paths below which the megakernel finishes a set (0 = auto) */
-    uint32_t block_size;     /* threads per block of the state kernels (0 = auto) */
+    uint32_t block_size;     /* threads per block of the state kernels: 0 (= 128) or a multiple of
+                              * 32 up to 128, else RT_INVALID_ARG; results do not depend on it */
     const volatile int32_t *abort_flag; /* host-mapped; nonzero -> stop between sets (A.4) */
     rt_guide *guide;         /* online path guiding (NULL = off) */
     rt_stats *stats;         /* optional host output */
@@ -285,9 +286,10 @@ typedef struct {
 rt_status rt_render_batch(const rt_render_job *jobs, int32_t njobs, const rt_render_opts *opts, void *stream);
 
 /* Autotuner (not in the paper): renders `sample_spp` of each job with every
- * candidate of path-pool capacity, tail threshold and traversal variant and
+ * candidate of path-pool capacity, tail threshold and traversal variant,
+ * then with 64, 96 and 128 threads per block at the best of those, and
  * writes the fastest into *opts (max_paths_in_flight, tail_threshold,
- * trace_kernel). The films receive those samples; callers clear them. Jobs
+ * trace_kernel, block_size). The films receive those samples; callers clear them. Jobs
  * with a guide are rejected (RT_NOT_SUPPORTED). */
 rt_status rt_autotune(const rt_render_job *jobs, int32_t njobs, uint32_t sample_spp, rt_render_opts *opts,
                       void *stream);

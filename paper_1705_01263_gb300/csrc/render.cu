@@ -921,6 +921,10 @@ inline TraceKernels trace_kernels(bool count, int variant, bool two_level, int b
     return count ? trace_kernels_of<true, false, false>(block) : trace_kernels_of<false, false, false>(block);
 }
 
+// Threads per block of the state kernels: 0 (128) or a multiple of 32 up to
+// the kernels' launch bound of 128.
+inline bool valid_block(uint32_t b) { return b == 0 || (b % 32 == 0 && b <= 128); }
+
 template <class K>
 int grid_for(K kernel, int block, int64_t work) {
     int per_sm = 0;
@@ -1148,6 +1152,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     if (opts_in) o = *opts_in;
     if (spp == 0) return RT_OK;
     if (o.trace_kernel < 0 || o.trace_kernel > 4) { set_error("rt_render: trace_kernel must be in [0, 4]"); return RT_INVALID_ARG; }
+    if (!valid_block(o.block_size)) { set_error("rt_render: block_size must be 0 or a multiple of 32 up to 128"); return RT_INVALID_ARG; }
     if (s->dev.two_level) o.trace_kernel = 0;   // the persistent variant is single-level only
     cudaStream_t st = (cudaStream_t)stream;
     RenderCache *rc = cache_of(film);
@@ -1287,7 +1292,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         if (o.stats) *o.stats = stats;
         return result;
     }
-    const int gb = 128;
+    const int gb = o.block_size ? (int)o.block_size : 128;
     const int g_ray = grid_for(k_raygen, 256, cap);
     const size_t smem = stack_smem(gb);
     const int g_trace = grid_persistent(k_trace_ext<false>, gb, smem);
@@ -1538,6 +1543,7 @@ extern "C" rt_status rt_render_probes(const rt_scene *s, const float *pos, const
     if (max_depth < 1 || max_depth > (uint32_t)kMaxDepth) { set_error("rt_render_probes: max_depth must be in [1, 64]"); return RT_INVALID_ARG; }
     rt_render_opts o{};
     if (opts_in) o = *opts_in;
+    if (!valid_block(o.block_size)) { set_error("rt_render_probes: block_size must be 0 or a multiple of 32 up to 128"); return RT_INVALID_ARG; }
     if (o.guide) { set_error("rt_render_probes: guiding needs rt_render"); return RT_NOT_SUPPORTED; }
     if (spp == 0) return RT_OK;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1574,7 +1580,7 @@ extern "C" rt_status rt_render_probes(const rt_scene *s, const float *pos, const
     P.rr = o.rr_enable;
     Pool pool = rc->pool.view;
     RT_CUDA_TRY(cudaMemsetAsync(pool.ctrl, 0, sizeof(Ctrl), st));
-    const int gb = 128;
+    const int gb = o.block_size ? (int)o.block_size : 128;
     const TraceKernels tk = trace_kernels(false, 0, s->dev.two_level, gb);
     const int g_start = grid_for(k_probe_start, 256, cap);
     const int g_shade = grid_persistent(k_shade<true>, gb, 0);
@@ -1643,6 +1649,7 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
     if (max_depth < 1 || max_depth > (uint32_t)kMaxDepth) { set_error("rt_render_static: max_depth must be in [1, 64]"); return RT_INVALID_ARG; }
     rt_render_opts o{};
     if (opts_in) o = *opts_in;
+    if (!valid_block(o.block_size)) { set_error("rt_render_static: block_size must be 0 or a multiple of 32 up to 128"); return RT_INVALID_ARG; }
     if (o.guide) { set_error("rt_render_static: guiding needs rt_render"); return RT_NOT_SUPPORTED; }
     if (o.max_paths_in_flight > kStaticMaxPaths) {
         set_error("rt_render_static: max_paths_in_flight exceeds the static pool of 65536 paths");
@@ -1687,7 +1694,7 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
     P.rr = o.rr_enable;
     const uint32_t tail = o.megakernel_only ? 0xFFFFFFFFu : (o.tail_threshold ? o.tail_threshold : 8192u);
     const uint64_t WH = (uint64_t)cam->width * cam->height;
-    const int gb = 128;
+    const int gb = o.block_size ? (int)o.block_size : 128;
     const size_t smem = stack_smem(gb);
     const int g_ray = grid_for(k_raygen, 256, cap);
     const int g_trace = grid_persistent(k_trace_ext<false>, gb, smem);
@@ -1963,6 +1970,7 @@ static rt_status render_batch_shared(const rt_render_job *jobs, int32_t njobs, c
                                      void *stream) {
     rt_render_opts o{};
     if (opts_in) o = *opts_in;
+    if (!valid_block(o.block_size)) { set_error("rt_render_batch: block_size must be 0 or a multiple of 32 up to 128"); return RT_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<BatchJob> hj((size_t)njobs);
     uint64_t total = 0;
@@ -2029,7 +2037,7 @@ static rt_status render_batch_shared(const rt_render_job *jobs, int32_t njobs, c
     if (rs != RT_OK) return rs;
     Pool pool = pa.view;
     RT_CUDA_TRY(cudaMemsetAsync(pool.ctrl, 0, sizeof(Ctrl), st));
-    const int gb = 128;
+    const int gb = o.block_size ? (int)o.block_size : 128;
     const int g_ray = grid_for(k_batch_raygen, 256, cap);
     const int g_trace = grid_persistent(k_batch_trace<false>, gb, 0);
     const int g_shade = grid_persistent(k_batch_shade, gb, 0);
@@ -2142,5 +2150,27 @@ extern "C" rt_status rt_autotune(const rt_render_job *jobs, int32_t njobs, uint3
     opts->max_paths_in_flight = pick.cap;
     opts->tail_threshold = pick.tail;
     opts->trace_kernel = pick.tk;
+    // then the block shape of the state kernels at those settings
+    uint32_t best_block = opts->block_size;
+    for (uint32_t b : {64u, 96u, 128u}) {
+        rt_render_opts o = *opts;
+        o.block_size = b;
+        o.stats = nullptr;
+        o.profile = 0;
+        RT_CUDA_TRY(cudaStreamSynchronize(st));
+        auto t0 = std::chrono::steady_clock::now();
+        rt_status s;
+        if (njobs == 1) s = rt_render(jobs[0].scene, &jobs[0].camera, sample_spp, jobs[0].max_depth, jobs[0].film, &o, stream);
+        else {
+            std::vector<rt_render_job> js(jobs, jobs + njobs);
+            for (auto &j : js) j.spp = sample_spp;
+            s = rt_render_batch(js.data(), njobs, &o, stream);
+        }
+        if (s != RT_OK) return s;
+        RT_CUDA_TRY(cudaStreamSynchronize(st));
+        double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (ms < best) { best = ms; best_block = b; }
+    }
+    opts->block_size = best_block;
     return RT_OK;
 }

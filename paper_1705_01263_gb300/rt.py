@@ -368,7 +368,7 @@ def make_camera(cam) -> rt_camera:
 def make_opts(sigma: float = 0.5, rr: bool = False, mis_mode: int = 0, seed: int = 0, time_budget_ms: float = 0.0,
               max_paths: int = 0, megakernel_only: bool = False, sort_by_material: bool = False,
               tail_threshold: int = 0, abort_flag=None, guide=None, stats: Optional[rt_stats] = None,
-              profile: int = 0, trace_kernel: int = 0, sort_rays: bool = False):
+              profile: int = 0, trace_kernel: int = 0, sort_rays: bool = False, block_size: int = 0):
     o = rt_render_opts()
     o.filter_sigma = sigma if sigma > 0 else -1.0
     o.rr_enable, o.mis_mode, o.seed = int(rr), mis_mode, seed
@@ -384,6 +384,7 @@ def make_opts(sigma: float = 0.5, rr: bool = False, mis_mode: int = 0, seed: int
     o.profile = profile
     o.trace_kernel = trace_kernel
     o.sort_rays = int(sort_rays)
+    o.block_size = block_size
     return o
 
 

@@ -86,6 +86,7 @@ def test_autotune_picks_a_candidate_and_renders():
     spec = [(s, cam, spp, d, f) for (s, cam, spp, d), f in zip(jobs, films)]
     o = rt.rt_autotune(spec, 1)
     assert o.max_paths_in_flight in (1 << 20, 1 << 21, 1 << 22, 1 << 23)
+    assert o.block_size in (0, 64, 96, 128)   # 0: none beat the first stage (128)
     o1 = rt.rt_autotune(spec[:1], 1)
     assert o1.trace_kernel in (0, 1) and o1.tail_threshold in (1, 8192, 65536)
     for f in films:
@@ -133,3 +134,21 @@ def test_batch_with_per_job_guides():
         assert out <= allowed_4sigma(mg.size), out
     with pytest.raises(rt.RtError):
         rt.rt_autotune(spec, 1)
+
+
+def test_block_size_changes_nothing_but_speed():
+    """rt_render_opts.block_size (64, 96 or 128 threads per block of the
+    state kernels) gives bit-identical films; other sizes are rejected."""
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.cornell_box()
+    s = rt.Scene(sd)
+    out = []
+    for b in (0, 64, 96):
+        f = rt.Film(cam.width, cam.height)
+        rt.rt_render(s, cam, 8, 8, f, rt.make_opts(block_size=b))
+        out.append(f.download())
+    for o in out[1:]:
+        assert all(np.array_equal(a, b) for a, b in zip(o, out[0]))
+    for bad in (48, 256):
+        with pytest.raises(rt.RtError):
+            rt.rt_render(s, cam, 1, 4, rt.Film(cam.width, cam.height), rt.make_opts(block_size=bad))
