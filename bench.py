@@ -267,6 +267,67 @@ def many_lights(spp=4, depth=12, ref_spp=128):
         del s
     h, a = out["light_hierarchy"], out["alias_table"]
     out["efficiency"] = (a["rmse"] ** 2 * a["ms"]) / (h["rmse"] ** 2 * h["ms"])
+    # direct light only (depth 1), where the choice of emitter is the whole
+    # of the next-event estimate: same comparison at 4 spp
+    direct, dref = {}, None
+    for name, bvh in (("light_hierarchy", True), ("alias_table", False)):
+        sd.light_bvh = bvh
+        s = rt.Scene(sd)
+
+        def run1(first, n):
+            film.clear()
+            film.seek(first)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rt.rt_render(s, cam, n, 1, film)
+            e1.record()
+            e1.synchronize()
+            return film.resolve()[0], e0.elapsed_time(e1)
+
+        if dref is None:
+            dref = run1(1 << 20, ref_spp)[0].clone()
+        run1(0, 1)
+        m, ms = run1(0, spp)
+        direct[name] = {"rmse": float((m - dref).double().pow(2).mean().sqrt()), "ms": ms}
+        del s
+    dh, da = direct["light_hierarchy"], direct["alias_table"]
+    direct["efficiency"] = (da["rmse"] ** 2 * da["ms"]) / (dh["rmse"] ** 2 * dh["ms"])
+    out["direct_only"] = direct
+    # irradiance probes (Sec. 4.2) among the instances, direct light only:
+    # no emitter is seen directly, so the error is the next-event
+    # estimate's alone
+    n_side, pspp = 64, 16
+    xs, zs = np.linspace(-26.0, 26.0, n_side), np.linspace(-43.0, 3.0, n_side)
+    X, Z = np.meshgrid(xs, zs)
+    pos = torch.from_numpy(np.stack([X.ravel(), np.full(X.size, 1.0), Z.ravel()], 1).astype(np.float32)).cuda()
+    nrm = torch.from_numpy(np.tile(np.array([[0.0, 1.0, 0.0]], np.float32), (X.size, 1))).cuda()
+    pfilm = rt.Film(X.size, 1)
+    probes_out, pref = {}, None
+    for name, bvh in (("light_hierarchy", True), ("alias_table", False)):
+        sd.light_bvh = bvh
+        s = rt.Scene(sd)
+
+        def runp(first, n):
+            pfilm.clear()
+            pfilm.seek(first)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rt.rt_render_probes(s, pos, nrm, n, 1, pfilm)
+            e1.record()
+            e1.synchronize()
+            return pfilm.resolve()[0], e0.elapsed_time(e1)
+
+        if pref is None:
+            pref = runp(1 << 20, 64 * pspp)[0].clone()
+        runp(0, 1)
+        m, ms = runp(0, pspp)
+        probes_out[name] = {"rmse": float((m - pref).double().pow(2).mean().sqrt()), "ms": ms}
+        del s
+    ph, pa = probes_out["light_hierarchy"], probes_out["alias_table"]
+    probes_out["efficiency"] = (pa["rmse"] ** 2 * pa["ms"]) / (ph["rmse"] ** 2 * ph["ms"])
+    probes_out["workload"] = f"{X.size} probes at height 1 among the instances, normals up, direct light, {pspp} spp"
+    out["probes_direct"] = probes_out
+    pfilm.close()
     out["bvh_nodes"], out["unique_tris"] = info["nodes"], info["leaf_tris"]
     film.close()
     return out
