@@ -213,7 +213,7 @@ extern "C" rt_status rt_debug_light_bvh_host(const rt_scene *s, const float *x, 
                                              int64_t n, uint32_t *emitter, float *p_sample, float *p_retraverse) {
     if (!s || !s->host_only || n < 0) { set_error("rt_debug_light_bvh_host: needs a host-only scene"); return RT_INVALID_ARG; }
     const DevScene &sc = s->host;
-    if (!sc.lb_nodes) { set_error("rt_debug_light_bvh_host: the scene has no light hierarchy"); return RT_INVALID_ARG; }
+    if (!sc.lb_rec) { set_error("rt_debug_light_bvh_host: the scene has no light hierarchy"); return RT_INVALID_ARG; }
     for (int64_t i = 0; i < n; ++i) {
         const V3 p = v3(x[3 * i], x[3 * i + 1], x[3 * i + 2]), nn = v3(nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]);
         float P;

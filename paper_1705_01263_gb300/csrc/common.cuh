@@ -74,15 +74,18 @@ struct DevScene {
     const uint32_t *light_tri; // emitter -> triangle id
     const uint32_t *light_inst;// emitter -> instance id (two-level scenes)
     const float4 *light_v;     // emitter -> three world-space vertices
-    // probabilistic light hierarchy (Sec. 2.1.1; null lb_nodes: the alias
-    // table picks emitters). Node i = lb_nodes[4i .. 4i+3]: (box centre, half
-    // diagonal), (I0..I3), (I4, I5, flux, 0) with I_k the directional value
-    // of cube-face region k (+x, -x, +y, -y, +z, -z), and the links as int
-    // bits (left, right, parent, leaf word): internal nodes have leaf word 0,
-    // leaves left = right = -1 and leaf word = first slot << 3 | count.
-    const float4 *lb_nodes;
+    // probabilistic light hierarchy (Sec. 2.1.1; null lb_rec: the alias
+    // table picks emitters). One record of 7 float4 per internal node (a
+    // tree of at most four emitters gets one record whose second child is
+    // empty), holding what a step of the descent needs for both children:
+    // per child (box centre, half diagonal), (I0..I3), (I4, I5, flux, link)
+    // with I_k the directional value of cube-face region k (+x, -x, +y, -y,
+    // +z, -z) and link = the child's record, or for a leaf 0x80000000 |
+    // first slot << 3 | count; then (parent record or 0xffffffff, side in the
+    // parent, 0, 0).
+    const float4 *lb_rec;
     const uint32_t *lb_perm;      // leaf slot -> emitter
-    const uint32_t *lb_leaf;      // emitter -> its leaf node
+    const uint32_t *lb_up;        // emitter -> record of its leaf's parent << 1 | side
     const float *lb_eflux;        // emitter -> flux (luminance x area)
     const uint32_t *lb_tri_rank;  // triangle -> rank among its mesh's emitters
     const uint32_t *lb_inst_base; // instance -> index of its first emitter

@@ -1387,7 +1387,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
                     stats.kernel_launches += 3;
                 }
                 e = mark(1);
-                (s->dev.lb_nodes ? k_shade<true> : k_shade<false>)<<<g_shade, gb, 0, st>>>(P, pool, sorted);
+                (s->dev.lb_rec ? k_shade<true> : k_shade<false>)<<<g_shade, gb, 0, st>>>(P, pool, sorted);
                 done(e);
                 e = mark(2);
                 if (o.trace_kernel != 1) {
@@ -1607,7 +1607,7 @@ extern "C" rt_status rt_render_probes(const rt_scene *s, const float *pos, const
         stats.kernel_launches += 4;
         for (uint32_t v = 2; v <= max_depth + 1; ++v) {
             tk.ext<<<tk.grid_ext, gb, tk.smem, st>>>(s->dev, pool, nullptr);
-            (s->dev.lb_nodes ? k_shade<true> : k_shade<false>)<<<g_shade, gb, 0, st>>>(P, pool, nullptr);
+            (s->dev.lb_rec ? k_shade<true> : k_shade<false>)<<<g_shade, gb, 0, st>>>(P, pool, nullptr);
             tk.shadow<<<tk.grid_shadow, gb, tk.smem, st>>>(s->dev, pool, nullptr);
             k_step_end<<<1, 1, 0, st>>>(pool);
             stats.kernel_launches += 4;
@@ -1723,7 +1723,7 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
                 if (o.trace_kernel != 1) tk.ext<<<tk.grid_ext, gb, tk.smem, st>>>(s->dev, pool, nullptr);
                 else k_trace_ext<false><<<g_trace, gb, smem, st>>>(s->dev, pool);
-                (s->dev.lb_nodes ? k_shade<true> : k_shade<false>)<<<g_shade, gb, 0, st>>>(P, pool, nullptr);
+                (s->dev.lb_rec ? k_shade<true> : k_shade<false>)<<<g_shade, gb, 0, st>>>(P, pool, nullptr);
                 if (o.trace_kernel != 1) tk.shadow<<<tk.grid_shadow, gb, tk.smem, st>>>(s->dev, pool, nullptr);
                 else k_trace_shadow<false><<<g_shadow, gb, smem, st>>>(s->dev, pool);
                 k_step_end<<<1, 1, 0, st>>>(pool);

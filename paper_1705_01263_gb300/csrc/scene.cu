@@ -171,10 +171,65 @@ void build_env_normal_tables(const std::vector<std::vector<double>> &lv, int32_t
 
 // ---- probabilistic light hierarchy (Sec. 2.1.1)
 struct LightBvh {
-    std::vector<float4> nodes;   // 4 float4 per node (see DevScene::lb_nodes)
+    std::vector<float4> nodes;   // 4 float4 per node: (centre, r), (I0..I3), (I4, I5, flux, 0), links (below)
     std::vector<uint32_t> perm;  // leaf slot -> emitter
     std::vector<uint32_t> leaf;  // emitter -> leaf node
 };
+// links of a node, as uint bits: left, right (0xffffffff in a leaf), parent
+// (0xffffffff at the root), leaf word (first slot << 3 | count; 0 if internal)
+
+// Descent records (DevScene::lb_rec) from the node tree: one per internal
+// node, both children's data and links side by side; per emitter the record
+// of its leaf's parent and the side.
+void light_bvh_records(const LightBvh &t, std::vector<float4> &rec, std::vector<uint32_t> &up) {
+    const size_t nn = t.nodes.size() / 4;
+    auto links = [&](size_t i) {
+        const float4 d = t.nodes[4 * i + 3];
+        return make_uint4(as_uint(d.x), as_uint(d.y), as_uint(d.z), as_uint(d.w));
+    };
+    std::vector<uint32_t> rmap(nn, 0xffffffffu);
+    uint32_t nrec = 0;
+    for (size_t i = 0; i < nn; ++i)
+        if (links(i).w == 0u) rmap[i] = nrec++;
+    rec.clear();
+    up.assign(t.leaf.size(), 0u);
+    const float4 empty = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (nrec == 0) {
+        // a single leaf: one record, the leaf on side 0, nothing on side 1
+        rec.push_back(t.nodes[0]);
+        rec.push_back(t.nodes[1]);
+        float4 c = t.nodes[2];
+        c.w = as_float(0x80000000u | links(0).w);
+        rec.push_back(c);
+        rec.push_back(empty);
+        rec.push_back(empty);
+        rec.push_back(make_float4(0.f, 0.f, 0.f, as_float(0x80000000u)));
+        rec.push_back(make_float4(as_float(0xffffffffu), as_float(0u), 0.f, 0.f));
+        return;
+    }
+    rec.resize(7 * (size_t)nrec);
+    for (size_t i = 0; i < nn; ++i) {
+        const uint4 L = links(i);
+        if (L.w != 0u) continue;
+        float4 *R = rec.data() + 7 * (size_t)rmap[i];
+        for (int side = 0; side < 2; ++side) {
+            const uint32_t ch = side ? L.y : L.x;
+            const uint4 cl = links(ch);
+            float4 c = t.nodes[4 * (size_t)ch + 2];
+            c.w = as_float(cl.w != 0u ? (0x80000000u | cl.w) : rmap[ch]);
+            R[3 * side] = t.nodes[4 * (size_t)ch];
+            R[3 * side + 1] = t.nodes[4 * (size_t)ch + 1];
+            R[3 * side + 2] = c;
+        }
+        const uint32_t par = L.z;
+        const uint32_t pside = par == 0xffffffffu ? 0u : (links(par).x == (uint32_t)i ? 0u : 1u);
+        R[6] = make_float4(as_float(par == 0xffffffffu ? 0xffffffffu : rmap[par]), as_float(pside), 0.f, 0.f);
+    }
+    for (size_t e = 0; e < t.leaf.size(); ++e) {
+        const uint32_t lf = t.leaf[e], par = links(lf).z;
+        up[e] = rmap[par] << 1 | (links(par).x == lf ? 0u : 1u);
+    }
+}
 
 // Binary tree over the emitters (three world-space vertices each in lv,
 // fluxes in flux): leaves of at most kLeaf emitters; a larger set is ordered
@@ -702,9 +757,12 @@ rt_status rtg::scene_create(const rt_scene_desc *d, rt_scene **out, bool host_on
             }
             LightBvh lb;
             build_light_bvh(light_v, flux, lb);
-            if ((st = upload(s, lb.nodes.data(), lb.nodes.size(), &D.lb_nodes, &Hs.lb_nodes)) != RT_OK) return fail(st);
+            std::vector<float4> rec;
+            std::vector<uint32_t> up;
+            light_bvh_records(lb, rec, up);
+            if ((st = upload(s, rec.data(), rec.size(), &D.lb_rec, &Hs.lb_rec)) != RT_OK) return fail(st);
             if ((st = upload(s, lb.perm.data(), lb.perm.size(), &D.lb_perm, &Hs.lb_perm)) != RT_OK) return fail(st);
-            if ((st = upload(s, lb.leaf.data(), lb.leaf.size(), &D.lb_leaf, &Hs.lb_leaf)) != RT_OK) return fail(st);
+            if ((st = upload(s, up.data(), up.size(), &D.lb_up, &Hs.lb_up)) != RT_OK) return fail(st);
             std::vector<float> ef(flux.begin(), flux.end());
             if ((st = upload(s, ef.data(), ef.size(), &D.lb_eflux, &Hs.lb_eflux)) != RT_OK) return fail(st);
             if ((st = upload(s, rank.data(), rank.size(), &D.lb_tri_rank, &Hs.lb_tri_rank)) != RT_OK) return fail(st);

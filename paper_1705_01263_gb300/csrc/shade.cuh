@@ -520,16 +520,14 @@ RT_HD V3 oct_decode(uint32_t c) {
     return normalize(v3(px, py, z));
 }
 
-// Estimated contribution of light-hierarchy node `id` to point x of normal
-// n (Sec. 2.1.1): its directional value for the region the point lies in,
+// Estimated contribution of a light-hierarchy node to point x of normal n
+// (Sec. 2.1.1): its directional value for the region the point lies in,
 // seen from the box centre, times a bound of the surface cosine over the
 // box's bounding sphere, over the squared distance to the centre; inside the
-// sphere the largest directional value over the squared radius. `flux`
-// returns the node's flux.
-RT_HD float lb_estimate(const DevScene &sc, uint32_t id, V3 x, V3 n, float &flux) {
-    const float4 *N = sc.lb_nodes + 4 * (size_t)id;
-    const float4 a = ldg(N), b = ldg(N + 1), c = ldg(N + 2);
-    flux = c.z;
+// sphere the largest directional value over the squared radius. The node
+// comes as its three float4 of a descent record: (centre, r), (I0..I3),
+// (I4, I5, flux, link).
+RT_HD float lb_estimate(float4 a, float4 b, float4 c, V3 x, V3 n) {
     if (!(c.z > 0.f)) return 0.f;
     const V3 v = x - v3(a.x, a.y, a.z);
     const float d2 = dot(v, v), r = a.w;
@@ -549,16 +547,29 @@ RT_HD float lb_estimate(const DevScene &sc, uint32_t id, V3 x, V3 n, float &flux
     return I * cs / d2;
 }
 
-// Probability of the left child: a child without flux is never chosen, else
-// the share of the estimates (of the fluxes when both vanish) clamped to
-// [0.1, 0.9].
-RT_HD float lb_p_left(const DevScene &sc, uint32_t left, uint32_t right, V3 x, V3 n) {
-    float fl, fr;
-    const float el = lb_estimate(sc, left, x, n, fl), er = lb_estimate(sc, right, x, n, fr);
-    if (!(fl > 0.f)) return 0.f;
-    if (!(fr > 0.f)) return 1.f;
-    const float p = el + er > 0.f ? el / (el + er) : fl / (fl + fr);
-    return fminf(fmaxf(p, 0.1f), 0.9f);
+// One step of the descent at record R: the two children's data (loaded
+// together) and the probability of the first child: a child without flux is
+// never chosen, else the share of the estimates (of the fluxes when both
+// vanish) clamped to [0.1, 0.9].
+struct LbStep {
+    float4 c0, c1;   // (I4, I5, flux, link) of each child
+    float p_left;
+};
+
+RT_HD LbStep lb_step(const float4 *R, V3 x, V3 n) {
+    const float4 a0 = ldg(R), b0 = ldg(R + 1), c0 = ldg(R + 2), a1 = ldg(R + 3), b1 = ldg(R + 4), c1 = ldg(R + 5);
+    LbStep st;
+    st.c0 = c0;
+    st.c1 = c1;
+    const float fl = c0.z, fr = c1.z;
+    if (!(fl > 0.f)) st.p_left = 0.f;
+    else if (!(fr > 0.f)) st.p_left = 1.f;
+    else {
+        const float el = lb_estimate(a0, b0, c0, x, n), er = lb_estimate(a1, b1, c1, x, n);
+        const float p = el + er > 0.f ? el / (el + er) : fl / (fl + fr);
+        st.p_left = fminf(fmaxf(p, 0.1f), 0.9f);
+    }
+    return st;
 }
 
 constexpr int kLbMaxDepth = 64;
@@ -568,14 +579,24 @@ constexpr int kLbMaxDepth = 64;
 // inlined, like lb_prob: the shading kernels then keep the registers of the
 // scenes without a hierarchy.
 RT_HD __noinline__ uint32_t lb_sample(const DevScene &sc, V3 x, V3 n, float u, float &P) {
-    uint32_t id = 0;
+    uint32_t rec = 0;
     P = 1.f;
     for (int depth = 0; depth < kLbMaxDepth; ++depth) {
-        const float4 L = ldg(sc.lb_nodes + 4 * (size_t)id + 3);
-        const uint32_t leaf = as_uint(L.w);
-        if (leaf) {
-            const uint32_t first = leaf >> 3, count = leaf & 7u;
-            const float target = u * ldg(sc.lb_nodes + 4 * (size_t)id + 2).z;
+        const LbStep st = lb_step(sc.lb_rec + 7 * (size_t)rec, x, n);
+        const bool left = u < st.p_left;
+        if (left) {
+            u = u / st.p_left;
+            P *= st.p_left;
+        } else {
+            u = (u - st.p_left) / (1.f - st.p_left);
+            if (u >= 1.f) u = 0.99999994f;
+            P *= 1.f - st.p_left;
+        }
+        const float4 c = left ? st.c0 : st.c1;
+        const uint32_t link = as_uint(c.w);
+        if (link & 0x80000000u) {
+            const uint32_t first = (link & 0x7fffffffu) >> 3, count = link & 7u;
+            const float target = u * c.z;
             float cum = 0.f;
             uint32_t pick = ldg(sc.lb_perm + first + count - 1);
             float fpick = 0.f;
@@ -585,21 +606,10 @@ RT_HD __noinline__ uint32_t lb_sample(const DevScene &sc, V3 x, V3 n, float u, f
                 cum += f;
                 if (target < cum || i + 1 == count) { pick = e; fpick = f; break; }
             }
-            P *= fpick / ldg(sc.lb_nodes + 4 * (size_t)id + 2).z;
+            P *= fpick / c.z;
             return pick;
         }
-        const uint32_t l = as_uint(L.x), r = as_uint(L.y);
-        const float p = lb_p_left(sc, l, r, x, n);
-        if (u < p) {
-            u = u / p;
-            P *= p;
-            id = l;
-        } else {
-            u = (u - p) / (1.f - p);
-            if (u >= 1.f) u = 0.99999994f;
-            P *= 1.f - p;
-            id = r;
-        }
+        rec = link;
     }
     P = 0.f;
     return 0u;
@@ -608,16 +618,23 @@ RT_HD __noinline__ uint32_t lb_sample(const DevScene &sc, V3 x, V3 n, float u, f
 // Probability that the descent from x (normal n) draws emitter e: the same
 // branch probabilities along the path from e's leaf up to the root.
 RT_HD __noinline__ float lb_prob(const DevScene &sc, V3 x, V3 n, uint32_t e) {
-    uint32_t id = ldg(sc.lb_leaf + e);
-    float P = ldg(sc.lb_eflux + e) / ldg(sc.lb_nodes + 4 * (size_t)id + 2).z;
+    const uint32_t up = ldg(sc.lb_up + e);
+    uint32_t rec = up >> 1, side = up & 1u;
+    float P = ldg(sc.lb_eflux + e);
+    bool first = true;
     for (int depth = 0; depth < kLbMaxDepth; ++depth) {
-        const uint32_t par = as_uint(ldg(sc.lb_nodes + 4 * (size_t)id + 3).z);
-        if (par == 0xffffffffu) break;
-        const float4 PL = ldg(sc.lb_nodes + 4 * (size_t)par + 3);
-        const uint32_t l = as_uint(PL.x), r = as_uint(PL.y);
-        const float p = lb_p_left(sc, l, r, x, n);
-        P *= l == id ? p : 1.f - p;
-        id = par;
+        const float4 *R = sc.lb_rec + 7 * (size_t)rec;
+        const float4 info = ldg(R + 6);
+        const LbStep st = lb_step(R, x, n);
+        if (first) {
+            P /= side ? st.c1.z : st.c0.z;   // the emitter's share of its leaf
+            first = false;
+        }
+        P *= side ? 1.f - st.p_left : st.p_left;
+        const uint32_t parent = as_uint(info.x);
+        if (parent == 0xffffffffu) break;
+        rec = parent;
+        side = as_uint(info.y);
     }
     return P;
 }
@@ -652,7 +669,7 @@ RT_HD NeePick nee_pick(const RenderParams &P, uint64_t index, int base) {
     k.lmid = 0;
     k.lpa = 0.f;
     k.l0 = k.l1 = k.l2 = v3(0.f, 0.f, 0.f);
-    if (!(k.us < sc.p_env) && !(kLb && sc.lb_nodes)) {
+    if (!(k.us < sc.p_env) && !(kLb && sc.lb_rec)) {
         float u2 = (k.us - sc.p_env) / (1.f - sc.p_env);
         float xn = u2 * (float)sc.num_lights;
         uint32_t bin = (uint32_t)xn;
@@ -706,7 +723,7 @@ RT_HD int scatter(const RenderParams &P, PathState &s, const Vertex &vx, const M
             V3 l0 = pk.l0, l1 = pk.l1, l2 = pk.l2;
             uint32_t lt = pk.lt, lmid = pk.lmid;
             float lpa = pk.lpa;
-            if (kLb && sc.lb_nodes) {
+            if (kLb && sc.lb_rec) {
                 // the light hierarchy draws the emitter from the offset
                 // origin and the normal as the path state keeps it, so that
                 // an emitter hit by the continuation gets the same number
@@ -858,7 +875,7 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
             else if (mode == 2) w = 0.f;
             else {
                 float pa = lpa;
-                if (kLb && sc.lb_nodes) {
+                if (kLb && sc.lb_rec) {
                     // the hierarchy's probability of this emitter from the
                     // previous vertex (offset origin s.o, its stored normal)
                     const uint32_t li = ldg(sc.lb_inst_base + h.inst) + ldg(sc.lb_tri_rank + prim);

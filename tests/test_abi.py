@@ -270,11 +270,12 @@ def test_env_normal_sampling_host_matches_oracle(plain):
         assert (np.einsum("ij,ij->i", wi, ng) > 0).mean() > 0.75
 
 
-def test_light_bvh_host_matches_oracle():
+@pytest.mark.parametrize("n_lights", [300, 3])
+def test_light_bvh_host_matches_oracle(n_lights):
     """The light hierarchy (Sec. 2.1.1) run on the host against the oracle:
     the emitter drawn for (x, n, u), its probability, and the re-traversal's
-    probability of it."""
-    sd, _ = scenes.many_emitters(n_lights=300, res=8)
+    probability of it (3 emitters: a tree that is a single leaf)."""
+    sd, _ = scenes.many_emitters(n_lights=n_lights, res=8)
     s, o = rt.Scene(sd, host_only=True), oracle.Scene(sd)
     rng = np.random.default_rng(12)
     n = 3000
