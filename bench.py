@@ -604,8 +604,9 @@ def main():
     ap.add_argument("--tail", type=int, default=0, help="live-path count below which the megakernel finishes a set (0 = default)")
     ap.add_argument("--render-once", action="store_true",
                     help="profiling aid: one untimed render of --spp, print its ray and launch counts, exit")
-    ap.add_argument("--scene", default="field", choices=["field", "cornell", "cornell-up"],
-                    help="scene of --render-once (cornell-up: emitter facing the ceiling)")
+    ap.add_argument("--scene", default="field", choices=["field", "cornell", "cornell-up", "many-lights"],
+                    help="scene of --render-once (cornell-up: emitter facing the ceiling; many-lights: the "
+                         "instanced 100k-emitter field with the light hierarchy, depth 12)")
     ap.add_argument("--guided", action="store_true",
                     help="--render-once with the guiding network: three calls of --spp (the first trains it)")
     ap.add_argument("--spp", type=int, default=SPP)
@@ -654,7 +655,14 @@ def main():
     if args.render_once:
         st = rt.rt_stats()
         what = WORKLOAD.replace("64 spp", f"{args.spp} spp")
-        if args.scene != "field" or args.guided:
+        if args.scene == "many-lights":
+            msd, mcam = scenes.instanced_field()
+            msd.light_bvh = True
+            mscene = rt.Scene(msd)
+            mfilm = rt.Film(mcam.width, mcam.height)
+            rt.rt_render(mscene, mcam, args.spp, 12, mfilm, rt.make_opts(stats=st))
+            what = f"many-lights 1920x1080 (light hierarchy), {args.spp} spp, depth 12"
+        elif args.scene != "field" or args.guided:
             csd, ccam = scenes.cornell_box(light="up" if args.scene == "cornell-up" else "down")
             cscene = rt.Scene(csd)
             cfilm = rt.Film(ccam.width, ccam.height)

@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_ext_simple(Dev
         Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, INFINITY};
         Hit h;
         h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
-        TraceResult tr = kTwoLevel    ? traverse_tlas<false>(sc, r, h)
+        TraceResult tr = kTwoLevel    ? traverse_two_level<false>(sc, r, h)
                          : kSmemStack ? traverse<false, SharedStack>(sc.nodes, sc.tris, 0u, r, h, 0u, &sst)
                                       : traverse<false>(sc.nodes, sc.tris, 0u, r, h);
         overflow |= tr.overflow;
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_shadow_simple(
         Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, o.w};
         Hit h;
         h.prim = RT_MISS; h.inst = 0; h.t = INFINITY;
-        TraceResult tr = kTwoLevel    ? traverse_tlas<true>(sc, r, h)
+        TraceResult tr = kTwoLevel    ? traverse_two_level<true>(sc, r, h)
                          : kSmemStack ? traverse<true, SharedStack>(sc.nodes, sc.tris, 0u, r, h, 0u, &sst)
                                       : traverse<true>(sc.nodes, sc.tris, 0u, r, h);
         overflow |= tr.overflow;
@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_user(DevScene 
         Ray r = job.load(i);
         Hit h;
         h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
-        TraceResult tr = kTwoLevel ? traverse_tlas<kAny>(sc, r, h) : traverse<kAny>(sc.nodes, sc.tris, 0u, r, h);
+        TraceResult tr = kTwoLevel ? traverse_two_level<kAny>(sc, r, h) : traverse<kAny>(sc.nodes, sc.tris, 0u, r, h);
         overflow |= tr.overflow;
         job.store(i, h);
     }

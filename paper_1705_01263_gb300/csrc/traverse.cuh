@@ -526,9 +526,123 @@ RT_HD TraceResult traverse_tlas(const DevScene &sc, const Ray &ray, Hit &hit) {
 }
 
 // Closest (or any) hit against the scene, one level or two.
+// Two-level traversal in one loop: every iteration visits one node of the
+// top-level BVH or of the current instance's BVH, or tests the triangles of
+// an instance's leaf, or enters the next instance of a top-level leaf, so
+// the lanes of a warp stay in step whichever level they are at (the nested
+// form runs a whole instance's traversal while the other lanes wait). One
+// stack holds both levels: entering an instance pushes the remaining
+// top-level group, the remaining instances of the leaf (x = first |
+// kInstGroup, y = mask) and a marker (x = 0xffffffff); popping the marker returns to
+// world space (node groups keep their hit bits in y; the flags live in x,
+// which for a node group is a node index below 2^31). Same hits and tie
+// rules as traverse_tlas.
+template <bool kAnyHit>
+RT_HD TraceResult traverse_two_level(const DevScene &sc, const Ray &ray, Hit &hit) {
+    constexpr uint32_t kInstGroup = 0x80000000u, kMarker = 0xffffffffu;
+    TraceResult res{false, 0u, 0u};
+    const RayPre rw = prepare(ray);
+    RayPre rp = rw;
+    uint2 stack[kStackSize];
+    int sp = 0;
+    uint2 ng = make_uint2(0u, (1u << (24 + (0u ^ rw.oct))) | 1u);   // the top-level root
+    const uint4 *nodes = sc.tlas_nodes;
+    bool in_inst = false;
+    uint32_t inst = 0u;
+    uint32_t ibase = 0u, imask = 0u;    // instances of a top-level leaf still to enter
+    const float tmin = ray.tmin;
+    float tbest = hit.prim == RT_MISS ? ray.tmax : hit.t;
+    for (;;) {
+        if (imask) {
+            // enter the next instance; what is left of this level resumes
+            // after it
+            const int k = ffs32(imask) - 1;
+            imask &= imask - 1u;
+            const uint32_t id = ldg(sc.tlas_inst + ibase + (uint32_t)k);
+            if (sp + 3 > kStackSize) { res.overflow = true; break; }
+            if (ng.y & 0xFF000000u) stack[sp++] = ng;
+            if (imask) stack[sp++] = make_uint2(ibase | kInstGroup, imask);
+            stack[sp++] = make_uint2(kMarker, 0u);
+            imask = 0u;
+            inst = id;
+            in_inst = true;
+            rp = prepare(to_object(sc.inst_xf, id, ray));
+            nodes = sc.nodes;
+            ng = make_uint2(ldg(sc.inst_root + id), (1u << (24 + (0u ^ rp.oct))) | 1u);
+            continue;
+        }
+        uint32_t tbase = 0u, tmask = 0u;
+        if (ng.y & 0xFF000000u) {
+            const int bit = 31 - clz32(ng.y);
+            const uint32_t slot = ((uint32_t)bit - 24u) ^ rp.oct;
+            const uint32_t rel = popc32((ng.y & 0xFFu) & ((1u << slot) - 1u));
+            const uint32_t child = ng.x + rel;
+            ng.y &= ~(1u << bit);
+            if (ng.y & 0xFF000000u) {
+                if (sp == kStackSize) { res.overflow = true; break; }
+                stack[sp++] = ng;
+            }
+            const uint4 *N = nodes + 5 * (size_t)child;
+            const uint4 n0 = ldg(N), n1 = ldg(N + 1), n2 = ldg(N + 2), n3 = ldg(N + 3), n4 = ldg(N + 4);
+            ++res.nodes;
+            uint32_t tb;
+            const uint32_t inner = intersect_children(rp, n0, n1, n2, n3, n4, tmin, tbest, tb);
+            ng = make_uint2(n1.x, inner | (n0.w >> 24));
+            if (in_inst) {
+                tbase = n1.y;
+                tmask = tb;
+            } else {
+                ibase = n1.y;
+                imask = tb;
+            }
+        } else {
+            ng.y = 0u;
+        }
+        while (tmask) {
+            const int k = ffs32(tmask) - 1;
+            tmask &= tmask - 1u;
+            const float4 *T = sc.tris + 3 * (size_t)(tbase + (uint32_t)k);
+            const float4 a = ldg(T), b = ldg(T + 1), c = ldg(T + 2);
+            ++res.tris;
+            float t, u, v;
+            if (intersect_tri(rp, f4xyz(a), f4xyz(b), f4xyz(c), tmin, ray.tmax, tbest, t, u, v)) {
+                const uint32_t prim = as_uint(a.w);
+                if (kAnyHit) {
+                    hit.prim = prim; hit.inst = inst; hit.t = t; hit.b1 = u; hit.b2 = v;
+                    return res;
+                }
+                if (t < tbest || hit.prim == RT_MISS || inst < hit.inst || (inst == hit.inst && prim < hit.prim)) {
+                    hit.prim = prim; hit.inst = inst; hit.t = t; hit.b1 = u; hit.b2 = v;
+                    tbest = t;
+                }
+            }
+        }
+        if (imask || (ng.y & 0xFF000000u)) continue;
+        // this group is done: pop (a marker leaves the instance)
+        for (;;) {
+            if (sp == 0) return res;
+            const uint2 e = stack[--sp];
+            if (e.x == kMarker) {
+                in_inst = false;
+                rp = rw;
+                nodes = sc.tlas_nodes;
+                continue;
+            }
+            if (e.x & kInstGroup) {
+                ibase = e.x & ~kInstGroup;
+                imask = e.y;
+            } else {
+                ng = e;
+            }
+            break;
+        }
+    }
+    return res;
+}
+
 template <bool kAnyHit>
 RT_HD TraceResult trace_scene(const DevScene &sc, const Ray &ray, Hit &hit) {
-    if (sc.two_level) return traverse_tlas<kAnyHit>(sc, ray, hit);
+    if (sc.two_level) return traverse_two_level<kAnyHit>(sc, ray, hit);
     return traverse<kAnyHit>(sc.nodes, sc.tris, 0u, ray, hit);
 }
 

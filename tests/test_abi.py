@@ -294,3 +294,29 @@ def test_light_bvh_host_matches_oracle(n_lights):
     assert np.allclose(pr, ps, rtol=1e-5, atol=0)
     pg = np.array([o.lb_prob(x[i].astype(np.float64), nrm[i].astype(np.float64), int(e[i])) for i in range(n)])
     assert np.allclose(pr, pg, rtol=1e-4, atol=0)
+
+
+@pytest.mark.parametrize("kind", ["primary", "incoherent", "shadow"])
+def test_two_level_traversal_host_matches_flattened_oracle(kind):
+    """Instanced scenes: the library's two-level traversal, run on the host,
+    against the oracle on the flattened copy ((instance, triangle) mapped to
+    the flattened index); the FP32 object-space and world-space geometries
+    differ by the rounding of the transforms, so a disagreement must be a
+    valid alternative hit."""
+    from test_gpu_trace import check_closest
+    sd, cam = scenes.instanced_field(n_meshes=6, n_instances=60, total_tris=60_000, n_emissive=300, width=64,
+                                     height=36, min_tris=300, max_tris=3000)
+    flat = sd.flattened()
+    s, o = rt.Scene(sd, host_only=True), oracle.Scene(flat)
+    rays = scenes.random_rays(flat, 20000, seed=9, kind=kind, cam=cam)
+    p, t, u, v, _, inst = rt.debug_trace_host(s, rays, any_hit=(kind == "shadow"), return_inst=True)
+    po, to, uo, vo = o.trace(rays, any_hit=(kind == "shadow"))
+    if kind == "shadow":
+        assert (np.asarray(p != rt.RT_MISS) == np.asarray(po != rt.RT_MISS)).mean() >= 0.9999
+        return
+    hit = p != rt.RT_MISS
+    counts = np.diff(sd.mesh_tri_offset)[sd.instance_mesh]
+    base = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    ii = np.where(hit, inst, 0).astype(np.int64)
+    fp = np.where(hit, base[ii] + (p.astype(np.int64) - sd.mesh_tri_offset[sd.instance_mesh[ii]]), rt.RT_MISS)
+    check_closest(flat, rays, (fp.astype(np.uint32), t, u, v), (po, to, uo, vo), min_agree=0.9999, t_rel=1e-4)
