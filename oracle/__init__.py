@@ -85,6 +85,8 @@ def _declare(L):
         "or_filter_offset": (None, [f64, f64, f64, vp, vp]),
         "or_render": (None, [vp, C.POINTER(_Cam), u32, u32, u32, C.POINTER(_Opts), vp, vp, vp, vp]),
         "or_render_pixels": (None, [vp, C.POINTER(_Cam), vp, vp, vp, i64, u32, C.POINTER(_Opts), vp]),
+        "or_render_two_way": (None, [vp, C.POINTER(_Cam), u32, u32, u32, C.POINTER(_Opts), C.c_int32, vp, vp, vp,
+                                     vp, vp]),
         "or_render_probes": (None, [vp, vp, vp, u32, u32, u32, u32, C.POINTER(_Opts), vp, vp, vp, vp]),
         "or_env_normal_cell": (C.c_int, [vp]),
         "or_env_sample_n": (None, [vp, vp, f64, f64, vp, vp]),
@@ -243,6 +245,21 @@ class Scene:
         lib().or_render(self.handle, C.byref(c), iter0, spp, max_depth, C.byref(o), _p(s), _p(s2),
                         _p(cnt), _p(rays))
         return s, s2, cnt, int(rays[0])
+
+    def render_two_way(self, cam, spp: int, max_depth: int, iter0: int = 0, sigma: float = 0.5,
+                       mis_mode: int = 0, lt_mode: int = 0, seed: int = 0, threads: int = 0):
+        """Two-way path tracing (Sec. 2): camera stage sums (with the light
+        tracer as a third MIS technique) and the light stage's splats; the
+        per-pixel estimate is (sum + splat) / count."""
+        c = _camera(cam)
+        o = _Opts(sigma, 0, mis_mode, seed, threads)
+        W, H = cam.width, cam.height
+        s, s2, sp = np.zeros((H, W, 3)), np.zeros((H, W, 3)), np.zeros((H, W, 3))
+        cnt = np.zeros((H, W), np.uint32)
+        rays = np.zeros(1, np.uint64)
+        lib().or_render_two_way(self.handle, C.byref(c), iter0, spp, max_depth, C.byref(o), lt_mode, _p(s),
+                                _p(s2), _p(cnt), _p(sp), _p(rays))
+        return s, s2, cnt, sp, int(rays[0])
 
     def render_samples(self, cam, px, py, sj, max_depth: int, sigma: float = 0.5, rr: bool = False,
                        mis_mode: int = 0, seed: int = 0):

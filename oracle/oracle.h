@@ -171,6 +171,20 @@ void or_render_pixels(const or_scene *s, const or_camera *cam,
                       const uint32_t *px, const uint32_t *py,
                       const uint32_t *sample_j, int64_t n, uint32_t max_depth,
                       const or_render_opts *opts, double *L /* n x 3 */);
+/* Two-way path tracing (render.c, two_way.c; Sec. 2): the camera stage into
+ * sum / sum2 / count as or_render, with the light tracer as a third MIS
+ * technique, and the light-tracing stage (W x H light paths per iteration)
+ * splatted into `splat` (H*W*3, accumulated; per pixel the estimate is
+ * (sum + splat) / count). lt_mode 0: MIS of the three techniques; 1: the
+ * light tracer alone wherever it can make the path, the camera techniques
+ * elsewhere; 2: the camera stage alone with the light tracer's density set
+ * to zero (equals or_render; no light stage); 3: the density check of
+ * two_way.c (counts, not radiance). mis_mode 0 or 1 only. */
+void or_render_two_way(const or_scene *s, const or_camera *cam, uint32_t iter0, uint32_t spp,
+                       uint32_t max_depth, const or_render_opts *opts, int32_t lt_mode, double *sum,
+                       double *sum2, uint32_t *count, double *splat, uint64_t *rays_traced);
+void or_light_trace(const or_scene *s, const or_camera *cam, uint32_t iter0, uint32_t spp, uint32_t D,
+                    const or_render_opts *opts, int lt_mode, double *splat, uint64_t *rays_traced);
 /* Irradiance probes (see render.c): sums of E = pi L per probe. */
 void or_render_probes(const or_scene *s, const double *pos, const double *nrm, uint32_t n,
                       uint32_t iter0, uint32_t spp, uint32_t max_depth,

@@ -66,4 +66,31 @@ void or_trace_one(const or_scene *s, const double o[3], const double d[3],
                   double *t, double *b1, double *b2);
 void or_tri_emission(const or_scene *s, uint32_t prim, double b1, double b2,
                      double Le[3]);
+/* ray origin moved off the surface along n (render.c) */
+void or_offset_origin(const double x[3], const double n[3], double out[3]);
+
+/* two-way path tracing (two_way.c) */
+typedef struct {
+    double x[3];
+    double ng[3];      /* unit geometric normal as stored (not turned) */
+    double ns[3];      /* unit interpolated shading normal (ng without normals) */
+    uint32_t prim;
+} or_tw_vertex;
+
+typedef struct {
+    double eye[3], fwd[3], right[3], up[3];
+    double th, asp, f;  /* tan(vfov / 2), W / H, focal length in pixels */
+    uint32_t W, H;
+    double sigma;       /* pixel filter (> 0 Gaussian, else box) */
+} or_tw_cam;
+
+void or_tw_cam_init(const or_camera *c, double sigma, or_tw_cam *tc);
+void or_tw_vertex_at(const or_scene *s, uint32_t prim, double b1, double b2, or_tw_vertex *v);
+/* area-measure densities of the three techniques for the path x[0] (eye) ..
+ * x[k] (emitter) through pixel (px, py); p_lt is zero where the light tracer
+ * does not connect to that pixel */
+void or_tw_pdfs(const or_scene *s, const or_tw_cam *tc, const or_tw_vertex *x, int k, uint32_t px, uint32_t py,
+                double *p_hit, double *p_nee, double *p_lt);
+/* heuristic weight of `mine` against two other (count-scaled) densities */
+double or_tw_weight(int mode, double mine, double other1, double other2);
 #endif

@@ -80,7 +80,7 @@ static double mis_weight(int mode, double pa, double pb) {
     return a / (a + b);
 }
 
-static void offset_origin(const double x[3], const double n[3], double out[3]) {
+void or_offset_origin(const double x[3], const double n[3], double out[3]) {
     double m = fmax(1.0, fmax(fabs(x[0]), fmax(fabs(x[1]), fabs(x[2]))));
     for (int a = 0; a < 3; ++a) out[a] = x[a] + n[a] * 1e-9 * m;
 }
@@ -93,7 +93,20 @@ typedef struct {
     uint32_t *factors; /* per dimension */
     int ndims;
     uint32_t D;
+    /* two-way path tracing: the light tracer is a third MIS technique */
+    int tw;            /* 1 + lt_mode of or_render_two_way, 0 = off */
+    or_tw_cam tc;
 } ctx_t;
+
+/* Weight of a camera technique (density `mine`, the other camera technique
+ * `other`) for a path the light tracer makes with density p_lt; W H light
+ * paths per iteration against one camera path per pixel. */
+static double tw_camera_weight(const ctx_t *c, double mine, double other, double p_lt) {
+    double nl = (double)c->cam->width * (double)c->cam->height * p_lt;
+    if (c->tw == 3) nl = 0.0;
+    if (c->tw == 2) return nl > 0.0 ? 0.0 : or_tw_weight(c->opts->mis_mode, mine, other, 0.0);
+    return or_tw_weight(c->opts->mis_mode, mine, other, nl);
+}
 
 static double dimv(const ctx_t *c, uint64_t idx, int dim) {
     return or_sample_dim(idx, dim, c->k, c->l, c->factors);
@@ -121,6 +134,12 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
     }
     double beta[3] = {1.0, 1.0, 1.0};
     double prev_pdf = 0.0;
+    /* two-way: the camera path's vertices, x[0] the eye */
+    or_tw_vertex X[68];
+    if (c->tw) {
+        memset(&X[0], 0, sizeof X[0]);
+        for (int a = 0; a < 3; ++a) X[0].x[a] = o[a];
+    }
     double prev_ng[3] = {0.0, 1.0, 0.0};   /* geometric normal of the previous vertex (env pdf) */
     int has_tris = s->nlights > 0, has_env = s->p_env > 0.0;
     for (uint32_t v = 1; v <= c->D + 1; ++v) {
@@ -131,7 +150,7 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
             ++*rays;
         }
         if (prim == OR_MISS) {
-            if (s->d.env) {
+            if (s->d.env && c->tw != 4) {
                 double Le[3];
                 or_env_lookup(s, d, Le);
                 double w = 1.0;
@@ -156,6 +175,7 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
             cog = dot3(wo, ng);
         }
         uint32_t m = at_probe ? 0u : s->d.tri_material[prim];
+        if (c->tw) or_tw_vertex_at(s, prim, b1, b2, &X[v]);
         if (!at_probe && cog > 0.0 && s->tri_light_pdf_area[prim] > 0.0) {
             double Le[3];
             or_tri_emission(s, prim, b1, b2, Le);
@@ -163,7 +183,15 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
             if (v > 1) {
                 if (mode == 3) w = 1.0;
                 else if (mode == 2) w = 0.0;
-                else {
+                else if (c->tw) {
+                    double ph, pn, pl;
+                    or_tw_pdfs(s, &c->tc, X, (int)v, px, py, &ph, &pn, &pl);
+                    w = tw_camera_weight(c, ph, pn, pl);
+                    if (c->tw == 4) {   /* density check: count the hit */
+                        if (pl > 0.0) L[0] += 1.0;
+                        w = 0.0;
+                    }
+                } else {
                     /* the light hierarchy's probability of this emitter from
                      * the previous vertex (its offset origin o and normal) */
                     double pa = s->lb_nodes ? (1.0 - s->p_env) * or_lb_prob(s, o, prev_ng, s->light_of_tri[prim]) /
@@ -172,6 +200,7 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
                     w = mis_weight(mode, prev_pdf, pa * t * t / cog);
                 }
             }
+            if (c->tw == 4 && v == 1) w = 0.0;
             for (int a = 0; a < 3; ++a) L[a] += beta[a] * Le[a] * w;
         }
         if (v == c->D + 1) break;
@@ -192,11 +221,12 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
         if (at_probe) { albedo[0] = albedo[1] = albedo[2] = 1.0; gw = 0.0; }
         int base = 2 + 7 * (int)(v - 1);
         double xo[3];
-        offset_origin(x, ng, xo);
+        or_offset_origin(x, ng, xo);
         /* next-event estimation */
         if ((has_tris || has_env) && mode != 3) {
             double us = dimv(c, idx, base), ua = dimv(c, idx, base + 1), ub = dimv(c, idx, base + 2);
             double wi[3], Le[3], sdir[3], pdf_l = 0.0, tmax = INFINITY;
+            int64_t tw_li = -1;
             if (us < s->p_env) {
                 double pe;
                 or_env_sample_n(s, ng, ua, ub, wi, &pe);
@@ -210,6 +240,7 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
                 int64_t li = s->lb_nodes ? or_lb_sample(s, xo, ng, u2, &psel)
                                          : or_alias_sample(s->alias_prob, s->alias_idx, s->nlights, u2);
                 uint32_t lt = (uint32_t)s->light_tri[li];
+                tw_li = li;
                 const double *lv = s->v64 + 9 * (size_t)lt;
                 double sq = sqrt(ua);
                 double lb1 = sq * (1.0 - ub), lb2 = sq * ub, lb0 = 1.0 - sq;
@@ -237,11 +268,29 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
                     }
                 }
             }
-            if (pdf_l > 0.0 && dot3(wi, ng) > 0.0) {
+            if (c->tw == 4 && tw_li >= 0 && pdf_l > 0.0 && dot3(wi, ng) > 0.0) {
+                /* density check: count next-event samples that make a
+                 * visible path the light tracer could make */
+                double sq = sqrt(ua), ph, pn, pl;
+                or_tw_vertex_at(s, (uint32_t)s->light_tri[tw_li], sq * (1.0 - ub), sq * ub, &X[v + 1]);
+                or_tw_pdfs(s, &c->tc, X, (int)v + 1, px, py, &ph, &pn, &pl);
+                if (pl > 0.0) {
+                    uint32_t sp; double st, sb1, sb2;
+                    or_trace_one(s, xo, sdir, 0.0, tmax, 1, &sp, &st, &sb1, &sb2);
+                    ++*rays;
+                    if (sp == OR_MISS) L[1] += 1.0;
+                }
+            } else if (c->tw != 4 && pdf_l > 0.0 && dot3(wi, ng) > 0.0) {
                 double f[3], pdf_b;
                 or_bsdf_eval(albedo, rough, gw, nsa, wo, wi, f, &pdf_b);
                 if (pdf_b > 0.0) {
                     double w = mode == 2 ? 1.0 : mis_weight(mode, pdf_l, pdf_b);
+                    if (c->tw && us >= s->p_env) {
+                        double sq = sqrt(ua), ph, pn, pl;
+                        or_tw_vertex_at(s, (uint32_t)s->light_tri[tw_li], sq * (1.0 - ub), sq * ub, &X[v + 1]);
+                        or_tw_pdfs(s, &c->tc, X, (int)v + 1, px, py, &ph, &pn, &pl);
+                        w = tw_camera_weight(c, pn, ph, pl);
+                    }
                     double ci = dot3(wi, nsa);
                     uint32_t sp; double st, sb1, sb2;
                     or_trace_one(s, xo, sdir, 0.0, tmax, 1, &sp, &st, &sb1, &sb2);
@@ -277,6 +326,7 @@ static void ctx_init(ctx_t *c, const or_scene *s, const or_camera *cam,
     uint64_t p2, p3;
     or_enum_params(cam->width, cam->height, &c->k, &c->l, &p2, &p3);
     c->ndims = 2 + 7 * (int)(D + 1);
+    c->tw = 0;
     c->factors = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)c->ndims);
     for (int d = 0; d < c->ndims; ++d)
         c->factors[d] = d < 2 ? 1u : or_scramble_factor(opts->seed, or_prime(d));
@@ -390,4 +440,37 @@ void or_render_probes(const or_scene *s, const double *pos, const double *nrm, u
     }
     if (rays_traced) *rays_traced = rays;
     free(c.factors);
+}
+
+void or_render_two_way(const or_scene *s, const or_camera *cam, uint32_t iter0, uint32_t spp,
+                       uint32_t max_depth, const or_render_opts *opts, int32_t lt_mode, double *sum,
+                       double *sum2, uint32_t *count, double *splat, uint64_t *rays_traced) {
+    ctx_t c;
+    ctx_init(&c, s, cam, max_depth, opts);
+    c.tw = 1 + lt_mode;
+    or_tw_cam_init(cam, opts->filter_sigma, &c.tc);
+    int nth = opts->threads > 0 ? opts->threads : (int)sysconf(_SC_NPROCESSORS_ONLN);
+    if (nth < 1) nth = 1;
+    uint32_t H = cam->height;
+    if ((uint32_t)nth > H) nth = (int)H;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nth);
+    job_t *jobs = (job_t *)calloc((size_t)nth, sizeof(job_t));
+    uint32_t rows_per = (H + (uint32_t)nth - 1) / (uint32_t)nth;
+    for (int t = 0; t < nth; ++t) {
+        jobs[t].c = &c; jobs[t].iter0 = iter0; jobs[t].spp = spp;
+        jobs[t].sum = sum; jobs[t].sum2 = sum2; jobs[t].count = count;
+        jobs[t].row0 = (uint32_t)t * rows_per;
+        jobs[t].row1 = jobs[t].row0 + rows_per > H ? H : jobs[t].row0 + rows_per;
+        if (jobs[t].row0 > H) jobs[t].row0 = H;
+        pthread_create(&th[t], NULL, render_rows, &jobs[t]);
+    }
+    uint64_t rays = 0;
+    for (int t = 0; t < nth; ++t) { pthread_join(th[t], NULL); rays += jobs[t].rays; }
+    free(th); free(jobs); free(c.factors);
+    if (lt_mode != 2) {
+        uint64_t lr = 0;
+        or_light_trace(s, cam, iter0, spp, max_depth, opts, lt_mode, splat, &lr);
+        rays += lr;
+    }
+    if (rays_traced) *rays_traced = rays;
 }

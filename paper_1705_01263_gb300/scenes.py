@@ -266,6 +266,24 @@ def cornell_box(seed: int = BASE_SEED + 1, light: str = "down"):
     return scene, cam
 
 
+def glossy_room(res: int = 64):
+    """The Cornell room lit through its ceiling (cornell_box(light="up")) with
+    glossy boxes (pure GGX coating, roughness 0.05) and a half-glossy floor
+    (GGX weight 0.6, roughness 0.08): every visible surface is lit along paths
+    that leave the emitter, bounce off the ceiling and often off a glossy
+    surface, which next-event estimation from the camera side reaches poorly
+    and a light tracer reaches directly."""
+    sd, cam = cornell_box(light="up")
+    rough = sd.roughness.copy()
+    gw = sd.ggx_weight.copy()
+    # materials in creation order: floor, ceiling, back, left, right, box, box, emitter
+    for mi, (r, w) in {0: (0.08, 0.6), 5: (0.05, 1.0), 6: (0.05, 1.0)}.items():
+        rough[mi] = r
+        gw[mi] = w
+    sd = dataclasses.replace(sd, roughness=rough, ggx_weight=gw, name="cornell-36-up-glossy")
+    return sd, dataclasses.replace(cam, width=res, height=res)
+
+
 # ------------------------------------------------------------ value noise
 def _value_noise(p: np.ndarray, seed: int) -> np.ndarray:
     """Trilinear value noise in [0, 1] on the integer lattice (smoothstep)."""
