@@ -222,6 +222,39 @@ rt_status rt_film_resolve(const rt_film *film, float *mean, float *var, void *st
 rt_status rt_render(const rt_scene *scene, const rt_camera *camera, uint32_t spp,
                     uint32_t max_depth, rt_film *film, const rt_render_opts *opts, void *stream);
 
+/* Two-way path tracing (Sec. 2): the path tracer and a light-tracing stage
+ * with the same number of paths per iteration (W x H), combined by multiple
+ * importance sampling. The light tracer starts on the triangle emitters in
+ * proportion to their flux, leaves them cosine-distributed, scatters by the
+ * BSDF sampler and connects every vertex to the pinhole camera, adding the
+ * connection to each pixel whose Gaussian filter centre lies within 3 sigma of
+ * the image point (the box filter: the pixel that holds it). Techniques for a
+ * path eye .. emitter with at least one scattering vertex: the camera path's
+ * BSDF-sampled emitter hit, next-event estimation, and the light tracer's
+ * camera connection (sample counts 1 per pixel against W x H); paths that see
+ * an emitter directly or end in the environment keep the path tracer's
+ * two-technique weights.
+ *   spp, max_depth, film: as rt_render; iterations continue from the film's
+ *             next iteration, which must start a pass (RT_INVALID_ARG
+ *             otherwise); the film's sums, sums of squares and counts receive
+ *             the camera stage (its squares cover that stage only)
+ *   opts:     filter_sigma, mis_mode (0 power or 1 balance, else
+ *             RT_INVALID_ARG), seed and rr_enable as rt_render; the scheduling
+ *             options are ignored; guide must be NULL (RT_NOT_SUPPORTED)
+ *   lt_mode:  0 MIS of the three techniques; 1 the light tracer alone for
+ *             every path it can make, the camera techniques elsewhere
+ *   lt_splat: DEVICE double [H][W][3] that the light stage adds into
+ *             (caller-owned; the estimate of a pixel is then
+ *             (sum + lt_splat) / count), or NULL to add into the film's sums
+ *   stats:    optional (paths, extension and shadow rays, kernel launches)
+ * The call returns when the work is done (it synchronises `stream`).
+ * Errors: RT_INVALID_ARG (null pointers, sizes, depth, modes),
+ * RT_NOT_SUPPORTED (instanced scenes, scenes with the light hierarchy, a
+ * guide), RT_CUDA_ERROR. */
+rt_status rt_render_two_way(const rt_scene *scene, const rt_camera *camera, uint32_t spp, uint32_t max_depth,
+                            rt_film *film, const rt_render_opts *opts, int32_t lt_mode, double *lt_splat,
+                            rt_stats *stats, void *stream);
+
 /* Irradiance probes (Sec. 4.2, alternate outputs): instead of camera rays,
  * n probe points with normals; each probe's film pixel accumulates estimates
  * of the irradiance E = integral over the hemisphere around its normal of

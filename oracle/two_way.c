@@ -310,7 +310,9 @@ static void light_path(lt_job *j, uint64_t m, or_tw_vertex *V, or_tw_vertex *X) 
         double we[3];
         unit_to(v->x, tc->eye, we);
         double sx, sy, czc;
-        if (dot3(we, ngf) > 0.0 && project(tc, v->x, &sx, &sy, &czc)) {
+        double mg = 3.0 * tc->sigma + 2.0;   /* image points beyond the splat window reach no pixel */
+        if (dot3(we, ngf) > 0.0 && project(tc, v->x, &sx, &sy, &czc) && sx > -mg && sx < (double)tc->W + mg &&
+            sy > -mg && sy < (double)tc->H + mg) {
             double nsa[3], f[3], pdf;
             or_adapt_shading_normal(nsf, ngf, we, nsa);
             or_bsdf_eval(albedo, rough, gw, nsa, we, wi, f, &pdf);

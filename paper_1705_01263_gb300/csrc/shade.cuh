@@ -439,6 +439,7 @@ RT_HD V3 offset_origin(V3 p, V3 n) {
 // (Appendix A.3).
 struct Vertex {
     V3 x, ng, ns, wo;
+    V3 nsr;           // shading normal before the adaptation (on ng's side)
     float cog;        // cos between wo and the unflipped geometric normal
 };
 
@@ -478,6 +479,7 @@ RT_HD void setup_vertex(const DevScene &sc, const PathState &s, const Hit &h, Ve
         if (dot(ns, ng) < 0.f) ns = -ns;
     }
     vx.ng = ng;
+    vx.nsr = ns;
     vx.ns = adapt_shading_normal(ns, ng, vx.wo);
 }
 
@@ -905,6 +907,7 @@ RT_HD int probe_vertex(const RenderParams &P, PathState &s, V3 pos, V3 nrm, Shad
     vx.x = pos;
     vx.ng = nrm;
     vx.ns = nrm;
+    vx.nsr = nrm;
     vx.wo = nrm;
     vx.cog = 1.f;
     Material m;

@@ -93,7 +93,7 @@ EXPORTED = [
     "rt_render_static", "rt_render_batch", "rt_autotune", "rt_sample_index", "rt_halton", "rt_divide_u64_host", "rt_guide_create", "rt_guide_destroy",
     "rt_guide_num_params", "rt_guide_get_params", "rt_guide_set_params", "rt_guide_state_size", "rt_guide_save",
     "rt_guide_load", "rt_guide_infer", "rt_guide_loss_grad", "rt_guide_train_step", "rt_last_error",
-    "rt_status_string", "rt_gemm_bf16", "rt_render_probes",
+    "rt_status_string", "rt_gemm_bf16", "rt_render_probes", "rt_render_two_way",
 ]
 
 
@@ -143,6 +143,8 @@ def _declare(L):
         "rt_debug_guide_infer_layers": [vp, vp, i64, vp, vp],
         "rt_debug_render_probes_host": [vp, vp, vp, u32, u32, C.POINTER(rt_render_opts), vp, vp, i64, vp],
         "rt_render_probes": [vp, vp, vp, u32, u32, u32, vp, C.POINTER(rt_render_opts), vp],
+        "rt_render_two_way": [vp, C.POINTER(rt_camera), u32, u32, vp, C.POINTER(rt_render_opts), C.c_int32, vp,
+                              vp, vp],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -623,6 +625,28 @@ def rt_render_probes(scene: Scene, pos, nrm, spp: int, max_depth: int, film: "Fi
         return st
     check(st)
     return st
+
+
+def rt_render_two_way(scene: Scene, cam, spp: int, max_depth: int, film: "Film",
+                      opts: Optional[rt_render_opts] = None, lt_mode: int = 0, lt_splat=None,
+                      stream=None) -> rt_stats:
+    """Two-way path tracing (rt_render_two_way): the camera stage into `film`,
+    the light stage into `lt_splat` (torch CUDA float64 [H][W][3], added into)
+    or, when None, into the film's sums. Returns the call's statistics."""
+    c = make_camera(cam)
+    o = opts if opts is not None else make_opts()
+    ptr = None
+    if lt_splat is not None:
+        import torch
+        if lt_splat.dtype != torch.float64 or not lt_splat.is_cuda or not lt_splat.is_contiguous():
+            raise ValueError("lt_splat must be a contiguous CUDA float64 tensor")
+        if tuple(lt_splat.shape) != (cam.height, cam.width, 3):
+            raise ValueError("lt_splat must be [H][W][3]")
+        ptr = lt_splat.data_ptr()
+    stats = rt_stats()
+    check(lib().rt_render_two_way(scene.handle, C.byref(c), spp, max_depth, film.handle, C.byref(o), lt_mode, ptr,
+                                  C.byref(stats), _stream(stream)))
+    return stats
 
 
 def debug_render_probes_host(scene: Scene, pos, nrm, max_depth, p, j, opts: Optional[rt_render_opts] = None):
