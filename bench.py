@@ -494,6 +494,66 @@ def env_normal_vs_plain(sd, cam, scene, spp=16, ref_spp=1024, reps=3):
     return out
 
 
+def two_way_vs_plain(res=256, depth=4, spp=64, ref_spp=4096, reps=3):
+    """Two-way path tracing (Sec. 2: the light tracer as a third MIS
+    technique, rt_render_two_way) against the path tracer (rt_render) in the
+    glossy room lit through its ceiling, at equal iterations: RMSE against a
+    two-way reference of `ref_spp` disjoint iterations and device time.
+    efficiency = (RMSE^2 x time) of the path tracer over two-way's (above 1:
+    two-way reaches equal error sooner)."""
+    import torch
+    from paper_1705_01263_gb300 import rt, scenes
+    sd, cam = scenes.glossy_room(res)
+    scene = rt.Scene(sd)
+    film = rt.Film(cam.width, cam.height)
+
+    def timed(fn):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        r = fn()
+        ev1.record()
+        ev1.synchronize()
+        return r, ev0.elapsed_time(ev1)
+
+    def plain(first, n):
+        film.clear()
+        film.seek(first)
+        _, ms = timed(lambda: rt.rt_render(scene, cam, n, depth, film))
+        mean, _ = film.resolve()
+        return mean, ms, None
+
+    def two_way(first, n):
+        film.clear()
+        film.seek(first)
+        st, ms = timed(lambda: rt.rt_render_two_way(scene, cam, n, depth, film))
+        mean, _ = film.resolve()
+        return mean, ms, st
+
+    ref, _, _ = two_way(1 << 22, ref_spp)
+    out = {"workload": f"glossy room lit through its ceiling, {res}x{res}, depth {depth}, {spp} iterations; "
+                       f"reference: two-way, {ref_spp} disjoint iterations"}
+    for name, fn in (("path_tracer", plain), ("two_way", two_way)):
+        fn(0, spp)   # warm-up
+        err, ms = [], []
+        st = None
+        for r in range(reps):
+            m, t, st = fn(r * spp, spp)
+            err.append(float((m - ref).double().pow(2).mean().sqrt()))
+            ms.append(t)
+        out[name] = {"rmse": statistics.mean(err), "ms": statistics.median(ms)}
+        if st is not None:
+            paths = 2 * spp * res * res   # camera paths + light paths
+            out[name].update({"Mpaths_per_s": paths / (out[name]["ms"] / 1e3) / 1e6,
+                              "Mrays_per_s": (st.extension_rays + st.shadow_rays) / (out[name]["ms"] / 1e3) / 1e6})
+        else:
+            out[name]["Mpaths_per_s"] = spp * res * res / (out[name]["ms"] / 1e3) / 1e6
+    p_, t_ = out["path_tracer"], out["two_way"]
+    out["rmse_ratio"] = t_["rmse"] / p_["rmse"]
+    out["efficiency"] = (p_["rmse"] ** 2 * p_["ms"]) / (t_["rmse"] ** 2 * t_["ms"])
+    film.close()
+    return out
+
+
 # FLOPs of one row of the guiding network: 224->64->64->64->64->40
 GUIDE_FLOP_PER_ROW = 2 * (224 * 64 + 3 * 64 * 64 + 64 * 40)
 
@@ -594,6 +654,10 @@ def main():
     ap.add_argument("--no-guided", action="store_true", help="skip the guided-vs-plain time-to-RMSE run")
     ap.add_argument("--no-many-lights", action="store_true", help="skip the instanced many-light workload")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-scene batched workload")
+    ap.add_argument("--no-two-way", action="store_true", help="skip the two-way against path-tracer comparison")
+    ap.add_argument("--two-way-once", action="store_true", help="only the two-way comparison (for profiling)")
+    ap.add_argument("--tw-spp", type=int, default=64, help="iterations per image of --two-way-once")
+    ap.add_argument("--tw-ref-spp", type=int, default=4096, help="reference iterations of --two-way-once")
     ap.add_argument("--no-traversal", action="store_true", help="skip the traversal-only ray batches")
     ap.add_argument("--no-probes", action="store_true", help="skip the irradiance-probe workload")
     ap.add_argument("--mlp-once", action="store_true",
@@ -651,6 +715,9 @@ def main():
     film.seek(base_iter)
     if args.mlp_once:
         print(json.dumps(guide_mlp(reps=3)), flush=True)
+        return 0
+    if args.two_way_once:
+        print(json.dumps(two_way_vs_plain(spp=args.tw_spp, ref_spp=args.tw_ref_spp, reps=1)), flush=True)
         return 0
     if args.render_once:
         st = rt.rt_stats()
@@ -778,6 +845,9 @@ def main():
     bt = None
     if rank == 0 and not args.no_batched:
         bt = batched()
+    tw = None
+    if rank == 0 and not args.no_two_way:
+        tw = two_way_vs_plain()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_oracle(sd, cam)
@@ -824,6 +894,7 @@ def main():
             "traversal_only": trv,
             "probes": prb,
             "env_normal_vs_plain": env_ab,
+            "two_way": tw,
             "wall_s": t_wall,
         }
         s = json.dumps(line)

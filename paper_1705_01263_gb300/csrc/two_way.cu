@@ -527,7 +527,10 @@ extern "C" rt_status rt_render_two_way(const rt_scene *s, const rt_camera *cam, 
     T.base = base;
     T.lt_mode = lt_mode;
     const uint64_t n = (uint64_t)spp * WH;
-    const int grid = (int)std::min<uint64_t>((n + 127) / 128, (uint64_t)sm_count() * 16);
+    // One path per thread: with several paths per thread the lanes of a warp
+    // drift apart (each starts its next path whenever its last one ends) and
+    // the warp runs their different phases one after another.
+    const int grid = (int)std::min<uint64_t>((n + 127) / 128, 0x7FFFFFFFull);
     k_tw_camera<<<grid, 128, 0, st>>>(P, T, film->sum, film->sum2, film->count, (uint32_t)j0, n, ctr);
     RT_CUDA_TRY(cudaGetLastError());
     if (P.sc.num_lights > 0) {
