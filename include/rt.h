@@ -249,8 +249,9 @@ rt_status rt_render(const rt_scene *scene, const rt_camera *camera, uint32_t spp
  *   stats:    optional (paths, extension and shadow rays, kernel launches)
  * The call returns when the work is done (it synchronises `stream`).
  * Errors: RT_INVALID_ARG (null pointers, sizes, depth, modes),
- * RT_NOT_SUPPORTED (instanced scenes, scenes with the light hierarchy, a
- * guide), RT_CUDA_ERROR. */
+ * RT_NOT_SUPPORTED (instanced scenes, a guide), RT_CUDA_ERROR. With the
+ * light hierarchy (Sec. 2.1.1) the camera stage's NEE draws through it and
+ * every weight uses its probability; the light stage still emits by flux. */
 rt_status rt_render_two_way(const rt_scene *scene, const rt_camera *camera, uint32_t spp, uint32_t max_depth,
                             rt_film *film, const rt_render_opts *opts, int32_t lt_mode, double *lt_splat,
                             rt_stats *stats, void *stream);

@@ -152,7 +152,13 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
             V3 Le = tri_emission(sc, prim, mid, h.b1, h.b2);
             float w = 1.f;
             if (v > 1) {
-                const float pa = lpa;   // next-event estimation's area pdf (alias table)
+                float pa = lpa;   // next-event estimation's area pdf of this point
+                if (sc.lb_rec) {
+                    // the light hierarchy's, from the previous vertex (its
+                    // offset origin and stored normal), as in shade()
+                    const uint32_t li = ldg(sc.lb_inst_base + h.inst) + ldg(sc.lb_tri_rank + prim);
+                    pa = (1.f - sc.p_env) * lb_prob(sc, s.o, oct_decode(s.prev_n), li) / emitter_area(sc, li);
+                }
                 const float r_nee = pa * t2 / (s.prev_pdf * vx.cog);
                 // light tracer / hit: the factor of x_v, (cos_y / pi) c / t^2,
                 // times the emitter's, pA_lt t^2 / (prev_pdf cos_y)
@@ -173,7 +179,7 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
             NeePick pk = nee_pick<false>(P, s.index, base);
             const float us = pk.us, ua = pk.ua, ub = pk.ub;
             V3 wi = v3(0.f, 0.f, 1.f), Le = v3(0.f, 0.f, 0.f), sdir = wi;
-            float pdf_l = 0.f, tmax = INFINITY, cl = 0.f, dist = 0.f;
+            float pdf_l = 0.f, tmax = INFINITY, cl = 0.f, dist = 0.f, lt_over_nee = 0.f;
             bool tri = false;
             if (us < sc.p_env) {
                 const uint32_t cell = env_cell(ng);
@@ -184,9 +190,21 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
                 Le = v3(e.x, e.y, e.z);
                 pdf_l = sc.p_env * e.w * env_cell_factor(sc, cell, tx);
             } else {
-                const V3 l0 = pk.l0, l1 = pk.l1, l2 = pk.l2;
-                const uint32_t lt = pk.lt, lmid = pk.lmid;
-                const float lpa_n = pk.lpa;
+                V3 l0 = pk.l0, l1 = pk.l1, l2 = pk.l2;
+                uint32_t lt = pk.lt, lmid = pk.lmid;
+                float lpa_n = pk.lpa;
+                if (sc.lb_rec) {
+                    float Pp;
+                    const uint32_t li =
+                        lb_sample(sc, xo, oct_decode(oct_encode(ng)), (us - sc.p_env) / (1.f - sc.p_env), Pp);
+                    const float4 *LV = sc.light_v + 3 * (size_t)li;
+                    l0 = f4xyz(ldg(LV));
+                    l1 = f4xyz(ldg(LV + 1));
+                    l2 = f4xyz(ldg(LV + 2));
+                    lt = ldg(sc.light_tri + li);
+                    lmid = ldg(sc.tri_material + lt);
+                    lpa_n = (1.f - sc.p_env) * Pp / (0.5f * length(cross(l1 - l0, l2 - l0)));
+                }
                 float sq = sqrtf(ua);
                 float lb1 = sq * (1.f - ub), lb2 = sq * ub;
                 V3 y = (1.f - sq) * l0 + lb1 * l1 + lb2 * l2;
@@ -205,6 +223,9 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
                             sdir = sv * (1.f / sl);
                             tmax = sl * (1.f - kShadowEps);
                             tri = true;
+                            // the light tracer's area pdf of the point (alias
+                            // table) over next-event estimation's
+                            lt_over_nee = ldg(sc.tri_light_pdf_area + lt) / ((1.f - sc.p_env) * lpa_n);
                         } else {
                             pdf_l = 0.f;
                         }
@@ -225,8 +246,7 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
                             if (v >= 2) fv1 = tw_dir_pdf(m, ng, vx.nsr, wi, wo) * cprev / t2;
                             // x_v: emission cosine over pi, cos at x_v towards y
                             const float fv = (cl / kPi) * dot(wi, ng) / (dist * dist * Cd);
-                            // the light tracer's area pdf of the point over NEE's
-                            r_lt = T.nL * Pi * fv1 * fv / (1.f - sc.p_env);
+                            r_lt = T.nL * Pi * fv1 * fv * lt_over_nee;
                         }
                         if (T.lt_mode == 1) w = r_lt > 0.f ? 0.f : w;
                         else w = tw_weight(mode, pdf_b / pdf_l, r_lt);
@@ -359,7 +379,13 @@ RT_D void tw_light_path(const RenderParams &P, const TwParams &T, uint64_t m, do
         const Material mat = load_material(sc, ldg(sc.tri_material + h.prim));
         const V3 xo = offset_origin(x, ng);
         // p_light of the emitter from x (next-event estimation's area pdf)
-        const float G_nee = t == 1 ? ldg(sc.tri_light_pdf_area + lt) / pa : 0.f;
+        float G_nee = 0.f;
+        if (t == 1) {
+            // next-event estimation's area pdf of the emission point from x
+            float pl = ldg(sc.tri_light_pdf_area + lt);
+            if (sc.lb_rec) pl = (1.f - sc.p_env) * lb_prob(sc, xo, oct_decode(oct_encode(ng)), li) / emitter_area(sc, li);
+            G_nee = pl / pa;
+        }
         // connection to the eye
         const V3 te = cam.eye - x;
         const float re2 = dot(te, te);
@@ -485,10 +511,6 @@ extern "C" rt_status rt_render_two_way(const rt_scene *s, const rt_camera *cam, 
     if (o.guide) { set_error("rt_render_two_way: guiding is not combined with light tracing"); return RT_NOT_SUPPORTED; }
     if (s->dev.two_level) {
         set_error("rt_render_two_way: light tracing needs a single-level scene");
-        return RT_NOT_SUPPORTED;
-    }
-    if (s->dev.lb_rec) {
-        set_error("rt_render_two_way: light tracing is combined with the alias-table emitter selection only");
         return RT_NOT_SUPPORTED;
     }
     const uint64_t WH = (uint64_t)cam->width * cam->height;

@@ -3,7 +3,7 @@ combined by MIS) through the C ABI: the camera stage and the light stage's
 splats against the oracle on the same samples (every heuristic, filter and
 light-tracer mode), the combined image against the GPU path tracer in
 expectation, the error reduction in the ceiling-lit glossy room, and the
-refused configurations."""
+refused configurations; scenes with the light hierarchy (Sec. 2.1.1) included."""
 import dataclasses
 
 import numpy as np
@@ -20,6 +20,8 @@ pytestmark = pytest.mark.gpu
 def _scene(name, res):
     if name == "glossy":
         sd, cam = scenes.glossy_room(res)
+    elif name == "many":
+        sd, cam = scenes.many_emitters(n_lights=64, res=res)   # light hierarchy
     else:
         sd, cam = scenes.cornell_box()
         cam = dataclasses.replace(cam, width=res, height=res)
@@ -41,7 +43,7 @@ def two_way_gpu(sd, cam, spp, depth, first=0, lt_mode=0, sigma=0.5, mis_mode=0, 
 
 @pytest.mark.parametrize("name,depth,lt_mode,mis_mode,sigma", [
     ("glossy", 3, 0, 0, 0.5), ("glossy", 3, 0, 1, 0.5), ("glossy", 3, 1, 0, 0.5), ("cornell", 4, 0, 0, 0.5),
-    ("cornell", 4, 0, 0, 0.0)])
+    ("cornell", 4, 0, 0, 0.0), ("many", 3, 0, 0, 0.5)])
 def test_two_way_matches_the_oracle_on_the_same_samples(name, depth, lt_mode, mis_mode, sigma):
     sd, cam = _scene(name, 32)
     s, s2, c, sp, stats = two_way_gpu(sd, cam, 64, depth, lt_mode=lt_mode, sigma=sigma, mis_mode=mis_mode)
@@ -130,6 +132,3 @@ def test_two_way_refuses_what_it_does_not_combine():
                                        height=16, min_tris=200, max_tris=1000)
     with pytest.raises(rt.RtError):
         rt.rt_render_two_way(rt.Scene(sdi), cami, 1, 3, rt.Film(16, 16))
-    sdm, camm = scenes.many_emitters(n_lights=16, res=16)
-    with pytest.raises(rt.RtError):
-        rt.rt_render_two_way(rt.Scene(sdm), camm, 1, 3, rt.Film(16, 16))

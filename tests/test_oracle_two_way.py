@@ -59,7 +59,7 @@ def _chunks(s, cam, spp, D, K, lt_mode, first=0, **kw):
 # The glossy room stops at depth 2: deeper, the ratio of the GGX pdfs of the
 # two directions of a vertex grows without bound at grazing angles and the
 # light tracer's mean converges too slowly for a short test.
-@pytest.mark.parametrize("name,D", [("cornell", 4), ("cornell-up", 3), ("glossy", 2)])
+@pytest.mark.parametrize("name,D", [("cornell", 4), ("cornell-up", 3), ("glossy", 2), ("many", 2)])
 def test_every_density_is_the_density_of_its_sampler(name, D):
     sd, cam = _scene(name)
     s = oracle.Scene(sd)
@@ -75,13 +75,18 @@ def test_every_density_is_the_density_of_its_sampler(name, D):
     ref = np.array(cam_blk).mean(axis=0)
     assert np.all(np.abs(mean) <= 4.5 * se + 1e-9), (mean, se)
     tot_cam, tot_diff = ref.sum(axis=(0, 1)), mean.sum(axis=(0, 1))
-    assert np.all(np.abs(tot_diff) <= 0.03 * tot_cam), (tot_diff, tot_cam)
-    assert tot_cam[0] > 0.005 and tot_cam[1] > 0.1   # both techniques were exercised
+    # over the image: within 3%, or within 4 standard errors where the counts
+    # are rare (BSDF-sampled hits of small emitters: ~0.2% of paths)
+    se_tot = d.sum(axis=(1, 2)).std(axis=0, ddof=1) / np.sqrt(K)
+    assert np.all(np.abs(tot_diff) <= np.maximum(0.03 * tot_cam, 4.0 * se_tot)), (tot_diff, tot_cam, se_tot)
+    assert tot_cam[0] > 0.001 and tot_cam[1] > 0.1   # both techniques were exercised
 
 
-@pytest.mark.parametrize("lt_mode,mis_mode,sigma", [(0, 0, 0.5), (0, 1, 0.5), (1, 0, 0.5), (0, 0, 0.0)])
-def test_two_way_image_has_the_path_tracer_expectation(lt_mode, mis_mode, sigma):
-    sd, cam = _scene("glossy")
+@pytest.mark.parametrize("name,lt_mode,mis_mode,sigma", [("glossy", 0, 0, 0.5), ("glossy", 0, 1, 0.5),
+                                                        ("glossy", 1, 0, 0.5), ("glossy", 0, 0, 0.0),
+                                                        ("many", 0, 0, 0.5)])
+def test_two_way_image_has_the_path_tracer_expectation(name, lt_mode, mis_mode, sigma):
+    sd, cam = _scene(name)
     s = oracle.Scene(sd)
     K = 8
     blocks = []
