@@ -249,7 +249,8 @@ rt_status rt_render(const rt_scene *scene, const rt_camera *camera, uint32_t spp
  *   stats:    optional (paths, extension and shadow rays, kernel launches)
  * The call returns when the work is done (it synchronises `stream`).
  * Errors: RT_INVALID_ARG (null pointers, sizes, depth, modes),
- * RT_NOT_SUPPORTED (instanced scenes, a guide), RT_CUDA_ERROR. With the
+ * RT_NOT_SUPPORTED (a guide), RT_CUDA_ERROR. Instanced scenes work as
+ * rt_render's (emitters are (instance, triangle) pairs). With the
  * light hierarchy (Sec. 2.1.1) the camera stage's NEE draws through it and
  * every weight uses its probability; the light stage still emits by flux. */
 rt_status rt_render_two_way(const rt_scene *scene, const rt_camera *camera, uint32_t spp, uint32_t max_depth,

@@ -509,10 +509,6 @@ extern "C" rt_status rt_render_two_way(const rt_scene *s, const rt_camera *cam, 
     }
     if (lt_mode < 0 || lt_mode > 1) { set_error("rt_render_two_way: lt_mode must be 0 or 1"); return RT_INVALID_ARG; }
     if (o.guide) { set_error("rt_render_two_way: guiding is not combined with light tracing"); return RT_NOT_SUPPORTED; }
-    if (s->dev.two_level) {
-        set_error("rt_render_two_way: light tracing needs a single-level scene");
-        return RT_NOT_SUPPORTED;
-    }
     const uint64_t WH = (uint64_t)cam->width * cam->height;
     if (film->next_task % WH) {
         set_error("rt_render_two_way: the film must hold whole passes");

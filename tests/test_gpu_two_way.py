@@ -128,7 +128,32 @@ def test_two_way_refuses_what_it_does_not_combine():
         rt.rt_render_two_way(scene, cam, 1, 3, film, rt.make_opts(mis_mode=2))
     with pytest.raises(rt.RtError):
         rt.rt_render_two_way(scene, cam, 1, 3, film, lt_mode=2)
-    sdi, cami = scenes.instanced_field(n_meshes=2, n_instances=4, total_tris=2000, n_emissive=10, width=16,
-                                       height=16, min_tris=200, max_tris=1000)
-    with pytest.raises(rt.RtError):
-        rt.rt_render_two_way(rt.Scene(sdi), cami, 1, 3, rt.Film(16, 16))
+
+
+@pytest.mark.parametrize("light_bvh", [False, True])
+def test_instanced_two_way_has_the_path_tracers_expectation(light_bvh):
+    """Two-level scene (emitters are (instance, triangle) pairs): the combined
+    image against rt_render on the same scene, per 4 x 4 pixel block."""
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.instanced_field(n_meshes=6, n_instances=60, total_tris=30_000, n_emissive=300, width=32,
+                                     height=32, min_tris=200, max_tris=4000)
+    sd.light_bvh = light_bvh
+    scene = rt.Scene(sd)
+    K = 8
+    blocks = []
+    for k in range(K):
+        s, s2, c, sp, _ = two_way_gpu(sd, cam, 128, 3, first=k * 128, scene=scene)
+        blocks.append(((s + sp) / c[..., None]).reshape(8, 4, 8, 4, 3).mean(axis=(1, 3)))
+    blocks = np.array(blocks)
+    m_tw, se_tw = blocks.mean(axis=0), blocks.std(axis=0, ddof=1) / np.sqrt(K)
+    assert sp.sum() > 0.0
+    film = rt.Film(cam.width, cam.height)
+    film.seek(1 << 20)
+    rt.rt_render(scene, cam, 4096, 3, film)
+    S, S2, C = film.download()
+    mean, var = oracle.resolve(S, S2, C)
+    m_pt = mean.reshape(8, 4, 8, 4, 3).mean(axis=(1, 3))
+    se_pt = np.sqrt(var.reshape(8, 4, 8, 4, 3).mean(axis=(1, 3)) / 16.0)
+    z = np.abs(m_tw - m_pt) / np.sqrt(se_tw ** 2 + se_pt ** 2 + 1e-30)
+    assert z.max() < 4.5, z.max()
+    assert m_tw.mean() == pytest.approx(m_pt.mean(), rel=0.03)
