@@ -82,9 +82,13 @@ typedef struct {
     double th, asp, f;  /* tan(vfov / 2), W / H, focal length in pixels */
     uint32_t W, H;
     double sigma;       /* pixel filter (> 0 Gaussian, else box) */
+    double bc[3], br;   /* the scene's bounding sphere (environment photons) */
 } or_tw_cam;
 
-void or_tw_cam_init(const or_camera *c, double sigma, or_tw_cam *tc);
+/* camera frame and the scene's bounding sphere (centre and half diagonal of
+ * the box of its vertices); an environment direction is stored as a vertex
+ * with prim OR_MISS and x the unit direction towards the environment */
+void or_tw_cam_init(const or_scene *s, const or_camera *c, double sigma, or_tw_cam *tc);
 void or_tw_vertex_at(const or_scene *s, uint32_t prim, double b1, double b2, or_tw_vertex *v);
 /* area-measure densities of the three techniques for the path x[0] (eye) ..
  * x[k] (emitter) through pixel (px, py); p_lt is zero where the light tracer

@@ -150,7 +150,7 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
             ++*rays;
         }
         if (prim == OR_MISS) {
-            if (s->d.env && c->tw != 4) {
+            if (s->d.env) {
                 double Le[3];
                 or_env_lookup(s, d, Le);
                 double w = 1.0;
@@ -158,7 +158,17 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
                     if (mode == 3) w = 1.0;
                     else if (mode == 2) w = 0.0;
                     else w = has_env ? mis_weight(mode, prev_pdf, s->p_env * or_env_pdf_n(s, prev_ng, d)) : 1.0;
+                    if (c->tw && has_env) {
+                        double ph, pn, pl;
+                        memset(&X[v], 0, sizeof X[v]);
+                        X[v].prim = OR_MISS;
+                        for (int a = 0; a < 3; ++a) X[v].x[a] = d[a];
+                        or_tw_pdfs(s, &c->tc, X, (int)v, px, py, &ph, &pn, &pl);
+                        w = tw_camera_weight(c, ph, pn, pl);
+                        if (c->tw == 4 && pl > 0.0) L[0] += 1.0;   /* density check: count the hit */
+                    }
                 }
+                if (c->tw == 4) w = 0.0;
                 for (int a = 0; a < 3; ++a) L[a] += beta[a] * Le[a] * w;
             }
             break;
@@ -268,11 +278,17 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
                     }
                 }
             }
-            if (c->tw == 4 && tw_li >= 0 && pdf_l > 0.0 && dot3(wi, ng) > 0.0) {
+            if (c->tw == 4 && pdf_l > 0.0 && dot3(wi, ng) > 0.0) {
                 /* density check: count next-event samples that make a
                  * visible path the light tracer could make */
                 double sq = sqrt(ua), ph, pn, pl;
-                or_tw_vertex_at(s, (uint32_t)s->light_tri[tw_li], sq * (1.0 - ub), sq * ub, &X[v + 1]);
+                if (tw_li >= 0) {
+                    or_tw_vertex_at(s, (uint32_t)s->light_tri[tw_li], sq * (1.0 - ub), sq * ub, &X[v + 1]);
+                } else {
+                    memset(&X[v + 1], 0, sizeof X[v + 1]);
+                    X[v + 1].prim = OR_MISS;
+                    for (int a = 0; a < 3; ++a) X[v + 1].x[a] = wi[a];
+                }
                 or_tw_pdfs(s, &c->tc, X, (int)v + 1, px, py, &ph, &pn, &pl);
                 if (pl > 0.0) {
                     uint32_t sp; double st, sb1, sb2;
@@ -285,9 +301,15 @@ static void path_radiance(const ctx_t *c, uint64_t idx, uint32_t px,
                 or_bsdf_eval(albedo, rough, gw, nsa, wo, wi, f, &pdf_b);
                 if (pdf_b > 0.0) {
                     double w = mode == 2 ? 1.0 : mis_weight(mode, pdf_l, pdf_b);
-                    if (c->tw && us >= s->p_env) {
+                    if (c->tw) {
                         double sq = sqrt(ua), ph, pn, pl;
-                        or_tw_vertex_at(s, (uint32_t)s->light_tri[tw_li], sq * (1.0 - ub), sq * ub, &X[v + 1]);
+                        if (us >= s->p_env) {
+                            or_tw_vertex_at(s, (uint32_t)s->light_tri[tw_li], sq * (1.0 - ub), sq * ub, &X[v + 1]);
+                        } else {
+                            memset(&X[v + 1], 0, sizeof X[v + 1]);
+                            X[v + 1].prim = OR_MISS;
+                            for (int a = 0; a < 3; ++a) X[v + 1].x[a] = wi[a];
+                        }
                         or_tw_pdfs(s, &c->tc, X, (int)v + 1, px, py, &ph, &pn, &pl);
                         w = tw_camera_weight(c, pn, ph, pl);
                     }
@@ -448,7 +470,7 @@ void or_render_two_way(const or_scene *s, const or_camera *cam, uint32_t iter0, 
     ctx_t c;
     ctx_init(&c, s, cam, max_depth, opts);
     c.tw = 1 + lt_mode;
-    or_tw_cam_init(cam, opts->filter_sigma, &c.tc);
+    or_tw_cam_init(s, cam, opts->filter_sigma, &c.tc);
     int nth = opts->threads > 0 ? opts->threads : (int)sysconf(_SC_NPROCESSORS_ONLN);
     if (nth < 1) nth = 1;
     uint32_t H = cam->height;

@@ -17,8 +17,9 @@
  *     k >= 2 seen through pixel j: the camera path reaching xk by its
  *     BSDF-sampled continuation ("hit"), next-event estimation at x(k-1)
  *     ("nee"), and the light path x(k) .. x1 connected to x0 ("lt"); paths
- *     with k = 1 (an emitter seen directly) and paths ending in the
- *     environment have no light-tracer technique;
+ *     with k = 1 (an emitter or the environment seen directly) have no
+ *     light-tracer technique; for a path ending in the environment xk is a
+ *     direction and its densities are solid angles at x(k-1);
  *   - one camera path per pixel and iteration against W x H light paths per
  *     iteration: the sample counts in the heuristic are 1 and W H; the same
  *     power (beta 2) or balance heuristic as the two-technique path tracer;
@@ -30,9 +31,15 @@
  *     tracer adds its connection to every pixel whose centre lies within
  *     3 sigma of u (the box filter: the pixel that holds u) and its density
  *     is zero for the other pixels, so the truncation costs no bias;
- *   - light path: emitter by the alias table of the path tracer (flux
- *     proportional), point uniform on the triangle (the same warp as NEE),
- *     direction cosine-distributed about the emitter's normal; at a vertex
+ *   - light path: the environment with next-event estimation's probability
+ *     p_env, else a triangle emitter by the alias table (flux proportional),
+ *     point uniform on the triangle (the same warp as NEE), direction
+ *     cosine-distributed about the emitter's normal; an environment photon
+ *     takes a direction w from the plain pyramid and a uniform point of the
+ *     disk of radius r across the scene's bounding sphere (centre and half
+ *     diagonal of its vertices' box; Sec. 2.1.3 names uniform aiming at a
+ *     bound of the whole scene as the usual practice) and travels along
+ *     -w, so its first hit has area density p_env p(w) |cos| / (pi r^2); at a vertex
  *     the next direction is drawn by the BSDF sampler with the arriving
  *     direction in the role of wo (its adapted shading normal too); the
  *     throughput takes the adjoint's shading-normal factor |wi.ns| / |wi.ng|
@@ -85,7 +92,21 @@ static void unit_to(const double a[3], const double b[3], double out[3]) {
     normalize3(out);
 }
 
-void or_tw_cam_init(const or_camera *c, double sigma, or_tw_cam *tc) {
+void or_tw_cam_init(const or_scene *s, const or_camera *c, double sigma, or_tw_cam *tc) {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < 3 * s->nt; ++i)
+        for (int a = 0; a < 3; ++a) {
+            double v = s->v64[3 * i + a];
+            if (v < lo[a]) lo[a] = v;
+            if (v > hi[a]) hi[a] = v;
+        }
+    if (s->nt > 0) {
+        for (int a = 0; a < 3; ++a) tc->bc[a] = 0.5 * (lo[a] + hi[a]);
+        tc->br = 0.5 * sqrt(dist2(lo, hi));
+    } else {
+        tc->bc[0] = tc->bc[1] = tc->bc[2] = 0.0;
+        tc->br = 1.0;
+    }
     for (int a = 0; a < 3; ++a) tc->eye[a] = c->eye[a];
     double fwd[3] = {c->look_at[0] - c->eye[0], c->look_at[1] - c->eye[1], c->look_at[2] - c->eye[2]};
     normalize3(fwd);
@@ -170,10 +191,7 @@ static double cos_to(const or_tw_vertex *v, const double p[3]) {
  * point a as wo, draws the direction to point b: geometric normal turned to
  * wo, shading normal to its side and adapted for wo (Appendix A.3); zero
  * below the geometric tangent plane. */
-static double dir_pdf(const or_scene *s, const or_tw_vertex *v, const double a[3], const double b[3]) {
-    double wo[3], wi[3];
-    unit_to(v->x, a, wo);
-    unit_to(v->x, b, wi);
+static double dir_pdf_w(const or_scene *s, const or_tw_vertex *v, const double wo[3], const double wi[3]) {
     double ng[3] = {v->ng[0], v->ng[1], v->ng[2]};
     if (dot3(wo, ng) < 0.0) { ng[0] = -ng[0]; ng[1] = -ng[1]; ng[2] = -ng[2]; }
     if (!(dot3(wi, ng) > 0.0)) return 0.0;
@@ -186,6 +204,19 @@ static double dir_pdf(const or_scene *s, const or_tw_vertex *v, const double a[3
     double f[3], pdf;
     or_bsdf_eval(albedo, s->d.roughness[m], s->d.ggx_weight[m], nsa, wo, wi, f, &pdf);
     return pdf;
+}
+
+/* the same, towards points a (wo) and b (wi); an environment vertex holds
+ * its direction instead of a point */
+static void toward(const or_tw_vertex *v, const or_tw_vertex *p, double w[3]) {
+    if (p->prim == OR_MISS) { w[0] = p->x[0]; w[1] = p->x[1]; w[2] = p->x[2]; }
+    else unit_to(v->x, p->x, w);
+}
+static double dir_pdf(const or_scene *s, const or_tw_vertex *v, const or_tw_vertex *a, const or_tw_vertex *b) {
+    double wo[3], wi[3];
+    toward(v, a, wo);
+    toward(v, b, wi);
+    return dir_pdf_w(s, v, wo, wi);
 }
 
 /* Area pdf with which next-event estimation at x(k-1) (wo towards x(k-2))
@@ -201,9 +232,21 @@ static double nee_density(const or_scene *s, const or_tw_vertex *xm, const doubl
     return (1.0 - s->p_env) * or_lb_prob(s, xo, ng, s->light_of_tri[xk->prim]) / s->area[xk->prim];
 }
 
-/* Area pdf of the light tracer's emission point on triangle prim. */
+/* Area pdf of the light tracer's emission point on triangle prim: the
+ * triangle emitters are chosen with probability 1 - p_env (the environment
+ * with p_env, as in next-event estimation), then by flux. */
 static double lt_point_density(const or_scene *s, uint32_t prim) {
-    return s->light_prob[s->light_of_tri[prim]] / s->area[prim];
+    return (1.0 - s->p_env) * s->light_prob[s->light_of_tri[prim]] / s->area[prim];
+}
+
+/* Solid-angle pdf with which next-event estimation at xm (wo towards point
+ * `from`) picks environment direction w. */
+static double env_nee_density(const or_scene *s, const or_tw_vertex *xm, const double from[3], const double w[3]) {
+    double wo[3];
+    unit_to(xm->x, from, wo);
+    double ng[3] = {xm->ng[0], xm->ng[1], xm->ng[2]};
+    if (dot3(wo, ng) < 0.0) { ng[0] = -ng[0]; ng[1] = -ng[1]; ng[2] = -ng[2]; }
+    return s->p_env * or_env_pdf_n(s, ng, w);
 }
 
 void or_tw_pdfs(const or_scene *s, const or_tw_cam *tc, const or_tw_vertex *x, int k, uint32_t px, uint32_t py,
@@ -211,27 +254,40 @@ void or_tw_pdfs(const or_scene *s, const or_tw_cam *tc, const or_tw_vertex *x, i
     *p_hit = *p_nee = *p_lt = 0.0;
     if (k < 2) return;
     const or_tw_vertex *xk = &x[k];
-    double cy;
-    {
+    const int env = xk->prim == OR_MISS;   /* xk: a direction towards the environment */
+    double cy = 0.0;
+    if (!env) {
         double w[3];
         unit_to(xk->x, x[k - 1].x, w);
         cy = dot3(w, xk->ng);   /* the emitter radiates on its normal's side */
+        if (!(cy > 0.0)) return;
     }
-    if (!(cy > 0.0)) return;
     int lt_ok;
     double pc = cam_density(tc, &x[1], px, py, &lt_ok);
     /* camera techniques: the shared prefix x1 .. x(k-1) */
     double pre = pc;
     for (int i = 1; i <= k - 2; ++i)
-        pre *= dir_pdf(s, &x[i], x[i - 1].x, x[i + 1].x) * cos_to(&x[i + 1], x[i].x) / dist2(x[i].x, x[i + 1].x);
-    *p_hit = pre * dir_pdf(s, &x[k - 1], x[k - 2].x, xk->x) * cy / dist2(x[k - 1].x, xk->x);
-    *p_nee = pre * nee_density(s, &x[k - 1], x[k - 2].x, xk);
-    /* light tracer: emission point, cosine direction, then BSDF samples
-     * with the arriving direction as wo, down to x1 */
+        pre *= dir_pdf(s, &x[i], &x[i - 1], &x[i + 1]) * cos_to(&x[i + 1], x[i].x) / dist2(x[i].x, x[i + 1].x);
+    if (env) {
+        /* solid angle at x(k-1): the continuation's pdf, NEE's environment pdf */
+        *p_hit = pre * dir_pdf(s, &x[k - 1], &x[k - 2], xk);
+        *p_nee = pre * env_nee_density(s, &x[k - 1], x[k - 2].x, xk->x);
+    } else {
+        *p_hit = pre * dir_pdf(s, &x[k - 1], &x[k - 2], xk) * cy / dist2(x[k - 1].x, xk->x);
+        *p_nee = pre * nee_density(s, &x[k - 1], x[k - 2].x, xk);
+    }
+    /* light tracer: emission point and cosine direction (a triangle), or a
+     * direction and a point of the disk of the scene's bounding sphere
+     * across it (the environment); then BSDF samples with the arriving
+     * direction as wo, down to x1 */
     if (!lt_ok) return;
-    double pl = lt_point_density(s, xk->prim) * (cy / OR_PI) * cos_to(&x[k - 1], xk->x) / dist2(x[k - 1].x, xk->x);
+    double pl;
+    if (env)
+        pl = s->p_env * or_env_pdf(s, xk->x) * fabs(dot3(x[k - 1].ng, xk->x)) / (OR_PI * tc->br * tc->br);
+    else
+        pl = lt_point_density(s, xk->prim) * (cy / OR_PI) * cos_to(&x[k - 1], xk->x) / dist2(x[k - 1].x, xk->x);
     for (int i = k - 1; i >= 2; --i)
-        pl *= dir_pdf(s, &x[i], x[i + 1].x, x[i - 1].x) * cos_to(&x[i - 1], x[i].x) / dist2(x[i].x, x[i - 1].x);
+        pl *= dir_pdf(s, &x[i], &x[i + 1], &x[i - 1]) * cos_to(&x[i - 1], x[i].x) / dist2(x[i].x, x[i - 1].x);
     *p_lt = pl;
 }
 
@@ -265,29 +321,55 @@ static double ltdim(const lt_job *j, uint64_t m, int dim) {
 static void light_path(lt_job *j, uint64_t m, or_tw_vertex *V, or_tw_vertex *X) {
     const or_scene *s = j->s;
     const or_tw_cam *tc = &j->tc;
-    if (s->nlights <= 0) return;
+    if (s->nlights <= 0 && !(s->p_env > 0.0)) return;
     const double nL = (double)tc->W * (double)tc->H;
-    int64_t e = or_alias_sample(s->alias_prob, s->alias_idx, s->nlights, ltdim(j, m, j->base));
-    uint32_t lt = (uint32_t)s->light_tri[e];
-    double ua = ltdim(j, m, j->base + 1), ub = ltdim(j, m, j->base + 2);
-    double sq = sqrt(ua);
-    double b1 = sq * (1.0 - ub), b2 = sq * ub;
-    or_tw_vertex_at(s, lt, b1, b2, &V[0]);
-    double Le[3];
-    or_tri_emission(s, lt, b1, b2, Le);
-    double pa = lt_point_density(s, lt);
+    double us = ltdim(j, m, j->base), ua = ltdim(j, m, j->base + 1), ub = ltdim(j, m, j->base + 2);
     double u3 = ltdim(j, m, j->base + 3), u4 = ltdim(j, m, j->base + 4);
-    double t1[3], t2[3];
-    or_onb(V[0].ng, t1, t2);
-    double r = sqrt(u3), phi = 2.0 * OR_PI * u4, cz = sqrt(fmax(0.0, 1.0 - u3));
-    if (!(cz > 0.0)) return;
-    double dir[3];
-    for (int a = 0; a < 3; ++a) dir[a] = r * cos(phi) * t1[a] + r * sin(phi) * t2[a] + cz * V[0].ng[a];
-    normalize3(dir);
-    /* Le cos / (pa cos / pi) */
-    double beta[3] = {Le[0] * OR_PI / pa, Le[1] * OR_PI / pa, Le[2] * OR_PI / pa};
-    double o[3];
-    or_offset_origin(V[0].x, V[0].ng, o);
+    double beta[3], o[3], dir[3];
+    if (us < s->p_env) {
+        /* environment photon: a direction from the plain pyramid, then a
+         * uniform point of the disk of radius br across the bounding sphere,
+         * travelling back along the direction */
+        double w[3], pw;
+        int32_t tx, ty;
+        or_env_sample(s, ua, ub, w, &pw, &tx, &ty);
+        if (!(pw > 0.0)) return;
+        double Le[3];
+        or_env_lookup(s, w, Le);
+        memset(&V[0], 0, sizeof V[0]);
+        V[0].prim = OR_MISS;
+        for (int a = 0; a < 3; ++a) V[0].x[a] = w[a];
+        double t1[3], t2[3];
+        or_onb(w, t1, t2);
+        double r = tc->br * sqrt(u3), phi = 2.0 * OR_PI * u4;
+        for (int a = 0; a < 3; ++a) {
+            o[a] = tc->bc[a] + 2.0 * tc->br * w[a] + r * cos(phi) * t1[a] + r * sin(phi) * t2[a];
+            dir[a] = -w[a];
+        }
+        /* Le / (p_env pw |cos| / (pi br^2)) with |cos| taken at the hit */
+        double k = OR_PI * tc->br * tc->br / (s->p_env * pw);
+        for (int a = 0; a < 3; ++a) beta[a] = Le[a] * k;
+    } else {
+        double u2 = (us - s->p_env) / (1.0 - s->p_env);
+        if (u2 >= 1.0) u2 = nextafter(1.0, 0.0);
+        int64_t e = or_alias_sample(s->alias_prob, s->alias_idx, s->nlights, u2);
+        uint32_t lt = (uint32_t)s->light_tri[e];
+        double sq = sqrt(ua);
+        double b1 = sq * (1.0 - ub), b2 = sq * ub;
+        or_tw_vertex_at(s, lt, b1, b2, &V[0]);
+        double Le[3];
+        or_tri_emission(s, lt, b1, b2, Le);
+        double pa = lt_point_density(s, lt);
+        double t1[3], t2[3];
+        or_onb(V[0].ng, t1, t2);
+        double r = sqrt(u3), phi = 2.0 * OR_PI * u4, cz = sqrt(fmax(0.0, 1.0 - u3));
+        if (!(cz > 0.0)) return;
+        for (int a = 0; a < 3; ++a) dir[a] = r * cos(phi) * t1[a] + r * sin(phi) * t2[a] + cz * V[0].ng[a];
+        normalize3(dir);
+        /* Le cos / (pa cos / pi) */
+        for (int a = 0; a < 3; ++a) beta[a] = Le[a] * OR_PI / pa;
+        or_offset_origin(V[0].x, V[0].ng, o);
+    }
     for (uint32_t t = 1; t <= j->D; ++t) {
         uint32_t prim; double th, hb1, hb2;
         or_trace_one(s, o, dir, 0.0, INFINITY, 0, &prim, &th, &hb1, &hb2);
@@ -410,7 +492,7 @@ void or_light_trace(const or_scene *s, const or_camera *cam, uint32_t iter0, uin
     for (int t = 0; t < nth; ++t) {
         lt_job *j = &jobs[t];
         j->s = s;
-        or_tw_cam_init(cam, opts->filter_sigma, &j->tc);
+        or_tw_cam_init(s, cam, opts->filter_sigma, &j->tc);
         j->D = D; j->k = k; j->l = l; j->factors = factors; j->base = base;
         j->mode = opts->mis_mode;
         j->lt_mode = lt_mode;

@@ -1,6 +1,7 @@
 """Pins of the oracle's two-way path tracing (Sec. 2: a path tracer and a light
 tracer combined by multiple importance sampling):
 
+- (environment photons included: the scene open to a sky)
 - with the light tracer's density set to zero the camera stage, whose weights
   are products of area-measure densities over the stored vertices, is the
   path tracer of render.c, whose weights are a ratio of two solid-angle pdfs;
@@ -28,6 +29,10 @@ def _scene(name, res=16):
         sd, cam = scenes.cornell_box()
     elif name == "cornell-up":
         sd, cam = scenes.cornell_box(light="up")
+    elif name == "cornell-env":
+        # the box is open towards the camera: a sky lights it too
+        sd, cam = scenes.cornell_box()
+        sd = dataclasses.replace(sd, env=scenes.procedural_sky(32, 16, seed=3)[0])
     elif name == "glossy":
         sd, cam = scenes.glossy_room()
     else:
@@ -35,7 +40,8 @@ def _scene(name, res=16):
     return sd, dataclasses.replace(cam, width=res, height=res)
 
 
-@pytest.mark.parametrize("name,mis_mode", [("cornell", 0), ("cornell", 1), ("glossy", 0), ("many", 0)])
+@pytest.mark.parametrize("name,mis_mode", [("cornell", 0), ("cornell", 1), ("glossy", 0), ("many", 0),
+                                           ("cornell-env", 0)])
 def test_camera_stage_without_the_light_tracer_is_the_path_tracer(name, mis_mode):
     sd, cam = _scene(name)
     s = oracle.Scene(sd)
@@ -59,7 +65,8 @@ def _chunks(s, cam, spp, D, K, lt_mode, first=0, **kw):
 # The glossy room stops at depth 2: deeper, the ratio of the GGX pdfs of the
 # two directions of a vertex grows without bound at grazing angles and the
 # light tracer's mean converges too slowly for a short test.
-@pytest.mark.parametrize("name,D", [("cornell", 4), ("cornell-up", 3), ("glossy", 2), ("many", 2)])
+@pytest.mark.parametrize("name,D", [("cornell", 4), ("cornell-up", 3), ("glossy", 2), ("many", 2),
+                                    ("cornell-env", 2)])
 def test_every_density_is_the_density_of_its_sampler(name, D):
     sd, cam = _scene(name)
     s = oracle.Scene(sd)
@@ -84,7 +91,7 @@ def test_every_density_is_the_density_of_its_sampler(name, D):
 
 @pytest.mark.parametrize("name,lt_mode,mis_mode,sigma", [("glossy", 0, 0, 0.5), ("glossy", 0, 1, 0.5),
                                                         ("glossy", 1, 0, 0.5), ("glossy", 0, 0, 0.0),
-                                                        ("many", 0, 0, 0.5)])
+                                                        ("many", 0, 0, 0.5), ("cornell-env", 0, 0, 0.5)])
 def test_two_way_image_has_the_path_tracer_expectation(name, lt_mode, mis_mode, sigma):
     sd, cam = _scene(name)
     s = oracle.Scene(sd)
