@@ -40,6 +40,9 @@ struct TwParams {
     float R;          // splat radius in pixels (3 sigma); <= 0: box filter
     int base;         // first light-path sample dimension
     int lt_mode;      // 0: MIS; 1: the light tracer alone wherever it makes the path
+    V3 bc;            // the scene's bounding sphere: centre,
+    float br;         // radius (half the diagonal of its box),
+    float inv_disk;   // 1 / (pi br^2): area density of an environment photon's disk
 };
 
 struct TwCounters {
@@ -119,10 +122,15 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
                 int tx = env_texel(sc, s.d);
                 float4 e = ldg(sc.env + tx);
                 float w = 1.f;
-                if (v > 1)
-                    w = sc.p_env > 0.f
-                            ? mis_weight(mode, s.prev_pdf, sc.p_env * e.w * env_cell_factor(sc, s.prev_cell, tx))
-                            : 1.f;
+                if (v > 1 && sc.p_env > 0.f) {
+                    const float pn = sc.p_env * e.w * env_cell_factor(sc, s.prev_cell, tx);
+                    // light tracer / hit: x(v-1)'s factor, |cos| / (pi r^2) over
+                    // its camera density, times the photon's direction pdf
+                    // over the continuation's
+                    const float r_lt = Pi > 0.f ? T.nL * Pi * cprev * T.inv_disk * sc.p_env * e.w / s.prev_pdf : 0.f;
+                    if (T.lt_mode == 1) w = r_lt > 0.f ? 0.f : mis_weight(mode, s.prev_pdf, pn);
+                    else w = tw_weight(mode, pn / s.prev_pdf, r_lt);
+                }
                 s.L = s.L + mul(s.beta, v3(e.x, e.y, e.z)) * w;
             }
             break;
@@ -162,7 +170,7 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
                 const float r_nee = pa * t2 / (s.prev_pdf * vx.cog);
                 // light tracer / hit: the factor of x_v, (cos_y / pi) c / t^2,
                 // times the emitter's, pA_lt t^2 / (prev_pdf cos_y)
-                const float pa_lt = lpa / (1.f - sc.p_env);
+                const float pa_lt = lpa;   // the light tracer's area pdf (alias table, 1 - p_env)
                 float r_lt = Pi > 0.f ? T.nL * Pi * cprev * pa_lt / (kPi * s.prev_pdf) : 0.f;
                 if (T.lt_mode == 1) w = r_lt > 0.f ? 0.f : mis_weight(mode, s.prev_pdf, pa * t2 / vx.cog);
                 else w = tw_weight(mode, r_nee, r_lt);
@@ -179,7 +187,7 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
             NeePick pk = nee_pick<false>(P, s.index, base);
             const float us = pk.us, ua = pk.ua, ub = pk.ub;
             V3 wi = v3(0.f, 0.f, 1.f), Le = v3(0.f, 0.f, 0.f), sdir = wi;
-            float pdf_l = 0.f, tmax = INFINITY, cl = 0.f, dist = 0.f, lt_over_nee = 0.f;
+            float pdf_l = 0.f, tmax = INFINITY, cl = 0.f, dist = 0.f, lt_over_nee = 0.f, env_pw = 0.f;
             bool tri = false;
             if (us < sc.p_env) {
                 const uint32_t cell = env_cell(ng);
@@ -189,6 +197,7 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
                 float4 e = ldg(sc.env + tx);
                 Le = v3(e.x, e.y, e.z);
                 pdf_l = sc.p_env * e.w * env_cell_factor(sc, cell, tx);
+                env_pw = e.w;
             } else {
                 V3 l0 = pk.l0, l1 = pk.l1, l2 = pk.l2;
                 uint32_t lt = pk.lt, lmid = pk.lmid;
@@ -225,7 +234,7 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
                             tri = true;
                             // the light tracer's area pdf of the point (alias
                             // table) over next-event estimation's
-                            lt_over_nee = ldg(sc.tri_light_pdf_area + lt) / ((1.f - sc.p_env) * lpa_n);
+                            lt_over_nee = ldg(sc.tri_light_pdf_area + lt) / lpa_n;
                         } else {
                             pdf_l = 0.f;
                         }
@@ -247,6 +256,18 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
                             // x_v: emission cosine over pi, cos at x_v towards y
                             const float fv = (cl / kPi) * dot(wi, ng) / (dist * dist * Cd);
                             r_lt = T.nL * Pi * fv1 * fv * lt_over_nee;
+                        }
+                        if (T.lt_mode == 1) w = r_lt > 0.f ? 0.f : w;
+                        else w = tw_weight(mode, pdf_b / pdf_l, r_lt);
+                    } else {
+                        // an environment direction: x_v's factor |cos| / (pi r^2)
+                        // over its camera density, the photon's direction pdf
+                        // over NEE's
+                        float r_lt = 0.f;
+                        if (Pi > 0.f) {
+                            float fv1 = 1.f;
+                            if (v >= 2) fv1 = tw_dir_pdf(m, ng, vx.nsr, wi, wo) * cprev / t2;
+                            r_lt = T.nL * Pi * fv1 * (dot(wi, ng) * T.inv_disk / Cd) * sc.p_env * env_pw / pdf_l;
                         }
                         if (T.lt_mode == 1) w = r_lt > 0.f ? 0.f : w;
                         else w = tw_weight(mode, pdf_b / pdf_l, r_lt);
@@ -327,37 +348,62 @@ RT_D void tw_light_path(const RenderParams &P, const TwParams &T, uint64_t m, do
     const CameraView &cam = P.cam;
     const int mode = P.mis_mode;
     const float beta_exp = mode == 1 ? 1.f : 2.f;
-    // emission
-    const float u_sel = dim_value(P, m, T.base);
-    float xn = u_sel * (float)sc.num_lights;
-    uint32_t bin = (uint32_t)xn;
-    if (bin >= sc.num_lights) bin = sc.num_lights - 1;
-    const float frac = xn - (float)bin;
-    const float2 al = ldg(sc.alias + bin);
-    const uint32_t li = frac < al.x ? bin : as_uint(al.y);
-    const uint32_t lt = ldg(sc.light_tri + li);
-    const float4 *LV = sc.light_v + 3 * (size_t)li;
-    const V3 l0 = f4xyz(ldg(LV)), l1 = f4xyz(ldg(LV + 1)), l2 = f4xyz(ldg(LV + 2));
+    // emission: the environment with next-event estimation's probability
+    // p_env, else a triangle emitter by flux
+    const float us = dim_value(P, m, T.base);
     const float ua = dim_value(P, m, T.base + 1), ub = dim_value(P, m, T.base + 2);
-    const float sq = sqrtf(ua);
-    const float lb1 = sq * (1.f - ub), lb2 = sq * ub;
-    const V3 y = (1.f - sq) * l0 + lb1 * l1 + lb2 * l2;
-    const V3 lng = normalize(cross(l1 - l0, l2 - l0));
-    const float pa = ldg(sc.tri_light_pdf_area + lt) / (1.f - sc.p_env);   // the light tracer's area pdf
-    const V3 Le = tri_emission(sc, lt, ldg(sc.tri_material + lt), lb1, lb2);
     const float u3 = dim_value(P, m, T.base + 3), u4 = dim_value(P, m, T.base + 4);
-    const float ce = sqrtf(fmaxf(0.f, 1.f - u3));
-    if (!(ce > 0.f)) return;
-    V3 t1, t2;
-    onb(lng, t1, t2);
     float sphi, cphi;
     sincosf(2.f * kPi * u4, &sphi, &cphi);
-    const float rr = sqrtf(u3);
-    V3 dir = normalize(rr * cphi * t1 + rr * sphi * t2 + ce * lng);
-    V3 beta = Le * (kPi / pa);
-    V3 o = offset_origin(y, lng);
-    float q_prev = ce / kPi;     // pdf of the direction that made the pending ray
-    float pend = ce / pa;        // |cos| at the previous vertex toward this one over its light density
+    const bool env = us < sc.p_env;
+    V3 beta, o, dir;
+    float pa;            // the light tracer's pdf of the emission: area (triangle) or solid angle (environment)
+    float q_prev = 0.f;  // pdf of the direction that made the pending ray (triangle emission)
+    float pend = 0.f;    // |cos| at the previous vertex toward this one over its light density
+    uint32_t li = 0, lt = 0;
+    float env_pw = 0.f;
+    if (env) {
+        // a direction w from the plain pyramid, a uniform point of the disk
+        // of radius br across the bounding sphere, travelling along -w
+        const V3 w = env_sample(sc, ua, ub);
+        const float4 e = ldg(sc.env + env_texel(sc, w));
+        env_pw = e.w;
+        if (!(env_pw > 0.f)) return;
+        pa = sc.p_env * env_pw;
+        V3 t1, t2;
+        onb(w, t1, t2);
+        const float r = T.br * sqrtf(u3);
+        o = T.bc + (2.f * T.br) * w + (r * cphi) * t1 + (r * sphi) * t2;
+        dir = -w;
+        beta = v3(e.x, e.y, e.z) * (1.f / (pa * T.inv_disk));
+    } else {
+        float u2 = (us - sc.p_env) / (1.f - sc.p_env);
+        float xn = u2 * (float)sc.num_lights;
+        uint32_t bin = (uint32_t)xn;
+        if (bin >= sc.num_lights) bin = sc.num_lights - 1;
+        const float frac = xn - (float)bin;
+        const float2 al = ldg(sc.alias + bin);
+        li = frac < al.x ? bin : as_uint(al.y);
+        lt = ldg(sc.light_tri + li);
+        const float4 *LV = sc.light_v + 3 * (size_t)li;
+        const V3 l0 = f4xyz(ldg(LV)), l1 = f4xyz(ldg(LV + 1)), l2 = f4xyz(ldg(LV + 2));
+        const float sq = sqrtf(ua);
+        const float lb1 = sq * (1.f - ub), lb2 = sq * ub;
+        const V3 y = (1.f - sq) * l0 + lb1 * l1 + lb2 * l2;
+        const V3 lng = normalize(cross(l1 - l0, l2 - l0));
+        pa = ldg(sc.tri_light_pdf_area + lt);   // (1 - p_env) x flux share / area
+        const V3 Le = tri_emission(sc, lt, ldg(sc.tri_material + lt), lb1, lb2);
+        const float ce = sqrtf(fmaxf(0.f, 1.f - u3));
+        if (!(ce > 0.f)) return;
+        V3 t1, t2;
+        onb(lng, t1, t2);
+        const float rr = sqrtf(u3);
+        dir = normalize(rr * cphi * t1 + rr * sphi * t2 + ce * lng);
+        beta = Le * (kPi / pa);
+        o = offset_origin(y, lng);
+        q_prev = ce / kPi;
+        pend = ce / pa;
+    }
     float S = 0.f;               // sum over camera techniques of prod (C / L)^beta, finished vertices
     for (uint32_t t = 1; t <= P.max_depth; ++t) {
         Hit h;
@@ -375,12 +421,20 @@ RT_D void tw_light_path(const RenderParams &P, const TwParams &T, uint64_t m, do
         const V3 x = vx.x, ng = vx.ng, wi = vx.wo;
         const float cwi = fabsf(vx.cog);
         const float t2 = h.t * h.t;
-        const float Ld = q_prev * cwi / t2;   // light-tracer density of x
+        // light-tracer density of x (given the direction, for an environment photon)
+        const float Ld = (t == 1 && env) ? cwi * T.inv_disk : q_prev * cwi / t2;
+        // factor that turns the BSDF pdf at x towards the previous vertex into
+        // (camera density / light density) of that vertex
+        const float gfac = (t == 1 && env) ? 1.f / pa : pend / t2;
         const Material mat = load_material(sc, ldg(sc.tri_material + h.prim));
         const V3 xo = offset_origin(x, ng);
         // p_light of the emitter from x (next-event estimation's area pdf)
         float G_nee = 0.f;
-        if (t == 1) {
+        if (t == 1 && env) {
+            // next-event estimation's solid-angle pdf of the photon's direction from x
+            const uint32_t cell = env_cell(ng);
+            G_nee = sc.p_env * env_pw * env_cell_factor(sc, cell, env_texel(sc, wi)) / pa;
+        } else if (t == 1) {
             // next-event estimation's area pdf of the emission point from x
             float pl = ldg(sc.tri_light_pdf_area + lt);
             if (sc.lb_rec) pl = (1.f - sc.p_env) * lb_prob(sc, xo, oct_decode(oct_encode(ng)), li) / emitter_area(sc, li);
@@ -410,7 +464,7 @@ RT_D void tw_light_path(const RenderParams &P, const TwParams &T, uint64_t m, do
                     vis = hs.prim == RT_MISS;
                 }
                 if (vis) {
-                    const float G = b_i * pend / t2;
+                    const float G = b_i * gfac;
                     const float Sc = t == 1 ? powf(G, beta_exp) + powf(G_nee, beta_exp) : S * powf(G, beta_exp);
                     const float c1 = dot(we, ng);
                     const V3 base_c = mul(beta, f) * (fabsf(dot(wi, nsa)) / cwi);
@@ -459,7 +513,7 @@ RT_D void tw_light_path(const RenderParams &P, const TwParams &T, uint64_t m, do
         V3 fc;
         float b_n;
         bsdf_eval(mat, nsn, wn, wi, fc, b_n);
-        const float G = b_n * pend / t2;
+        const float G = b_n * gfac;
         S = t == 1 ? powf(G, beta_exp) + powf(G_nee, beta_exp) : S * powf(G, beta_exp);
         S = fminf(S, 1e30f);
         beta = mul(beta, fc) * (fabsf(dot(wi, nsn)) / cwi * dot(wn, ng) / q);
@@ -544,6 +598,15 @@ extern "C" rt_status rt_render_two_way(const rt_scene *s, const rt_camera *cam, 
     T.R = P.sigma > 0.f ? 3.f * P.sigma : 0.f;
     T.base = base;
     T.lt_mode = lt_mode;
+    {
+        const float3 lo = s->dev.bb_lo, hi = s->dev.bb_hi;
+        const double dx = (double)hi.x - lo.x, dy = (double)hi.y - lo.y, dz = (double)hi.z - lo.z;
+        const double r = 0.5 * std::sqrt(dx * dx + dy * dy + dz * dz);
+        T.bc = v3((float)(0.5 * ((double)lo.x + hi.x)), (float)(0.5 * ((double)lo.y + hi.y)),
+                  (float)(0.5 * ((double)lo.z + hi.z)));
+        T.br = r > 0.0 ? (float)r : 1.f;
+        T.inv_disk = (float)(1.0 / (3.14159265358979323846 * (double)T.br * T.br));
+    }
     const uint64_t n = (uint64_t)spp * WH;
     // One path per thread: with several paths per thread the lanes of a warp
     // drift apart (each starts its next path whenever its last one ends) and
@@ -551,7 +614,7 @@ extern "C" rt_status rt_render_two_way(const rt_scene *s, const rt_camera *cam, 
     const int grid = (int)std::min<uint64_t>((n + 127) / 128, 0x7FFFFFFFull);
     k_tw_camera<<<grid, 128, 0, st>>>(P, T, film->sum, film->sum2, film->count, (uint32_t)j0, n, ctr);
     RT_CUDA_TRY(cudaGetLastError());
-    if (P.sc.num_lights > 0) {
+    if (P.sc.num_lights > 0 || P.sc.p_env > 0.f) {
         double *dst = lt_splat ? lt_splat : film->sum;
         k_tw_light<<<grid, 128, 0, st>>>(P, T, dst, j0 * WH, n, ctr);
         RT_CUDA_TRY(cudaGetLastError());
@@ -567,7 +630,7 @@ extern "C" rt_status rt_render_two_way(const rt_scene *s, const rt_camera *cam, 
         stats->extension_rays = hc.ext_rays;
         stats->shadow_rays = hc.shadow_rays;
         stats->waves = 1;
-        stats->kernel_launches = P.sc.num_lights > 0 ? 2 : 1;
+        stats->kernel_launches = (P.sc.num_lights > 0 || P.sc.p_env > 0.f) ? 2 : 1;
     }
     return RT_OK;
 }

@@ -22,6 +22,11 @@ def _scene(name, res):
         sd, cam = scenes.glossy_room(res)
     elif name == "many":
         sd, cam = scenes.many_emitters(n_lights=64, res=res)   # light hierarchy
+    elif name == "cornell-env":
+        # open towards the camera and lit by a sky too: environment photons
+        sd, cam = scenes.cornell_box()
+        sd = dataclasses.replace(sd, env=scenes.procedural_sky(32, 16, seed=3)[0])
+        cam = dataclasses.replace(cam, width=res, height=res)
     else:
         sd, cam = scenes.cornell_box()
         cam = dataclasses.replace(cam, width=res, height=res)
@@ -43,7 +48,7 @@ def two_way_gpu(sd, cam, spp, depth, first=0, lt_mode=0, sigma=0.5, mis_mode=0, 
 
 @pytest.mark.parametrize("name,depth,lt_mode,mis_mode,sigma", [
     ("glossy", 3, 0, 0, 0.5), ("glossy", 3, 0, 1, 0.5), ("glossy", 3, 1, 0, 0.5), ("cornell", 4, 0, 0, 0.5),
-    ("cornell", 4, 0, 0, 0.0), ("many", 3, 0, 0, 0.5)])
+    ("cornell", 4, 0, 0, 0.0), ("many", 3, 0, 0, 0.5), ("cornell-env", 3, 0, 0, 0.5), ("cornell-env", 3, 1, 0, 0.5)])
 def test_two_way_matches_the_oracle_on_the_same_samples(name, depth, lt_mode, mis_mode, sigma):
     sd, cam = _scene(name, 32)
     s, s2, c, sp, stats = two_way_gpu(sd, cam, 64, depth, lt_mode=lt_mode, sigma=sigma, mis_mode=mis_mode)
@@ -67,11 +72,12 @@ def test_two_way_matches_the_oracle_on_the_same_samples(name, depth, lt_mode, mi
     assert SP.sum() > 0.05 * S.sum()   # the light stage carries part of the image
 
 
-def test_two_way_has_the_path_tracers_expectation():
+@pytest.mark.parametrize("name", ["glossy", "cornell-env"])
+def test_two_way_has_the_path_tracers_expectation(name):
     """The combined image (8 batches of 256 iterations) against rt_render at
     4096 iterations from a disjoint range, per 4 x 4 pixel block."""
     from paper_1705_01263_gb300 import rt
-    sd, cam = _scene("glossy", 32)
+    sd, cam = _scene(name, 32)
     scene = rt.Scene(sd)
     K = 8
     blocks = []
