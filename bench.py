@@ -494,7 +494,7 @@ def env_normal_vs_plain(sd, cam, scene, spp=16, ref_spp=1024, reps=3):
     return out
 
 
-def two_way_vs_plain(res=256, depth=4, spp=64, ref_spp=4096, reps=3):
+def two_way_vs_plain(res=256, depth=4, spp=64, ref_spp=4096, reps=3, scene_name="glossy"):
     """Two-way path tracing (Sec. 2: the light tracer as a third MIS
     technique, rt_render_two_way) against the path tracer (rt_render) in the
     glossy room lit through its ceiling, at equal iterations: RMSE against a
@@ -503,9 +503,18 @@ def two_way_vs_plain(res=256, depth=4, spp=64, ref_spp=4096, reps=3):
     two-way reaches equal error sooner)."""
     import torch
     from paper_1705_01263_gb300 import rt, scenes
-    sd, cam = scenes.glossy_room(res)
+    if scene_name == "glossy":
+        sd, cam = scenes.glossy_room(res)
+        what = f"glossy room lit through its ceiling, {res}x{res}"
+    else:
+        # the main scene, open and lit by the sky: environment photons spread
+        # over the disk across the whole bounding sphere (no photon aiming)
+        sd, cam = scenes.sphere_field()
+        cam.width, cam.height = 2 * res, res
+        what = f"sphere field (sky-lit, open), {2 * res}x{res}"
     scene = rt.Scene(sd)
     film = rt.Film(cam.width, cam.height)
+    npix = cam.width * cam.height
 
     def timed(fn):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -530,8 +539,7 @@ def two_way_vs_plain(res=256, depth=4, spp=64, ref_spp=4096, reps=3):
         return mean, ms, st
 
     ref, _, _ = two_way(1 << 22, ref_spp)
-    out = {"workload": f"glossy room lit through its ceiling, {res}x{res}, depth {depth}, {spp} iterations; "
-                       f"reference: two-way, {ref_spp} disjoint iterations"}
+    out = {"workload": f"{what}, depth {depth}, {spp} iterations; reference: two-way, {ref_spp} disjoint iterations"}
     for name, fn in (("path_tracer", plain), ("two_way", two_way)):
         fn(0, spp)   # warm-up
         err, ms = [], []
@@ -542,11 +550,11 @@ def two_way_vs_plain(res=256, depth=4, spp=64, ref_spp=4096, reps=3):
             ms.append(t)
         out[name] = {"rmse": statistics.mean(err), "ms": statistics.median(ms)}
         if st is not None:
-            paths = 2 * spp * res * res   # camera paths + light paths
+            paths = 2 * spp * npix   # camera paths + light paths
             out[name].update({"Mpaths_per_s": paths / (out[name]["ms"] / 1e3) / 1e6,
                               "Mrays_per_s": (st.extension_rays + st.shadow_rays) / (out[name]["ms"] / 1e3) / 1e6})
         else:
-            out[name]["Mpaths_per_s"] = spp * res * res / (out[name]["ms"] / 1e3) / 1e6
+            out[name]["Mpaths_per_s"] = spp * npix / (out[name]["ms"] / 1e3) / 1e6
     p_, t_ = out["path_tracer"], out["two_way"]
     out["rmse_ratio"] = t_["rmse"] / p_["rmse"]
     out["efficiency"] = (p_["rmse"] ** 2 * p_["ms"]) / (t_["rmse"] ** 2 * t_["ms"])
@@ -718,6 +726,8 @@ def main():
         return 0
     if args.two_way_once:
         print(json.dumps(two_way_vs_plain(spp=args.tw_spp, ref_spp=args.tw_ref_spp, reps=1)), flush=True)
+        print(json.dumps(two_way_vs_plain(res=270, depth=8, spp=16, ref_spp=256, reps=1, scene_name="spheres")),
+              flush=True)
         return 0
     if args.render_once:
         st = rt.rt_stats()
@@ -848,6 +858,7 @@ def main():
     tw = None
     if rank == 0 and not args.no_two_way:
         tw = two_way_vs_plain()
+        tw["open_scene"] = two_way_vs_plain(res=270, depth=8, spp=16, ref_spp=256, scene_name="spheres")
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_oracle(sd, cam)
