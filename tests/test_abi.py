@@ -320,3 +320,12 @@ def test_two_level_traversal_host_matches_flattened_oracle(kind):
     ii = np.where(hit, inst, 0).astype(np.int64)
     fp = np.where(hit, base[ii] + (p.astype(np.int64) - sd.mesh_tri_offset[sd.instance_mesh[ii]]), rt.RT_MISS)
     check_closest(flat, rays, (fp.astype(np.uint32), t, u, v), (po, to, uo, vo), min_agree=0.9999, t_rel=1e-4)
+
+
+def test_two_way_checks_its_arguments_on_the_host():
+    """rt_render_two_way (Sec. 2, two-way path tracing) refuses null scene,
+    camera or film before touching a device."""
+    L = rt.lib()
+    st = L.rt_render_two_way(None, None, 1, 3, None, None, 0, None, None, None)
+    assert rt.STATUS[st] == "RT_INVALID_ARG"
+    assert b"null argument" in L.rt_last_error()
