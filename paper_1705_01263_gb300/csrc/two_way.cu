@@ -1,17 +1,19 @@
 // Two-way path tracing (paper Sec. 2): the forward path tracer and a light
 // tracer run as separate stages with the same number of paths per iteration
 // and are combined by multiple importance sampling. The light tracer starts
-// on the triangle emitters in proportion to their flux (the emission that
-// Sec. 2.1.3's photon aiming improves on) and connects every vertex of a
-// light path to the pinhole camera, adding the connection to the pixels whose
-// filter reaches the image point.
+// on the environment with next-event estimation's probability p_env (a
+// direction from the plain pyramid, then a uniform point of the disk across
+// the scene's bounding sphere) or on a triangle emitter in proportion to its
+// flux (the emission that Sec. 2.1.3's photon aiming improves on), and
+// connects every vertex of a light path to the pinhole camera, adding the
+// connection to the pixels whose filter reaches the image point.
 //
-// Techniques for a path x0 (eye) .. xk (triangle emitter), k >= 2, through
-// pixel j: the camera path's BSDF-sampled hit of xk, next-event estimation at
-// x(k-1), and the light path xk .. x1 connected to x0; one camera path per
-// pixel against W H light paths per iteration; power or balance heuristic.
-// Paths with k = 1 and paths ending in the environment keep the path
-// tracer's two-technique weights.
+// Techniques for a path x0 (eye) .. xk (triangle emitter, or a direction
+// towards the environment), k >= 2, through pixel j: the camera path's
+// BSDF-sampled hit of xk, next-event estimation at x(k-1), and the light path
+// xk .. x1 connected to x0; one camera path per pixel against W H light
+// paths per iteration; power or balance heuristic. Paths with k = 1 (an
+// emitter or the sky seen directly) keep the path tracer's weights.
 //
 // Neither side stores its path. Each keeps two numbers between vertices:
 //  - camera side: Pi, the product over the finished vertices x1 .. x(v-1)
@@ -99,7 +101,7 @@ RT_HD float tw_filter(float sigma, float R, float dx, float dy, bool &ok) {
 // ------------------------------------------------------------ camera stage
 // One camera path (pixel, iteration j): the path tracer of shade()/scatter()
 // without guiding, with the light tracer as a third technique in the weights
-// of emitter hits and triangle NEE.
+// of emitter and environment hits and of next-event samples.
 RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel, uint32_t j, uint32_t &ext,
                        uint32_t &shadow) {
     const DevScene &sc = P.sc;
