@@ -224,16 +224,18 @@ rt_status rt_render(const rt_scene *scene, const rt_camera *camera, uint32_t spp
 
 /* Two-way path tracing (Sec. 2): the path tracer and a light-tracing stage
  * with the same number of paths per iteration (W x H), combined by multiple
- * importance sampling. The light tracer starts on the triangle emitters in
- * proportion to their flux, leaves them cosine-distributed, scatters by the
- * BSDF sampler and connects every vertex to the pinhole camera, adding the
- * connection to each pixel whose Gaussian filter centre lies within 3 sigma of
- * the image point (the box filter: the pixel that holds it). Techniques for a
- * path eye .. emitter with at least one scattering vertex: the camera path's
- * BSDF-sampled emitter hit, next-event estimation, and the light tracer's
- * camera connection (sample counts 1 per pixel against W x H); paths that see
- * an emitter directly or end in the environment keep the path tracer's
- * two-technique weights.
+ * importance sampling. The light tracer starts on the environment with
+ * next-event estimation's probability (a direction from the plain pyramid,
+ * then a uniform point of the disk across the scene's bounding sphere, Sec.
+ * 2.1.3's unaimed emission) or on a triangle emitter in proportion to its
+ * flux (cosine-distributed), scatters by the BSDF sampler and connects every
+ * vertex to the pinhole camera, adding the connection to each pixel whose
+ * Gaussian filter centre lies within 3 sigma of the image point (the box
+ * filter: the pixel that holds it). Techniques for a path eye .. emitter or
+ * environment with at least one scattering vertex: the camera path's
+ * BSDF-sampled hit, next-event estimation, and the light tracer's camera
+ * connection (sample counts 1 per pixel against W x H); paths that see an
+ * emitter or the environment directly keep the path tracer's weights.
  *   spp, max_depth, film: as rt_render; iterations continue from the film's
  *             next iteration, which must start a pass (RT_INVALID_ARG
  *             otherwise); the film's sums, sums of squares and counts receive
