@@ -156,3 +156,103 @@ def test_shading_normal_adaptation():
         if wo[2] < 5e-4:
             continue
         assert np.array_equal(oracle.adapt_shading_normal(ng, ng, wo), ng)
+
+
+def _schlick(c):
+    """Schlick's approximation with F0 = 0.04, the reading's Fresnel term."""
+    return 0.04 + 0.96 * (1.0 - min(1.0, max(0.0, c))) ** 5
+
+
+def test_fresnel_f0_is_dielectric_normal_incidence():
+    """F0 = 0.04 is the exact Fresnel reflectance at normal incidence of a
+    dielectric of refractive index 1.5, ((n - 1) / (n + 1))^2; the oracle's
+    mirror-limit albedo at normal incidence must equal it (computed here from
+    the index, not from the reading's constant)."""
+    n = 1.5
+    f0 = ((n - 1) / (n + 1)) ** 2
+    ns = np.array([0, 0, 1.0])
+    wo = np.array([0, 0, 1.0])
+    # roughness 0.01: alpha is clamped at 1e-4, a mirror for all purposes
+    good, wi, f, pdf = oracle.bsdf_sample(np.ones(3), 0.01, 1.0, ns, wo, 0.0, 0.25, 0.5)
+    assert good
+    assert f[0] * wi[2] / pdf == pytest.approx(f0, rel=1e-6)
+
+
+@pytest.mark.parametrize("theta_o", [0.0, 0.3, 0.6, 0.9, 1.2, 1.4])
+def test_ggx_mirror_limit_albedo_is_schlick(theta_o):
+    """Roughness -> 0: the GGX lobe becomes a mirror, D * G2 / (4 cos_o cos_i)
+    collapses to a delta and its directional albedo to the Fresnel factor at
+    the mirror angle, F(cos theta_o). Estimated with the oracle's own
+    visible-normal sampler on a stratified grid; a wrong F0, a wrong Fresnel
+    exponent or a wrong normalisation of the lobe fails it."""
+    ns = np.array([0, 0, 1.0])
+    wo = np.array([math.sin(theta_o), 0, math.cos(theta_o)])
+    m = 24
+    acc = 0.0
+    for i in range(m):
+        for j in range(m):
+            good, wi, f, pdf = oracle.bsdf_sample(np.ones(3), 0.02, 1.0, ns, wo, 0.0, (i + 0.5) / m, (j + 0.5) / m)
+            if good:
+                acc += f[0] * wi[2] / pdf
+    albedo = acc / (m * m)
+    assert albedo == pytest.approx(_schlick(math.cos(theta_o)), abs=1e-3)
+
+
+def test_ggx_G2_is_height_correlated():
+    """The masking-shadowing term inside the evaluated lobe, recovered as
+    G2 = f * 4 cos_o cos_i / (D F), must lie strictly above the separable
+    product G1(o) G1(i) and at most min(G1(o), G1(i)) at pairs away from the
+    normal (Heitz 2014: height correlation only ever adds visibility relative
+    to independent masking and shadowing). A separable G2 sits on the lower
+    bound and fails."""
+    rng = np.random.default_rng(11)
+    ns = np.array([0, 0, 1.0])
+    checked = 0
+    for _ in range(400):
+        rough = rng.uniform(0.2, 0.8)
+        alpha = rough * rough
+        to, ti = rng.uniform(0.35, 1.35, 2)
+        po, pi_ = rng.uniform(0, 2 * math.pi, 2)
+        wo = np.array([math.sin(to) * math.cos(po), math.sin(to) * math.sin(po), math.cos(to)])
+        wi = np.array([math.sin(ti) * math.cos(pi_), math.sin(ti) * math.sin(pi_), math.cos(ti)])
+        f, _ = oracle.bsdf_eval(np.ones(3), rough, 1.0, ns, wo, wi)
+        h = unit(wo + wi)
+        D = oracle.ggx_D(alpha, h[2])
+        F = _schlick(float(np.dot(wi, h)))
+        if D < 1e-8:
+            continue
+        G2 = f[0] * 4 * wo[2] * wi[2] / (D * F)
+        g1o, g1i = oracle.ggx_G1(alpha, wo[2]), oracle.ggx_G1(alpha, wi[2])
+        assert G2 > g1o * g1i * (1 + 1e-9), (rough, to, ti, G2, g1o * g1i)
+        assert G2 <= min(g1o, g1i) * (1 + 1e-12)
+        checked += 1
+    assert checked > 300
+    # along wi == wo the height-correlated form is 1 / (1 + 2 Lambda) while
+    # the separable one is 1 / (1 + Lambda)^2: both from G1 alone
+    for rough in (0.3, 0.6):
+        alpha = rough * rough
+        w = unit((0.7, 0.1, 0.5))
+        f, _ = oracle.bsdf_eval(np.ones(3), rough, 1.0, ns, w, w)
+        g1 = oracle.ggx_G1(alpha, w[2])
+        lam = 1.0 / g1 - 1.0
+        # h = normalize(w + w) = w, so D is taken at cos = w.z and F at wi.h = 1
+        G2 = f[0] * 4 * w[2] * w[2] / (oracle.ggx_D(alpha, w[2]) * _schlick(1.0))
+        assert G2 == pytest.approx(1.0 / (1.0 + 2.0 * lam), rel=1e-10)
+
+
+@pytest.mark.parametrize("rough,theta_o", [(0.3, 0.2), (0.5, 0.8), (0.8, 1.2), (0.4, 1.45)])
+def test_ggx_G1_normalises_visible_normals(rough, theta_o):
+    """The visible-normal identity integral D(m) G1(o) max(0, o.m) dm = cos theta_o
+    ties the oracle's Smith G1 to its D: a wrong Lambda (a dropped 1/2, a
+    missing alpha) breaks it."""
+    alpha = rough * rough
+    n_t, n_p = 4000, 720
+    ct = (np.arange(n_t) + 0.5) / n_t
+    D = np.array([oracle.ggx_D(alpha, c) for c in ct])
+    ph = 2 * np.pi * (np.arange(n_p) + 0.5) / n_p
+    st = np.sqrt(1 - ct * ct)
+    o = np.array([math.sin(theta_o), 0.0, math.cos(theta_o)])
+    om = np.maximum(0.0, o[0] * st[:, None] * np.cos(ph)[None, :] + o[2] * ct[:, None])
+    integral = (D[:, None] * om).sum() * (1.0 / n_t) * (2 * np.pi / n_p)
+    g1 = oracle.ggx_G1(alpha, o[2])
+    assert g1 * integral == pytest.approx(o[2], rel=2e-3)
