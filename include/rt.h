@@ -183,8 +183,16 @@ rt_status rt_scene_info(const rt_scene *scene, int64_t *nodes, int64_t *leaf_tri
 /* ---------------------------------------------------------------- trace */
 /* rays -> hits (Sec. 3.1, the ray-casting state kernels). Closest hit when
  * any_hit == 0 (ties in t: lower (inst, prim) wins); otherwise any hit in
- * (tmin, tmax) and prim != RT_MISS iff occluded. Asynchronous on `stream`.
- * n == 0 is a no-op. */
+ * (tmin, tmax) and prim != RT_MISS iff occluded. The kernel runs on
+ * `stream`; its ray-fetch counter and overflow flag are this call's own (8
+ * bytes from the stream-ordered allocator, released on the stream), so calls
+ * in flight on different streams or host threads do not interfere. The call
+ * waits for its kernel before returning, so that it can report
+ * RT_STACK_OVERFLOW: a ray whose traversal needed more than the fixed stack
+ * (48 node groups; BVHs built by rt_scene_create stay far below it) has an
+ * incomplete hit. n == 0 is a no-op. Errors: RT_INVALID_ARG (null scene,
+ * rays or hit pointers, n < 0 or n >= 2^32, host-only scene),
+ * RT_STACK_OVERFLOW, RT_CUDA_ERROR. */
 rt_status rt_trace(const rt_scene *scene, const rt_rays *rays, int64_t n, const rt_hits *hits,
                    int32_t any_hit, void *stream);
 
@@ -284,18 +292,25 @@ rt_status rt_render_probes(const rt_scene *scene, const float *pos, const float 
  * which an allocation would synchronise the device. Same estimator and
  * kernels as rt_render, but the path-state pool (at most 65,536 paths in
  * flight), control block and sampling table live in one file-scope device
- * array of about 9.6 MB that every device loading the library holds until
- * the process exits. The caller passes the scene (created earlier with
- * rt_scene_create) and owns the outputs: DEVICE buffers sum and sum2 (H*W*3
- * doubles) and count (H*W uint32), which are accumulated into, so zero them
- * before the first call. Renders iterations [first_iteration,
- * first_iteration + spp). opts may be NULL; opts->max_paths_in_flight above
- * 65,536 is rejected with RT_INVALID_ARG; guiding is RT_NOT_SUPPORTED.
- * The first call on a device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture. Every call reuses the same array: calls that overlap on the GPU
+ * array of RT_STATIC_ARENA_BYTES (9.91 MiB) that every device loading the
+ * library holds until the process exits. The caller passes the scene
+ * (created earlier with rt_scene_create) and owns the outputs: DEVICE
+ * buffers sum and sum2 (H*W*3 doubles) and count (H*W uint32), which are
+ * accumulated into, so zero them before the first call. Renders iterations
+ * [first_iteration, first_iteration + spp). opts may be NULL;
+ * opts->max_paths_in_flight above 65,536 is rejected with RT_INVALID_ARG;
+ * guiding and the sorted-queue options are RT_NOT_SUPPORTED.
+ * Every call looks up the array's device address in the current context
+ * (cudaGetSymbolAddress, which allocates nothing); the first call on a
+ * device sets up that lookup, so make it before any stream capture. Every
+ * call reuses the same array (the control block is cleared and the sampling
+ * table rewritten at the start of each call): calls that overlap on the GPU
  * (other streams, other host threads) race and must not be issued. Blocking
- * with respect to the host, like rt_render. */
+ * with respect to the host, like rt_render. The time budget and abort flag
+ * are checked where an iteration is complete only: on RT_TIMEOUT the sums
+ * hold iterations [first_iteration, first_iteration + stats.paths / (W H)),
+ * and the caller resumes from there. */
+#define RT_STATIC_ARENA_BYTES 10388480u
 rt_status rt_render_static(const rt_scene *scene, const rt_camera *camera, uint32_t spp, uint32_t max_depth,
                            uint32_t first_iteration, double *sum, double *sum2, uint32_t *count,
                            const rt_render_opts *opts, void *stream);

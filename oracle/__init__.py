@@ -471,6 +471,16 @@ def mlp_forward(params, x):
     return out
 
 
+def mlp_forward_acts(params, x):
+    """Outputs [n][40] and the four hidden activations [n][4][64]."""
+    p = _f64(params)
+    x = np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1, 224))
+    out = np.zeros((x.shape[0], 40))
+    acts = np.zeros((x.shape[0], 4, 64))
+    lib().or_mlp_forward(_p(p), _p(x), x.shape[0], _p(out), _p(acts))
+    return out, acts
+
+
 def mixture_pdf(raw, w):
     return lib().or_mixture_pdf(_p(_f64(raw, 40)), _p(_f64(w, 3)))
 

@@ -184,6 +184,41 @@ extern "C" rt_status rt_debug_trace_host(const rt_scene *s, const float *rays, i
     return RT_OK;
 }
 
+/* Host execution of the single-level traversal with a stack of only
+ * `stack_entries` (1..48) node groups: the overflow path of the kernels'
+ * traversal (a ray that needs more entries ends and the call returns
+ * RT_STACK_OVERFLOW) made reachable on small scenes. Otherwise as
+ * rt_debug_trace_host. */
+extern "C" rt_status rt_debug_trace_host_stack(const rt_scene *s, const float *rays, int64_t n, int32_t any_hit,
+                                               int32_t stack_entries, uint32_t *prim, float *t) {
+    if (!s || !s->host_only || n < 0 || !prim || !t || (n > 0 && !rays)) {
+        set_error("rt_debug_trace_host_stack: needs a host-only scene and outputs");
+        return RT_INVALID_ARG;
+    }
+    if (s->host.two_level) { set_error("rt_debug_trace_host_stack: single-level scenes only"); return RT_INVALID_ARG; }
+    if (stack_entries < 1 || stack_entries > kStackSize) {
+        set_error("rt_debug_trace_host_stack: stack_entries must be in [1, 48]");
+        return RT_INVALID_ARG;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        const float *r = rays + 8 * i;
+        Ray ray{v3(r[0], r[1], r[2]), v3(r[3], r[4], r[5]), r[6], r[7]};
+        Hit h;
+        h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
+        BoundedStack stack;
+        stack.cap = stack_entries;
+        TraceResult tr = any_hit ? traverse<true, BoundedStack>(s->host.nodes, s->host.tris, 0u, ray, h, 0u, &stack)
+                                 : traverse<false, BoundedStack>(s->host.nodes, s->host.tris, 0u, ray, h, 0u, &stack);
+        if (tr.overflow) {
+            set_error("BVH traversal stack overflow (ray " + std::to_string(i) + ")");
+            return RT_STACK_OVERFLOW;
+        }
+        prim[i] = h.prim;
+        t[i] = h.prim == RT_MISS ? INFINITY : h.t;
+    }
+    return RT_OK;
+}
+
 /* Host execution of the environment's NEE sampling (Sec. 2.1.2): for n
  * vertices with geometric normals ng (n x 3) and sample pairs (u, v), the
  * direction drawn for the normal's cell (wi, n x 3), the normal cell, and the

@@ -504,6 +504,38 @@ extern "C" rt_status rt_debug_guide_infer_layers(const rt_guide *gc, const float
     return check_err(g, st);
 }
 
+namespace rtg {
+// The device mixture code of guided shading on given raw outputs: the
+// density at wi, a direction drawn with (u_sel, u1, u2), and the density at
+// that direction.
+__global__ void k_debug_mixture(const float *raw, const float *wi, const float *u, int64_t n, float *pdf_wi,
+                                float *ws, float *pdf_ws) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        Mixture m;
+        decode_mixture(raw + kGuideOut * i, m);
+        pdf_wi[i] = mixture_pdf(m, v3(wi[3 * i], wi[3 * i + 1], wi[3 * i + 2]));
+        const V3 w = mixture_sample(m, u[3 * i], u[3 * i + 1], u[3 * i + 2]);
+        ws[3 * i] = w.x; ws[3 * i + 1] = w.y; ws[3 * i + 2] = w.z;
+        pdf_ws[i] = mixture_pdf(m, w);
+    }
+}
+}  // namespace rtg
+
+/* Test hook: the device-side von Mises-Fisher mixture of guided shading
+ * (decode, density, sampling) on DEVICE arrays raw [n][40], wi [n][3],
+ * u [n][3] (lobe select, u1, u2) -> pdf_wi [n], ws [n][3], pdf_ws [n]. */
+extern "C" rt_status rt_debug_guide_mixture(const float *raw, const float *wi, const float *u, int64_t n,
+                                            float *pdf_wi, float *ws, float *pdf_ws, void *stream) {
+    if (n < 0 || (n > 0 && (!raw || !wi || !u || !pdf_wi || !ws || !pdf_ws))) {
+        set_error("rt_debug_guide_mixture: invalid argument");
+        return RT_INVALID_ARG;
+    }
+    if (n == 0) return RT_OK;
+    k_debug_mixture<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(raw, wi, u, n, pdf_wi, ws, pdf_ws);
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
 extern "C" rt_status rt_guide_loss_grad(const rt_guide *gc, const float *features, const float *wi, const float *weight,
                                         int64_t n, float *grad, float *loss, void *stream) {
     rt_guide *g = const_cast<rt_guide *>(gc);

@@ -1048,21 +1048,35 @@ extern "C" rt_status rt_trace(const rt_scene *s, const rt_rays *rays, int64_t n,
         return RT_INVALID_ARG;
     }
     if (n > 0xFFFFFFFFll) { set_error("rt_trace: at most 2^32 - 1 rays per call"); return RT_INVALID_ARG; }
-    // per-device scratch: ray fetch counter and overflow flag
-    static uint32_t *scratch[64] = {nullptr};
-    int dev = 0;
-    RT_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) { set_error("rt_trace: device index out of range"); return RT_INVALID_ARG; }
-    if (!scratch[dev]) RT_CUDA_TRY(cudaMalloc(&scratch[dev], 2 * sizeof(uint32_t)));
+    // Scratch of this call only (ray fetch counter, overflow flag), taken
+    // from the stream-ordered allocator: calls in flight on different streams
+    // never share a counter. The overflow flag comes back to the host, so the
+    // call waits for its kernel before it returns.
     cudaStream_t st = (cudaStream_t)stream;
-    RT_CUDA_TRY(cudaMemsetAsync(scratch[dev], 0, 2 * sizeof(uint32_t), st));
+    uint32_t *scratch = nullptr;
+    RT_CUDA_TRY(cudaMallocAsync(&scratch, 2 * sizeof(uint32_t), st));
+    struct Release {
+        uint32_t *p;
+        cudaStream_t st;
+        ~Release() { if (p) cudaFreeAsync(p, st); }
+    } release{scratch, st};
+    RT_CUDA_TRY(cudaMemsetAsync(scratch, 0, 2 * sizeof(uint32_t), st));
     const int gb = 128;
     using UserFn = void (*)(DevScene, rt_rays, uint32_t, rt_hits, uint32_t *);
     const UserFn fn = any_hit ? (s->dev.two_level ? (UserFn)k_trace_user<true, true> : (UserFn)k_trace_user<true, false>)
                               : (s->dev.two_level ? (UserFn)k_trace_user<false, true> : (UserFn)k_trace_user<false, false>);
     const int g = grid_persistent(fn, gb, 0);
-    fn<<<g, gb, 0, st>>>(s->dev, *rays, (uint32_t)n, *hits, scratch[dev]);
+    fn<<<g, gb, 0, st>>>(s->dev, *rays, (uint32_t)n, *hits, scratch);
     RT_CUDA_TRY(cudaGetLastError());
+    uint32_t overflow = 0;
+    RT_CUDA_TRY(cudaMemcpyAsync(&overflow, scratch + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    release.p = nullptr;
+    RT_CUDA_TRY(cudaFreeAsync(scratch, st));
+    RT_CUDA_TRY(cudaStreamSynchronize(st));
+    if (overflow) {
+        set_error("rt_trace: BVH traversal stack overflow (hits of the affected rays are incomplete)");
+        return RT_STACK_OVERFLOW;
+    }
     return RT_OK;
 }
 
@@ -1506,26 +1520,22 @@ constexpr size_t kStaticU32Bytes = align_up(sizeof(uint32_t) * kStaticMaxPaths);
 constexpr size_t kStaticPixel = kStaticIndex + align_up(sizeof(uint2) * kStaticMaxPaths);
 constexpr size_t kStaticHitInst = kStaticPixel + kStaticU32Bytes;
 constexpr size_t kStaticQueues = kStaticHitInst + kStaticU32Bytes;
-constexpr size_t kStaticBytes = kStaticQueues + 3 * kStaticU32Bytes;   // about 9.9 MiB
+constexpr size_t kStaticBytes = kStaticQueues + 3 * kStaticU32Bytes;   // 9.91 MiB
+static_assert(kStaticBytes == RT_STATIC_ARENA_BYTES, "include/rt.h states the static array's size");
 
 static __device__ __align__(256) unsigned char g_static_arena[kStaticBytes];
 
-// Device address of g_static_arena per device. In host code the symbol name is
-// only a host-side stand-in, so the address is looked up once per device,
-// with that device current, and cached.
-static unsigned char *g_static_addr[64] = {nullptr};
-
+// Device address of g_static_arena in the current context. In host code the
+// symbol name is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress on every call (after the first call on a device this
+// is a host-side table lookup that allocates nothing). It is not cached: a
+// cached address would go stale after cudaDeviceReset or belong to another
+// context when the caller switches to a non-primary context.
 static rt_status static_arena(unsigned char **out) {
-    int dev = 0;
-    RT_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) { set_error("rt_render_static: device index out of range"); return RT_INVALID_ARG; }
-    if (!g_static_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_arena);
-        if (e != cudaSuccess || !p) return cuda_status(e, "cudaGetSymbolAddress(g_static_arena)");
-        g_static_addr[dev] = (unsigned char *)p;
-    }
-    *out = g_static_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_arena);
+    if (e != cudaSuccess || !p) return cuda_status(e, "cudaGetSymbolAddress(g_static_arena)");
+    *out = (unsigned char *)p;
     return RT_OK;
 }
 
@@ -1651,6 +1661,10 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
     if (opts_in) o = *opts_in;
     if (!valid_block(o.block_size)) { set_error("rt_render_static: block_size must be 0 or a multiple of 32 up to 128"); return RT_INVALID_ARG; }
     if (o.guide) { set_error("rt_render_static: guiding needs rt_render"); return RT_NOT_SUPPORTED; }
+    if (o.sort_by_material || o.sort_rays) {
+        set_error("rt_render_static: sorted queues need buffers of their own (use rt_render)");
+        return RT_NOT_SUPPORTED;
+    }
     if (o.max_paths_in_flight > kStaticMaxPaths) {
         set_error("rt_render_static: max_paths_in_flight exceeds the static pool of 65536 paths");
         return RT_INVALID_ARG;
@@ -1744,8 +1758,12 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
         ++stats.waves;
         if (host_ctrl.overflow) { set_error("BVH traversal stack overflow"); result = RT_STACK_OVERFLOW; break; }
         double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-        if (t < t_end && ((o.abort_flag && *o.abort_flag) || (o.time_budget_ms > 0 && ms >= o.time_budget_ms))) {
-            set_error("rt_render_static: stopped by time budget or abort flag (resume at the next iteration set)");
+        // stop only where an iteration is complete: the caller resumes at
+        // first_iteration + stats.paths / (W H) without repeating samples
+        if (t < t_end && t % WH == 0 &&
+            ((o.abort_flag && *o.abort_flag) || (o.time_budget_ms > 0 && ms >= o.time_budget_ms))) {
+            set_error("rt_render_static: stopped by time budget or abort flag (resume at first_iteration + "
+                      "stats.paths / (width * height))");
             result = RT_TIMEOUT;
             break;
         }

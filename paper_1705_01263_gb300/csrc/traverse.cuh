@@ -349,6 +349,15 @@ struct TraceResult {
 struct LocalStack {
     uint2 e[kStackSize];
     RT_HD uint2 &operator[](int i) { return e[i]; }
+    RT_HD static constexpr int capacity() { return kStackSize; }
+};
+// Thread-local stack with fewer usable entries than kStackSize (host test
+// hook: drives the overflow path of the traversal on small scenes).
+struct BoundedStack {
+    uint2 e[kStackSize];
+    int cap;
+    RT_HD uint2 &operator[](int i) { return e[i]; }
+    RT_HD int capacity() const { return cap; }
 };
 #ifdef __CUDACC__
 // Traversal stack whose top kSharedEntries entries live in shared memory,
@@ -361,6 +370,7 @@ struct SharedStack {
     int stride;
     uint2 deep[kStackSize - kSharedEntries];
     __device__ uint2 &operator[](int i) { return i < kSharedEntries ? base[i * stride] : deep[i - kSharedEntries]; }
+    __device__ static constexpr int capacity() { return kStackSize; }
 };
 #endif
 
@@ -399,7 +409,7 @@ struct Traversal {
             uint32_t child = ng.x + rel;
             ng.y &= ~(1u << bit);
             if (ng.y & 0xFF000000u) {
-                if (sp == kStackSize) { res.overflow = true; return false; }
+                if (sp == stack.capacity()) { res.overflow = true; return false; }
                 stack[sp++] = ng;
             }
             const uint4 *N = nodes + 5 * (size_t)child;

@@ -578,10 +578,17 @@ extern "C" rt_status rt_render_two_way(const rt_scene *s, const rt_camera *cam, 
     const int base = 2 + 7 * (int)(max_depth + 1);
     const int ndims = base + 5 + 3 * (int)max_depth;
     std::vector<HaltonDim> dims = make_dims(o.seed, ndims);
-    HaltonDim *dd = nullptr;
-    TwCounters *ctr = nullptr;
-    RT_CUDA_TRY(cudaMallocAsync(&dd, dims.size() * sizeof(HaltonDim), st));
-    RT_CUDA_TRY(cudaMallocAsync(&ctr, sizeof(TwCounters), st));
+    // the dimension table and counters live for this call only; every exit
+    // path, the error returns included, releases them on the stream
+    struct Scoped {
+        void *p = nullptr;
+        cudaStream_t st;
+        ~Scoped() { if (p) cudaFreeAsync(p, st); }
+    } dd_mem{nullptr, st}, ctr_mem{nullptr, st};
+    RT_CUDA_TRY(cudaMallocAsync(&dd_mem.p, dims.size() * sizeof(HaltonDim), st));
+    RT_CUDA_TRY(cudaMallocAsync(&ctr_mem.p, sizeof(TwCounters), st));
+    HaltonDim *dd = (HaltonDim *)dd_mem.p;
+    TwCounters *ctr = (TwCounters *)ctr_mem.p;
     RT_CUDA_TRY(cudaMemcpyAsync(dd, dims.data(), dims.size() * sizeof(HaltonDim), cudaMemcpyHostToDevice, st));
     RT_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(TwCounters), st));
     RenderParams P;
@@ -623,6 +630,7 @@ extern "C" rt_status rt_render_two_way(const rt_scene *s, const rt_camera *cam, 
     }
     TwCounters hc{};
     RT_CUDA_TRY(cudaMemcpyAsync(&hc, ctr, sizeof(TwCounters), cudaMemcpyDeviceToHost, st));
+    dd_mem.p = ctr_mem.p = nullptr;
     RT_CUDA_TRY(cudaFreeAsync(dd, st));
     RT_CUDA_TRY(cudaFreeAsync(ctr, st));
     RT_CUDA_TRY(cudaStreamSynchronize(st));

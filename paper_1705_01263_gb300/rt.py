@@ -135,12 +135,14 @@ def _declare(L):
         "rt_divide_u64_host": [vp, i64, u32, vp],
         "rt_gemm_bf16": [vp, vp, vp, i32, i32, i32, i32, i32, i32, i32, vp],
         "rt_debug_trace_host": [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp],
+        "rt_debug_trace_host_stack": [vp, vp, i64, i32, i32, vp, vp],
         "rt_debug_env_sample_host": [vp, vp, vp, vp, i64, vp, vp, vp],
         "rt_debug_light_bvh_host": [vp, vp, vp, vp, i64, vp, vp, vp],
         "rt_debug_render_host": [vp, C.POINTER(rt_camera), u32, C.POINTER(rt_render_opts), vp, vp, vp, i64, vp],
         "rt_debug_halton_host": [u32, u32, u64, vp, i64, i32, vp],
         "rt_debug_sample_index_host": [u32, u32, u32, u32, u32, C.POINTER(u64)],
         "rt_debug_guide_infer_layers": [vp, vp, i64, vp, vp],
+        "rt_debug_guide_mixture": [vp, vp, vp, i64, vp, vp, vp, vp],
         "rt_debug_render_probes_host": [vp, vp, vp, u32, u32, C.POINTER(rt_render_opts), vp, vp, i64, vp],
         "rt_render_probes": [vp, vp, vp, u32, u32, u32, vp, C.POINTER(rt_render_opts), vp],
         "rt_render_two_way": [vp, C.POINTER(rt_camera), u32, u32, vp, C.POINTER(rt_render_opts), C.c_int32, vp,
@@ -550,6 +552,20 @@ class Guide:
             pass
 
 
+def debug_guide_mixture(raw, wi, u, stream=None):
+    """Test hook: (pdf at wi, sampled direction, pdf at it) from the device
+    mixture code of guided shading; torch CUDA float32 inputs [n][40],
+    [n][3], [n][3]."""
+    import torch
+    n = raw.shape[0]
+    pdf_wi = torch.empty(n, dtype=torch.float32, device=raw.device)
+    ws = torch.empty((n, 3), dtype=torch.float32, device=raw.device)
+    pdf_ws = torch.empty(n, dtype=torch.float32, device=raw.device)
+    check(lib().rt_debug_guide_mixture(raw.data_ptr(), wi.data_ptr(), u.data_ptr(), n, pdf_wi.data_ptr(),
+                                       ws.data_ptr(), pdf_ws.data_ptr(), _stream(stream)))
+    return pdf_wi, ws, pdf_ws
+
+
 # -------------------------------------------------- host test hooks (CPU)
 def debug_trace_host(scene: Scene, rays: np.ndarray, any_hit: bool = False, return_inst: bool = False):
     r = np.ascontiguousarray(rays, np.float32)
@@ -563,6 +579,18 @@ def debug_trace_host(scene: Scene, rays: np.ndarray, any_hit: bool = False, retu
     if return_inst:
         return prim, t, u, v, nodes, inst
     return prim, t, u, v, nodes
+
+
+def debug_trace_host_stack(scene: Scene, rays: np.ndarray, stack_entries: int, any_hit: bool = False):
+    """(prim, t) of the traversal run on the host with a stack of only
+    `stack_entries` node groups; RtError(RT_STACK_OVERFLOW) when a ray needs more."""
+    r = np.ascontiguousarray(rays, np.float32)
+    n = r.shape[0]
+    prim = np.zeros(n, np.uint32)
+    t = np.zeros(n, np.float32)
+    check(lib().rt_debug_trace_host_stack(scene.handle, r.ctypes.data, n, int(any_hit), int(stack_entries),
+                                          prim.ctypes.data, t.ctypes.data))
+    return prim, t
 
 
 def debug_env_sample_host(scene: Scene, ng, u, v):

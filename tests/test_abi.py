@@ -329,3 +329,49 @@ def test_two_way_checks_its_arguments_on_the_host():
     st = L.rt_render_two_way(None, None, 1, 3, None, None, 0, None, None, None)
     assert rt.STATUS[st] == "RT_INVALID_ARG"
     assert b"null argument" in L.rt_last_error()
+
+
+def test_stack_overflow_is_reported_as_a_status_on_the_host():
+    """The traversal's overflow path: a ray that needs more stack entries than
+    the stack holds ends and the call returns RT_STACK_OVERFLOW (never a trap
+    or a silently wrong hit). Scene: clusters of 16 parallel triangles at
+    exponentially spaced depths (a comb-shaped BVH); the rays run inside every
+    box and miss every triangle, so every internal node is visited and
+    pending siblings pile up on the stack."""
+    from test_oracle_geometry import tri_scene
+    V, I = [], []
+    for k in range(100):
+        for j in range(16):
+            z = 1.5 ** k * (1 + 1e-3 * j / 16)
+            b = len(V)
+            V += [[-1, -1, z], [1, -1, z], [0, 1, z]]
+            I.append([b, b + 1, b + 2])
+    s = rt.Scene(tri_scene(np.array(V, np.float32), np.array(I)), host_only=True)
+    miss = np.array([[0.9, 0.9, 0.5, 0, 0, 1, 0, np.inf], [-0.9, 0.9, 0.5, 0, 0, 1, 0, np.inf]], np.float32)
+    hit = np.array([[0.0, 0.0, 0.5, 0, 0, 1, 0, np.inf]], np.float32)
+    rays = np.concatenate([miss, hit])
+    p_full, t_full, _, _, _ = rt.debug_trace_host(s, rays)
+    assert p_full[0] == rt.RT_MISS and p_full[1] == rt.RT_MISS and p_full[2] != rt.RT_MISS
+    # the full stack (48 entries) gives the kernels' answer
+    p48, t48 = rt.debug_trace_host_stack(s, rays, 48)
+    assert np.array_equal(p48, p_full) and np.array_equal(t48, t_full)
+    # the smallest stack that suffices, and one entry less overflows
+    need = next(k for k in range(1, 49) if _no_overflow(s, miss, k))
+    assert need >= 2
+    with pytest.raises(rt.RtError) as e:
+        rt.debug_trace_host_stack(s, miss, need - 1)
+    assert e.value.status == 6 and "overflow" in str(e.value)
+    for k in range(need, 49):
+        p, t = rt.debug_trace_host_stack(s, miss, k)
+        assert np.all(p == rt.RT_MISS) and np.all(np.isinf(t))
+    with pytest.raises(rt.RtError):
+        rt.debug_trace_host_stack(s, miss, 0)
+
+
+def _no_overflow(s, rays, k):
+    try:
+        rt.debug_trace_host_stack(s, rays, k)
+        return True
+    except rt.RtError as e:
+        assert e.status == 6
+        return False

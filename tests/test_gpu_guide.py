@@ -154,3 +154,152 @@ def test_gemm_split_k_accumulate_into_strided_c():
     scale = (A.double().cpu().abs() @ B.double().cpu().abs().T).max().item()
     assert (C.cpu().double() - ref).abs().max().item() <= 1e-5 * scale + 1e-4
     assert torch.all(big[:, :16] == 2.0) and torch.all(big[:, 64:] == 2.0)
+
+
+# ---------------------------------------------------------------------------
+# Element-wise parity with the oracle
+
+U_BF16 = 2.0 ** -8   # unit roundoff of BF16 (8 significant bits, round to nearest)
+G_ACC = 2.0 ** -24   # unit roundoff of the FP32 accumulation
+
+
+def _layers(p):
+    """Oracle parameter vector -> [W1..W5] ([out][in]) in float64."""
+    dims = [224, 64, 64, 64, 64, 40]
+    Ws, o = [], 0
+    for l in range(5):
+        n = dims[l] * dims[l + 1]
+        Ws.append(p[o:o + n].reshape(dims[l + 1], dims[l]))
+        o += n
+    return Ws
+
+
+def forward_error_bound(p, x0, acts):
+    """Per-element bound on |GPU - oracle| of the raw outputs when both take
+    the same BF16 weights and inputs: the GPU accumulates in FP32 (error at
+    most K u_acc |W||h| per product) and rounds each hidden activation to
+    BF16 (at most u_bf16 of its magnitude); an input bin may round to the
+    neighbouring BF16 value (the GPU builds it in FP32). Errors propagate
+    through |W| (ReLU is 1-Lipschitz)."""
+    Ws = [np.abs(W) for W in _layers(p)]
+    h = np.abs(x0)
+    e = 2 * U_BF16 * h
+    for l in range(4):
+        K = Ws[l].shape[1]
+        ez = e @ Ws[l].T + K * G_ACC * (h @ Ws[l].T)
+        a = np.abs(acts[:, l, :])
+        e = ez + U_BF16 * (a + ez)
+        h = a
+    return e @ Ws[4].T + 64 * G_ACC * (h @ Ws[4].T)
+
+
+@pytest.mark.parametrize("trained", [False, True])
+def test_forward_matches_oracle_per_element(trained):
+    """Every raw output of the fused inference kernel within its derived
+    bound of the FP64 oracle on the same BF16 weights and inputs (an
+    untrained network and one after 20 Adam steps)."""
+    from paper_1705_01263_gb300 import rt
+    guide = rt.Guide(seed=21)
+    f = features(3000, 6)
+    x = torch.tensor(f, dtype=torch.float32, device="cuda")
+    if trained:
+        rng = np.random.default_rng(8)
+        wi = rng.normal(size=(3000, 3)) + np.array([0.0, 2.0, 0.0])
+        wi /= np.linalg.norm(wi, axis=1, keepdims=True)
+        for _ in range(20):
+            guide.train_step(x, torch.tensor(wi, dtype=torch.float32, device="cuda"),
+                             torch.ones(3000, device="cuda"))
+    raw = guide.infer(x).cpu().numpy().astype(np.float64)
+    p = bf16_round(guide.get_params())
+    x0 = bf16_round(oracle_inputs(f))
+    want, acts = oracle.mlp_forward_acts(p, x0)
+    bound = forward_error_bound(p, x0, acts)
+    err = np.abs(raw - want)
+    assert np.all(err <= bound + 1e-7), (err - bound).max()
+    # the bound is not vacuous: it stays well below the outputs' own scale
+    assert np.median(bound) < 0.05 * np.median(np.abs(want)) + 1e-3
+
+
+def test_adam_update_matches_oracle_element_wise():
+    """Two GPU training steps against the oracle's Adam (first steps of the
+    textbook update, beta1 0.9, beta2 0.999, eps 1e-8, lr 1e-2) fed with the
+    GPU's gradient at the same weights: parameters and both moments element
+    by element at FP32 rounding."""
+    from paper_1705_01263_gb300 import rt
+    n = 4096
+    guide = rt.Guide(seed=31, lr=1e-2)
+    f = torch.tensor(features(n, 9), dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(10)
+    wi = rng.normal(size=(n, 3))
+    wi /= np.linalg.norm(wi, axis=1, keepdims=True)
+    wi = torch.tensor(wi, dtype=torch.float32, device="cuda")
+    w = torch.tensor(rng.uniform(0.2, 3.0, n), dtype=torch.float32, device="cuda")
+    npar = guide.num_params()
+
+    def unpack(blob):
+        a = np.frombuffer(blob, np.uint8)
+        P = a[: 4 * npar].view(np.float32).astype(np.float64)
+        M = a[4 * npar: 8 * npar].view(np.float32).astype(np.float64)
+        V = a[8 * npar: 12 * npar].view(np.float32).astype(np.float64)
+        step = int(a[12 * npar: 12 * npar + 8].view(np.int64)[0])
+        return P, M, V, step
+
+    P, M, V, step = unpack(guide.state())
+    assert step == 0 and not M.any() and not V.any()
+    for t in (1, 2):
+        _, g = guide.loss_grad(f, wi, w)
+        g = g.cpu().numpy().astype(np.float64)
+        guide.train_step(f, wi, w)
+        Pg, Mg, Vg, step = unpack(guide.state())
+        assert step == t
+        Po, Mo, Vo = P.copy(), M.copy(), V.copy()
+        oracle.adam_step(Po, g, Mo, Vo, t)
+        assert np.allclose(Mg, Mo, rtol=4e-7, atol=1e-30)
+        assert np.allclose(Vg, Vo, rtol=4e-7, atol=1e-38)
+        step_size = np.abs(Po - P)
+        assert np.all(np.abs(Pg - Po) <= 4e-6 * step_size + 2 * np.spacing(np.abs(P).astype(np.float32))), \
+            np.abs(Pg - Po).max()
+        assert np.abs(Pg - P).max() > 0
+        P, M, V = Pg, Mg, Vg
+
+
+def test_device_mixture_pdf_and_sampler_match_oracle():
+    """The von Mises-Fisher mixture code that guided shading runs (decode of
+    the raw outputs, density, lobe choice and Jakob's sampling) against the
+    oracle's on the same raw outputs and uniforms, sample by sample, from
+    broad to sharp lobes (kappa 1e-2 .. 1e3)."""
+    from paper_1705_01263_gb300 import rt
+    rng = np.random.default_rng(12)
+    n = 20000
+    raw = rng.normal(size=(n, 40))
+    sharp = rng.random(n) < 0.3
+    for k in range(8):
+        raw[:, 5 * k + 3] = np.where(sharp, rng.uniform(5.0, 1000.0, n), rng.uniform(-6.0, 4.0, n))
+        raw[:, 5 * k + 4] *= 2.0
+    raw = raw.astype(np.float32).astype(np.float64)
+    wi = rng.normal(size=(n, 3))
+    wi /= np.linalg.norm(wi, axis=1, keepdims=True)
+    wi = wi.astype(np.float32).astype(np.float64)
+    u = rng.random((n, 3)).astype(np.float32).astype(np.float64)
+    t = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    pdf_wi, ws, pdf_ws = rt.debug_guide_mixture(t(raw), t(wi), t(u))
+    pdf_wi, ws, pdf_ws = (x.cpu().numpy().astype(np.float64) for x in (pdf_wi, ws, pdf_ws))
+    kmax = np.log1p(np.exp(np.minimum(raw[:, 3::5], 700.0))).clip(1e-2, 1e4).max(axis=1)
+    # density: FP32 exponent kappa (mu.w - 1) carries ~kappa 2^-22 absolute error
+    po = np.array([oracle.mixture_pdf(raw[i], wi[i]) for i in range(n)])
+    tol = po * (2e-5 + 4.0 * kmax * 2.0 ** -23) + 1e-30
+    assert np.all(np.abs(pdf_wi - po) <= tol), np.max(np.abs(pdf_wi - po) / tol)
+    # sampling: the same lobe (away from the FP32/FP64 boundary of the
+    # cumulative weights) and the same direction
+    z = np.exp(raw[:, 4::5] - raw[:, 4::5].max(axis=1, keepdims=True))
+    cw = np.cumsum(z / z.sum(axis=1, keepdims=True), axis=1)
+    clear = np.min(np.abs(cw[:, :7] - u[:, :1]), axis=1) > 1e-5
+    wo = np.array([oracle.mixture_sample(raw[i], *u[i]) for i in range(n)])
+    d = np.linalg.norm(ws - wo, axis=1)
+    assert clear.mean() > 0.99
+    assert np.all(d[clear] <= 2e-4), d[clear].max()
+    assert np.all(np.abs(np.linalg.norm(ws, axis=1) - 1) < 1e-5)
+    # the density at the sampled direction agrees too
+    pos = np.array([oracle.mixture_pdf(raw[i], ws[i]) for i in range(n)])
+    tol = pos * (2e-5 + 4.0 * kmax * 2.0 ** -23) + 1e-30
+    assert np.all(np.abs(pdf_ws - pos) <= tol), np.max(np.abs(pdf_ws - pos) / tol)

@@ -158,3 +158,42 @@ def test_degenerate_inputs():
     e = rt.Scene(tri_scene(np.zeros((3, 3)), np.zeros((0, 3))))
     p, t, _, _ = gpu_trace(e, rays)
     assert np.all(p == MISS)
+
+
+def test_concurrent_calls_on_two_streams_equal_serial(field_full):
+    """Two rt_trace calls in flight at once, on two streams from two host
+    threads, each with its own ray batch: every call has its own fetch counter
+    and overflow flag, so both equal their serial results bit for bit."""
+    import threading
+    from paper_1705_01263_gb300 import rt
+    sd, scene = field_full[0], field_full[2]
+    batches = [torch.from_numpy(np.ascontiguousarray(scenes.random_rays(sd, 1 << 20, seed=40 + k,
+                                                                        kind="incoherent"))).cuda()
+               for k in range(2)]
+    serial = []
+    for r in batches:
+        (p, _, t, _, _), _ = rt.rt_trace(scene, r)
+        torch.cuda.synchronize()
+        serial.append((p.cpu().numpy(), t.cpu().numpy()))
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    out, errs = [None, None], []
+
+    def run(k):
+        try:
+            with torch.cuda.stream(streams[k]):
+                for _ in range(3):
+                    (p, _, t, _, _), _ = rt.rt_trace(scene, batches[k], stream=streams[k].cuda_stream)
+                out[k] = (p, t)
+        except Exception as e:  # surfaced below
+            errs.append(e)
+
+    th = [threading.Thread(target=run, args=(k,)) for k in range(2)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    torch.cuda.synchronize()
+    assert not errs, errs
+    for k in range(2):
+        assert np.array_equal(out[k][0].cpu().numpy(), serial[k][0])
+        assert np.array_equal(out[k][1].cpu().numpy(), serial[k][1])

@@ -163,3 +163,28 @@ def test_instanced_two_way_has_the_path_tracers_expectation(light_bvh):
     z = np.abs(m_tw - m_pt) / np.sqrt(se_tw ** 2 + se_pt ** 2 + 1e-30)
     assert z.max() < 4.5, z.max()
     assert m_tw.mean() == pytest.approx(m_pt.mean(), rel=0.03)
+
+
+@pytest.mark.parametrize("name,lt_mode", [("glossy", 0), ("cornell-env", 0), ("cornell-env", 1)])
+def test_two_way_splats_match_the_oracle_per_pixel(name, lt_mode):
+    """The light stage's splat image against the oracle's on the same light
+    paths, pixel by pixel: K batches of iterations give both sides a
+    per-pixel mean and a standard error (the spread of the batch splats);
+    every pixel channel within 4 sigma, up to the Gaussian allowance."""
+    from paper_1705_01263_gb300 import rt
+    sd, cam = _scene(name, 32)
+    scene = rt.Scene(sd)
+    osc = oracle.Scene(sd)
+    K, per = 8, 16
+    g, o = [], []
+    for k in range(K):
+        _, _, _, sp, _ = two_way_gpu(sd, cam, per, 3, first=k * per, lt_mode=lt_mode, scene=scene)
+        _, _, _, SP, _ = osc.render_two_way(cam, per, 3, iter0=k * per, lt_mode=lt_mode)
+        g.append(sp / per)
+        o.append(SP / per)
+    g, o = np.array(g), np.array(o)
+    mg, mo = g.mean(axis=0), o.mean(axis=0)
+    var = g.var(axis=0, ddof=1) / K + o.var(axis=0, ddof=1) / K
+    out = np.abs(mg - mo) > 4 * np.sqrt(var) + 1e-9 * np.maximum(np.abs(mo), 1e-3)
+    assert out.sum() <= allowed_4sigma(out.size), (int(out.sum()), out.size)
+    assert mo.sum() > 0 and np.abs(mg - mo).sum() <= 0.02 * mo.sum()
