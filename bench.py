@@ -145,6 +145,156 @@ def cpu_baseline_oracle(sd, cam):
             "mrays_per_s": rays / dt / 1e6, "cpu": cpu_model()}
 
 
+def _oracle_many_lights_worker(conn):
+    """Spawned process: builds the oracle's scene of the many-light workload
+    (not timed: about a minute, single-threaded), then waits for "go" and
+    times a bounded sample, 1 spp over the full 1920 x 1080 image at depth 12,
+    on all host cores."""
+    import oracle
+    from paper_1705_01263_gb300 import scenes as sc_mod
+    sd, cam = sc_mod.instanced_field()
+    t0 = time.time()
+    osc = oracle.Scene(sd)
+    build_s = time.time() - t0
+    conn.send({"built": build_s})
+    if conn.recv() != "go":
+        return
+    t0 = time.time()
+    _, _, cnt, rays = osc.render(cam, 1, 12)
+    dt = time.time() - t0
+    paths = int(cnt.sum())
+    conn.send({"value": paths / dt / 1e6, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"{cam.width}x{cam.height} px x 1 of the 256 spp (depth 12), {paths} paths in {dt:.1f} s; "
+                         f"oracle scene build {build_s:.1f} s (flattened 10M triangles) not timed",
+               "mrays_per_s": rays / dt / 1e6, "cpu": cpu_model()})
+
+
+class OracleManyLights:
+    """The many-light oracle sample in a process of its own, started with
+    spawn before the first GPU call so that its scene build overlaps the GPU
+    measurements; its timed render runs once they are done."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.conn, child = ctx.Pipe()
+        self.proc = ctx.Process(target=_oracle_many_lights_worker, args=(child,), daemon=True)
+        self.proc.start()
+
+    def result(self, timeout=600):
+        try:
+            if not self.conn.poll(timeout):
+                return None
+            self.conn.recv()            # built
+            self.conn.send("go")
+            if not self.conn.poll(timeout):
+                return None
+            return self.conn.recv()
+        finally:
+            self.proc.join(1)
+            if self.proc.is_alive():
+                self.proc.terminate()
+
+    def cancel(self):
+        if self.proc.is_alive():
+            self.proc.terminate()
+
+
+def l2_peak(mb=16, reps=200):
+    """Measured L2 copy bandwidth: a device-to-device copy of an `mb` MiB
+    buffer (source and destination both resident in the 129 MB L2) repeated
+    `reps` times, read + write bytes over the CUDA-event time (best of 3)."""
+    import torch
+    n = mb << 20
+    a = torch.empty(n, dtype=torch.uint8, device="cuda")
+    b = torch.empty_like(a)
+    a.fill_(1)
+    for _ in range(10):
+        b.copy_(a)
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record()
+        e1.synchronize()
+        gbs = 2 * n * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+        best = gbs if best is None else max(best, gbs)
+    return best
+
+
+def scheduler_sweep(scene, cam, spp, depth, pools=(1 << 22, 1 << 23, 1 << 24, 1 << 25)):
+    """Regeneration (Sec. 3.1.3) against iteration sets on the benchmark
+    workload: one timed render (CUDA events, L2 flushed before) per pool size
+    with the paper's refill rule (half the pool ended), one with refills at
+    every step, and the iteration-set scheduler holding the whole request."""
+    import torch
+    from paper_1705_01263_gb300 import rt
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    film = rt.Film(cam.width, cam.height)
+    paths = cam.width * cam.height * spp
+
+    def timed(**kw):
+        film.clear()
+        rt.rt_render(scene, cam, spp, depth, film, rt.make_opts(**kw))   # warm: allocations
+        film.clear()
+        flush.zero_()
+        st = rt.rt_stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rt.rt_render(scene, cam, spp, depth, film, rt.make_opts(stats=st, **kw))
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        return {"Mpaths_per_s": paths / ms / 1e3, "ms": ms, "regen_steps": st.regen_sets,
+                "wavefront_steps": st.wavefront_steps}
+
+    out = {"workload": f"{cam.width}x{cam.height}, {spp} spp, depth {depth}"}
+    out["iteration_sets_whole_request"] = timed(scheduler=1)
+    whole = out["iteration_sets_whole_request"]["Mpaths_per_s"]
+    for p in pools:
+        r = timed(max_paths=p)
+        r["of_whole_request"] = r["Mpaths_per_s"] / whole
+        out[f"regen_pool_{p >> 20}M"] = r
+    r = timed(max_paths=1 << 24, regen_fraction=1e-6)
+    r["of_whole_request"] = r["Mpaths_per_s"] / whole
+    out["regen_pool_16M_every_step"] = r
+    film.close()
+    return out
+
+
+def many_lights_full(spp=256, depth=12):
+    """The many-light configuration at its own size: 10M instanced triangles,
+    100k textured emitters picked by the alias table, 1920 x 1080, 256 spp,
+    depth 12 (530.8M paths), one timed render (CUDA events) after a warm-up
+    render of 1 spp."""
+    import torch
+    from paper_1705_01263_gb300 import rt, scenes
+    sd, cam = scenes.instanced_field()
+    sd.light_bvh = False
+    scene = rt.Scene(sd)
+    film = rt.Film(cam.width, cam.height)
+    rt.rt_render(scene, cam, 1, depth, film)
+    film.clear()
+    st = rt.rt_stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    rt.rt_render(scene, cam, spp, depth, film, rt.make_opts(stats=st))
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = {"workload": f"instanced field 10M tris (1000 instances of 100 meshes), 100k textured emitters, alias "
+                       f"table, {cam.width}x{cam.height}, {spp} spp, depth {depth}",
+           "paths": st.paths, "ms": ms, "Mpaths_per_s": st.paths / ms / 1e3,
+           "Mrays_per_s": (st.extension_rays + st.shadow_rays) / ms / 1e3,
+           "rays_per_path": (st.extension_rays + st.shadow_rays) / max(1, st.paths),
+           "regen_steps": st.regen_sets, "wavefront_steps": st.wavefront_steps}
+    film.close()
+    del scene
+    return out
+
+
 def guided_vs_plain(light="down", target_spp=16384, chunk=512, max_factor=2, seed=5, guide_kw=None, opts_kw=None):
     """Time to equal RMSE, guided vs plain, on the Cornell configuration (64 x
     64, depth 8): light "down" is the configuration itself; "up" turns the
@@ -690,11 +840,22 @@ def main():
     ap.add_argument("--megakernel-only", action="store_true", help="A/B baseline: megakernel per iteration set")
     ap.add_argument("--sort-by-material", action="store_true", help="A/B: material-sorted shading queue")
     ap.add_argument("--sort-rays", action="store_true", help="A/B: reorder extension rays by octant and origin cell")
+    ap.add_argument("--scheduler", type=int, default=0, help="0 regeneration (default), 1 iteration sets")
+    ap.add_argument("--regen-fraction", type=float, default=0.0, help="refill once this fraction ended (0 = 0.5)")
+    ap.add_argument("--no-scheduler-sweep", action="store_true", help="skip the regeneration pool-size sweep")
+    ap.add_argument("--no-many-lights-full", action="store_true",
+                    help="skip the many-light configuration at its own size (256 spp) and its oracle sample")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    import torch
     rank, world, local = env_rank()
+    quick = args.render_once or args.mlp_once or args.two_way_once
+    # the many-light oracle sample: spawned before the first GPU call, its
+    # scene build overlaps the GPU measurements
+    oml = None
+    if rank == 0 and world == 1 and not quick and not args.no_cpu_baseline and not args.no_many_lights_full:
+        oml = OracleManyLights()
+    import torch
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -714,7 +875,8 @@ def main():
     def opts(**kw):
         return rt.make_opts(seed=0, trace_kernel=args.trace_kernel, megakernel_only=args.megakernel_only,
                             sort_by_material=args.sort_by_material, sort_rays=args.sort_rays,
-                            max_paths=args.pool, tail_threshold=args.tail, **kw)
+                            max_paths=args.pool, tail_threshold=args.tail, scheduler=args.scheduler,
+                            regen_fraction=args.regen_fraction, **kw)
 
     def render_step(stats=None, profile=0):
         o = opts(stats=stats, profile=profile)
@@ -800,7 +962,11 @@ def main():
     ext_rays_timed = ext
     nodes_per_ray = wstats.ext_nodes / max(1, wstats.extension_rays)
     tris_per_ray = wstats.ext_tris / max(1, wstats.extension_rays)
-    bytes_per_ray = nodes_per_ray * 80 + tris_per_ray * 48 + 32 + 16 + 4
+    # algorithmic bytes per extension ray: node visits x 80 B + triangle tests
+    # x 36 B (three FP32 vertices) + 32 B ray in + 20 B hit out; the stored
+    # triangle record is 48 B (vertices padded to float4, id in the pad)
+    bytes_per_ray = nodes_per_ray * 80 + tris_per_ray * 36 + 32 + 20
+    bytes_per_ray_stored = nodes_per_ray * 80 + tris_per_ray * 48 + 32 + 20
     # per launch: bytes of all rays of all launches / their total device time
     achieved_gbs = ext_rays_timed * bytes_per_ray / (trace_ms / 1e3) / 1e9 if trace_ms > 0 else None
     hbm, bf16, peak_src = peaks()
@@ -859,11 +1025,34 @@ def main():
     if rank == 0 and not args.no_two_way:
         tw = two_way_vs_plain()
         tw["open_scene"] = two_way_vs_plain(res=270, depth=8, spp=16, ref_spp=256, scene_name="spheres")
+    sweep = None
+    if rank == 0 and not args.no_scheduler_sweep:
+        sweep = scheduler_sweep(scene, cam, args.spp, DEPTH)
+    mlf = None
+    if rank == 0 and not args.no_many_lights_full:
+        mlf = many_lights_full()
+    l2 = l2_peak() if rank == 0 else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_oracle(sd, cam)
+        if oml is not None and mlf is not None:
+            mlf["cpu_baseline"] = oml.result()
+    if oml is not None:
+        oml.cancel()
     clocks = clk.summary()
     if rank == 0:
+        achieved_l2 = (achieved_gbs / l2) if (achieved_gbs and l2) else None
+        summary = {
+            "mrays_per_s": mrays,
+            "trace_ext_frac_hbm": (achieved_gbs / hbm) if achieved_gbs else None,
+            "trace_ext_frac_l2": achieved_l2,
+            "guided_speedup": {k: (gvp[k] or {}).get("guided_speedup") for k in ("indirect_lit", "config")}
+            if gvp else None,
+            "guide_mlp_frac_bf16": gmlp["roofline"]["frac"] if gmlp else None,
+            "many_lights_full_Mpaths_per_s": mlf["Mpaths_per_s"] if mlf else None,
+            "regen_vs_whole_request": {k: v.get("of_whole_request") for k, v in sweep.items()
+                                       if isinstance(v, dict) and "of_whole_request" in v} if sweep else None,
+        }
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
@@ -873,6 +1062,8 @@ def main():
                        "height": cam.height, "spp": args.spp, "max_depth": DEPTH,
                        "paths_per_step": paths_per_step, "l2": "flushed between steps (256 MiB write)",
                        "film": "FP64 sums", "parallelism": f"weak: {world} rank(s), disjoint iteration ranges",
+                       "scheduler": ["regeneration (Sec. 3.1.3)", "iteration sets"][args.scheduler],
+                       "pool": args.pool or "library default",
                        "trace_kernel": ["closest hit one ray per thread, shadow rays with lane refill",
                                         "persistent warps, lane refill",
                                         "one ray per thread, shared-memory stack",
@@ -880,8 +1071,9 @@ def main():
                        "ray_order": "octant + origin cell" if args.sort_rays else "compaction order",
                        "schedule": "megakernel only" if args.megakernel_only else "wavefront + megakernel tail",
                        "shading_queue": "material-sorted" if args.sort_by_material else "compaction order"},
-            "mrays_per_s": mrays,
-            "rays_per_path": (ext + shd) / (paths_per_step * args.steps),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": cam_bytes,
+                    "d2h_bytes_per_step": cam.width * cam.height * 3 * 4},
+            "gpu_launches": launches,
             "roofline": {"bound": "hbm", "kernel": "k_trace_ext (closest-hit BVH8 traversal)",
                          "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                          "frac": (achieved_gbs / hbm) if achieved_gbs else None,
@@ -889,15 +1081,19 @@ def main():
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per extension ray "
                                            "(4-spp capture) x rays per timed launch",
                          "peak_source": f"{peak_src} hbm_gbs",
-                         "bytes_per_ray": bytes_per_ray, "nodes_per_ray": nodes_per_ray,
+                         "l2_peak": l2, "l2_frac": achieved_l2,
+                         "l2_peak_source": "measured here: 16 MiB device-to-device copy, L2-resident",
+                         "bytes_per_ray": bytes_per_ray, "bytes_per_ray_stored_layout": bytes_per_ray_stored,
+                         "nodes_per_ray": nodes_per_ray,
                          "tris_per_ray": tris_per_ray, "launches": tl,
                          "avg_launch_ms": trace_ms / max(1, tl)},
-            "kernel_ms_share": {k: v / max(1e-9, sum(shares.values())) for k, v in shares.items()},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": cam_bytes,
-                    "d2h_bytes_per_step": cam.width * cam.height * 3 * 4},
-            "gpu_launches": launches,
-            "clocks": clocks,
             "cpu_baseline": cpu,
+            "clocks": clocks,
+            "summary": summary,
+            "kernel_ms_share": {k: v / max(1e-9, sum(shares.values())) for k, v in shares.items()},
+            "rays_per_path": (ext + shd) / (paths_per_step * args.steps),
+            "many_lights_full": mlf,
+            "scheduler_sweep": sweep,
             "guided_vs_plain": gvp,
             "guide_mlp": gmlp,
             "many_lights": ml,

@@ -141,6 +141,7 @@ typedef struct {
     /* traversal work, filled when rt_render_opts.profile >= 2 (counted by
      * an instrumented variant of the trace kernels) */
     uint64_t ext_nodes, ext_tris, shadow_nodes, shadow_tris;
+    uint32_t regen_sets;     /* regeneration scheduler: bounce steps that started new paths */
 } rt_stats;
 
 /* Render options. Zero-initialise and set what you need; zero means the
@@ -150,14 +151,17 @@ typedef struct {
     int32_t rr_enable;       /* Russian roulette from the 3rd vertex (default off) */
     int32_t mis_mode;        /* 0 power heuristic, 1 balance, 2 NEE only, 3 BSDF only */
     uint64_t seed;           /* scrambling seed for the Halton digits (A.2) */
-    double time_budget_ms;   /* stop between iteration sets after this (0 = none) */
-    uint32_t max_paths_in_flight; /* state-pool capacity; 0 = every requested path, at most 2^27 and a quarter of free device memory */
+    double time_budget_ms;   /* stop issuing new paths after this (0 = none); see rt_render */
+    uint32_t max_paths_in_flight; /* state-pool capacity; 0 = 2^24 paths with regeneration (scheduler 0), every
+                                   * requested path with iteration sets (scheduler 1); at most 2^27 and a quarter
+                                   * of free device memory */
     int32_t megakernel_only; /* 1: one megakernel per iteration set (A/B baseline) */
     int32_t sort_by_material;/* 1: material-sorted shading queue */
     uint32_t tail_threshold; /* live paths below which the megakernel finishes a set (0 = auto) */
     uint32_t block_size;     /* threads per block of the state kernels: 0 (= 128) or a multiple of
                               * 32 up to 128, else RT_INVALID_ARG; results do not depend on it */
-    const volatile int32_t *abort_flag; /* host-mapped; nonzero -> stop between sets (A.4) */
+    const volatile int32_t *abort_flag; /* host memory; nonzero -> stop (A.4); the library's host thread
+                              * polls it while it waits for the device and relays it to the kernels */
     rt_guide *guide;         /* online path guiding (NULL = off) */
     rt_stats *stats;         /* optional host output */
     int32_t profile;         /* 1: per-kernel event timing; 2: also count traversal work */
@@ -168,6 +172,11 @@ typedef struct {
                               * 4: one ray per thread for both. Two-level scenes always use 0's closest-hit
                               * kernel for both. */
     int32_t sort_rays;       /* 1: reorder extension rays by direction octant and origin cell (A/B) */
+    int32_t scheduler;       /* 0: regeneration (Sec. 3.1.3): a bounded pool whose ended paths are
+                              * refilled with the next tasks; 1: iteration sets, each held whole in
+                              * the pool (A/B). Guided rendering and megakernel_only use iteration sets. */
+    float regen_fraction;    /* scheduler 0: refill once this fraction of the pool has ended (0 = 0.5,
+                              * the paper's rule); must be in [0, 1] */
 } rt_render_opts;
 
 /* ---------------------------------------------------------------- scene */
@@ -224,9 +233,17 @@ rt_status rt_film_resolve(const rt_film *film, float *mean, float *var, void *st
  * time budget) first completes that iteration, so rendering
  * total - next more iterations always ends exactly at `total`. max_depth = number of
  * scattering vertices (1 = direct lighting). Blocking with respect to the
- * host (it waits for each iteration set to finish); kernels run on `stream`.
- * Returns RT_TIMEOUT if the time budget or abort flag stopped it early: the
- * film then holds whole iteration sets only and the next call resumes. */
+ * host; kernels run on `stream`. Each pixel's sums receive its samples in
+ * sample order, so results do not depend on the scheduler, the pool size or
+ * how a range is split over calls (up to the megakernel tail's FP32 order).
+ * Timeout (Appendix A.4): with the regeneration scheduler (the default) the
+ * kernels check a host-mapped stop word and the device clock at every bounce
+ * step; once the abort flag is seen or the time budget is spent no new path
+ * starts, the paths in flight finish (at most max_depth + 1 more steps) and
+ * the film receives every task that completed, a contiguous range that may
+ * end inside an iteration. With iteration sets (scheduler 1) and guided
+ * rendering the check happens between sets. Returns RT_TIMEOUT when stopped
+ * early; the next call resumes at the film's next task. */
 rt_status rt_render(const rt_scene *scene, const rt_camera *camera, uint32_t spp,
                     uint32_t max_depth, rt_film *film, const rt_render_opts *opts, void *stream);
 

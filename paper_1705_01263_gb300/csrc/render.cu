@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -29,6 +30,11 @@ struct Ctrl {
     uint32_t fetch_ext, fetch_shadow, fetch_shade, n_train;
     unsigned long long ext_rays, shadow_rays;
     unsigned long long ext_nodes, ext_tris, shadow_nodes, shadow_tris;
+    // regeneration (Sec. 3.1.3): paths that ended this step, emptied slots,
+    // tasks of the window issued so far and in total, and the stop state
+    uint32_t n_dead, n_free, task_next, n_tasks;
+    uint32_t stop, regen_sets, pad2[2];
+    unsigned long long deadline_ns;   // %globaltimer value after which no task is issued
 };
 
 // Structure-of-arrays path state (capacity = pool size).
@@ -49,6 +55,11 @@ struct Pool {
     Ctrl *ctrl;
     uint32_t capacity;
     uint32_t *nrec;  // guided rendering: training records per path (count | pending flag), else null
+    // regeneration only (null otherwise): task of each slot (offset in the
+    // window), slots whose path ended this step, slots emptied and not refilled
+    uint32_t *task;
+    uint32_t *qd;
+    uint32_t *qfree;
 };
 
 RT_D void store_state(const Pool &p, uint32_t q, const PathState &s) {
@@ -226,6 +237,7 @@ __global__ void __launch_bounds__(128, 8) k_shade(RenderParams P, Pool pool, con
         }
         warp_append(next, &c->n_next, valid && (r & 1), q);
         warp_append(pool.qs, &c->n_shadow, valid && (r & 2), q);
+        if (pool.qd) warp_append(pool.qd, &c->n_dead, valid && !(r & 1), q);
     }
 }
 
@@ -651,6 +663,181 @@ __global__ void k_resolve(const double *sum, const double *sum2, const uint32_t 
     }
 }
 
+// ------------------------------------------------ regeneration (Sec. 3.1.3)
+// A window of n_tasks consecutive tasks (pixel samples, pass-major, from
+// absolute task t0) streams through a pool of `capacity` slots. A path that
+// ends is retired: its radiance goes to stage[task], indexed by the task's
+// offset in the window, and its slot is emptied. Once at least `regen_min`
+// slots are empty the next tasks are started in them, so the pool stays
+// between half and fully occupied instead of emptying towards the end of a
+// set. The film is accumulated from the staging buffer in sample order per
+// pixel (k_film_range), so the result does not depend on which slot a task
+// ran in or when. Every decision (how many tasks start, which slots they take)
+// is a function of counts read at kernel start, made identically by k_regen
+// and k_regen_step_end, so neither needs an atomic or a grid-wide barrier.
+
+RT_D unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void k_regen_init(RenderParams P, Pool pool, uint64_t t0, uint32_t n_tasks, uint32_t WH,
+                             uint32_t tail_threshold, unsigned long long budget_ns,
+                             const volatile uint32_t *stop_word) {
+    const uint32_t cap = pool.capacity;
+    const uint32_t k = min(cap, n_tasks);
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cap; q += gridDim.x * blockDim.x) {
+        if (q < k) {
+            const uint64_t t = t0 + q;
+            PathState s;
+            raygen(P, (uint32_t)(t % WH), (uint32_t)(t / WH), s);
+            store_state(pool, q, s);
+            pool.task[q] = q;
+            pool.q[0][q] = q;
+        } else {
+            pool.qfree[q - k] = q;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Ctrl *c = pool.ctrl;
+        c->n_ext = k;
+        c->n_next = c->n_shadow = c->cur = 0;
+        c->fetch_ext = c->fetch_shadow = c->fetch_shade = 0;
+        c->n_dead = 0;
+        c->n_free = cap - k;
+        c->task_next = k;
+        c->n_tasks = n_tasks;
+        c->tail_threshold = tail_threshold;
+        c->tail = (k == n_tasks && k < tail_threshold) ? 1u : 0u;
+        c->deadline_ns = budget_ns ? globaltimer_ns() + budget_ns : ~0ull;
+        c->stop = (stop_word && *stop_word) ? 1u : 0u;   // set before the call: only this first load runs
+    }
+}
+
+// Tasks started by this step's regeneration (identical in k_regen and
+// k_regen_step_end: both read the same counts, and `stop` changes only
+// after both ran).
+RT_HD uint32_t regen_count(const Ctrl *c, uint32_t regen_min) {
+    const uint32_t left = c->n_tasks - c->task_next;
+    const uint32_t empty = c->n_dead + c->n_free;
+    if (c->stop || left == 0 || empty < regen_min) return 0u;
+    return left < empty ? left : empty;
+}
+
+// Slot bookkeeping of thread j of k_regen: retire dead[j] (returned in
+// *retire, else ~0u) and return the slot that task task_next + j starts in
+// (~0u when j starts none); a dead slot that is not refilled goes onto the
+// free list.
+RT_HD uint32_t regen_slot(uint32_t j, uint32_t n_dead, uint32_t n_free, uint32_t n_new, const uint32_t *qd,
+                          uint32_t *qfree, uint32_t *retire) {
+    uint32_t slot = ~0u;
+    *retire = ~0u;
+    if (j < n_dead) {
+        slot = qd[j];
+        *retire = slot;
+    }
+    if (j < n_new) {
+        if (j >= n_dead) slot = qfree[n_free - 1 - (j - n_dead)];
+        return slot;
+    }
+    if (j < n_dead) qfree[n_free + (j - n_new)] = slot;
+    return ~0u;
+}
+
+// Counts after a step's regeneration (k_regen_step_end, without the stop
+// check and the tail switch).
+RT_HD void regen_advance(Ctrl *c, uint32_t regen_min) {
+    const uint32_t n_dead = c->n_dead, n_free = c->n_free;
+    const uint32_t n_new = regen_count(c, regen_min);
+    c->n_free = n_new <= n_dead ? n_free + (n_dead - n_new) : n_free - (n_new - n_dead);
+    c->task_next += n_new;
+    if (n_new) ++c->regen_sets;
+    c->n_ext = c->n_next + n_new;
+    c->n_next = 0;
+    c->n_dead = 0;
+    c->cur ^= 1u;
+}
+
+// After the shadow rays of a step: retire the paths that ended, then (when
+// enough slots are empty) start the next tasks, appended to the next
+// extension queue after the paths that continue. Thread j retires dead[j]
+// and starts task task_next + j in dead[j], or in the top of the free list
+// once the dead slots are used up; dead slots not refilled go onto the free
+// list.
+__global__ void k_regen(RenderParams P, Pool pool, float4 *stage, uint64_t t0, uint32_t WH, uint32_t regen_min) {
+    const Ctrl *c = pool.ctrl;
+    if (c->tail) return;
+    const uint32_t n_dead = c->n_dead, n_free = c->n_free, n_next = c->n_next, base = c->task_next;
+    const uint32_t n_new = regen_count(c, regen_min);
+    uint32_t *next = pool.q[c->cur ^ 1u];
+    const uint32_t m = max(n_dead, n_new);
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+        uint32_t retire;
+        const uint32_t slot = regen_slot(j, n_dead, n_free, n_new, pool.qd, pool.qfree, &retire);
+        if (retire != ~0u) stage[pool.task[retire]] = pool.L[retire];
+        if (slot != ~0u) {
+            const uint32_t off = base + j;
+            const uint64_t t = t0 + off;
+            PathState s;
+            raygen(P, (uint32_t)(t % WH), (uint32_t)(t / WH), s);
+            store_state(pool, slot, s);
+            pool.task[slot] = off;
+            next[n_next + j] = slot;
+        }
+    }
+}
+
+// End of a bounce step with regeneration: counts for the next step, the stop
+// check (a host-mapped word the library's host thread sets on abort or time
+// budget, and the device clock against the deadline: one read each, never a
+// wait), and the switch to the megakernel tail once no task is left to start.
+__global__ void k_regen_step_end(Pool pool, uint32_t regen_min, const volatile uint32_t *stop_word) {
+    Ctrl *c = pool.ctrl;
+    if (c->tail) return;
+    regen_advance(c, regen_min);
+    c->n_shadow = 0;
+    c->fetch_ext = c->fetch_shadow = c->fetch_shade = 0;
+    if (!c->stop && ((stop_word && *stop_word) || globaltimer_ns() >= c->deadline_ns)) c->stop = 1u;
+    if ((c->stop || c->task_next == c->n_tasks) && c->n_ext < c->tail_threshold) c->tail = 1u;
+}
+
+// After the megakernel finished the tail: retire the paths it finished.
+__global__ void k_regen_retire_tail(Pool pool, float4 *stage) {
+    const Ctrl *c = pool.ctrl;
+    if (!c->tail) return;
+    const uint32_t n = c->n_ext;
+    const uint32_t *queue = pool.q[c->cur];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t slot = queue[i];
+        stage[pool.task[slot]] = pool.L[slot];
+    }
+}
+
+// Film accumulation of tasks [t_first, t_first + n) from the staging buffer
+// (stage[t - t_first]): one thread per pixel adds its samples in increasing
+// sample order, the order in which iteration sets would add them.
+__global__ void k_film_range(const float4 *stage, double *sum, double *sum2, uint32_t *count, uint64_t t_first,
+                             uint64_t n, uint32_t WH) {
+    const uint32_t r0 = (uint32_t)(t_first % WH);
+    for (uint32_t px = blockIdx.x * blockDim.x + threadIdx.x; px < WH; px += gridDim.x * blockDim.x) {
+        uint64_t off = (uint64_t)((px + WH - r0) % WH);   // first task of this pixel in the range
+        if (off >= n) continue;
+        double s0 = sum[3 * (size_t)px], s1 = sum[3 * (size_t)px + 1], s2 = sum[3 * (size_t)px + 2];
+        double q0 = sum2[3 * (size_t)px], q1 = sum2[3 * (size_t)px + 1], q2 = sum2[3 * (size_t)px + 2];
+        uint32_t k = 0;
+        for (; off < n; off += WH, ++k) {
+            const float4 L = stage[off];
+            const double a = L.x, b = L.y, cc = L.z;
+            s0 += a; s1 += b; s2 += cc;
+            q0 += a * a; q1 += b * b; q2 += cc * cc;
+        }
+        sum[3 * (size_t)px] = s0; sum[3 * (size_t)px + 1] = s1; sum[3 * (size_t)px + 2] = s2;
+        sum2[3 * (size_t)px] = q0; sum2[3 * (size_t)px + 1] = q1; sum2[3 * (size_t)px + 2] = q2;
+        count[px] += k;
+    }
+}
+
 // rays -> hits over caller-owned SoA buffers.
 struct UserJob {
     rt_rays rays;
@@ -937,6 +1124,9 @@ int grid_for(K kernel, int block, int64_t work) {
 
 struct PoolAlloc {
     Pool view{};
+    // regeneration arrays (task per slot, dead and free slot lists): set in
+    // the view only by the scheduler that uses them
+    uint32_t *task = nullptr, *qd = nullptr, *qfree = nullptr;
     void *block = nullptr;
     uint32_t capacity = 0;
     ~PoolAlloc() {
@@ -945,8 +1135,9 @@ struct PoolAlloc {
 };
 
 // Device bytes of one path's state in the pool (eight float4 arrays, the
-// sequence index, pixel, instance of the hit and three queue entries).
-constexpr size_t kPoolBytesPerPath = 8 * sizeof(float4) + sizeof(uint2) + 4 + 4 + 3 * 4;
+// sequence index, pixel, instance of the hit, three queue entries and the
+// regeneration scheduler's task, dead and free entries).
+constexpr size_t kPoolBytesPerPath = 8 * sizeof(float4) + sizeof(uint2) + 4 + 4 + 3 * 4 + 3 * 4;
 
 // Pool capacity when the caller leaves it to the library: every requested
 // path at once when that fits, up to 2^27 paths (about 21 GB of state) and a
@@ -965,7 +1156,8 @@ rt_status ensure_pool(PoolAlloc &pa, uint32_t capacity) {
     if (pa.block) { cudaFree(pa.block); pa.block = nullptr; }
     size_t P = capacity;
     size_t f4 = P * sizeof(float4);
-    size_t bytes = 8 * f4 + P * sizeof(uint2) + P * 4 /*pixel*/ + P * 4 /*hit_inst*/ + 3 * P * 4 /*queues*/ + 64 * 256;
+    size_t bytes = 8 * f4 + P * sizeof(uint2) + P * 4 /*pixel*/ + P * 4 /*hit_inst*/ + 3 * P * 4 /*queues*/ +
+                   3 * P * 4 /*regeneration*/ + 64 * 256;
     cudaError_t e = cudaMalloc(&pa.block, bytes);
     if (e != cudaSuccess) { set_error("path-state pool allocation failed"); return RT_OOM; }
     char *p = (char *)pa.block;
@@ -978,6 +1170,7 @@ rt_status ensure_pool(PoolAlloc &pa, uint32_t capacity) {
     v.pixel = (uint32_t *)take(P * 4);
     v.hit_inst = (uint32_t *)take(P * 4);
     v.q[0] = (uint32_t *)take(P * 4); v.q[1] = (uint32_t *)take(P * 4); v.qs = (uint32_t *)take(P * 4);
+    pa.task = (uint32_t *)take(P * 4); pa.qd = (uint32_t *)take(P * 4); pa.qfree = (uint32_t *)take(P * 4);
     v.capacity = capacity;
     pa.capacity = capacity;
     if ((size_t)(p - (char *)pa.block) > bytes) { set_error("pool layout overflow"); return RT_CUDA_ERROR; }
@@ -998,6 +1191,12 @@ struct RenderCache {
     // sorted queues (A/B options)
     uint32_t *sort_hist = nullptr, *sort_buf[2] = {nullptr, nullptr};
     uint32_t sort_cap = 0, sort_nkeys = 0;
+    // regeneration: radiance per task of the window, host-mapped stop word
+    float4 *stage = nullptr;
+    uint64_t stage_cap = 0;
+    uint32_t *stop_host = nullptr, *stop_dev = nullptr;
+    Ctrl *ctrl_ring = nullptr;   // pinned copies of the control block, one per chunk in flight
+    cudaEvent_t chunk_ev[2] = {nullptr, nullptr};
     // guided rendering
     uint32_t gcap = 0, gbatch = 0;
     __nv_bfloat16 *gfeat = nullptr;   // network outputs [cap][40] (BF16) of one bounce step
@@ -1007,6 +1206,11 @@ struct RenderCache {
     ~RenderCache() {
         if (dims) cudaFree(dims);
         if (host_ctrl) cudaFreeHost(host_ctrl);
+        if (stage) cudaFree(stage);
+        if (stop_host) cudaFreeHost(stop_host);
+        if (ctrl_ring) cudaFreeHost(ctrl_ring);
+        for (cudaEvent_t e : chunk_ev)
+            if (e) cudaEventDestroy(e);
         for (void *p : {(void *)gfeat, (void *)tr_feat, (void *)tr_wi, (void *)tr_w, (void *)grec, (void *)gnrec,
                         (void *)sort_hist, (void *)sort_buf[0], (void *)sort_buf[1]})
             if (p) cudaFree(p);
@@ -1156,6 +1360,268 @@ static RenderCache *cache_of(rt_film *f) {
     return (RenderCache *)f->cache;
 }
 
+// Pool capacity of the regeneration scheduler when the caller leaves it to
+// the library: 2^24 paths (about 2.8 GB of state) or the whole request if
+// smaller, at most a quarter of the free device memory.
+static uint32_t regen_capacity(uint64_t paths) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)1 << 30;
+    const uint64_t by_mem = (uint64_t)(free_b / 4 / kPoolBytesPerPath);
+    return (uint32_t)std::max<uint64_t>(std::min<uint64_t>({paths, (uint64_t)1 << 24, by_mem}), 32u);
+}
+
+// rt_render with regeneration (Sec. 3.1.3): windows of consecutive tasks
+// stream through the pool; bounce steps are issued in chunks and the host
+// reads the control block of the chunk before the last one (so one chunk is
+// always queued behind the running one) to see when the window is done.
+// While it waits it relays the caller's abort flag and the time budget to a
+// host-mapped word that k_regen_step_end reads; the device also compares its
+// own clock with the deadline. Once stopped, no task starts, the paths in
+// flight finish, and the film receives the contiguous range of tasks that
+// completed (possibly ending inside an iteration; the next call continues
+// there).
+static rt_status render_regen(const rt_scene *s, const rt_camera *cam, uint32_t spp, uint32_t max_depth,
+                              rt_film *film, const rt_render_opts &o, cudaStream_t st, RenderCache *rc,
+                              uint32_t cap) {
+    const uint32_t W = cam->width, H = cam->height;
+    const uint64_t WH = (uint64_t)W * H;
+    RenderParams P;
+    P.sc = s->dev;
+    P.cam = make_camera(*cam);
+    P.en = make_enum(W, H);
+    P.dims = rc->dims;
+    P.max_depth = max_depth;
+    P.sigma = o.filter_sigma == 0.f ? 0.5f : o.filter_sigma;
+    P.mis_mode = o.mis_mode;
+    P.rr = o.rr_enable;
+    const uint32_t tail = o.tail_threshold ? o.tail_threshold : 8192u;
+    const float frac = o.regen_fraction > 0.f ? o.regen_fraction : 0.5f;
+    const uint32_t regen_min = std::max<uint32_t>(1u, (uint32_t)std::min<double>((double)cap, std::ceil(frac * cap)));
+    Pool pool = rc->pool.view;
+    pool.task = rc->pool.task;
+    pool.qd = rc->pool.qd;
+    pool.qfree = rc->pool.qfree;
+    // staging window: the request, at most 2^30 tasks and a quarter of the
+    // free device memory (16 bytes per task)
+    const uint64_t t_begin = film->next_task, t_end = (film->next_task / WH + (uint64_t)spp) * WH;
+    uint64_t win = std::min<uint64_t>(t_end - t_begin, (uint64_t)1 << 30);
+    {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && rc->stage_cap < win)
+            win = std::max<uint64_t>(std::min<uint64_t>(win, free_b / 4 / sizeof(float4)), std::min<uint64_t>(win, cap));
+    }
+    if (rc->stage_cap < win) {
+        if (rc->stage) cudaFree(rc->stage);
+        rc->stage = nullptr;
+        rc->stage_cap = 0;
+        if (cudaMalloc(&rc->stage, win * sizeof(float4)) != cudaSuccess) {
+            set_error("rt_render: staging buffer allocation failed");
+            return RT_OOM;
+        }
+        rc->stage_cap = win;
+    }
+    if (!rc->stop_host) {
+        RT_CUDA_TRY(cudaHostAlloc(&rc->stop_host, sizeof(uint32_t), cudaHostAllocMapped));
+        RT_CUDA_TRY(cudaHostGetDevicePointer((void **)&rc->stop_dev, rc->stop_host, 0));
+    }
+    if (!rc->ctrl_ring) RT_CUDA_TRY(cudaMallocHost(&rc->ctrl_ring, 2 * sizeof(Ctrl)));
+    for (cudaEvent_t &e : rc->chunk_ev)
+        if (!e) RT_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    *(volatile uint32_t *)rc->stop_host = 0u;
+
+    const int gb = o.block_size ? (int)o.block_size : 128;
+    const bool prof = o.profile >= 1, count = o.profile >= 2;
+    const TraceKernels tk = trace_kernels(count, o.trace_kernel == 1 ? 0 : o.trace_kernel, s->dev.two_level, gb);
+    const int g_shade = grid_persistent(k_shade<true>, gb, 0);
+    const int g_regen = grid_for(k_regen, 256, cap);
+    const int g_init = grid_for(k_regen_init, 256, cap);
+    const int g_mega = grid_for(k_megakernel, gb, cap);
+    const uint32_t nmat = s->num_materials;
+    const uint32_t nkeys_mat = nmat + 1, nkeys_ray = 8u * 512u;
+    const int g_hist = grid_for(k_sort_scatter<RayKey>, 256, cap);
+    if ((o.sort_by_material || o.sort_rays) && (rc->sort_cap < cap || rc->sort_nkeys < std::max(nkeys_mat, nkeys_ray))) {
+        for (void *p : {(void *)rc->sort_hist, (void *)rc->sort_buf[0], (void *)rc->sort_buf[1]})
+            if (p) cudaFree(p);
+        rc->sort_hist = rc->sort_buf[0] = rc->sort_buf[1] = nullptr;
+        const uint32_t nk = std::max(nkeys_mat, nkeys_ray);
+        if (cudaMalloc(&rc->sort_hist, sizeof(uint32_t) * nk) != cudaSuccess ||
+            cudaMalloc(&rc->sort_buf[0], sizeof(uint32_t) * (size_t)cap) != cudaSuccess ||
+            cudaMalloc(&rc->sort_buf[1], sizeof(uint32_t) * (size_t)cap) != cudaSuccess) {
+            set_error("rt_render: sort buffers");
+            return RT_OOM;
+        }
+        rc->sort_cap = cap;
+        rc->sort_nkeys = nk;
+    }
+    RayKey rkey;
+    rkey.lo = s->dev.bb_lo;
+    rkey.inv_ext = make_float3(1.f / fmaxf(s->dev.bb_hi.x - s->dev.bb_lo.x, 1e-20f),
+                               1.f / fmaxf(s->dev.bb_hi.y - s->dev.bb_lo.y, 1e-20f),
+                               1.f / fmaxf(s->dev.bb_hi.z - s->dev.bb_lo.z, 1e-20f));
+    MatKey mkey{s->dev, nmat};
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> evs;
+    auto mark = [&](int kind) -> cudaEvent_t {
+        if (!prof) return nullptr;
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, st);
+        evs.push_back({kind, {a, b}});
+        return b;
+    };
+    auto done_ev = [&](cudaEvent_t b) {
+        if (b) cudaEventRecord(b, st);
+    };
+    rt_stats stats{};
+    const auto t_start = std::chrono::steady_clock::now();
+    auto elapsed_ms = [&]() {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    };
+    bool stop_sent = false;
+    auto relay = [&]() {
+        if (stop_sent) return;
+        if ((o.abort_flag && *o.abort_flag) || (o.time_budget_ms > 0 && elapsed_ms() >= o.time_budget_ms)) {
+            *(volatile uint32_t *)rc->stop_host = 1u;
+            stop_sent = true;
+        }
+    };
+    // wait for an event, relaying the stop conditions meanwhile
+    auto wait = [&](cudaEvent_t e) -> rt_status {
+        for (;;) {
+            const cudaError_t q = cudaEventQuery(e);
+            if (q == cudaSuccess) return RT_OK;
+            if (q != cudaErrorNotReady) return cuda_status(q, "rt_render: waiting for a bounce-step chunk");
+            relay();
+            std::this_thread::yield();
+        }
+    };
+    RT_CUDA_TRY(cudaMemsetAsync(pool.ctrl, 0, sizeof(Ctrl), st));
+    constexpr int kChunk = 4;                       // bounce steps per host check
+    const uint64_t step_limit = 64ull + 4ull * (max_depth + 2) * ((t_end - t_begin) / std::max<uint64_t>(cap / 2, 1) + 2);
+    uint64_t t = t_begin;
+    rt_status result = RT_OK;
+    bool stopped = false;
+    while (t < t_end && !stopped) {
+        const uint32_t n_win = (uint32_t)std::min<uint64_t>(t_end - t, win);
+        double left_ms = o.time_budget_ms > 0 ? o.time_budget_ms - elapsed_ms() : 0.0;
+        const unsigned long long budget_ns =
+            o.time_budget_ms > 0 ? (unsigned long long)std::max(1.0, left_ms * 1e6) : 0ull;
+        cudaEvent_t e = mark(4);
+        relay();
+        k_regen_init<<<g_init, 256, 0, st>>>(P, pool, t, n_win, (uint32_t)WH, tail, budget_ns, rc->stop_dev);
+        done_ev(e);
+        ++stats.kernel_launches;
+        uint64_t steps = 0;
+        // a window that fits in the pool starts every task at once: its paths
+        // end within max_depth + 1 steps, issued without a host check
+        const bool one_load = n_win <= cap;
+        const int per_chunk = one_load ? (int)max_depth + 1 : kChunk;
+        for (int chunk = 0;; ++chunk) {
+            for (int k = 0; k < per_chunk; ++k) {
+                const uint32_t *rsorted = nullptr;
+                if (o.sort_rays) {
+                    e = mark(4);
+                    RT_CUDA_TRY(cudaMemsetAsync(rc->sort_hist, 0, sizeof(uint32_t) * nkeys_ray, st));
+                    k_sort_hist<RayKey><<<g_hist, 256, nkeys_ray * sizeof(uint32_t), st>>>(rkey, pool, nkeys_ray,
+                                                                                          rc->sort_hist);
+                    k_sort_scan<<<1, 1024, 0, st>>>(pool, nkeys_ray, rc->sort_hist);
+                    k_sort_scatter<RayKey><<<g_hist, 256, 0, st>>>(rkey, pool, rc->sort_hist, rc->sort_buf[0]);
+                    done_ev(e);
+                    rsorted = rc->sort_buf[0];
+                    stats.kernel_launches += 3;
+                }
+                e = mark(0);
+                tk.ext<<<tk.grid_ext, gb, tk.smem, st>>>(s->dev, pool, rsorted);
+                done_ev(e);
+                const uint32_t *sorted = rsorted;
+                if (o.sort_by_material) {
+                    e = mark(4);
+                    RT_CUDA_TRY(cudaMemsetAsync(rc->sort_hist, 0, sizeof(uint32_t) * nkeys_mat, st));
+                    k_sort_hist<MatKey><<<g_hist, 256, nkeys_mat * sizeof(uint32_t), st>>>(mkey, pool, nkeys_mat,
+                                                                                          rc->sort_hist);
+                    k_sort_scan<<<1, 1024, 0, st>>>(pool, nkeys_mat, rc->sort_hist);
+                    k_sort_scatter<MatKey><<<g_hist, 256, 0, st>>>(mkey, pool, rc->sort_hist, rc->sort_buf[1]);
+                    done_ev(e);
+                    sorted = rc->sort_buf[1];
+                    stats.kernel_launches += 3;
+                }
+                e = mark(1);
+                (s->dev.lb_rec ? k_shade<true> : k_shade<false>)<<<g_shade, gb, 0, st>>>(P, pool, sorted);
+                done_ev(e);
+                e = mark(2);
+                tk.shadow<<<tk.grid_shadow, gb, tk.smem, st>>>(s->dev, pool, nullptr);
+                done_ev(e);
+                e = mark(4);
+                k_regen<<<g_regen, 256, 0, st>>>(P, pool, rc->stage, t, (uint32_t)WH, regen_min);
+                k_regen_step_end<<<1, 1, 0, st>>>(pool, regen_min, rc->stop_dev);
+                done_ev(e);
+                stats.kernel_launches += 5;
+                ++stats.trace_launches;
+                ++stats.wavefront_steps;
+            }
+            steps += per_chunk;
+            RT_CUDA_TRY(cudaGetLastError());
+            if (one_load) break;
+            Ctrl *ring = rc->ctrl_ring;
+            RT_CUDA_TRY(cudaMemcpyAsync(ring + (chunk & 1), pool.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+            RT_CUDA_TRY(cudaEventRecord(rc->chunk_ev[chunk & 1], st));
+            if (chunk == 0) continue;
+            rt_status ws = wait(rc->chunk_ev[(chunk - 1) & 1]);
+            if (ws != RT_OK) return ws;
+            const Ctrl &hc = ring[(chunk - 1) & 1];
+            if (hc.tail || (hc.n_ext == 0 && (hc.stop || hc.task_next == hc.n_tasks))) break;
+            if (steps > step_limit) {
+                set_error("rt_render: the regeneration scheduler did not drain its window");
+                return RT_CUDA_ERROR;
+            }
+        }
+        e = mark(3);
+        k_megakernel<<<g_mega, gb, 0, st>>>(P, pool);
+        done_ev(e);
+        e = mark(4);
+        k_regen_retire_tail<<<g_regen, 256, 0, st>>>(pool, rc->stage);
+        RT_CUDA_TRY(cudaMemcpyAsync(rc->host_ctrl, pool.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+        rt_status ws = RT_OK;
+        RT_CUDA_TRY(cudaEventRecord(rc->chunk_ev[0], st));
+        if ((ws = wait(rc->chunk_ev[0])) != RT_OK) return ws;
+        const uint32_t done_tasks = rc->host_ctrl->task_next;
+        k_film_range<<<grid_for(k_film_range, 256, WH), 256, 0, st>>>(rc->stage, film->sum, film->sum2, film->count,
+                                                                      t, done_tasks, (uint32_t)WH);
+        done_ev(e);
+        stats.kernel_launches += 3;
+        ++stats.tail_launches;
+        ++stats.waves;
+        RT_CUDA_TRY(cudaGetLastError());
+        RT_CUDA_TRY(cudaStreamSynchronize(st));
+        t += done_tasks;
+        film->next_task = t;
+        stats.paths += done_tasks;
+        if (rc->host_ctrl->overflow) { set_error("BVH traversal stack overflow"); result = RT_STACK_OVERFLOW; break; }
+        if (rc->host_ctrl->stop || done_tasks < n_win) stopped = true;
+    }
+    if (stopped && t < t_end && result == RT_OK) {
+        set_error("rt_render: stopped by time budget or abort flag (resumable: the film holds the completed tasks)");
+        result = RT_TIMEOUT;
+    }
+    for (auto &kv : evs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, kv.second.first, kv.second.second);
+        double *dst[5] = {&stats.trace_ms, &stats.shade_ms, &stats.shadow_ms, &stats.megakernel_ms, &stats.other_ms};
+        *dst[kv.first] += ms;
+        cudaEventDestroy(kv.second.first);
+        cudaEventDestroy(kv.second.second);
+    }
+    stats.extension_rays = rc->host_ctrl->ext_rays;
+    stats.shadow_rays = rc->host_ctrl->shadow_rays;
+    stats.ext_nodes = rc->host_ctrl->ext_nodes;
+    stats.ext_tris = rc->host_ctrl->ext_tris;
+    stats.shadow_nodes = rc->host_ctrl->shadow_nodes;
+    stats.shadow_tris = rc->host_ctrl->shadow_tris;
+    stats.regen_sets = rc->host_ctrl->regen_sets;
+    if (o.stats) *o.stats = stats;
+    return result;
+}
+
 extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t spp, uint32_t max_depth,
                                rt_film *film, const rt_render_opts *opts_in, void *stream) {
     if (!s || !cam || !film) { set_error("rt_render: null argument"); return RT_INVALID_ARG; }
@@ -1172,8 +1638,17 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     RenderCache *rc = cache_of(film);
     const uint32_t W = cam->width, H = cam->height;
     const uint64_t WH = (uint64_t)W * H;
+    const uint64_t request = (film->next_task / WH + (uint64_t)spp) * WH - film->next_task;
+    // the regeneration scheduler streams tasks through a bounded pool; the
+    // iteration-set scheduler (A/B) holds a whole set at once
+    const bool regen = !o.guide && o.scheduler == 0 && !o.megakernel_only;
+    if (o.scheduler < 0 || o.scheduler > 1) { set_error("rt_render: scheduler must be 0 or 1"); return RT_INVALID_ARG; }
+    if (!(o.regen_fraction >= 0.f && o.regen_fraction <= 1.f)) {
+        set_error("rt_render: regen_fraction must be in [0, 1]");
+        return RT_INVALID_ARG;
+    }
     uint32_t cap = o.max_paths_in_flight ? o.max_paths_in_flight
-                                         : default_capacity((film->next_task / WH + (uint64_t)spp) * WH - film->next_task);
+                                         : (regen ? regen_capacity(request) : default_capacity(request));
     cap = std::max<uint32_t>(cap, 32u);
     rt_status rs = ensure_pool(rc->pool, cap);
     if (rs != RT_OK) return rs;
@@ -1187,6 +1662,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         rc->dims_n = ndims;
     }
     if (!rc->host_ctrl) RT_CUDA_TRY(cudaMallocHost(&rc->host_ctrl, sizeof(Ctrl)));
+    if (regen) return render_regen(s, cam, spp, max_depth, film, o, st, rc, cap);
     RenderParams P;
     P.sc = s->dev;
     P.cam = make_camera(*cam);
@@ -2190,5 +2666,68 @@ extern "C" rt_status rt_autotune(const rt_render_job *jobs, int32_t njobs, uint3
         if (ms < best) { best = ms; best_block = b; }
     }
     opts->block_size = best_block;
+    return RT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host test hook of the regeneration bookkeeping: the slot decisions of
+// k_regen_init, k_regen and k_regen_step_end (the same functions) driven by
+// synthetic path lengths instead of shading. n_tasks tasks, `cap` slots,
+// task k lives life[k] >= 1 bounce steps; a stop after `stop_step` steps
+// (~0u: none). Writes per task the step at which it was retired (~0u: never
+// started) and returns the steps taken and the steps that refilled slots.
+extern "C" rt_status rt_debug_regen_host(uint32_t n_tasks, uint32_t cap, uint32_t regen_min, const uint8_t *life,
+                                         uint32_t stop_step, uint32_t *retired_at, uint32_t *steps,
+                                         uint32_t *regen_steps) {
+    if (cap == 0 || regen_min == 0 || !life || !retired_at || !steps || !regen_steps) {
+        rtg::set_error("rt_debug_regen_host: invalid argument");
+        return RT_INVALID_ARG;
+    }
+    using namespace rtg;
+    std::vector<uint32_t> task(cap, ~0u), q[2] = {std::vector<uint32_t>(cap), std::vector<uint32_t>(cap)};
+    std::vector<uint32_t> qd(cap), qfree(cap), left(cap, 0);
+    for (uint32_t k = 0; k < n_tasks; ++k) retired_at[k] = ~0u;
+    Ctrl c{};
+    const uint32_t k0 = std::min(cap, n_tasks);
+    for (uint32_t s = 0; s < cap; ++s) {
+        if (s < k0) { task[s] = s; left[s] = life[s]; q[0][s] = s; }
+        else qfree[s - k0] = s;
+    }
+    c.n_ext = k0; c.n_free = cap - k0; c.task_next = k0; c.n_tasks = n_tasks;
+    uint32_t step = 0;
+    const uint32_t limit = 64u + 4u * 256u * (n_tasks / std::max(1u, cap / 2) + 2u);
+    while (c.n_ext > 0 || (!c.stop && c.task_next < c.n_tasks)) {
+        if (++step > limit) { set_error("rt_debug_regen_host: no progress"); return RT_CUDA_ERROR; }
+        // "shade": every live path takes one step; ended ones go to the dead list
+        std::vector<uint32_t> &cur = q[c.cur], &next = q[c.cur ^ 1u];
+        for (uint32_t i = 0; i < c.n_ext; ++i) {
+            const uint32_t s = cur[i];
+            if (--left[s] > 0) next[c.n_next++] = s;
+            else qd[c.n_dead++] = s;
+        }
+        if (c.n_next + c.n_dead != c.n_ext) { set_error("rt_debug_regen_host: lost a path"); return RT_CUDA_ERROR; }
+        // k_regen
+        const uint32_t n_dead = c.n_dead, n_free = c.n_free, n_new = regen_count(&c, regen_min);
+        for (uint32_t j = 0; j < std::max(n_dead, n_new); ++j) {
+            uint32_t retire;
+            const uint32_t slot = regen_slot(j, n_dead, n_free, n_new, qd.data(), qfree.data(), &retire);
+            if (retire != ~0u) {
+                if (retired_at[task[retire]] != ~0u) { set_error("rt_debug_regen_host: task retired twice"); return RT_CUDA_ERROR; }
+                retired_at[task[retire]] = step;
+            }
+            if (slot != ~0u) {
+                if (slot >= cap || c.n_next + j >= cap) { set_error("rt_debug_regen_host: slot out of range"); return RT_CUDA_ERROR; }
+                const uint32_t off = c.task_next + j;
+                task[slot] = off;
+                left[slot] = life[off];
+                next[c.n_next + j] = slot;
+            }
+        }
+        regen_advance(&c, regen_min);
+        if (c.n_ext + c.n_free != cap) { set_error("rt_debug_regen_host: slots lost or duplicated"); return RT_CUDA_ERROR; }
+        if (step >= stop_step) c.stop = 1u;
+    }
+    *steps = step;
+    *regen_steps = c.regen_sets;
     return RT_OK;
 }

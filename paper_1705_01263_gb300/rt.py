@@ -62,7 +62,7 @@ class rt_stats(C.Structure):
                 ("kernel_launches", C.c_uint32), ("trace_ms", C.c_double), ("shade_ms", C.c_double),
                 ("shadow_ms", C.c_double), ("megakernel_ms", C.c_double), ("other_ms", C.c_double),
                 ("trace_launches", C.c_uint32), ("ext_nodes", C.c_uint64), ("ext_tris", C.c_uint64),
-                ("shadow_nodes", C.c_uint64), ("shadow_tris", C.c_uint64)]
+                ("shadow_nodes", C.c_uint64), ("shadow_tris", C.c_uint64), ("regen_sets", C.c_uint32)]
 
 
 class rt_render_opts(C.Structure):
@@ -71,7 +71,8 @@ class rt_render_opts(C.Structure):
                 ("megakernel_only", C.c_int32), ("sort_by_material", C.c_int32),
                 ("tail_threshold", C.c_uint32), ("block_size", C.c_uint32),
                 ("abort_flag", C.c_void_p), ("guide", C.c_void_p), ("stats", C.POINTER(rt_stats)),
-                ("profile", C.c_int32), ("trace_kernel", C.c_int32), ("sort_rays", C.c_int32)]
+                ("profile", C.c_int32), ("trace_kernel", C.c_int32), ("sort_rays", C.c_int32),
+                ("scheduler", C.c_int32), ("regen_fraction", C.c_float)]
 
 
 class rt_render_job(C.Structure):
@@ -136,6 +137,7 @@ def _declare(L):
         "rt_gemm_bf16": [vp, vp, vp, i32, i32, i32, i32, i32, i32, i32, vp],
         "rt_debug_trace_host": [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp],
         "rt_debug_trace_host_stack": [vp, vp, i64, i32, i32, vp, vp],
+        "rt_debug_regen_host": [u32, u32, u32, vp, u32, vp, vp, vp],
         "rt_debug_env_sample_host": [vp, vp, vp, vp, i64, vp, vp, vp],
         "rt_debug_light_bvh_host": [vp, vp, vp, vp, i64, vp, vp, vp],
         "rt_debug_render_host": [vp, C.POINTER(rt_camera), u32, C.POINTER(rt_render_opts), vp, vp, vp, i64, vp],
@@ -372,7 +374,8 @@ def make_camera(cam) -> rt_camera:
 def make_opts(sigma: float = 0.5, rr: bool = False, mis_mode: int = 0, seed: int = 0, time_budget_ms: float = 0.0,
               max_paths: int = 0, megakernel_only: bool = False, sort_by_material: bool = False,
               tail_threshold: int = 0, abort_flag=None, guide=None, stats: Optional[rt_stats] = None,
-              profile: int = 0, trace_kernel: int = 0, sort_rays: bool = False, block_size: int = 0):
+              profile: int = 0, trace_kernel: int = 0, sort_rays: bool = False, block_size: int = 0,
+              scheduler: int = 0, regen_fraction: float = 0.0):
     o = rt_render_opts()
     o.filter_sigma = sigma if sigma > 0 else -1.0
     o.rr_enable, o.mis_mode, o.seed = int(rr), mis_mode, seed
@@ -389,6 +392,8 @@ def make_opts(sigma: float = 0.5, rr: bool = False, mis_mode: int = 0, seed: int
     o.trace_kernel = trace_kernel
     o.sort_rays = int(sort_rays)
     o.block_size = block_size
+    o.scheduler = scheduler
+    o.regen_fraction = regen_fraction
     return o
 
 
@@ -591,6 +596,19 @@ def debug_trace_host_stack(scene: Scene, rays: np.ndarray, stack_entries: int, a
     check(lib().rt_debug_trace_host_stack(scene.handle, r.ctypes.data, n, int(any_hit), int(stack_entries),
                                           prim.ctypes.data, t.ctypes.data))
     return prim, t
+
+
+def debug_regen_host(life: np.ndarray, cap: int, regen_min: int, stop_step: int = 0xFFFFFFFF):
+    """Host run of the regeneration scheduler's slot bookkeeping with path
+    lengths `life` (uint8, >= 1 per task): (step at which each task was
+    retired, or 0xFFFFFFFF if never started; steps; refilling steps)."""
+    life = np.ascontiguousarray(life, np.uint8)
+    n = life.size
+    out = np.zeros(n, np.uint32)
+    steps, regen = C.c_uint32(), C.c_uint32()
+    check(lib().rt_debug_regen_host(n, cap, regen_min, life.ctypes.data, stop_step, out.ctypes.data,
+                                    C.byref(steps), C.byref(regen)))
+    return out, steps.value, regen.value
 
 
 def debug_env_sample_host(scene: Scene, ng, u, v):

@@ -2,6 +2,7 @@
 function declared in include/rt.h; host logic (strength-reduced division,
 BVH8 build, traversal and per-sample path code executed on the host) agrees
 with the oracle."""
+import math
 import os
 import re
 import subprocess
@@ -375,3 +376,43 @@ def _no_overflow(s, rays, k):
     except rt.RtError as e:
         assert e.status == 6
         return False
+
+
+@pytest.mark.parametrize("n,cap,frac", [(10_000, 1000, 0.5), (10_000, 1000, 1e-9), (10_000, 1000, 1.0),
+                                        (5000, 8192, 0.5), (777, 64, 0.5), (1, 32, 0.5), (65_536, 4096, 0.25)])
+def test_regeneration_bookkeeping_on_the_host(n, cap, frac):
+    """The slot decisions of the regeneration scheduler (the same functions
+    the kernels call), driven by random path lengths: every task starts and
+    is retired exactly once, after exactly its length in steps; the pool
+    never holds more than its capacity; refills happen only once at least
+    the fraction has ended."""
+    rng = np.random.default_rng(n + cap)
+    life = rng.integers(1, 18, n).astype(np.uint8)
+    regen_min = max(1, int(math.ceil(frac * cap)))
+    at, steps, regen = rt.debug_regen_host(life, cap, regen_min)
+    assert np.all(at != 0xFFFFFFFF)
+    # tasks start in order; a task started at step s0 retires at s0 + life
+    # (tasks of the first load start at step 0)
+    start = at.astype(np.int64) - life
+    assert np.all(start[:min(n, cap)] == 0)
+    assert np.all(np.diff(start) >= 0)
+    assert steps == at.max()
+    if n > cap:
+        assert regen > 0
+        # never more live paths than slots
+        for s in np.unique(start):
+            live = np.sum((start <= s) & (at > s))
+            assert live <= cap
+    else:
+        assert regen == 0
+
+
+def test_regeneration_stop_drains_a_contiguous_range_on_the_host():
+    """After a stop no task starts; the retired tasks are exactly a prefix."""
+    rng = np.random.default_rng(3)
+    life = rng.integers(1, 18, 50_000).astype(np.uint8)
+    at, steps, _ = rt.debug_regen_host(life, 2048, 1024, stop_step=20)
+    done = at != 0xFFFFFFFF
+    k = int(done.sum())
+    assert 2048 < k < 50_000 and np.all(done[:k]) and not done[k:].any()
+    assert steps <= 20 + 17

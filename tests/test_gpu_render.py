@@ -198,18 +198,20 @@ def test_deterministic_and_split_merge():
 
 
 def test_abort_flag_and_resume():
+    """Iteration-set scheduler: the abort flag is checked between sets, the
+    film holds whole sets."""
     from paper_1705_01263_gb300 import rt
     sd, cam = scenes.cornell_box()
     s = rt.Scene(sd)
-    ref, _, _ = gpu_render(s, cam, 12, 8, max_paths=4096 * 3)
+    ref, _, _ = gpu_render(s, cam, 12, 8, max_paths=4096 * 3, scheduler=1)
     flag = np.ones(1, np.int32)
     f = rt.Film(cam.width, cam.height)
     _, st1, status = gpu_render(s, cam, 12, 8, film=f, max_paths=4096 * 3, abort_flag=flag.ctypes.data,
-                                allow_timeout=True)
+                                allow_timeout=True, scheduler=1)
     assert status == rt.RT_TIMEOUT and st1.waves == 1 and f.next_iteration() == 3
     _, _, c_mid = f.download()
     assert np.all(c_mid == 3)
-    _, st2, status = gpu_render(s, cam, 9, 8, film=f, max_paths=4096 * 3)
+    _, st2, status = gpu_render(s, cam, 9, 8, film=f, max_paths=4096 * 3, scheduler=1)
     assert status == rt.RT_OK and f.next_iteration() == 12
     sa, s2a, ca = ref.download()
     sb, s2b, cb = f.download()
@@ -224,7 +226,7 @@ def test_small_pool_partial_passes():
     sd, cam = scenes.cornell_box()
     s = rt.Scene(sd)
     a, _, _ = gpu_render(s, cam, 4, 8)
-    b, st, _ = gpu_render(s, cam, 4, 8, max_paths=1000)
+    b, st, _ = gpu_render(s, cam, 4, 8, max_paths=1000, scheduler=1)
     assert st.waves == 4 * 5
     ma, _, ca = resolved(a)
     mb, _, cb = resolved(b)
