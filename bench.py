@@ -106,8 +106,16 @@ class ClockSampler:
 
 
 def cpu_model():
-    """Host CPU model from /proc/cpuinfo (x86 "model name", Arm implementer /
-    part), or "unknown"."""
+    """Host CPU model: lscpu's "Model name" (and vendor), else /proc/cpuinfo
+    (x86 "model name", Arm implementer / part), else "unknown"."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        kv = dict(l.split(":", 1) for l in out.splitlines() if ":" in l)
+        kv = {k.strip(): v.strip() for k, v in kv.items()}
+        if kv.get("Model name"):
+            return " ".join(x for x in (kv.get("Vendor ID"), kv["Model name"]) if x)
+    except (OSError, subprocess.SubprocessError, ValueError):
+        pass
     try:
         txt = open("/proc/cpuinfo").read()
     except OSError:
@@ -139,10 +147,17 @@ def cpu_baseline_oracle(sd, cam):
     dt = time.time() - t0
     paths = int(cnt.sum())
     cores = os.cpu_count() or 1
+    # one core: the same camera at a quarter of the resolution, 1 spp
+    c1 = sc_mod.Camera(cam.eye, cam.look_at, cam.up, cam.vfov_deg, W // 4, H // 4)
+    t0 = time.time()
+    _, _, cnt1, _ = osc.render(c1, 1, DEPTH, threads=1)
+    dt1 = time.time() - t0
     return {"value": paths / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{W}x{H} px x {spp} spp of the same scene and camera (depth {DEPTH}), "
                       f"{paths} paths in {dt:.1f} s; oracle BVH build {build_s:.1f} s not timed",
-            "mrays_per_s": rays / dt / 1e6, "cpu": cpu_model()}
+            "mrays_per_s": rays / dt / 1e6, "cpu": cpu_model(),
+            "one_core": {"value": int(cnt1.sum()) / dt1 / 1e6, "unit": UNIT, "cores": 1,
+                         "sample": f"{W // 4}x{H // 4} px x 1 spp, {int(cnt1.sum())} paths in {dt1:.1f} s"}}
 
 
 def _oracle_many_lights_worker(conn):
@@ -778,14 +793,17 @@ def run_reference(args):
     sd, cam = scenes.sphere_field()
     import oracle
     osc = oracle.Scene(sd)
-    W, H = 240, 135
+    # each timed step: the workload's own image (1920 x 1080) at one of its
+    # 64 iterations (about 2 s on 16 cores); warm-up steps on a small crop
+    W, H = cam.width, cam.height
     c2 = scenes.Camera(cam.eye, cam.look_at, cam.up, cam.vfov_deg, W, H)
+    cw = scenes.Camera(cam.eye, cam.look_at, cam.up, cam.vfov_deg, 240, 135)
     for _ in range(args.warmup):
-        osc.render(c2, 1, DEPTH)
+        osc.render(cw, 1, DEPTH)
     times, paths = [], 0
     for k in range(args.steps):
         t0 = time.time()
-        _, _, cnt, _ = osc.render(c2, 1, DEPTH, iter0=k)
+        _, _, cnt, _ = osc.render(c2, 1, DEPTH, iter0=k % SPP)
         times.append(time.time() - t0)
         paths += int(cnt.sum())
     total = sum(times)
@@ -794,7 +812,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "reference_sample": f"{W}x{H} px, 1 spp per step"},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "reference_sample": f"{W}x{H} px, 1 of the {SPP} spp per step"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                              "sample": f"{W}x{H} px x 1 spp per step of the same scene/camera, depth {DEPTH}"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -52,7 +52,7 @@ class _Cam(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("filter_sigma", C.c_double), ("rr_enable", C.c_int32), ("mis_mode", C.c_int32),
-                ("seed", C.c_uint64), ("threads", C.c_int32)]
+                ("seed", C.c_uint64), ("threads", C.c_int32), ("lt_aim", C.c_int32)]
 
 
 def _declare(L):
@@ -100,6 +100,13 @@ def _declare(L):
         "or_lb_node_info": (None, [vp, C.c_int32, vp, vp, vp, vp]),
         "or_lb_region": (C.c_int, [vp]),
         "or_lb_light_of_tri": (i64, [vp, i64]),
+        "or_pa_info": (C.c_int32, [vp, vp, vp, vp]),
+        "or_pa_eye": (None, [vp, C.POINTER(_Cam), vp]),
+        "or_pa_probs": (None, [vp, vp, vp, vp, vp]),
+        "or_pa_sample": (C.c_int32, [vp, vp, vp, vp, f64, vp]),
+        "or_pa_env_density": (f64, [vp, vp, vp, vp]),
+        "or_pa_dir_density": (f64, [vp, vp, vp, vp, vp]),
+        "or_pa_cone_sample": (None, [vp, C.c_int32, vp, f64, f64, vp]),
         "or_vmf_pdf": (f64, [f64, vp, vp]),
         "or_vmf_sample": (None, [f64, vp, f64, f64, vp]),
         "or_oneblob": (None, [vp, vp]),
@@ -247,12 +254,13 @@ class Scene:
         return s, s2, cnt, int(rays[0])
 
     def render_two_way(self, cam, spp: int, max_depth: int, iter0: int = 0, sigma: float = 0.5,
-                       mis_mode: int = 0, lt_mode: int = 0, seed: int = 0, threads: int = 0):
+                       mis_mode: int = 0, lt_mode: int = 0, seed: int = 0, threads: int = 0, aim: bool = True):
         """Two-way path tracing (Sec. 2): camera stage sums (with the light
         tracer as a third MIS technique) and the light stage's splats; the
-        per-pixel estimate is (sum + splat) / count."""
+        per-pixel estimate is (sum + splat) / count. aim: photon aiming
+        (Sec. 2.1.3), else emission uniform over the scene's bound."""
         c = _camera(cam)
-        o = _Opts(sigma, 0, mis_mode, seed, threads)
+        o = _Opts(sigma, 0, mis_mode, seed, threads, int(aim))
         W, H = cam.width, cam.height
         s, s2, sp = np.zeros((H, W, 3)), np.zeros((H, W, 3)), np.zeros((H, W, 3))
         cnt = np.zeros((H, W), np.uint32)
@@ -320,6 +328,48 @@ class Scene:
 
     def lb_light_of_tri(self, t: int) -> int:
         return lib().or_lb_light_of_tri(self.handle, t)
+
+    # ------------------------------------------ photon aiming (Sec. 2.1.3)
+    def pa_clusters(self):
+        """(cluster spheres [n][4]: centre, radius; cluster of every object)."""
+        n_obj = C.c_int32()
+        n = lib().or_pa_info(self.handle, None, None, C.byref(n_obj))
+        cc = np.zeros((n, 4))
+        oc = np.zeros(n_obj.value, np.int32)
+        lib().or_pa_info(self.handle, _p(cc), _p(oc), None)
+        return cc, oc
+
+    def pa_eye(self, cam):
+        """Photon aiming's eye vector of a camera: (position, solid angle of its view cone)."""
+        out = np.zeros(4)
+        c = _camera(cam)
+        lib().or_pa_eye(self.handle, C.byref(c), _p(out))
+        return out
+
+    def pa_probs(self, eye, y=None, ny=None):
+        n = self.pa_clusters()[0].shape[0]
+        P = np.zeros(n)
+        lib().or_pa_probs(self.handle, _p(_f64(eye, 4)), None if y is None else _p(_f64(y, 3)),
+                          None if ny is None else _p(_f64(ny, 3)), _p(P))
+        return P
+
+    def pa_sample(self, eye, u, y=None, ny=None):
+        p = C.c_double()
+        c = lib().or_pa_sample(self.handle, _p(_f64(eye, 4)), None if y is None else _p(_f64(y, 3)),
+                               None if ny is None else _p(_f64(ny, 3)), u, C.byref(p))
+        return c, p.value
+
+    def pa_env_density(self, eye, x, w):
+        return lib().or_pa_env_density(self.handle, _p(_f64(eye, 4)), _p(_f64(x, 3)), _p(_f64(w, 3)))
+
+    def pa_dir_density(self, eye, y, ny, w):
+        return lib().or_pa_dir_density(self.handle, _p(_f64(eye, 4)), _p(_f64(y, 3)), _p(_f64(ny, 3)),
+                                       _p(_f64(w, 3)))
+
+    def pa_cone_sample(self, c, y, u1, u2):
+        w = np.zeros(3)
+        lib().or_pa_cone_sample(self.handle, c, _p(_f64(y, 3)), u1, u2, _p(w))
+        return w
 
     def render_probes(self, pos, nrm, spp: int, max_depth: int, iter0: int = 0, mis_mode: int = 0,
                       seed: int = 0, rr: bool = False):

@@ -609,6 +609,7 @@ or_scene *or_scene_create(const or_scene_desc *d) {
         or_build_lights(s);
         or_build_light_bvh(s);
     }
+    or_build_photon_aiming(s);
     return s;
 }
 
@@ -621,5 +622,6 @@ void or_scene_destroy(or_scene *s) {
     free(s->lb_nodes); free(s->lb_perm); free(s->lb_leaf_of);
     for (int l = 0; l < s->env_levels; ++l) free(s->env_w[l]);
     free(s->env_w); free(s->env_lw); free(s->env_lh); free(s->env_nw);
+    free(s->pa_cc); free(s->pa_nodes); free(s->pa_obj_cluster);
     free(s);
 }

@@ -157,6 +157,7 @@ typedef struct {
     int32_t mis_mode;      /* 0 power heuristic, 1 balance, 2 NEE only, 3 BSDF only */
     uint64_t seed;         /* scramble seed */
     int32_t threads;       /* worker threads, 0 = all cores */
+    int32_t lt_aim;        /* two-way: 1 photon aiming (Sec. 2.1.3), 0 uniform over the scene's bound */
 } or_render_opts;
 
 void or_camera_ray(const or_camera *c, double sx, double sy, double o[3],

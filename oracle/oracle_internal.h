@@ -43,7 +43,34 @@ struct or_scene {
     double *env_nw;          /* 64 cells x env_nstride */
     int64_t env_noff[32];    /* offset of level l inside a cell's block */
     int64_t env_nstride;
+    /* photon aiming (photon_aiming.c): clusters of objects (centre and
+     * radius of each cluster's sphere), the cluster of every object, and a
+     * binary hierarchy over the clusters, node 0 the root */
+    int32_t pa_nclusters, pa_nobjects, pa_nnodes;
+    double *pa_cc;           /* pa_nclusters x 4: centre, radius */
+    int32_t *pa_obj_cluster; /* pa_nobjects */
+    struct or_pa_node *pa_nodes;
 };
+
+typedef struct or_pa_node {
+    double c[3], r;          /* sphere enclosing every cluster sphere below */
+    int32_t left, right;     /* children, -1 in a leaf */
+    int32_t cluster;         /* leaf: its cluster; -1 otherwise */
+} or_pa_node;
+
+/* photon aiming (photon_aiming.c, Sec. 2.1.3); eye = (position, solid
+ * angle of the camera's view cone); y, ny = NULL for an environment photon */
+void or_build_photon_aiming(or_scene *s);
+double or_pa_p_left(const or_scene *s, int32_t node, const double eye[4], const double *y, const double *ny);
+int32_t or_pa_sample(const or_scene *s, const double eye[4], const double *y, const double *ny, double u,
+                     double *prob);
+void or_pa_probs(const or_scene *s, const double eye[4], const double *y, const double *ny, double *P);
+double or_pa_env_density(const or_scene *s, const double eye[4], const double x[3], const double w[3]);
+double or_pa_dir_density(const or_scene *s, const double eye[4], const double y[3], const double ny[3],
+                         const double w[3]);
+void or_pa_cone_sample(const or_scene *s, int32_t c, const double y[3], double u1, double u2, double w[3]);
+int32_t or_pa_info(const or_scene *s, double *spheres, int32_t *obj_cluster, int32_t *n_objects);
+void or_pa_eye(const or_scene *s, const or_camera *c, double out[4]);
 
 #define OR_LB_LEAF 4       /* emitters per leaf of the light hierarchy, at most */
 #define OR_LB_PMIN 0.1     /* clamp of a child's probability */
@@ -83,6 +110,8 @@ typedef struct {
     uint32_t W, H;
     double sigma;       /* pixel filter (> 0 Gaussian, else box) */
     double bc[3], br;   /* the scene's bounding sphere (environment photons) */
+    int aim;            /* photon aiming (Sec. 2.1.3) instead of uniform emission */
+    double aim_eye[4];  /* eye position and the solid angle of the view cone (photon aiming's estimates) */
 } or_tw_cam;
 
 /* camera frame and the scene's bounding sphere (centre and half diagonal of

@@ -471,6 +471,7 @@ void or_render_two_way(const or_scene *s, const or_camera *cam, uint32_t iter0, 
     ctx_init(&c, s, cam, max_depth, opts);
     c.tw = 1 + lt_mode;
     or_tw_cam_init(s, cam, opts->filter_sigma, &c.tc);
+    c.tc.aim = opts->lt_aim;
     int nth = opts->threads > 0 ? opts->threads : (int)sysconf(_SC_NPROCESSORS_ONLN);
     if (nth < 1) nth = 1;
     uint32_t H = cam->height;

@@ -56,8 +56,15 @@
  *     only if every density is the density of the sampler it names;
  *   - sample dimensions of light path m = iteration * W H + i (i < W H):
  *     base = 2 + 7 (D + 1) (after the camera path's), base + {0: emitter,
- *     1,2: point, 3,4: direction}, then vertex t (1-based) base + 5 +
- *     3 (t - 1) + {0: lobe, 1,2: direction}.
+ *     1,2: point (environment: direction), 3,4: direction (environment:
+ *     disk point), 5: cluster of photon aiming}, then vertex t (1-based)
+ *     base + 6 + 3 (t - 1) + {0: lobe, 1,2: direction};
+ *   - photon aiming (Sec. 2.1.3, photon_aiming.c; lt_aim): an environment
+ *     photon's disk is that of the chosen cluster, its first hit's area
+ *     density p_env p(w) |cos| D(x, w) with D the line density of
+ *     or_pa_env_density; a triangle photon's direction is drawn in the
+ *     chosen cluster's cone, its solid-angle density or_pa_dir_density
+ *     replacing the cosine distribution's cos / pi.
  */
 #include "oracle.h"
 #include "oracle_internal.h"
@@ -122,6 +129,19 @@ void or_tw_cam_init(const or_scene *s, const or_camera *c, double sigma, or_tw_c
     tc->W = c->width;
     tc->H = c->height;
     tc->sigma = sigma;
+    /* view cone: around the optical axis, through the image corners */
+    double tan_c = tc->th * sqrt(1.0 + tc->asp * tc->asp);
+    double cos_c = 1.0 / sqrt(1.0 + tan_c * tan_c);
+    for (int a = 0; a < 3; ++a) tc->aim_eye[a] = tc->eye[a];
+    tc->aim_eye[3] = 2.0 * OR_PI * (1.0 - cos_c);
+}
+
+/* Photon aiming's eye vector of a camera: position and the solid angle of
+ * its view cone. */
+void or_pa_eye(const or_scene *s, const or_camera *c, double out[4]) {
+    or_tw_cam tc;
+    or_tw_cam_init(s, c, 0.5, &tc);
+    for (int a = 0; a < 4; ++a) out[a] = tc.aim_eye[a];
 }
 
 void or_tw_vertex_at(const or_scene *s, uint32_t prim, double b1, double b2, or_tw_vertex *v) {
@@ -282,10 +302,24 @@ void or_tw_pdfs(const or_scene *s, const or_tw_cam *tc, const or_tw_vertex *x, i
      * direction as wo, down to x1 */
     if (!lt_ok) return;
     double pl;
-    if (env)
-        pl = s->p_env * or_env_pdf(s, xk->x) * fabs(dot3(x[k - 1].ng, xk->x)) / (OR_PI * tc->br * tc->br);
-    else
-        pl = lt_point_density(s, xk->prim) * (cy / OR_PI) * cos_to(&x[k - 1], xk->x) / dist2(x[k - 1].x, xk->x);
+    if (env) {
+        /* per unit area across w: uniform over the scene's bound, or aimed
+         * at the clusters whose spheres the photon's line meets */
+        double across = tc->aim ? or_pa_env_density(s, tc->aim_eye, x[k - 1].x, xk->x) : 1.0 / (OR_PI * tc->br * tc->br);
+        pl = s->p_env * or_env_pdf(s, xk->x) * fabs(dot3(x[k - 1].ng, xk->x)) * across;
+    } else {
+        /* per solid angle at the emitter: cosine, or aimed at the clusters
+         * whose cones hold the direction */
+        double pw;
+        if (tc->aim) {
+            double w[3];
+            unit_to(xk->x, x[k - 1].x, w);
+            pw = or_pa_dir_density(s, tc->aim_eye, xk->x, xk->ng, w);
+        } else {
+            pw = cy / OR_PI;
+        }
+        pl = lt_point_density(s, xk->prim) * pw * cos_to(&x[k - 1], xk->x) / dist2(x[k - 1].x, xk->x);
+    }
     for (int i = k - 1; i >= 2; --i)
         pl *= dir_pdf(s, &x[i], &x[i + 1], &x[i - 1]) * cos_to(&x[i - 1], x[i].x) / dist2(x[i].x, x[i - 1].x);
     *p_lt = pl;
@@ -324,8 +358,10 @@ static void light_path(lt_job *j, uint64_t m, or_tw_vertex *V, or_tw_vertex *X) 
     if (s->nlights <= 0 && !(s->p_env > 0.0)) return;
     const double nL = (double)tc->W * (double)tc->H;
     double us = ltdim(j, m, j->base), ua = ltdim(j, m, j->base + 1), ub = ltdim(j, m, j->base + 2);
-    double u3 = ltdim(j, m, j->base + 3), u4 = ltdim(j, m, j->base + 4);
+    double u3 = ltdim(j, m, j->base + 3), u4 = ltdim(j, m, j->base + 4), uc = ltdim(j, m, j->base + 5);
     double beta[3], o[3], dir[3];
+    int env_photon = 0;
+    double env_k = 0.0;   /* aimed environment photon: Le / (p_env pw), divided by the line density at the hit */
     if (us < s->p_env) {
         /* environment photon: a direction from the plain pyramid, then a
          * uniform point of the disk of radius br across the bounding sphere,
@@ -341,14 +377,29 @@ static void light_path(lt_job *j, uint64_t m, or_tw_vertex *V, or_tw_vertex *X) 
         for (int a = 0; a < 3; ++a) V[0].x[a] = w[a];
         double t1[3], t2[3];
         or_onb(w, t1, t2);
-        double r = tc->br * sqrt(u3), phi = 2.0 * OR_PI * u4;
-        for (int a = 0; a < 3; ++a) {
-            o[a] = tc->bc[a] + 2.0 * tc->br * w[a] + r * cos(phi) * t1[a] + r * sin(phi) * t2[a];
-            dir[a] = -w[a];
+        if (tc->aim && s->pa_nclusters > 0) {
+            /* a cluster by the hierarchy, a uniform point of the disk of
+             * its sphere across w, moved back along w outside the scene */
+            int32_t c = or_pa_sample(s, tc->aim_eye, NULL, NULL, uc, NULL);
+            const double *cc = s->pa_cc + 4 * c;
+            double r = cc[3] * sqrt(u3), phi = 2.0 * OR_PI * u4;
+            double p[3];
+            for (int a = 0; a < 3; ++a) p[a] = cc[a] + r * cos(phi) * t1[a] + r * sin(phi) * t2[a];
+            double back = sqrt(dist2(p, tc->bc)) + tc->br;
+            for (int a = 0; a < 3; ++a) { o[a] = p[a] + back * w[a]; dir[a] = -w[a]; }
+            env_photon = 1;
+            env_k = 1.0 / (s->p_env * pw);
+            for (int a = 0; a < 3; ++a) beta[a] = Le[a];
+        } else {
+            double r = tc->br * sqrt(u3), phi = 2.0 * OR_PI * u4;
+            for (int a = 0; a < 3; ++a) {
+                o[a] = tc->bc[a] + 2.0 * tc->br * w[a] + r * cos(phi) * t1[a] + r * sin(phi) * t2[a];
+                dir[a] = -w[a];
+            }
+            /* Le / (p_env pw |cos| / (pi br^2)) with |cos| taken at the hit */
+            double k = OR_PI * tc->br * tc->br / (s->p_env * pw);
+            for (int a = 0; a < 3; ++a) beta[a] = Le[a] * k;
         }
-        /* Le / (p_env pw |cos| / (pi br^2)) with |cos| taken at the hit */
-        double k = OR_PI * tc->br * tc->br / (s->p_env * pw);
-        for (int a = 0; a < 3; ++a) beta[a] = Le[a] * k;
     } else {
         double u2 = (us - s->p_env) / (1.0 - s->p_env);
         if (u2 >= 1.0) u2 = nextafter(1.0, 0.0);
@@ -360,14 +411,27 @@ static void light_path(lt_job *j, uint64_t m, or_tw_vertex *V, or_tw_vertex *X) 
         double Le[3];
         or_tri_emission(s, lt, b1, b2, Le);
         double pa = lt_point_density(s, lt);
-        double t1[3], t2[3];
-        or_onb(V[0].ng, t1, t2);
-        double r = sqrt(u3), phi = 2.0 * OR_PI * u4, cz = sqrt(fmax(0.0, 1.0 - u3));
-        if (!(cz > 0.0)) return;
-        for (int a = 0; a < 3; ++a) dir[a] = r * cos(phi) * t1[a] + r * sin(phi) * t2[a] + cz * V[0].ng[a];
-        normalize3(dir);
-        /* Le cos / (pa cos / pi) */
-        for (int a = 0; a < 3; ++a) beta[a] = Le[a] * OR_PI / pa;
+        if (tc->aim && s->pa_nclusters > 0) {
+            /* a cluster by the hierarchy (seen from the emitter point), a
+             * direction uniform in the cone its sphere subtends */
+            int32_t c = or_pa_sample(s, tc->aim_eye, V[0].x, V[0].ng, uc, NULL);
+            or_pa_cone_sample(s, c, V[0].x, u3, u4, dir);
+            double cy = dot3(dir, V[0].ng);
+            if (!(cy > 0.0)) return;   /* behind the one-sided emitter: no power */
+            double pw = or_pa_dir_density(s, tc->aim_eye, V[0].x, V[0].ng, dir);
+            if (!(pw > 0.0)) return;
+            /* Le cos / (pa pw) */
+            for (int a = 0; a < 3; ++a) beta[a] = Le[a] * cy / (pa * pw);
+        } else {
+            double t1[3], t2[3];
+            or_onb(V[0].ng, t1, t2);
+            double r = sqrt(u3), phi = 2.0 * OR_PI * u4, cz = sqrt(fmax(0.0, 1.0 - u3));
+            if (!(cz > 0.0)) return;
+            for (int a = 0; a < 3; ++a) dir[a] = r * cos(phi) * t1[a] + r * sin(phi) * t2[a] + cz * V[0].ng[a];
+            normalize3(dir);
+            /* Le cos / (pa cos / pi) */
+            for (int a = 0; a < 3; ++a) beta[a] = Le[a] * OR_PI / pa;
+        }
         or_offset_origin(V[0].x, V[0].ng, o);
     }
     for (uint32_t t = 1; t <= j->D; ++t) {
@@ -377,6 +441,12 @@ static void light_path(lt_job *j, uint64_t m, or_tw_vertex *V, or_tw_vertex *X) 
         if (prim == OR_MISS) return;
         or_tw_vertex_at(s, prim, hb1, hb2, &V[t]);
         const or_tw_vertex *v = &V[t];
+        if (t == 1 && env_photon) {
+            /* Le |cos| / (p_env pw |cos| D): the line density D at the hit */
+            double D = or_pa_env_density(s, tc->aim_eye, v->x, V[0].x);
+            if (!(D > 0.0)) return;
+            for (int a = 0; a < 3; ++a) beta[a] *= env_k / D;
+        }
         double wi[3] = {-dir[0], -dir[1], -dir[2]};
         double ngf[3] = {v->ng[0], v->ng[1], v->ng[2]};
         if (dot3(wi, ngf) < 0.0) { ngf[0] = -ngf[0]; ngf[1] = -ngf[1]; ngf[2] = -ngf[2]; }
@@ -448,7 +518,7 @@ static void light_path(lt_job *j, uint64_t m, or_tw_vertex *V, or_tw_vertex *X) 
         }
         if (t == j->D) return;
         /* continuation: BSDF sampling with the arriving direction as wo */
-        int bb = j->base + 5 + 3 * (int)(t - 1);
+        int bb = j->base + 6 + 3 * (int)(t - 1);
         double nsl[3], wn[3], fs[3], q;
         or_adapt_shading_normal(nsf, ngf, wi, nsl);
         if (!or_bsdf_sample(albedo, rough, gw, nsl, wi, ltdim(j, m, bb), ltdim(j, m, bb + 1), ltdim(j, m, bb + 2),
@@ -480,7 +550,7 @@ void or_light_trace(const or_scene *s, const or_camera *cam, uint32_t iter0, uin
     uint32_t k, l; uint64_t p2, p3;
     or_enum_params(W, H, &k, &l, &p2, &p3);
     int base = 2 + 7 * (int)(D + 1);
-    int ndims = base + 5 + 3 * (int)D;
+    int ndims = base + 6 + 3 * (int)D;
     uint32_t *factors = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)ndims);
     for (int d = 0; d < ndims; ++d) factors[d] = d < 2 ? 1u : or_scramble_factor(opts->seed, or_prime(d));
     int nth = opts->threads > 0 ? opts->threads : (int)sysconf(_SC_NPROCESSORS_ONLN);
@@ -493,6 +563,7 @@ void or_light_trace(const or_scene *s, const or_camera *cam, uint32_t iter0, uin
         lt_job *j = &jobs[t];
         j->s = s;
         or_tw_cam_init(s, cam, opts->filter_sigma, &j->tc);
+        j->tc.aim = opts->lt_aim;
         j->D = D; j->k = k; j->l = l; j->factors = factors; j->base = base;
         j->mode = opts->mis_mode;
         j->lt_mode = lt_mode;

@@ -10,6 +10,7 @@
 
 #include "internal.h"
 #include "shade.cuh"
+#include "aiming.cuh"
 
 namespace rtg {
 
@@ -215,6 +216,63 @@ extern "C" rt_status rt_debug_trace_host_stack(const rt_scene *s, const float *r
         }
         prim[i] = h.prim;
         t[i] = h.prim == RT_MISS ? INFINITY : h.t;
+    }
+    return RT_OK;
+}
+
+/* Photon aiming's cluster hierarchy of a host-only scene: node spheres
+ * (n x 4: centre, radius) and links (n x 2: left, right; a leaf -1,
+ * cluster). Pass null outputs to query the counts. */
+extern "C" rt_status rt_debug_aim_tree_host(const rt_scene *s, float *spheres, int32_t *links, int32_t *nnodes,
+                                            int32_t *nclusters) {
+    if (!s || !s->host_only) { set_error("rt_debug_aim_tree_host: needs a host-only scene"); return RT_INVALID_ARG; }
+    const DevScene &sc = s->host;
+    if (nnodes) *nnodes = sc.pa_nnodes;
+    if (nclusters) *nclusters = sc.pa_nclusters;
+    for (int32_t i = 0; i < sc.pa_nnodes; ++i) {
+        if (spheres) {
+            const float4 q = sc.pa_node[i];
+            spheres[4 * i] = q.x; spheres[4 * i + 1] = q.y; spheres[4 * i + 2] = q.z; spheres[4 * i + 3] = q.w;
+        }
+        if (links) { links[2 * i] = sc.pa_link[i].x; links[2 * i + 1] = sc.pa_link[i].y; }
+    }
+    return RT_OK;
+}
+
+/* Host execution of photon aiming's queries (the kernels' code) for n rows
+ * of q (9 floats each) with the eye at `eye`:
+ *   kind 0: q = (x, w): out[0] = density across w of the environment
+ *           photon line through x;
+ *   kind 1: q = (y, ny, w): out[0] = solid-angle density of a triangle
+ *           photon from y (emitter normal ny) along w;
+ *   kind 2: q = (y, ny, u, from_tri): out = sphere of the cluster the
+ *           descent picks with u (from_tri = 0: an environment photon);
+ *   kind 3: q = (sphere centre, radius, y, u1, u2): out[0..2] = the cone
+ *           sample. */
+extern "C" rt_status rt_debug_aim_host(const rt_scene *s, const float *eye, int32_t kind, const float *q, int64_t n,
+                                       float *out) {
+    if (!s || !s->host_only || !eye || n < 0 || (n > 0 && (!q || !out)) || kind < 0 || kind > 3) {
+        set_error("rt_debug_aim_host: invalid argument");
+        return RT_INVALID_ARG;
+    }
+    const DevScene &sc = s->host;
+    const V3 e = v3(eye[0], eye[1], eye[2]);
+    for (int64_t i = 0; i < n; ++i) {
+        const float *r = q + 9 * i;
+        float *o = out + 4 * i;
+        o[0] = o[1] = o[2] = o[3] = 0.f;
+        if (kind == 0) {
+            o[0] = aim_env_density(sc, e, v3(r[0], r[1], r[2]), v3(r[3], r[4], r[5]));
+        } else if (kind == 1) {
+            o[0] = aim_dir_density(sc, e, v3(r[0], r[1], r[2]), v3(r[3], r[4], r[5]), v3(r[6], r[7], r[8]));
+        } else if (kind == 2) {
+            if (sc.pa_nnodes <= 0) continue;
+            const float4 sph = aim_sample(sc, e, r[7] != 0.f, v3(r[0], r[1], r[2]), v3(r[3], r[4], r[5]), r[6]);
+            o[0] = sph.x; o[1] = sph.y; o[2] = sph.z; o[3] = sph.w;
+        } else {
+            const V3 w = aim_cone_sample(make_float4(r[0], r[1], r[2], r[3]), v3(r[4], r[5], r[6]), r[7], r[8]);
+            o[0] = w.x; o[1] = w.y; o[2] = w.z;
+        }
     }
     return RT_OK;
 }

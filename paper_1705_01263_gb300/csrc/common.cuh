@@ -124,6 +124,13 @@ struct DevScene {
     int64_t env_nstride;
     int64_t env_noff_h[16];
     float3 bb_lo, bb_hi;       // scene bounds (guiding features)
+    // photon aiming (Sec. 2.1.3): binary hierarchy over clusters of objects,
+    // node 0 the root; per node its sphere (centre, radius: encloses every
+    // cluster sphere below; a leaf's is its cluster's) and its link
+    // (left, right) or, for a leaf, (-1, cluster)
+    const float4 *pa_node;
+    const int2 *pa_link;
+    int32_t pa_nnodes, pa_nclusters;
 };
 
 // ---------------------------------------------------------- error helpers

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <vector>
 
 #include "internal.h"
@@ -375,6 +376,121 @@ using namespace rtg;
 
 namespace rtg {
 rt_status scene_create(const rt_scene_desc *d, rt_scene **out, bool host_only);
+
+// Photon aiming (Sec. 2.1.3): clusters of objects and the hierarchy that
+// samples them. Objects: the connected components of the mesh (single-level
+// scenes) or the instances; two objects belong to one cluster when a chain
+// of links joins them, a link being a pair of similar size (neither radius
+// above twice the other) whose boxes intersect; a cluster's sphere is the
+// centre and half diagonal of its box. The hierarchy splits a set of
+// clusters at its median cluster along the longest axis of the centres
+// (order: centre, then cluster index); a node's sphere is centred on its
+// box and encloses each cluster sphere below it.
+struct AimBox {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    void add(const double *p) {
+        for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], p[a]); hi[a] = std::max(hi[a], p[a]); }
+    }
+    void add(const AimBox &b) { add(b.lo); add(b.hi); }
+    void centre(double c[3]) const { for (int a = 0; a < 3; ++a) c[a] = 0.5 * (lo[a] + hi[a]); }
+    double radius() const {
+        double e2 = 0.0;
+        for (int a = 0; a < 3; ++a) e2 += (hi[a] - lo[a]) * (hi[a] - lo[a]);
+        return 0.5 * std::sqrt(e2);
+    }
+};
+
+struct DisjointSets {
+    std::vector<int32_t> up;
+    explicit DisjointSets(size_t n) : up(n) { for (size_t i = 0; i < n; ++i) up[i] = (int32_t)i; }
+    int32_t root(int32_t a) {
+        while (up[a] != a) { up[a] = up[up[a]]; a = up[a]; }
+        return a;
+    }
+    void join(int32_t a, int32_t b) {
+        a = root(a); b = root(b);
+        if (a != b) { if (a < b) up[b] = a; else up[a] = b; }
+    }
+};
+
+struct AimTree {
+    std::vector<float4> node;
+    std::vector<int2> link;
+    int32_t nclusters = 0;
+};
+
+static void aim_tree(const std::vector<AimBox> &objects, AimTree &out) {
+    const int32_t n = (int32_t)objects.size();
+    if (n == 0) return;
+    std::vector<double> oc(3 * (size_t)n), orad(n);
+    for (int32_t i = 0; i < n; ++i) { objects[i].centre(&oc[3 * (size_t)i]); orad[i] = objects[i].radius(); }
+    DisjointSets ds(n);
+    for (int32_t a = 0; a < n; ++a)
+        for (int32_t b = a + 1; b < n; ++b) {
+            if (!(orad[a] <= 2.0 * orad[b] && orad[b] <= 2.0 * orad[a])) continue;
+            bool meet = true;
+            for (int k = 0; k < 3; ++k)
+                if (objects[a].lo[k] > objects[b].hi[k] || objects[b].lo[k] > objects[a].hi[k]) meet = false;
+            if (meet) ds.join(a, b);
+        }
+    // clusters numbered in the order of their first object
+    std::vector<int32_t> cl_of(n, -1), obj_cl(n);
+    int32_t ncl = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t r = ds.root(i);
+        if (cl_of[r] < 0) cl_of[r] = ncl++;
+        obj_cl[i] = cl_of[r];
+    }
+    std::vector<AimBox> cb(ncl);
+    for (int32_t i = 0; i < n; ++i) cb[obj_cl[i]].add(objects[i]);
+    std::vector<double> cc(3 * (size_t)ncl), cr(ncl);
+    for (int32_t c = 0; c < ncl; ++c) { cb[c].centre(&cc[3 * (size_t)c]); cr[c] = cb[c].radius(); }
+    out.nclusters = ncl;
+    out.node.clear();
+    out.link.clear();
+    std::vector<int32_t> idx(ncl);
+    for (int32_t c = 0; c < ncl; ++c) idx[c] = c;
+    std::function<int32_t(int32_t, int32_t)> build = [&](int32_t first, int32_t count) -> int32_t {
+        const int32_t id = (int32_t)out.node.size();
+        out.node.push_back(make_float4(0.f, 0.f, 0.f, 0.f));
+        out.link.push_back(make_int2(-1, -1));
+        AimBox nb;
+        for (int32_t i = first; i < first + count; ++i) nb.add(cb[idx[i]]);
+        double c[3];
+        nb.centre(c);
+        double r = 0.0;
+        for (int32_t i = first; i < first + count; ++i) {
+            const double *q = &cc[3 * (size_t)idx[i]];
+            const double dd = std::sqrt((q[0] - c[0]) * (q[0] - c[0]) + (q[1] - c[1]) * (q[1] - c[1]) +
+                                        (q[2] - c[2]) * (q[2] - c[2]));
+            r = std::max(r, dd + cr[idx[i]]);
+        }
+        out.node[id] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)r);
+        if (count == 1) {
+            out.link[id] = make_int2(-1, idx[first]);
+            return id;
+        }
+        double clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int32_t i = first; i < first + count; ++i)
+            for (int a = 0; a < 3; ++a) {
+                clo[a] = std::min(clo[a], cc[3 * (size_t)idx[i] + a]);
+                chi[a] = std::max(chi[a], cc[3 * (size_t)idx[i] + a]);
+            }
+        int axis = 0;
+        for (int a = 1; a < 3; ++a)
+            if (chi[a] - clo[a] > chi[axis] - clo[axis]) axis = a;
+        std::sort(idx.begin() + first, idx.begin() + first + count, [&](int32_t p, int32_t q) {
+            const double a = cc[3 * (size_t)p + axis], b = cc[3 * (size_t)q + axis];
+            return a < b || (a == b && p < q);
+        });
+        const int32_t h = count / 2;
+        const int32_t l = build(first, h);
+        const int32_t rr = build(first + h, count - h);
+        out.link[id] = make_int2(l, rr);
+        return id;
+    };
+    build(0, ncl);
+}
 }
 
 extern "C" rt_status rt_scene_create(const rt_scene_desc *d, rt_scene **out) {
@@ -451,6 +567,7 @@ rt_status rtg::scene_create(const rt_scene_desc *d, rt_scene **out, bool host_on
     // ---- BVH: one level, or per-mesh bottom levels + a top level over instances
     rt_status st;
     std::vector<double> o2w, w2o;   // 12 doubles per instance
+    AimTree aim;
     if (d->num_instances > 0) {
         const int32_t M = d->num_meshes, I = d->num_instances;
         std::vector<uint32_t> nodes_all;
@@ -536,6 +653,15 @@ rt_status rtg::scene_create(const rt_scene_desc *d, rt_scene **out, bool host_on
         if ((st = upload(s, iroot.data(), iroot.size(), &D.inst_root, &Hs.inst_root)) != RT_OK) return fail(st);
         D.two_level = Hs.two_level = 1;
         D.num_instances = Hs.num_instances = (uint32_t)I;
+        // photon aiming: the instances are the objects
+        std::vector<AimBox> objs(I);
+        for (int32_t k = 0; k < I; ++k) {
+            double lo3[3] = {ilo[3 * (size_t)k], ilo[3 * (size_t)k + 1], ilo[3 * (size_t)k + 2]};
+            double hi3[3] = {ihi[3 * (size_t)k], ihi[3 * (size_t)k + 1], ihi[3 * (size_t)k + 2]};
+            objs[k].add(lo3);
+            objs[k].add(hi3);
+        }
+        aim_tree(objs, aim);
         D.bb_lo = Hs.bb_lo = make_float3(blo[0], blo[1], blo[2]);
         D.bb_hi = Hs.bb_hi = make_float3(bhi[0], bhi[1], bhi[2]);
     } else {
@@ -548,6 +674,35 @@ rt_status rtg::scene_create(const rt_scene_desc *d, rt_scene **out, bool host_on
         if ((st = upload(s, (const float4 *)bvh.tris.data(), bvh.tris.size() / 4, &D.tris, &Hs.tris)) != RT_OK) return fail(st);
         D.bb_lo = Hs.bb_lo = make_float3(bvh.lo[0], bvh.lo[1], bvh.lo[2]);
         D.bb_hi = Hs.bb_hi = make_float3(bvh.hi[0], bvh.hi[1], bvh.hi[2]);
+        // photon aiming: connected components of the mesh (shared vertex
+        // indices) are the objects, numbered by their first triangle
+        if (T > 0) {
+            DisjointSets vs((size_t)V);
+            for (int64_t t = 0; t < T; ++t) {
+                const uint32_t *id = d->indices + 3 * (size_t)t;
+                vs.join((int32_t)id[0], (int32_t)id[1]);
+                vs.join((int32_t)id[0], (int32_t)id[2]);
+            }
+            std::vector<int32_t> obj_of(V, -1);
+            std::vector<AimBox> objs;
+            for (int64_t t = 0; t < T; ++t) {
+                const int32_t r = vs.root((int32_t)d->indices[3 * (size_t)t]);
+                if (obj_of[r] < 0) { obj_of[r] = (int32_t)objs.size(); objs.emplace_back(); }
+                AimBox &b = objs[obj_of[r]];
+                for (int k = 0; k < 3; ++k) {
+                    const float *pv = d->vertices + 3 * (size_t)d->indices[3 * (size_t)t + k];
+                    const double q[3] = {pv[0], pv[1], pv[2]};
+                    b.add(q);
+                }
+            }
+            aim_tree(objs, aim);
+        }
+    }
+    if (!aim.node.empty()) {
+        if ((st = upload(s, aim.node.data(), aim.node.size(), &D.pa_node, &Hs.pa_node)) != RT_OK) return fail(st);
+        if ((st = upload(s, aim.link.data(), aim.link.size(), &D.pa_link, &Hs.pa_link)) != RT_OK) return fail(st);
+        D.pa_nnodes = Hs.pa_nnodes = (int32_t)aim.node.size();
+        D.pa_nclusters = Hs.pa_nclusters = aim.nclusters;
     }
 
     // ---- shading arrays

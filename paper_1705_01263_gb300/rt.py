@@ -138,6 +138,8 @@ def _declare(L):
         "rt_debug_trace_host": [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp],
         "rt_debug_trace_host_stack": [vp, vp, i64, i32, i32, vp, vp],
         "rt_debug_regen_host": [u32, u32, u32, vp, u32, vp, vp, vp],
+        "rt_debug_aim_tree_host": [vp, vp, vp, vp, vp],
+        "rt_debug_aim_host": [vp, vp, i32, vp, i64, vp],
         "rt_debug_env_sample_host": [vp, vp, vp, vp, i64, vp, vp, vp],
         "rt_debug_light_bvh_host": [vp, vp, vp, vp, i64, vp, vp, vp],
         "rt_debug_render_host": [vp, C.POINTER(rt_camera), u32, C.POINTER(rt_render_opts), vp, vp, vp, i64, vp],
@@ -609,6 +611,25 @@ def debug_regen_host(life: np.ndarray, cap: int, regen_min: int, stop_step: int 
     check(lib().rt_debug_regen_host(n, cap, regen_min, life.ctypes.data, stop_step, out.ctypes.data,
                                     C.byref(steps), C.byref(regen)))
     return out, steps.value, regen.value
+
+
+def debug_aim_tree_host(scene: Scene):
+    """Photon aiming's hierarchy of a host-only scene: (spheres [n][4], links [n][2], clusters)."""
+    nn, nc = C.c_int32(), C.c_int32()
+    check(lib().rt_debug_aim_tree_host(scene.handle, None, None, C.byref(nn), C.byref(nc)))
+    sph = np.zeros((nn.value, 4), np.float32)
+    links = np.zeros((nn.value, 2), np.int32)
+    check(lib().rt_debug_aim_tree_host(scene.handle, sph.ctypes.data, links.ctypes.data, None, None))
+    return sph, links, nc.value
+
+
+def debug_aim_host(scene: Scene, eye, kind: int, q):
+    """Photon aiming's queries run on the host (see rt_debug_aim_host)."""
+    q = np.ascontiguousarray(q, np.float32).reshape(-1, 9)
+    out = np.zeros((q.shape[0], 4), np.float32)
+    e = np.ascontiguousarray(eye, np.float32)
+    check(lib().rt_debug_aim_host(scene.handle, e.ctypes.data, kind, q.ctypes.data, q.shape[0], out.ctypes.data))
+    return out
 
 
 def debug_env_sample_host(scene: Scene, ng, u, v):

@@ -431,6 +431,36 @@ def sphere_field(seed: int = BASE_SEED + 2, n_spheres: int = 200, seg: int = 64,
     return scene, cam
 
 
+def turntable(res: int = 64, seed: int = BASE_SEED + 7, sun_radius_deg: float = 3.0, sun_gain: float = 300.0):
+    """A close-up object on a turntable in an open, sky-lit scene (the setting
+    Sec. 2.1.3 describes): a glossy sphere (radius 0.2, pure GGX, roughness
+    0.05) resting on a matte stand (0.6 x 0.5 x 0.6) near the camera, a 400 x
+    400 ground, three large boxes 100-150 away that make the scene's bound a
+    few hundred times the object's; a 256 x 128 sky with a sun disk of
+    `sun_radius_deg` whose reflections off the sphere light the stand. Not a
+    configuration of the task: the photon-aiming test and bench scene."""
+    rng = Rng(seed)
+    b = _Builder()
+    gm = b.material((0.5, 0.5, 0.5), 0.5, 0.0)
+    p, t = _oriented_quad((-200, 0, -200), (200, 0, -200), (200, 0, 200), (-200, 0, 200), (0, 1, 0))
+    b.add(p, t, gm)
+    v, t = _box((0.0, 0.25, 0.0), (0.6, 0.5, 0.6), 0.0)
+    b.add(v, t, b.material((0.75, 0.75, 0.7), 0.5, 0.0))
+    sv, si = uv_sphere(48, 24)
+    sp = sv * 0.2 + np.array([0.0, 0.7005, 0.0])
+    b.add(sp, si, b.material((0.9, 0.9, 0.9), 0.02, 1.0), normals=_vertex_normals(sp, si))
+    for k in range(3):
+        ang = 2 * np.pi * (k / 3.0 + 0.1)
+        dist = float(rng.uniform(1, 100.0, 150.0)[0])
+        c = (dist * np.cos(ang), 10.0, dist * np.sin(ang))
+        v, t = _box(c, (20.0, 20.0, 20.0), float(rng.uniform(1, 0, 90)[0]))
+        b.add(v, t, b.material(tuple(rng.uniform(3, 0.3, 0.7)), 0.5, 0.0))
+    env, _ = procedural_sky(256, 128, seed ^ 0x7A7A, sun_radius_deg=sun_radius_deg, sun_gain=sun_gain)
+    scene = b.build(env=env, with_normals=True, name="turntable")
+    cam = Camera((0.0, 1.1, 1.6), (0.0, 0.55, 0.0), (0.0, 1.0, 0.0), 35.0, res, res)
+    return scene, cam
+
+
 # ---------------------------------------------------------- pin scenes
 def furnace_sphere(seg: int = 48, rings: int = 24, env_size=(8, 4), radiance: float = 1.0,
                    res: int = 32, albedo: float = 1.0):
