@@ -177,6 +177,8 @@ typedef struct {
                               * the pool (A/B). Guided rendering and megakernel_only use iteration sets. */
     float regen_fraction;    /* scheduler 0: refill once this fraction of the pool has ended (0 = 0.5,
                               * the paper's rule); must be in [0, 1] */
+    int32_t lt_emission;     /* rt_render_two_way: 0 photon aiming (Sec. 2.1.3), 1 uniform emission over
+                              * the scene's bound and cosine directions (A/B) */
 } rt_render_opts;
 
 /* ---------------------------------------------------------------- scene */
@@ -250,10 +252,19 @@ rt_status rt_render(const rt_scene *scene, const rt_camera *camera, uint32_t spp
 /* Two-way path tracing (Sec. 2): the path tracer and a light-tracing stage
  * with the same number of paths per iteration (W x H), combined by multiple
  * importance sampling. The light tracer starts on the environment with
- * next-event estimation's probability (a direction from the plain pyramid,
- * then a uniform point of the disk across the scene's bounding sphere, Sec.
- * 2.1.3's unaimed emission) or on a triangle emitter in proportion to its
- * flux (cosine-distributed), scatters by the BSDF sampler and connects every
+ * next-event estimation's probability (a direction from the plain pyramid)
+ * or on a triangle emitter in proportion to its flux (a uniform point). With
+ * photon aiming (Sec. 2.1.3, the default) it then picks a cluster of objects
+ * (connected components of the mesh, or instances, joined when of similar
+ * size and touching) through a hierarchy over the clusters, each step in
+ * proportion to the solid angle under which the eye sees a child's bounding
+ * sphere (at most the view cone's), and aims at it: an environment photon
+ * starts on the cluster sphere's disk across its direction, a triangle
+ * photon leaves in a direction uniform in the cone the sphere subtends; the
+ * MIS densities sum over every cluster the emission passes. Without it
+ * (opts->lt_emission = 1) photons start on the disk across the scene's
+ * bounding sphere or leave cosine-distributed. The light tracer scatters by
+ * the BSDF sampler and connects every
  * vertex to the pinhole camera, adding the connection to each pixel whose
  * Gaussian filter centre lies within 3 sigma of the image point (the box
  * filter: the pixel that holds it). Techniques for a path eye .. emitter or
@@ -266,8 +277,9 @@ rt_status rt_render(const rt_scene *scene, const rt_camera *camera, uint32_t spp
  *             otherwise); the film's sums, sums of squares and counts receive
  *             the camera stage (its squares cover that stage only)
  *   opts:     filter_sigma, mis_mode (0 power or 1 balance, else
- *             RT_INVALID_ARG), seed and rr_enable as rt_render; the scheduling
- *             options are ignored; guide must be NULL (RT_NOT_SUPPORTED)
+ *             RT_INVALID_ARG), seed and rr_enable as rt_render; lt_emission
+ *             (0 aimed, 1 uniform); the scheduling options are ignored; guide
+ *             must be NULL (RT_NOT_SUPPORTED)
  *   lt_mode:  0 MIS of the three techniques; 1 the light tracer alone for
  *             every path it can make, the camera techniques elsewhere
  *   lt_splat: DEVICE double [H][W][3] that the light stage adds into

@@ -8,13 +8,17 @@
 //
 // Estimate of a node (the optimistic bound the paper asks for): the solid
 // angle 2 pi (1 - sqrt(1 - r^2/d^2)) under which the eye sees the node's
-// sphere, 4 pi when the eye is inside; a photon aimed uniformly at a sphere
-// of radius r lays 1 / (pi r^2) photons per unit area across it and a pixel
-// at distance d covers an area proportional to d^2, so clusters chosen in
-// proportion to their solid angle receive about as many photons per pixel.
-// For a photon from a triangle emitter (point y, normal ny) a node whose
-// sphere lies wholly behind the emitter's plane gets zero (the emitter
-// radiates on its normal's side only).
+// sphere, 4 pi when the eye is inside, at most the solid angle of the
+// camera's view cone (the cone around the optical axis through the image
+// corners): no cluster takes more than the whole screen. A photon aimed
+// uniformly at a sphere of radius r lays 1 / (pi r^2) photons per unit area
+// across it and a pixel at distance d covers an area proportional to d^2,
+// so clusters chosen in proportion to their solid angle receive about as
+// many photons per pixel; the cap keeps a cluster around the eye (a ground)
+// from taking photons that its huge sphere mostly sends out of view. For a
+// photon from a triangle emitter (point y, normal ny) a node whose sphere
+// lies wholly behind the emitter's plane gets zero (the emitter radiates on
+// its normal's side only). `eye` = (position, view-cone solid angle).
 #pragma once
 
 #include "common.cuh"
@@ -23,17 +27,20 @@ namespace rtg {
 
 constexpr int kAimStack = 48;   // traversal stack: the hierarchy is a median split, depth <= log2(clusters) + 1
 
-RT_HD float aim_estimate(float4 sph, V3 eye, bool from_tri, V3 y, V3 ny) {
+RT_HD float aim_estimate(float4 sph, float4 eye, bool from_tri, V3 y, V3 ny) {
     const V3 c = v3(sph.x, sph.y, sph.z);
     if (from_tri && !(dot(c - y, ny) > -sph.w)) return 0.f;
-    const V3 v = c - eye;
+    const V3 v = c - v3(eye.x, eye.y, eye.z);
     const float d2 = dot(v, v), r2 = sph.w * sph.w;
-    if (d2 <= r2) return 4.f * kPi;
-    const float x = r2 / d2;
-    return 2.f * kPi * x / (1.f + sqrtf(1.f - x));   // 2 pi (1 - sqrt(1 - x)), without cancellation
+    float om = 4.f * kPi;
+    if (d2 > r2) {
+        const float x = r2 / d2;
+        om = 2.f * kPi * x / (1.f + sqrtf(1.f - x));   // 2 pi (1 - sqrt(1 - x)), without cancellation
+    }
+    return fminf(om, eye.w);
 }
 
-RT_HD float aim_p_left(const DevScene &sc, int2 link, V3 eye, bool from_tri, V3 y, V3 ny) {
+RT_HD float aim_p_left(const DevScene &sc, int2 link, float4 eye, bool from_tri, V3 y, V3 ny) {
     const float wl = aim_estimate(ldg(sc.pa_node + link.x), eye, from_tri, y, ny);
     const float wr = aim_estimate(ldg(sc.pa_node + link.y), eye, from_tri, y, ny);
     if (!(wl + wr > 0.f)) return 0.5f;
@@ -42,7 +49,7 @@ RT_HD float aim_p_left(const DevScene &sc, int2 link, V3 eye, bool from_tri, V3 
 
 // Descent driven by one uniform number (rescaled at each level); returns the
 // chosen cluster's sphere.
-RT_HD float4 aim_sample(const DevScene &sc, V3 eye, bool from_tri, V3 y, V3 ny, float u) {
+RT_HD float4 aim_sample(const DevScene &sc, float4 eye, bool from_tri, V3 y, V3 ny, float u) {
     int node = 0;
     for (;;) {
         const int2 link = ldg(sc.pa_link + node);
@@ -77,7 +84,7 @@ RT_HD bool aim_cone_holds(float4 sph, V3 y, V3 w) {
 
 // Environment photon: density per unit area across w of the photon line
 // through x, sum over clusters whose sphere the line meets of P_c / (pi r^2).
-RT_HD float aim_env_density(const DevScene &sc, V3 eye, V3 x, V3 w) {
+RT_HD float aim_env_density(const DevScene &sc, float4 eye, V3 x, V3 w) {
     if (sc.pa_nnodes <= 0) return 0.f;
     int stack[kAimStack];
     float pstack[kAimStack];
@@ -107,7 +114,7 @@ RT_HD float aim_env_density(const DevScene &sc, V3 eye, V3 x, V3 w) {
 // Triangle photon from y (emitter normal ny) leaving along w: solid-angle
 // density, sum over clusters whose cone holds w of P_c(y) / (2 pi (1 - cos
 // theta_c)), or P_c(y) / (4 pi) when y is inside the cluster's sphere.
-RT_HD float aim_dir_density(const DevScene &sc, V3 eye, V3 y, V3 ny, V3 w) {
+RT_HD float aim_dir_density(const DevScene &sc, float4 eye, V3 y, V3 ny, V3 w) {
     if (sc.pa_nnodes <= 0) return 0.f;
     int stack[kAimStack];
     float pstack[kAimStack];

@@ -240,7 +240,7 @@ extern "C" rt_status rt_debug_aim_tree_host(const rt_scene *s, float *spheres, i
 }
 
 /* Host execution of photon aiming's queries (the kernels' code) for n rows
- * of q (9 floats each) with the eye at `eye`:
+ * of q (9 floats each) with eye = (position, view-cone solid angle):
  *   kind 0: q = (x, w): out[0] = density across w of the environment
  *           photon line through x;
  *   kind 1: q = (y, ny, w): out[0] = solid-angle density of a triangle
@@ -256,7 +256,7 @@ extern "C" rt_status rt_debug_aim_host(const rt_scene *s, const float *eye, int3
         return RT_INVALID_ARG;
     }
     const DevScene &sc = s->host;
-    const V3 e = v3(eye[0], eye[1], eye[2]);
+    const float4 e = make_float4(eye[0], eye[1], eye[2], eye[3]);
     for (int64_t i = 0; i < n; ++i) {
         const float *r = q + 9 * i;
         float *o = out + 4 * i;

@@ -2,11 +2,12 @@
 // tracer run as separate stages with the same number of paths per iteration
 // and are combined by multiple importance sampling. The light tracer starts
 // on the environment with next-event estimation's probability p_env (a
-// direction from the plain pyramid, then a uniform point of the disk across
-// the scene's bounding sphere) or on a triangle emitter in proportion to its
-// flux (the emission that Sec. 2.1.3's photon aiming improves on), and
-// connects every vertex of a light path to the pinhole camera, adding the
-// connection to the pixels whose filter reaches the image point.
+// direction from the plain pyramid) or on a triangle emitter in proportion to
+// its flux, aims the photon at a cluster of objects picked for the camera's
+// view (Sec. 2.1.3, aiming.cuh) or, as an A/B option, emits uniformly over
+// the scene's bound, and connects every vertex of a light path to the
+// pinhole camera, adding the connection to the pixels whose filter reaches
+// the image point.
 //
 // Techniques for a path x0 (eye) .. xk (triangle emitter, or a direction
 // towards the environment), k >= 2, through pixel j: the camera path's
@@ -33,6 +34,7 @@
 #include <vector>
 #include "internal.h"
 #include "shade.cuh"
+#include "aiming.cuh"
 
 namespace rtg {
 
@@ -44,8 +46,24 @@ struct TwParams {
     int lt_mode;      // 0: MIS; 1: the light tracer alone wherever it makes the path
     V3 bc;            // the scene's bounding sphere: centre,
     float br;         // radius (half the diagonal of its box),
-    float inv_disk;   // 1 / (pi br^2): area density of an environment photon's disk
+    float inv_disk;   // 1 / (pi br^2): area density of an environment photon's disk (uniform emission)
+    int aim;          // photon aiming (Sec. 2.1.3) instead of uniform emission
+    float4 aim_eye;   // eye position and the solid angle of the camera's view cone
 };
+
+// Density per unit area across w of an environment photon's line through x:
+// aimed (the clusters whose spheres the line meets) or uniform over the
+// scene's bounding sphere.
+RT_D float tw_env_across(const DevScene &sc, const TwParams &T, V3 x, V3 w) {
+    return T.aim ? aim_env_density(sc, T.aim_eye, x, w) : T.inv_disk;
+}
+
+// Solid-angle density of a triangle photon from y (emitter normal ny) along
+// w: aimed, or cosine-distributed.
+RT_D float tw_emit_dir(const DevScene &sc, const TwParams &T, V3 y, V3 ny, V3 w) {
+    if (T.aim) return aim_dir_density(sc, T.aim_eye, y, ny, w);
+    return fmaxf(dot(w, ny), 0.f) * (1.f / kPi);
+}
 
 struct TwCounters {
     unsigned long long ext_rays, shadow_rays;
@@ -129,7 +147,8 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
                     // light tracer / hit: x(v-1)'s factor, |cos| / (pi r^2) over
                     // its camera density, times the photon's direction pdf
                     // over the continuation's
-                    const float r_lt = Pi > 0.f ? T.nL * Pi * cprev * T.inv_disk * sc.p_env * e.w / s.prev_pdf : 0.f;
+                    const float r_lt =
+                        Pi > 0.f ? T.nL * Pi * cprev * tw_env_across(sc, T, s.o, s.d) * sc.p_env * e.w / s.prev_pdf : 0.f;
                     if (T.lt_mode == 1) w = r_lt > 0.f ? 0.f : mis_weight(mode, s.prev_pdf, pn);
                     else w = tw_weight(mode, pn / s.prev_pdf, r_lt);
                 }
@@ -170,10 +189,15 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
                     pa = (1.f - sc.p_env) * lb_prob(sc, s.o, oct_decode(s.prev_n), li) / emitter_area(sc, li);
                 }
                 const float r_nee = pa * t2 / (s.prev_pdf * vx.cog);
-                // light tracer / hit: the factor of x_v, (cos_y / pi) c / t^2,
-                // times the emitter's, pA_lt t^2 / (prev_pdf cos_y)
+                // light tracer / hit: the factor of x_v, q(y -> x_(v-1)) c / t^2
+                // (q the emission's direction density), times the emitter's,
+                // pA_lt t^2 / (prev_pdf cos_y)
                 const float pa_lt = lpa;   // the light tracer's area pdf (alias table, 1 - p_env)
-                float r_lt = Pi > 0.f ? T.nL * Pi * cprev * pa_lt / (kPi * s.prev_pdf) : 0.f;
+                float r_lt = 0.f;
+                if (Pi > 0.f) {
+                    const float qd = tw_emit_dir(sc, T, vx.x, vx.ng, vx.wo);
+                    r_lt = T.nL * Pi * cprev * pa_lt * qd / (vx.cog * s.prev_pdf);
+                }
                 if (T.lt_mode == 1) w = r_lt > 0.f ? 0.f : mis_weight(mode, s.prev_pdf, pa * t2 / vx.cog);
                 else w = tw_weight(mode, r_nee, r_lt);
             }
@@ -191,6 +215,7 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
             V3 wi = v3(0.f, 0.f, 1.f), Le = v3(0.f, 0.f, 0.f), sdir = wi;
             float pdf_l = 0.f, tmax = INFINITY, cl = 0.f, dist = 0.f, lt_over_nee = 0.f, env_pw = 0.f;
             bool tri = false;
+            V3 ly = v3(0.f, 0.f, 0.f), lnrm = v3(0.f, 0.f, 1.f);   // sampled light point and its normal
             if (us < sc.p_env) {
                 const uint32_t cell = env_cell(ng);
                 wi = env_sample_cell(sc, cell, ua, ub);
@@ -224,6 +249,8 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
                 if (dist > 0.f) {
                     wi = dv * (1.f / dist);
                     V3 lng = normalize(cross(l1 - l0, l2 - l0));
+                    ly = y;
+                    lnrm = lng;
                     cl = -dot(wi, lng);
                     if (cl > 0.f) {
                         pdf_l = lpa_n * dist * dist / cl;
@@ -255,8 +282,9 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
                             // x(v-1): reverse pdf at x_v from the light point
                             float fv1 = 1.f;
                             if (v >= 2) fv1 = tw_dir_pdf(m, ng, vx.nsr, wi, wo) * cprev / t2;
-                            // x_v: emission cosine over pi, cos at x_v towards y
-                            const float fv = (cl / kPi) * dot(wi, ng) / (dist * dist * Cd);
+                            // x_v: the emission's direction density from y
+                            // towards x_v, cos at x_v towards y
+                            const float fv = tw_emit_dir(sc, T, ly, lnrm, -wi) * dot(wi, ng) / (dist * dist * Cd);
                             r_lt = T.nL * Pi * fv1 * fv * lt_over_nee;
                         }
                         if (T.lt_mode == 1) w = r_lt > 0.f ? 0.f : w;
@@ -269,7 +297,8 @@ RT_D V3 tw_camera_path(const RenderParams &P, const TwParams &T, uint32_t pixel,
                         if (Pi > 0.f) {
                             float fv1 = 1.f;
                             if (v >= 2) fv1 = tw_dir_pdf(m, ng, vx.nsr, wi, wo) * cprev / t2;
-                            r_lt = T.nL * Pi * fv1 * (dot(wi, ng) * T.inv_disk / Cd) * sc.p_env * env_pw / pdf_l;
+                            r_lt = T.nL * Pi * fv1 * (dot(wi, ng) * tw_env_across(sc, T, vx.x, wi) / Cd) * sc.p_env *
+                                   env_pw / pdf_l;
                         }
                         if (T.lt_mode == 1) w = r_lt > 0.f ? 0.f : w;
                         else w = tw_weight(mode, pdf_b / pdf_l, r_lt);
@@ -339,11 +368,18 @@ __global__ void __launch_bounds__(128) k_tw_camera(RenderParams P, TwParams T, d
 }
 
 // ------------------------------------------------------------- light stage
-// Light path m (iteration m / (W H)): emitter by the alias table, point
-// uniform on it, cosine direction about its normal; at vertex t = 1..D a
-// connection to the eye, then (t < D) a BSDF sample with the arriving
-// direction as wo. Sample dimensions from T.base: {0: emitter, 1,2: point,
-// 3,4: direction}, vertex t: T.base + 5 + 3 (t - 1) + {0: lobe, 1,2: direction}.
+// Light path m (iteration m / (W H)): the environment with next-event
+// estimation's probability, else an emitter by the alias table and a point
+// uniform on it; with photon aiming (Sec. 2.1.3) a cluster picked through
+// the cluster hierarchy with the eye's view, then a uniform point of that
+// cluster's disk across the environment direction, or a direction uniform in
+// the cone its sphere subtends from the emitter point; without, a point of
+// the disk across the scene's bounding sphere or a cosine direction. At
+// vertex t = 1..D a connection to the eye, then (t < D) a BSDF sample with
+// the arriving direction as wo. Sample dimensions from T.base: {0: emitter,
+// 1,2: point (environment: direction), 3,4: direction (environment: disk
+// point), 5: cluster}, vertex t: T.base + 6 + 3 (t - 1) + {0: lobe, 1,2:
+// direction}.
 RT_D void tw_light_path(const RenderParams &P, const TwParams &T, uint64_t m, double *splat, uint32_t &ext,
                         uint32_t &shadow) {
     const DevScene &sc = P.sc;
@@ -355,6 +391,8 @@ RT_D void tw_light_path(const RenderParams &P, const TwParams &T, uint64_t m, do
     const float us = dim_value(P, m, T.base);
     const float ua = dim_value(P, m, T.base + 1), ub = dim_value(P, m, T.base + 2);
     const float u3 = dim_value(P, m, T.base + 3), u4 = dim_value(P, m, T.base + 4);
+    const float uc = dim_value(P, m, T.base + 5);
+    const bool aim = T.aim != 0;
     float sphi, cphi;
     sincosf(2.f * kPi * u4, &sphi, &cphi);
     const bool env = us < sc.p_env;
@@ -374,10 +412,21 @@ RT_D void tw_light_path(const RenderParams &P, const TwParams &T, uint64_t m, do
         pa = sc.p_env * env_pw;
         V3 t1, t2;
         onb(w, t1, t2);
-        const float r = T.br * sqrtf(u3);
-        o = T.bc + (2.f * T.br) * w + (r * cphi) * t1 + (r * sphi) * t2;
+        if (aim) {
+            // a uniform point of the chosen cluster's disk across w, moved
+            // back along w outside the scene; the line density at the first
+            // hit completes the throughput there
+            const float4 sph = aim_sample(sc, T.aim_eye, false, w, w, uc);
+            const float r = sph.w * sqrtf(u3);
+            const V3 p = v3(sph.x, sph.y, sph.z) + (r * cphi) * t1 + (r * sphi) * t2;
+            o = p + (length(p - T.bc) + T.br) * w;
+            beta = v3(e.x, e.y, e.z) * (1.f / pa);
+        } else {
+            const float r = T.br * sqrtf(u3);
+            o = T.bc + (2.f * T.br) * w + (r * cphi) * t1 + (r * sphi) * t2;
+            beta = v3(e.x, e.y, e.z) * (1.f / (pa * T.inv_disk));
+        }
         dir = -w;
-        beta = v3(e.x, e.y, e.z) * (1.f / (pa * T.inv_disk));
     } else {
         float u2 = (us - sc.p_env) / (1.f - sc.p_env);
         float xn = u2 * (float)sc.num_lights;
@@ -395,16 +444,28 @@ RT_D void tw_light_path(const RenderParams &P, const TwParams &T, uint64_t m, do
         const V3 lng = normalize(cross(l1 - l0, l2 - l0));
         pa = ldg(sc.tri_light_pdf_area + lt);   // (1 - p_env) x flux share / area
         const V3 Le = tri_emission(sc, lt, ldg(sc.tri_material + lt), lb1, lb2);
-        const float ce = sqrtf(fmaxf(0.f, 1.f - u3));
-        if (!(ce > 0.f)) return;
-        V3 t1, t2;
-        onb(lng, t1, t2);
-        const float rr = sqrtf(u3);
-        dir = normalize(rr * cphi * t1 + rr * sphi * t2 + ce * lng);
-        beta = Le * (kPi / pa);
+        if (aim) {
+            const float4 sph = aim_sample(sc, T.aim_eye, true, y, lng, uc);
+            dir = aim_cone_sample(sph, y, u3, u4);
+            const float ce = dot(dir, lng);
+            if (!(ce > 0.f)) return;   // behind the one-sided emitter: no power
+            const float qd = aim_dir_density(sc, T.aim_eye, y, lng, dir);
+            if (!(qd > 0.f)) return;
+            beta = Le * (ce / (pa * qd));
+            q_prev = qd;
+            pend = ce / pa;
+        } else {
+            const float ce = sqrtf(fmaxf(0.f, 1.f - u3));
+            if (!(ce > 0.f)) return;
+            V3 t1, t2;
+            onb(lng, t1, t2);
+            const float rr = sqrtf(u3);
+            dir = normalize(rr * cphi * t1 + rr * sphi * t2 + ce * lng);
+            beta = Le * (kPi / pa);
+            q_prev = ce / kPi;
+            pend = ce / pa;
+        }
         o = offset_origin(y, lng);
-        q_prev = ce / kPi;
-        pend = ce / pa;
     }
     float S = 0.f;               // sum over camera techniques of prod (C / L)^beta, finished vertices
     for (uint32_t t = 1; t <= P.max_depth; ++t) {
@@ -424,7 +485,13 @@ RT_D void tw_light_path(const RenderParams &P, const TwParams &T, uint64_t m, do
         const float cwi = fabsf(vx.cog);
         const float t2 = h.t * h.t;
         // light-tracer density of x (given the direction, for an environment photon)
-        const float Ld = (t == 1 && env) ? cwi * T.inv_disk : q_prev * cwi / t2;
+        float across = T.inv_disk;
+        if (t == 1 && env && aim) {
+            across = aim_env_density(sc, T.aim_eye, x, -dir);
+            if (!(across > 0.f)) return;
+            beta = beta * (1.f / across);
+        }
+        const float Ld = (t == 1 && env) ? cwi * across : q_prev * cwi / t2;
         // factor that turns the BSDF pdf at x towards the previous vertex into
         // (camera density / light density) of that vertex
         const float gfac = (t == 1 && env) ? 1.f / pa : pend / t2;
@@ -504,7 +571,7 @@ RT_D void tw_light_path(const RenderParams &P, const TwParams &T, uint64_t m, do
         }
         if (t == P.max_depth) return;
         // continuation: the BSDF sampler with the arriving direction as wo
-        const int bb = T.base + 5 + 3 * (int)(t - 1);
+        const int bb = T.base + 6 + 3 * (int)(t - 1);
         V3 wn, fs;
         float q;
         if (!bsdf_sample(mat, vx.ns, wi, dim_value(P, m, bb), dim_value(P, m, bb + 1), dim_value(P, m, bb + 2), wn,
@@ -564,6 +631,10 @@ extern "C" rt_status rt_render_two_way(const rt_scene *s, const rt_camera *cam, 
         return RT_INVALID_ARG;
     }
     if (lt_mode < 0 || lt_mode > 1) { set_error("rt_render_two_way: lt_mode must be 0 or 1"); return RT_INVALID_ARG; }
+    if (o.lt_emission < 0 || o.lt_emission > 1) {
+        set_error("rt_render_two_way: lt_emission must be 0 (photon aiming) or 1 (uniform)");
+        return RT_INVALID_ARG;
+    }
     if (o.guide) { set_error("rt_render_two_way: guiding is not combined with light tracing"); return RT_NOT_SUPPORTED; }
     const uint64_t WH = (uint64_t)cam->width * cam->height;
     if (film->next_task % WH) {
@@ -576,7 +647,7 @@ extern "C" rt_status rt_render_two_way(const rt_scene *s, const rt_camera *cam, 
     if (j0 + spp > 0xFFFFFFFFull) { set_error("rt_render_two_way: iteration index overflow"); return RT_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
     const int base = 2 + 7 * (int)(max_depth + 1);
-    const int ndims = base + 5 + 3 * (int)max_depth;
+    const int ndims = base + 6 + 3 * (int)max_depth;
     std::vector<HaltonDim> dims = make_dims(o.seed, ndims);
     // the dimension table and counters live for this call only; every exit
     // path, the error returns included, releases them on the stream
@@ -615,6 +686,16 @@ extern "C" rt_status rt_render_two_way(const rt_scene *s, const rt_camera *cam, 
                   (float)(0.5 * ((double)lo.z + hi.z)));
         T.br = r > 0.0 ? (float)r : 1.f;
         T.inv_disk = (float)(1.0 / (3.14159265358979323846 * (double)T.br * T.br));
+    }
+    // photon aiming: on unless uniform emission is asked for (A/B); the eye
+    // and the solid angle of the view cone through the image corners
+    T.aim = (o.lt_emission == 0 && s->dev.pa_nnodes > 0) ? 1 : 0;
+    {
+        const double th = std::tan(0.5 * (double)cam->vfov_deg * 3.14159265358979323846 / 180.0);
+        const double asp = (double)cam->width / (double)cam->height;
+        const double tc = th * std::sqrt(1.0 + asp * asp);
+        const double om = 2.0 * 3.14159265358979323846 * (1.0 - 1.0 / std::sqrt(1.0 + tc * tc));
+        T.aim_eye = make_float4(cam->eye[0], cam->eye[1], cam->eye[2], (float)om);
     }
     const uint64_t n = (uint64_t)spp * WH;
     // One path per thread: with several paths per thread the lanes of a warp

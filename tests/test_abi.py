@@ -416,3 +416,55 @@ def test_regeneration_stop_drains_a_contiguous_range_on_the_host():
     k = int(done.sum())
     assert 2048 < k < 50_000 and np.all(done[:k]) and not done[k:].any()
     assert steps <= 20 + 17
+
+
+@pytest.mark.parametrize("name", ["cornell", "field", "many", "turntable"])
+def test_photon_aiming_host_matches_oracle(name):
+    """Photon aiming (Sec. 2.1.3) as the kernels compute it, run on the host
+    in FP32, against the FP64 oracle: the same clusters and hierarchy, the
+    same line and cone densities, the same cluster picked by the descent
+    (away from the FP32/FP64 boundaries of the cumulative probabilities)."""
+    sd, cam = {"cornell": scenes.cornell_box, "field": scenes.sphere_field,
+               "many": lambda: scenes.many_emitters(n_lights=64, res=16),
+               "turntable": lambda: scenes.turntable(res=16)}[name]()
+    s, o = rt.Scene(sd, host_only=True), oracle.Scene(sd)
+    sph, links, ncl = rt.debug_aim_tree_host(s)
+    cc, _ = o.pa_clusters()
+    assert ncl == cc.shape[0] and sph.shape[0] == 2 * ncl - 1
+    leaf = links[:, 0] < 0
+    assert np.allclose(sph[leaf], cc[links[leaf, 1]], rtol=1e-6, atol=1e-6)
+    eye = o.pa_eye(cam)
+    rng = np.random.default_rng(9)
+    lo, hi = sd.vertices.min(0), sd.vertices.max(0)
+    n = 400
+    x = lo + rng.random((n, 3)) * (hi - lo)
+    w = rng.normal(size=(n, 3))
+    w /= np.linalg.norm(w, axis=1, keepdims=True)
+    ny = rng.normal(size=(n, 3))
+    ny /= np.linalg.norm(ny, axis=1, keepdims=True)
+    x, w, ny = (a.astype(np.float32).astype(np.float64) for a in (x, w, ny))
+    env_g = rt.debug_aim_host(s, eye, 0, np.concatenate([x, w, np.zeros((n, 3))], 1))[:, 0]
+    dir_g = rt.debug_aim_host(s, eye, 1, np.concatenate([x, ny, w], 1))[:, 0]
+    env_o = np.array([o.pa_env_density(eye, x[i], w[i]) for i in range(n)])
+    dir_o = np.array([o.pa_dir_density(eye, x[i], ny[i], w[i]) for i in range(n)])
+    # a query on the boundary of a cluster's disk or cone may fall on either
+    # side in FP32: at most 2% of them
+    for g_, o_ in ((env_g, env_o), (dir_g, dir_o)):
+        ok = np.isclose(g_, o_, rtol=2e-4, atol=1e-30)
+        assert ok.mean() >= 0.98, (ok.mean(), g_[~ok][:5], o_[~ok][:5])
+        assert np.any(o_ > 0)
+    # the descent: environment photons and triangle photons
+    u = (np.arange(n) + 0.5) / n
+    for tri in (0.0, 1.0):
+        q = np.concatenate([x, ny, u[:, None], np.full((n, 1), tri), np.zeros((n, 1))], 1)
+        got = rt.debug_aim_host(s, eye, 2, q)
+        same = 0
+        for i in range(n):
+            c, _ = o.pa_sample(eye, u[i], x[i] if tri else None, ny[i] if tri else None)
+            same += np.allclose(got[i], cc[c], rtol=1e-6, atol=1e-6)
+        assert same >= 0.98 * n
+    # cone samples
+    q = np.concatenate([np.tile(cc[:1], (n, 1)), x, rng.random((n, 2))], 1)
+    gw = rt.debug_aim_host(s, eye, 3, q)[:, :3]
+    ow = np.array([o.pa_cone_sample(0, x[i], q[i, 7], q[i, 8]) for i in range(n)])
+    assert np.abs(gw - ow).max() < 2e-4

@@ -22,6 +22,8 @@ def _scene(name, res):
         sd, cam = scenes.glossy_room(res)
     elif name == "many":
         sd, cam = scenes.many_emitters(n_lights=64, res=res)   # light hierarchy
+    elif name == "turntable":
+        sd, cam = scenes.turntable(res=res)   # open scene: photon aiming at the object in view
     elif name == "cornell-env":
         # open towards the camera and lit by a sky too: environment photons
         sd, cam = scenes.cornell_box()
@@ -33,27 +35,29 @@ def _scene(name, res):
     return sd, cam
 
 
-def two_way_gpu(sd, cam, spp, depth, first=0, lt_mode=0, sigma=0.5, mis_mode=0, scene=None):
+def two_way_gpu(sd, cam, spp, depth, first=0, lt_mode=0, sigma=0.5, mis_mode=0, scene=None, aim=True):
     from paper_1705_01263_gb300 import rt
     scene = scene or rt.Scene(sd)
     film = rt.Film(cam.width, cam.height)
     film.seek(first)
     splat = torch.zeros((cam.height, cam.width, 3), dtype=torch.float64, device="cuda")
-    opts = rt.make_opts(sigma=sigma, mis_mode=mis_mode)
+    opts = rt.make_opts(sigma=sigma, mis_mode=mis_mode, lt_emission=0 if aim else 1)
     stats = rt.rt_render_two_way(scene, cam, spp, depth, film, opts, lt_mode=lt_mode, lt_splat=splat)
     torch.cuda.synchronize()
     s, s2, c = film.download()
     return s, s2, c, splat.cpu().numpy(), stats
 
 
-@pytest.mark.parametrize("name,depth,lt_mode,mis_mode,sigma", [
-    ("glossy", 3, 0, 0, 0.5), ("glossy", 3, 0, 1, 0.5), ("glossy", 3, 1, 0, 0.5), ("cornell", 4, 0, 0, 0.5),
-    ("cornell", 4, 0, 0, 0.0), ("many", 3, 0, 0, 0.5), ("cornell-env", 3, 0, 0, 0.5), ("cornell-env", 3, 1, 0, 0.5)])
-def test_two_way_matches_the_oracle_on_the_same_samples(name, depth, lt_mode, mis_mode, sigma):
+@pytest.mark.parametrize("name,depth,lt_mode,mis_mode,sigma,aim", [
+    ("glossy", 3, 0, 0, 0.5, True), ("glossy", 3, 0, 1, 0.5, True), ("glossy", 3, 1, 0, 0.5, True),
+    ("cornell", 4, 0, 0, 0.5, True), ("cornell", 4, 0, 0, 0.0, True), ("many", 3, 0, 0, 0.5, True),
+    ("cornell-env", 3, 0, 0, 0.5, True), ("cornell-env", 3, 1, 0, 0.5, True), ("turntable", 3, 0, 0, 0.5, True),
+    ("turntable", 3, 1, 0, 0.5, True), ("glossy", 3, 0, 0, 0.5, False), ("cornell-env", 3, 1, 0, 0.5, False)])
+def test_two_way_matches_the_oracle_on_the_same_samples(name, depth, lt_mode, mis_mode, sigma, aim):
     sd, cam = _scene(name, 32)
-    s, s2, c, sp, stats = two_way_gpu(sd, cam, 64, depth, lt_mode=lt_mode, sigma=sigma, mis_mode=mis_mode)
+    s, s2, c, sp, stats = two_way_gpu(sd, cam, 64, depth, lt_mode=lt_mode, sigma=sigma, mis_mode=mis_mode, aim=aim)
     S, S2, C, SP, _ = oracle.Scene(sd).render_two_way(cam, 64, depth, sigma=sigma, mis_mode=mis_mode,
-                                                      lt_mode=lt_mode)
+                                                      lt_mode=lt_mode, aim=aim)
     assert np.array_equal(c, C)
     assert stats.paths == 64 * 32 * 32 and stats.extension_rays > 0 and stats.shadow_rays > 0
     # camera stage: per pixel within 4 sigma of its own noise
@@ -165,7 +169,7 @@ def test_instanced_two_way_has_the_path_tracers_expectation(light_bvh):
     assert m_tw.mean() == pytest.approx(m_pt.mean(), rel=0.03)
 
 
-@pytest.mark.parametrize("name,lt_mode", [("glossy", 0), ("cornell-env", 0), ("cornell-env", 1)])
+@pytest.mark.parametrize("name,lt_mode", [("glossy", 0), ("cornell-env", 0), ("cornell-env", 1), ("turntable", 1)])
 def test_two_way_splats_match_the_oracle_per_pixel(name, lt_mode):
     """The light stage's splat image against the oracle's on the same light
     paths, pixel by pixel: K batches of iterations give both sides a
