@@ -88,12 +88,14 @@ __global__ void k_relu_pack(const float *Z, int64_t n, int64_t n_pad, __nv_bfloa
     store_tile_and_transpose<kGuideHid>(r0, n_pad, val, H, HT);
 }
 
+// Adam (Kingma and Ba 2015); omb1 = 1 - beta1 and omb2 = 1 - beta2 come from
+// the host in double precision (1 - 0.999f in FP32 is 1.3e-5 off 0.001).
 __global__ void k_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
-                       float eps, float c1, float c2) {
+                       float omb1, float omb2, float eps, float c1, float c2) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float gi = g[i];
-        float mi = b1 * m[i] + (1.f - b1) * gi;
-        float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        float mi = b1 * m[i] + omb1 * gi;
+        float vi = b2 * v[i] + omb2 * gi * gi;
         m[i] = mi;
         v[i] = vi;
         p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
@@ -356,7 +358,7 @@ rt_status guide_train_async(rt_guide *g, const float *feat, const float *wi, con
         float b1 = 0.9f, b2 = 0.999f;
         float c1 = 1.f - (float)std::pow(0.9, (double)g->step), c2 = 1.f - (float)std::pow(0.999, (double)g->step);
         k_adam<<<grid1d(g->nparams), 256, 0, st>>>(g->W32, g->grad, g->m, g->v, g->nparams, g->opts.learning_rate, b1,
-                                                   b2, 1e-8f, c1, c2);
+                                                   b2, (float)(1.0 - 0.9), (float)(1.0 - 0.999), 1e-8f, c1, c2);
         if ((s = repack(g, st))) return s;
     }
     return RT_OK;

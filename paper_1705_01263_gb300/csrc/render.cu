@@ -1360,16 +1360,6 @@ static RenderCache *cache_of(rt_film *f) {
     return (RenderCache *)f->cache;
 }
 
-// Pool capacity of the regeneration scheduler when the caller leaves it to
-// the library: 2^24 paths (about 2.8 GB of state) or the whole request if
-// smaller, at most a quarter of the free device memory.
-static uint32_t regen_capacity(uint64_t paths) {
-    size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)1 << 30;
-    const uint64_t by_mem = (uint64_t)(free_b / 4 / kPoolBytesPerPath);
-    return (uint32_t)std::max<uint64_t>(std::min<uint64_t>({paths, (uint64_t)1 << 24, by_mem}), 32u);
-}
-
 // rt_render with regeneration (Sec. 3.1.3): windows of consecutive tasks
 // stream through the pool; bounce steps are issued in chunks and the host
 // reads the control block of the chunk before the last one (so one chunk is
@@ -1401,6 +1391,7 @@ static rt_status render_regen(const rt_scene *s, const rt_camera *cam, uint32_t 
     pool.task = rc->pool.task;
     pool.qd = rc->pool.qd;
     pool.qfree = rc->pool.qfree;
+    pool.capacity = cap;   // the allocation may be larger (kept from an earlier call)
     // staging window: the request, at most 2^30 tasks and a quarter of the
     // free device memory (16 bytes per task)
     const uint64_t t_begin = film->next_task, t_end = (film->next_task / WH + (uint64_t)spp) * WH;
@@ -1647,8 +1638,11 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         set_error("rt_render: regen_fraction must be in [0, 1]");
         return RT_INVALID_ARG;
     }
-    uint32_t cap = o.max_paths_in_flight ? o.max_paths_in_flight
-                                         : (regen ? regen_capacity(request) : default_capacity(request));
+    // default pool: the whole request at once when it fits (at most 2^27
+    // paths and a quarter of free memory); fewer bounce steps, so fewer
+    // launch tails, than a smaller pool refilled by regeneration, which then
+    // engages only for larger requests
+    uint32_t cap = o.max_paths_in_flight ? o.max_paths_in_flight : default_capacity(request);
     cap = std::max<uint32_t>(cap, 32u);
     rt_status rs = ensure_pool(rc->pool, cap);
     if (rs != RT_OK) return rs;
