@@ -671,9 +671,13 @@ def two_way_vs_plain(res=256, depth=4, spp=64, ref_spp=4096, reps=3, scene_name=
     if scene_name == "glossy":
         sd, cam = scenes.glossy_room(res)
         what = f"glossy room lit through its ceiling, {res}x{res}"
+    elif scene_name == "turntable":
+        # a near-mirror sphere on a stand close to the camera in an open,
+        # sky-lit scene a few hundred times larger (Sec. 2.1.3's setting)
+        sd, cam = scenes.turntable(res)
+        what = f"turntable (near-mirror sphere, open sky-lit scene), {res}x{res}"
     else:
-        # the main scene, open and lit by the sky: environment photons spread
-        # over the disk across the whole bounding sphere (no photon aiming)
+        # the main scene, open and lit by the sky
         sd, cam = scenes.sphere_field()
         cam.width, cam.height = 2 * res, res
         what = f"sphere field (sky-lit, open), {2 * res}x{res}"
@@ -696,16 +700,21 @@ def two_way_vs_plain(res=256, depth=4, spp=64, ref_spp=4096, reps=3, scene_name=
         mean, _ = film.resolve()
         return mean, ms, None
 
-    def two_way(first, n):
+    def two_way(first, n, lt_emission=0, lt_mode=0):
         film.clear()
         film.seek(first)
-        st, ms = timed(lambda: rt.rt_render_two_way(scene, cam, n, depth, film))
+        o = rt.make_opts(lt_emission=lt_emission)
+        st, ms = timed(lambda: rt.rt_render_two_way(scene, cam, n, depth, film, o, lt_mode=lt_mode))
         mean, _ = film.resolve()
         return mean, ms, st
 
     ref, _, _ = two_way(1 << 22, ref_spp)
     out = {"workload": f"{what}, depth {depth}, {spp} iterations; reference: two-way, {ref_spp} disjoint iterations"}
-    for name, fn in (("path_tracer", plain), ("two_way", two_way)):
+    runs = (("path_tracer", plain), ("two_way", two_way),
+            ("two_way_uniform_emission", lambda f, n: two_way(f, n, lt_emission=1)),
+            ("light_tracer_alone_aimed", lambda f, n: two_way(f, n, lt_mode=1)),
+            ("light_tracer_alone_uniform", lambda f, n: two_way(f, n, lt_emission=1, lt_mode=1)))
+    for name, fn in runs:
         fn(0, spp)   # warm-up
         err, ms = [], []
         st = None
@@ -720,9 +729,14 @@ def two_way_vs_plain(res=256, depth=4, spp=64, ref_spp=4096, reps=3, scene_name=
                               "Mrays_per_s": (st.extension_rays + st.shadow_rays) / (out[name]["ms"] / 1e3) / 1e6})
         else:
             out[name]["Mpaths_per_s"] = spp * npix / (out[name]["ms"] / 1e3) / 1e6
-    p_, t_ = out["path_tracer"], out["two_way"]
+    p_, t_, u_ = out["path_tracer"], out["two_way"], out["two_way_uniform_emission"]
     out["rmse_ratio"] = t_["rmse"] / p_["rmse"]
     out["efficiency"] = (p_["rmse"] ** 2 * p_["ms"]) / (t_["rmse"] ** 2 * t_["ms"])
+    # photon aiming (Sec. 2.1.3) against uniform emission, with MIS and for
+    # the light tracer alone (where the emission decides the error)
+    out["aiming_efficiency"] = (u_["rmse"] ** 2 * u_["ms"]) / (t_["rmse"] ** 2 * t_["ms"])
+    la, lu = out["light_tracer_alone_aimed"], out["light_tracer_alone_uniform"]
+    out["aiming_efficiency_light_tracer_alone"] = (lu["rmse"] ** 2 * lu["ms"]) / (la["rmse"] ** 2 * la["ms"])
     film.close()
     return out
 
@@ -908,6 +922,8 @@ def main():
         print(json.dumps(two_way_vs_plain(spp=args.tw_spp, ref_spp=args.tw_ref_spp, reps=1)), flush=True)
         print(json.dumps(two_way_vs_plain(res=270, depth=8, spp=16, ref_spp=256, reps=1, scene_name="spheres")),
               flush=True)
+        print(json.dumps(two_way_vs_plain(res=128, depth=4, spp=64, ref_spp=4096, reps=1, scene_name="turntable")),
+              flush=True)
         return 0
     if args.render_once:
         st = rt.rt_stats()
@@ -1043,6 +1059,7 @@ def main():
     if rank == 0 and not args.no_two_way:
         tw = two_way_vs_plain()
         tw["open_scene"] = two_way_vs_plain(res=270, depth=8, spp=16, ref_spp=256, scene_name="spheres")
+        tw["turntable"] = two_way_vs_plain(res=128, depth=4, spp=64, ref_spp=4096, scene_name="turntable")
     sweep = None
     if rank == 0 and not args.no_scheduler_sweep:
         sweep = scheduler_sweep(scene, cam, args.spp, DEPTH)

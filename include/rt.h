@@ -152,9 +152,9 @@ typedef struct {
     int32_t mis_mode;        /* 0 power heuristic, 1 balance, 2 NEE only, 3 BSDF only */
     uint64_t seed;           /* scrambling seed for the Halton digits (A.2) */
     double time_budget_ms;   /* stop issuing new paths after this (0 = none); see rt_render */
-    uint32_t max_paths_in_flight; /* state-pool capacity; 0 = 2^24 paths with regeneration (scheduler 0), every
-                                   * requested path with iteration sets (scheduler 1); at most 2^27 and a quarter
-                                   * of free device memory */
+    uint32_t max_paths_in_flight; /* state-pool capacity; 0 = every requested path at once, at most 2^27 and a
+                                   * quarter of free device memory (regeneration refills it beyond); with an abort
+                                   * flag or a time budget under scheduler 0, at most 2^24 paths */
     int32_t megakernel_only; /* 1: one megakernel per iteration set (A/B baseline) */
     int32_t sort_by_material;/* 1: material-sorted shading queue */
     uint32_t tail_threshold; /* live paths below which the megakernel finishes a set (0 = auto) */

@@ -66,20 +66,23 @@ RT_HD float4 aim_sample(const DevScene &sc, float4 eye, bool from_tri, V3 y, V3 
     }
 }
 
-// Line through x along w meets the sphere.
+// Line through x along unit w meets the sphere: the centre's distance to
+// the line, |v x w| (no cancellation, unlike |v|^2 - (v.w)^2 in FP32 far
+// from the sphere), at most the radius.
 RT_HD bool aim_line_meets(float4 sph, V3 x, V3 w) {
-    const V3 v = v3(sph.x, sph.y, sph.z) - x;
-    const float t = dot(v, w);
-    return dot(v, v) - t * t <= sph.w * sph.w;
+    const V3 q = cross(v3(sph.x, sph.y, sph.z) - x, w);
+    return dot(q, q) <= sph.w * sph.w;
 }
 
-// Ray from y along w passes through the sphere (w inside the cone it
-// subtends from y, or y inside it).
+// Ray from y along unit w passes through the sphere: y inside it, or the
+// centre ahead and within the radius of the ray's line (the same as w inside
+// the cone the sphere subtends from y, without comparing two cosines near 1).
 RT_HD bool aim_cone_holds(float4 sph, V3 y, V3 w) {
     const V3 v = v3(sph.x, sph.y, sph.z) - y;
-    const float d2 = dot(v, v), r2 = sph.w * sph.w;
-    if (d2 <= r2) return true;
-    return dot(v, w) / sqrtf(d2) >= sqrtf(1.f - r2 / d2);
+    const float r2 = sph.w * sph.w;
+    if (dot(v, v) <= r2) return true;
+    const V3 q = cross(v, w);
+    return dot(v, w) > 0.f && dot(q, q) <= r2;
 }
 
 // Environment photon: density per unit area across w of the photon line

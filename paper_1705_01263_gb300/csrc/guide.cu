@@ -356,7 +356,8 @@ rt_status guide_train_async(rt_guide *g, const float *feat, const float *wi, con
         if ((s = train_forward(g, feat, wi, weight, n, st)) || (s = backward(g, n, st))) return s;
         ++g->step;
         float b1 = 0.9f, b2 = 0.999f;
-        float c1 = 1.f - (float)std::pow(0.9, (double)g->step), c2 = 1.f - (float)std::pow(0.999, (double)g->step);
+        // bias corrections in double: 1.f - (float)0.999^t loses 1.3e-5 to cancellation
+        float c1 = (float)(1.0 - std::pow(0.9, (double)g->step)), c2 = (float)(1.0 - std::pow(0.999, (double)g->step));
         k_adam<<<grid1d(g->nparams), 256, 0, st>>>(g->W32, g->grad, g->m, g->v, g->nparams, g->opts.learning_rate, b1,
                                                    b2, (float)(1.0 - 0.9), (float)(1.0 - 0.999), 1e-8f, c1, c2);
         if ((s = repack(g, st))) return s;

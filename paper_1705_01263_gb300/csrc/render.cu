@@ -1639,10 +1639,15 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         return RT_INVALID_ARG;
     }
     // default pool: the whole request at once when it fits (at most 2^27
-    // paths and a quarter of free memory); fewer bounce steps, so fewer
+    // paths and a quarter of free memory): fewer bounce steps, so fewer
     // launch tails, than a smaller pool refilled by regeneration, which then
-    // engages only for larger requests
+    // engages only for larger requests. A call that can be stopped (abort
+    // flag or time budget) takes 2^24 paths at most instead, so that a stop
+    // leaves most of the request unstarted and the paths in flight drain
+    // quickly.
+    const bool stoppable = o.abort_flag || o.time_budget_ms > 0;
     uint32_t cap = o.max_paths_in_flight ? o.max_paths_in_flight : default_capacity(request);
+    if (regen && stoppable && !o.max_paths_in_flight) cap = std::min<uint32_t>(cap, 1u << 24);
     cap = std::max<uint32_t>(cap, 32u);
     rt_status rs = ensure_pool(rc->pool, cap);
     if (rs != RT_OK) return rs;

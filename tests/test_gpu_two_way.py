@@ -52,7 +52,7 @@ def two_way_gpu(sd, cam, spp, depth, first=0, lt_mode=0, sigma=0.5, mis_mode=0, 
     ("glossy", 3, 0, 0, 0.5, True), ("glossy", 3, 0, 1, 0.5, True), ("glossy", 3, 1, 0, 0.5, True),
     ("cornell", 4, 0, 0, 0.5, True), ("cornell", 4, 0, 0, 0.0, True), ("many", 3, 0, 0, 0.5, True),
     ("cornell-env", 3, 0, 0, 0.5, True), ("cornell-env", 3, 1, 0, 0.5, True), ("turntable", 3, 0, 0, 0.5, True),
-    ("turntable", 3, 1, 0, 0.5, True), ("glossy", 3, 0, 0, 0.5, False), ("cornell-env", 3, 1, 0, 0.5, False)])
+    ("turntable", 3, 0, 1, 0.5, True), ("glossy", 3, 0, 0, 0.5, False), ("cornell-env", 3, 1, 0, 0.5, False)])
 def test_two_way_matches_the_oracle_on_the_same_samples(name, depth, lt_mode, mis_mode, sigma, aim):
     sd, cam = _scene(name, 32)
     s, s2, c, sp, stats = two_way_gpu(sd, cam, 64, depth, lt_mode=lt_mode, sigma=sigma, mis_mode=mis_mode, aim=aim)
@@ -169,7 +169,7 @@ def test_instanced_two_way_has_the_path_tracers_expectation(light_bvh):
     assert m_tw.mean() == pytest.approx(m_pt.mean(), rel=0.03)
 
 
-@pytest.mark.parametrize("name,lt_mode", [("glossy", 0), ("cornell-env", 0), ("cornell-env", 1), ("turntable", 1)])
+@pytest.mark.parametrize("name,lt_mode", [("glossy", 0), ("cornell-env", 0), ("cornell-env", 1), ("turntable", 0)])
 def test_two_way_splats_match_the_oracle_per_pixel(name, lt_mode):
     """The light stage's splat image against the oracle's on the same light
     paths, pixel by pixel: K batches of iterations give both sides a
