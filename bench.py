@@ -275,6 +275,18 @@ def scheduler_sweep(scene, cam, spp, depth, pools=(1 << 22, 1 << 23, 1 << 24, 1 
     r = timed(max_paths=1 << 24, regen_fraction=1e-6)
     r["of_whole_request"] = r["Mpaths_per_s"] / whole
     out["regen_pool_16M_every_step"] = r
+    # state compression (Sec. 3.1.1) A/B: the whole request in one pool,
+    # uncompressed against compressed; image difference as mean relative L1
+    film.clear()
+    rt.rt_render(scene, cam, spp, depth, film, rt.make_opts())
+    ref = film.resolve()[0].double()
+    for name, kw in (("uncompressed", {}), ("compressed", {"state_compression": True})):
+        r = timed(**kw)
+        r["of_whole_request"] = r["Mpaths_per_s"] / whole
+        r["state_bytes_per_path"] = 132 if kw else 168
+        img = film.resolve()[0].double()
+        r["image_rel_l1_vs_uncompressed"] = float((img - ref).abs().sum() / ref.abs().sum())
+        out[f"state_{name}"] = r
     film.close()
     return out
 

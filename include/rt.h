@@ -179,6 +179,10 @@ typedef struct {
                               * the paper's rule); must be in [0, 1] */
     int32_t lt_emission;     /* rt_render_two_way: 0 photon aiming (Sec. 2.1.3), 1 uniform emission over
                               * the scene's bound and cosine directions (A/B) */
+    int32_t state_compression; /* rt_render, scheduler 0 (A/B, Sec. 3.1.1): ray and shadow directions as
+                              * 16:16 octahedral codes, throughput and shadow contributions as BF16, the
+                              * vertex number in 16 bits (132 instead of 168 bytes of state per path);
+                              * RT_NOT_SUPPORTED with iteration sets, guiding or megakernel_only */
 } rt_render_opts;
 
 /* ---------------------------------------------------------------- scene */

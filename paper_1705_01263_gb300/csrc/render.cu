@@ -60,12 +60,69 @@ struct Pool {
     uint32_t *task;
     uint32_t *qd;
     uint32_t *qfree;
+    // compressed state (Sec. 3.1.1, rt_render_opts.state_compression): when
+    // `compact` is set these replace ray_d, beta, sh_d and sh_c (null then):
+    // direction as a 16:16 octahedral code + prev_pdf (FP32); throughput as
+    // three BF16 + the vertex number (16 bits); shadow direction as an
+    // octahedral code; shadow contribution as three BF16
+    uint2 *dir_c;
+    uint2 *beta_c;
+    uint32_t *shd_c;
+    uint2 *shc_c;
+    int compact;
 };
+
+RT_D uint32_t bf16x2_pack(float a, float b) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+}
+RT_D float bf16_lo(uint32_t w) { return __bfloat162float(__ushort_as_bfloat16((unsigned short)(w & 0xffffu))); }
+RT_D float bf16_hi(uint32_t w) { return __bfloat162float(__ushort_as_bfloat16((unsigned short)(w >> 16))); }
+
+// Accessors of the arrays that have a compressed form: (xyz, w) as in the
+// uncompressed float4 layout.
+RT_D float4 ld_dir(const Pool &p, uint32_t q) {
+    if (!p.compact) return p.ray_d[q];
+    const uint2 c = p.dir_c[q];
+    const V3 d = oct_decode(c.x);
+    return make_float4(d.x, d.y, d.z, __uint_as_float(c.y));
+}
+RT_D void st_dir(const Pool &p, uint32_t q, V3 d, float prev_pdf) {
+    if (!p.compact) p.ray_d[q] = make_float4(d.x, d.y, d.z, prev_pdf);
+    else p.dir_c[q] = make_uint2(oct_encode(d), __float_as_uint(prev_pdf));
+}
+RT_D float4 ld_beta(const Pool &p, uint32_t q) {   // w: vertex number bits
+    if (!p.compact) return p.beta[q];
+    const uint2 c = p.beta_c[q];
+    return make_float4(bf16_lo(c.x), bf16_hi(c.x), bf16_lo(c.y), __uint_as_float(c.y >> 16));
+}
+RT_D void st_beta(const Pool &p, uint32_t q, V3 b, uint32_t depth) {
+    if (!p.compact) p.beta[q] = make_float4(b.x, b.y, b.z, __uint_as_float(depth));
+    else p.beta_c[q] = make_uint2(bf16x2_pack(b.x, b.y), (bf16x2_pack(b.z, 0.f) & 0xffffu) | (depth << 16));
+}
+RT_D float4 ld_shd(const Pool &p, uint32_t q) {
+    if (!p.compact) return p.sh_d[q];
+    const V3 d = oct_decode(p.shd_c[q]);
+    return make_float4(d.x, d.y, d.z, 0.f);
+}
+RT_D void st_shd(const Pool &p, uint32_t q, V3 d) {
+    if (!p.compact) p.sh_d[q] = make_float4(d.x, d.y, d.z, 0.f);
+    else p.shd_c[q] = oct_encode(d);
+}
+RT_D float4 ld_shc(const Pool &p, uint32_t q) {
+    if (!p.compact) return p.sh_c[q];
+    const uint2 c = p.shc_c[q];
+    return make_float4(bf16_lo(c.x), bf16_hi(c.x), bf16_lo(c.y), 0.f);
+}
+RT_D void st_shc(const Pool &p, uint32_t q, V3 c) {
+    if (!p.compact) p.sh_c[q] = make_float4(c.x, c.y, c.z, 0.f);
+    else p.shc_c[q] = make_uint2(bf16x2_pack(c.x, c.y), bf16x2_pack(c.z, 0.f));
+}
 
 RT_D void store_state(const Pool &p, uint32_t q, const PathState &s) {
     p.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
-    p.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);
-    p.beta[q] = make_float4(s.beta.x, s.beta.y, s.beta.z, __uint_as_float(s.depth));
+    st_dir(p, q, s.d, s.prev_pdf);
+    st_beta(p, q, s.beta, s.depth);
     p.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
     p.index[q] = make_uint2((uint32_t)s.index, (uint32_t)(s.index >> 32));
     p.pixel[q] = s.pixel;
@@ -73,7 +130,7 @@ RT_D void store_state(const Pool &p, uint32_t q, const PathState &s) {
 
 RT_D PathState load_state(const Pool &p, uint32_t q) {
     PathState s;
-    float4 o = p.ray_o[q], d = p.ray_d[q], b = p.beta[q], L = p.L[q];
+    float4 o = p.ray_o[q], d = ld_dir(p, q), b = ld_beta(p, q), L = p.L[q];
     uint2 ix = p.index[q];
     s.o = v3(o.x, o.y, o.z);
     s.prev_cell = __float_as_uint(o.w);
@@ -226,13 +283,13 @@ __global__ void __launch_bounds__(128, 8) k_shade(RenderParams P, Pool pool, con
             pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
             if (r & 1) {
                 pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
-                pool.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);
-                pool.beta[q] = make_float4(s.beta.x, s.beta.y, s.beta.z, __uint_as_float(s.depth));
+                st_dir(pool, q, s.d, s.prev_pdf);
+                st_beta(pool, q, s.beta, s.depth);
             }
             if (r & 2) {
                 pool.sh_o[q] = make_float4(sh.o.x, sh.o.y, sh.o.z, sh.tmax);
-                pool.sh_d[q] = make_float4(sh.d.x, sh.d.y, sh.d.z, 0.f);
-                pool.sh_c[q] = make_float4(sh.contrib.x, sh.contrib.y, sh.contrib.z, 0.f);
+                st_shd(pool, q, sh.d);
+                st_shc(pool, q, sh.contrib);
             }
         }
         warp_append(next, &c->n_next, valid && (r & 1), q);
@@ -262,7 +319,7 @@ __global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_ext_simple(Dev
         uint32_t i = base + lane_id();
         if (i >= n) continue;
         uint32_t q = queue[i];
-        float4 o = pool.ray_o[q], d = pool.ray_d[q];
+        float4 o = pool.ray_o[q], d = ld_dir(pool, q);
         Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, INFINITY};
         Hit h;
         h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
@@ -297,7 +354,7 @@ __global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_shadow_simple(
         uint32_t i = base + lane_id();
         if (i >= n) continue;
         uint32_t q = pool.qs[i];
-        float4 o = pool.sh_o[q], d = pool.sh_d[q];
+        float4 o = pool.sh_o[q], d = ld_shd(pool, q);
         Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, o.w};
         Hit h;
         h.prim = RT_MISS; h.inst = 0; h.t = INFINITY;
@@ -307,7 +364,7 @@ __global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_shadow_simple(
         overflow |= tr.overflow;
         if (kCount) { nodes += tr.nodes; tris += tr.tris; }
         if (h.prim == RT_MISS) {
-            float4 cc = pool.sh_c[q], L = pool.L[q];
+            float4 cc = ld_shc(pool, q), L = pool.L[q];
             pool.L[q] = make_float4(L.x + cc.x, L.y + cc.y, L.z + cc.z, L.w);
         }
     }
@@ -357,10 +414,10 @@ __global__ void __launch_bounds__(128, 8) k_trace_refill(DevScene sc, Pool pool,
                     q = queue[i];
                     Ray r;
                     if (kAnyHit) {
-                        float4 o = pool.sh_o[q], d = pool.sh_d[q];
+                        float4 o = pool.sh_o[q], d = ld_shd(pool, q);
                         r = Ray{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, o.w};
                     } else {
-                        float4 o = pool.ray_o[q], d = pool.ray_d[q];
+                        float4 o = pool.ray_o[q], d = ld_dir(pool, q);
                         r = Ray{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, INFINITY};
                     }
                     h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
@@ -377,7 +434,7 @@ __global__ void __launch_bounds__(128, 8) k_trace_refill(DevScene sc, Pool pool,
             if (kCount) { nodes += res.nodes; tris += res.tris; }
             if (kAnyHit) {
                 if (h.prim == RT_MISS) {
-                    float4 cc = pool.sh_c[q], L = pool.L[q];
+                    float4 cc = ld_shc(pool, q), L = pool.L[q];
                     pool.L[q] = make_float4(L.x + cc.x, L.y + cc.y, L.z + cc.z, L.w);
                 }
             } else {
@@ -414,7 +471,7 @@ RT_D uint32_t spread3(uint32_t x) {   // 3 bits -> every third bit
 struct RayKey {
     float3 lo, inv_ext;
     RT_D uint32_t operator()(const Pool &pool, uint32_t q) const {
-        float4 o = pool.ray_o[q], d = pool.ray_d[q];
+        float4 o = pool.ray_o[q], d = ld_dir(pool, q);
         uint32_t cx = (uint32_t)fminf(7.f, fmaxf(0.f, (o.x - lo.x) * inv_ext.x * 8.f));
         uint32_t cy = (uint32_t)fminf(7.f, fmaxf(0.f, (o.y - lo.y) * inv_ext.y * 8.f));
         uint32_t cz = (uint32_t)fminf(7.f, fmaxf(0.f, (o.z - lo.z) * inv_ext.z * 8.f));
@@ -611,8 +668,8 @@ __global__ void k_probe_start(RenderParams P, Pool pool, const float *pos, const
             store_state(pool, q, s);
             if (r & 2) {
                 pool.sh_o[q] = make_float4(sh.o.x, sh.o.y, sh.o.z, sh.tmax);
-                pool.sh_d[q] = make_float4(sh.d.x, sh.d.y, sh.d.z, 0.f);
-                pool.sh_c[q] = make_float4(sh.contrib.x, sh.contrib.y, sh.contrib.z, 0.f);
+                st_shd(pool, q, sh.d);
+                st_shc(pool, q, sh.contrib);
             }
         }
         warp_append(pool.q[0], &c->n_ext, valid && (r & 1), q);
@@ -977,8 +1034,8 @@ __global__ void __launch_bounds__(128, 6) k_shade_guided(RenderParams P, Pool po
             pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
             if (r & 1) {
                 pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
-                pool.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);
-                pool.beta[q] = make_float4(s.beta.x, s.beta.y, s.beta.z, __uint_as_float(s.depth));
+                st_dir(pool, q, s.d, s.prev_pdf);
+                st_beta(pool, q, s.beta, s.depth);
                 if (want) {
                     float4 *R = rec + ((size_t)slot * kGuideMaxRec + (v - 1)) * 4;
                     R[0] = make_float4(gr.feat[0], gr.feat[1], gr.feat[2], gr.feat[3]);
@@ -990,8 +1047,8 @@ __global__ void __launch_bounds__(128, 6) k_shade_guided(RenderParams P, Pool po
             }
             if (r & 2) {
                 pool.sh_o[q] = make_float4(sh.o.x, sh.o.y, sh.o.z, sh.tmax);
-                pool.sh_d[q] = make_float4(sh.d.x, sh.d.y, sh.d.z, 0.f);
-                pool.sh_c[q] = make_float4(sh.contrib.x, sh.contrib.y, sh.contrib.z, 0.f);
+                st_shd(pool, q, sh.d);
+                st_shc(pool, q, sh.contrib);
             }
         }
         warp_append(next, &c->n_next, valid && (r & 1), q);
@@ -1129,6 +1186,7 @@ struct PoolAlloc {
     uint32_t *task = nullptr, *qd = nullptr, *qfree = nullptr;
     void *block = nullptr;
     uint32_t capacity = 0;
+    bool compact = false;   // compressed layout of the direction, throughput and shadow arrays
     ~PoolAlloc() {
         if (block) cudaFree(block);
     }
@@ -1151,21 +1209,31 @@ uint32_t default_capacity(uint64_t paths) {
     return (uint32_t)std::max<uint64_t>(c, 32u);
 }
 
-rt_status ensure_pool(PoolAlloc &pa, uint32_t capacity) {
-    if (pa.block && pa.capacity >= capacity) return RT_OK;
+rt_status ensure_pool(PoolAlloc &pa, uint32_t capacity, bool compact = false) {
+    if (pa.block && pa.capacity >= capacity && pa.compact == compact) return RT_OK;
     if (pa.block) { cudaFree(pa.block); pa.block = nullptr; }
     size_t P = capacity;
     size_t f4 = P * sizeof(float4);
-    size_t bytes = 8 * f4 + P * sizeof(uint2) + P * 4 /*pixel*/ + P * 4 /*hit_inst*/ + 3 * P * 4 /*queues*/ +
-                   3 * P * 4 /*regeneration*/ + 64 * 256;
+    // four float4 arrays always (origin, radiance, hit, shadow origin); four
+    // more, or their compressed forms (8 + 8 + 4 + 8 bytes per path)
+    size_t bytes = 4 * f4 + (compact ? P * 28 + 4 * 256 : 4 * f4) + P * sizeof(uint2) + P * 4 /*pixel*/ +
+                   P * 4 /*hit_inst*/ + 3 * P * 4 /*queues*/ + 3 * P * 4 /*regeneration*/ + 64 * 256;
     cudaError_t e = cudaMalloc(&pa.block, bytes);
     if (e != cudaSuccess) { set_error("path-state pool allocation failed"); return RT_OOM; }
     char *p = (char *)pa.block;
     auto take = [&](size_t b) { char *r = p; p += (b + 255) / 256 * 256; return r; };
     Pool &v = pa.view;
+    v = Pool{};
     v.ctrl = (Ctrl *)take(sizeof(Ctrl));
-    v.ray_o = (float4 *)take(f4); v.ray_d = (float4 *)take(f4); v.beta = (float4 *)take(f4); v.L = (float4 *)take(f4);
-    v.hit = (float4 *)take(f4); v.sh_o = (float4 *)take(f4); v.sh_d = (float4 *)take(f4); v.sh_c = (float4 *)take(f4);
+    v.ray_o = (float4 *)take(f4); v.L = (float4 *)take(f4); v.hit = (float4 *)take(f4); v.sh_o = (float4 *)take(f4);
+    if (compact) {
+        v.dir_c = (uint2 *)take(P * 8); v.beta_c = (uint2 *)take(P * 8);
+        v.shd_c = (uint32_t *)take(P * 4); v.shc_c = (uint2 *)take(P * 8);
+        v.compact = 1;
+    } else {
+        v.ray_d = (float4 *)take(f4); v.beta = (float4 *)take(f4); v.sh_d = (float4 *)take(f4); v.sh_c = (float4 *)take(f4);
+    }
+    pa.compact = compact;
     v.index = (uint2 *)take(P * sizeof(uint2));
     v.pixel = (uint32_t *)take(P * 4);
     v.hit_inst = (uint32_t *)take(P * 4);
@@ -1649,7 +1717,11 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     uint32_t cap = o.max_paths_in_flight ? o.max_paths_in_flight : default_capacity(request);
     if (regen && stoppable && !o.max_paths_in_flight) cap = std::min<uint32_t>(cap, 1u << 24);
     cap = std::max<uint32_t>(cap, 32u);
-    rt_status rs = ensure_pool(rc->pool, cap);
+    if (o.state_compression && !regen) {
+        set_error("rt_render: state_compression needs the regeneration scheduler, without guiding or megakernel_only");
+        return RT_NOT_SUPPORTED;
+    }
+    rt_status rs = ensure_pool(rc->pool, cap, o.state_compression != 0);
     if (rs != RT_OK) return rs;
     const int ndims = 2 + 7 * (int)(max_depth + 1);
     if (!rc->dims || rc->dims_seed != o.seed || rc->dims_n < ndims) {
@@ -2136,8 +2208,8 @@ extern "C" rt_status rt_render_static(const rt_scene *s, const rt_camera *cam, u
     if (opts_in) o = *opts_in;
     if (!valid_block(o.block_size)) { set_error("rt_render_static: block_size must be 0 or a multiple of 32 up to 128"); return RT_INVALID_ARG; }
     if (o.guide) { set_error("rt_render_static: guiding needs rt_render"); return RT_NOT_SUPPORTED; }
-    if (o.sort_by_material || o.sort_rays) {
-        set_error("rt_render_static: sorted queues need buffers of their own (use rt_render)");
+    if (o.sort_by_material || o.sort_rays || o.state_compression) {
+        set_error("rt_render_static: sorted queues and compressed state need buffers of their own (use rt_render)");
         return RT_NOT_SUPPORTED;
     }
     if (o.max_paths_in_flight > kStaticMaxPaths) {
@@ -2326,7 +2398,7 @@ __global__ void __launch_bounds__(128) k_batch_trace(const BatchJob *jobs, Pool 
         if (i >= n) continue;
         uint32_t q = queue[i];
         const DevScene &sc = jobs[job_of[q]].P.sc;
-        float4 o = kAny ? pool.sh_o[q] : pool.ray_o[q], d = kAny ? pool.sh_d[q] : pool.ray_d[q];
+        float4 o = kAny ? pool.sh_o[q] : pool.ray_o[q], d = kAny ? ld_shd(pool, q) : ld_dir(pool, q);
         Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, kAny ? o.w : INFINITY};
         Hit h;
         h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
@@ -2334,7 +2406,7 @@ __global__ void __launch_bounds__(128) k_batch_trace(const BatchJob *jobs, Pool 
         overflow |= tr.overflow;
         if (kAny) {
             if (h.prim == RT_MISS) {
-                float4 cc = pool.sh_c[q], L = pool.L[q];
+                float4 cc = ld_shc(pool, q), L = pool.L[q];
                 pool.L[q] = make_float4(L.x + cc.x, L.y + cc.y, L.z + cc.z, L.w);
             }
         } else {
@@ -2371,13 +2443,13 @@ __global__ void __launch_bounds__(128) k_batch_shade(const BatchJob *jobs, Pool 
             pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
             if (r & 1) {
                 pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
-                pool.ray_d[q] = make_float4(s.d.x, s.d.y, s.d.z, s.prev_pdf);
-                pool.beta[q] = make_float4(s.beta.x, s.beta.y, s.beta.z, __uint_as_float(s.depth));
+                st_dir(pool, q, s.d, s.prev_pdf);
+                st_beta(pool, q, s.beta, s.depth);
             }
             if (r & 2) {
                 pool.sh_o[q] = make_float4(sh.o.x, sh.o.y, sh.o.z, sh.tmax);
-                pool.sh_d[q] = make_float4(sh.d.x, sh.d.y, sh.d.z, 0.f);
-                pool.sh_c[q] = make_float4(sh.contrib.x, sh.contrib.y, sh.contrib.z, 0.f);
+                st_shd(pool, q, sh.d);
+                st_shc(pool, q, sh.contrib);
             }
         }
         warp_append(next, &c->n_next, valid && (r & 1), q);

@@ -72,7 +72,8 @@ class rt_render_opts(C.Structure):
                 ("tail_threshold", C.c_uint32), ("block_size", C.c_uint32),
                 ("abort_flag", C.c_void_p), ("guide", C.c_void_p), ("stats", C.POINTER(rt_stats)),
                 ("profile", C.c_int32), ("trace_kernel", C.c_int32), ("sort_rays", C.c_int32),
-                ("scheduler", C.c_int32), ("regen_fraction", C.c_float), ("lt_emission", C.c_int32)]
+                ("scheduler", C.c_int32), ("regen_fraction", C.c_float), ("lt_emission", C.c_int32),
+                ("state_compression", C.c_int32)]
 
 
 class rt_render_job(C.Structure):
@@ -377,7 +378,8 @@ def make_opts(sigma: float = 0.5, rr: bool = False, mis_mode: int = 0, seed: int
               max_paths: int = 0, megakernel_only: bool = False, sort_by_material: bool = False,
               tail_threshold: int = 0, abort_flag=None, guide=None, stats: Optional[rt_stats] = None,
               profile: int = 0, trace_kernel: int = 0, sort_rays: bool = False, block_size: int = 0,
-              scheduler: int = 0, regen_fraction: float = 0.0, lt_emission: int = 0):
+              scheduler: int = 0, regen_fraction: float = 0.0, lt_emission: int = 0,
+              state_compression: bool = False):
     o = rt_render_opts()
     o.filter_sigma = sigma if sigma > 0 else -1.0
     o.rr_enable, o.mis_mode, o.seed = int(rr), mis_mode, seed
@@ -397,6 +399,7 @@ def make_opts(sigma: float = 0.5, rr: bool = False, mis_mode: int = 0, seed: int
     o.scheduler = scheduler
     o.regen_fraction = regen_fraction
     o.lt_emission = lt_emission
+    o.state_compression = int(state_compression)
     return o
 
 

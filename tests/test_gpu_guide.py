@@ -262,8 +262,11 @@ def test_adam_update_matches_oracle_element_wise():
         assert step == t
         Po, Mo, Vo = P.copy(), M.copy(), V.copy()
         oracle.adam_step(Po, g, Mo, Vo, t)
-        assert np.allclose(Mg, Mo, rtol=4e-7, atol=1e-30)
-        assert np.allclose(Vg, Vo, rtol=4e-7, atol=1e-38)
+        # FP32 rounding of b M + (1 - b) g (a few units in the last place of
+        # the larger term; the sum itself may cancel)
+        u = 2.0 ** -24
+        assert np.all(np.abs(Mg - Mo) <= 4 * u * (0.9 * np.abs(M) + 0.1 * np.abs(g)) + 1e-38)
+        assert np.all(np.abs(Vg - Vo) <= 4 * u * (0.999 * V + 0.001 * g * g) + 1e-38)
         step_size = np.abs(Po - P)
         assert np.all(np.abs(Pg - Po) <= 4e-6 * step_size + 2 * np.spacing(np.abs(P).astype(np.float32))), \
             np.abs(Pg - Po).max()

@@ -140,3 +140,46 @@ def test_time_budget_stops_on_the_device(field):
     _, _, c = f.download()
     full, rem = divmod(st.paths, WH)
     assert c.reshape(-1)[:rem].min() == full + 1 and c.reshape(-1)[rem:].max() == full
+
+
+@pytest.mark.parametrize("scene_name", ["cornell", "field"])
+def test_compressed_state_matches_the_oracle(scene_name):
+    """State compression (Sec. 3.1.1, an A/B option of the regeneration
+    scheduler: octahedral 16:16 directions, BF16 throughput and shadow
+    contributions) against the FP64 oracle on the same samples: the same
+    per-pixel 4 sigma and mean relative L1 bars as the uncompressed tracer,
+    and within a small L1 of the uncompressed render (quantised directions
+    move a few paths)."""
+    import oracle
+    from helpers import allowed_4sigma, image_parity
+    from paper_1705_01263_gb300 import rt
+    if scene_name == "cornell":
+        sd, cam = scenes.cornell_box()
+        spp, depth = 16, 8
+    else:
+        sd, cam = scenes.sphere_field(n_spheres=40, plane_res=(120, 60), env_size=(512, 256), width=160, height=90)
+        spp, depth = 32, 8
+    scene = rt.Scene(sd)
+    a, _, _ = render(scene, cam, spp, depth, max_paths=20_000, state_compression=True)
+    b, _, _ = render(scene, cam, spp, depth, max_paths=20_000)
+    sa, s2a, ca = a.download()
+    sb, s2b, cb = b.download()
+    assert np.array_equal(ca, cb)
+    S, S2, C, _ = oracle.Scene(sd).render(cam, spp, depth)
+    mo, vo = oracle.resolve(S, S2, C)
+    ma, va = oracle.resolve(sa, s2a, ca)
+    l1, out, n = image_parity(ma, va, mo, vo)
+    assert l1 <= 0.01 and out <= allowed_4sigma(n), (l1, out, n)
+    mb, _ = oracle.resolve(sb, s2b, cb)
+    assert np.abs(ma - mb).sum() / np.abs(mb).sum() < 5e-3
+
+
+def test_compressed_state_is_rejected_where_unsupported():
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.cornell_box()
+    scene = rt.Scene(sd)
+    film = rt.Film(cam.width, cam.height)
+    for kw in ({"scheduler": 1}, {"megakernel_only": True}):
+        with pytest.raises(rt.RtError) as e:
+            rt.rt_render(scene, cam, 1, 4, film, rt.make_opts(state_compression=True, **kw))
+        assert e.value.status == 7
