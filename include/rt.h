@@ -199,9 +199,10 @@ rt_status rt_scene_info(const rt_scene *scene, int64_t *nodes, int64_t *leaf_tri
 /* rays -> hits (Sec. 3.1, the ray-casting state kernels). Closest hit when
  * any_hit == 0 (ties in t: lower (inst, prim) wins); otherwise any hit in
  * (tmin, tmax) and prim != RT_MISS iff occluded. The kernel runs on
- * `stream`; its ray-fetch counter and overflow flag are this call's own (8
- * bytes from the stream-ordered allocator, released on the stream), so calls
- * in flight on different streams or host threads do not interfere. The call
+ * `stream`; its ray-fetch counter and overflow flag belong to that stream (8
+ * bytes of device memory and a pinned word per device and stream, allocated
+ * on the stream's first call and kept until exit), so calls in flight on
+ * different streams or host threads do not interfere. The call
  * waits for its kernel before returning, so that it can report
  * RT_STACK_OVERFLOW: a ray whose traversal needed more than the fixed stack
  * (48 node groups; BVHs built by rt_scene_create stay far below it) has an

@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
+#include <map>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -1310,6 +1312,27 @@ static rt_status ensure_guided(RenderCache *rc, uint32_t cap, uint32_t batch) {
 
 static RenderCache *cache_of(rt_film *f);
 
+// Per (device, stream) scratch of rt_trace: 8 bytes of device memory and a
+// pinned word, allocated on first use and kept until the process exits.
+struct TraceScratch {
+    uint32_t *dev = nullptr;
+    uint32_t *host = nullptr;
+};
+static rt_status trace_scratch(cudaStream_t st, TraceScratch **out) {
+    static std::mutex mu;
+    static std::map<std::pair<int, cudaStream_t>, TraceScratch> table;
+    int dev = 0;
+    RT_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    TraceScratch &ts = table[{dev, st}];
+    if (!ts.dev) {
+        RT_CUDA_TRY(cudaMalloc(&ts.dev, 2 * sizeof(uint32_t)));
+        RT_CUDA_TRY(cudaMallocHost(&ts.host, sizeof(uint32_t)));
+    }
+    *out = &ts;
+    return RT_OK;
+}
+
 extern "C" rt_status rt_trace(const rt_scene *s, const rt_rays *rays, int64_t n, const rt_hits *hits,
                               int32_t any_hit, void *stream) {
     if (!s || !rays || !hits || n < 0) { set_error("rt_trace: invalid argument"); return RT_INVALID_ARG; }
@@ -1320,32 +1343,26 @@ extern "C" rt_status rt_trace(const rt_scene *s, const rt_rays *rays, int64_t n,
         return RT_INVALID_ARG;
     }
     if (n > 0xFFFFFFFFll) { set_error("rt_trace: at most 2^32 - 1 rays per call"); return RT_INVALID_ARG; }
-    // Scratch of this call only (ray fetch counter, overflow flag), taken
-    // from the stream-ordered allocator: calls in flight on different streams
-    // never share a counter. The overflow flag comes back to the host, so the
-    // call waits for its kernel before it returns.
+    // Scratch of this stream (ray fetch counter, overflow flag) and a pinned
+    // word for the overflow flag: calls on one stream run one after another,
+    // so they can share it; calls in flight on different streams (or host
+    // threads) never share a counter. The overflow flag comes back to the
+    // host, so the call waits for its kernel before it returns.
     cudaStream_t st = (cudaStream_t)stream;
-    uint32_t *scratch = nullptr;
-    RT_CUDA_TRY(cudaMallocAsync(&scratch, 2 * sizeof(uint32_t), st));
-    struct Release {
-        uint32_t *p;
-        cudaStream_t st;
-        ~Release() { if (p) cudaFreeAsync(p, st); }
-    } release{scratch, st};
-    RT_CUDA_TRY(cudaMemsetAsync(scratch, 0, 2 * sizeof(uint32_t), st));
+    TraceScratch *ts = nullptr;
+    rt_status rs0 = trace_scratch(st, &ts);
+    if (rs0 != RT_OK) return rs0;
+    RT_CUDA_TRY(cudaMemsetAsync(ts->dev, 0, 2 * sizeof(uint32_t), st));
     const int gb = 128;
     using UserFn = void (*)(DevScene, rt_rays, uint32_t, rt_hits, uint32_t *);
     const UserFn fn = any_hit ? (s->dev.two_level ? (UserFn)k_trace_user<true, true> : (UserFn)k_trace_user<true, false>)
                               : (s->dev.two_level ? (UserFn)k_trace_user<false, true> : (UserFn)k_trace_user<false, false>);
     const int g = grid_persistent(fn, gb, 0);
-    fn<<<g, gb, 0, st>>>(s->dev, *rays, (uint32_t)n, *hits, scratch);
+    fn<<<g, gb, 0, st>>>(s->dev, *rays, (uint32_t)n, *hits, ts->dev);
     RT_CUDA_TRY(cudaGetLastError());
-    uint32_t overflow = 0;
-    RT_CUDA_TRY(cudaMemcpyAsync(&overflow, scratch + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    release.p = nullptr;
-    RT_CUDA_TRY(cudaFreeAsync(scratch, st));
+    RT_CUDA_TRY(cudaMemcpyAsync(ts->host, ts->dev + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     RT_CUDA_TRY(cudaStreamSynchronize(st));
-    if (overflow) {
+    if (*ts->host) {
         set_error("rt_trace: BVH traversal stack overflow (hits of the affected rays are incomplete)");
         return RT_STACK_OVERFLOW;
     }
@@ -1733,7 +1750,12 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         rc->dims_n = ndims;
     }
     if (!rc->host_ctrl) RT_CUDA_TRY(cudaMallocHost(&rc->host_ctrl, sizeof(Ctrl)));
-    if (regen) return render_regen(s, cam, spp, max_depth, film, o, st, rc, cap);
+    // a request that fits one pool load has nothing to regenerate: unless the
+    // call can be stopped (or its state is compressed, which only the
+    // regeneration path lays out) it runs as one load of the plain schedule,
+    // without staging its radiance per task
+    const bool one_load = request <= cap && !stoppable && !o.state_compression;
+    if (regen && !one_load) return render_regen(s, cam, spp, max_depth, film, o, st, rc, cap);
     RenderParams P;
     P.sc = s->dev;
     P.cam = make_camera(*cam);
