@@ -535,33 +535,40 @@ def batched(spp_divisor=16):
     ev1.record()
     ev1.synchronize()
     ms = ev0.elapsed_time(ev1)
-    # the same batch with a guiding network on every 8th job (each trained
-    # from scratch during the call, rendered through the guided path)
-    for f in films:
-        f.clear()
-    guides = [rt.Guide(s, seed=7 + k) if k % 8 == 0 else None for k, (s, _, _, _, _) in enumerate(jobs)]
-    gjobs = [j + (g,) for j, g in zip(jobs, guides)]
-    go = rt.make_opts(tail_threshold=o.tail_threshold, trace_kernel=o.trace_kernel, block_size=o.block_size)
-    gst = rt.rt_stats()
-    go.stats = C_pointer(gst)
-    torch.cuda.synchronize()
-    ev0.record()
-    rt.rt_render_batch(gjobs, go)
-    ev1.record()
-    ev1.synchronize()
-    gms = ev0.elapsed_time(ev1)
-    for g in guides:
-        if g is not None:
-            g.close()
+    # the same batch with a guiding network on every job (each trained from
+    # scratch during the call): one shared wavefront over the jobs' tasks
+    # interleaved image by image, one network launch per job and bounce step,
+    # training after every set of 2^21 paths (every 4th set after 8 warm-up
+    # steps)
+    with_guides = {}
+    for every in (8, 1):
+        for f in films:
+            f.clear()
+        guides = [rt.Guide(s, seed=7 + k, warm_steps=8, train_every=4) if k % every == 0 else None
+                  for k, (s, _, _, _, _) in enumerate(jobs)]
+        gjobs = [j + (g,) for j, g in zip(jobs, guides)]
+        go = rt.make_opts(tail_threshold=o.tail_threshold, trace_kernel=o.trace_kernel, block_size=o.block_size)
+        gst = rt.rt_stats()
+        go.stats = C_pointer(gst)
+        torch.cuda.synchronize()
+        ev0.record()
+        rt.rt_render_batch(gjobs, go)
+        ev1.record()
+        ev1.synchronize()
+        gms = ev0.elapsed_time(ev1)
+        for g in guides:
+            if g is not None:
+                g.close()
+        n_g = sum(g is not None for g in guides)
+        with_guides[f"{n_g}_of_64"] = {"guided_jobs": n_g, "ms": gms, "Mpaths_per_s": gst.paths / gms / 1e3,
+                                       "sets": gst.waves, "kernel_launches": gst.kernel_launches}
     return {"workload": f"64 seeded scenes ({sum(sd.num_triangles for sd, _, _, _ in specs)} triangles in all), "
                         f"spp / {spp_divisor}, one batched wavefront replayed as a CUDA graph",
             "paths": st.paths, "Mpaths_per_s": st.paths / ms / 1e3,
             "Mrays_per_s": (st.extension_rays + st.shadow_rays) / ms / 1e3, "ms": ms,
             "graph_replays": st.waves, "autotuned_pool": o.max_paths_in_flight, "autotuned_block": o.block_size,
             "scene_setup_s": setup_s,
-            "with_guides": {"guided_jobs": sum(g is not None for g in guides), "ms": gms,
-                            "Mpaths_per_s": gst.paths / gms / 1e3,
-                            "note": "guided jobs rendered after the shared wavefront, each with its own network"}}
+            "with_guides": with_guides}
 
 
 def traversal_only(sd, cam, scene, n=1 << 22, reps=5):

@@ -123,6 +123,7 @@ struct ArrayFeatures {
     const float *feat;
     uint32_t n;
     __device__ uint32_t count() const { return n; }
+    __device__ uint32_t out_row(uint32_t row) const { return row; }
     __device__ void operator()(uint32_t row, float f[7]) const {
 #pragma unroll
         for (int k = 0; k < 7; ++k) f[k] = feat[7 * (size_t)row + k];

@@ -89,8 +89,10 @@ __device__ __forceinline__ void mlp_issue(uint32_t taddr, uint32_t a0, uint32_t 
     umma::mma_commit(bar);
 }
 
-// Features: `void operator()(uint32_t row, float f[7]) const` (device) and
-// `uint32_t count() const` (rows to infer, read once per launch).
+// Features: `void operator()(uint32_t row, float f[7]) const` (device),
+// `uint32_t count() const` (rows to infer, read once per launch) and, for
+// the inference kernel, `uint32_t out_row(uint32_t row) const` (the output
+// row of that input row).
 template <bool kTrain, class Features>
 __device__ void mlp_tiles(const MlpWeights &w, const Features &feat, float *raw, uint32_t *err, const MlpTrain &tr) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -404,7 +406,9 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, Out *
         }
         if (!ok) break;
         umma::fence_after_sync();
-        // outputs 0..39
+        // outputs 0..39, to the row the features name (the row itself, or
+        // the path slot it came from)
+        const size_t orow = row < n ? (size_t)feat.out_row(row) : 0;
 #pragma unroll 1
         for (uint32_t c0 = 0; c0 < (uint32_t)kGuideOutPad; c0 += 16) {
             float v[16];
@@ -412,12 +416,12 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, Out *
             if (row < n) {
                 const int nv = c0 + 16 <= (uint32_t)kGuideOut ? 4 : 2;   // groups of four columns
                 if constexpr (sizeof(Out) == 4) {
-                    float4 *dst = (float4 *)(out + (size_t)row * kGuideOut + c0);
+                    float4 *dst = (float4 *)(out + orow * kGuideOut + c0);
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
                         if (e < nv) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
                 } else {
-                    uint2 *dst = (uint2 *)(out + (size_t)row * kGuideOut + c0);
+                    uint2 *dst = (uint2 *)(out + orow * kGuideOut + c0);
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
                         if (e < nv)

@@ -967,6 +967,7 @@ struct PathFeatures {
     Pool pool;
     float3 lo, hi;
     __device__ uint32_t count() const { return pool.ctrl->n_ext; }
+    __device__ uint32_t out_row(uint32_t row) const { return row; }
     __device__ void operator()(uint32_t i, float f[7]) const {
         const uint32_t q = pool.q[pool.ctrl->cur][i];
         PathState s = load_state(pool, q);
@@ -2510,9 +2511,250 @@ __global__ void k_batch_film(const BatchJob *jobs, uint32_t njobs, BatchCtl *bc,
 // Advance to the next iteration set (after the film kernel has finished).
 __global__ void k_batch_advance(BatchCtl *bc) { bc->t0 += bc->n; }
 
+// ---------------------------------------------------------------------------
+// Batched rendering with guiding networks inside the shared wavefront. The
+// task order interleaves the jobs: block b is chunk c of job j (tasks
+// [c WH_j, (c + 1) WH_j) of the job, one image's worth), blocks ordered by
+// chunk, then job, so that every iteration set holds tasks of many jobs and
+// each guided job collects training samples in every set. Each bounce step
+// sorts the extension queue by guided job (counting sort) and runs the fused
+// network kernel once per guided job over its range, writing the outputs of
+// each path at its slot; shading then takes its job's mixture probability
+// (zero until the job's network has trained). Training records come from
+// every rec_stride-th slot and are routed to their job's batch after the set.
+struct BatchBlock {
+    uint64_t off;     // first global task of the block
+    uint32_t job;
+    uint32_t chunk;   // the block holds the job's local tasks [chunk WH, chunk WH + len)
+};
+
+struct BatchGuide {
+    float3 lo, hi;        // the guide's feature bounds (its scene box)
+    float *tr_feat, *tr_wi, *tr_w;   // the job's training batch
+    uint32_t batch;       // its capacity
+    uint32_t guided;      // 0: the job has no network
+};
+
+RT_D uint32_t find_block(const BatchBlock *blocks, uint32_t nblocks, uint64_t t) {
+    uint32_t lo = 0, hi = nblocks;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (blocks[mid].off <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// job and job-local task (from the film's first task of the call) of global task t
+RT_D uint32_t batch_task(const BatchJob *jobs, const BatchBlock *blocks, uint32_t nblocks, uint64_t t,
+                         uint64_t &local) {
+    const BatchBlock &B = blocks[find_block(blocks, nblocks, t)];
+    local = jobs[B.job].film_task0 + (uint64_t)B.chunk * jobs[B.job].WH + (t - B.off);
+    return B.job;
+}
+
+__global__ void k_batchg_raygen(const BatchJob *jobs, const BatchBlock *blocks, uint32_t nblocks, BatchCtl *bc,
+                                Pool pool, uint32_t *job_of) {
+    const uint64_t t0 = bc->t0;
+    const uint32_t n = (uint32_t)min((uint64_t)bc->cap, bc->total - min(bc->total, t0));
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        uint64_t local;
+        const uint32_t j = batch_task(jobs, blocks, nblocks, t0 + q, local);
+        const BatchJob &J = jobs[j];
+        PathState s;
+        raygen(J.P, (uint32_t)(local % J.WH), (uint32_t)(local / J.WH), s);
+        store_state(pool, q, s);
+        pool.q[0][q] = q;
+        pool.nrec[q] = 0;
+        job_of[q] = j;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Ctrl *c = pool.ctrl;
+        bc->n = n;
+        c->n_ext = n;
+        c->n_next = 0;
+        c->n_shadow = 0;
+        c->cur = 0;
+        c->fetch_ext = c->fetch_shadow = c->fetch_shade = 0;
+        c->tail = 0;
+    }
+}
+
+// sort key of a queue entry: its job when the job has a network, else njobs
+struct GuidedJobKey {
+    const uint32_t *job_of;
+    const BatchGuide *guides;
+    uint32_t njobs;
+    RT_D uint32_t operator()(const Pool &, uint32_t q) const {
+        const uint32_t j = job_of[q];
+        return guides[j].guided ? j : njobs;
+    }
+};
+
+__global__ void k_copy_u32(const uint32_t *src, uint32_t *dst, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+// network inputs of job j's paths: range [starts[j], ends[j]) of the sorted
+// queue; no rows while the job's mixture probability is zero
+struct JobPathFeatures {
+    const BatchJob *jobs;
+    const BatchGuide *guides;
+    Pool pool;
+    const uint32_t *sorted, *starts, *ends;
+    const float *alpha;
+    uint32_t j;
+    __device__ uint32_t count() const { return alpha[j] > 0.f ? ends[j] - starts[j] : 0u; }
+    __device__ uint32_t out_row(uint32_t row) const { return sorted[starts[j] + row]; }
+    __device__ void operator()(uint32_t row, float f[7]) const {
+        const uint32_t q = sorted[starts[j] + row];
+        const RenderParams &P = jobs[j].P;
+        PathState s = load_state(pool, q);
+        const float4 hv = pool.hit[q];
+        Hit h;
+        h.prim = __float_as_uint(hv.x); h.inst = pool.hit_inst[q];
+        h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
+        if (h.prim != RT_MISS && s.depth <= P.max_depth) {
+            Vertex vx;
+            setup_vertex(P.sc, s, h, vx);
+            guide_features(vx.x, vx.wo, vx.ns, guides[j].lo, guides[j].hi, f);
+        }
+    }
+};
+
+__global__ void __launch_bounds__(512, 1) k_guide_mlp_job(MlpWeights w, JobPathFeatures pf, __nv_bfloat16 *raw,
+                                                          uint32_t *err) {
+    mlp_infer_tiles(w, pf, raw, err);
+}
+
+// shading of the shared queue: a path of a guided job samples the mixture of
+// its network's outputs (at its slot) with its job's probability and, on a
+// recording slot, keeps the training record of each continuing vertex
+__global__ void __launch_bounds__(128, 6) k_batchg_shade(const BatchJob *jobs, const BatchGuide *guides,
+                                                         const float *alpha, Pool pool, const uint32_t *job_of,
+                                                         const __nv_bfloat16 *raw, float4 *rec, uint32_t rec_stride,
+                                                         uint32_t rec_slots) {
+    Ctrl *c = pool.ctrl;
+    const uint32_t n = c->n_ext;
+    const uint32_t cur = c->cur;
+    const uint32_t *queue = pool.q[cur];
+    uint32_t *next = pool.q[cur ^ 1u];
+    for (;;) {
+        uint32_t base = warp_fetch32(&c->fetch_shade);
+        if (base >= n) break;
+        uint32_t i = base + lane_id();
+        bool valid = i < n;
+        uint32_t q = 0;
+        int r = 0;
+        if (valid) {
+            q = queue[i];
+            const uint32_t j = job_of[q];
+            const RenderParams &P = jobs[j].P;
+            const BatchGuide &G = guides[j];
+            PathState s = load_state(pool, q);
+            const bool recording = G.guided && recording_path(q, rec_stride, rec_slots);
+            const uint32_t slot = q / rec_stride;
+            uint32_t nr = recording ? pool.nrec[q] : 0u;
+            if (nr & kRecPending) {
+                nr &= ~kRecPending;
+                float4 *R = rec + ((size_t)slot * kGuideMaxRec + (nr - 1)) * 4;
+                R[3] = make_float4(R[3].x, s.L.x, s.L.y, s.L.z);
+                pool.nrec[q] = nr;
+            }
+            float4 hv = pool.hit[q];
+            Hit h;
+            h.prim = __float_as_uint(hv.x); h.inst = pool.hit_inst[q]; h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
+            ShadowRay sh;
+            GuideRecord gr;
+            const uint32_t v = s.depth;
+            const bool want = recording && v <= kGuideMaxRec;
+            const float a = G.guided ? alpha[j] : 0.f;
+            r = shade(P, s, h, sh, a > 0.f ? raw + (size_t)kGuideOut * q : nullptr, a, want ? &gr : nullptr, G.lo,
+                      G.hi);
+            pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
+            if (r & 1) {
+                pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
+                st_dir(pool, q, s.d, s.prev_pdf);
+                st_beta(pool, q, s.beta, s.depth);
+                if (want) {
+                    float4 *R = rec + ((size_t)slot * kGuideMaxRec + (v - 1)) * 4;
+                    R[0] = make_float4(gr.feat[0], gr.feat[1], gr.feat[2], gr.feat[3]);
+                    R[1] = make_float4(gr.feat[4], gr.feat[5], gr.feat[6], gr.wi.x);
+                    R[2] = make_float4(gr.wi.y, gr.wi.z, gr.beta.x, gr.beta.y);
+                    R[3] = make_float4(gr.beta.z, 0.f, 0.f, 0.f);
+                    pool.nrec[q] = v | kRecPending;
+                }
+            }
+            if (r & 2) {
+                pool.sh_o[q] = make_float4(sh.o.x, sh.o.y, sh.o.z, sh.tmax);
+                st_shd(pool, q, sh.d);
+                st_shc(pool, q, sh.contrib);
+            }
+        }
+        warp_append(next, &c->n_next, valid && (r & 1), q);
+        warp_append(pool.qs, &c->n_shadow, valid && (r & 2), q);
+    }
+}
+
+__global__ void k_batchg_film(const BatchJob *jobs, const BatchBlock *blocks, uint32_t nblocks, BatchCtl *bc, Pool pool,
+                              const uint32_t *job_of) {
+    const uint32_t n = bc->n;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        uint64_t local;
+        const uint32_t j = batch_task(jobs, blocks, nblocks, bc->t0 + q, local);
+        const BatchJob &J = jobs[j];
+        const uint32_t px = (uint32_t)(local % J.WH);
+        const float4 L = pool.L[q];
+        const double a = L.x, b = L.y, cc = L.z;
+        atomicAdd(&J.sum[3 * (size_t)px], a);
+        atomicAdd(&J.sum[3 * (size_t)px + 1], b);
+        atomicAdd(&J.sum[3 * (size_t)px + 2], cc);
+        atomicAdd(&J.sum2[3 * (size_t)px], a * a);
+        atomicAdd(&J.sum2[3 * (size_t)px + 1], b * b);
+        atomicAdd(&J.sum2[3 * (size_t)px + 2], cc * cc);
+        atomicAdd(&J.count[px], 1u);
+    }
+}
+
+// training samples of the set's recording slots, routed to their job's batch
+// (the sampled f cos Li / p of each finished record, as k_guide_collect)
+__global__ void k_batchg_collect(const BatchGuide *guides, BatchCtl *bc, Pool pool, const uint32_t *job_of,
+                                 const float4 *rec, uint32_t rec_stride, uint32_t rec_slots, uint32_t *ntrain) {
+    const uint32_t n = bc->n;
+    const uint32_t slots = min(rec_slots, (n + rec_stride - 1) / rec_stride);
+    for (uint32_t k0 = blockIdx.x * blockDim.x + threadIdx.x; k0 < slots; k0 += gridDim.x * blockDim.x) {
+        const uint32_t q = k0 * rec_stride;
+        const uint32_t j = job_of[q];
+        const BatchGuide &G = guides[j];
+        if (!G.guided) continue;
+        const uint32_t nr = pool.nrec[q];
+        const uint32_t complete = (nr & kRecPending) ? (nr & ~kRecPending) - 1 : nr;
+        const float4 L = pool.L[q];
+        for (uint32_t k = 0; k < complete; ++k) {
+            const float4 *R = rec + ((size_t)k0 * kGuideMaxRec + k) * 4;
+            const float4 r0 = R[0], r1 = R[1], r2 = R[2], r3 = R[3];
+            const float bx = r2.z, by = r2.w, bz = r3.x;
+            const float ax = bx > 0.f ? fmaxf(L.x - r3.y, 0.f) / bx : 0.f;
+            const float ay = by > 0.f ? fmaxf(L.y - r3.z, 0.f) / by : 0.f;
+            const float az = bz > 0.f ? fmaxf(L.z - r3.w, 0.f) / bz : 0.f;
+            const float w = lum(v3(ax, ay, az));
+            if (!(w > 0.f) || !isfinite(w)) continue;
+            const uint32_t idx = atomicAdd(&ntrain[j], 1u);
+            if (idx >= G.batch) continue;
+            const float f[7] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z};
+            for (int e = 0; e < 7; ++e) G.tr_feat[7 * (size_t)idx + e] = f[e];
+            G.tr_wi[3 * (size_t)idx] = r1.w;
+            G.tr_wi[3 * (size_t)idx + 1] = r2.x;
+            G.tr_wi[3 * (size_t)idx + 2] = r2.y;
+            G.tr_w[idx] = w;
+        }
+    }
+}
+
 }  // namespace rtg
 
 static rt_status render_batch_shared(const rt_render_job *jobs, int32_t njobs, const rt_render_opts *opts_in,
+                                     void *stream);
+static rt_status render_batch_guided(const rt_render_job *jobs, int32_t njobs, const rt_render_opts *opts_in,
                                      void *stream);
 
 extern "C" rt_status rt_render_batch(const rt_render_job *jobs, int32_t njobs, const rt_render_opts *opts_in,
@@ -2522,35 +2764,9 @@ extern "C" rt_status rt_render_batch(const rt_render_job *jobs, int32_t njobs, c
         set_error("rt_render_batch: guiding networks go with the jobs (rt_render_job.guide)");
         return RT_NOT_SUPPORTED;
     }
-    std::vector<rt_render_job> shared, guided;
-    for (int32_t j = 0; j < njobs; ++j) (jobs[j].guide ? guided : shared).push_back(jobs[j]);
-    rt_status rs = RT_OK;
-    if (!shared.empty()) rs = render_batch_shared(shared.data(), (int32_t)shared.size(), opts_in, stream);
-    if (rs != RT_OK) return rs;
-    // guided jobs: one guided render each (their networks differ)
-    rt_render_opts o{};
-    if (opts_in) o = *opts_in;
-    rt_stats total{};
-    rt_stats *user_stats = o.stats;
-    if (user_stats && !shared.empty()) total = *user_stats;
-    for (const rt_render_job &J : guided) {
-        rt_render_opts oj = o;
-        rt_stats sj{};
-        oj.guide = J.guide;
-        oj.stats = user_stats ? &sj : nullptr;
-        rs = rt_render(J.scene, &J.camera, J.spp, J.max_depth, J.film, &oj, stream);
-        if (user_stats) {
-            total.paths += sj.paths;
-            total.extension_rays += sj.extension_rays;
-            total.shadow_rays += sj.shadow_rays;
-            total.waves += sj.waves;
-            total.wavefront_steps += sj.wavefront_steps;
-            total.kernel_launches += sj.kernel_launches;
-        }
-        if (rs != RT_OK) break;
-    }
-    if (user_stats && !guided.empty()) *user_stats = total;
-    return rs;
+    for (int32_t j = 0; j < njobs; ++j)
+        if (jobs[j].guide) return render_batch_guided(jobs, njobs, opts_in, stream);
+    return render_batch_shared(jobs, njobs, opts_in, stream);
 }
 
 static rt_status render_batch_shared(const rt_render_job *jobs, int32_t njobs, const rt_render_opts *opts_in,
@@ -2685,6 +2901,264 @@ static rt_status render_batch_shared(const rt_render_job *jobs, int32_t njobs, c
         uint64_t dj = done_tasks > B.off ? std::min<uint64_t>(B.ntask, done_tasks - B.off) : 0;
         jobs[j].film->next_task += dj;
     }
+    stats.paths = done_tasks;
+    stats.waves = (uint32_t)done_sets;
+    stats.wavefront_steps = (uint32_t)(done_sets * (maxd + 1));
+    stats.extension_rays = hctl.ext_rays;
+    stats.shadow_rays = hctl.shadow_rays;
+    if (o.stats) *o.stats = stats;
+    return result;
+}
+
+// All jobs of a batch in which some carry a guiding network: one shared
+// wavefront over interleaved tasks (see BatchBlock), the set captured once
+// as a CUDA graph with one network launch per guided job and bounce step;
+// between replays every guided job whose network is due trains on the
+// samples its paths left in the set.
+static rt_status render_batch_guided(const rt_render_job *jobs, int32_t njobs, const rt_render_opts *opts_in,
+                                     void *stream) {
+    rt_render_opts o{};
+    if (opts_in) o = *opts_in;
+    if (!valid_block(o.block_size)) { set_error("rt_render_batch: block_size must be 0 or a multiple of 32 up to 128"); return RT_INVALID_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<BatchJob> hj((size_t)njobs);
+    std::vector<BatchGuide> hg((size_t)njobs);
+    uint32_t maxd = 1;
+    int ndims_max = 0;
+    for (int32_t j = 0; j < njobs; ++j) {
+        const rt_render_job &J = jobs[j];
+        if (!J.scene || !J.film || J.scene->host_only || J.camera.width != J.film->W || J.camera.height != J.film->H ||
+            J.max_depth < 1 || J.max_depth > (uint32_t)kMaxDepth) {
+            set_error("rt_render_batch: invalid job " + std::to_string(j));
+            return RT_INVALID_ARG;
+        }
+        maxd = std::max(maxd, J.max_depth);
+        ndims_max = std::max(ndims_max, 2 + 7 * (int)(J.max_depth + 1));
+    }
+    struct Scratch {
+        std::vector<void *> ptrs;
+        ~Scratch() { for (void *p : ptrs) cudaFree(p); }
+    } scratch;
+    auto dalloc = [&](void **p, size_t bytes) -> rt_status {
+        if (cudaMalloc(p, bytes) != cudaSuccess) { set_error("rt_render_batch: out of device memory"); return RT_OOM; }
+        scratch.ptrs.push_back(*p);
+        return RT_OK;
+    };
+    rt_status rs;
+    std::vector<HaltonDim> dims = make_dims(o.seed, ndims_max);
+    HaltonDim *ddims = nullptr;
+    if ((rs = dalloc((void **)&ddims, dims.size() * sizeof(HaltonDim))) != RT_OK) return rs;
+    RT_CUDA_TRY(cudaMemcpyAsync(ddims, dims.data(), dims.size() * sizeof(HaltonDim), cudaMemcpyHostToDevice, st));
+    // jobs, their chunks, and the interleaved block table
+    uint64_t total = 0;
+    uint32_t max_chunks = 0;
+    std::vector<uint32_t> nchunks((size_t)njobs);
+    for (int32_t j = 0; j < njobs; ++j) {
+        const rt_render_job &J = jobs[j];
+        BatchJob &B = hj[(size_t)j];
+        B.P.sc = J.scene->dev;
+        B.P.cam = make_camera(J.camera);
+        B.P.en = make_enum(J.camera.width, J.camera.height);
+        B.P.dims = ddims;
+        B.P.max_depth = J.max_depth;
+        B.P.sigma = o.filter_sigma == 0.f ? 0.5f : o.filter_sigma;
+        B.P.mis_mode = o.mis_mode;
+        B.P.rr = o.rr_enable;
+        B.sum = J.film->sum;
+        B.sum2 = J.film->sum2;
+        B.count = J.film->count;
+        B.WH = J.camera.width * J.camera.height;
+        B.ntask = (J.film->next_task / B.WH + (uint64_t)J.spp) * B.WH - J.film->next_task;
+        B.film_task0 = J.film->next_task;
+        B.off = 0;
+        nchunks[(size_t)j] = (uint32_t)((B.ntask + B.WH - 1) / B.WH);
+        max_chunks = std::max(max_chunks, nchunks[(size_t)j]);
+        total += B.ntask;
+    }
+    if (total == 0) return RT_OK;
+    std::vector<BatchBlock> blocks;
+    for (uint32_t c = 0; c < max_chunks; ++c)
+        for (int32_t j = 0; j < njobs; ++j) {
+            if (c >= nchunks[(size_t)j]) continue;
+            BatchBlock b;
+            b.off = blocks.empty() ? 0 : blocks.back().off +
+                                          std::min<uint64_t>(hj[blocks.back().job].WH,
+                                                             hj[blocks.back().job].ntask -
+                                                                 (uint64_t)blocks.back().chunk * hj[blocks.back().job].WH);
+            b.job = (uint32_t)j;
+            b.chunk = c;
+            blocks.push_back(b);
+        }
+    // set size: the user's pool, else 2^21 paths (training follows every set)
+    const uint32_t cap = std::max<uint32_t>(
+        32u, (uint32_t)std::min<uint64_t>(total, o.max_paths_in_flight ? o.max_paths_in_flight : (1u << 21)));
+    // guides: bounds, training batches, mixture probabilities
+    uint32_t nguided = 0;
+    std::vector<float> alpha_h((size_t)njobs, 0.f);
+    for (int32_t j = 0; j < njobs; ++j) {
+        BatchGuide &G = hg[(size_t)j];
+        G = BatchGuide{};
+        rt_guide *gd = jobs[j].guide;
+        if (!gd) continue;
+        ++nguided;
+        G.guided = 1;
+        guide_bounds(gd, G.lo, G.hi);
+        G.batch = guide_batch(gd);
+        if ((rs = dalloc((void **)&G.tr_feat, (size_t)G.batch * 7 * 4)) != RT_OK ||
+            (rs = dalloc((void **)&G.tr_wi, (size_t)G.batch * 3 * 4)) != RT_OK ||
+            (rs = dalloc((void **)&G.tr_w, (size_t)G.batch * 4)) != RT_OK)
+            return rs;
+        alpha_h[(size_t)j] = guide_trained(gd) ? guide_alpha(gd) : 0.f;
+    }
+    // training records: every rec_stride-th slot of the set, at most 2^18
+    const uint32_t rec_slots = std::min<uint32_t>(cap, 1u << 18);
+    const uint32_t rec_stride = std::max<uint32_t>(1u, (cap + rec_slots - 1) / rec_slots);
+    BatchJob *djobs = nullptr;
+    BatchGuide *dguides = nullptr;
+    BatchBlock *dblocks = nullptr;
+    BatchCtl *dctl = nullptr;
+    float *dalpha = nullptr;
+    uint32_t *job_of = nullptr, *ntrain = nullptr, *hist = nullptr, *starts = nullptr, *sorted = nullptr;
+    float4 *rec = nullptr;
+    __nv_bfloat16 *raw = nullptr;
+    const uint32_t nkeys = (uint32_t)njobs + 1;
+    if ((rs = dalloc((void **)&djobs, hj.size() * sizeof(BatchJob))) != RT_OK ||
+        (rs = dalloc((void **)&dguides, hg.size() * sizeof(BatchGuide))) != RT_OK ||
+        (rs = dalloc((void **)&dblocks, blocks.size() * sizeof(BatchBlock))) != RT_OK ||
+        (rs = dalloc((void **)&dctl, sizeof(BatchCtl))) != RT_OK ||
+        (rs = dalloc((void **)&dalpha, sizeof(float) * (size_t)njobs)) != RT_OK ||
+        (rs = dalloc((void **)&job_of, sizeof(uint32_t) * (size_t)cap)) != RT_OK ||
+        (rs = dalloc((void **)&ntrain, sizeof(uint32_t) * (size_t)njobs)) != RT_OK ||
+        (rs = dalloc((void **)&hist, sizeof(uint32_t) * (size_t)nkeys)) != RT_OK ||
+        (rs = dalloc((void **)&starts, sizeof(uint32_t) * (size_t)nkeys)) != RT_OK ||
+        (rs = dalloc((void **)&sorted, sizeof(uint32_t) * (size_t)cap)) != RT_OK ||
+        (rs = dalloc((void **)&rec, sizeof(float4) * 4 * kGuideMaxRec * (size_t)rec_slots)) != RT_OK ||
+        (rs = dalloc((void **)&raw, sizeof(__nv_bfloat16) * kGuideOut * (size_t)cap)) != RT_OK)
+        return rs;
+    uint32_t *nrec = nullptr;
+    if ((rs = dalloc((void **)&nrec, sizeof(uint32_t) * (size_t)cap)) != RT_OK) return rs;
+    RT_CUDA_TRY(cudaMemcpyAsync(djobs, hj.data(), hj.size() * sizeof(BatchJob), cudaMemcpyHostToDevice, st));
+    RT_CUDA_TRY(cudaMemcpyAsync(dguides, hg.data(), hg.size() * sizeof(BatchGuide), cudaMemcpyHostToDevice, st));
+    RT_CUDA_TRY(cudaMemcpyAsync(dblocks, blocks.data(), blocks.size() * sizeof(BatchBlock), cudaMemcpyHostToDevice, st));
+    RT_CUDA_TRY(cudaMemcpyAsync(dalpha, alpha_h.data(), sizeof(float) * (size_t)njobs, cudaMemcpyHostToDevice, st));
+    BatchCtl hc{0ull, total, 0u, cap};
+    RT_CUDA_TRY(cudaMemcpyAsync(dctl, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
+    PoolAlloc pa;
+    if ((rs = ensure_pool(pa, cap)) != RT_OK) return rs;
+    Pool pool = pa.view;
+    pool.nrec = nrec;
+    RT_CUDA_TRY(cudaMemsetAsync(pool.ctrl, 0, sizeof(Ctrl), st));
+    if ((rs = mlp_kernel_attr((const void *)k_guide_mlp_job, kMlpInferSmem)) != RT_OK) return rs;
+    const int gb = o.block_size ? (int)o.block_size : 128;
+    const uint32_t nb = (uint32_t)blocks.size();
+    const int g_ray = grid_for(k_batchg_raygen, 256, cap);
+    const int g_trace = grid_persistent(k_batch_trace<false>, gb, 0);
+    const int g_shade = grid_persistent(k_batchg_shade, gb, 0);
+    const int g_film = grid_for(k_batchg_film, 256, cap);
+    const int g_hist = grid_for(k_sort_scatter<GuidedJobKey>, 256, cap);
+    const int g_coll = grid_for(k_batchg_collect, 256, rec_slots);
+    GuidedJobKey key{job_of, dguides, (uint32_t)njobs};
+    // capture one iteration set
+    cudaStream_t cs = nullptr;
+    RT_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { if (s) cudaStreamDestroy(s); }
+    } guard{cs};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    RT_CUDA_TRY(cudaStreamSynchronize(st));
+    RT_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaMemsetAsync(ntrain, 0, sizeof(uint32_t) * (size_t)njobs, cs);
+    k_batchg_raygen<<<g_ray, 256, 0, cs>>>(djobs, dblocks, nb, dctl, pool, job_of);
+    for (uint32_t v = 1; v <= maxd + 1; ++v) {
+        k_batch_trace<false><<<g_trace, gb, 0, cs>>>(djobs, pool, job_of);
+        if (v <= maxd) {
+            // the network of each guided job over its paths (not at the last
+            // vertex, which only adds emission)
+            cudaMemsetAsync(hist, 0, sizeof(uint32_t) * nkeys, cs);
+            k_sort_hist<GuidedJobKey><<<g_hist, 256, nkeys * sizeof(uint32_t), cs>>>(key, pool, nkeys, hist);
+            k_sort_scan<<<1, 1024, 0, cs>>>(pool, nkeys, hist);
+            k_copy_u32<<<1, 256, 0, cs>>>(hist, starts, nkeys);
+            k_sort_scatter<GuidedJobKey><<<g_hist, 256, 0, cs>>>(key, pool, hist, sorted);
+            for (int32_t j = 0; j < njobs; ++j) {
+                if (!jobs[j].guide) continue;
+                const JobPathFeatures pf{djobs, dguides, pool, sorted, starts, hist, dalpha, (uint32_t)j};
+                k_guide_mlp_job<<<sm_count(), kMlpThreads, kMlpInferSmem, cs>>>(guide_weights(jobs[j].guide), pf, raw,
+                                                                                guide_err(jobs[j].guide));
+            }
+        }
+        k_batchg_shade<<<g_shade, gb, 0, cs>>>(djobs, dguides, dalpha, pool, job_of, raw, rec, rec_stride, rec_slots);
+        k_batch_trace<true><<<g_trace, gb, 0, cs>>>(djobs, pool, job_of);
+        k_batch_step_end<<<1, 1, 0, cs>>>(pool);
+    }
+    k_batchg_film<<<g_film, 256, 0, cs>>>(djobs, dblocks, nb, dctl, pool, job_of);
+    k_batchg_collect<<<g_coll, 256, 0, cs>>>(dguides, dctl, pool, job_of, rec, rec_stride, rec_slots, ntrain);
+    k_batch_advance<<<1, 1, 0, cs>>>(dctl);
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (ce != cudaSuccess) return cuda_status(ce, "rt_render_batch: graph capture");
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) { cudaGraphDestroy(graph); return cuda_status(ce, "rt_render_batch: instantiate"); }
+    struct GraphGuard {
+        cudaGraph_t g;
+        cudaGraphExec_t e;
+        ~GraphGuard() { if (e) cudaGraphExecDestroy(e); if (g) cudaGraphDestroy(g); }
+    } gguard{graph, exec};
+    const uint64_t sets = (total + cap - 1) / cap;
+    // memset, raygen; per bounce step trace, shade, shadow, step end, and
+    // before each shade but the last the job sort (5) and the networks; film,
+    // collect, advance
+    const uint32_t launches_per_set = 2 + 4 * (maxd + 1) + maxd * (5 + nguided) + 3;
+    std::vector<uint32_t> ntrain_h((size_t)njobs);
+    rt_stats stats{};
+    rt_status result = RT_OK;
+    uint64_t done_sets = 0;
+    const auto t_start = std::chrono::steady_clock::now();
+    for (; done_sets < sets; ++done_sets) {
+        ce = cudaGraphLaunch(exec, st);
+        if (ce != cudaSuccess) { result = cuda_status(ce, "rt_render_batch: graph launch"); break; }
+        stats.kernel_launches += launches_per_set;
+        RT_CUDA_TRY(cudaMemcpyAsync(ntrain_h.data(), ntrain, sizeof(uint32_t) * (size_t)njobs, cudaMemcpyDeviceToHost, st));
+        RT_CUDA_TRY(cudaStreamSynchronize(st));
+        // training after the set, each due network on its own samples
+        bool alpha_changed = false;
+        for (int32_t j = 0; j < njobs; ++j) {
+            rt_guide *gd = jobs[j].guide;
+            if (!gd) continue;
+            if ((rs = guide_check(gd, st)) != RT_OK) return rs;
+            const uint32_t nt = std::min(ntrain_h[(size_t)j], hg[(size_t)j].batch);
+            if (nt >= 256 && guide_should_train(gd)) {
+                const BatchGuide &G = hg[(size_t)j];
+                if ((rs = guide_train_async(gd, G.tr_feat, G.tr_wi, G.tr_w, nt, st)) != RT_OK) return rs;
+                stats.kernel_launches += 40;
+                const float a = guide_alpha(gd);
+                if (alpha_h[(size_t)j] != a) { alpha_h[(size_t)j] = a; alpha_changed = true; }
+            }
+        }
+        if (alpha_changed)
+            RT_CUDA_TRY(cudaMemcpyAsync(dalpha, alpha_h.data(), sizeof(float) * (size_t)njobs, cudaMemcpyHostToDevice, st));
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        if (done_sets + 1 < sets && ((o.abort_flag && *o.abort_flag) || (o.time_budget_ms > 0 && ms >= o.time_budget_ms))) {
+            ++done_sets;
+            set_error("rt_render_batch: stopped by time budget or abort flag");
+            result = RT_TIMEOUT;
+            break;
+        }
+    }
+    Ctrl hctl{};
+    RT_CUDA_TRY(cudaMemcpyAsync(&hctl, pool.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    RT_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hctl.overflow && result == RT_OK) { set_error("BVH traversal stack overflow"); result = RT_STACK_OVERFLOW; }
+    // films advance by the tasks of theirs that were completed: the blocks
+    // wholly before the end of the completed sets, and part of the last one
+    const uint64_t done_tasks = std::min<uint64_t>(total, done_sets * (uint64_t)cap);
+    std::vector<uint64_t> done_j((size_t)njobs, 0);
+    for (const BatchBlock &b : blocks) {
+        if (b.off >= done_tasks) break;
+        const uint64_t len = std::min<uint64_t>(hj[b.job].WH, hj[b.job].ntask - (uint64_t)b.chunk * hj[b.job].WH);
+        done_j[b.job] += std::min<uint64_t>(len, done_tasks - b.off);
+    }
+    for (int32_t j = 0; j < njobs; ++j) jobs[j].film->next_task += done_j[(size_t)j];
     stats.paths = done_tasks;
     stats.waves = (uint32_t)done_sets;
     stats.wavefront_steps = (uint32_t)(done_sets * (maxd + 1));

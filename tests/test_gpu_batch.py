@@ -152,3 +152,35 @@ def test_block_size_changes_nothing_but_speed():
     for bad in (48, 256):
         with pytest.raises(rt.RtError):
             rt.rt_render(s, cam, 1, 4, rt.Film(cam.width, cam.height), rt.make_opts(block_size=bad))
+
+
+def test_sixty_four_guided_jobs_in_one_wavefront():
+    """64 jobs, each with its own guiding network, in one rt_render_batch
+    call: one shared wavefront over the jobs' interleaved tasks, every
+    network trained during the call on its own paths' samples; every job's
+    film converges to the FP64 oracle's reference (per pixel within 4
+    sigma, up to the Gaussian allowance)."""
+    import os
+    from paper_1705_01263_gb300 import rt
+    from helpers import allowed_4sigma
+    sd, cam = scenes.cornell_box()
+    scene = rt.Scene(sd)
+    guides = [rt.Guide(scene, seed=100 + k) for k in range(64)]
+    p0 = [g.get_params() for g in guides]
+    films = [rt.Film(cam.width, cam.height) for _ in guides]
+    spp = 128
+    stats = rt.rt_stats()
+    rt.rt_render_batch([(scene, cam, spp, 8, f, g) for f, g in zip(films, guides)], rt.make_opts(stats=stats))
+    torch.cuda.synchronize()
+    assert stats.paths == 64 * cam.width * cam.height * spp and stats.waves > 1
+    d = np.load(os.path.join(os.path.dirname(__file__), "golden", "cornell_64_depth8_ref.npz"))
+    mr, vr = d["mean"], d["var"]
+    trained = 0
+    for g, q0, f in zip(guides, p0, films):
+        trained += not np.array_equal(q0, g.get_params())
+        s, s2, c = f.download()
+        assert np.all(c == spp)
+        mg, vg = oracle.resolve(s, s2, c)
+        out = int((np.abs(mg - mr) > 4 * np.sqrt(vg + vr) + 1e-6).sum())
+        assert out <= allowed_4sigma(mg.size), out
+    assert trained == 64
