@@ -867,6 +867,8 @@ def main():
     ap.add_argument("--two-way-once", action="store_true", help="only the two-way comparison (for profiling)")
     ap.add_argument("--tw-spp", type=int, default=64, help="iterations per image of --two-way-once")
     ap.add_argument("--tw-ref-spp", type=int, default=4096, help="reference iterations of --two-way-once")
+    ap.add_argument("--tw-scene", default="all", choices=["all", "glossy", "spheres", "turntable"],
+                    help="scene of --two-way-once")
     ap.add_argument("--no-traversal", action="store_true", help="skip the traversal-only ray batches")
     ap.add_argument("--no-probes", action="store_true", help="skip the irradiance-probe workload")
     ap.add_argument("--mlp-once", action="store_true",
@@ -887,7 +889,8 @@ def main():
     ap.add_argument("--trace-kernel", type=int, default=0,
                     help="0 closest hit one ray per thread with warp fetch, shadow rays with lane refill; "
                          "1 persistent warps refilling lanes; 2 one ray per thread with a shared-memory stack; "
-                         "3 lane refill between node visits for both; 4 one ray per thread for both")
+                         "3 lane refill between node visits for both; 4 one ray per thread for both; "
+                         "5 as 0 for camera rays, as 3 for later bounces")
     ap.add_argument("--megakernel-only", action="store_true", help="A/B baseline: megakernel per iteration set")
     ap.add_argument("--sort-by-material", action="store_true", help="A/B: material-sorted shading queue")
     ap.add_argument("--sort-rays", action="store_true", help="A/B: reorder extension rays by octant and origin cell")
@@ -938,11 +941,14 @@ def main():
         print(json.dumps(guide_mlp(reps=3)), flush=True)
         return 0
     if args.two_way_once:
-        print(json.dumps(two_way_vs_plain(spp=args.tw_spp, ref_spp=args.tw_ref_spp, reps=1)), flush=True)
-        print(json.dumps(two_way_vs_plain(res=270, depth=8, spp=16, ref_spp=256, reps=1, scene_name="spheres")),
-              flush=True)
-        print(json.dumps(two_way_vs_plain(res=128, depth=4, spp=64, ref_spp=4096, reps=1, scene_name="turntable")),
-              flush=True)
+        if args.tw_scene in ("all", "glossy"):
+            print(json.dumps(two_way_vs_plain(spp=args.tw_spp, ref_spp=args.tw_ref_spp, reps=1)), flush=True)
+        if args.tw_scene in ("all", "spheres"):
+            print(json.dumps(two_way_vs_plain(res=270, depth=8, spp=16, ref_spp=256, reps=1, scene_name="spheres")),
+                  flush=True)
+        if args.tw_scene in ("all", "turntable"):
+            print(json.dumps(two_way_vs_plain(res=128, depth=4, spp=args.tw_spp, ref_spp=args.tw_ref_spp, reps=1,
+                                              scene_name="turntable")), flush=True)
         return 0
     if args.render_once:
         st = rt.rt_stats()
@@ -1121,7 +1127,8 @@ def main():
                        "trace_kernel": ["closest hit one ray per thread, shadow rays with lane refill",
                                         "persistent warps, lane refill",
                                         "one ray per thread, shared-memory stack",
-                                        "lane refill between node visits", "one ray per thread"][args.trace_kernel],
+                                        "lane refill between node visits", "one ray per thread",
+                                        "camera rays one per thread, later bounces with lane refill"][args.trace_kernel],
                        "ray_order": "octant + origin cell" if args.sort_rays else "compaction order",
                        "schedule": "megakernel only" if args.megakernel_only else "wavefront + megakernel tail",
                        "shading_queue": "material-sorted" if args.sort_by_material else "compaction order"},

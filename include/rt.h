@@ -169,8 +169,9 @@ typedef struct {
                               * rays with lane refill; 1: persistent warps refilling idle lanes, one node or
                               * triangle per step; 2: one ray per thread with the stack top in shared
                               * memory; 3: warps refill idle lanes between node visits (both ray kinds);
-                              * 4: one ray per thread for both. Two-level scenes always use 0's closest-hit
-                              * kernel for both. */
+                              * 4: one ray per thread for both; 5: as 0 for camera rays, as 3 for later
+                              * bounces (the regeneration scheduler runs 5 as 0). Two-level scenes always
+                              * use 0's closest-hit kernel for both. */
     int32_t sort_rays;       /* 1: reorder extension rays by direction octant and origin cell (A/B) */
     int32_t scheduler;       /* 0: regeneration (Sec. 3.1.3): a bounded pool whose ended paths are
                               * refilled with the next tasks; 1: iteration sets, each held whole in

@@ -1508,7 +1508,8 @@ static rt_status render_regen(const rt_scene *s, const rt_camera *cam, uint32_t 
 
     const int gb = o.block_size ? (int)o.block_size : 128;
     const bool prof = o.profile >= 1, count = o.profile >= 2;
-    const TraceKernels tk = trace_kernels(count, o.trace_kernel == 1 ? 0 : o.trace_kernel, s->dev.two_level, gb);
+    const TraceKernels tk =
+        trace_kernels(count, (o.trace_kernel == 1 || o.trace_kernel == 5) ? 0 : o.trace_kernel, s->dev.two_level, gb);
     const int g_shade = grid_persistent(k_shade<true>, gb, 0);
     const int g_regen = grid_for(k_regen, 256, cap);
     const int g_init = grid_for(k_regen_init, 256, cap);
@@ -1708,7 +1709,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     rt_render_opts o{};
     if (opts_in) o = *opts_in;
     if (spp == 0) return RT_OK;
-    if (o.trace_kernel < 0 || o.trace_kernel > 4) { set_error("rt_render: trace_kernel must be in [0, 4]"); return RT_INVALID_ARG; }
+    if (o.trace_kernel < 0 || o.trace_kernel > 5) { set_error("rt_render: trace_kernel must be in [0, 5]"); return RT_INVALID_ARG; }
     if (!valid_block(o.block_size)) { set_error("rt_render: block_size must be 0 or a multiple of 32 up to 128"); return RT_INVALID_ARG; }
     if (s->dev.two_level) o.trace_kernel = 0;   // the persistent variant is single-level only
     cudaStream_t st = (cudaStream_t)stream;
@@ -1884,7 +1885,10 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     const int g_shadow = grid_persistent(k_trace_shadow<false>, gb, smem);
     const int g_mega = grid_for(k_megakernel, gb, cap);
     const bool prof = o.profile >= 1, count = o.profile >= 2;
-    const TraceKernels tk = trace_kernels(count, o.trace_kernel, s->dev.two_level, gb);
+    // variant 5: camera rays one per thread (coherent), later bounces with
+    // lane refill (incoherent rays that end at very different times)
+    const TraceKernels tk = trace_kernels(count, o.trace_kernel == 5 ? 0 : o.trace_kernel, s->dev.two_level, gb);
+    const TraceKernels tk_late = o.trace_kernel == 5 && !s->dev.two_level ? trace_kernels(count, 3, false, gb) : tk;
     const uint32_t nmat = s->num_materials;
     const uint32_t nkeys_mat = nmat + 1, nkeys_ray = 8u * 512u;
     const int g_hist = grid_for(k_sort_scatter<RayKey>, 256, cap);
@@ -1952,7 +1956,8 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
                 }
                 e = mark(0);
                 if (o.trace_kernel != 1) {
-                    tk.ext<<<tk.grid_ext, gb, tk.smem, st>>>(s->dev, pool, rsorted);
+                    const TraceKernels &tv = v >= 2 ? tk_late : tk;
+                    tv.ext<<<tv.grid_ext, gb, tv.smem, st>>>(s->dev, pool, rsorted);
                 } else if (count) {
                     k_trace_ext<true><<<g_trace, gb, smem, st>>>(s->dev, pool);
                 } else {
@@ -3065,6 +3070,25 @@ static rt_status render_batch_guided(const rt_render_job *jobs, int32_t njobs, c
         cudaStream_t s;
         ~StreamGuard() { if (s) cudaStreamDestroy(s); }
     } guard{cs};
+    // side streams: parallel branches of the set graph (the networks of
+    // different jobs) and concurrent training steps between replays
+    constexpr int kSide = 8;
+    struct SideStreams {
+        cudaStream_t s[kSide] = {};
+        cudaEvent_t fork = nullptr, join[kSide] = {};
+        ~SideStreams() {
+            for (cudaStream_t x : s) if (x) cudaStreamDestroy(x);
+            for (cudaEvent_t e : join) if (e) cudaEventDestroy(e);
+            if (fork) cudaEventDestroy(fork);
+        }
+    } ss;
+    for (int b = 0; b < kSide; ++b) {
+        RT_CUDA_TRY(cudaStreamCreateWithFlags(&ss.s[b], cudaStreamNonBlocking));
+        RT_CUDA_TRY(cudaEventCreateWithFlags(&ss.join[b], cudaEventDisableTiming));
+    }
+    RT_CUDA_TRY(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
+    cudaStream_t *side = ss.s;
+    cudaEvent_t fork_ev = ss.fork, *join_ev = ss.join;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     RT_CUDA_TRY(cudaStreamSynchronize(st));
@@ -3081,11 +3105,19 @@ static rt_status render_batch_guided(const rt_render_job *jobs, int32_t njobs, c
             k_sort_scan<<<1, 1024, 0, cs>>>(pool, nkeys, hist);
             k_copy_u32<<<1, 256, 0, cs>>>(hist, starts, nkeys);
             k_sort_scatter<GuidedJobKey><<<g_hist, 256, 0, cs>>>(key, pool, hist, sorted);
+            // the jobs' networks in up to kSide parallel branches of the graph
+            RT_CUDA_TRY(cudaEventRecord(fork_ev, cs));
+            for (int b = 0; b < kSide; ++b) RT_CUDA_TRY(cudaStreamWaitEvent(side[b], fork_ev, 0));
+            int k = 0;
             for (int32_t j = 0; j < njobs; ++j) {
                 if (!jobs[j].guide) continue;
                 const JobPathFeatures pf{djobs, dguides, pool, sorted, starts, hist, dalpha, (uint32_t)j};
-                k_guide_mlp_job<<<sm_count(), kMlpThreads, kMlpInferSmem, cs>>>(guide_weights(jobs[j].guide), pf, raw,
-                                                                                guide_err(jobs[j].guide));
+                k_guide_mlp_job<<<sm_count(), kMlpThreads, kMlpInferSmem, side[k++ % kSide]>>>(
+                    guide_weights(jobs[j].guide), pf, raw, guide_err(jobs[j].guide));
+            }
+            for (int b = 0; b < kSide; ++b) {
+                RT_CUDA_TRY(cudaEventRecord(join_ev[b], side[b]));
+                RT_CUDA_TRY(cudaStreamWaitEvent(cs, join_ev[b], 0));
             }
         }
         k_batchg_shade<<<g_shade, gb, 0, cs>>>(djobs, dguides, dalpha, pool, job_of, raw, rec, rec_stride, rec_slots);
@@ -3120,8 +3152,12 @@ static rt_status render_batch_guided(const rt_render_job *jobs, int32_t njobs, c
         stats.kernel_launches += launches_per_set;
         RT_CUDA_TRY(cudaMemcpyAsync(ntrain_h.data(), ntrain, sizeof(uint32_t) * (size_t)njobs, cudaMemcpyDeviceToHost, st));
         RT_CUDA_TRY(cudaStreamSynchronize(st));
-        // training after the set, each due network on its own samples
+        // training after the set, each due network on its own samples; the
+        // networks are independent, so their steps run on the side streams
         bool alpha_changed = false;
+        RT_CUDA_TRY(cudaEventRecord(fork_ev, st));
+        for (int b = 0; b < kSide; ++b) RT_CUDA_TRY(cudaStreamWaitEvent(side[b], fork_ev, 0));
+        int k = 0;
         for (int32_t j = 0; j < njobs; ++j) {
             rt_guide *gd = jobs[j].guide;
             if (!gd) continue;
@@ -3129,11 +3165,15 @@ static rt_status render_batch_guided(const rt_render_job *jobs, int32_t njobs, c
             const uint32_t nt = std::min(ntrain_h[(size_t)j], hg[(size_t)j].batch);
             if (nt >= 256 && guide_should_train(gd)) {
                 const BatchGuide &G = hg[(size_t)j];
-                if ((rs = guide_train_async(gd, G.tr_feat, G.tr_wi, G.tr_w, nt, st)) != RT_OK) return rs;
+                if ((rs = guide_train_async(gd, G.tr_feat, G.tr_wi, G.tr_w, nt, side[k++ % kSide])) != RT_OK) return rs;
                 stats.kernel_launches += 40;
                 const float a = guide_alpha(gd);
                 if (alpha_h[(size_t)j] != a) { alpha_h[(size_t)j] = a; alpha_changed = true; }
             }
+        }
+        for (int b = 0; b < kSide; ++b) {
+            RT_CUDA_TRY(cudaEventRecord(join_ev[b], side[b]));
+            RT_CUDA_TRY(cudaStreamWaitEvent(st, join_ev[b], 0));
         }
         if (alpha_changed)
             RT_CUDA_TRY(cudaMemcpyAsync(dalpha, alpha_h.data(), sizeof(float) * (size_t)njobs, cudaMemcpyHostToDevice, st));

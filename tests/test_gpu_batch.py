@@ -165,10 +165,13 @@ def test_sixty_four_guided_jobs_in_one_wavefront():
     from helpers import allowed_4sigma
     sd, cam = scenes.cornell_box()
     scene = rt.Scene(sd)
-    guides = [rt.Guide(scene, seed=100 + k) for k in range(64)]
+    guides = [rt.Guide(scene, seed=100 + k, train_every=4) for k in range(64)]
     p0 = [g.get_params() for g in guides]
     films = [rt.Film(cam.width, cam.height) for _ in guides]
-    spp = 128
+    # 1024 spp, as the other guided parity tests: at a few hundred samples
+    # the per-pixel spread of this scene's QMC estimate (plain or guided)
+    # still leaves more than the Gaussian allowance of pixels beyond 4 sigma
+    spp = 1024
     stats = rt.rt_stats()
     rt.rt_render_batch([(scene, cam, spp, 8, f, g) for f, g in zip(films, guides)], rt.make_opts(stats=stats))
     torch.cuda.synchronize()
