@@ -283,7 +283,7 @@ def scheduler_sweep(scene, cam, spp, depth, pools=(1 << 22, 1 << 23, 1 << 24, 1 
     for name, kw in (("uncompressed", {}), ("compressed", {"state_compression": True})):
         r = timed(**kw)
         r["of_whole_request"] = r["Mpaths_per_s"] / whole
-        r["state_bytes_per_path"] = 132 if kw else 168
+        r["state_bytes_per_path"] = 128 if kw else 164
         img = film.resolve()[0].double()
         r["image_rel_l1_vs_uncompressed"] = float((img - ref).abs().sum() / ref.abs().sum())
         out[f"state_{name}"] = r
@@ -890,7 +890,8 @@ def main():
                     help="0 closest hit one ray per thread with warp fetch, shadow rays with lane refill; "
                          "1 persistent warps refilling lanes; 2 one ray per thread with a shared-memory stack; "
                          "3 lane refill between node visits for both; 4 one ray per thread for both; "
-                         "5 as 0 for camera rays, as 3 for later bounces")
+                         "5 as 0 for camera rays, as 3 for later bounces; 6 closest hit one ray per thread with "
+                         "postponed triangle tests, shadow rays as 0; 7 postponed triangle tests for both")
     ap.add_argument("--megakernel-only", action="store_true", help="A/B baseline: megakernel per iteration set")
     ap.add_argument("--sort-by-material", action="store_true", help="A/B: material-sorted shading queue")
     ap.add_argument("--sort-rays", action="store_true", help="A/B: reorder extension rays by octant and origin cell")
@@ -1128,7 +1129,10 @@ def main():
                                         "persistent warps, lane refill",
                                         "one ray per thread, shared-memory stack",
                                         "lane refill between node visits", "one ray per thread",
-                                        "camera rays one per thread, later bounces with lane refill"][args.trace_kernel],
+                                        "camera rays one per thread, later bounces with lane refill",
+                                        "closest hit one ray per thread with postponed triangle tests, "
+                                        "shadow rays with lane refill",
+                                        "one ray per thread with postponed triangle tests"][args.trace_kernel],
                        "ray_order": "octant + origin cell" if args.sort_rays else "compaction order",
                        "schedule": "megakernel only" if args.megakernel_only else "wavefront + megakernel tail",
                        "shading_queue": "material-sorted" if args.sort_by_material else "compaction order"},

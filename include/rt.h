@@ -170,8 +170,10 @@ typedef struct {
                               * triangle per step; 2: one ray per thread with the stack top in shared
                               * memory; 3: warps refill idle lanes between node visits (both ray kinds);
                               * 4: one ray per thread for both; 5: as 0 for camera rays, as 3 for later
-                              * bounces (the regeneration scheduler runs 5 as 0). Two-level scenes always
-                              * use 0's closest-hit kernel for both. */
+                              * bounces (the regeneration scheduler runs 5 as 0); 6: as 0 with the
+                              * closest-hit triangle tests postponed while few lanes want them; 7: both
+                              * kinds one ray per thread with postponed triangle tests. Two-level scenes
+                              * always use 0's closest-hit kernel for both. */
     int32_t sort_rays;       /* 1: reorder extension rays by direction octant and origin cell (A/B) */
     int32_t scheduler;       /* 0: regeneration (Sec. 3.1.3): a bounded pool whose ended paths are
                               * refilled with the next tasks; 1: iteration sets, each held whole in
@@ -182,7 +184,7 @@ typedef struct {
                               * the scene's bound and cosine directions (A/B) */
     int32_t state_compression; /* rt_render, scheduler 0 (A/B, Sec. 3.1.1): ray and shadow directions as
                               * 16:16 octahedral codes, throughput and shadow contributions as BF16, the
-                              * vertex number in 16 bits (132 instead of 168 bytes of state per path);
+                              * vertex number in 16 bits (128 instead of 164 bytes of state per path);
                               * RT_NOT_SUPPORTED with iteration sets, guiding or megakernel_only */
 } rt_render_opts;
 

@@ -102,14 +102,18 @@ __global__ void k_adam(float *p, const float *g, float *m, float *v, int64_t n, 
     }
 }
 
-// BF16 copies of layer l: W [out_pad][in] and W^T [in][out_pad].
-__global__ void k_pack_layer(const float *W32, int in, int out, int out_pad, __nv_bfloat16 *W, __nv_bfloat16 *WT) {
+// BF16 copies of layer l: W [out_pad][in], W^T [in][out_pad] and the layer's
+// part of the fused kernels' shared-memory image (canonical K-major layout
+// at byte offset mlp_image_base(l)).
+__global__ void k_pack_layer(const float *W32, int in, int out, int out_pad, __nv_bfloat16 *W, __nv_bfloat16 *WT,
+                             unsigned char *image, uint32_t image_base) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < out_pad * in; i += gridDim.x * blockDim.x) {
         int o = i / in, k = i % in;
         float v = o < out ? W32[(int64_t)o * in + k] : 0.f;
         __nv_bfloat16 b = __float2bfloat16(v);
         W[i] = b;
         if (WT) WT[(int64_t)k * out_pad + o] = b;
+        *(__nv_bfloat16 *)(image + image_base + umma::kmajor_offset((uint32_t)o, (uint32_t)k, (uint32_t)in)) = b;
     }
 }
 
@@ -130,7 +134,7 @@ struct ArrayFeatures {
     }
 };
 
-__global__ void __launch_bounds__(512, 1) k_guide_mlp(MlpWeights w, ArrayFeatures feat, float *raw, uint32_t *err) {
+__global__ void __launch_bounds__(kMiThreads, 1) k_guide_mlp(MlpWeights w, ArrayFeatures feat, float *raw, uint32_t *err) {
     mlp_infer_tiles(w, feat, raw, err);
 }
 
@@ -154,6 +158,7 @@ struct rt_guide {
     int64_t nparams = 0;
     float *W32 = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
     __nv_bfloat16 *Wb[5] = {nullptr}, *WTb[5] = {nullptr};
+    unsigned char *image = nullptr;   // the five layers in the fused kernels' shared-memory layout
     int64_t step = 0;
     uint64_t sets = 0;   // iteration sets rendered with this guide
     // scratch for a batch of up to cap rows
@@ -179,7 +184,8 @@ rt_status galloc(rt_guide *g, T **p, size_t count) {
 rt_status repack(rt_guide *g, cudaStream_t st) {
     for (int l = 0; l < 5; ++l) {
         k_pack_layer<<<grid1d((int64_t)kOutPad[l] * kIn[l]), 256, 0, st>>>(g->W32 + param_offset(l), kIn[l], kOut[l],
-                                                                            kOutPad[l], g->Wb[l], g->WTb[l]);
+                                                                            kOutPad[l], g->Wb[l], g->WTb[l], g->image,
+                                                                            mlp_image_base(l));
     }
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
@@ -311,6 +317,7 @@ rt_status guide_check(rt_guide *g, cudaStream_t st) { return check_err(g, st); }
 MlpWeights guide_weights(const rt_guide *g) {
     MlpWeights w;
     for (int l = 0; l < 5; ++l) w.W[l] = g->Wb[l];
+    w.image = g->image;
     return w;
 }
 uint32_t *guide_err(const rt_guide *g) { return g->err; }
@@ -332,9 +339,9 @@ rt_status mlp_kernel_attr(const void *kernel, uint32_t bytes) {
 rt_status guide_infer_async(rt_guide *g, const float *feat, int64_t n, float *out, cudaStream_t st) {
     rt_status s;
     if ((s = mlp_kernel_attr((const void *)k_guide_mlp, kMlpInferSmem)) != RT_OK) return s;
-    const int64_t per_cta = kMiGroups * kMlpTile;   // four groups, one tile each
+    const int64_t per_cta = kMiGroups * kMlpTile;   // one tile per group
     const int grid = (int)std::min<int64_t>((n + per_cta - 1) / per_cta, (int64_t)sm_count());
-    k_guide_mlp<<<grid, kMlpThreads, kMlpInferSmem, st>>>(guide_weights(g), ArrayFeatures{feat, (uint32_t)n}, out,
+    k_guide_mlp<<<grid, kMiThreads, kMlpInferSmem, st>>>(guide_weights(g), ArrayFeatures{feat, (uint32_t)n}, out,
                                                            g->err);
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
@@ -405,6 +412,7 @@ extern "C" rt_status rt_guide_create(const rt_scene *scene, const rt_guide_opts 
     for (int l = 0; l < 5; ++l)
         if ((s = galloc(g, &g->Wb[l], (size_t)kOutPad[l] * kIn[l])) || (s = galloc(g, &g->WTb[l], (size_t)kOutPad[l] * kIn[l])))
             return fail(s);
+    if ((s = galloc(g, &g->image, (size_t)kMlpX))) return fail(s);
     // He-style initialisation from SplitMix64 (seeded), uniform in +-sqrt(6 / fan_in)
     std::vector<float> w(g->nparams);
     uint64_t st = g->opts.seed ^ 0x6A09E667F3BCC908ull;

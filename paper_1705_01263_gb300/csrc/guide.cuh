@@ -28,11 +28,19 @@ constexpr float kKappaMin = 1e-2f, kKappaMax = 1e4f;
 // exponential, its neighbours by the ratio of consecutive bins,
 // g(c + 1) = g(c) r_c with r_c = exp(32 (s - (c + 1/2) / 32) - 1/2) and
 // r_{c+1} = r_c / e (two exponentials per eight bins instead of eight).
+RT_HD float oneblob_exp(float x) {
+#ifdef __CUDA_ARCH__
+    return __expf(x);   // the bins are rounded to BF16: the fast exponential's error is far below that
+#else
+    return expf(x);
+#endif
+}
+
 RT_HD void oneblob_chunk(float s, int c0, float *g8) {
     const float sig = 1.f / kGuideBins;
     const float d = s - ((float)c0 + 0.5f) / kGuideBins;
-    float g = expf(-d * d / (2.f * sig * sig));
-    float r = expf((float)kGuideBins * d - 0.5f);
+    float g = oneblob_exp(-d * d / (2.f * sig * sig));
+    float r = oneblob_exp((float)kGuideBins * d - 0.5f);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         g8[e] = g;

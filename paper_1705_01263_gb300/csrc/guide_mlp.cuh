@@ -1,8 +1,8 @@
 // Fused forward pass of the guiding network on the tensor cores. The
 // training forward (mlp_tiles<true>) works as follows; the inference kernel
-// (mlp_infer_tiles, below) keeps four tiles in flight instead of one. One
-// persistent CTA of 512 threads per SM keeps all five BF16 weight matrices (58 KB) in
-// shared memory and walks tiles of 128 rows, four threads per row (part p =
+// (mlp_infer_tiles, below) keeps five tiles in flight instead of one. One
+// persistent CTA of 512 threads per SM keeps all five BF16 weight matrices
+// (58 KB, copied in by one bulk copy of a prepared image) in shared memory and walks tiles of 128 rows, four threads per row (part p =
 // warp / 4 of row 32 (warp % 4) + lane), so that each SM sub-partition has
 // four warps to switch between. The CTA gathers the 7 features of four
 // tiles at once (one row per thread, so that the dependent loads behind a
@@ -26,6 +26,8 @@
 
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "guide.cuh"
 #include "umma.cuh"
 
@@ -33,6 +35,9 @@ namespace rtg {
 
 struct MlpWeights {
     const __nv_bfloat16 *W[5];   // [out_pad][in] row-major BF16 (layer 5 padded to 48 rows)
+    // the five matrices as the kernels hold them in shared memory (offsets
+    // kMlpW1 .. kMlpW5, canonical K-major layout): kMlpX bytes, 16-byte aligned
+    const void *image;
 };
 
 // Training forward pass: besides the network outputs, the kernel keeps what
@@ -65,14 +70,29 @@ constexpr uint32_t kMlpSmem = kMlpBar + 64;                              // 149,
 constexpr uint32_t kMlpOut = kMlpSmem;                                   // training: 128 x 48 FP32 outputs
 constexpr uint32_t kMlpSmemTrain = kMlpOut + kMlpTile * kGuideOutPad * 4; // 174,144 bytes
 
-// Row-major [rows][kdim] BF16 from global memory into the canonical layout.
-__device__ __forceinline__ void mlp_stage_rows(unsigned char *dst, const __nv_bfloat16 *src, int rows, int kdim) {
-    const int chunks = kdim / 8;
-    for (int c = threadIdx.x; c < rows * chunks; c += blockDim.x) {
-        const int r = c / chunks, g8 = c % chunks;
-        const uint4 v = *(const uint4 *)(src + (size_t)r * kdim + 8 * g8);
-        *(uint4 *)(dst + umma::kmajor_offset((uint32_t)r, (uint32_t)(8 * g8), (uint32_t)kdim)) = v;
+// Byte offset in the shared-memory weight image of element (o, k) of layer
+// l (row o of the [out_pad][in] matrix).
+__host__ __device__ constexpr uint32_t mlp_image_base(int l) {
+    return l == 0 ? kMlpW1 : (l == 1 ? kMlpW2 : (l == 2 ? kMlpW3 : (l == 3 ? kMlpW4 : kMlpW5)));
+}
+
+// The weight image into shared memory at offset 0 with one bulk copy (one
+// thread issues it; every thread then waits on `bar`, bounded). Returns
+// false, in every thread of the block, on a timeout. The barrier completes
+// its phase 0 here.
+__device__ __forceinline__ bool mlp_load_image(unsigned char *smem, const void *image, uint64_t *bar) {
+    if (threadIdx.x == 0) {
+        umma::mbar_init(bar, 1);
+        const uint32_t b = umma::smem_addr(bar);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(kMlpX) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                umma::smem_addr(smem)),
+            "l"(image), "r"(kMlpX), "r"(b)
+            : "memory");
     }
+    __syncthreads();
+    return __syncthreads_and(umma::mbar_wait(bar, 0u) ? 1 : 0) != 0;
 }
 
 // Issue one layer: D[128 x n] = A[128 x k] * B[n x k]^T, K in steps of 16.
@@ -106,11 +126,7 @@ __device__ void mlp_tiles(const MlpWeights &w, const Features &feat, float *raw,
     const uint32_t tiles = (n + kMlpTile - 1) / kMlpTile;
     const uint32_t groups = (tiles + kMlpGroup - 1) / kMlpGroup;
     if (blockIdx.x >= groups) return;
-    mlp_stage_rows(smem + kMlpW1, w.W[0], kGuideHid, kGuideIn);
-    mlp_stage_rows(smem + kMlpW2, w.W[1], kGuideHid, kGuideHid);
-    mlp_stage_rows(smem + kMlpW3, w.W[2], kGuideHid, kGuideHid);
-    mlp_stage_rows(smem + kMlpW4, w.W[3], kGuideHid, kGuideHid);
-    mlp_stage_rows(smem + kMlpW5, w.W[4], kGuideOutPad, kGuideHid);
+    const bool image_ok = mlp_load_image(smem, w.image, (uint64_t *)(smem + kMlpBar + 32));
     if (warp == 0) umma::tmem_alloc(s_taddr, 64);
     if (tid == 0) umma::mbar_init(bar, 1);
     umma::fence_before_sync();
@@ -120,7 +136,7 @@ __device__ void mlp_tiles(const MlpWeights &w, const Features &feat, float *raw,
     const uint32_t lane_addr = taddr + ((32u * quarter) << 16);
     const uint32_t sbase = umma::smem_addr(smem);
     uint32_t phase = 0;
-    bool ok = true;
+    bool ok = image_ok;
     // Bounded wait for the layer just issued; the outcome is made uniform
     // over the block, so that all threads leave (or stay) together.
     auto wait_layer = [&]() -> bool {
@@ -128,7 +144,7 @@ __device__ void mlp_tiles(const MlpWeights &w, const Features &feat, float *raw,
         phase ^= 1u;
         return __syncthreads_and(done ? 1 : 0) != 0;
     };
-    for (uint32_t gi = blockIdx.x; gi < groups; gi += gridDim.x) {
+    for (uint32_t gi = blockIdx.x; gi < groups && ok; gi += gridDim.x) {
       {
         // features of the group's 512 rows, one per thread
         const uint32_t grow = gi * kMlpGroup * kMlpTile + tid;
@@ -262,11 +278,12 @@ __device__ void mlp_tiles(const MlpWeights &w, const Features &feat, float *raw,
 }
 
 // ---------------------------------------------------------------- inference
-// Four tiles in flight: the 512 threads form four independent groups of 128
+// kMiGroups tiles in flight: the threads form independent groups of 128
 // (four warps), one thread per row (warp w of a group reaches tensor-memory
 // lanes 32 (w % 4) + 0..31, its rows), each group with its own 64
-// tensor-memory columns, mbarrier and named barrier (ids 1..4), sharing the
-// weights. A group's shared buffer is 128 x 112 BF16: layer 1 runs in two K
+// tensor-memory columns, mbarrier and named barrier (ids 1..kMiGroups),
+// sharing the weights. A group loads the next tile's features before it
+// works on the current one, so that their latency overlaps the products. A group's shared buffer is 128 x 112 BF16: layer 1 runs in two K
 // halves, the one-blob columns 0..111 then 112..223 encoded into the same
 // buffer (the second after the first product has completed, the products
 // accumulating in tensor memory), and the hidden activations (128 x 64) then
@@ -276,9 +293,14 @@ __device__ void mlp_tiles(const MlpWeights &w, const Features &feat, float *raw,
 constexpr uint32_t kMiHalfK = kGuideIn / 2;                                // 112
 constexpr uint32_t kMiBuf = kMlpTile * kMiHalfK * 2;                       // 28,672 bytes
 constexpr uint32_t kMiGroup0 = kMlpX;                                      // after the weights (59,392)
-constexpr uint32_t kMiGroups = 4;
-constexpr uint32_t kMiBar = kMiGroup0 + kMiGroups * kMiBuf;                // 4 mbarriers, TMEM address
-constexpr uint32_t kMlpInferSmem = kMiBar + 64;                            // 174,144 bytes
+constexpr uint32_t kMiGroups = 5;
+constexpr uint32_t kMiThreads = 128 * kMiGroups;
+constexpr uint32_t kMiTmemCols = 64 * kMiGroups <= 256 ? 256 : 512;       // a power of two
+// weight-image mbarrier, one mbarrier per group, TMEM address
+constexpr uint32_t kMiBar = kMiGroup0 + kMiGroups * kMiBuf;
+constexpr uint32_t kMiBarBytes = 16 + 8 * kMiGroups + 16;
+constexpr uint32_t kMlpInferSmem = kMiBar + kMiBarBytes;                   // 202,888 bytes
+static_assert(kMlpInferSmem <= 227 * 1024, "inference kernel shared memory");
 
 __device__ __forceinline__ void group_sync(uint32_t id) {
     asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
@@ -328,19 +350,15 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, Out *
     const uint32_t g = warp >> 2, quarter = warp & 3u, gtid = tid & 127u;
     const uint32_t r = 32u * quarter + lane;                     // this thread's row in the tile
     const uint32_t bar_id = 1u + g;
-    uint64_t *bar = (uint64_t *)(smem + kMiBar) + g;
-    uint32_t *s_taddr = (uint32_t *)(smem + kMiBar + 32);
+    uint64_t *bar = (uint64_t *)(smem + kMiBar + 16) + g;
+    uint32_t *s_taddr = (uint32_t *)(smem + kMiBar + 16 + 8 * kMiGroups);
     unsigned char *buf = smem + kMiGroup0 + g * kMiBuf;
     const uint32_t n = feat.count();
     const uint32_t tiles = (n + kMlpTile - 1) / kMlpTile;
     if (kMiGroups * blockIdx.x >= tiles) return;
-    mlp_stage_rows(smem + kMlpW1, w.W[0], kGuideHid, kGuideIn);
-    mlp_stage_rows(smem + kMlpW2, w.W[1], kGuideHid, kGuideHid);
-    mlp_stage_rows(smem + kMlpW3, w.W[2], kGuideHid, kGuideHid);
-    mlp_stage_rows(smem + kMlpW4, w.W[3], kGuideHid, kGuideHid);
-    mlp_stage_rows(smem + kMlpW5, w.W[4], kGuideOutPad, kGuideHid);
-    if (warp == 0) umma::tmem_alloc(s_taddr, 256);
-    if (tid < kMiGroups) umma::mbar_init((uint64_t *)(smem + kMiBar) + tid, 1);
+    const bool image_ok = mlp_load_image(smem, w.image, (uint64_t *)(smem + kMiBar));
+    if (warp == 0) umma::tmem_alloc(s_taddr, kMiTmemCols);
+    if (tid < kMiGroups) umma::mbar_init((uint64_t *)(smem + kMiBar + 16) + tid, 1);
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
@@ -348,20 +366,25 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, Out *
     const uint32_t lane_addr = taddr + ((32u * quarter) << 16);
     const uint32_t sbase = umma::smem_addr(smem), bbase = umma::smem_addr(buf);
     uint32_t phase = 0;
-    bool ok = true;
+    bool ok = image_ok;
     auto wait_layer = [&]() -> bool {
         const bool done = umma::mbar_wait(bar, phase);
         phase ^= 1u;
         return group_all(bar_id, done);
     };
-    // one-blob columns [c0, c0 + 112) of this row into the buffer (kdim 112)
-    auto encode_half = [&](const float *f, uint32_t c0) {
-#pragma unroll 1
+    // this row's 16-byte chunk j of a 112-column K half sits at row_off + 128 j
+    unsigned char *const row_half = buf + umma::kmajor_offset(r, 0u, kMiHalfK);
+    unsigned char *const row_hid = buf + umma::kmajor_offset(r, 0u, kGuideHid);
+    // one-blob columns [112 h, 112 h + 112) of this row into the buffer; the
+    // chunks are unrolled so that each one's feature and bins are constants
+    auto encode_half = [&](const float *f, auto half) {
+        constexpr uint32_t c0 = decltype(half)::value * kMiHalfK;
+#pragma unroll
         for (uint32_t j = 0; j < kMiHalfK / 8; ++j) {
             const uint32_t col = c0 + 8u * j;
             float g8[8];
             oneblob_chunk(f[col / kGuideBins], (int)(col % kGuideBins), g8);
-            *(uint4 *)(buf + umma::kmajor_offset(r, 8u * j, kMiHalfK)) =
+            *(uint4 *)(row_half + 128u * j) =
                 make_uint4(pack_bf16x2<false>(g8[0], g8[1]), pack_bf16x2<false>(g8[2], g8[3]),
                            pack_bf16x2<false>(g8[4], g8[5]), pack_bf16x2<false>(g8[6], g8[7]));
         }
@@ -369,14 +392,23 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, Out *
         umma::fence_before_sync();
         group_sync(bar_id);
     };
-    for (uint32_t t = kMiGroups * blockIdx.x + g; t < tiles && ok; t += kMiGroups * gridDim.x) {
+    const uint32_t stride = kMiGroups * gridDim.x;
+    float f[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    {
+        const uint32_t row0 = (kMiGroups * blockIdx.x + g) * kMlpTile + r;
+        if (row0 < n) feat(row0, f);
+    }
+    for (uint32_t t = kMiGroups * blockIdx.x + g; t < tiles && ok; t += stride) {
         const uint32_t row = t * kMlpTile + r;
-        float f[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (row < n) feat(row, f);
-        encode_half(f, 0u);
+        float fn[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // the next tile's
+        {
+            const uint32_t nrow = (t + stride) * kMlpTile + r;
+            if (t + stride < tiles && nrow < n) feat(nrow, fn);
+        }
+        encode_half(f, std::integral_constant<uint32_t, 0>{});
         if (gtid == 0) mlp_issue_half(taddr, bbase, sbase + kMlpW1, 0u, bar);
         if (!(ok = wait_layer())) break;
-        encode_half(f, kMiHalfK);
+        encode_half(f, std::integral_constant<uint32_t, 1>{});
         if (gtid == 0) mlp_issue_half(taddr, bbase, sbase + kMlpW1, 1u, bar);
         if (!(ok = wait_layer())) break;
         // layers 2..5: read back, ReLU -> BF16 -> the activation buffer
@@ -384,16 +416,26 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, Out *
 #pragma unroll 1
         for (int l = 1; l < 5; ++l) {
             umma::fence_after_sync();
-#pragma unroll 1
-            for (uint32_t c0 = 0; c0 < (uint32_t)kGuideHid; c0 += 16) {
-                float v[16];
-                umma::tmem_ld16(lane_addr + c0, v);
-                *(uint4 *)(buf + umma::kmajor_offset(r, c0, kGuideHid)) =
+            // 32 columns per wait: two 16-column loads in flight
+#pragma unroll
+            for (uint32_t c0 = 0; c0 < (uint32_t)kGuideHid; c0 += 32) {
+                uint32_t a[16], b[16];
+                umma::tmem_ld16_async(lane_addr + c0, a);
+                umma::tmem_ld16_async(lane_addr + c0 + 16, b);
+                umma::tmem_wait_ld32(a, b);
+                const float *v = (const float *)a, *w = (const float *)b;
+                *(uint4 *)(row_hid + 16u * c0) =
                     make_uint4(pack_bf16x2<true>(v[0], v[1]), pack_bf16x2<true>(v[2], v[3]),
                                pack_bf16x2<true>(v[4], v[5]), pack_bf16x2<true>(v[6], v[7]));
-                *(uint4 *)(buf + umma::kmajor_offset(r, c0 + 8, kGuideHid)) =
+                *(uint4 *)(row_hid + 16u * c0 + 128u) =
                     make_uint4(pack_bf16x2<true>(v[8], v[9]), pack_bf16x2<true>(v[10], v[11]),
                                pack_bf16x2<true>(v[12], v[13]), pack_bf16x2<true>(v[14], v[15]));
+                *(uint4 *)(row_hid + 16u * c0 + 256u) =
+                    make_uint4(pack_bf16x2<true>(w[0], w[1]), pack_bf16x2<true>(w[2], w[3]),
+                               pack_bf16x2<true>(w[4], w[5]), pack_bf16x2<true>(w[6], w[7]));
+                *(uint4 *)(row_hid + 16u * c0 + 384u) =
+                    make_uint4(pack_bf16x2<true>(w[8], w[9]), pack_bf16x2<true>(w[10], w[11]),
+                               pack_bf16x2<true>(w[12], w[13]), pack_bf16x2<true>(w[14], w[15]));
             }
             umma::fence_proxy_async();
             umma::fence_before_sync();
@@ -433,6 +475,8 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, Out *
         // the accumulator and the buffer are reused by the next tile
         umma::fence_before_sync();
         group_sync(bar_id);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) f[k] = fn[k];
     }
     if (!ok && gtid == 0) {
         // the product in flight may still complete: wait for it once more
@@ -443,7 +487,7 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, Out *
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
-    if (warp == 0) umma::tmem_dealloc(*s_taddr, 256);
+    if (warp == 0) umma::tmem_dealloc(*s_taddr, kMiTmemCols);
 }
 
 }  // namespace rtg

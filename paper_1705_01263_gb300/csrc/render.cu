@@ -58,10 +58,9 @@ struct Pool {
     uint32_t capacity;
     uint32_t *nrec;  // guided rendering: training records per path (count | pending flag), else null
     // regeneration only (null otherwise): task of each slot (offset in the
-    // window), slots whose path ended this step, slots emptied and not refilled
+    // window) and the slots whose path ended this step
     uint32_t *task;
     uint32_t *qd;
-    uint32_t *qfree;
     // compressed state (Sec. 3.1.1, rt_render_opts.state_compression): when
     // `compact` is set these replace ray_d, beta, sh_d and sh_c (null then):
     // direction as a 16:16 octahedral code + prev_pdf (FP32); throughput as
@@ -305,7 +304,7 @@ __global__ void __launch_bounds__(128, 8) k_shade(RenderParams P, Pool pool, con
 // single-level kernels carry none of its state and need about a third fewer
 // registers, which raises the resident warps per SM from 20 to 32 (the launch
 // bounds hold them at 64 registers, 8 blocks of 128 per SM).
-template <bool kCount, bool kSmemStack, bool kTwoLevel>
+template <bool kCount, bool kSmemStack, bool kTwoLevel, bool kPostpone = false>
 __global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_ext_simple(DevScene sc, Pool pool, const uint32_t *sorted) {
     Ctrl *c = pool.ctrl;
     if (c->tail) return;
@@ -326,6 +325,7 @@ __global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_ext_simple(Dev
         Hit h;
         h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
         TraceResult tr = kTwoLevel    ? traverse_two_level<false>(sc, r, h)
+                         : kPostpone  ? traverse_pp<false>(sc.nodes, sc.tris, r, h)
                          : kSmemStack ? traverse<false, SharedStack>(sc.nodes, sc.tris, 0u, r, h, 0u, &sst)
                                       : traverse<false>(sc.nodes, sc.tris, 0u, r, h);
         overflow |= tr.overflow;
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_ext_simple(Dev
     }
 }
 
-template <bool kCount, bool kSmemStack, bool kTwoLevel>
+template <bool kCount, bool kSmemStack, bool kTwoLevel, bool kPostpone = false>
 __global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_shadow_simple(DevScene sc, Pool pool, const uint32_t *) {
     Ctrl *c = pool.ctrl;
     if (c->tail) return;
@@ -361,6 +361,7 @@ __global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_shadow_simple(
         Hit h;
         h.prim = RT_MISS; h.inst = 0; h.t = INFINITY;
         TraceResult tr = kTwoLevel    ? traverse_two_level<true>(sc, r, h)
+                         : kPostpone  ? traverse_pp<true>(sc.nodes, sc.tris, r, h)
                          : kSmemStack ? traverse<true, SharedStack>(sc.nodes, sc.tris, 0u, r, h, 0u, &sst)
                                       : traverse<true>(sc.nodes, sc.tris, 0u, r, h);
         overflow |= tr.overflow;
@@ -731,9 +732,14 @@ __global__ void k_resolve(const double *sum, const double *sum2, const uint32_t 
 // between half and fully occupied instead of emptying towards the end of a
 // set. The film is accumulated from the staging buffer in sample order per
 // pixel (k_film_range), so the result does not depend on which slot a task
-// ran in or when. Every decision (how many tasks start, which slots they take)
-// is a function of counts read at kernel start, made identically by k_regen
-// and k_regen_step_end, so neither needs an atomic or a grid-wide barrier.
+// ran in or when. A refill also compacts the pool: the paths that continue
+// move to slots 0 .. n_next - 1 in queue order and the new tasks take the
+// slots after them, so that queue position and slot coincide again and the
+// state kernels' loads and stores stay coalesced (paths end at random, so
+// refilling the emptied slots in place would scatter every later access).
+// Every decision (how many tasks start) is a function of counts read at
+// kernel start, made identically by k_regen_gather, k_regen and
+// k_regen_step_end, so none needs an atomic or a grid-wide barrier.
 
 RT_D unsigned long long globaltimer_ns() {
     unsigned long long t;
@@ -746,17 +752,13 @@ __global__ void k_regen_init(RenderParams P, Pool pool, uint64_t t0, uint32_t n_
                              const volatile uint32_t *stop_word) {
     const uint32_t cap = pool.capacity;
     const uint32_t k = min(cap, n_tasks);
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cap; q += gridDim.x * blockDim.x) {
-        if (q < k) {
-            const uint64_t t = t0 + q;
-            PathState s;
-            raygen(P, (uint32_t)(t % WH), (uint32_t)(t / WH), s);
-            store_state(pool, q, s);
-            pool.task[q] = q;
-            pool.q[0][q] = q;
-        } else {
-            pool.qfree[q - k] = q;
-        }
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < k; q += gridDim.x * blockDim.x) {
+        const uint64_t t = t0 + q;
+        PathState s;
+        raygen(P, (uint32_t)(t % WH), (uint32_t)(t / WH), s);
+        store_state(pool, q, s);
+        pool.task[q] = q;
+        pool.q[0][q] = q;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         Ctrl *c = pool.ctrl;
@@ -774,9 +776,9 @@ __global__ void k_regen_init(RenderParams P, Pool pool, uint64_t t0, uint32_t n_
     }
 }
 
-// Tasks started by this step's regeneration (identical in k_regen and
-// k_regen_step_end: both read the same counts, and `stop` changes only
-// after both ran).
+// Tasks started by this step's regeneration (identical in k_regen_gather,
+// k_regen and k_regen_step_end: they read the same counts, and `stop`
+// changes only after all ran).
 RT_HD uint32_t regen_count(const Ctrl *c, uint32_t regen_min) {
     const uint32_t left = c->n_tasks - c->task_next;
     const uint32_t empty = c->n_dead + c->n_free;
@@ -784,24 +786,15 @@ RT_HD uint32_t regen_count(const Ctrl *c, uint32_t regen_min) {
     return left < empty ? left : empty;
 }
 
-// Slot bookkeeping of thread j of k_regen: retire dead[j] (returned in
-// *retire, else ~0u) and return the slot that task task_next + j starts in
-// (~0u when j starts none); a dead slot that is not refilled goes onto the
-// free list.
-RT_HD uint32_t regen_slot(uint32_t j, uint32_t n_dead, uint32_t n_free, uint32_t n_new, const uint32_t *qd,
-                          uint32_t *qfree, uint32_t *retire) {
-    uint32_t slot = ~0u;
-    *retire = ~0u;
-    if (j < n_dead) {
-        slot = qd[j];
-        *retire = slot;
-    }
-    if (j < n_new) {
-        if (j >= n_dead) slot = qfree[n_free - 1 - (j - n_dead)];
-        return slot;
-    }
-    if (j < n_dead) qfree[n_free + (j - n_new)] = slot;
-    return ~0u;
+// What the regeneration kernels of one step do: retire n_dead paths; on a
+// refill, move the n_move = n_next continuing paths to slots 0 .. n_move - 1
+// and start n_new tasks in slots n_move .. n_move + n_new - 1.
+struct RegenPlan {
+    uint32_t n_dead, n_move, n_new;
+};
+RT_HD RegenPlan regen_plan(const Ctrl *c, uint32_t regen_min) {
+    const uint32_t n_new = regen_count(c, regen_min);
+    return RegenPlan{c->n_dead, n_new ? c->n_next : 0u, n_new};
 }
 
 // Counts after a step's regeneration (k_regen_step_end, without the stop
@@ -818,32 +811,83 @@ RT_HD void regen_advance(Ctrl *c, uint32_t regen_min) {
     c->cur ^= 1u;
 }
 
-// After the shadow rays of a step: retire the paths that ended, then (when
-// enough slots are empty) start the next tasks, appended to the next
-// extension queue after the paths that continue. Thread j retires dead[j]
-// and starts task task_next + j in dead[j], or in the top of the free list
-// once the dead slots are used up; dead slots not refilled go onto the free
-// list.
-__global__ void k_regen(RenderParams P, Pool pool, float4 *stage, uint64_t t0, uint32_t WH, uint32_t regen_min) {
+// The persistent state of the paths that continue through a refill, as raw
+// words (the compressed arrays keep their encoding: x, y of d and b), in
+// queue order.
+struct RegenScratch {
+    uint4 *o, *d, *b, *L;
+    uint2 *index;
+    uint32_t *pixel, *task;
+};
+
+// After the shadow rays of a step: retire the paths that ended (thread j
+// retires dead[j]) and, on a step that refills, copy the state of the path
+// at position j of the next extension queue to scratch position j.
+__global__ void k_regen_gather(Pool pool, float4 *stage, uint32_t regen_min, RegenScratch g) {
     const Ctrl *c = pool.ctrl;
     if (c->tail) return;
-    const uint32_t n_dead = c->n_dead, n_free = c->n_free, n_next = c->n_next, base = c->task_next;
-    const uint32_t n_new = regen_count(c, regen_min);
-    uint32_t *next = pool.q[c->cur ^ 1u];
-    const uint32_t m = max(n_dead, n_new);
+    const RegenPlan pl = regen_plan(c, regen_min);
+    const uint32_t n_dead = pl.n_dead, n_move = pl.n_move;
+    const uint32_t *next = pool.q[c->cur ^ 1u];
+    const uint32_t m = max(n_dead, n_move);
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
-        uint32_t retire;
-        const uint32_t slot = regen_slot(j, n_dead, n_free, n_new, pool.qd, pool.qfree, &retire);
-        if (retire != ~0u) stage[pool.task[retire]] = pool.L[retire];
-        if (slot != ~0u) {
-            const uint32_t off = base + j;
+        if (j < n_dead) {
+            const uint32_t slot = pool.qd[j];
+            stage[pool.task[slot]] = pool.L[slot];
+        }
+        if (j < n_move) {
+            const uint32_t slot = next[j];
+            g.o[j] = ((const uint4 *)pool.ray_o)[slot];
+            if (pool.compact) {
+                const uint2 d = pool.dir_c[slot], b = pool.beta_c[slot];
+                g.d[j] = make_uint4(d.x, d.y, 0u, 0u);
+                g.b[j] = make_uint4(b.x, b.y, 0u, 0u);
+            } else {
+                g.d[j] = ((const uint4 *)pool.ray_d)[slot];
+                g.b[j] = ((const uint4 *)pool.beta)[slot];
+            }
+            g.L[j] = ((const uint4 *)pool.L)[slot];
+            g.index[j] = pool.index[slot];
+            g.pixel[j] = pool.pixel[slot];
+            g.task[j] = pool.task[slot];
+        }
+    }
+}
+
+// On a step that refills (after k_regen_gather): the continuing paths take
+// slots 0 .. n_next - 1 in queue order, tasks task_next + j start in slots
+// n_next + j, and the next extension queue becomes the identity.
+__global__ void k_regen(RenderParams P, Pool pool, uint64_t t0, uint32_t WH, uint32_t regen_min, RegenScratch g) {
+    const Ctrl *c = pool.ctrl;
+    if (c->tail) return;
+    const RegenPlan pl = regen_plan(c, regen_min);
+    if (pl.n_new == 0) return;
+    const uint32_t n_next = pl.n_move, base = c->task_next;
+    uint32_t *next = pool.q[c->cur ^ 1u];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_next + pl.n_new; i += gridDim.x * blockDim.x) {
+        if (i < n_next) {
+            ((uint4 *)pool.ray_o)[i] = g.o[i];
+            if (pool.compact) {
+                const uint4 d = g.d[i], b = g.b[i];
+                pool.dir_c[i] = make_uint2(d.x, d.y);
+                pool.beta_c[i] = make_uint2(b.x, b.y);
+            } else {
+                ((uint4 *)pool.ray_d)[i] = g.d[i];
+                ((uint4 *)pool.beta)[i] = g.b[i];
+            }
+            ((uint4 *)pool.L)[i] = g.L[i];
+            pool.index[i] = g.index[i];
+            pool.pixel[i] = g.pixel[i];
+            pool.task[i] = g.task[i];
+        } else {
+            const uint32_t off = base + (i - n_next);
             const uint64_t t = t0 + off;
             PathState s;
             raygen(P, (uint32_t)(t % WH), (uint32_t)(t / WH), s);
-            store_state(pool, slot, s);
-            pool.task[slot] = off;
-            next[n_next + j] = slot;
+            store_state(pool, i, s);
+            pool.task[i] = off;
         }
+        next[i] = i;
     }
 }
 
@@ -983,7 +1027,7 @@ struct PathFeatures {
     }
 };
 
-__global__ void __launch_bounds__(512, 1) k_guide_mlp_paths(MlpWeights w, PathFeatures pf, __nv_bfloat16 *raw,
+__global__ void __launch_bounds__(kMiThreads, 1) k_guide_mlp_paths(MlpWeights w, PathFeatures pf, __nv_bfloat16 *raw,
                                                             uint32_t *err) {
     mlp_infer_tiles(w, pf, raw, err);
 }
@@ -1125,11 +1169,11 @@ struct TraceKernels {
     size_t smem;
 };
 
-template <bool kCount, bool kSmem, bool kTwo>
+template <bool kCount, bool kSmem, bool kTwo, bool kPostpone = false>
 TraceKernels trace_kernels_of(int block) {
     TraceKernels k;
-    k.ext = k_trace_ext_simple<kCount, kSmem, kTwo>;
-    k.shadow = k_trace_shadow_simple<kCount, kSmem, kTwo>;
+    k.ext = k_trace_ext_simple<kCount, kSmem, kTwo, kPostpone>;
+    k.shadow = k_trace_shadow_simple<kCount, kSmem, kTwo, kPostpone>;
     k.smem = kSmem ? (size_t)kSharedEntries * block * sizeof(uint2) : 0;
     k.grid_ext = grid_persistent(k.ext, block, k.smem);
     k.grid_shadow = grid_persistent(k.shadow, block, k.smem);
@@ -1150,13 +1194,20 @@ TraceKernels refill_kernels(int block) {
 // variant: 0 (default) closest hit one-shot per ray, shadow rays with lane
 // refill (any-hit rays end at very different times, and an occlusion answer
 // does not depend on the order of the traversal); 2 both one-shot with the
-// stack top in shared memory; 3 both with lane refill; 4 both one-shot.
+// stack top in shared memory; 3 both with lane refill; 4 both one-shot;
+// 6 closest hit one-shot with postponed triangle tests, shadow rays as 0;
+// 7 both one-shot with postponed triangle tests.
 // Two-level scenes always use the one-shot kernels with a thread-local stack.
 inline TraceKernels trace_kernels(bool count, int variant, bool two_level, int block) {
     if (two_level) return count ? trace_kernels_of<true, false, true>(block) : trace_kernels_of<false, false, true>(block);
     if (variant == 3) return count ? refill_kernels<true>(block) : refill_kernels<false>(block);
-    if (variant == 0) {
-        TraceKernels k = count ? trace_kernels_of<true, false, false>(block) : trace_kernels_of<false, false, false>(block);
+    if (variant == 7)
+        return count ? trace_kernels_of<true, false, false, true>(block) : trace_kernels_of<false, false, false, true>(block);
+    if (variant == 0 || variant == 6) {
+        TraceKernels k = variant == 6
+                             ? (count ? trace_kernels_of<true, false, false, true>(block)
+                                      : trace_kernels_of<false, false, false, true>(block))
+                             : (count ? trace_kernels_of<true, false, false>(block) : trace_kernels_of<false, false, false>(block));
         const TraceKernels r = count ? refill_kernels<true>(block) : refill_kernels<false>(block);
         k.shadow = r.shadow;
         k.grid_shadow = r.grid_shadow;
@@ -1186,7 +1237,7 @@ struct PoolAlloc {
     Pool view{};
     // regeneration arrays (task per slot, dead and free slot lists): set in
     // the view only by the scheduler that uses them
-    uint32_t *task = nullptr, *qd = nullptr, *qfree = nullptr;
+    uint32_t *task = nullptr, *qd = nullptr;
     void *block = nullptr;
     uint32_t capacity = 0;
     bool compact = false;   // compressed layout of the direction, throughput and shadow arrays
@@ -1197,8 +1248,11 @@ struct PoolAlloc {
 
 // Device bytes of one path's state in the pool (eight float4 arrays, the
 // sequence index, pixel, instance of the hit, three queue entries and the
-// regeneration scheduler's task, dead and free entries).
-constexpr size_t kPoolBytesPerPath = 8 * sizeof(float4) + sizeof(uint2) + 4 + 4 + 3 * 4 + 3 * 4;
+// regeneration scheduler's task and dead entries), and of the scratch copy
+// of a continuing path that a refill moves (regeneration with a pool smaller
+// than the request).
+constexpr size_t kPoolBytesPerPath = 8 * sizeof(float4) + sizeof(uint2) + 4 + 4 + 3 * 4 + 2 * 4;
+constexpr size_t kRegenScratchBytesPerPath = 4 * sizeof(uint4) + sizeof(uint2) + 4 + 4;
 
 // Pool capacity when the caller leaves it to the library: every requested
 // path at once when that fits, up to 2^27 paths (about 21 GB of state) and a
@@ -1208,7 +1262,9 @@ uint32_t default_capacity(uint64_t paths) {
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)1 << 30;
     const uint64_t by_mem = (uint64_t)(free_b / 4 / kPoolBytesPerPath);
-    const uint64_t c = std::min<uint64_t>({paths, (uint64_t)1 << 27, by_mem});
+    uint64_t c = std::min<uint64_t>({paths, (uint64_t)1 << 27, by_mem});
+    // a pool that is refilled also holds the scratch copy of its continuing paths
+    if (c < paths) c = std::min<uint64_t>(c, free_b / 4 / (kPoolBytesPerPath + kRegenScratchBytesPerPath));
     return (uint32_t)std::max<uint64_t>(c, 32u);
 }
 
@@ -1220,7 +1276,7 @@ rt_status ensure_pool(PoolAlloc &pa, uint32_t capacity, bool compact = false) {
     // four float4 arrays always (origin, radiance, hit, shadow origin); four
     // more, or their compressed forms (8 + 8 + 4 + 8 bytes per path)
     size_t bytes = 4 * f4 + (compact ? P * 28 + 4 * 256 : 4 * f4) + P * sizeof(uint2) + P * 4 /*pixel*/ +
-                   P * 4 /*hit_inst*/ + 3 * P * 4 /*queues*/ + 3 * P * 4 /*regeneration*/ + 64 * 256;
+                   P * 4 /*hit_inst*/ + 3 * P * 4 /*queues*/ + 2 * P * 4 /*regeneration*/ + 64 * 256;
     cudaError_t e = cudaMalloc(&pa.block, bytes);
     if (e != cudaSuccess) { set_error("path-state pool allocation failed"); return RT_OOM; }
     char *p = (char *)pa.block;
@@ -1241,7 +1297,7 @@ rt_status ensure_pool(PoolAlloc &pa, uint32_t capacity, bool compact = false) {
     v.pixel = (uint32_t *)take(P * 4);
     v.hit_inst = (uint32_t *)take(P * 4);
     v.q[0] = (uint32_t *)take(P * 4); v.q[1] = (uint32_t *)take(P * 4); v.qs = (uint32_t *)take(P * 4);
-    pa.task = (uint32_t *)take(P * 4); pa.qd = (uint32_t *)take(P * 4); pa.qfree = (uint32_t *)take(P * 4);
+    pa.task = (uint32_t *)take(P * 4); pa.qd = (uint32_t *)take(P * 4);
     v.capacity = capacity;
     pa.capacity = capacity;
     if ((size_t)(p - (char *)pa.block) > bytes) { set_error("pool layout overflow"); return RT_CUDA_ERROR; }
@@ -1265,6 +1321,8 @@ struct RenderCache {
     // regeneration: radiance per task of the window, host-mapped stop word
     float4 *stage = nullptr;
     uint64_t stage_cap = 0;
+    void *gscr = nullptr;   // RegenScratch storage for gscr_cap paths
+    uint32_t gscr_cap = 0;
     uint32_t *stop_host = nullptr, *stop_dev = nullptr;
     Ctrl *ctrl_ring = nullptr;   // pinned copies of the control block, one per chunk in flight
     cudaEvent_t chunk_ev[2] = {nullptr, nullptr};
@@ -1278,6 +1336,7 @@ struct RenderCache {
         if (dims) cudaFree(dims);
         if (host_ctrl) cudaFreeHost(host_ctrl);
         if (stage) cudaFree(stage);
+        if (gscr) cudaFree(gscr);
         if (stop_host) cudaFreeHost(stop_host);
         if (ctrl_ring) cudaFreeHost(ctrl_ring);
         for (cudaEvent_t e : chunk_ev)
@@ -1476,7 +1535,6 @@ static rt_status render_regen(const rt_scene *s, const rt_camera *cam, uint32_t 
     Pool pool = rc->pool.view;
     pool.task = rc->pool.task;
     pool.qd = rc->pool.qd;
-    pool.qfree = rc->pool.qfree;
     pool.capacity = cap;   // the allocation may be larger (kept from an earlier call)
     // staging window: the request, at most 2^30 tasks and a quarter of the
     // free device memory (16 bytes per task)
@@ -1496,6 +1554,27 @@ static rt_status render_regen(const rt_scene *s, const rt_camera *cam, uint32_t 
             return RT_OOM;
         }
         rc->stage_cap = win;
+    }
+    // scratch of the continuing paths that a refill moves (only a window
+    // larger than the pool refills)
+    RegenScratch gs{};
+    if (win > cap) {
+        if (rc->gscr_cap < cap) {
+            if (rc->gscr) cudaFree(rc->gscr);
+            rc->gscr = nullptr;
+            rc->gscr_cap = 0;
+            if (cudaMalloc(&rc->gscr, (size_t)cap * kRegenScratchBytesPerPath + 8 * 256) != cudaSuccess) {
+                set_error("rt_render: regeneration scratch allocation failed");
+                return RT_OOM;
+            }
+            rc->gscr_cap = cap;
+        }
+        char *g = (char *)rc->gscr;
+        const size_t C = rc->gscr_cap;
+        auto take = [&](size_t b) { char *r = g; g += (b + 255) / 256 * 256; return r; };
+        gs.o = (uint4 *)take(C * 16); gs.d = (uint4 *)take(C * 16); gs.b = (uint4 *)take(C * 16);
+        gs.L = (uint4 *)take(C * 16); gs.index = (uint2 *)take(C * 8);
+        gs.pixel = (uint32_t *)take(C * 4); gs.task = (uint32_t *)take(C * 4);
     }
     if (!rc->stop_host) {
         RT_CUDA_TRY(cudaHostAlloc(&rc->stop_host, sizeof(uint32_t), cudaHostAllocMapped));
@@ -1630,10 +1709,11 @@ static rt_status render_regen(const rt_scene *s, const rt_camera *cam, uint32_t 
                 tk.shadow<<<tk.grid_shadow, gb, tk.smem, st>>>(s->dev, pool, nullptr);
                 done_ev(e);
                 e = mark(4);
-                k_regen<<<g_regen, 256, 0, st>>>(P, pool, rc->stage, t, (uint32_t)WH, regen_min);
+                k_regen_gather<<<g_regen, 256, 0, st>>>(pool, rc->stage, regen_min, gs);
+                k_regen<<<g_regen, 256, 0, st>>>(P, pool, t, (uint32_t)WH, regen_min, gs);
                 k_regen_step_end<<<1, 1, 0, st>>>(pool, regen_min, rc->stop_dev);
                 done_ev(e);
-                stats.kernel_launches += 5;
+                stats.kernel_launches += 6;
                 ++stats.trace_launches;
                 ++stats.wavefront_steps;
             }
@@ -1709,7 +1789,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     rt_render_opts o{};
     if (opts_in) o = *opts_in;
     if (spp == 0) return RT_OK;
-    if (o.trace_kernel < 0 || o.trace_kernel > 5) { set_error("rt_render: trace_kernel must be in [0, 5]"); return RT_INVALID_ARG; }
+    if (o.trace_kernel < 0 || o.trace_kernel > 7) { set_error("rt_render: trace_kernel must be in [0, 7]"); return RT_INVALID_ARG; }
     if (!valid_block(o.block_size)) { set_error("rt_render: block_size must be 0 or a multiple of 32 up to 128"); return RT_INVALID_ARG; }
     if (s->dev.two_level) o.trace_kernel = 0;   // the persistent variant is single-level only
     cudaStream_t st = (cudaStream_t)stream;
@@ -1833,7 +1913,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
                 // at the last vertex (it only adds emission) nor past gdepth
                 const float av = v <= gdepth ? a : 0.f;
                 if (av > 0.f) {
-                    k_guide_mlp_paths<<<sm_count(), kMlpThreads, kMlpInferSmem, st>>>(guide_weights(gd), pf, rc->gfeat,
+                    k_guide_mlp_paths<<<sm_count(), kMiThreads, kMlpInferSmem, st>>>(guide_weights(gd), pf, rc->gfeat,
                                                                             guide_err(gd));
                     stats.kernel_launches += 1;
                 }
@@ -2626,7 +2706,7 @@ struct JobPathFeatures {
     }
 };
 
-__global__ void __launch_bounds__(512, 1) k_guide_mlp_job(MlpWeights w, JobPathFeatures pf, __nv_bfloat16 *raw,
+__global__ void __launch_bounds__(kMiThreads, 1) k_guide_mlp_job(MlpWeights w, JobPathFeatures pf, __nv_bfloat16 *raw,
                                                           uint32_t *err) {
     mlp_infer_tiles(w, pf, raw, err);
 }
@@ -3112,7 +3192,7 @@ static rt_status render_batch_guided(const rt_render_job *jobs, int32_t njobs, c
             for (int32_t j = 0; j < njobs; ++j) {
                 if (!jobs[j].guide) continue;
                 const JobPathFeatures pf{djobs, dguides, pool, sorted, starts, hist, dalpha, (uint32_t)j};
-                k_guide_mlp_job<<<sm_count(), kMlpThreads, kMlpInferSmem, side[k++ % kSide]>>>(
+                k_guide_mlp_job<<<sm_count(), kMiThreads, kMlpInferSmem, side[k++ % kSide]>>>(
                     guide_weights(jobs[j].guide), pf, raw, guide_err(jobs[j].guide));
             }
             for (int b = 0; b < kSide; ++b) {
@@ -3277,12 +3357,14 @@ extern "C" rt_status rt_autotune(const rt_render_job *jobs, int32_t njobs, uint3
 }
 
 // ---------------------------------------------------------------------------
-// Host test hook of the regeneration bookkeeping: the slot decisions of
-// k_regen_init, k_regen and k_regen_step_end (the same functions) driven by
-// synthetic path lengths instead of shading. n_tasks tasks, `cap` slots,
-// task k lives life[k] >= 1 bounce steps; a stop after `stop_step` steps
-// (~0u: none). Writes per task the step at which it was retired (~0u: never
-// started) and returns the steps taken and the steps that refilled slots.
+// Host test hook of the regeneration bookkeeping: the decisions of
+// k_regen_init, k_regen_gather, k_regen and k_regen_step_end (the same
+// counting functions) driven by synthetic path lengths instead of shading.
+// n_tasks tasks, `cap` slots, task k lives life[k] >= 1 bounce steps; a stop
+// after `stop_step` steps (~0u: none). Writes per task the step at which it
+// was retired (~0u: never started) and returns the steps taken and the steps
+// that refilled slots. Checks that no task is retired twice and that the
+// live paths always occupy distinct slots below `cap`.
 extern "C" rt_status rt_debug_regen_host(uint32_t n_tasks, uint32_t cap, uint32_t regen_min, const uint8_t *life,
                                          uint32_t stop_step, uint32_t *retired_at, uint32_t *steps,
                                          uint32_t *regen_steps) {
@@ -3292,14 +3374,12 @@ extern "C" rt_status rt_debug_regen_host(uint32_t n_tasks, uint32_t cap, uint32_
     }
     using namespace rtg;
     std::vector<uint32_t> task(cap, ~0u), q[2] = {std::vector<uint32_t>(cap), std::vector<uint32_t>(cap)};
-    std::vector<uint32_t> qd(cap), qfree(cap), left(cap, 0);
+    std::vector<uint32_t> qd(cap), left(cap, 0), g_task(cap), g_left(cap);
+    std::vector<uint8_t> seen(cap);
     for (uint32_t k = 0; k < n_tasks; ++k) retired_at[k] = ~0u;
     Ctrl c{};
     const uint32_t k0 = std::min(cap, n_tasks);
-    for (uint32_t s = 0; s < cap; ++s) {
-        if (s < k0) { task[s] = s; left[s] = life[s]; q[0][s] = s; }
-        else qfree[s - k0] = s;
-    }
+    for (uint32_t s = 0; s < k0; ++s) { task[s] = s; left[s] = life[s]; q[0][s] = s; }
     c.n_ext = k0; c.n_free = cap - k0; c.task_next = k0; c.n_tasks = n_tasks;
     uint32_t step = 0;
     const uint32_t limit = 64u + 4u * 256u * (n_tasks / std::max(1u, cap / 2) + 2u);
@@ -3313,25 +3393,37 @@ extern "C" rt_status rt_debug_regen_host(uint32_t n_tasks, uint32_t cap, uint32_
             else qd[c.n_dead++] = s;
         }
         if (c.n_next + c.n_dead != c.n_ext) { set_error("rt_debug_regen_host: lost a path"); return RT_CUDA_ERROR; }
+        const RegenPlan pl = regen_plan(&c, regen_min);
+        // k_regen_gather
+        for (uint32_t j = 0; j < pl.n_dead; ++j) {
+            const uint32_t s = qd[j];
+            if (retired_at[task[s]] != ~0u) { set_error("rt_debug_regen_host: task retired twice"); return RT_CUDA_ERROR; }
+            retired_at[task[s]] = step;
+        }
+        for (uint32_t j = 0; j < pl.n_move; ++j) { g_task[j] = task[next[j]]; g_left[j] = left[next[j]]; }
         // k_regen
-        const uint32_t n_dead = c.n_dead, n_free = c.n_free, n_new = regen_count(&c, regen_min);
-        for (uint32_t j = 0; j < std::max(n_dead, n_new); ++j) {
-            uint32_t retire;
-            const uint32_t slot = regen_slot(j, n_dead, n_free, n_new, qd.data(), qfree.data(), &retire);
-            if (retire != ~0u) {
-                if (retired_at[task[retire]] != ~0u) { set_error("rt_debug_regen_host: task retired twice"); return RT_CUDA_ERROR; }
-                retired_at[task[retire]] = step;
-            }
-            if (slot != ~0u) {
-                if (slot >= cap || c.n_next + j >= cap) { set_error("rt_debug_regen_host: slot out of range"); return RT_CUDA_ERROR; }
-                const uint32_t off = c.task_next + j;
-                task[slot] = off;
-                left[slot] = life[off];
-                next[c.n_next + j] = slot;
+        if (pl.n_new) {
+            for (uint32_t i = 0; i < pl.n_move + pl.n_new; ++i) {
+                if (i >= cap) { set_error("rt_debug_regen_host: slot out of range"); return RT_CUDA_ERROR; }
+                if (i < pl.n_move) {
+                    task[i] = g_task[i];
+                    left[i] = g_left[i];
+                } else {
+                    const uint32_t off = c.task_next + (i - pl.n_move);
+                    task[i] = off;
+                    left[i] = life[off];
+                }
+                next[i] = i;
             }
         }
         regen_advance(&c, regen_min);
         if (c.n_ext + c.n_free != cap) { set_error("rt_debug_regen_host: slots lost or duplicated"); return RT_CUDA_ERROR; }
+        std::fill(seen.begin(), seen.end(), 0);
+        for (uint32_t i = 0; i < c.n_ext; ++i) {
+            const uint32_t s = q[c.cur][i];
+            if (s >= cap || seen[s]) { set_error("rt_debug_regen_host: two live paths in one slot"); return RT_CUDA_ERROR; }
+            seen[s] = 1;
+        }
         if (step >= stop_step) c.stop = 1u;
     }
     *steps = step;

@@ -467,6 +467,91 @@ RT_HD TraceResult traverse(const uint4 *nodes, const float4 *tris, uint32_t root
     return res;
 }
 
+#ifdef __CUDACC__
+// One ray per thread with the triangle tests postponed (Ylitie, Karras and
+// Laine 2017). A loop iteration visits one child node, or tests ONE triangle
+// of the pending triangle group; when fewer than a fifth of the lanes that
+// are still traversing have triangles to test and this lane has nodes left,
+// its pending triangles go onto the stack as a group (x = first triangle,
+// y = its mask in bits 0..23; node groups always carry hit bits in 24..31)
+// and it descends further, so that the lanes of a warp stay on the same
+// branch instead of idling through another lane's leaf. Groups are postponed
+// only while the stack keeps kPostponeSpare free entries for node groups.
+// Same hits and tie rule as `traverse` (the closest hit does not depend on
+// the order of the tests).
+constexpr int kPostponeSpare = 16;
+
+template <bool kAnyHit, class Stack = LocalStack>
+__device__ __forceinline__ TraceResult traverse_pp(const uint4 *nodes, const float4 *tris, const Ray &ray,
+                                                   Hit &hit) {
+    TraceResult res{false, 0u, 0u};
+    Stack stack;
+    const RayPre rp = prepare(ray);
+    const float tmin = ray.tmin, tmax = ray.tmax;
+    float tbest = hit.prim == RT_MISS ? ray.tmax : hit.t;
+    int sp = 0;
+    uint2 ng = make_uint2(0u, (1u << (24 + (0u ^ rp.oct))) | 1u);
+    uint32_t tbase = 0u, tmask = 0u;
+    for (;;) {
+        const uint32_t act = __activemask();
+        if (ng.y & 0xFF000000u) {
+            const int bit = 31 - __clz(ng.y);
+            const uint32_t slot = ((uint32_t)bit - 24u) ^ rp.oct;
+            const uint32_t rel = __popc((ng.y & 0xFFu) & ((1u << slot) - 1u));
+            const uint32_t child = ng.x + rel;
+            ng.y &= ~(1u << bit);
+            if (ng.y & 0xFF000000u) {
+                if (sp == stack.capacity()) { res.overflow = true; return res; }
+                stack[sp++] = ng;
+            }
+            const uint4 *N = nodes + 5 * (size_t)child;
+            const uint4 n0 = __ldg(N), n1 = __ldg(N + 1), n2 = __ldg(N + 2), n3 = __ldg(N + 3), n4 = __ldg(N + 4);
+            ++res.nodes;
+            uint32_t tb;
+            const uint32_t inner = intersect_children(rp, n0, n1, n2, n3, n4, tmin, tbest, tb);
+            ng = make_uint2(n1.x, inner | (n0.w >> 24));
+            tbase = n1.y;
+            tmask = tb;
+        }
+        while (tmask) {
+            if ((ng.y & 0xFF000000u) && sp + kPostponeSpare < stack.capacity() &&
+                __popc(__activemask()) * 5 < __popc(act)) {
+                stack[sp++] = make_uint2(tbase, tmask);
+                tmask = 0u;
+                break;
+            }
+            const int k = __ffs(tmask) - 1;
+            tmask &= tmask - 1u;
+            const float4 *T = tris + 3 * (size_t)(tbase + (uint32_t)k);
+            const float4 a = __ldg(T), b = __ldg(T + 1), c = __ldg(T + 2);
+            ++res.tris;
+            float t, u, v;
+            if (intersect_tri(rp, f4xyz(a), f4xyz(b), f4xyz(c), tmin, tmax, tbest, t, u, v)) {
+                const uint32_t prim = __float_as_uint(a.w);
+                if (kAnyHit) {
+                    hit.prim = prim; hit.inst = 0u; hit.t = t; hit.b1 = u; hit.b2 = v;
+                    return res;
+                }
+                if (t < tbest || hit.prim == RT_MISS || prim < hit.prim) {
+                    hit.prim = prim; hit.inst = 0u; hit.t = t; hit.b1 = u; hit.b2 = v;
+                    tbest = t;
+                }
+            }
+        }
+        if (!(ng.y & 0xFF000000u)) {
+            if (sp == 0) return res;
+            const uint2 e = stack[--sp];
+            if (e.y & 0xFF000000u) {
+                ng = e;
+            } else {
+                tbase = e.x;
+                tmask = e.y;
+            }
+        }
+    }
+}
+#endif
+
 // Ray in the object space of instance `inst`: rows 0..2 of inst_xf hold the
 // world->object affine map. The direction is not renormalised, so t is the
 // same in both spaces.
