@@ -124,6 +124,7 @@ __global__ void k_copy_rows(const float *src, int rows, int cols, float *dst) {
 
 // Fused inference (guide_mlp.cuh) over rows of given features [n][7].
 struct ArrayFeatures {
+    static constexpr bool kContiguous = true;   // output row of row r is r
     const float *feat;
     uint32_t n;
     __device__ uint32_t count() const { return n; }

@@ -112,7 +112,8 @@ __device__ __forceinline__ void mlp_issue(uint32_t taddr, uint32_t a0, uint32_t 
 // Features: `void operator()(uint32_t row, float f[7]) const` (device),
 // `uint32_t count() const` (rows to infer, read once per launch) and, for
 // the inference kernel, `uint32_t out_row(uint32_t row) const` (the output
-// row of that input row).
+// row of that input row) and `static constexpr bool kContiguous` (out_row is
+// the identity).
 template <bool kTrain, class Features>
 __device__ void mlp_tiles(const MlpWeights &w, const Features &feat, float *raw, uint32_t *err, const MlpTrain &tr) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -294,6 +295,8 @@ constexpr uint32_t kMiHalfK = kGuideIn / 2;                                // 11
 constexpr uint32_t kMiBuf = kMlpTile * kMiHalfK * 2;                       // 28,672 bytes
 constexpr uint32_t kMiGroup0 = kMlpX;                                      // after the weights (59,392)
 constexpr uint32_t kMiGroups = 5;
+constexpr uint32_t kMiOutRow = kGuideOut * 4;                              // an output row, bytes (FP32)
+static_assert(kMlpTile * kMiOutRow <= kMiBuf, "output staging fits the group buffer");
 constexpr uint32_t kMiThreads = 128 * kMiGroups;
 constexpr uint32_t kMiTmemCols = 64 * kMiGroups <= 256 ? 256 : 512;       // a power of two
 // weight-image mbarrier, one mbarrier per group, TMEM address
@@ -405,6 +408,11 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, Out *
             const uint32_t nrow = (t + stride) * kMlpTile + r;
             if (t + stride < tiles && nrow < n) feat(nrow, fn);
         }
+        if (t != kMiGroups * blockIdx.x + g) {
+            // the previous tile's output copies have read the buffer
+            umma::bulk_wait_read();
+            group_sync(bar_id);
+        }
         encode_half(f, std::integral_constant<uint32_t, 0>{});
         if (gtid == 0) mlp_issue_half(taddr, bbase, sbase + kMlpW1, 0u, bar);
         if (!(ok = wait_layer())) break;
@@ -448,33 +456,63 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, Out *
         }
         if (!ok) break;
         umma::fence_after_sync();
-        // outputs 0..39, to the row the features name (the row itself, or
-        // the path slot it came from)
-        const size_t orow = row < n ? (size_t)feat.out_row(row) : 0;
-#pragma unroll 1
-        for (uint32_t c0 = 0; c0 < (uint32_t)kGuideOutPad; c0 += 16) {
-            float v[16];
-            umma::tmem_ld16(lane_addr + c0, v);
-            if (row < n) {
-                const int nv = c0 + 16 <= (uint32_t)kGuideOut ? 4 : 2;   // groups of four columns
-                if constexpr (sizeof(Out) == 4) {
-                    float4 *dst = (float4 *)(out + orow * kGuideOut + c0);
+        // outputs 0..39 of this row. Rows that are consecutive in the output
+        // (Features::kContiguous) go through the now free buffer, row-major,
+        // and leave with one bulk copy per tile that runs while the group goes
+        // on (the buffer is rewritten only after the copy has read it); rows
+        // that go to path slots are stored from registers, 16 bytes at a time.
+        {
+            uint32_t a[16], b[16], c[16];
+            umma::tmem_ld16_async(lane_addr, a);
+            umma::tmem_ld16_async(lane_addr + 16, b);
+            umma::tmem_wait_ld32(a, b);
+            umma::tmem_ld16_async(lane_addr + 32, c);
+            umma::tmem_wait_ld16(c);
+            uint4 o[kMiOutRow / 16];   // the row as stored (FP32: 10 x 16 bytes, BF16: 5)
+            if constexpr (sizeof(Out) == 4) {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (e < nv) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
-                } else {
-                    uint2 *dst = (uint2 *)(out + orow * kGuideOut + c0);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (e < nv)
-                            dst[e] = make_uint2(pack_bf16x2<false>(v[4 * e], v[4 * e + 1]),
-                                                pack_bf16x2<false>(v[4 * e + 2], v[4 * e + 3]));
+                for (int e = 0; e < 4; ++e) {
+                    o[e] = make_uint4(a[4 * e], a[4 * e + 1], a[4 * e + 2], a[4 * e + 3]);
+                    o[4 + e] = make_uint4(b[4 * e], b[4 * e + 1], b[4 * e + 2], b[4 * e + 3]);
                 }
+                o[8] = make_uint4(c[0], c[1], c[2], c[3]);
+                o[9] = make_uint4(c[4], c[5], c[6], c[7]);
+            } else {
+                const float *v = (const float *)a, *v2 = (const float *)b, *v3 = (const float *)c;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    o[e] = make_uint4(pack_bf16x2<false>(v[8 * e], v[8 * e + 1]), pack_bf16x2<false>(v[8 * e + 2], v[8 * e + 3]),
+                                      pack_bf16x2<false>(v[8 * e + 4], v[8 * e + 5]), pack_bf16x2<false>(v[8 * e + 6], v[8 * e + 7]));
+                    o[2 + e] = make_uint4(
+                        pack_bf16x2<false>(v2[8 * e], v2[8 * e + 1]), pack_bf16x2<false>(v2[8 * e + 2], v2[8 * e + 3]),
+                        pack_bf16x2<false>(v2[8 * e + 4], v2[8 * e + 5]), pack_bf16x2<false>(v2[8 * e + 6], v2[8 * e + 7]));
+                }
+                o[4] = make_uint4(pack_bf16x2<false>(v3[0], v3[1]), pack_bf16x2<false>(v3[2], v3[3]),
+                                  pack_bf16x2<false>(v3[4], v3[5]), pack_bf16x2<false>(v3[6], v3[7]));
+            }
+            constexpr int kParts = kGuideOut * (int)sizeof(Out) / 16;
+            if constexpr (Features::kContiguous) {
+                uint4 *srow = (uint4 *)(buf + r * kGuideOut * (uint32_t)sizeof(Out));
+#pragma unroll
+                for (int e = 0; e < kParts; ++e) srow[e] = o[e];
+                umma::fence_proxy_async();
+            } else if (row < n) {
+                uint4 *dst = (uint4 *)(out + (size_t)feat.out_row(row) * kGuideOut);
+#pragma unroll
+                for (int e = 0; e < kParts; ++e) dst[e] = o[e];
             }
         }
         // the accumulator and the buffer are reused by the next tile
         umma::fence_before_sync();
         group_sync(bar_id);
+        if constexpr (Features::kContiguous) {
+            if (gtid == 0) {
+                const uint32_t rows = min(kMlpTile, n - t * kMlpTile);
+                umma::bulk_store(out + (size_t)feat.out_row(t * kMlpTile) * kGuideOut, bbase,
+                                 rows * kGuideOut * (uint32_t)sizeof(Out));
+                umma::bulk_commit();
+            }
+        }
 #pragma unroll
         for (int k = 0; k < 7; ++k) f[k] = fn[k];
     }
@@ -484,6 +522,7 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, Out *
         umma::mbar_wait(bar, phase ^ 1u);
         atomicExch(err, 1u);
     }
+    umma::bulk_wait_all();   // this thread's output copies are done
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();

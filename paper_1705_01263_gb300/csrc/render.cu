@@ -1007,6 +1007,7 @@ constexpr uint32_t kRecPending = 0x80000000u;
 // by row, reading the queue length on the device, so that no host round trip
 // sizes the launch.
 struct PathFeatures {
+    static constexpr bool kContiguous = false;   // output rows are path slots
     RenderParams P;
     Pool pool;
     float3 lo, hi;
@@ -2682,6 +2683,7 @@ __global__ void k_copy_u32(const uint32_t *src, uint32_t *dst, uint32_t n) {
 // network inputs of job j's paths: range [starts[j], ends[j]) of the sorted
 // queue; no rows while the job's mixture probability is zero
 struct JobPathFeatures {
+    static constexpr bool kContiguous = false;   // output rows are path slots
     const BatchJob *jobs;
     const BatchGuide *guides;
     Pool pool;

@@ -144,5 +144,27 @@ __device__ __forceinline__ void tmem_wait_ld32(uint32_t *a, uint32_t *b) {
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t *a) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
+                   "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]),
+                   "+r"(a[15])
+                 :
+                 : "memory");
+}
+
+// Shared -> global bulk copy (the async proxy: the caller fences its
+// shared-memory writes with fence_proxy_async first). Both addresses 16-byte
+// aligned, bytes a multiple of 16. Copies join the thread's bulk group on
+// bulk_commit; bulk_wait_read returns once their sources have been read
+// (the shared memory may be rewritten), bulk_wait_all once they are done.
+__device__ __forceinline__ void bulk_store(void *gdst, uint32_t ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 }  // namespace umma
 }  // namespace rtg
