@@ -437,9 +437,19 @@ rt_status rt_guide_save(const rt_guide *guide, void *host_buffer);
 rt_status rt_guide_load(rt_guide *guide, const void *host_buffer);
 /* Batched inference: DEVICE features (n x 7 floats in [0,1]: position in the
  * scene box, outgoing direction, normal) -> raw network outputs (n x 40
- * floats, device). */
+ * floats, device). Waits for `stream`; RT_TIMEOUT if a tensor-core
+ * completion wait inside the kernel ran out (the outputs are then invalid). */
 rt_status rt_guide_infer(const rt_guide *guide, const float *features, int64_t n, float *raw,
                          void *stream);
+/* As rt_guide_infer, but only enqueued on `stream` (returns at once, no
+ * wait): a completion-wait timeout is recorded in the guide and reported by
+ * the next rt_guide_check or rt_guide_infer. The buffers must stay valid
+ * until the stream reaches the launch. */
+rt_status rt_guide_infer_async(const rt_guide *guide, const float *features, int64_t n, float *raw,
+                               void *stream);
+/* Waits for `stream`; RT_TIMEOUT (and the record cleared) if an earlier
+ * asynchronous call on this guide timed out, else RT_OK. */
+rt_status rt_guide_check(const rt_guide *guide, void *stream);
 /* Loss and gradient on a DEVICE batch (features n x 7, wi n x 3, weight n);
  * grad (device, num_params floats) receives d loss / d weight, *loss (host)
  * the batch loss. Does not update the weights. Synchronous. */

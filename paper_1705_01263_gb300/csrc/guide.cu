@@ -504,6 +504,20 @@ extern "C" rt_status rt_guide_infer(const rt_guide *gc, const float *features, i
     return check_err(g, st);
 }
 
+extern "C" rt_status rt_guide_infer_async(const rt_guide *gc, const float *features, int64_t n, float *raw,
+                                          void *stream) {
+    rt_guide *g = const_cast<rt_guide *>(gc);
+    if (!g || (n > 0 && (!features || !raw)) || n < 0) { set_error("rt_guide_infer_async: invalid argument"); return RT_INVALID_ARG; }
+    if (n == 0) return RT_OK;
+    return guide_infer_async(g, features, n, raw, (cudaStream_t)stream);
+}
+
+extern "C" rt_status rt_guide_check(const rt_guide *gc, void *stream) {
+    rt_guide *g = const_cast<rt_guide *>(gc);
+    if (!g) { set_error("rt_guide_check: invalid argument"); return RT_INVALID_ARG; }
+    return check_err(g, (cudaStream_t)stream);
+}
+
 extern "C" rt_status rt_debug_guide_infer_layers(const rt_guide *gc, const float *features, int64_t n, float *raw,
                                                  void *stream) {
     rt_guide *g = const_cast<rt_guide *>(gc);

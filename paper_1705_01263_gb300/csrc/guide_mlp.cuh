@@ -284,17 +284,22 @@ __device__ void mlp_tiles(const MlpWeights &w, const Features &feat, float *raw,
 // lanes 32 (w % 4) + 0..31, its rows), each group with its own 64
 // tensor-memory columns, mbarrier and named barrier (ids 1..kMiGroups),
 // sharing the weights. A group loads the next tile's features before it
-// works on the current one, so that their latency overlaps the products. A group's shared buffer is 128 x 112 BF16: layer 1 runs in two K
-// halves, the one-blob columns 0..111 then 112..223 encoded into the same
-// buffer (the second after the first product has completed, the products
-// accumulating in tensor memory), and the hidden activations (128 x 64) then
-// overlay it. While one group waits on its tensor-core product the others
-// encode, read back or store. Outputs: 40 floats per row (row stride
-// kGuideOut).
-constexpr uint32_t kMiHalfK = kGuideIn / 2;                                // 112
-constexpr uint32_t kMiBuf = kMlpTile * kMiHalfK * 2;                       // 28,672 bytes
+// works on the current one, so that their latency overlaps the products.
+// A group's shared buffer is 128 x 80 BF16: layer 1 runs in three K chunks,
+// the one-blob columns 0..79, 80..159 and 160..223 encoded in turn into the
+// same buffer (each after the previous product has completed, the products
+// accumulating in tensor memory); the hidden activations (128 x 64) and at
+// the end the tile's output rows then overlay it. Six tiles are in flight per
+// SM (the weights and six buffers fill 182 KB of shared memory and the six
+// accumulators 384 tensor-memory columns): each product takes ~1,300 cycles
+// from issue to the completion seen by the group, most of it latency, so the
+// throughput comes from how many groups wait at once. While one group waits
+// on its tensor-core product the others encode, read back or store.
+constexpr uint32_t kMiChunkK = 80;                                         // layer-1 K per product
+static_assert((kGuideIn + kMiChunkK - 1) / kMiChunkK == 3, "layer 1 runs as three chunk products");
+constexpr uint32_t kMiBuf = kMlpTile * kMiChunkK * 2;                      // 20,480 bytes
 constexpr uint32_t kMiGroup0 = kMlpX;                                      // after the weights (59,392)
-constexpr uint32_t kMiGroups = 5;
+constexpr uint32_t kMiGroups = 6;
 constexpr uint32_t kMiOutRow = kGuideOut * 4;                              // an output row, bytes (FP32)
 static_assert(kMlpTile * kMiOutRow <= kMiBuf, "output staging fits the group buffer");
 constexpr uint32_t kMiThreads = 128 * kMiGroups;
@@ -302,7 +307,7 @@ constexpr uint32_t kMiTmemCols = 64 * kMiGroups <= 256 ? 256 : 512;       // a p
 // weight-image mbarrier, one mbarrier per group, TMEM address
 constexpr uint32_t kMiBar = kMiGroup0 + kMiGroups * kMiBuf;
 constexpr uint32_t kMiBarBytes = 16 + 8 * kMiGroups + 16;
-constexpr uint32_t kMlpInferSmem = kMiBar + kMiBarBytes;                   // 202,888 bytes
+constexpr uint32_t kMlpInferSmem = kMiBar + kMiBarBytes;                   // 182,352 bytes
 static_assert(kMlpInferSmem <= 227 * 1024, "inference kernel shared memory");
 
 __device__ __forceinline__ void group_sync(uint32_t id) {
@@ -330,16 +335,23 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return d;
 }
 
-// Layer-1 product over one K half: D (+)= A[128 x 112] * W1[:, k0 .. k0 + 111]^T.
-__device__ __forceinline__ void mlp_issue_half(uint32_t taddr, uint32_t a0, uint32_t w1, uint32_t half, uint64_t *bar) {
+// Width of layer-1 K chunk c (80, 80, 64).
+__host__ __device__ constexpr uint32_t mlp_chunk_k(uint32_t c) {
+    return (c + 1) * kMiChunkK <= (uint32_t)kGuideIn ? kMiChunkK : (uint32_t)kGuideIn - c * kMiChunkK;
+}
+
+// Layer-1 product over K chunk c: D (+)= A[128 x kc] * W1[:, 80 c .. 80 c + kc - 1]^T,
+// A in the chunk buffer (rows of kMiChunkK elements).
+__device__ __forceinline__ void mlp_issue_chunk(uint32_t taddr, uint32_t a0, uint32_t w1, uint32_t c, uint64_t *bar) {
     const uint32_t idesc = umma::make_idesc_bf16(kMlpTile, kGuideHid);
-    const uint32_t sbo_a = kMiHalfK / 8 * 128, sbo_b = kGuideIn / 8 * 128;
-    const uint32_t b0 = w1 + half * (kMiHalfK / 8) * 128;
+    const uint32_t sbo_a = kMiChunkK / 8 * 128, sbo_b = kGuideIn / 8 * 128;
+    const uint32_t b0 = w1 + c * (kMiChunkK / 8) * 128;
+    const uint32_t kc = mlp_chunk_k(c);
     umma::fence_after_sync();
-    for (uint32_t kk = 0; kk < kMiHalfK / 16; ++kk) {
+    for (uint32_t kk = 0; kk < kc / 16; ++kk) {
         const uint64_t ad = umma::make_desc(a0 + kk * 256, 128, sbo_a);
         const uint64_t bd = umma::make_desc(b0 + kk * 256, 128, sbo_b);
-        umma::mma_bf16(taddr, ad, bd, idesc, (half > 0 || kk > 0) ? 1u : 0u);
+        umma::mma_bf16(taddr, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
     }
     umma::mma_commit(bar);
 }
@@ -375,19 +387,21 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, Out *
         phase ^= 1u;
         return group_all(bar_id, done);
     };
-    // this row's 16-byte chunk j of a 112-column K half sits at row_off + 128 j
-    unsigned char *const row_half = buf + umma::kmajor_offset(r, 0u, kMiHalfK);
+    // this row's 16-byte piece j of a layer-1 chunk sits at row_chunk + 128 j
+    unsigned char *const row_chunk = buf + umma::kmajor_offset(r, 0u, kMiChunkK);
     unsigned char *const row_hid = buf + umma::kmajor_offset(r, 0u, kGuideHid);
-    // one-blob columns [112 h, 112 h + 112) of this row into the buffer; the
-    // chunks are unrolled so that each one's feature and bins are constants
-    auto encode_half = [&](const float *f, auto half) {
-        constexpr uint32_t c0 = decltype(half)::value * kMiHalfK;
+    // one-blob columns [80 c, 80 c + kc) of this row into the buffer; the
+    // 8-column pieces are unrolled so that each one's feature and bins are
+    // constants
+    auto encode_chunk = [&](const float *f, auto chunk) {
+        constexpr uint32_t c0 = decltype(chunk)::value * kMiChunkK;
+        constexpr uint32_t kc = mlp_chunk_k(decltype(chunk)::value);
 #pragma unroll
-        for (uint32_t j = 0; j < kMiHalfK / 8; ++j) {
+        for (uint32_t j = 0; j < kc / 8; ++j) {
             const uint32_t col = c0 + 8u * j;
             float g8[8];
             oneblob_chunk(f[col / kGuideBins], (int)(col % kGuideBins), g8);
-            *(uint4 *)(row_half + 128u * j) =
+            *(uint4 *)(row_chunk + 128u * j) =
                 make_uint4(pack_bf16x2<false>(g8[0], g8[1]), pack_bf16x2<false>(g8[2], g8[3]),
                            pack_bf16x2<false>(g8[4], g8[5]), pack_bf16x2<false>(g8[6], g8[7]));
         }
@@ -413,11 +427,14 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, Out *
             umma::bulk_wait_read();
             group_sync(bar_id);
         }
-        encode_half(f, std::integral_constant<uint32_t, 0>{});
-        if (gtid == 0) mlp_issue_half(taddr, bbase, sbase + kMlpW1, 0u, bar);
+        encode_chunk(f, std::integral_constant<uint32_t, 0>{});
+        if (gtid == 0) mlp_issue_chunk(taddr, bbase, sbase + kMlpW1, 0u, bar);
         if (!(ok = wait_layer())) break;
-        encode_half(f, std::integral_constant<uint32_t, 1>{});
-        if (gtid == 0) mlp_issue_half(taddr, bbase, sbase + kMlpW1, 1u, bar);
+        encode_chunk(f, std::integral_constant<uint32_t, 1>{});
+        if (gtid == 0) mlp_issue_chunk(taddr, bbase, sbase + kMlpW1, 1u, bar);
+        if (!(ok = wait_layer())) break;
+        encode_chunk(f, std::integral_constant<uint32_t, 2>{});
+        if (gtid == 0) mlp_issue_chunk(taddr, bbase, sbase + kMlpW1, 2u, bar);
         if (!(ok = wait_layer())) break;
         // layers 2..5: read back, ReLU -> BF16 -> the activation buffer
         // (overlaying the one-blob buffer), next product

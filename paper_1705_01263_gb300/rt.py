@@ -94,7 +94,7 @@ EXPORTED = [
     "rt_film_clear", "rt_film_next_iteration", "rt_film_seek", "rt_film_buffers", "rt_film_resolve", "rt_render",
     "rt_render_static", "rt_render_batch", "rt_autotune", "rt_sample_index", "rt_halton", "rt_divide_u64_host", "rt_guide_create", "rt_guide_destroy",
     "rt_guide_num_params", "rt_guide_get_params", "rt_guide_set_params", "rt_guide_state_size", "rt_guide_save",
-    "rt_guide_load", "rt_guide_infer", "rt_guide_loss_grad", "rt_guide_train_step", "rt_last_error",
+    "rt_guide_load", "rt_guide_infer", "rt_guide_infer_async", "rt_guide_check", "rt_guide_loss_grad", "rt_guide_train_step", "rt_last_error",
     "rt_status_string", "rt_gemm_bf16", "rt_render_probes", "rt_render_two_way",
 ]
 
@@ -172,6 +172,8 @@ def _declare(L):
         "rt_guide_save": [vp, vp],
         "rt_guide_load": [vp, vp],
         "rt_guide_infer": [vp, vp, i64, vp, vp],
+        "rt_guide_infer_async": [vp, vp, i64, vp, vp],
+        "rt_guide_check": [vp, vp],
         "rt_guide_loss_grad": [vp, vp, vp, vp, i64, vp, C.POINTER(C.c_float), vp],
         "rt_guide_train_step": [vp, vp, vp, vp, i64, vp],
     }.items():
@@ -528,6 +530,16 @@ class Guide:
         raw = torch.empty((n, 40), dtype=torch.float32, device=features.device)
         check(lib().rt_guide_infer(self.handle, features.data_ptr(), n, raw.data_ptr(), _stream(stream)))
         return raw
+
+    def infer_async(self, features, raw, stream=None):
+        """Enqueue the fused inference into `raw` (n x 40, device) without
+        waiting; check() reports a completion-wait timeout."""
+        check(lib().rt_guide_infer_async(self.handle, features.data_ptr(), features.shape[0], raw.data_ptr(),
+                                         _stream(stream)))
+        return raw
+
+    def check(self, stream=None):
+        check(lib().rt_guide_check(self.handle, _stream(stream)))
 
     def infer_layers(self, features, stream=None):
         """Test hook: the same outputs layer by layer through the GEMM path

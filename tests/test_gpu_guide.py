@@ -83,6 +83,11 @@ def test_fused_inference_equals_layer_by_layer(n):
     a = guide.infer(x).cpu().numpy()
     b = guide.infer_layers(x).cpu().numpy()
     assert np.isfinite(a).all()
+    # the asynchronous entry point runs the same kernel
+    raw = torch.full((n, 40), float("nan"), device="cuda")
+    guide.infer_async(x, raw)
+    guide.check()
+    assert np.array_equal(raw.cpu().numpy(), a)
     assert np.abs(a - b).max() <= 1e-5 * max(1.0, np.abs(b).max()), np.abs(a - b).max()
     # after training steps the weights the fused kernel stages change too
     wi = torch.nn.functional.normalize(torch.randn(n, 3, device="cuda"), dim=1)
