@@ -283,7 +283,7 @@ def scheduler_sweep(scene, cam, spp, depth, pools=(1 << 22, 1 << 23, 1 << 24, 1 
     for name, kw in (("uncompressed", {}), ("compressed", {"state_compression": True})):
         r = timed(**kw)
         r["of_whole_request"] = r["Mpaths_per_s"] / whole
-        r["state_bytes_per_path"] = 128 if kw else 164
+        r["state_bytes_per_path"] = 132 if kw else 168
         img = film.resolve()[0].double()
         r["image_rel_l1_vs_uncompressed"] = float((img - ref).abs().sum() / ref.abs().sum())
         out[f"state_{name}"] = r

@@ -184,7 +184,7 @@ typedef struct {
                               * the scene's bound and cosine directions (A/B) */
     int32_t state_compression; /* rt_render, scheduler 0 (A/B, Sec. 3.1.1): ray and shadow directions as
                               * 16:16 octahedral codes, throughput and shadow contributions as BF16, the
-                              * vertex number in 16 bits (128 instead of 164 bytes of state per path);
+                              * vertex number in 16 bits (132 instead of 168 bytes of state per path);
                               * RT_NOT_SUPPORTED with iteration sets, guiding or megakernel_only */
 } rt_render_opts;
 

@@ -35,7 +35,10 @@ struct Ctrl {
     // regeneration (Sec. 3.1.3): paths that ended this step, emptied slots,
     // tasks of the window issued so far and in total, and the stop state
     uint32_t n_dead, n_free, task_next, n_tasks;
-    uint32_t stop, regen_sets, pad2[2];
+    uint32_t stop, regen_sets;
+    // entries of Pool::split written by the closest-hit kernel: hits in the
+    // low 32 bits, misses in the high 32 bits (one atomic per warp for both)
+    unsigned long long split_counts;
     unsigned long long deadline_ns;   // %globaltimer value after which no task is issued
 };
 
@@ -71,6 +74,11 @@ struct Pool {
     uint32_t *shd_c;
     uint2 *shc_c;
     int compact;
+    // The extension queue as the closest-hit kernel leaves it for shading
+    // (null = off): the paths whose ray hit a surface from the front, those
+    // whose ray left the scene from the back, so that shading warps run one
+    // of the two branches instead of both.
+    uint32_t *split;
 };
 
 RT_D uint32_t bf16x2_pack(float a, float b) {
@@ -217,6 +225,7 @@ __global__ void k_raygen(RenderParams P, Pool pool, uint64_t t0, uint32_t n, uin
         c->fetch_ext = 0;
         c->fetch_shadow = 0;
         c->fetch_shade = 0;
+        c->split_counts = 0;
         c->n_train = 0;
         c->tail_threshold = tail_threshold;
         c->tail = n < tail_threshold ? 1u : 0u;
@@ -255,11 +264,28 @@ __global__ void __launch_bounds__(128) k_trace_ext(DevScene sc, Pool pool) {
     }
 }
 
+// Pool::split entry of every lane with `valid` (one atomic per warp): hits
+// from the front in queue order, misses from the back.
+RT_D void split_append(uint32_t *split, Ctrl *c, uint32_t n, bool valid, bool hit, uint32_t q) {
+    const uint32_t full = 0xFFFFFFFFu, lane = lane_id();
+    const uint32_t hm = __ballot_sync(full, valid && hit), mm = __ballot_sync(full, valid && !hit);
+    unsigned long long b = 0;
+    if (lane == 0)
+        b = atomicAdd(&c->split_counts, (unsigned long long)__popc(hm) | ((unsigned long long)__popc(mm) << 32));
+    b = __shfl_sync(full, b, 0);
+    const uint32_t hb = (uint32_t)b, mb = (uint32_t)(b >> 32);
+    const uint32_t below = (1u << lane) - 1u;
+    if (valid && hit) split[hb + (uint32_t)__popc(hm & below)] = q;
+    if (valid && !hit) split[n - 1u - (mb + (uint32_t)__popc(mm & below))] = q;
+}
+
 // Capped at 64 registers (8 blocks of 128 per SM): the kernel is latency
 // bound, and the extra resident warps outweigh a few spilled registers.
 template <bool kLb>
 __global__ void __launch_bounds__(128, 8) k_shade(RenderParams P, Pool pool, const uint32_t *sorted) {
     Ctrl *c = pool.ctrl;
+    // the closest-hit kernel of this step is done with the split counters
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->split_counts = 0;
     if (c->tail) return;
     const uint32_t n = c->n_ext;
     const uint32_t cur = c->cur;
@@ -317,21 +343,27 @@ __global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_ext_simple(Dev
     for (;;) {
         uint32_t base = warp_fetch32(&c->fetch_ext);
         if (base >= n) break;
-        uint32_t i = base + lane_id();
-        if (i >= n) continue;
-        uint32_t q = queue[i];
-        float4 o = pool.ray_o[q], d = ld_dir(pool, q);
-        Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, INFINITY};
-        Hit h;
-        h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
-        TraceResult tr = kTwoLevel    ? traverse_two_level<false>(sc, r, h)
-                         : kPostpone  ? traverse_pp<false>(sc.nodes, sc.tris, r, h)
-                         : kSmemStack ? traverse<false, SharedStack>(sc.nodes, sc.tris, 0u, r, h, 0u, &sst)
-                                      : traverse<false>(sc.nodes, sc.tris, 0u, r, h);
-        overflow |= tr.overflow;
-        if (kCount) { nodes += tr.nodes; tris += tr.tris; }
-        pool.hit[q] = make_float4(__uint_as_float(h.prim), h.t, h.b1, h.b2);
-        if (kTwoLevel) pool.hit_inst[q] = h.inst;
+        const uint32_t i = base + lane_id();
+        const bool valid = i < n;
+        uint32_t q = 0;
+        bool hit = false;
+        if (valid) {
+            q = queue[i];
+            float4 o = pool.ray_o[q], d = ld_dir(pool, q);
+            Ray r{v3(o.x, o.y, o.z), v3(d.x, d.y, d.z), 0.f, INFINITY};
+            Hit h;
+            h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
+            TraceResult tr = kTwoLevel    ? traverse_two_level<false>(sc, r, h)
+                             : kPostpone  ? traverse_pp<false>(sc.nodes, sc.tris, r, h)
+                             : kSmemStack ? traverse<false, SharedStack>(sc.nodes, sc.tris, 0u, r, h, 0u, &sst)
+                                          : traverse<false>(sc.nodes, sc.tris, 0u, r, h);
+            overflow |= tr.overflow;
+            if (kCount) { nodes += tr.nodes; tris += tr.tris; }
+            pool.hit[q] = make_float4(__uint_as_float(h.prim), h.t, h.b1, h.b2);
+            if (kTwoLevel) pool.hit_inst[q] = h.inst;
+            hit = h.prim != RT_MISS;
+        }
+        if (pool.split) split_append(pool.split, c, n, valid, hit, q);
     }
     if (overflow) atomicOr(&c->overflow, 1u);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&c->ext_rays, (unsigned long long)n);
@@ -765,6 +797,7 @@ __global__ void k_regen_init(RenderParams P, Pool pool, uint64_t t0, uint32_t n_
         c->n_ext = k;
         c->n_next = c->n_shadow = c->cur = 0;
         c->fetch_ext = c->fetch_shadow = c->fetch_shade = 0;
+        c->split_counts = 0;
         c->n_dead = 0;
         c->n_free = cap - k;
         c->task_next = k;
@@ -1220,6 +1253,13 @@ inline TraceKernels trace_kernels(bool count, int variant, bool two_level, int b
     return count ? trace_kernels_of<true, false, false>(block) : trace_kernels_of<false, false, false>(block);
 }
 
+// Whether the closest-hit kernel of `variant` (trace_kernels above) fills
+// Pool::split: the one-ray-per-thread kernels do (variants 0, 2, 4, 6, 7 and
+// every two-level scene), the lane-refill and persistent ones do not.
+inline bool variant_splits(int variant, bool two_level) {
+    return two_level || !(variant == 1 || variant == 3 || variant == 5);
+}
+
 // Threads per block of the state kernels: 0 (128) or a multiple of 32 up to
 // the kernels' launch bound of 128.
 inline bool valid_block(uint32_t b) { return b == 0 || (b % 32 == 0 && b <= 128); }
@@ -1239,6 +1279,7 @@ struct PoolAlloc {
     // regeneration arrays (task per slot, dead and free slot lists): set in
     // the view only by the scheduler that uses them
     uint32_t *task = nullptr, *qd = nullptr;
+    uint32_t *split = nullptr;   // Pool::split storage, set in the view by the renders that use it
     void *block = nullptr;
     uint32_t capacity = 0;
     bool compact = false;   // compressed layout of the direction, throughput and shadow arrays
@@ -1248,11 +1289,12 @@ struct PoolAlloc {
 };
 
 // Device bytes of one path's state in the pool (eight float4 arrays, the
-// sequence index, pixel, instance of the hit, three queue entries and the
-// regeneration scheduler's task and dead entries), and of the scratch copy
+// sequence index, pixel, instance of the hit, four queue entries (the two
+// extension queues, the shadow queue, the hit/miss-split shading queue) and
+// the regeneration scheduler's task and dead entries), and of the scratch copy
 // of a continuing path that a refill moves (regeneration with a pool smaller
 // than the request).
-constexpr size_t kPoolBytesPerPath = 8 * sizeof(float4) + sizeof(uint2) + 4 + 4 + 3 * 4 + 2 * 4;
+constexpr size_t kPoolBytesPerPath = 8 * sizeof(float4) + sizeof(uint2) + 4 + 4 + 4 * 4 + 2 * 4;
 constexpr size_t kRegenScratchBytesPerPath = 4 * sizeof(uint4) + sizeof(uint2) + 4 + 4;
 
 // Pool capacity when the caller leaves it to the library: every requested
@@ -1277,7 +1319,7 @@ rt_status ensure_pool(PoolAlloc &pa, uint32_t capacity, bool compact = false) {
     // four float4 arrays always (origin, radiance, hit, shadow origin); four
     // more, or their compressed forms (8 + 8 + 4 + 8 bytes per path)
     size_t bytes = 4 * f4 + (compact ? P * 28 + 4 * 256 : 4 * f4) + P * sizeof(uint2) + P * 4 /*pixel*/ +
-                   P * 4 /*hit_inst*/ + 3 * P * 4 /*queues*/ + 2 * P * 4 /*regeneration*/ + 64 * 256;
+                   P * 4 /*hit_inst*/ + 4 * P * 4 /*queues*/ + 2 * P * 4 /*regeneration*/ + 64 * 256;
     cudaError_t e = cudaMalloc(&pa.block, bytes);
     if (e != cudaSuccess) { set_error("path-state pool allocation failed"); return RT_OOM; }
     char *p = (char *)pa.block;
@@ -1299,6 +1341,7 @@ rt_status ensure_pool(PoolAlloc &pa, uint32_t capacity, bool compact = false) {
     v.hit_inst = (uint32_t *)take(P * 4);
     v.q[0] = (uint32_t *)take(P * 4); v.q[1] = (uint32_t *)take(P * 4); v.qs = (uint32_t *)take(P * 4);
     pa.task = (uint32_t *)take(P * 4); pa.qd = (uint32_t *)take(P * 4);
+    pa.split = (uint32_t *)take(P * 4);
     v.capacity = capacity;
     pa.capacity = capacity;
     if ((size_t)(p - (char *)pa.block) > bytes) { set_error("pool layout overflow"); return RT_CUDA_ERROR; }
@@ -1588,8 +1631,9 @@ static rt_status render_regen(const rt_scene *s, const rt_camera *cam, uint32_t 
 
     const int gb = o.block_size ? (int)o.block_size : 128;
     const bool prof = o.profile >= 1, count = o.profile >= 2;
-    const TraceKernels tk =
-        trace_kernels(count, (o.trace_kernel == 1 || o.trace_kernel == 5) ? 0 : o.trace_kernel, s->dev.two_level, gb);
+    const int variant = (o.trace_kernel == 1 || o.trace_kernel == 5) ? 0 : o.trace_kernel;
+    const TraceKernels tk = trace_kernels(count, variant, s->dev.two_level, gb);
+    pool.split = variant_splits(variant, s->dev.two_level) ? rc->pool.split : nullptr;
     const int g_shade = grid_persistent(k_shade<true>, gb, 0);
     const int g_regen = grid_for(k_regen, 256, cap);
     const int g_init = grid_for(k_regen_init, 256, cap);
@@ -1691,7 +1735,7 @@ static rt_status render_regen(const rt_scene *s, const rt_camera *cam, uint32_t 
                 e = mark(0);
                 tk.ext<<<tk.grid_ext, gb, tk.smem, st>>>(s->dev, pool, rsorted);
                 done_ev(e);
-                const uint32_t *sorted = rsorted;
+                const uint32_t *sorted = pool.split ? pool.split : rsorted;
                 if (o.sort_by_material) {
                     e = mark(4);
                     RT_CUDA_TRY(cudaMemsetAsync(rc->sort_hist, 0, sizeof(uint32_t) * nkeys_mat, st));
@@ -1970,6 +2014,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     // lane refill (incoherent rays that end at very different times)
     const TraceKernels tk = trace_kernels(count, o.trace_kernel == 5 ? 0 : o.trace_kernel, s->dev.two_level, gb);
     const TraceKernels tk_late = o.trace_kernel == 5 && !s->dev.two_level ? trace_kernels(count, 3, false, gb) : tk;
+    pool.split = o.trace_kernel != 5 && variant_splits(o.trace_kernel, s->dev.two_level) ? rc->pool.split : nullptr;
     const uint32_t nmat = s->num_materials;
     const uint32_t nkeys_mat = nmat + 1, nkeys_ray = 8u * 512u;
     const int g_hist = grid_for(k_sort_scatter<RayKey>, 256, cap);
@@ -2045,7 +2090,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
                     k_trace_ext<false><<<g_trace, gb, smem, st>>>(s->dev, pool);
                 }
                 done(e);
-                const uint32_t *sorted = rsorted;
+                const uint32_t *sorted = pool.split ? pool.split : rsorted;
                 if (o.sort_by_material) {
                     e = mark(4);
                     RT_CUDA_TRY(cudaMemsetAsync(rc->sort_hist, 0, sizeof(uint32_t) * nkeys_mat, st));
