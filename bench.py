@@ -903,7 +903,8 @@ def main():
                          "1 persistent warps refilling lanes; 2 one ray per thread with a shared-memory stack; "
                          "3 lane refill between node visits for both; 4 one ray per thread for both; "
                          "5 as 0 for camera rays, as 3 for later bounces; 6 closest hit one ray per thread with "
-                         "postponed triangle tests, shadow rays as 0; 7 postponed triangle tests for both")
+                         "postponed triangle tests, shadow rays as 0; 7 postponed triangle tests for both; 8 closest hit with "
+                         "per-child stack entries, nearest child next, far entries dropped on pop")
     ap.add_argument("--megakernel-only", action="store_true", help="A/B baseline: megakernel per iteration set")
     ap.add_argument("--sort-by-material", action="store_true", help="A/B: material-sorted shading queue")
     ap.add_argument("--sort-rays", action="store_true", help="A/B: reorder extension rays by octant and origin cell")
@@ -1144,7 +1145,9 @@ def main():
                                         "camera rays one per thread, later bounces with lane refill",
                                         "closest hit one ray per thread with postponed triangle tests, "
                                         "shadow rays with lane refill",
-                                        "one ray per thread with postponed triangle tests"][args.trace_kernel],
+                                        "one ray per thread with postponed triangle tests",
+                                        "closest hit one ray per thread, nearest child next, far stack entries "
+                                        "dropped"][args.trace_kernel],
                        "ray_order": "octant + origin cell" if args.sort_rays else "compaction order",
                        "schedule": "megakernel only" if args.megakernel_only else "wavefront + megakernel tail",
                        "shading_queue": "material-sorted" if args.sort_by_material else "compaction order"},

@@ -172,8 +172,10 @@ typedef struct {
                               * 4: one ray per thread for both; 5: as 0 for camera rays, as 3 for later
                               * bounces (the regeneration scheduler runs 5 as 0); 6: as 0 with the
                               * closest-hit triangle tests postponed while few lanes want them; 7: both
-                              * kinds one ray per thread with postponed triangle tests. Two-level scenes
-                              * always use 0's closest-hit kernel for both. */
+                              * kinds one ray per thread with postponed triangle tests; 8: as 0 with one
+                              * stack entry per child, the nearest child next and entries beyond the
+                              * best hit dropped on pop. Two-level scenes always use 0's closest-hit
+                              * kernel for both. */
     int32_t sort_rays;       /* 1: reorder extension rays by direction octant and origin cell (A/B) */
     int32_t scheduler;       /* 0: regeneration (Sec. 3.1.3): a bounded pool whose ended paths are
                               * refilled with the next tasks; 1: iteration sets, each held whole in

@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(128, 8) k_shade(RenderParams P, Pool pool, con
 // single-level kernels carry none of its state and need about a third fewer
 // registers, which raises the resident warps per SM from 20 to 32 (the launch
 // bounds hold them at 64 registers, 8 blocks of 128 per SM).
-template <bool kCount, bool kSmemStack, bool kTwoLevel, bool kPostpone = false>
+template <bool kCount, bool kSmemStack, bool kTwoLevel, bool kPostpone = false, bool kNear = false>
 __global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_ext_simple(DevScene sc, Pool pool, const uint32_t *sorted) {
     Ctrl *c = pool.ctrl;
     if (c->tail) return;
@@ -354,6 +354,7 @@ __global__ void __launch_bounds__(128, kTwoLevel ? 5 : 8) k_trace_ext_simple(Dev
             Hit h;
             h.prim = RT_MISS; h.inst = 0; h.t = INFINITY; h.b1 = h.b2 = 0.f;
             TraceResult tr = kTwoLevel    ? traverse_two_level<false>(sc, r, h)
+                             : kNear      ? traverse_near(sc.nodes, sc.tris, r, h)
                              : kPostpone  ? traverse_pp<false>(sc.nodes, sc.tris, r, h)
                              : kSmemStack ? traverse<false, SharedStack>(sc.nodes, sc.tris, 0u, r, h, 0u, &sst)
                                           : traverse<false>(sc.nodes, sc.tris, 0u, r, h);
@@ -1203,10 +1204,10 @@ struct TraceKernels {
     size_t smem;
 };
 
-template <bool kCount, bool kSmem, bool kTwo, bool kPostpone = false>
+template <bool kCount, bool kSmem, bool kTwo, bool kPostpone = false, bool kNear = false>
 TraceKernels trace_kernels_of(int block) {
     TraceKernels k;
-    k.ext = k_trace_ext_simple<kCount, kSmem, kTwo, kPostpone>;
+    k.ext = k_trace_ext_simple<kCount, kSmem, kTwo, kPostpone, kNear>;
     k.shadow = k_trace_shadow_simple<kCount, kSmem, kTwo, kPostpone>;
     k.smem = kSmem ? (size_t)kSharedEntries * block * sizeof(uint2) : 0;
     k.grid_ext = grid_persistent(k.ext, block, k.smem);
@@ -1230,17 +1231,22 @@ TraceKernels refill_kernels(int block) {
 // does not depend on the order of the traversal); 2 both one-shot with the
 // stack top in shared memory; 3 both with lane refill; 4 both one-shot;
 // 6 closest hit one-shot with postponed triangle tests, shadow rays as 0;
-// 7 both one-shot with postponed triangle tests.
+// 7 both one-shot with postponed triangle tests; 8 closest hit one-shot with
+// one stack entry per child, nearest child next and far entries dropped on
+// pop (traverse_near), shadow rays as 0.
 // Two-level scenes always use the one-shot kernels with a thread-local stack.
 inline TraceKernels trace_kernels(bool count, int variant, bool two_level, int block) {
     if (two_level) return count ? trace_kernels_of<true, false, true>(block) : trace_kernels_of<false, false, true>(block);
     if (variant == 3) return count ? refill_kernels<true>(block) : refill_kernels<false>(block);
     if (variant == 7)
         return count ? trace_kernels_of<true, false, false, true>(block) : trace_kernels_of<false, false, false, true>(block);
-    if (variant == 0 || variant == 6) {
+    if (variant == 0 || variant == 6 || variant == 8) {
         TraceKernels k = variant == 6
                              ? (count ? trace_kernels_of<true, false, false, true>(block)
                                       : trace_kernels_of<false, false, false, true>(block))
+                         : variant == 8
+                             ? (count ? trace_kernels_of<true, false, false, false, true>(block)
+                                      : trace_kernels_of<false, false, false, false, true>(block))
                              : (count ? trace_kernels_of<true, false, false>(block) : trace_kernels_of<false, false, false>(block));
         const TraceKernels r = count ? refill_kernels<true>(block) : refill_kernels<false>(block);
         k.shadow = r.shadow;
@@ -1834,7 +1840,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     rt_render_opts o{};
     if (opts_in) o = *opts_in;
     if (spp == 0) return RT_OK;
-    if (o.trace_kernel < 0 || o.trace_kernel > 7) { set_error("rt_render: trace_kernel must be in [0, 7]"); return RT_INVALID_ARG; }
+    if (o.trace_kernel < 0 || o.trace_kernel > 8) { set_error("rt_render: trace_kernel must be in [0, 8]"); return RT_INVALID_ARG; }
     if (!valid_block(o.block_size)) { set_error("rt_render: block_size must be 0 or a multiple of 32 up to 128"); return RT_INVALID_ARG; }
     if (s->dev.two_level) o.trace_kernel = 0;   // the persistent variant is single-level only
     cudaStream_t st = (cudaStream_t)stream;

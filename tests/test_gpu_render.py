@@ -145,7 +145,7 @@ def test_traversal_variants_agree():
     s = rt.Scene(sd)
     a, _, _ = gpu_render(s, cam, 2, 16, trace_kernel=0)
     sa, _, _ = a.download()
-    for k in (1, 3, 4, 5, 6, 7):
+    for k in (1, 3, 4, 5, 6, 7, 8):
         b, _, _ = gpu_render(s, cam, 2, 16, trace_kernel=k)
         sb, _, _ = b.download()
         assert np.array_equal(sa, sb), k
@@ -246,7 +246,7 @@ def test_invalid_arguments():
         rt.rt_render(s, cam, 1, 0, f2)          # max_depth 0
     rt.rt_render(s, cam, 0, 8, f2)              # spp 0 is a no-op
     assert f2.next_iteration() == 0
-    for k in (-1, 8):
+    for k in (-1, 9):
         with pytest.raises(rt.RtError):
             rt.rt_render(s, cam, 1, 8, f2, rt.make_opts(trace_kernel=k))
     assert f2.next_iteration() == 0
