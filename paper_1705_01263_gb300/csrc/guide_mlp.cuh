@@ -371,6 +371,12 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, Out *
     const uint32_t n = feat.count();
     const uint32_t tiles = (n + kMlpTile - 1) / kMlpTile;
     if (kMiGroups * blockIdx.x >= tiles) return;
+    // the first tile's features load while the weights arrive
+    float f[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    {
+        const uint32_t row0 = (kMiGroups * blockIdx.x + g) * kMlpTile + r;
+        if (row0 < n) feat(row0, f);
+    }
     const bool image_ok = mlp_load_image(smem, w.image, (uint64_t *)(smem + kMiBar));
     if (warp == 0) umma::tmem_alloc(s_taddr, kMiTmemCols);
     if (tid < kMiGroups) umma::mbar_init((uint64_t *)(smem + kMiBar + 16) + tid, 1);
@@ -410,11 +416,6 @@ __device__ void mlp_infer_tiles(const MlpWeights &w, const Features &feat, Out *
         group_sync(bar_id);
     };
     const uint32_t stride = kMiGroups * gridDim.x;
-    float f[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    {
-        const uint32_t row0 = (kMiGroups * blockIdx.x + g) * kMlpTile + r;
-        if (row0 < n) feat(row0, f);
-    }
     for (uint32_t t = kMiGroups * blockIdx.x + g; t < tiles && ok; t += stride) {
         const uint32_t row = t * kMlpTile + r;
         float fn[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // the next tile's
