@@ -1260,10 +1260,13 @@ inline TraceKernels trace_kernels(bool count, int variant, bool two_level, int b
 }
 
 // Whether the closest-hit kernel of `variant` (trace_kernels above) fills
-// Pool::split: the one-ray-per-thread kernels do (variants 0, 2, 4, 6, 7 and
-// every two-level scene), the lane-refill and persistent ones do not.
+// Pool::split: the one-ray-per-thread single-level kernels do (variants 0,
+// 2, 4, 6, 7, 8), the lane-refill and persistent ones do not; two-level
+// scenes keep one queue (their kernel runs at 102 registers, and the split
+// measured slower on the instanced many-light field: 639.7 against 661.8
+// Mpaths/s).
 inline bool variant_splits(int variant, bool two_level) {
-    return two_level || !(variant == 1 || variant == 3 || variant == 5);
+    return !two_level && !(variant == 1 || variant == 3 || variant == 5);
 }
 
 // Threads per block of the state kernels: 0 (128) or a multiple of 32 up to
