@@ -1,6 +1,6 @@
 // Fused forward pass of the guiding network on the tensor cores. The
 // training forward (mlp_tiles<true>) works as follows; the inference kernel
-// (mlp_infer_tiles, below) keeps five tiles in flight instead of one. One
+// (mlp_infer_tiles, below) keeps six tiles in flight instead of one. One
 // persistent CTA of 512 threads per SM keeps all five BF16 weight matrices
 // (58 KB, copied in by one bulk copy of a prepared image) in shared memory and walks tiles of 128 rows, four threads per row (part p =
 // warp / 4 of row 32 (warp % 4) + lane), so that each SM sub-partition has
