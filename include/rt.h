@@ -178,8 +178,11 @@ typedef struct {
                               * kernel for both. */
     int32_t sort_rays;       /* 1: reorder extension rays by direction octant and origin cell (A/B) */
     int32_t scheduler;       /* 0: regeneration (Sec. 3.1.3): a bounded pool whose ended paths are
-                              * refilled with the next tasks; 1: iteration sets, each held whole in
-                              * the pool (A/B). Guided rendering and megakernel_only use iteration sets. */
+                              * refilled with the next tasks (a pool of at least 2^21 paths that refills
+                              * runs as two half-pools on two streams unless the call can be stopped or
+                              * sorts its queues; the film is the same); 1: iteration sets, each held
+                              * whole in the pool (A/B). Guided rendering and megakernel_only use
+                              * iteration sets. */
     float regen_fraction;    /* scheduler 0: refill once this fraction of the pool has ended (0 = 0.5,
                               * the paper's rule); must be in [0, 1] */
     int32_t lt_emission;     /* rt_render_two_way: 0 photon aiming (Sec. 2.1.3), 1 uniform emission over

@@ -1377,8 +1377,13 @@ struct RenderCache {
     void *gscr = nullptr;   // RegenScratch storage for gscr_cap paths
     uint32_t gscr_cap = 0;
     uint32_t *stop_host = nullptr, *stop_dev = nullptr;
-    Ctrl *ctrl_ring = nullptr;   // pinned copies of the control block, one per chunk in flight
-    cudaEvent_t chunk_ev[2] = {nullptr, nullptr};
+    Ctrl *ctrl_ring = nullptr;   // pinned copies of the control block, one per chunk in flight (x2 half-pools)
+    cudaEvent_t chunk_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // regeneration as two half-pools: the second half-pool's control block
+    // and stream, and a fork / join event
+    Ctrl *ctrl2 = nullptr;
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     // guided rendering
     uint32_t gcap = 0, gbatch = 0;
     __nv_bfloat16 *gfeat = nullptr;   // network outputs [cap][40] (BF16) of one bounce step
@@ -1394,6 +1399,10 @@ struct RenderCache {
         if (ctrl_ring) cudaFreeHost(ctrl_ring);
         for (cudaEvent_t e : chunk_ev)
             if (e) cudaEventDestroy(e);
+        if (ctrl2) cudaFree(ctrl2);
+        if (st2) cudaStreamDestroy(st2);
+        if (fork_ev) cudaEventDestroy(fork_ev);
+        if (join_ev) cudaEventDestroy(join_ev);
         for (void *p : {(void *)gfeat, (void *)tr_feat, (void *)tr_wi, (void *)tr_w, (void *)grec, (void *)gnrec,
                         (void *)sort_hist, (void *)sort_buf[0], (void *)sort_buf[1]})
             if (p) cudaFree(p);
@@ -1568,6 +1577,27 @@ static RenderCache *cache_of(rt_film *f) {
 // flight finish, and the film receives the contiguous range of tasks that
 // completed (possibly ending inside an iteration; the next call continues
 // there).
+// Slots [off, off + n) of a pool as a pool of their own, with its own
+// control block (every per-slot array offset, the queues included).
+static Pool sub_pool(const Pool &p, uint32_t off, uint32_t n, Ctrl *ctrl) {
+    Pool v = p;
+    auto sh = [&](auto *&a) {
+        if (a) a += off;
+    };
+    sh(v.ray_o); sh(v.ray_d); sh(v.beta); sh(v.L); sh(v.index); sh(v.pixel); sh(v.hit); sh(v.hit_inst);
+    sh(v.sh_o); sh(v.sh_d); sh(v.sh_c); sh(v.q[0]); sh(v.q[1]); sh(v.qs); sh(v.nrec); sh(v.task); sh(v.qd);
+    sh(v.dir_c); sh(v.beta_c); sh(v.shd_c); sh(v.shc_c); sh(v.split);
+    v.ctrl = ctrl;
+    v.capacity = n;
+    return v;
+}
+static RegenScratch sub_scratch(const RegenScratch &g, uint32_t off) {
+    RegenScratch v = g;
+    if (!v.o) return v;
+    v.o += off; v.d += off; v.b += off; v.L += off; v.index += off; v.pixel += off; v.task += off;
+    return v;
+}
+
 static rt_status render_regen(const rt_scene *s, const rt_camera *cam, uint32_t spp, uint32_t max_depth,
                               rt_film *film, const rt_render_opts &o, cudaStream_t st, RenderCache *rc,
                               uint32_t cap) {
@@ -1633,7 +1663,7 @@ static rt_status render_regen(const rt_scene *s, const rt_camera *cam, uint32_t 
         RT_CUDA_TRY(cudaHostAlloc(&rc->stop_host, sizeof(uint32_t), cudaHostAllocMapped));
         RT_CUDA_TRY(cudaHostGetDevicePointer((void **)&rc->stop_dev, rc->stop_host, 0));
     }
-    if (!rc->ctrl_ring) RT_CUDA_TRY(cudaMallocHost(&rc->ctrl_ring, 2 * sizeof(Ctrl)));
+    if (!rc->ctrl_ring) RT_CUDA_TRY(cudaMallocHost(&rc->ctrl_ring, 4 * sizeof(Ctrl)));
     for (cudaEvent_t &e : rc->chunk_ev)
         if (!e) RT_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     *(volatile uint32_t *)rc->stop_host = 0u;
@@ -1707,6 +1737,26 @@ static rt_status render_regen(const rt_scene *s, const rt_camera *cam, uint32_t 
         }
     };
     RT_CUDA_TRY(cudaMemsetAsync(pool.ctrl, 0, sizeof(Ctrl), st));
+    // Two half-pools on two streams: a window that refills is split in two
+    // halves of its tasks, each run by half of the pool with its own control
+    // block, so that the kernels of one half run in the drain at the end of
+    // the other's launches. A task's result depends only on its index and
+    // the film is accumulated from the staging buffer afterwards, so the film
+    // is the same. Not for stoppable calls (a stop must leave a prefix of the
+    // tasks done), sorted queues (shared sort buffers) or per-kernel timing.
+    const bool stoppable = o.abort_flag || o.time_budget_ms > 0;
+    const bool dual = !stoppable && !o.sort_rays && !o.sort_by_material && !prof && cap >= (1u << 21) && win > cap;
+    if (dual) {
+        if (!rc->ctrl2) RT_CUDA_TRY(cudaMalloc(&rc->ctrl2, sizeof(Ctrl)));
+        if (!rc->st2) RT_CUDA_TRY(cudaStreamCreateWithFlags(&rc->st2, cudaStreamNonBlocking));
+        if (!rc->fork_ev) RT_CUDA_TRY(cudaEventCreateWithFlags(&rc->fork_ev, cudaEventDisableTiming));
+        if (!rc->join_ev) RT_CUDA_TRY(cudaEventCreateWithFlags(&rc->join_ev, cudaEventDisableTiming));
+    }
+    auto regen_min_of = [&](uint32_t c) {
+        return std::max<uint32_t>(1u, (uint32_t)std::min<double>((double)c, std::ceil(frac * c)));
+    };
+    bool any_single = false;
+    unsigned long long dual_counts[7] = {0, 0, 0, 0, 0, 0, 0};   // ext, shadow rays; nodes, tris x2; refills
     constexpr int kChunk = 4;                       // bounce steps per host check
     const uint64_t step_limit = 64ull + 4ull * (max_depth + 2) * ((t_end - t_begin) / std::max<uint64_t>(cap / 2, 1) + 2);
     uint64_t t = t_begin;
@@ -1717,6 +1767,100 @@ static rt_status render_regen(const rt_scene *s, const rt_camera *cam, uint32_t 
         double left_ms = o.time_budget_ms > 0 ? o.time_budget_ms - elapsed_ms() : 0.0;
         const unsigned long long budget_ns =
             o.time_budget_ms > 0 ? (unsigned long long)std::max(1.0, left_ms * 1e6) : 0ull;
+        if (dual && n_win > cap) {
+            const uint32_t capA = (cap / 2) & ~255u, capB = cap - capA;
+            const uint32_t nA = n_win / 2, nB = n_win - nA;
+            const Pool sp[2] = {sub_pool(pool, 0u, capA, pool.ctrl), sub_pool(pool, capA, capB, rc->ctrl2)};
+            const RegenScratch sg[2] = {gs, sub_scratch(gs, capA)};
+            const cudaStream_t ss[2] = {st, rc->st2};
+            float4 *const sstage[2] = {rc->stage, rc->stage + nA};
+            const uint64_t st0[2] = {t, t + nA};
+            const uint32_t sn[2] = {nA, nB}, srm[2] = {regen_min_of(capA), regen_min_of(capB)};
+            RT_CUDA_TRY(cudaEventRecord(rc->fork_ev, st));
+            RT_CUDA_TRY(cudaStreamWaitEvent(rc->st2, rc->fork_ev, 0));
+            for (int i = 0; i < 2; ++i) {
+                RT_CUDA_TRY(cudaMemsetAsync(sp[i].ctrl, 0, sizeof(Ctrl), ss[i]));
+                k_regen_init<<<g_init, 256, 0, ss[i]>>>(P, sp[i], st0[i], sn[i], (uint32_t)WH, tail, 0ull,
+                                                         rc->stop_dev);
+            }
+            stats.kernel_launches += 2;
+            bool fin[2] = {false, false};
+            uint64_t steps2 = 0;
+            for (int chunk = 0;; ++chunk) {
+                for (int i = 0; i < 2; ++i) {
+                    if (fin[i]) continue;
+                    for (int k = 0; k < kChunk; ++k) {
+                        tk.ext<<<tk.grid_ext, gb, tk.smem, ss[i]>>>(s->dev, sp[i], nullptr);
+                        (s->dev.lb_rec ? k_shade<true> : k_shade<false>)<<<g_shade, gb, 0, ss[i]>>>(P, sp[i],
+                                                                                                  sp[i].split);
+                        tk.shadow<<<tk.grid_shadow, gb, tk.smem, ss[i]>>>(s->dev, sp[i], nullptr);
+                        k_regen_gather<<<g_regen, 256, 0, ss[i]>>>(sp[i], sstage[i], srm[i], sg[i]);
+                        k_regen<<<g_regen, 256, 0, ss[i]>>>(P, sp[i], st0[i], (uint32_t)WH, srm[i], sg[i]);
+                        k_regen_step_end<<<1, 1, 0, ss[i]>>>(sp[i], srm[i], rc->stop_dev);
+                        stats.kernel_launches += 6;
+                        ++stats.trace_launches;
+                        ++stats.wavefront_steps;
+                    }
+                    RT_CUDA_TRY(cudaMemcpyAsync(rc->ctrl_ring + 2 * i + (chunk & 1), sp[i].ctrl, sizeof(Ctrl),
+                                                cudaMemcpyDeviceToHost, ss[i]));
+                    RT_CUDA_TRY(cudaEventRecord(rc->chunk_ev[2 * i + (chunk & 1)], ss[i]));
+                }
+                steps2 += kChunk;
+                RT_CUDA_TRY(cudaGetLastError());
+                if (chunk == 0) continue;
+                for (int i = 0; i < 2; ++i) {
+                    if (fin[i]) continue;
+                    const rt_status ws = wait(rc->chunk_ev[2 * i + ((chunk - 1) & 1)]);
+                    if (ws != RT_OK) return ws;
+                    const Ctrl &hc = rc->ctrl_ring[2 * i + ((chunk - 1) & 1)];
+                    if (hc.tail || (hc.n_ext == 0 && (hc.stop || hc.task_next == hc.n_tasks))) fin[i] = true;
+                }
+                if (fin[0] && fin[1]) break;
+                if (steps2 > step_limit) {
+                    set_error("rt_render: the regeneration scheduler did not drain its window");
+                    return RT_CUDA_ERROR;
+                }
+            }
+            for (int i = 0; i < 2; ++i) {
+                k_megakernel<<<g_mega, gb, 0, ss[i]>>>(P, sp[i]);
+                k_regen_retire_tail<<<g_regen, 256, 0, ss[i]>>>(sp[i], sstage[i]);
+                RT_CUDA_TRY(cudaMemcpyAsync(rc->ctrl_ring + 2 * i, sp[i].ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost,
+                                            ss[i]));
+            }
+            RT_CUDA_TRY(cudaEventRecord(rc->join_ev, rc->st2));
+            RT_CUDA_TRY(cudaStreamWaitEvent(st, rc->join_ev, 0));
+            k_film_range<<<grid_for(k_film_range, 256, WH), 256, 0, st>>>(rc->stage, film->sum, film->sum2,
+                                                                          film->count, t, n_win, (uint32_t)WH);
+            // the first half-pool's control block is the single pool's too
+            RT_CUDA_TRY(cudaMemsetAsync(pool.ctrl, 0, sizeof(Ctrl), st));
+            stats.kernel_launches += 5;
+            stats.tail_launches += 2;
+            ++stats.waves;
+            RT_CUDA_TRY(cudaGetLastError());
+            RT_CUDA_TRY(cudaStreamSynchronize(st));
+            bool ovf = false;
+            for (int i = 0; i < 2; ++i) {
+                const Ctrl &c = rc->ctrl_ring[2 * i];
+                if (c.task_next != sn[i] || c.n_tasks != sn[i]) {
+                    set_error("rt_render: a half-pool did not finish its tasks");
+                    return RT_CUDA_ERROR;
+                }
+                dual_counts[0] += c.ext_rays;
+                dual_counts[1] += c.shadow_rays;
+                dual_counts[2] += c.ext_nodes;
+                dual_counts[3] += c.ext_tris;
+                dual_counts[4] += c.shadow_nodes;
+                dual_counts[5] += c.shadow_tris;
+                dual_counts[6] += c.regen_sets;
+                ovf |= c.overflow != 0;
+            }
+            t += n_win;
+            film->next_task = t;
+            stats.paths += n_win;
+            if (ovf) { set_error("BVH traversal stack overflow"); result = RT_STACK_OVERFLOW; break; }
+            continue;
+        }
+        any_single = true;
         cudaEvent_t e = mark(4);
         relay();
         k_regen_init<<<g_init, 256, 0, st>>>(P, pool, t, n_win, (uint32_t)WH, tail, budget_ns, rc->stop_dev);
@@ -1823,13 +1967,15 @@ static rt_status render_regen(const rt_scene *s, const rt_camera *cam, uint32_t 
         cudaEventDestroy(kv.second.first);
         cudaEventDestroy(kv.second.second);
     }
-    stats.extension_rays = rc->host_ctrl->ext_rays;
-    stats.shadow_rays = rc->host_ctrl->shadow_rays;
-    stats.ext_nodes = rc->host_ctrl->ext_nodes;
-    stats.ext_tris = rc->host_ctrl->ext_tris;
-    stats.shadow_nodes = rc->host_ctrl->shadow_nodes;
-    stats.shadow_tris = rc->host_ctrl->shadow_tris;
-    stats.regen_sets = rc->host_ctrl->regen_sets;
+    const Ctrl zero{};
+    const Ctrl &hcs = any_single ? *rc->host_ctrl : zero;
+    stats.extension_rays = hcs.ext_rays + dual_counts[0];
+    stats.shadow_rays = hcs.shadow_rays + dual_counts[1];
+    stats.ext_nodes = hcs.ext_nodes + dual_counts[2];
+    stats.ext_tris = hcs.ext_tris + dual_counts[3];
+    stats.shadow_nodes = hcs.shadow_nodes + dual_counts[4];
+    stats.shadow_tris = hcs.shadow_tris + dual_counts[5];
+    stats.regen_sets = hcs.regen_sets + (uint32_t)dual_counts[6];
     if (o.stats) *o.stats = stats;
     return result;
 }

@@ -58,6 +58,25 @@ def test_regeneration_equals_iteration_sets_bit_for_bit(field, pool, frac):
     assert sa.extension_rays == sb.extension_rays and sa.shadow_rays == sb.shadow_rays
 
 
+@pytest.mark.parametrize("pool,frac", [(1 << 21, 0.5), (3 << 20, 0.0)])
+def test_two_half_pools_equal_iteration_sets_bit_for_bit(field, pool, frac):
+    """A pool of at least 2^21 slots that refills runs as two half-pools on
+    two streams, each with half of the window's tasks; the film, the ray
+    counts and the sample counts are those of the iteration-set scheduler."""
+    sd, cam, scene = field
+    cam = small(cam, 640, 360)
+    a, sa, _ = render(scene, cam, 16, 16, scheduler=1, tail_threshold=1)
+    b, sb, _ = render(scene, cam, 16, 16, max_paths=pool, regen_fraction=frac, tail_threshold=1)
+    A, B = a.download(), b.download()
+    for x, y in zip(A, B):
+        assert np.array_equal(x, y)
+    assert sb.paths == 16 * 640 * 360 and sb.regen_sets > 0
+    assert sa.extension_rays == sb.extension_rays and sa.shadow_rays == sb.shadow_rays
+    # and with the megakernel tail (default threshold) every task is still done once
+    c, sc, _ = render(scene, cam, 16, 16, max_paths=pool, regen_fraction=frac)
+    assert np.all(c.download()[2] == 16) and sc.paths == 16 * 640 * 360
+
+
 def test_regeneration_with_tail_and_sorting_matches(field):
     """With the megakernel tail and the sorted-queue options the film is the
     same up to FP32 operation order."""
