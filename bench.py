@@ -326,20 +326,25 @@ def guided_vs_plain(light="down", target_spp=16384, chunk=512, max_factor=2, see
     """Time to equal RMSE, guided vs plain, on the Cornell configuration (64 x
     64, depth 8): light "down" is the configuration itself; "up" turns the
     emitter to face the ceiling, so that the room is lit through the bright
-    patch it makes there (the case a guide is for; on "down" the pixel error
-    is almost all direct light, which next-event estimation already samples).
-    RMSE against the stored FP64 oracle reference (2^15 spp from a disjoint
-    part of the sample sequence) after every call of `chunk` spp; the target
-    is the plain tracer's RMSE at `target_spp`; guided time includes its
-    inference and training from an untrained network."""
+    patch it makes there; "door" lights the room from a closed side chamber
+    through a door (the case a guide is for: from almost every visible point
+    next-event estimation is blocked and a path must find the door; on "down"
+    the pixel error is almost all direct light, which next-event estimation
+    already samples). RMSE against the stored FP64 oracle reference (2^15 spp,
+    2^17 for "door", from a disjoint part of the sample sequence) after every
+    call of `chunk` spp; the target is the plain tracer's RMSE at
+    `target_spp`; guided time includes its inference and training from an
+    untrained network."""
     import torch
     from paper_1705_01263_gb300 import rt, scenes
-    name = "cornell_64_depth8_ref.npz" if light == "down" else "cornell_up_64_depth8_ref.npz"
+    name = {"down": "cornell_64_depth8_ref.npz", "up": "cornell_up_64_depth8_ref.npz",
+            "door": "cornell_door_64_depth8_ref.npz"}[light]
     ref_path = os.path.join(ROOT, "tests", "golden", name)
     if not os.path.exists(ref_path):
         return None
-    ref = np.load(ref_path)["mean"]
-    sd, cam = scenes.cornell_box(light=light)
+    ref_npz = np.load(ref_path)
+    ref = ref_npz["mean"]
+    sd, cam = scenes.door_room() if light == "door" else scenes.cornell_box(light=light)
     scene = rt.Scene(sd)
     mean = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
 
@@ -365,12 +370,30 @@ def guided_vs_plain(light="down", target_spp=16384, chunk=512, max_factor=2, see
             pts.append((spp, el, float(np.sqrt(np.mean((img - ref) ** 2)))))
             if stop_rmse is not None and pts[-1][2] <= stop_rmse:
                 break
-        return pts
+        return pts, guide
 
-    plain = curve(False)
+    plain, _ = curve(False)
     target = plain[-1][2]
     t_plain = plain[-1][1]
-    guided = curve(True, stop_rmse=target, max_spp=max_factor * target_spp)
+    guided, trained = curve(True, stop_rmse=target, max_spp=max_factor * target_spp)
+
+    # per-sample gain of the network as trained by that run, frozen (no more
+    # training steps): 2048 spp guided against 2048 spp plain on the same
+    # iterations (2^19 on, disjoint from both curves and the reference)
+    def frozen_rmse(g, spp=2048):
+        f = rt.Film(cam.width, cam.height)
+        f.seek(1 << 19)
+        rt.rt_render(scene, cam, spp, 8, f, rt.make_opts(guide=g))
+        f.resolve(mean)
+        torch.cuda.synchronize()
+        return float(np.sqrt(np.mean((mean.cpu().numpy().astype(np.float64) - ref) ** 2)))
+
+    # (the first set of a call still runs one Adam step; at this learning
+    # rate it moves no weight)
+    frozen = rt.Guide(scene, seed=seed, train_every=1 << 30, lr=1e-30,
+                      **{k: v for k, v in (guide_kw or {}).items() if k not in ("train_every", "lr")})
+    frozen.load(trained.state())
+    r_frozen, r_plain2k = frozen_rmse(frozen), frozen_rmse(None)
     t_guided, spp_guided = None, None
     for spp, el, r in guided:
         if r <= target:
@@ -392,12 +415,16 @@ def guided_vs_plain(light="down", target_spp=16384, chunk=512, max_factor=2, see
     short = {"target_rmse": r256, "plain_seconds": t256, "plain_spp": 256,
              "guided_seconds": g256[1] if g256 else None, "guided_spp": g256[0] if g256 else None,
              "guided_speedup": (t256 / g256[1]) if g256 else None}
-    return {"scene": f"cornell 64x64, depth 8, emitter {'under the ceiling facing down' if light == 'down' else 'facing the ceiling'}",
-            "reference": "FP64 oracle, 32768 spp from sequence iteration 2^20", "target_rmse": target,
+    where = {"down": "emitter under the ceiling facing down", "up": "emitter facing the ceiling",
+             "door": "lit from a side chamber through a door"}[light]
+    return {"scene": f"cornell 64x64, depth 8, {where}",
+            "reference": f"FP64 oracle, {int(ref_npz['spp'])} spp from sequence iteration 2^20", "target_rmse": target,
             "target": f"plain RMSE at {target_spp} spp", "plain_seconds": t_plain, "plain_spp": plain[-1][0],
             "guided_seconds": t_guided, "guided_spp": spp_guided,
             "guided_speedup": (t_plain / t_guided) if t_guided else None,
             "rmse_at_equal_spp": per_sample[-4:], "target_256spp": short,
+            "trained_guide_frozen_2048spp": {"guided_rmse": r_frozen, "plain_rmse": r_plain2k,
+                                             "mse_gain": (r_plain2k / r_frozen) ** 2},
             "plain_curve": plain[::4], "guided_curve": guided[::4]}
 
 
@@ -873,6 +900,8 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-guided", action="store_true", help="skip the guided-vs-plain time-to-RMSE run")
+    ap.add_argument("--guided-once", default="", help="only the guided-vs-plain comparison on these scenes "
+                    "(comma-separated: up, down, door), printed one line each")
     ap.add_argument("--no-many-lights", action="store_true", help="skip the instanced many-light workload")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-scene batched workload")
     ap.add_argument("--no-two-way", action="store_true", help="skip the two-way against path-tracer comparison")
@@ -953,6 +982,10 @@ def main():
     film.seek(base_iter)
     if args.mlp_once:
         print(json.dumps(guide_mlp(reps=3)), flush=True)
+        return 0
+    if args.guided_once:
+        for light in args.guided_once.split(","):
+            print(json.dumps({"light": light, **(guided_vs_plain(light) or {})}), flush=True)
         return 0
     if args.two_way_once:
         if args.tw_scene in ("all", "glossy"):
@@ -1064,7 +1097,8 @@ def main():
     e2e_value = paths_per_step * world / (statistics.mean(e2e_ms) / 1e3) / 1e6
     gvp = None
     if rank == 0 and not args.no_guided:
-        gvp = {"indirect_lit": guided_vs_plain("up"), "config": guided_vs_plain("down")}
+        gvp = {"indirect_lit": guided_vs_plain("up"), "config": guided_vs_plain("down"),
+               "door": guided_vs_plain("door")}
         # the same comparison with the network guiding only the first one or
         # two vertices, 8 warm-up steps and training after every 4th set
         variants = []
@@ -1120,7 +1154,7 @@ def main():
             "mrays_per_s": mrays,
             "trace_ext_frac_hbm": (achieved_gbs / hbm) if achieved_gbs else None,
             "trace_ext_frac_l2": achieved_l2,
-            "guided_speedup": {k: (gvp[k] or {}).get("guided_speedup") for k in ("indirect_lit", "config")}
+            "guided_speedup": {k: (gvp[k] or {}).get("guided_speedup") for k in ("indirect_lit", "config", "door")}
             if gvp else None,
             "guide_mlp_frac_bf16": gmlp["roofline"]["frac"] if gmlp else None,
             "many_lights_full_Mpaths_per_s": mlf["Mpaths_per_s"] if mlf else None,

@@ -266,6 +266,64 @@ def cornell_box(seed: int = BASE_SEED + 1, light: str = "down"):
     return scene, cam
 
 
+def door_room(seed: int = BASE_SEED + 1, res: int = 64):
+    """The Cornell room lit from a closed side chamber through a door (not a
+    configuration of the task; the guiding scene where next-event estimation
+    fails for most of the image). Room [0,1]^3 as in cornell_box (same walls,
+    boxes, albedos and camera) without its emitter; its right wall (x = 1)
+    has a door z in [0.55, 0.75], y in [0, 0.65] into a chamber x in [1, 1.6],
+    y in [0, 1], z in [0.35, 1] (white walls, albedo 0.8) whose ceiling
+    carries a 0.3 x 0.45 emitter 1e-3 below it facing down, radiance
+    (85, 60, 20). Light reaches the room only through the door: from almost
+    every visible point a shadow ray towards the emitter is blocked, and a
+    path must pass the door (a small solid angle) to reach the lit chamber."""
+    rng = Rng(seed)
+    b = _Builder()
+
+    def mat():
+        return b.material(tuple(rng.uniform(3, 0.2, 0.8)), 0.5, 0.0)
+
+    z0, z1, yd = 0.55, 0.75, 0.65
+    right = [((1, 0, 0), (1, 0, z0), (1, 1, z0), (1, 1, 0)),
+             ((1, 0, z1), (1, 0, 1), (1, 1, 1), (1, 1, z1)),
+             ((1, yd, z0), (1, yd, z1), (1, 1, z1), (1, 1, z0))]
+    walls = [
+        ([((0, 0, 0), (1, 0, 0), (1, 0, 1), (0, 0, 1))], (0, 1, 0)),    # floor
+        ([((0, 1, 0), (1, 1, 0), (1, 1, 1), (0, 1, 1))], (0, -1, 0)),   # ceiling
+        ([((0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1))], (0, 0, -1)),   # back
+        ([((0, 0, 0), (0, 0, 1), (0, 1, 1), (0, 1, 0))], (1, 0, 0)),    # left
+        (right, (-1, 0, 0)),                                              # right, with the door
+    ]
+    for quads, facing in walls:
+        m = mat()
+        for quad in quads:
+            p, t = _oriented_quad(*quad, facing)
+            b.add(p, t, m)
+    for center, size, ang in (((0.33, 0.151, 0.62), (0.3, 0.3, 0.3), 17.0),
+                              ((0.68, 0.301, 0.42), (0.3, 0.6, 0.3), -17.0)):
+        v, t = _box(center, size, ang)
+        b.add(v, t, mat())
+    white = b.material((0.8, 0.8, 0.8), 0.5, 0.0)
+    x0, x1, c0, c1 = 1.0, 1.6, 0.35, 1.0
+    chamber = [
+        (((x0, 0, c0), (x1, 0, c0), (x1, 0, c1), (x0, 0, c1)), (0, 1, 0)),     # floor
+        (((x0, 1, c0), (x1, 1, c0), (x1, 1, c1), (x0, 1, c1)), (0, -1, 0)),    # ceiling
+        (((x1, 0, c0), (x1, 0, c1), (x1, 1, c1), (x1, 1, c0)), (-1, 0, 0)),    # far wall
+        (((x0, 0, c1), (x1, 0, c1), (x1, 1, c1), (x0, 1, c1)), (0, 0, -1)),    # back
+        (((x0, 0, c0), (x1, 0, c0), (x1, 1, c0), (x0, 1, c0)), (0, 0, 1)),     # front
+    ]
+    for quad, facing in chamber:
+        p, t = _oriented_quad(*quad, facing)
+        b.add(p, t, white)
+    lm = b.material((0.78, 0.78, 0.78), 0.5, 0.0, (85.0, 60.0, 20.0))
+    y = 1.0 - 1e-3
+    p, t = _oriented_quad((1.15, y, 0.45), (1.45, y, 0.45), (1.45, y, 0.9), (1.15, y, 0.9), (0, -1, 0))
+    b.add(p, t, lm)
+    scene = b.build(name="cornell-door")
+    cam = Camera((0.5, 0.5, -1.4), (0.5, 0.5, 0.0), (0.0, 1.0, 0.0), 40.0, res, res)
+    return scene, cam
+
+
 def glossy_room(res: int = 64):
     """The Cornell room lit through its ceiling (cornell_box(light="up")) with
     glossy boxes (pure GGX coating, roughness 0.05) and a half-glossy floor
