@@ -410,11 +410,14 @@ rt_status rt_divide_u64_host(const uint64_t *n, int64_t count, uint32_t d, uint6
  * accumulation on the tensor cores -> 8-lobe von Mises-Fisher mixture,
  * combined with BSDF sampling by one-sample MIS (mixture probability
  * `alpha`). Trained with Adam on up to `batch` radiance samples after each
- * iteration set. For its first `warm_steps` steps a set renders `batch` paths
- * (at most; fewer if rt_render_opts.max_paths_in_flight is smaller) and
- * every set is followed by training; after that a set renders 16 x `batch`
- * paths (rt_render_opts.max_paths_in_flight sets this size) and training
- * follows every `train_every`-th set. */
+ * iteration set. A set renders 16 x `batch` paths
+ * (rt_render_opts.max_paths_in_flight sets this size). For the first
+ * `warm_steps` steps (the warm-up) a set renders at most `warm_set_batches`
+ * x `batch` of them, records training samples from more of its paths and is
+ * followed by up to `warm_set_batches` steps, each on its own `batch` of
+ * those samples; until the first step the proposal is BSDF sampling alone.
+ * After the warm-up one step on one batch follows every `train_every`-th
+ * set. */
 typedef struct {
     uint32_t batch;          /* training samples per pass (0 = 65536) */
     float learning_rate;     /* Adam lr (0 = 1e-2) */
@@ -426,6 +429,8 @@ typedef struct {
                               * sampling beyond (0 = every vertex); training records still
                               * come from every vertex */
     uint32_t warm_steps;     /* training steps taken with small sets before the large ones (0 = 32) */
+    uint32_t warm_set_batches; /* training batches (steps) per warm-up set (0 = 32; 1: one step
+                                * after each set of `batch` paths) */
 } rt_guide_opts;
 
 rt_status rt_guide_create(const rt_scene *scene, const rt_guide_opts *opts, rt_guide **out);

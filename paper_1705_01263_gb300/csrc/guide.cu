@@ -381,6 +381,12 @@ uint32_t guide_depth(const rt_guide *g) { return g->opts.guide_depth; }
 // Training cadence: after every set for the first warm_steps steps, then
 // after every train_every-th set.
 bool guide_young(const rt_guide *g) { return g->step < (int64_t)g->opts.warm_steps; }
+uint32_t guide_warm_left(const rt_guide *g) {
+    if (!guide_young(g)) return 0u;
+    const int64_t per = std::max(1u, g->opts.train_steps);
+    return (uint32_t)(((int64_t)g->opts.warm_steps - g->step + per - 1) / per);
+}
+uint32_t guide_warm_set_batches(const rt_guide *g) { return g->opts.warm_set_batches; }
 bool guide_should_train(rt_guide *g) {
     const uint64_t k = g->sets++;
     const uint32_t every = std::max(1u, g->opts.train_every);
@@ -401,6 +407,7 @@ extern "C" rt_status rt_guide_create(const rt_scene *scene, const rt_guide_opts 
     if (g->opts.alpha > 1.f) { delete g; set_error("rt_guide_create: alpha must be in (0, 1]"); return RT_INVALID_ARG; }
     if (!g->opts.train_steps) g->opts.train_steps = 1;
     if (!g->opts.warm_steps) g->opts.warm_steps = 32;
+    if (!g->opts.warm_set_batches) g->opts.warm_set_batches = 32;
     g->nparams = kGuideParams;
     if (scene) { g->bb_lo = scene->dev.bb_lo; g->bb_hi = scene->dev.bb_hi; }
     else { g->bb_lo = make_float3(0.f, 0.f, 0.f); g->bb_hi = make_float3(1.f, 1.f, 1.f); }

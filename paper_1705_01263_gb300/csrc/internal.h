@@ -51,6 +51,8 @@ bool guide_trained(const rt_guide *g);
 uint32_t guide_depth(const rt_guide *g);   // last guided vertex (0 = all)
 bool guide_should_train(rt_guide *g);   // advances the set counter
 bool guide_young(const rt_guide *g);    // fewer than its warm-up training steps taken
+uint32_t guide_warm_left(const rt_guide *g);          // warm-up training calls (of train_steps steps) still to take
+uint32_t guide_warm_set_batches(const rt_guide *g);   // training batches per warm-up set
 struct MlpWeights;
 MlpWeights guide_weights(const rt_guide *g);   // BF16 layers for the fused inference kernel
 uint32_t *guide_err(const rt_guide *g);        // set by a tensor-core wait that timed out

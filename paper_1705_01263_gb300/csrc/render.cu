@@ -1068,17 +1068,17 @@ __global__ void __launch_bounds__(kMiThreads, 1) k_guide_mlp_paths(MlpWeights w,
 }
 
 // Shading with the guided mixture. Every rec_stride-th path of the set (at
-// most `batch` of them, spread over its pixels and passes) records
+// most `rec_paths` of them, spread over its pixels and passes) records
 // (features, wi, throughput) at every continuing vertex and, at the next
 // vertex, the radiance gathered so far, so that the radiance returned
 // through wi is L_end - L_snapshot; they are the training samples. Record
 // slot of path q: q / rec_stride.
-__device__ __forceinline__ bool recording_path(uint32_t q, uint32_t rec_stride, uint32_t batch) {
-    return q % rec_stride == 0u && q / rec_stride < batch;
+__device__ __forceinline__ bool recording_path(uint32_t q, uint32_t rec_stride, uint32_t rec_paths) {
+    return q % rec_stride == 0u && q / rec_stride < rec_paths;
 }
 
 __global__ void __launch_bounds__(128, 6) k_shade_guided(RenderParams P, Pool pool, const __nv_bfloat16 *raw, float alpha,
-                                                      float4 *rec, uint32_t rec_stride, uint32_t batch, float3 lo,
+                                                      float4 *rec, uint32_t rec_stride, uint32_t rec_paths, float3 lo,
                                                       float3 hi) {
     Ctrl *c = pool.ctrl;
     const uint32_t n = c->n_ext;
@@ -1095,7 +1095,7 @@ __global__ void __launch_bounds__(128, 6) k_shade_guided(RenderParams P, Pool po
         if (valid) {
             q = queue[i];
             PathState s = load_state(pool, q);
-            const bool recording = recording_path(q, rec_stride, batch);
+            const bool recording = recording_path(q, rec_stride, rec_paths);
             const uint32_t slot = q / rec_stride;
             uint32_t nr = recording ? pool.nrec[q] : 0u;
             if (nr & kRecPending) {
@@ -1140,11 +1140,11 @@ __global__ void __launch_bounds__(128, 6) k_shade_guided(RenderParams P, Pool po
 
 // Training samples of finished paths: weight = luminance of the radiance that
 // came back through wi divided by the throughput on arrival, i.e. the
-// sampled f cos Li / p of that vertex.
+// sampled f cos Li / p of that vertex. The first `keep` samples are kept.
 __global__ void k_guide_collect(Pool pool, uint32_t n, const float4 *rec, uint32_t rec_stride, float *tr_feat,
-                                float *tr_wi, float *tr_w, uint32_t batch) {
+                                float *tr_wi, float *tr_w, uint32_t rec_paths, uint32_t keep) {
     Ctrl *c = pool.ctrl;
-    const uint32_t slots = min(batch, (n + rec_stride - 1) / rec_stride);
+    const uint32_t slots = min(rec_paths, (n + rec_stride - 1) / rec_stride);
     for (uint32_t k0 = blockIdx.x * blockDim.x + threadIdx.x; k0 < slots; k0 += gridDim.x * blockDim.x) {
         const uint32_t q = k0 * rec_stride;
         uint32_t nr = pool.nrec[q];
@@ -1160,7 +1160,7 @@ __global__ void k_guide_collect(Pool pool, uint32_t n, const float4 *rec, uint32
             float w = lum(v3(ax, ay, az));
             if (!(w > 0.f) || !isfinite(w)) continue;
             uint32_t idx = atomicAdd(&c->n_train, 1u);
-            if (idx >= batch) continue;
+            if (idx >= keep) continue;
             float f[7] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z};
             for (int j = 0; j < 7; ++j) tr_feat[7 * (size_t)idx + j] = f[j];
             tr_wi[3 * (size_t)idx] = r1.w;
@@ -1385,7 +1385,7 @@ struct RenderCache {
     cudaStream_t st2 = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     // guided rendering
-    uint32_t gcap = 0, gbatch = 0;
+    uint32_t gcap = 0, gbatch = 0, grec_paths = 0;   // guided buffers: network rows, training samples, record paths
     __nv_bfloat16 *gfeat = nullptr;   // network outputs [cap][40] (BF16) of one bounce step
     float *tr_feat = nullptr, *tr_wi = nullptr, *tr_w = nullptr;
     float4 *grec = nullptr;
@@ -1409,8 +1409,13 @@ struct RenderCache {
     }
 };
 
-static rt_status ensure_guided(RenderCache *rc, uint32_t cap, uint32_t batch) {
-    if (rc->gcap >= cap && rc->gbatch >= batch) return RT_OK;
+// Guided-rendering buffers: network rows for `cap` paths, training records
+// of `rec_paths` paths and `samples` training samples.
+static rt_status ensure_guided(RenderCache *rc, uint32_t cap, uint32_t rec_paths, uint32_t samples) {
+    if (rc->gcap >= cap && rc->grec_paths >= rec_paths && rc->gbatch >= samples) return RT_OK;
+    cap = std::max(cap, rc->gcap);
+    rec_paths = std::max(rec_paths, rc->grec_paths);
+    samples = std::max(samples, rc->gbatch);
     for (void *p : {(void *)rc->gfeat, (void *)rc->tr_feat, (void *)rc->tr_wi, (void *)rc->tr_w, (void *)rc->grec,
                     (void *)rc->gnrec})
         if (p) cudaFree(p);
@@ -1419,16 +1424,17 @@ static rt_status ensure_guided(RenderCache *rc, uint32_t cap, uint32_t batch) {
     rc->grec = nullptr;
     rc->gnrec = nullptr;
     if (cudaMalloc(&rc->gfeat, (size_t)cap * kGuideOut * sizeof(__nv_bfloat16)) != cudaSuccess ||
-        cudaMalloc(&rc->grec, (size_t)std::min(cap, batch) * kGuideMaxRec * 4 * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc(&rc->grec, (size_t)rec_paths * kGuideMaxRec * 4 * sizeof(float4)) != cudaSuccess ||
         cudaMalloc(&rc->gnrec, (size_t)cap * 4) != cudaSuccess ||
-        cudaMalloc(&rc->tr_feat, (size_t)batch * 7 * 4) != cudaSuccess ||
-        cudaMalloc(&rc->tr_wi, (size_t)batch * 3 * 4) != cudaSuccess ||
-        cudaMalloc(&rc->tr_w, (size_t)batch * 4) != cudaSuccess) {
+        cudaMalloc(&rc->tr_feat, (size_t)samples * 7 * 4) != cudaSuccess ||
+        cudaMalloc(&rc->tr_wi, (size_t)samples * 3 * 4) != cudaSuccess ||
+        cudaMalloc(&rc->tr_w, (size_t)samples * 4) != cudaSuccess) {
         set_error("guided rendering: out of device memory");
         return RT_OOM;
     }
     rc->gcap = cap;
-    rc->gbatch = batch;
+    rc->grec_paths = rec_paths;
+    rc->gbatch = samples;
     return RT_OK;
 }
 
@@ -2064,15 +2070,18 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         rt_guide *gd = o.guide;
         const uint32_t batch = guide_batch(gd);
         // Iteration sets: while the proposal is young (fewer than its warm-up
-        // training steps) at most one training batch of paths per set, so
-        // that it learns fast; then 16 batches (2^20 paths by default;
-        // max_paths_in_flight sets this size), so that the per-set launches
-        // and the host round trip are spread over many paths. Training
-        // follows a set on `batch` of its samples.
+        // training steps) a set holds `wsb` training batches of paths, every
+        // path of it records its vertices, and up to `wsb` steps follow, each
+        // on a batch of its own, so that the proposal learns fast while the
+        // per-set launches and the host round trip are spread over several
+        // steps; then 16 batches (2^20 paths by default;
+        // max_paths_in_flight sets this size) with one step on `batch` of
+        // their samples.
         const uint32_t cap_full = cap;
+        const uint32_t wsb = std::max(1u, guide_warm_set_batches(gd));
         if (!o.max_paths_in_flight) cap = std::min<uint64_t>(cap, 16ull * std::max(batch, 32u));
-        const uint32_t cap_young = std::min(cap, std::max(batch, 32u));
-        if ((rs = ensure_guided(rc, cap_full, batch)) != RT_OK) return rs;
+        const uint32_t cap_young = (uint32_t)std::min<uint64_t>(cap, (uint64_t)std::max(batch, 32u) * wsb);
+        if ((rs = ensure_guided(rc, cap_full, std::max(batch, batch * wsb / 4u), batch * wsb)) != RT_OK) return rs;
         rc->pool.view.nrec = rc->gnrec;
         Pool gpool = rc->pool.view;
         float3 glo, ghi;
@@ -2101,7 +2110,15 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
             }
             uint32_t n = (uint32_t)n64;
             const float a = guide_trained(gd) ? alpha : 0.f;
-            const uint32_t rec_stride = std::max(1u, n / std::max(batch, 1u));
+            // recording paths and the samples kept: in a young set enough
+            // paths for wsb batches at four samples per path (a path records
+            // up to kGuideMaxRec vertices), later every rec_stride-th path for
+            // one batch
+            const bool young = guide_young(gd);
+            const uint32_t keep = young ? batch * wsb : batch;
+            const uint32_t want = young ? std::max(1u, keep / 4u) : batch;
+            const uint32_t rec_stride = std::max(1u, n / std::max(want, 1u));
+            const uint32_t rec_paths = want;
             k_raygen<<<g_ray, 256, 0, st>>>(P, gpool, t, n, (uint32_t)WH, 0u);
             stats.kernel_launches += 1;
             // every bounce step runs on the device-side queue lengths: no
@@ -2118,7 +2135,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
                     stats.kernel_launches += 1;
                 }
                 k_shade_guided<<<g_shade, gbk, 0, st>>>(P, gpool, av > 0.f ? rc->gfeat : nullptr, av, rc->grec,
-                                                        rec_stride, batch, glo, ghi);
+                                                        rec_stride, rec_paths, glo, ghi);
                 tk.shadow<<<tk.grid_shadow, gbk, 0, st>>>(s->dev, gpool, nullptr);
                 k_step_end<<<1, 1, 0, st>>>(gpool);
                 stats.kernel_launches += 4;
@@ -2126,8 +2143,8 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
             }
             int g_film = grid_for(k_film, 256, passes ? WH : n);
             k_film<<<g_film, 256, 0, st>>>(gpool, film->sum, film->sum2, film->count, t, n, (uint32_t)WH, passes);
-            k_guide_collect<<<grid_for(k_guide_collect, 256, std::min(n, batch)), 256, 0, st>>>(
-                gpool, n, rc->grec, rec_stride, rc->tr_feat, rc->tr_wi, rc->tr_w, batch);
+            k_guide_collect<<<grid_for(k_guide_collect, 256, std::min(n, rec_paths)), 256, 0, st>>>(
+                gpool, n, rc->grec, rec_stride, rc->tr_feat, rc->tr_wi, rc->tr_w, rec_paths, keep);
             stats.kernel_launches += 2;
             RT_CUDA_TRY(cudaGetLastError());
             RT_CUDA_TRY(cudaMemcpyAsync(rc->host_ctrl, gpool.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
@@ -2138,10 +2155,19 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
             ++stats.waves;
             if (rc->host_ctrl->overflow) { set_error("BVH traversal stack overflow"); result = RT_STACK_OVERFLOW; break; }
             if ((rs = guide_check(gd, st)) != RT_OK) return rs;
-            const uint32_t n_train = std::min(rc->host_ctrl->n_train, batch);
+            const uint32_t n_train = std::min(rc->host_ctrl->n_train, keep);
             if (n_train >= 256 && guide_should_train(gd)) {
-                if ((rs = guide_train_async(gd, rc->tr_feat, rc->tr_wi, rc->tr_w, n_train, st)) != RT_OK) return rs;
-                stats.kernel_launches += 40;
+                // one training call per full batch (a young set: at most the
+                // warm-up calls still to take), else one on what there is
+                const uint32_t steps = young ? std::max(1u, std::min(n_train / batch, guide_warm_left(gd))) : 1u;
+                for (uint32_t k = 0; k < steps; ++k) {
+                    const size_t off = (size_t)k * batch;
+                    const uint32_t m = steps > 1 ? batch : std::min(n_train, batch);
+                    if ((rs = guide_train_async(gd, rc->tr_feat + 7 * off, rc->tr_wi + 3 * off, rc->tr_w + off, m, st)) !=
+                        RT_OK)
+                        return rs;
+                    stats.kernel_launches += 40;
+                }
             }
             double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
             if (t < t_end && ((o.abort_flag && *o.abort_flag) || (o.time_budget_ms > 0 && ms >= o.time_budget_ms))) {

@@ -84,7 +84,7 @@ class rt_render_job(C.Structure):
 class rt_guide_opts(C.Structure):
     _fields_ = [("batch", C.c_uint32), ("learning_rate", C.c_float), ("alpha", C.c_float),
                 ("train_steps", C.c_uint32), ("seed", C.c_uint64), ("train_every", C.c_uint32),
-                ("guide_depth", C.c_uint32), ("warm_steps", C.c_uint32)]
+                ("guide_depth", C.c_uint32), ("warm_steps", C.c_uint32), ("warm_set_batches", C.c_uint32)]
 
 
 _lib = None
@@ -494,8 +494,9 @@ class Guide:
     """Online path-guiding network (rt_guide_*)."""
 
     def __init__(self, scene=None, batch=0, lr=0.0, alpha=0.0, train_steps=0, seed=0, train_every=0, guide_depth=0,
-                 warm_steps=0):
-        o = rt_guide_opts(batch, lr, alpha, train_steps, seed, train_every, guide_depth, warm_steps)
+                 warm_steps=0, warm_set_batches=0):
+        o = rt_guide_opts(batch, lr, alpha, train_steps, seed, train_every, guide_depth, warm_steps,
+                          warm_set_batches)
         h = C.c_void_p()
         check(lib().rt_guide_create(scene.handle if scene is not None else None, C.byref(o), C.byref(h)))
         self.handle = h
