@@ -75,20 +75,40 @@ RT_HD void guide_features(V3 x, V3 wo, V3 n, float3 lo, float3 hi, float *f) {
 
 RT_HD float softplusf(float x) { return x > 20.f ? x : log1pf(expf(x)); }
 
+// A decoded mixture: per lobe the mean direction mu (xyz), kappa, the
+// weight w and c = w kappa / (2 pi (1 - e^{-2 kappa})), the weighted lobe's
+// normalisation. Element (k, f) of lobe k, field f (0-2 mu, 3 kappa, 4 w,
+// 5 c): Mixture keeps them in a thread-local array; MixtureStrided at
+// p[(6 k + f) stride], so that a block's threads keep theirs in shared
+// memory side by side (stride = threads of the block), out of the local
+// memory that a thread-local array indexed by the sampled lobe lives in.
+constexpr int kMixFields = 6;
 struct Mixture {
-    V3 mu[kGuideLobes];
-    float kappa[kGuideLobes];
-    float w[kGuideLobes];
-    float c[kGuideLobes];   // w kappa / (2 pi (1 - e^{-2 kappa})): the weighted lobe's normalisation
+    float v[kGuideLobes * kMixFields];
+    RT_HD float &at(int k, int f) { return v[kMixFields * k + f]; }
+    RT_HD float at(int k, int f) const { return v[kMixFields * k + f]; }
 };
+struct MixtureStrided {
+    float *p;
+    uint32_t stride;
+    RT_HD float &at(int k, int f) const { return p[(size_t)(kMixFields * k + f) * stride]; }
+};
+template <class M>
+RT_HD V3 mix_mu(const M &m, int k) { return v3(m.at(k, 0), m.at(k, 1), m.at(k, 2)); }
+template <class M>
+RT_HD float mix_kappa(const M &m, int k) { return m.at(k, 3); }
+template <class M>
+RT_HD float mix_w(const M &m, int k) { return m.at(k, 4); }
+template <class M>
+RT_HD float mix_c(const M &m, int k) { return m.at(k, 5); }
 
 RT_HD float raw_value(float v) { return v; }
 RT_HD float raw_value(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 // Raw outputs in FP32 (training, the API) or BF16 (the rows the guided
 // render writes and reads back).
-template <class T>
-RT_HD void decode_mixture(const T *raw, Mixture &m) {
+template <class T, class M>
+RT_HD void decode_mixture(const T *raw, M &m) {
     float mx = -INFINITY;
     for (int k = 0; k < kGuideLobes; ++k) mx = fmaxf(mx, raw_value(raw[5 * k + 4]));
     float z = 0.f;
@@ -96,14 +116,19 @@ RT_HD void decode_mixture(const T *raw, Mixture &m) {
         const T *rr = raw + 5 * k;
         const float r[4] = {raw_value(rr[0]), raw_value(rr[1]), raw_value(rr[2]), raw_value(rr[3])};
         float l = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-        m.mu[k] = l > 0.f ? v3(r[0] / l, r[1] / l, r[2] / l) : v3(0.f, 0.f, 1.f);
-        m.kappa[k] = fminf(kKappaMax, fmaxf(kKappaMin, softplusf(r[3])));
-        m.w[k] = expf(raw_value(rr[4]) - mx);
-        z += m.w[k];
+        const V3 mu = l > 0.f ? v3(r[0] / l, r[1] / l, r[2] / l) : v3(0.f, 0.f, 1.f);
+        m.at(k, 0) = mu.x;
+        m.at(k, 1) = mu.y;
+        m.at(k, 2) = mu.z;
+        m.at(k, 3) = fminf(kKappaMax, fmaxf(kKappaMin, softplusf(r[3])));
+        const float w = expf(raw_value(rr[4]) - mx);
+        m.at(k, 4) = w;
+        z += w;
     }
     for (int k = 0; k < kGuideLobes; ++k) {
-        m.w[k] /= z;
-        m.c[k] = m.w[k] * m.kappa[k] / (2.f * kPi * -expm1f(-2.f * m.kappa[k]));
+        const float w = m.at(k, 4) / z, kap = m.at(k, 3);
+        m.at(k, 4) = w;
+        m.at(k, 5) = w * kap / (2.f * kPi * -expm1f(-2.f * kap));
     }
 }
 
@@ -111,22 +136,24 @@ RT_HD float vmf_pdf(float kappa, V3 mu, V3 w) {
     return kappa / (2.f * kPi * -expm1f(-2.f * kappa)) * expf(kappa * (dot(mu, w) - 1.f));
 }
 
-RT_HD float mixture_pdf(const Mixture &m, V3 w) {
+template <class M>
+RT_HD float mixture_pdf(const M &m, V3 w) {
     float p = 0.f;
-    for (int k = 0; k < kGuideLobes; ++k) p += m.c[k] * expf(m.kappa[k] * (dot(m.mu[k], w) - 1.f));
+    for (int k = 0; k < kGuideLobes; ++k) p += mix_c(m, k) * expf(mix_kappa(m, k) * (dot(mix_mu(m, k), w) - 1.f));
     return p;
 }
 
 // Lobe by u_sel, then cos theta = 1 + ln(u1 + (1 - u1) e^{-2k}) / k about mu.
-RT_HD V3 mixture_sample(const Mixture &m, float u_sel, float u1, float u2) {
+template <class M>
+RT_HD V3 mixture_sample(const M &m, float u_sel, float u1, float u2) {
     int k = 0;
     float acc = 0.f;
     for (k = 0; k < kGuideLobes - 1; ++k) {
-        if (u_sel < acc + m.w[k]) break;
-        acc += m.w[k];
+        if (u_sel < acc + mix_w(m, k)) break;
+        acc += mix_w(m, k);
     }
-    const float kap = m.kappa[k];
-    const V3 n = m.mu[k];
+    const float kap = mix_kappa(m, k);
+    const V3 n = mix_mu(m, k);
     float ct = 1.f + logf(u1 + (1.f - u1) * expf(-2.f * kap)) / kap;
     ct = fminf(1.f, fmaxf(-1.f, ct));
     float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
@@ -147,28 +174,29 @@ RT_HD float mixture_loss_grad(const float *raw, const float *wi3, float scale, f
     V3 wi = v3(wi3[0], wi3[1], wi3[2]);
     float q[kGuideLobes], qm = 0.f;
     for (int k = 0; k < kGuideLobes; ++k) {
-        q[k] = vmf_pdf(m.kappa[k], m.mu[k], wi);
-        qm += m.w[k] * q[k];
+        q[k] = vmf_pdf(mix_kappa(m, k), mix_mu(m, k), wi);
+        qm += mix_w(m, k) * q[k];
     }
     qm = fmaxf(qm, 1e-30f);
     for (int k = 0; k < kGuideLobes; ++k) {
         const float *rk = raw + 5 * k;
-        float resp = m.w[k] * q[k] / qm;
-        float c = dot(m.mu[k], wi);
+        float resp = mix_w(m, k) * q[k] / qm;
+        const V3 mu = mix_mu(m, k);
+        const float kk = mix_kappa(m, k);
+        float c = dot(mu, wi);
         float l = sqrtf(rk[0] * rk[0] + rk[1] * rk[1] + rk[2] * rk[2]);
         float inv_l = l > 0.f ? 1.f / l : 0.f;
-        g[5 * k + 0] = -scale * resp * m.kappa[k] * (wi.x - c * m.mu[k].x) * inv_l;
-        g[5 * k + 1] = -scale * resp * m.kappa[k] * (wi.y - c * m.mu[k].y) * inv_l;
-        g[5 * k + 2] = -scale * resp * m.kappa[k] * (wi.z - c * m.mu[k].z) * inv_l;
+        g[5 * k + 0] = -scale * resp * kk * (wi.x - c * mu.x) * inv_l;
+        g[5 * k + 1] = -scale * resp * kk * (wi.y - c * mu.y) * inv_l;
+        g[5 * k + 2] = -scale * resp * kk * (wi.z - c * mu.z) * inv_l;
         float sp = softplusf(rk[3]);
         float dk = 0.f;
         if (sp > kKappaMin && sp < kKappaMax) {
-            float kk = m.kappa[k];
             float dlogq = 1.f / kk - 2.f / expm1f(2.f * kk) + (c - 1.f);
             dk = resp * dlogq / (1.f + expf(-rk[3]));
         }
         g[5 * k + 3] = -scale * dk;
-        g[5 * k + 4] = -scale * (resp - m.w[k]);
+        g[5 * k + 4] = -scale * (resp - mix_w(m, k));
     }
     return -scale * logf(qm);
 }

@@ -1077,7 +1077,11 @@ __device__ __forceinline__ bool recording_path(uint32_t q, uint32_t rec_stride, 
     return q % rec_stride == 0u && q / rec_stride < rec_paths;
 }
 
-__global__ void __launch_bounds__(128, 6) k_shade_guided(RenderParams P, Pool pool, const __nv_bfloat16 *raw, float alpha,
+// Threads per block of the guided shading kernels: each keeps its decoded
+// mixture in the block's shared memory (24 KB).
+constexpr uint32_t kGuidedShadeThreads = 128;
+
+__global__ void __launch_bounds__(kGuidedShadeThreads, 6) k_shade_guided(RenderParams P, Pool pool, const __nv_bfloat16 *raw, float alpha,
                                                       float4 *rec, uint32_t rec_stride, uint32_t rec_paths, float3 lo,
                                                       float3 hi) {
     Ctrl *c = pool.ctrl;
@@ -1085,6 +1089,8 @@ __global__ void __launch_bounds__(128, 6) k_shade_guided(RenderParams P, Pool po
     const uint32_t cur = c->cur;
     const uint32_t *queue = pool.q[cur];
     uint32_t *next = pool.q[cur ^ 1u];
+    __shared__ float s_mix[kMixFields * kGuideLobes * kGuidedShadeThreads];
+    const MixtureStrided mix{s_mix + threadIdx.x, kGuidedShadeThreads};
     for (;;) {
         uint32_t base = warp_fetch32(&c->fetch_shade);
         if (base >= n) break;
@@ -1112,7 +1118,8 @@ __global__ void __launch_bounds__(128, 6) k_shade_guided(RenderParams P, Pool po
             GuideRecord gr;
             const uint32_t v = s.depth;
             const bool want = recording && v <= kGuideMaxRec;
-            r = shade(P, s, h, sh, raw ? raw + (size_t)kGuideOut * i : nullptr, alpha, want ? &gr : nullptr, lo, hi);
+            r = shade<true, MixtureStrided>(P, s, h, sh, raw ? raw + (size_t)kGuideOut * i : nullptr, alpha,
+                                            want ? &gr : nullptr, lo, hi, mix);
             pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
             if (r & 1) {
                 pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
@@ -2087,7 +2094,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         float3 glo, ghi;
         guide_bounds(gd, glo, ghi);
         const float alpha = guide_alpha(gd);
-        const int gbk = 128;
+        const int gbk = (int)kGuidedShadeThreads;
         const int g_ray = grid_for(k_raygen, 256, cap);
         const TraceKernels tk = trace_kernels(false, 0, s->dev.two_level, gbk);
         const int g_shade = grid_persistent(k_shade_guided, gbk, 0);
@@ -2942,7 +2949,7 @@ __global__ void __launch_bounds__(kMiThreads, 1) k_guide_mlp_job(MlpWeights w, J
 // shading of the shared queue: a path of a guided job samples the mixture of
 // its network's outputs (at its slot) with its job's probability and, on a
 // recording slot, keeps the training record of each continuing vertex
-__global__ void __launch_bounds__(128, 6) k_batchg_shade(const BatchJob *jobs, const BatchGuide *guides,
+__global__ void __launch_bounds__(kGuidedShadeThreads, 6) k_batchg_shade(const BatchJob *jobs, const BatchGuide *guides,
                                                          const float *alpha, Pool pool, const uint32_t *job_of,
                                                          const __nv_bfloat16 *raw, float4 *rec, uint32_t rec_stride,
                                                          uint32_t rec_slots) {
@@ -2951,6 +2958,9 @@ __global__ void __launch_bounds__(128, 6) k_batchg_shade(const BatchJob *jobs, c
     const uint32_t cur = c->cur;
     const uint32_t *queue = pool.q[cur];
     uint32_t *next = pool.q[cur ^ 1u];
+    // blocks of up to kGuidedShadeThreads threads (the autotuner's block size)
+    __shared__ float s_mix[kMixFields * kGuideLobes * kGuidedShadeThreads];
+    const MixtureStrided mix{s_mix + threadIdx.x, blockDim.x};
     for (;;) {
         uint32_t base = warp_fetch32(&c->fetch_shade);
         if (base >= n) break;
@@ -2981,8 +2991,8 @@ __global__ void __launch_bounds__(128, 6) k_batchg_shade(const BatchJob *jobs, c
             const uint32_t v = s.depth;
             const bool want = recording && v <= kGuideMaxRec;
             const float a = G.guided ? alpha[j] : 0.f;
-            r = shade(P, s, h, sh, a > 0.f ? raw + (size_t)kGuideOut * q : nullptr, a, want ? &gr : nullptr, G.lo,
-                      G.hi);
+            r = shade<true, MixtureStrided>(P, s, h, sh, a > 0.f ? raw + (size_t)kGuideOut * q : nullptr, a,
+                                            want ? &gr : nullptr, G.lo, G.hi, mix);
             pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
             if (r & 1) {
                 pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));

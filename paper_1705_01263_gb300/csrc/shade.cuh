@@ -694,16 +694,17 @@ RT_HD NeePick nee_pick(const RenderParams &P, uint64_t index, int base) {
 // path s, vertex number s.depth: the scattering half of shade(), shared with
 // the probe vertex. Returns bit 0 when the path continues and bit 1 when `sh`
 // holds a shadow ray (see shade()).
-template <bool kLb = true>
+// `mix` holds the decoded guiding mixture of a guided vertex (thread-local
+// storage by default; the guided kernels pass shared-memory storage).
+template <bool kLb = true, class Mix = Mixture>
 RT_HD int scatter(const RenderParams &P, PathState &s, const Vertex &vx, const Material &m, bool nee,
                   const NeePick &pk, ShadowRay &sh, const __nv_bfloat16 *graw, float alpha, GuideRecord *rec, float3 glo,
-                  float3 ghi) {
+                  float3 ghi, Mix mix = Mix()) {
     const DevScene &sc = P.sc;
     const int mode = P.mis_mode;
     const uint32_t v = s.depth;
     const int base = 2 + 7 * (int)(v - 1);
     const V3 x = vx.x, ng = vx.ng, ns = vx.ns, wo = vx.wo;
-    Mixture mix;
     const bool guided = graw != nullptr && alpha > 0.f;
     if (guided) decode_mixture(graw, mix);
     V3 xo = offset_origin(x, ng);
@@ -834,10 +835,10 @@ RT_HD int scatter(const RenderParams &P, PathState &s, const Vertex &vx, const M
 // from the one-sample MIS mixture alpha * vMF-mixture + (1 - alpha) * BSDF
 // and every pdf used for MIS is that mixture's; with `rec` the vertex's
 // training record is filled when the path continues.
-template <bool kLb = true>
+template <bool kLb = true, class Mix = Mixture>
 RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh, const __nv_bfloat16 *graw = nullptr,
                 float alpha = 0.f, GuideRecord *rec = nullptr, float3 glo = float3{0.f, 0.f, 0.f},
-                float3 ghi = float3{1.f, 1.f, 1.f}) {
+                float3 ghi = float3{1.f, 1.f, 1.f}, Mix mix = Mix()) {
     const DevScene &sc = P.sc;
     const int mode = P.mis_mode;
     const uint32_t v = s.depth;
@@ -890,7 +891,7 @@ RT_HD int shade(const RenderParams &P, PathState &s, const Hit &h, ShadowRay &sh
     }
     if (last) return 0;
     const Material m = load_material(sc, mid);
-    return scatter<kLb>(P, s, vx, m, nee, pk, sh, graw, alpha, rec, glo, ghi);
+    return scatter<kLb, Mix>(P, s, vx, m, nee, pk, sh, graw, alpha, rec, glo, ghi, mix);
 }
 
 // Vertex 1 of an irradiance-probe path (Sec. 4.2): a virtual white
