@@ -170,14 +170,31 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(GemmArgs g) {
     if (warp == 0) umma::tmem_dealloc(taddr, ncols);
 }
 
-// C (+)= the sum of the splits' partial products (one thread per element).
-__global__ void k_sum_splits(const float *part, int splits, int M, int N, float *C, int ldc, int accumulate) {
+// C (+)= the sum of the splits' partial products. A block takes 32
+// consecutive elements; its eight warps sum the splits z = g, g + 8, ... of
+// them (warp g; loads coalesced over the elements), and the eight partial
+// sums are added in warp order: a fixed order, so the result is the same on
+// every run.
+constexpr int kSumGroups = 8;
+__global__ void __launch_bounds__(32 * kSumGroups) k_sum_splits(const float *part, int splits, int M, int N, float *C,
+                                                                int ldc, int accumulate) {
+    __shared__ float s_part[kSumGroups][32];
     const int64_t n = (int64_t)M * N;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int e = threadIdx.x & 31, g = threadIdx.x >> 5;
+    for (int64_t i0 = (int64_t)blockIdx.x * 32; i0 < n; i0 += (int64_t)gridDim.x * 32) {
+        const int64_t i = i0 + e;
         float acc = 0.f;
-        for (int z = 0; z < splits; ++z) acc += part[(size_t)z * n + i];
-        float *dst = C + (i / N) * ldc + (i % N);
-        *dst = accumulate ? *dst + acc : acc;
+        if (i < n)
+            for (int z = g; z < splits; z += kSumGroups) acc += part[(size_t)z * n + i];
+        s_part[g][e] = acc;
+        __syncthreads();
+        if (g == 0 && i < n) {
+            float sum = s_part[0][e];
+            for (int k = 1; k < kSumGroups; ++k) sum += s_part[k][e];
+            float *dst = C + (i / N) * ldc + (i % N);
+            *dst = accumulate ? *dst + sum : sum;
+        }
+        __syncthreads();
     }
 }
 
@@ -242,8 +259,8 @@ static rt_status gemm_launch(GemmArgs g, int accumulate, bool relu_bwd, cudaStre
     RT_CUDA_TRY(cudaGetLastError());
     if (g.mode == 3) {
         const int64_t n = (int64_t)M * N;
-        const int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
-        k_sum_splits<<<blocks, 256, 0, st>>>(g.part, splits, M, N, g.C, g.ldc, accumulate);
+        const int blocks = (int)std::min<int64_t>((n + 31) / 32, 4096);
+        k_sum_splits<<<blocks, 32 * kSumGroups, 0, st>>>(g.part, splits, M, N, g.C, g.ldc, accumulate);
         RT_CUDA_TRY(cudaGetLastError());
     }
     return RT_OK;
