@@ -2130,7 +2130,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
             stats.kernel_launches += 1;
             // every bounce step runs on the device-side queue lengths: no
             // host round trip until the set is done
-            const uint32_t gdepth = guide_depth(gd) ? std::min(guide_depth(gd), max_depth) : max_depth;
+            const uint32_t gdepth = std::min(guide_depth(gd), max_depth);
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
                 tk.ext<<<tk.grid_ext, gbk, 0, st>>>(s->dev, gpool, nullptr);
                 // the network runs only where a continuation is guided: not
@@ -2852,6 +2852,7 @@ struct BatchGuide {
     float *tr_feat, *tr_wi, *tr_w;   // the job's training batch
     uint32_t batch;       // its capacity
     uint32_t guided;      // 0: the job has no network
+    uint32_t depth;       // the last guided vertex (BSDF sampling beyond it)
 };
 
 RT_D uint32_t find_block(const BatchBlock *blocks, uint32_t nblocks, uint64_t t) {
@@ -2933,7 +2934,7 @@ struct JobPathFeatures {
         Hit h;
         h.prim = __float_as_uint(hv.x); h.inst = pool.hit_inst[q];
         h.t = hv.y; h.b1 = hv.z; h.b2 = hv.w;
-        if (h.prim != RT_MISS && s.depth <= P.max_depth) {
+        if (h.prim != RT_MISS && s.depth <= P.max_depth && s.depth <= guides[j].depth) {
             Vertex vx;
             setup_vertex(P.sc, s, h, vx);
             guide_features(vx.x, vx.wo, vx.ns, guides[j].lo, guides[j].hi, f);
@@ -2990,7 +2991,7 @@ __global__ void __launch_bounds__(kGuidedShadeThreads, 6) k_batchg_shade(const B
             GuideRecord gr;
             const uint32_t v = s.depth;
             const bool want = recording && v <= kGuideMaxRec;
-            const float a = G.guided ? alpha[j] : 0.f;
+            const float a = G.guided && s.depth <= G.depth ? alpha[j] : 0.f;
             r = shade<true, MixtureStrided>(P, s, h, sh, a > 0.f ? raw + (size_t)kGuideOut * q : nullptr, a,
                                             want ? &gr : nullptr, G.lo, G.hi, mix);
             pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
@@ -3327,6 +3328,7 @@ static rt_status render_batch_guided(const rt_render_job *jobs, int32_t njobs, c
         G.guided = 1;
         guide_bounds(gd, G.lo, G.hi);
         G.batch = guide_batch(gd);
+        G.depth = guide_depth(gd);
         if ((rs = dalloc((void **)&G.tr_feat, (size_t)G.batch * 7 * 4)) != RT_OK ||
             (rs = dalloc((void **)&G.tr_wi, (size_t)G.batch * 3 * 4)) != RT_OK ||
             (rs = dalloc((void **)&G.tr_w, (size_t)G.batch * 4)) != RT_OK)

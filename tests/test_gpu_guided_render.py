@@ -29,11 +29,12 @@ def reference(light="down"):
     return oracle.resolve(S, S2, C)
 
 
-@pytest.mark.parametrize("pool,gdepth,warm", [(0, 0, 0), (65536, 0, 0), (0, 1, 8), (0, 2, 0)])
+@pytest.mark.parametrize("pool,gdepth,warm", [(0, 0, 0), (65536, 0, 0), (0, 1, 8), (0, 2, 0), (0, 64, 0)])
 def test_guided_render_is_consistent_with_the_oracle(pool, gdepth, warm):
     """pool 0: the library's iteration sets; 65536: 16 spp per set, so that
     a training step follows every set; gdepth 1 or 2: only the first vertices
-    guided (BSDF sampling and its MIS weights beyond them)."""
+    guided (BSDF sampling and its MIS weights beyond them); 0: the default
+    (vertices 1-4); 64: every vertex."""
     from paper_1705_01263_gb300 import rt
     sd, cam = scenes.cornell_box()
     scene = rt.Scene(sd)
