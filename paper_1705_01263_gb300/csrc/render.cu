@@ -1068,7 +1068,8 @@ __global__ void __launch_bounds__(kMiThreads, 1) k_guide_mlp_paths(MlpWeights w,
 }
 
 // Shading with the guided mixture. Every rec_stride-th path of the set (at
-// most `rec_paths` of them, spread over its pixels and passes) records
+// most `rec_paths` of them, spread over its pixels and passes) records, at
+// its vertices 1..rec_depth (at most kGuideMaxRec),
 // (features, wi, throughput) at every continuing vertex and, at the next
 // vertex, the radiance gathered so far, so that the radiance returned
 // through wi is L_end - L_snapshot; they are the training samples. Record
@@ -1082,8 +1083,8 @@ __device__ __forceinline__ bool recording_path(uint32_t q, uint32_t rec_stride, 
 constexpr uint32_t kGuidedShadeThreads = 128;
 
 __global__ void __launch_bounds__(kGuidedShadeThreads, 6) k_shade_guided(RenderParams P, Pool pool, const __nv_bfloat16 *raw, float alpha,
-                                                      float4 *rec, uint32_t rec_stride, uint32_t rec_paths, float3 lo,
-                                                      float3 hi) {
+                                                      float4 *rec, uint32_t rec_stride, uint32_t rec_paths,
+                                                      uint32_t rec_depth, float3 lo, float3 hi) {
     Ctrl *c = pool.ctrl;
     const uint32_t n = c->n_ext;
     const uint32_t cur = c->cur;
@@ -1117,7 +1118,7 @@ __global__ void __launch_bounds__(kGuidedShadeThreads, 6) k_shade_guided(RenderP
             ShadowRay sh;
             GuideRecord gr;
             const uint32_t v = s.depth;
-            const bool want = recording && v <= kGuideMaxRec;
+            const bool want = recording && v <= rec_depth;
             r = shade<true, MixtureStrided>(P, s, h, sh, raw ? raw + (size_t)kGuideOut * i : nullptr, alpha,
                                             want ? &gr : nullptr, lo, hi, mix);
             pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
@@ -2088,9 +2089,21 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         const uint32_t wsb = std::max(1u, guide_warm_set_batches(gd));
         if (!o.max_paths_in_flight) cap = std::min<uint64_t>(cap, 16ull * std::max(batch, 32u));
         const uint32_t cap_young = (uint32_t)std::min<uint64_t>(cap, (uint64_t)std::max(batch, 32u) * wsb);
-        if ((rs = ensure_guided(rc, cap_full, std::max(batch, batch * wsb / 4u), batch * wsb)) != RT_OK) return rs;
+        // training records come from the guided vertices 1..gdepth only (the
+        // network is asked about no other). Samples kept: up to wsb batches
+        // after a young set, one batch later. Recording paths: in a young set
+        // enough for its samples at min(4, rec_depth) samples per path, later
+        // `batch`; the record buffer holds the larger of the two.
+        const uint32_t gdepth = std::min(guide_depth(gd), max_depth);
+        const uint32_t rec_depth = std::min(gdepth, kGuideMaxRec);
+        const uint32_t keep_young = (uint32_t)std::min<uint64_t>((uint64_t)batch * wsb, 1ull << 28);
+        const uint32_t rec_young = std::max(1u, keep_young / std::max(1u, std::min(4u, rec_depth)));
+        if ((rs = ensure_guided(rc, cap_full, std::max(batch, rec_young), std::max(batch, keep_young))) != RT_OK)
+            return rs;
         rc->pool.view.nrec = rc->gnrec;
         Pool gpool = rc->pool.view;
+        gpool.qd = nullptr;      // no regeneration: ended paths are not queued
+        gpool.split = nullptr;   // one shading queue
         float3 glo, ghi;
         guide_bounds(gd, glo, ghi);
         const float alpha = guide_alpha(gd);
@@ -2098,6 +2111,7 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         const int g_ray = grid_for(k_raygen, 256, cap);
         const TraceKernels tk = trace_kernels(false, 0, s->dev.two_level, gbk);
         const int g_shade = grid_persistent(k_shade_guided, gbk, 0);
+        const int g_shade_plain = grid_persistent(k_shade<true>, gbk, 0);
         if ((rs = mlp_kernel_attr((const void *)k_guide_mlp_paths, kMlpInferSmem)) != RT_OK) return rs;
         const PathFeatures pf{P, gpool, glo, ghi};
         rt_stats stats{};
@@ -2117,20 +2131,16 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
             }
             uint32_t n = (uint32_t)n64;
             const float a = guide_trained(gd) ? alpha : 0.f;
-            // recording paths and the samples kept: in a young set enough
-            // paths for wsb batches at four samples per path (a path records
-            // up to kGuideMaxRec vertices), later every rec_stride-th path for
-            // one batch
+            // recording paths and the samples kept (both within the buffers
+            // sized above): every rec_stride-th path records
             const bool young = guide_young(gd);
-            const uint32_t keep = young ? batch * wsb : batch;
-            const uint32_t want = young ? std::max(1u, keep / 4u) : batch;
-            const uint32_t rec_stride = std::max(1u, n / std::max(want, 1u));
-            const uint32_t rec_paths = want;
+            const uint32_t keep = young ? std::max(batch, keep_young) : batch;
+            const uint32_t rec_paths = young ? std::max(batch, rec_young) : batch;
+            const uint32_t rec_stride = std::max(1u, n / rec_paths);
             k_raygen<<<g_ray, 256, 0, st>>>(P, gpool, t, n, (uint32_t)WH, 0u);
             stats.kernel_launches += 1;
             // every bounce step runs on the device-side queue lengths: no
             // host round trip until the set is done
-            const uint32_t gdepth = std::min(guide_depth(gd), max_depth);
             for (uint32_t v = 1; v <= max_depth + 1; ++v) {
                 tk.ext<<<tk.grid_ext, gbk, 0, st>>>(s->dev, gpool, nullptr);
                 // the network runs only where a continuation is guided: not
@@ -2141,8 +2151,13 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
                                                                             guide_err(gd));
                     stats.kernel_launches += 1;
                 }
-                k_shade_guided<<<g_shade, gbk, 0, st>>>(P, gpool, av > 0.f ? rc->gfeat : nullptr, av, rc->grec,
-                                                        rec_stride, rec_paths, glo, ghi);
+                if (v <= rec_depth + 1) {
+                    // guided, or finishing the records of the vertex before
+                    k_shade_guided<<<g_shade, gbk, 0, st>>>(P, gpool, av > 0.f ? rc->gfeat : nullptr, av, rc->grec,
+                                                            rec_stride, rec_paths, rec_depth, glo, ghi);
+                } else {
+                    (s->dev.lb_rec ? k_shade<true> : k_shade<false>)<<<g_shade_plain, gbk, 0, st>>>(P, gpool, nullptr);
+                }
                 tk.shadow<<<tk.grid_shadow, gbk, 0, st>>>(s->dev, gpool, nullptr);
                 k_step_end<<<1, 1, 0, st>>>(gpool);
                 stats.kernel_launches += 4;
@@ -2990,7 +3005,7 @@ __global__ void __launch_bounds__(kGuidedShadeThreads, 6) k_batchg_shade(const B
             ShadowRay sh;
             GuideRecord gr;
             const uint32_t v = s.depth;
-            const bool want = recording && v <= kGuideMaxRec;
+            const bool want = recording && v <= min(kGuideMaxRec, G.depth);
             const float a = G.guided && s.depth <= G.depth ? alpha[j] : 0.f;
             r = shade<true, MixtureStrided>(P, s, h, sh, a > 0.f ? raw + (size_t)kGuideOut * q : nullptr, a,
                                             want ? &gr : nullptr, G.lo, G.hi, mix);
