@@ -410,14 +410,14 @@ rt_status rt_divide_u64_host(const uint64_t *n, int64_t count, uint32_t d, uint6
  * accumulation on the tensor cores -> 8-lobe von Mises-Fisher mixture,
  * combined with BSDF sampling by one-sample MIS (mixture probability
  * `alpha`). Trained with Adam on up to `batch` radiance samples after each
- * iteration set. A set renders 16 x `batch` paths
- * (rt_render_opts.max_paths_in_flight sets this size). For the first
- * `warm_steps` steps (the warm-up) a set renders at most `warm_set_batches`
- * x `batch` of them, records training samples from more of its paths and is
- * followed by up to `warm_set_batches` steps, each on its own `batch` of
- * those samples; until the first step the proposal is BSDF sampling alone.
- * After the warm-up one step on one batch follows every `train_every`-th
- * set. */
+ * iteration set. For the first `warm_steps` steps (the warm-up) a set
+ * renders at most min(`warm_set_batches`, 16) x `batch` paths, records
+ * training samples from more of its paths and is followed by up to
+ * `warm_set_batches` steps, each on its own `batch` of those samples; until
+ * the first step the proposal is BSDF sampling alone. After the warm-up a
+ * set renders up to 64 x `batch` paths (rt_render_opts.max_paths_in_flight
+ * sets this size) and every `train_every`-th set is followed by one step per
+ * 16 x `batch` paths it rendered (at least one, at most four). */
 typedef struct {
     uint32_t batch;          /* training samples per pass (0 = 65536) */
     float learning_rate;     /* Adam lr (0 = 1e-2) */

@@ -2077,29 +2077,33 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         // step the proposal is BSDF-only.
         rt_guide *gd = o.guide;
         const uint32_t batch = guide_batch(gd);
-        // Iteration sets: while the proposal is young (fewer than its warm-up
-        // training steps) a set holds `wsb` training batches of paths, every
-        // path of it records its vertices, and up to `wsb` steps follow, each
-        // on a batch of its own, so that the proposal learns fast while the
-        // per-set launches and the host round trip are spread over several
-        // steps; then 16 batches (2^20 paths by default;
-        // max_paths_in_flight sets this size) with one step on `batch` of
-        // their samples.
+        // Iteration sets. While the proposal is young (fewer than its warm-up
+        // training steps) a set holds at most min(wsb, 16) batches of paths
+        // and up to wsb training steps follow, each on its own batch of the
+        // set's samples, so that it learns fast (until the first step the
+        // proposal is BSDF sampling alone). Later a set holds up to 64
+        // batches of paths (max_paths_in_flight sets this size) and one step
+        // follows per 16 batches rendered, so that the per-set launches,
+        // their drains and the host round trip are spread over more paths at
+        // the same training rate.
+        if (batch > (1u << 24)) { set_error("rt_render: guide batch above 2^24 samples"); return RT_INVALID_ARG; }
+        const uint32_t per_step = 16u * std::max(batch, 32u);   // paths rendered per training step after the warm-up
         const uint32_t cap_full = cap;
         const uint32_t wsb = std::max(1u, guide_warm_set_batches(gd));
-        if (!o.max_paths_in_flight) cap = std::min<uint64_t>(cap, 16ull * std::max(batch, 32u));
-        const uint32_t cap_young = (uint32_t)std::min<uint64_t>(cap, (uint64_t)std::max(batch, 32u) * wsb);
+        if (!o.max_paths_in_flight) cap = std::min<uint64_t>(cap, 64ull * std::max(batch, 32u));
+        const uint32_t cap_young =
+            (uint32_t)std::min<uint64_t>({(uint64_t)cap, (uint64_t)per_step, (uint64_t)std::max(batch, 32u) * wsb});
         // training records come from the guided vertices 1..gdepth only (the
         // network is asked about no other). Samples kept: up to wsb batches
-        // after a young set, one batch later. Recording paths: in a young set
+        // after a young set, up to four later. Recording paths: in a young set
         // enough for its samples at min(4, rec_depth) samples per path, later
         // `batch`; the record buffer holds the larger of the two.
         const uint32_t gdepth = std::min(guide_depth(gd), max_depth);
         const uint32_t rec_depth = std::min(gdepth, kGuideMaxRec);
         const uint32_t keep_young = (uint32_t)std::min<uint64_t>((uint64_t)batch * wsb, 1ull << 28);
         const uint32_t rec_young = std::max(1u, keep_young / std::max(1u, std::min(4u, rec_depth)));
-        if ((rs = ensure_guided(rc, cap_full, std::max(batch, rec_young), std::max(batch, keep_young))) != RT_OK)
-            return rs;
+        const uint32_t keep_max = std::max(4u * batch, keep_young);
+        if ((rs = ensure_guided(rc, cap_full, std::max(batch, rec_young), keep_max)) != RT_OK) return rs;
         rc->pool.view.nrec = rc->gnrec;
         Pool gpool = rc->pool.view;
         gpool.qd = nullptr;      // no regeneration: ended paths are not queued
@@ -2134,7 +2138,8 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
             // recording paths and the samples kept (both within the buffers
             // sized above): every rec_stride-th path records
             const bool young = guide_young(gd);
-            const uint32_t keep = young ? std::max(batch, keep_young) : batch;
+            const uint32_t set_steps = std::min(4u, std::max(1u, n / per_step));   // trained phase
+            const uint32_t keep = young ? std::max(batch, keep_young) : set_steps * batch;
             const uint32_t rec_paths = young ? std::max(batch, rec_young) : batch;
             const uint32_t rec_stride = std::max(1u, n / rec_paths);
             k_raygen<<<g_ray, 256, 0, st>>>(P, gpool, t, n, (uint32_t)WH, 0u);
@@ -2180,8 +2185,9 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
             const uint32_t n_train = std::min(rc->host_ctrl->n_train, keep);
             if (n_train >= 256 && guide_should_train(gd)) {
                 // one training call per full batch (a young set: at most the
-                // warm-up calls still to take), else one on what there is
-                const uint32_t steps = young ? std::max(1u, std::min(n_train / batch, guide_warm_left(gd))) : 1u;
+                // warm-up calls still to take; later one per 16 batches of
+                // paths rendered), else one on what there is
+                const uint32_t steps = std::max(1u, std::min(n_train / batch, young ? guide_warm_left(gd) : set_steps));
                 for (uint32_t k = 0; k < steps; ++k) {
                     const size_t off = (size_t)k * batch;
                     const uint32_t m = steps > 1 ? batch : std::min(n_train, batch);

@@ -46,7 +46,8 @@ def test_guided_render_is_consistent_with_the_oracle(pool, gdepth, warm):
     # transient (the plain tracer fails it at 128 spp just the same)
     rt.rt_render(scene, cam, 1024, 8, film, rt.make_opts(guide=guide, stats=stats, max_paths=pool))
     torch.cuda.synchronize()
-    assert stats.waves >= 4
+    # a warm-up set, then at least one trained set (16 spp each with pool 65536)
+    assert stats.waves >= 2
     assert not np.array_equal(p0, guide.get_params())   # trained during the render
     s, s2, c = film.download()
     assert np.all(c == 1024)
