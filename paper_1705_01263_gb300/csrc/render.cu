@@ -1082,6 +1082,7 @@ __device__ __forceinline__ bool recording_path(uint32_t q, uint32_t rec_stride, 
 // mixture in the block's shared memory (24 KB).
 constexpr uint32_t kGuidedShadeThreads = 128;
 
+template <bool kLb>
 __global__ void __launch_bounds__(kGuidedShadeThreads, 6) k_shade_guided(RenderParams P, Pool pool, const __nv_bfloat16 *raw, float alpha,
                                                       float4 *rec, uint32_t rec_stride, uint32_t rec_paths,
                                                       uint32_t rec_depth, float3 lo, float3 hi) {
@@ -1119,8 +1120,8 @@ __global__ void __launch_bounds__(kGuidedShadeThreads, 6) k_shade_guided(RenderP
             GuideRecord gr;
             const uint32_t v = s.depth;
             const bool want = recording && v <= rec_depth;
-            r = shade<true, MixtureStrided>(P, s, h, sh, raw ? raw + (size_t)kGuideOut * i : nullptr, alpha,
-                                            want ? &gr : nullptr, lo, hi, mix);
+            r = shade<kLb, MixtureStrided>(P, s, h, sh, raw ? raw + (size_t)kGuideOut * i : nullptr, alpha,
+                                           want ? &gr : nullptr, lo, hi, mix);
             pool.L[q] = make_float4(s.L.x, s.L.y, s.L.z, __uint_as_float(s.prev_n));
             if (r & 1) {
                 pool.ray_o[q] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.prev_cell));
@@ -2114,7 +2115,9 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         const int gbk = (int)kGuidedShadeThreads;
         const int g_ray = grid_for(k_raygen, 256, cap);
         const TraceKernels tk = trace_kernels(false, 0, s->dev.two_level, gbk);
-        const int g_shade = grid_persistent(k_shade_guided, gbk, 0);
+        // both kernels compiled with and without the light hierarchy
+        const auto shade_guided = s->dev.lb_rec ? k_shade_guided<true> : k_shade_guided<false>;
+        const int g_shade = grid_persistent(shade_guided, gbk, 0);
         const int g_shade_plain = grid_persistent(k_shade<true>, gbk, 0);
         if ((rs = mlp_kernel_attr((const void *)k_guide_mlp_paths, kMlpInferSmem)) != RT_OK) return rs;
         const PathFeatures pf{P, gpool, glo, ghi};
@@ -2158,8 +2161,8 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
                 }
                 if (v <= rec_depth + 1) {
                     // guided, or finishing the records of the vertex before
-                    k_shade_guided<<<g_shade, gbk, 0, st>>>(P, gpool, av > 0.f ? rc->gfeat : nullptr, av, rc->grec,
-                                                            rec_stride, rec_paths, rec_depth, glo, ghi);
+                    shade_guided<<<g_shade, gbk, 0, st>>>(P, gpool, av > 0.f ? rc->gfeat : nullptr, av, rc->grec,
+                                                          rec_stride, rec_paths, rec_depth, glo, ghi);
                 } else {
                     (s->dev.lb_rec ? k_shade<true> : k_shade<false>)<<<g_shade_plain, gbk, 0, st>>>(P, gpool, nullptr);
                 }
