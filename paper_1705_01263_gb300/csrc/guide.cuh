@@ -115,8 +115,9 @@ RT_HD void decode_mixture(const T *raw, M &m) {
     for (int k = 0; k < kGuideLobes; ++k) {
         const T *rr = raw + 5 * k;
         const float r[4] = {raw_value(rr[0]), raw_value(rr[1]), raw_value(rr[2]), raw_value(rr[3])};
-        float l = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-        const V3 mu = l > 0.f ? v3(r[0] / l, r[1] / l, r[2] / l) : v3(0.f, 0.f, 1.f);
+        const float l = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        const float il = l > 0.f ? 1.f / l : 0.f;
+        const V3 mu = l > 0.f ? v3(r[0] * il, r[1] * il, r[2] * il) : v3(0.f, 0.f, 1.f);
         m.at(k, 0) = mu.x;
         m.at(k, 1) = mu.y;
         m.at(k, 2) = mu.z;
@@ -125,10 +126,12 @@ RT_HD void decode_mixture(const T *raw, M &m) {
         m.at(k, 4) = w;
         z += w;
     }
+    const float iz = 1.f / z;
     for (int k = 0; k < kGuideLobes; ++k) {
-        const float w = m.at(k, 4) / z, kap = m.at(k, 3);
+        const float w = m.at(k, 4) * iz, kap = m.at(k, 3);
         m.at(k, 4) = w;
-        m.at(k, 5) = w * kap / (2.f * kPi * -expm1f(-2.f * kap));
+        // 1 - e^{-2 kappa} rounds to 1 in FP32 once kappa > 9
+        m.at(k, 5) = w * kap / (2.f * kPi * (kap > 9.f ? 1.f : -expm1f(-2.f * kap)));
     }
 }
 
