@@ -3439,11 +3439,20 @@ static rt_status render_batch_guided(const rt_render_job *jobs, int32_t njobs, c
     RT_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     cudaMemsetAsync(ntrain, 0, sizeof(uint32_t) * (size_t)njobs, cs);
     k_batchg_raygen<<<g_ray, 256, 0, cs>>>(djobs, dblocks, nb, dctl, pool, job_of);
+    // the guided jobs' networks run at their vertices 1..guide depth (paths
+    // of a set advance one vertex per bounce step)
+    uint32_t max_gdepth = 0, net_launches = 0;
+    for (int32_t j = 0; j < njobs; ++j)
+        if (jobs[j].guide) {
+            const uint32_t d = std::min(guide_depth(jobs[j].guide), jobs[j].max_depth);
+            max_gdepth = std::max(max_gdepth, d);
+            net_launches += d;
+        }
     for (uint32_t v = 1; v <= maxd + 1; ++v) {
         k_batch_trace<false><<<g_trace, gb, 0, cs>>>(djobs, pool, job_of);
-        if (v <= maxd) {
+        if (v <= maxd && v <= max_gdepth) {
             // the network of each guided job over its paths (not at the last
-            // vertex, which only adds emission)
+            // vertex, which only adds emission, nor past its guide depth)
             cudaMemsetAsync(hist, 0, sizeof(uint32_t) * nkeys, cs);
             k_sort_hist<GuidedJobKey><<<g_hist, 256, nkeys * sizeof(uint32_t), cs>>>(key, pool, nkeys, hist);
             k_sort_scan<<<1, 1024, 0, cs>>>(pool, nkeys, hist);
@@ -3454,7 +3463,7 @@ static rt_status render_batch_guided(const rt_render_job *jobs, int32_t njobs, c
             for (int b = 0; b < kSide; ++b) RT_CUDA_TRY(cudaStreamWaitEvent(side[b], fork_ev, 0));
             int k = 0;
             for (int32_t j = 0; j < njobs; ++j) {
-                if (!jobs[j].guide) continue;
+                if (!jobs[j].guide || v > std::min(guide_depth(jobs[j].guide), jobs[j].max_depth)) continue;
                 const JobPathFeatures pf{djobs, dguides, pool, sorted, starts, hist, dalpha, (uint32_t)j};
                 k_guide_mlp_job<<<sm_count(), kMiThreads, kMlpInferSmem, side[k++ % kSide]>>>(
                     guide_weights(jobs[j].guide), pf, raw, guide_err(jobs[j].guide));
@@ -3484,7 +3493,7 @@ static rt_status render_batch_guided(const rt_render_job *jobs, int32_t njobs, c
     // memset, raygen; per bounce step trace, shade, shadow, step end, and
     // before each shade but the last the job sort (5) and the networks; film,
     // collect, advance
-    const uint32_t launches_per_set = 2 + 4 * (maxd + 1) + maxd * (5 + nguided) + 3;
+    const uint32_t launches_per_set = 2 + 4 * (maxd + 1) + std::min(maxd, max_gdepth) * 5 + net_launches + 3;
     std::vector<uint32_t> ntrain_h((size_t)njobs);
     rt_stats stats{};
     rt_status result = RT_OK;
