@@ -426,7 +426,7 @@ typedef struct {
     uint64_t seed;           /* weight initialisation seed */
     uint32_t train_every;    /* after the warm-up steps, train after every train_every-th set (0 = 1) */
     uint32_t guide_depth;    /* guide the continuation of vertices 1..guide_depth only, BSDF
-                              * sampling beyond (0 = 4; max_depth or more: every vertex);
+                              * sampling beyond (0 = 3; max_depth or more: every vertex);
                               * training records come from those vertices (at most 8) */
     uint32_t warm_steps;     /* training steps taken with small sets before the large ones (0 = 32) */
     uint32_t warm_set_batches; /* training batches (steps) per warm-up set (0 = 32; 1: one step

@@ -408,7 +408,7 @@ extern "C" rt_status rt_guide_create(const rt_scene *scene, const rt_guide_opts 
     if (!g->opts.train_steps) g->opts.train_steps = 1;
     if (!g->opts.warm_steps) g->opts.warm_steps = 32;
     if (!g->opts.warm_set_batches) g->opts.warm_set_batches = 32;
-    if (!g->opts.guide_depth) g->opts.guide_depth = 4;
+    if (!g->opts.guide_depth) g->opts.guide_depth = 3;
     g->nparams = kGuideParams;
     if (scene) { g->bb_lo = scene->dev.bb_lo; g->bb_hi = scene->dev.bb_hi; }
     else { g->bb_lo = make_float3(0.f, 0.f, 0.f); g->bb_hi = make_float3(1.f, 1.f, 1.f); }

@@ -34,7 +34,7 @@ def test_guided_render_is_consistent_with_the_oracle(pool, gdepth, warm):
     """pool 0: the library's iteration sets; 65536: 16 spp per set, so that
     a training step follows every set; gdepth 1 or 2: only the first vertices
     guided (BSDF sampling and its MIS weights beyond them); 0: the default
-    (vertices 1-4); 64: every vertex."""
+    (vertices 1-3); 64: every vertex."""
     from paper_1705_01263_gb300 import rt
     sd, cam = scenes.cornell_box()
     scene = rt.Scene(sd)
