@@ -2102,7 +2102,8 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         const uint32_t gdepth = std::min(guide_depth(gd), max_depth);
         const uint32_t rec_depth = std::min(gdepth, kGuideMaxRec);
         const uint32_t keep_young = (uint32_t)std::min<uint64_t>((uint64_t)batch * wsb, 1ull << 28);
-        const uint32_t rec_young = std::max(1u, keep_young / std::max(1u, std::min(4u, rec_depth)));
+        const uint32_t rec_young =
+            std::max(1u, std::min(cap_young, keep_young / std::max(1u, std::min(4u, rec_depth))));
         const uint32_t keep_max = std::max(4u * batch, keep_young);
         if ((rs = ensure_guided(rc, cap_full, std::max(batch, rec_young), keep_max)) != RT_OK) return rs;
         rc->pool.view.nrec = rc->gnrec;
