@@ -2071,11 +2071,10 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
     rt_status result = RT_OK;
     if (o.guide) {
         // Guided iteration sets: every bounce step reads the queue length,
-        // runs the network on the queue's vertices, shades with the
-        // one-sample MIS mixture and records training samples; each set ends
-        // with one training step on up to `batch` samples. The megakernel
-        // tail is off (it has no guided branch). Until the first training
-        // step the proposal is BSDF-only.
+        // runs the network on the queue's vertices (vertices 1..gdepth),
+        // shades with the one-sample MIS mixture and records training
+        // samples; training steps follow the set (below). The megakernel
+        // tail is off (it has no guided branch).
         rt_guide *gd = o.guide;
         const uint32_t batch = guide_batch(gd);
         // Iteration sets. While the proposal is young (fewer than its warm-up
