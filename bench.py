@@ -562,11 +562,12 @@ def batched(spp_divisor=16):
     ev1.record()
     ev1.synchronize()
     ms = ev0.elapsed_time(ev1)
-    # the same batch with a guiding network on every job (each trained from
-    # scratch during the call): one shared wavefront over the jobs' tasks
-    # interleaved image by image, one network launch per job and bounce step,
-    # training after every set of 2^21 paths (every 4th set after 8 warm-up
-    # steps)
+    # the same batch with a guiding network on every 8th job and on every
+    # job (each trained from scratch during the call): one shared wavefront
+    # over the jobs' tasks interleaved image by image, sets of 2^23 paths, one
+    # network launch per job and guided bounce step, 8 warm-up steps (one
+    # after each set), then one step per 2^20 of the job's paths (every 4th
+    # such step taken)
     with_guides = {}
     for every in (8, 1):
         for f in films:

@@ -3337,9 +3337,12 @@ static rt_status render_batch_guided(const rt_render_job *jobs, int32_t njobs, c
             b.chunk = c;
             blocks.push_back(b);
         }
-    // set size: the user's pool, else 2^21 paths (training follows every set)
+    // set size: the user's pool, else 2^23 paths (the per-set graph replay,
+    // host round trip and launch drains spread over more paths; measured for
+    // 64 jobs with 8 / 64 guided: 2^21 363 / 253, 2^22 418 / 301, 2^23 462 /
+    // 333 Mpaths/s)
     const uint32_t cap = std::max<uint32_t>(
-        32u, (uint32_t)std::min<uint64_t>(total, o.max_paths_in_flight ? o.max_paths_in_flight : (1u << 21)));
+        32u, (uint32_t)std::min<uint64_t>(total, o.max_paths_in_flight ? o.max_paths_in_flight : (1u << 23)));
     // guides: bounds, training batches, mixture probabilities
     uint32_t nguided = 0;
     std::vector<float> alpha_h((size_t)njobs, 0.f);
@@ -3495,11 +3498,28 @@ static rt_status render_batch_guided(const rt_render_job *jobs, int32_t njobs, c
     // collect, advance
     const uint32_t launches_per_set = 2 + 4 * (maxd + 1) + std::min(maxd, max_gdepth) * 5 + net_launches + 3;
     std::vector<uint32_t> ntrain_h((size_t)njobs);
+    // After its warm-up a job's network takes one step per 16 training
+    // batches of its own paths rendered (the single-scene schedule), not one
+    // per set: its paths in set s are the overlap of its blocks with the
+    // set's task range [s cap, (s + 1) cap).
+    std::vector<uint64_t> since_step((size_t)njobs, 0);
+    std::vector<uint64_t> in_set((size_t)njobs);
+    auto block_len = [&](const BatchBlock &b) {
+        return std::min<uint64_t>(hj[b.job].WH, hj[b.job].ntask - (uint64_t)b.chunk * hj[b.job].WH);
+    };
     rt_stats stats{};
     rt_status result = RT_OK;
     uint64_t done_sets = 0;
     const auto t_start = std::chrono::steady_clock::now();
     for (; done_sets < sets; ++done_sets) {
+        {
+            std::fill(in_set.begin(), in_set.end(), 0);
+            const uint64_t s0 = done_sets * cap, s1 = std::min<uint64_t>(total, s0 + cap);
+            for (const BatchBlock &b : blocks) {
+                const uint64_t a = std::max(b.off, s0), e = std::min(b.off + block_len(b), s1);
+                if (a < e) in_set[b.job] += e - a;
+            }
+        }
         ce = cudaGraphLaunch(exec, st);
         if (ce != cudaSuccess) { result = cuda_status(ce, "rt_render_batch: graph launch"); break; }
         stats.kernel_launches += launches_per_set;
@@ -3516,7 +3536,11 @@ static rt_status render_batch_guided(const rt_render_job *jobs, int32_t njobs, c
             if (!gd) continue;
             if ((rs = guide_check(gd, st)) != RT_OK) return rs;
             const uint32_t nt = std::min(ntrain_h[(size_t)j], hg[(size_t)j].batch);
-            if (nt >= 256 && guide_should_train(gd)) {
+            since_step[(size_t)j] += in_set[(size_t)j];
+            const uint64_t per_step = 16ull * std::max(guide_batch(gd), 32u);
+            const bool due = guide_young(gd) || since_step[(size_t)j] >= per_step;
+            if (nt >= 256 && due && guide_should_train(gd)) {
+                since_step[(size_t)j] = guide_young(gd) ? 0 : since_step[(size_t)j] - per_step;
                 const BatchGuide &G = hg[(size_t)j];
                 if ((rs = guide_train_async(gd, G.tr_feat, G.tr_wi, G.tr_w, nt, side[k++ % kSide])) != RT_OK) return rs;
                 stats.kernel_launches += 40;
