@@ -365,10 +365,15 @@ rt_status rt_render_static(const rt_scene *scene, const rt_camera *camera, uint3
  * additions: equal to rt_render up to FP64 addition order). Blocking;
  * RT_TIMEOUT when the abort flag or time budget stopped it between sets
  * (films hold the completed tasks). A job may carry its own guiding network
- * (`guide`, or NULL): such jobs are rendered inside the call after the
- * shared wavefront, one after another through the guided path (each needs its
- * own network in its inference and training launches); opts->guide must be
- * NULL. */
+ * (`guide`, or NULL; opts->guide must be NULL). A call with guided jobs
+ * renders all its jobs in one shared wavefront of iteration sets (2^23 paths
+ * unless opts->max_paths_in_flight is set; the jobs' tasks interleaved image
+ * by image): before each guided bounce step the queue is sorted by job and
+ * each guided job's network runs on its paths; after each set the due jobs
+ * take a training step on their own samples (every set during a job's
+ * warm-up, then one per 16 x `batch` of its paths rendered, subject to
+ * `train_every`). Unguided jobs in such a call give the films they would
+ * give alone, bit for bit. */
 typedef struct {
     const rt_scene *scene;
     rt_camera camera;
