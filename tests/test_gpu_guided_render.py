@@ -116,6 +116,31 @@ def test_guided_render_consistent_in_the_room_lit_through_a_door():
     assert res["guided"][0] <= max(allowed_4sigma(mr.size), 2 * res["plain"][0]), res
 
 
+@pytest.mark.parametrize("wsb", [1, 4])
+def test_warm_up_schedules_train_and_stay_consistent(wsb):
+    """Warm-up sets of `wsb` training batches (1: a step after each set of
+    2^16 paths): the network takes its warm-up steps and the image agrees in
+    mean with the plain tracer's."""
+    from paper_1705_01263_gb300 import rt
+    sd, cam = scenes.cornell_box(light="up")
+    scene = rt.Scene(sd)
+    guide = rt.Guide(scene, seed=9, warm_set_batches=wsb, warm_steps=8)
+    p0 = guide.get_params()
+    a = rt.Film(cam.width, cam.height)
+    b = rt.Film(cam.width, cam.height)
+    stats = rt.rt_stats()
+    rt.rt_render(scene, cam, 512, 8, a, rt.make_opts(guide=guide, stats=stats))
+    rt.rt_render(scene, cam, 512, 8, b)
+    torch.cuda.synchronize()
+    assert not np.array_equal(p0, guide.get_params())
+    assert stats.waves >= 2
+    ma, va = oracle.resolve(*a.download())
+    mb, vb = oracle.resolve(*b.download())
+    d = abs(ma.mean() - mb.mean())
+    s_tot = np.sqrt(va.sum() + vb.sum()) / ma.size
+    assert d <= 4 * s_tot + 1e-4 * mb.mean(), (d, s_tot)
+
+
 def test_guided_and_plain_agree_in_mean():
     from paper_1705_01263_gb300 import rt
     sd, cam = scenes.cornell_box()
