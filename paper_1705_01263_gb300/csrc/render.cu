@@ -1418,6 +1418,62 @@ struct RenderCache {
     }
 };
 
+// The set sizes and buffer sizes of a guided render (host arithmetic, also
+// run by the host test hook). While the proposal is young (fewer than its
+// warm-up training steps) a set holds at most min(wsb, 16) batches of paths
+// and up to wsb training steps follow, each on its own batch of the set's
+// samples, so that it learns fast (until the first step the proposal is BSDF
+// sampling alone). Later a set holds up to 64 batches of paths (a caller's
+// max_paths_in_flight sets this size instead) and one step follows per 16
+// batches rendered, so that the per-set launches, their drains and the host
+// round trip are spread over more paths at the same training rate. Training
+// records come from the guided vertices 1..gdepth only (the network is asked
+// about no other); a young set records from enough paths for its samples at
+// min(4, rec_depth) samples per path, a later one from `batch` paths.
+struct GuidedPlan {
+    uint32_t cap;          // paths per set after the warm-up
+    uint32_t cap_young;    // paths per warm-up set
+    uint32_t per_step;     // paths rendered per training step after the warm-up
+    uint32_t gdepth;       // last guided vertex
+    uint32_t rec_depth;    // last recorded vertex
+    uint32_t keep_young;   // samples kept after a warm-up set
+    uint32_t rec_young;    // recording paths of a warm-up set
+    uint32_t rec_alloc;    // recording paths the record buffer holds
+    uint32_t keep_alloc;   // samples the training buffers hold
+};
+struct GuidedSet {
+    uint32_t keep;         // samples kept after this set
+    uint32_t rec_paths;    // recording paths (every rec_stride-th path)
+    uint32_t rec_stride;
+    uint32_t set_steps;    // training steps due after a trained-phase set
+};
+// batch <= 2^24 (checked by the caller); cap = the pool's paths per set
+// before the guided limit; fixed_pool: the caller set max_paths_in_flight.
+static GuidedPlan guided_plan(uint32_t batch, uint32_t wsb, uint32_t guide_depth, uint32_t max_depth, uint32_t cap,
+                              bool fixed_pool) {
+    GuidedPlan g;
+    wsb = std::max(1u, wsb);
+    g.per_step = 16u * std::max(batch, 32u);
+    g.cap = fixed_pool ? cap : (uint32_t)std::min<uint64_t>(cap, 64ull * std::max(batch, 32u));
+    g.cap_young = (uint32_t)std::min<uint64_t>({(uint64_t)g.cap, (uint64_t)g.per_step,
+                                                (uint64_t)std::max(batch, 32u) * wsb});
+    g.gdepth = std::min(guide_depth, max_depth);
+    g.rec_depth = std::min(g.gdepth, kGuideMaxRec);
+    g.keep_young = (uint32_t)std::min<uint64_t>((uint64_t)batch * wsb, 1ull << 28);
+    g.rec_young = std::max(1u, std::min(g.cap_young, g.keep_young / std::max(1u, std::min(4u, g.rec_depth))));
+    g.rec_alloc = std::max(batch, g.rec_young);
+    g.keep_alloc = std::max(4u * batch, g.keep_young);
+    return g;
+}
+static GuidedSet guided_set(const GuidedPlan &g, uint32_t batch, uint32_t n, bool young) {
+    GuidedSet e;
+    e.set_steps = std::min(4u, std::max(1u, n / g.per_step));
+    e.keep = young ? std::max(batch, g.keep_young) : e.set_steps * batch;
+    e.rec_paths = young ? std::max(batch, g.rec_young) : batch;
+    e.rec_stride = std::max(1u, n / e.rec_paths);
+    return e;
+}
+
 // Guided-rendering buffers: network rows for `cap` paths, training records
 // of `rec_paths` paths and `samples` training samples.
 static rt_status ensure_guided(RenderCache *rc, uint32_t cap, uint32_t rec_paths, uint32_t samples) {
@@ -2077,34 +2133,14 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
         // tail is off (it has no guided branch).
         rt_guide *gd = o.guide;
         const uint32_t batch = guide_batch(gd);
-        // Iteration sets. While the proposal is young (fewer than its warm-up
-        // training steps) a set holds at most min(wsb, 16) batches of paths
-        // and up to wsb training steps follow, each on its own batch of the
-        // set's samples, so that it learns fast (until the first step the
-        // proposal is BSDF sampling alone). Later a set holds up to 64
-        // batches of paths (max_paths_in_flight sets this size) and one step
-        // follows per 16 batches rendered, so that the per-set launches,
-        // their drains and the host round trip are spread over more paths at
-        // the same training rate.
+        // iteration sets, training schedule and buffer sizes: guided_plan
         if (batch > (1u << 24)) { set_error("rt_render: guide batch above 2^24 samples"); return RT_INVALID_ARG; }
-        const uint32_t per_step = 16u * std::max(batch, 32u);   // paths rendered per training step after the warm-up
         const uint32_t cap_full = cap;
-        const uint32_t wsb = std::max(1u, guide_warm_set_batches(gd));
-        if (!o.max_paths_in_flight) cap = std::min<uint64_t>(cap, 64ull * std::max(batch, 32u));
-        const uint32_t cap_young =
-            (uint32_t)std::min<uint64_t>({(uint64_t)cap, (uint64_t)per_step, (uint64_t)std::max(batch, 32u) * wsb});
-        // training records come from the guided vertices 1..gdepth only (the
-        // network is asked about no other). Samples kept: up to wsb batches
-        // after a young set, up to four later. Recording paths: in a young set
-        // enough for its samples at min(4, rec_depth) samples per path, later
-        // `batch`; the record buffer holds the larger of the two.
-        const uint32_t gdepth = std::min(guide_depth(gd), max_depth);
-        const uint32_t rec_depth = std::min(gdepth, kGuideMaxRec);
-        const uint32_t keep_young = (uint32_t)std::min<uint64_t>((uint64_t)batch * wsb, 1ull << 28);
-        const uint32_t rec_young =
-            std::max(1u, std::min(cap_young, keep_young / std::max(1u, std::min(4u, rec_depth))));
-        const uint32_t keep_max = std::max(4u * batch, keep_young);
-        if ((rs = ensure_guided(rc, cap_full, std::max(batch, rec_young), keep_max)) != RT_OK) return rs;
+        const GuidedPlan gp = guided_plan(batch, guide_warm_set_batches(gd), guide_depth(gd), max_depth, cap,
+                                          o.max_paths_in_flight != 0);
+        cap = gp.cap;
+        const uint32_t cap_young = gp.cap_young, gdepth = gp.gdepth, rec_depth = gp.rec_depth;
+        if ((rs = ensure_guided(rc, cap_full, gp.rec_alloc, gp.keep_alloc)) != RT_OK) return rs;
         rc->pool.view.nrec = rc->gnrec;
         Pool gpool = rc->pool.view;
         gpool.qd = nullptr;      // no regeneration: ended paths are not queued
@@ -2141,10 +2177,9 @@ extern "C" rt_status rt_render(const rt_scene *s, const rt_camera *cam, uint32_t
             // recording paths and the samples kept (both within the buffers
             // sized above): every rec_stride-th path records
             const bool young = guide_young(gd);
-            const uint32_t set_steps = std::min(4u, std::max(1u, n / per_step));   // trained phase
-            const uint32_t keep = young ? std::max(batch, keep_young) : set_steps * batch;
-            const uint32_t rec_paths = young ? std::max(batch, rec_young) : batch;
-            const uint32_t rec_stride = std::max(1u, n / rec_paths);
+            const GuidedSet gs = guided_set(gp, batch, n, young);
+            const uint32_t set_steps = gs.set_steps, keep = gs.keep, rec_paths = gs.rec_paths,
+                           rec_stride = gs.rec_stride;
             k_raygen<<<g_ray, 256, 0, st>>>(P, gpool, t, n, (uint32_t)WH, 0u);
             stats.kernel_launches += 1;
             // every bounce step runs on the device-side queue lengths: no
@@ -3725,5 +3760,25 @@ extern "C" rt_status rt_debug_regen_host(uint32_t n_tasks, uint32_t cap, uint32_
     }
     *steps = step;
     *regen_steps = c.regen_sets;
+    return RT_OK;
+}
+
+// Host test hook: the guided render's set and buffer sizes for a pool of
+// `cap` paths per set (fixed_pool: the caller set max_paths_in_flight) and a
+// set of n paths, young or not. out[13] = cap, cap_young, per_step, gdepth,
+// rec_depth, keep_young, rec_young, rec_alloc, keep_alloc, keep, rec_paths,
+// rec_stride, set_steps. Never called by the product entry points.
+extern "C" rt_status rt_debug_guided_plan_host(uint32_t batch, uint32_t wsb, uint32_t guide_depth, uint32_t max_depth,
+                                               uint32_t cap, int32_t fixed_pool, uint32_t n, int32_t young,
+                                               uint32_t *out) {
+    if (!out || batch == 0 || batch > (1u << 24) || cap < 32 || n == 0) {
+        set_error("rt_debug_guided_plan_host: invalid argument");
+        return RT_INVALID_ARG;
+    }
+    const GuidedPlan g = guided_plan(batch, wsb, guide_depth, max_depth, cap, fixed_pool != 0);
+    const GuidedSet e = guided_set(g, batch, n, young != 0);
+    const uint32_t v[13] = {g.cap, g.cap_young, g.per_step, g.gdepth, g.rec_depth, g.keep_young, g.rec_young,
+                            g.rec_alloc, g.keep_alloc, e.keep, e.rec_paths, e.rec_stride, e.set_steps};
+    for (int k = 0; k < 13; ++k) out[k] = v[k];
     return RT_OK;
 }

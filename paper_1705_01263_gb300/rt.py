@@ -139,6 +139,7 @@ def _declare(L):
         "rt_debug_trace_host": [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp],
         "rt_debug_trace_host_stack": [vp, vp, i64, i32, i32, vp, vp],
         "rt_debug_regen_host": [u32, u32, u32, vp, u32, vp, vp, vp],
+        "rt_debug_guided_plan_host": [u32, u32, u32, u32, u32, i32, u32, i32, vp],
         "rt_debug_aim_tree_host": [vp, vp, vp, vp, vp],
         "rt_debug_aim_host": [vp, vp, i32, vp, i64, vp],
         "rt_debug_env_sample_host": [vp, vp, vp, vp, i64, vp, vp, vp],
@@ -628,6 +629,21 @@ def debug_regen_host(life: np.ndarray, cap: int, regen_min: int, stop_step: int 
     check(lib().rt_debug_regen_host(n, cap, regen_min, life.ctypes.data, stop_step, out.ctypes.data,
                                     C.byref(steps), C.byref(regen)))
     return out, steps.value, regen.value
+
+
+GUIDED_PLAN_FIELDS = ("cap", "cap_young", "per_step", "gdepth", "rec_depth", "keep_young", "rec_young",
+                      "rec_alloc", "keep_alloc", "keep", "rec_paths", "rec_stride", "set_steps")
+
+
+def debug_guided_plan_host(batch: int, wsb: int, guide_depth: int, max_depth: int, cap: int, fixed_pool: bool,
+                           n: int, young: bool) -> dict:
+    """Host run of the guided render's set and buffer arithmetic: a dict of
+    GUIDED_PLAN_FIELDS for a pool of `cap` paths per set and a set of n
+    paths."""
+    out = np.zeros(13, np.uint32)
+    check(lib().rt_debug_guided_plan_host(batch, wsb, guide_depth, max_depth, cap, int(fixed_pool), n, int(young),
+                                          out.ctypes.data))
+    return dict(zip(GUIDED_PLAN_FIELDS, (int(x) for x in out)))
 
 
 def debug_aim_tree_host(scene: Scene):

@@ -468,3 +468,35 @@ def test_photon_aiming_host_matches_oracle(name):
     gw = rt.debug_aim_host(s, eye, 3, q)[:, :3]
     ow = np.array([o.pa_cone_sample(0, x[i], q[i, 7], q[i, 8]) for i in range(n)])
     assert np.abs(gw - ow).max() < 2e-4
+
+
+def test_guided_plan_buffers_hold_every_set():
+    """The guided render's set and buffer arithmetic (host hook of the code
+    the render runs): for batches, warm-up sizes, guide depths, pools and set
+    sizes, the recording paths and kept samples of every set fit the buffers,
+    the records cover min(n, recording paths) paths, and the training steps
+    read only kept samples."""
+    from paper_1705_01263_gb300 import rt
+    rng = np.random.default_rng(21)
+    for _ in range(3000):
+        batch = int(rng.choice([256, 1000, 1 << 14, 1 << 16, 1 << 20]))
+        wsb = int(rng.integers(0, 70))
+        gdepth = int(rng.integers(1, 70))
+        max_depth = int(rng.integers(0, 17))
+        cap = int(rng.choice([32, 4096, 65536, 1 << 20, 1 << 24, 1 << 27]))
+        fixed = bool(rng.integers(0, 2))
+        young = bool(rng.integers(0, 2))
+        g = rt.debug_guided_plan_host(batch, wsb, gdepth, max_depth, cap, fixed, 1, young)
+        cset = g["cap_young"] if young else g["cap"]
+        assert 1 <= g["cap_young"] <= g["cap"] <= cap
+        assert g["rec_depth"] <= min(gdepth, max_depth, 8)
+        for n in {1, cset, max(1, cset // 3), int(rng.integers(1, cset + 1))}:
+            e = rt.debug_guided_plan_host(batch, wsb, gdepth, max_depth, cap, fixed, n, young)
+            assert e["rec_paths"] <= e["rec_alloc"], e
+            assert e["keep"] <= e["keep_alloc"], e
+            assert e["rec_stride"] >= 1
+            recorded = min(e["rec_paths"], -(-n // e["rec_stride"]))
+            assert recorded == min(n, e["rec_paths"]), (n, e)
+            assert e["keep"] >= batch
+            if not young:
+                assert 1 <= e["set_steps"] <= 4 and e["set_steps"] * batch <= e["keep"]
